@@ -1,0 +1,253 @@
+/*
+ * FP64 CPU oracle for the line-of-sight projection and the C_l k-integral.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or
+ * call this file; only the tests, the package smoke check and the benchmark's
+ * CPU-baseline leg do.  It shares no code, header, table or helper with the
+ * CUDA library.
+ *
+ * What it computes (arXiv 2509.25110, Sec. 2.1):
+ *   Eq. (2), discretised on the tau nodes with trapezoid weights w_i:
+ *       Delta_l(k) = sum_i  w_i S(k, tau_i) j_l(k (tau0 - tau_i))
+ *   Eq. (1), for X = Y = T, discretised on the k nodes with trapezoid weights
+ *   in u = ln k (the dk/k measure), P = P_R:
+ *       C_l = 4 pi sum_j  w_j P(k_j) Delta_l(k_j)^2
+ * The sums are dense: every tau node is used, no activity cut.
+ *
+ * The paper fixes neither the Bessel kernel's evaluation nor the quadrature
+ * (it names phi_l only as "related to spherical Bessel functions", Sec. 2.1,
+ * and evaluates it inside the line-of-sight loop, Sec. 3.2 / Algorithm 1).
+ * This oracle takes phi_l = j_l (flat space) and evaluates j_l(x) for all
+ * l = 0..lmax at once by
+ *   - Miller's backward recurrence (J. C. P. Miller, British Association
+ *     Mathematical Tables vol. X, 1952; stability: W. Gautschi, SIAM Review 9,
+ *     1967) started far above max(lmax, x), for the orders above x;
+ *   - the forward recurrence from the closed forms of j_0 and j_1 for the
+ *     orders at or below x (x >= 1), where the forward direction is stable;
+ *   - for x < 1, the backward sequence normalised to j_0 = sin(x)/x.
+ * Three-term recurrence used in both directions:
+ *       j_{l-1}(x) + j_{l+1}(x) = (2l+1)/x j_l(x).
+ *
+ * Build: gcc -O2 -fopenmp -shared -fPIC -o liboracle.so gcamb_oracle.c -lm
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* Quadrature weights                                                       */
+/* ------------------------------------------------------------------------ */
+
+/* Trapezoid weights on arbitrary increasing nodes x[0..n-1]:
+ * w_0 = (x_1-x_0)/2, w_i = (x_{i+1}-x_{i-1})/2, w_{n-1} = (x_{n-1}-x_{n-2})/2.
+ * n == 1 gives w_0 = 0 (a single node spans no interval). */
+void orc_trapz_weights(int n, const double *x, double *w)
+{
+    if (n <= 0) return;
+    if (n == 1) { w[0] = 0.0; return; }
+    w[0] = 0.5 * (x[1] - x[0]);
+    for (int i = 1; i < n - 1; ++i) w[i] = 0.5 * (x[i + 1] - x[i - 1]);
+    w[n - 1] = 0.5 * (x[n - 1] - x[n - 2]);
+}
+
+/* Trapezoid weights in u = ln k, for the dk/k measure of Eq. (1). */
+void orc_lnk_weights(int n, const double *k, double *w)
+{
+    if (n <= 0) return;
+    double *u = (double *)malloc(sizeof(double) * (size_t)n);
+    for (int i = 0; i < n; ++i) u[i] = log(k[i]);
+    orc_trapz_weights(n, u, w);
+    free(u);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Spherical Bessel functions j_0..j_lmax at one argument                   */
+/* ------------------------------------------------------------------------ */
+
+/* j[l], l = 0..lmax, for x >= 0. */
+void orc_sph_bessel(int lmax, double x, double *j)
+{
+    if (lmax < 0) return;
+    if (x == 0.0) {
+        j[0] = 1.0;
+        for (int l = 1; l <= lmax; ++l) j[l] = 0.0;
+        return;
+    }
+    /* Orders at or below ls come from the forward recurrence (x >= 1). */
+    int ls = -1;
+    if (x >= 1.0) {
+        double fl = floor(x);
+        ls = fl > (double)lmax ? lmax : (int)fl;
+        double s = sin(x), c = cos(x);
+        j[0] = s / x;
+        if (lmax >= 1) j[1] = (s / x - c) / x;
+        for (int l = 1; l < ls; ++l) j[l + 1] = (2.0 * l + 1.0) / x * j[l] - j[l - 1];
+        if (ls == lmax) return;
+    }
+    /* Backward recurrence from a start far above max(lmax, x). */
+    double big = x > (double)lmax ? ceil(x) : (double)lmax;
+    int Lstart = (int)big + 30 + (int)ceil(2.0 * cbrt(big)) + (int)ceil(sqrt(40.0 * big));
+    int lo = (x < 1.0) ? 0 : ls - 1;      /* lowest order the backward pass reaches */
+    double fhi = 0.0;                      /* f_{l+1} */
+    double f = 1e-300;                     /* f_l, starting at l = Lstart */
+    double f_at_ls = 0.0, f_at_lsm1 = 0.0; /* backward values at the matching pair */
+    /* The backward values for orders above ls are stored straight into j[];
+     * orders ls and ls-1 keep their forward values, their backward values are
+     * kept aside for the normalisation. */
+    for (int l = Lstart; l >= lo; --l) {
+        if (l <= lmax && l > ls) j[l] = f;
+        if (l == ls) f_at_ls = f;
+        if (l == ls - 1) f_at_lsm1 = f;
+        if (x < 1.0 && l <= lmax) j[l] = f;
+        if (l == lo) break;
+        double fm = (2.0 * l + 1.0) / x * f - fhi;   /* f_{l-1} */
+        fhi = f;
+        f = fm;
+        if (fabs(f) > 1e250) {                        /* rescale everything kept */
+            f *= 1e-250;
+            fhi *= 1e-250;
+            int top = Lstart < lmax ? Lstart : lmax;
+            for (int q = l; q <= top; ++q)
+                if (q > ls || x < 1.0) j[q] *= 1e-250;
+            if (l <= ls) f_at_ls *= 1e-250;
+        }
+    }
+    double scale;
+    if (x < 1.0) {
+        double j0 = sin(x) / x;
+        scale = j0 / j[0];
+        int top = Lstart < lmax ? Lstart : lmax;
+        for (int l = 0; l <= top; ++l) j[l] *= scale;
+        for (int l = top + 1; l <= lmax; ++l) j[l] = 0.0;
+        return;
+    }
+    /* Match at whichever of (ls-1, ls) has the larger forward magnitude. */
+    if (fabs(j[ls]) >= fabs(j[ls - 1])) scale = j[ls] / f_at_ls;
+    else scale = j[ls - 1] / f_at_lsm1;
+    int top = Lstart < lmax ? Lstart : lmax;
+    for (int l = ls + 1; l <= top; ++l) j[l] *= scale;
+    for (int l = top + 1; l <= lmax; ++l) j[l] = 0.0;
+}
+
+/* out[n][lmax+1] for many arguments. */
+void orc_sph_bessel_many(int n, const double *x, int lmax, double *out)
+{
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int i = 0; i < n; ++i) orc_sph_bessel(lmax, x[i], out + (size_t)i * (size_t)(lmax + 1));
+}
+
+/* ------------------------------------------------------------------------ */
+/* Line-of-sight transfer (Eq. 2) and C_l (Eq. 1)                           */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * S     [M][nk][ntau]   source function on the nodes
+ * Pk    [M][nk]         primordial spectrum (may be NULL if Cl == NULL)
+ * Delta [M][nk][nl]     output transfer functions, nl = lmax-lmin+1 (may be NULL)
+ * Cl    [M][nl]         output spectra (may be NULL)
+ * wtau, wk: optional caller weights (NULL = trapezoid in tau / in ln k).
+ * Returns 0 on success, -1 on bad arguments.
+ *
+ * Parallel over k; each thread keeps private C_l partial sums, which are added
+ * in thread order at the end.
+ */
+int orc_los_cl(int nk, const double *k, int ntau, const double *tau, double tau0,
+               int lmin, int lmax, int M, const double *S, const double *Pk,
+               const double *wtau_in, const double *wk_in,
+               double *Delta, double *Cl, int nthreads)
+{
+    if (nk < 0 || ntau < 0 || lmin < 0 || lmax < lmin || M < 0) return -1;
+    const int nl = lmax - lmin + 1;
+    double *wtau = (double *)malloc(sizeof(double) * (size_t)(ntau > 0 ? ntau : 1));
+    double *wk = (double *)malloc(sizeof(double) * (size_t)(nk > 0 ? nk : 1));
+    if (wtau_in) memcpy(wtau, wtau_in, sizeof(double) * (size_t)ntau);
+    else orc_trapz_weights(ntau, tau, wtau);
+    if (wk_in) memcpy(wk, wk_in, sizeof(double) * (size_t)nk);
+    else orc_lnk_weights(nk, k, wk);
+    if (Cl) memset(Cl, 0, sizeof(double) * (size_t)M * (size_t)nl);
+
+    int nt = 1;
+#ifdef _OPENMP
+    nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#endif
+    double *clpart = NULL;
+    if (Cl) clpart = (double *)calloc((size_t)nt * (size_t)M * (size_t)nl, sizeof(double));
+
+    #pragma omp parallel num_threads(nt)
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        double *jl = (double *)malloc(sizeof(double) * (size_t)(lmax + 1));
+        double *dk = (double *)malloc(sizeof(double) * (size_t)M * (size_t)nl);
+        #pragma omp for schedule(static)
+        for (int q = 0; q < nk; ++q) {
+            memset(dk, 0, sizeof(double) * (size_t)M * (size_t)nl);
+            for (int i = 0; i < ntau; ++i) {
+                double x = k[q] * (tau0 - tau[i]);
+                orc_sph_bessel(lmax, x, jl);
+                for (int m = 0; m < M; ++m) {
+                    double ws = wtau[i] * S[((size_t)m * nk + q) * ntau + i];
+                    double *d = dk + (size_t)m * nl;
+                    for (int l = lmin; l <= lmax; ++l) d[l - lmin] += ws * jl[l];
+                }
+            }
+            if (Delta)
+                for (int m = 0; m < M; ++m)
+                    memcpy(Delta + ((size_t)m * nk + q) * nl, dk + (size_t)m * nl, sizeof(double) * (size_t)nl);
+            if (Cl) {
+                double *cp = clpart + (size_t)tid * M * nl;
+                for (int m = 0; m < M; ++m) {
+                    double f = 4.0 * M_PI * wk[q] * Pk[(size_t)m * nk + q];
+                    const double *d = dk + (size_t)m * nl;
+                    for (int l = 0; l < nl; ++l) cp[(size_t)m * nl + l] += f * d[l] * d[l];
+                }
+            }
+        }
+        free(jl);
+        free(dk);
+    }
+    if (Cl) {
+        for (int t = 0; t < nt; ++t)
+            for (size_t e = 0; e < (size_t)M * nl; ++e) Cl[e] += clpart[(size_t)t * M * nl + e];
+        free(clpart);
+    }
+    free(wtau);
+    free(wk);
+    return 0;
+}
+
+/* C_l from given transfer functions: Cl[m][l] = 4 pi sum_j wk_j P[m][j] Delta[m][j][l]^2,
+ * summed in increasing j.  wk_in NULL = trapezoid in ln k. */
+int orc_cl(int nk, const double *k, int nl, int M, const double *Delta, const double *Pk,
+           const double *wk_in, double *Cl)
+{
+    if (nk < 0 || nl < 0 || M < 0) return -1;
+    double *wk = (double *)malloc(sizeof(double) * (size_t)(nk > 0 ? nk : 1));
+    if (wk_in) memcpy(wk, wk_in, sizeof(double) * (size_t)nk);
+    else orc_lnk_weights(nk, k, wk);
+    for (int m = 0; m < M; ++m)
+        for (int l = 0; l < nl; ++l) {
+            double acc = 0.0;
+            for (int q = 0; q < nk; ++q) {
+                double d = Delta[((size_t)m * nk + q) * nl + l];
+                acc += 4.0 * M_PI * wk[q] * Pk[(size_t)m * nk + q] * d * d;
+            }
+            Cl[(size_t)m * nl + l] = acc;
+        }
+    free(wk);
+    return 0;
+}
+
+int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

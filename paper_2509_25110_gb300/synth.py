@@ -1,0 +1,239 @@
+"""Seeded synthetic inputs for the line-of-sight projection.
+
+This module only *creates inputs*: wavenumber and conformal-time grids, the
+per-model generator parameters, the source functions S(k, tau) and the
+primordial spectrum P(k).  It holds none of the projection's arithmetic
+(no quadrature weights, no Bessel functions, no transfer or C_l sums), so the
+CPU oracle and the CUDA path can both be fed from it without sharing any code
+of the method itself.
+
+The paper's workloads are full CAMB runs with Planck parameters (Sec. 3.1);
+those source functions come from a Boltzmann ODE that is out of scope here.
+The synthetic source below stands in for them: a visibility-like Gaussian peak
+near recombination, modulated by acoustic oscillations and Silk-like damping,
+plus a broad late-time (ISW-like) term.  With S_T playing the role of the
+temperature source of Eq. (2) and P playing P_R of Eq. (1), the sizes and
+value distributions follow the five workloads of the build's scope table.
+
+Random numbers: a counter-based generator, the SplitMix64 output function
+(Steele, Lea & Flood, "Fast splittable pseudorandom number generators",
+OOPSLA 2014) applied to the counter (seed << 40) | (model << 8) | slot, so any
+model's parameters can be regenerated independently of batch composition.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Optional
+
+import numpy as np
+
+MASK64 = (1 << 64) - 1
+
+# Fixed generator constants of the synthetic source family.
+TAU_L = 11000.0   # centre of the late-time term [Mpc]
+S_L = 2000.0      # width of the late-time term [Mpc]
+K_L = 0.01        # k-scale of the late-time term [1/Mpc]
+A_S = 2.1e-9      # primordial amplitude
+K_PIVOT = 0.05    # pivot scale [1/Mpc]
+
+# Parameter slots drawn per model, in counter order.
+SLOT_TAU_STAR, SLOT_SIGMA, SLOT_RS, SLOT_PHI, SLOT_KD, SLOT_B, SLOT_NS, SLOT_LMAX = range(8)
+PARAM_RANGES = {
+    "tau_star": (270.0, 300.0),
+    "sigma": (15.0, 25.0),
+    "r_s": (140.0, 150.0),
+    "phi": (0.0, math.pi),
+    "k_D": (0.1, 0.2),
+    "b": (0.0, 0.1),
+    "n_s": (0.94, 0.99),
+}
+PARAM_NAMES = ("tau_star", "sigma", "r_s", "phi", "k_D", "b", "n_s")
+
+
+def splitmix64(counter: int) -> int:
+    """SplitMix64 output for one counter value (one step from state=counter)."""
+    z = (counter + 0x9E3779B97F4A7C15) & MASK64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & MASK64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & MASK64
+    return z ^ (z >> 31)
+
+
+def uniform(seed: int, model: int, slot: int) -> float:
+    """U[0,1) double from the top 53 bits of the SplitMix64 output."""
+    c = ((seed & 0xFFFFFF) << 40) | ((model & 0xFFFFFFFF) << 8) | (slot & 0xFF)
+    return (splitmix64(c) >> 11) * (1.0 / 9007199254740992.0)
+
+
+@dataclasses.dataclass
+class ModelParams:
+    """Generator parameters of M models (arrays of length M)."""
+    tau_star: np.ndarray
+    sigma: np.ndarray
+    r_s: np.ndarray
+    phi: np.ndarray
+    k_D: np.ndarray
+    b: np.ndarray
+    n_s: np.ndarray
+    lmax: Optional[np.ndarray] = None  # only for the uneven-batch workload
+
+    @property
+    def M(self) -> int:
+        return int(self.tau_star.shape[0])
+
+    def subset(self, idx) -> "ModelParams":
+        idx = np.asarray(idx)
+        kw = {n: getattr(self, n)[idx] for n in PARAM_NAMES}
+        kw["lmax"] = None if self.lmax is None else self.lmax[idx]
+        return ModelParams(**kw)
+
+    def as_matrix(self) -> np.ndarray:
+        """[M, 7] float64 in PARAM_NAMES order."""
+        return np.stack([getattr(self, n) for n in PARAM_NAMES], axis=1)
+
+
+def model_params(M: int, seed: int = 0, first_model: int = 0,
+                 lmax_range: Optional[tuple] = None) -> ModelParams:
+    """Draw M models' parameters (models first_model .. first_model+M-1)."""
+    out = {n: np.empty(M) for n in PARAM_NAMES}
+    slots = dict(zip(PARAM_NAMES, (SLOT_TAU_STAR, SLOT_SIGMA, SLOT_RS, SLOT_PHI,
+                                   SLOT_KD, SLOT_B, SLOT_NS)))
+    lm = np.empty(M, dtype=np.int64) if lmax_range else None
+    for i in range(M):
+        m = first_model + i
+        for n in PARAM_NAMES:
+            lo, hi = PARAM_RANGES[n]
+            out[n][i] = lo + (hi - lo) * uniform(seed, m, slots[n])
+        if lm is not None:
+            lo, hi = lmax_range
+            lm[i] = lo + int(math.floor(uniform(seed, m, SLOT_LMAX) * (hi - lo + 1)))
+    return ModelParams(lmax=lm, **out)
+
+
+# ----------------------------------------------------------------------------
+# Grids
+# ----------------------------------------------------------------------------
+
+def log_grid(lo: float, hi: float, n: int) -> np.ndarray:
+    return np.exp(np.linspace(math.log(lo), math.log(hi), n))
+
+
+def uniform_grid(lo: float, hi: float, n: int) -> np.ndarray:
+    return np.linspace(lo, hi, n)
+
+
+def dense_tau_grid(n_peak: int = 1000, n_rest: int = 1000) -> np.ndarray:
+    """Grid dense around recombination: n_peak points on [200, 600) then
+    n_rest points on [600, 14000]."""
+    a = 200.0 + (600.0 - 200.0) * np.arange(n_peak) / n_peak
+    b = np.linspace(600.0, 14000.0, n_rest)
+    return np.concatenate([a, b])
+
+
+def master_linear_k(n: int = 3000, kmax: float = 0.5) -> np.ndarray:
+    """Shared linear k grid of the uneven batch: k_j = (j+1) * kmax / n."""
+    return (np.arange(n) + 1.0) * (kmax / n)
+
+
+def uneven_nk(lmax: np.ndarray, n_master: int = 3000) -> np.ndarray:
+    """k-prefix length of each uneven-batch model, scaled with its l_max."""
+    return 1000 + np.rint(2000.0 * (np.asarray(lmax) - 1500) / 4500.0).astype(np.int64)
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    k: np.ndarray
+    tau: np.ndarray
+    tau0: float
+    lmin: int
+    lmax: int
+    M: int
+
+    @property
+    def nk(self):
+        return int(self.k.shape[0])
+
+    @property
+    def ntau(self):
+        return int(self.tau.shape[0])
+
+    @property
+    def nl(self):
+        return self.lmax - self.lmin + 1
+
+
+def workload(name: str, M: Optional[int] = None) -> Workload:
+    """The named synthetic workloads.
+
+    plain_lmax500      : 1 model, l 2..500, 300 k log 1e-4..0.3, 400 tau uniform [200,14000]
+    plain_lmax5000     : 1 model, l 2..5000, 3000 k log 1e-5..1.0, 2000 tau dense near tau*
+    batched_lmax2500   : 256 models, l 2..2500, 2000 k log 1e-4..0.3, 1000 tau uniform
+    uneven_lmax6000    : 1000 models on a 3000-point linear k grid, 1000 tau uniform
+    """
+    tau0 = 14000.0
+    if name == "plain_lmax500":
+        wl = Workload(name, log_grid(1e-4, 0.3, 300), uniform_grid(200.0, 14000.0, 400), tau0, 2, 500, 1)
+    elif name == "plain_lmax5000":
+        wl = Workload(name, log_grid(1e-5, 1.0, 3000), dense_tau_grid(), tau0, 2, 5000, 1)
+    elif name == "batched_lmax2500":
+        wl = Workload(name, log_grid(1e-4, 0.3, 2000), uniform_grid(200.0, 14000.0, 1000), tau0, 2, 2500, 256)
+    elif name == "uneven_lmax6000":
+        wl = Workload(name, master_linear_k(), uniform_grid(200.0, 14000.0, 1000), tau0, 2, 6000, 1000)
+    else:
+        raise KeyError(name)
+    if M is not None:
+        wl.M = M
+    return wl
+
+
+# ----------------------------------------------------------------------------
+# Sources and primordial spectrum
+# ----------------------------------------------------------------------------
+
+def sources(k: np.ndarray, tau: np.ndarray, p: ModelParams, dtype=np.float64) -> np.ndarray:
+    """S[M][nk][ntau] evaluated in float64, returned in `dtype`.
+
+    S(k,tau) = g(tau) cos(k r_s + phi) exp(-(k/k_D)^2)
+             + b exp(-(tau-tau_L)^2 / (2 s_L^2)) exp(-k/k_L),
+    g = unit-area Gaussian of mean tau_star and width sigma.
+    """
+    k = np.asarray(k, dtype=np.float64)
+    tau = np.asarray(tau, dtype=np.float64)
+    out = np.empty((p.M, k.size, tau.size), dtype=dtype)
+    late_tau = np.exp(-(tau - TAU_L) ** 2 / (2.0 * S_L ** 2))
+    late_k = np.exp(-k / K_L)
+    for m in range(p.M):
+        g = np.exp(-(tau - p.tau_star[m]) ** 2 / (2.0 * p.sigma[m] ** 2)) / (p.sigma[m] * math.sqrt(2.0 * math.pi))
+        ak = np.cos(k * p.r_s[m] + p.phi[m]) * np.exp(-(k / p.k_D[m]) ** 2)
+        out[m] = (ak[:, None] * g[None, :] + p.b[m] * late_k[:, None] * late_tau[None, :]).astype(dtype)
+    return out
+
+
+def sources_torch(k, tau, p: ModelParams, device, dtype=None, nk_per_model=None):
+    """Same as `sources`, evaluated with torch in float64 on `device` and cast
+    to `dtype` (default float32).  For the full-size benchmark inputs.
+
+    If nk_per_model is given, rows k >= nk_per_model[m] are set to zero."""
+    import torch
+    dtype = dtype or torch.float32
+    kt = torch.as_tensor(np.asarray(k, dtype=np.float64), device=device)
+    tt = torch.as_tensor(np.asarray(tau, dtype=np.float64), device=device)
+    out = torch.empty((p.M, kt.numel(), tt.numel()), dtype=dtype, device=device)
+    late_tau = torch.exp(-(tt - TAU_L) ** 2 / (2.0 * S_L ** 2))
+    late_k = torch.exp(-kt / K_L)
+    for m in range(p.M):
+        g = torch.exp(-(tt - float(p.tau_star[m])) ** 2 / (2.0 * float(p.sigma[m]) ** 2)) / (
+            float(p.sigma[m]) * math.sqrt(2.0 * math.pi))
+        ak = torch.cos(kt * float(p.r_s[m]) + float(p.phi[m])) * torch.exp(-(kt / float(p.k_D[m])) ** 2)
+        s = ak[:, None] * g[None, :] + float(p.b[m]) * late_k[:, None] * late_tau[None, :]
+        if nk_per_model is not None:
+            s[int(nk_per_model[m]):] = 0.0
+        out[m] = s.to(dtype)
+    return out
+
+
+def primordial(k: np.ndarray, p: ModelParams, A_s: float = A_S) -> np.ndarray:
+    """P[M][nk] = A_s (k/0.05)^(n_s-1), float64."""
+    k = np.asarray(k, dtype=np.float64)
+    return A_s * np.power(k[None, :] / K_PIVOT, (p.n_s[:, None] - 1.0))
