@@ -76,6 +76,19 @@ void orc_sph_bessel(int lmax, double x, double *j)
         for (int l = 1; l <= lmax; ++l) j[l] = 0.0;
         return;
     }
+    if (x < 1e-3) {
+        /* Power series (the definition):
+         * j_l(x) = x^l/(2l+1)!! [1 - x^2/(2(2l+3)) + x^4/(8(2l+3)(2l+5)) - ...];
+         * the dropped terms are below 1e-21 relative.  The backward recurrence
+         * would overflow here, its step factor (2l+1)/x being huge. */
+        double t = 1.0, x2 = x * x;  /* t = x^l / (2l+1)!! */
+        for (int l = 0; l <= lmax; ++l) {
+            if (l > 0) t *= x / (2.0 * l + 1.0);
+            double a = 2.0 * l + 3.0, b = 2.0 * l + 5.0;
+            j[l] = t * (1.0 - x2 / (2.0 * a) + x2 * x2 / (8.0 * a * b));
+        }
+        return;
+    }
     /* Orders at or below ls come from the forward recurrence (x >= 1). */
     int ls = -1;
     if (x >= 1.0) {

@@ -47,6 +47,19 @@ def test_closed_forms_j0_j1_j2(orc):
             assert abs(j[l] - ref[l]) <= tol, (l, x, j[l], ref[l])
 
 
+def test_tiny_arguments(orc):
+    """Below x = 1e-3 the leading series terms; compared with 30-digit mpmath."""
+    pytest.importorskip("mpmath")
+    for x in (1e-200, 1e-40, 1e-7, 9.9e-4):
+        j = orc.sph_bessel(12, x)
+        for l in (0, 1, 2, 5, 12):
+            ref = jl_mpmath(l, x)
+            if abs(ref) < 1e-300:
+                assert abs(j[l]) < 1e-300
+            else:
+                assert abs(j[l] - ref) <= 1e-15 * abs(ref), (l, x, j[l], ref)
+
+
 def test_x_zero(orc):
     j = orc.sph_bessel(7, 0.0)
     assert j[0] == 1.0 and np.all(j[1:] == 0.0)
