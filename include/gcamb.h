@@ -1,0 +1,203 @@
+/*
+ * gcamb.h -- C ABI of the GB300 line-of-sight projection library (libgcamb.so).
+ *
+ * The library computes, on one GPU, the two sums that the paper
+ * (arXiv 2509.25110, "gCAMB") offloads and assembles:
+ *
+ *   Eq. (2), flat space, discretised on the conformal-time nodes tau_i:
+ *       Delta_l(k) = sum_i w_i S(k, tau_i) j_l(k (tau0 - tau_i))
+ *   Eq. (1), for X = Y = T, discretised on the wavenumber nodes k_j:
+ *       C_l = 4 pi sum_j w_j P(k_j) Delta_l(k_j)^2
+ *
+ * w_i are trapezoid weights in tau and w_j trapezoid weights in u = ln k (the
+ * dk/k measure of Eq. 1).  The paper does not state its quadrature; this is
+ * the library's reading.  The paper's kernel phi_l is "related to spherical
+ * Bessel functions" in flat space (Sec. 2.1); the library uses j_l.
+ *
+ * Conventions for every entry point:
+ *  - Return value: GCAMB_OK (0) or a negative GCAMB_E* code.  The text of the
+ *    last error of the calling thread is returned by gcamb_last_error().
+ *    No C++ exception and no abort crosses this boundary.
+ *  - Arrays documented "host" are read (or written) before the call returns.
+ *  - Arrays documented "device" are caller-owned CUDA device memory, C
+ *    contiguous in the stated layout; they must stay valid until the work
+ *    enqueued on `stream` has finished.  The library never frees them.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Device work is enqueued asynchronously on it.  Errors raised on the
+ *    device (a bounded wait that gave up) are reported by gcamb_sync().
+ *  - Handles (gcamb_grid*) are owned by the library and released with the
+ *    matching *_destroy call.
+ */
+#ifndef GCAMB_H
+#define GCAMB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define GCAMB_OK            0
+#define GCAMB_EINVAL      (-1)  /* bad argument (size, order, pointer, mode) */
+#define GCAMB_ENOMEM      (-2)  /* device or host allocation failed */
+#define GCAMB_ECUDA       (-3)  /* a CUDA runtime call failed */
+#define GCAMB_ESTATE      (-4)  /* call out of order, e.g. table not built for this mode */
+#define GCAMB_EUNSUPPORTED (-5) /* feature not available on this device */
+#define GCAMB_ETIMEOUT    (-6)  /* a device-side bounded wait gave up */
+
+/* Arithmetic modes (the form in which the Bessel table is stored and the
+ * tau-contraction of Eq. 2 is computed). */
+#define GCAMB_PLAIN64 0  /* FP64 table, FP64 sums */
+#define GCAMB_PLAIN32 1  /* FP32 table, FP32 sums */
+#define GCAMB_BF16X3  2  /* tensor cores: bf16 hi/lo split, hi*hi + hi*lo + lo*hi, FP32 accumulate */
+#define GCAMB_TF32X3  3  /* tensor cores: tf32 hi/lo split, same three products, FP32 accumulate */
+
+/* Element types of Delta arrays. */
+#define GCAMB_F64 0
+#define GCAMB_F32 1
+
+/* Number of int64 fields written by gcamb_grid_info. */
+#define GCAMB_INFO_N 8
+
+typedef struct gcamb_grid gcamb_grid;
+
+/* Library version string (static storage). */
+const char *gcamb_version(void);
+
+/* Text of the calling thread's last error ("" if none); valid until the next
+ * gcamb call on the same thread. */
+const char *gcamb_last_error(void);
+
+/*
+ * Creates the integration grid of Eqs. (1)-(2): the k nodes, the tau nodes,
+ * tau0 and the multipole range l = lmin..lmax (every l, no l-sampling).
+ * Plays the role of CAMB's IntegrationVars_init (Sec. 3.2).
+ *
+ *   k[nk]      host, strictly increasing, > 0                      [1/Mpc]
+ *   tau[ntau]  host, strictly increasing, tau[ntau-1] <= tau0      [Mpc]
+ *   lmin, lmax 0 <= lmin <= lmax <= 20000
+ *   eps_cut    activity threshold (> 0, <= 1e-3; 0 selects 1e-30): for each
+ *              (k, 128-multipole tile) only the tau-prefix on which Watson's
+ *              bound (Abramowitz & Stegun 9.1.63) allows |j_l| >= eps_cut for
+ *              some l of the tile is summed.  This prefix is Algorithm 1's
+ *              n_min..n_max window.
+ *   out        receives the handle.
+ *
+ * Computes the quadrature weights and the active extents on the host; the
+ * host arrays are copied.  No device memory is touched (device copies are
+ * made by the first call that needs them).  Errors: GCAMB_EINVAL for bad
+ * sizes, non-increasing nodes, tau beyond tau0 or a NULL pointer.
+ */
+int gcamb_grid_create(const double *k, int nk, const double *tau, int ntau, double tau0,
+                      int lmin, int lmax, double eps_cut, gcamb_grid **out);
+
+/* Releases the grid, its tables and its device copies.  NULL is accepted. */
+int gcamb_grid_destroy(gcamb_grid *g);
+
+/*
+ * Grid summary (host, int64[GCAMB_INFO_N]):
+ *   [0] nk  [1] ntau  [2] nl = lmax-lmin+1  [3] n_ltile = ceil(nl/128)
+ *   [4] active (l, k, tau) entries (sum over k and l of the per-l prefix)
+ *   [5] stored (l, k, tau) entries of the PLAIN64 table (tile granularity)
+ *   [6] lmin  [7] lmax
+ */
+int gcamb_grid_info(const gcamb_grid *g, int64_t *info);
+
+/* Active tau-prefix length per (k, l-tile), host int32[nk][n_ltile]. */
+int gcamb_grid_extents(const gcamb_grid *g, int32_t *ext);
+
+/* Quadrature weights the grid uses (host): wtau[ntau] trapezoid in tau,
+ * wk[nk] trapezoid in ln k.  Either pointer may be NULL. */
+int gcamb_grid_weights(const gcamb_grid *g, double *wtau, double *wk);
+
+/*
+ * Builds (or rebuilds) the grid's table of w_i j_l(k (tau0 - tau_i)) over the
+ * active extents, in the layout of `mode`, by an FP64 recurrence on the
+ * device (Miller's backward recurrence above x = k(tau0-tau), the forward
+ * recurrence at and below it).  This is the "calculation of the spherical
+ * Bessel-function" inside the line-of-sight loop (Sec. 3.2), hoisted out of
+ * it because the table is shared by all sources on the grid.
+ * The table is device memory owned by the grid (size: gcamb_table_bytes).
+ * Errors: GCAMB_EINVAL (mode), GCAMB_ENOMEM, GCAMB_ECUDA.
+ */
+int gcamb_bessel_table(gcamb_grid *g, int mode, void *stream);
+
+/* Bytes the table of `mode` occupies (host size_t*). */
+int gcamb_table_bytes(const gcamb_grid *g, int mode, size_t *bytes);
+
+/*
+ * Spherical Bessel functions by the table's device routine:
+ *   x[n]              device double, x >= 0
+ *   out[n][lmax+1]    device double, j_0..j_lmax at each x
+ * Entries below 1e-300 in magnitude may be returned as 0.
+ * Errors: GCAMB_EINVAL (n < 0, lmax < 0 or > 20000, NULL with n > 0).
+ */
+int gcamb_sph_bessel(const double *x, int n, int lmax, double *out, void *stream);
+
+/*
+ * Line-of-sight transfer, Eq. (2), for M sources on the grid (Algorithm 1:
+ * every k, every l, the tau-window sum).
+ *   S[M][nk][ntau]      device; double for GCAMB_PLAIN64, float for GCAMB_PLAIN32
+ *   Delta[M][nk][nl]    device; same type as S; every entry is written
+ *                       (zero where the whole tile is inactive)
+ * Requires gcamb_bessel_table(g, mode) first (else GCAMB_ESTATE).
+ * mode must be GCAMB_PLAIN64 or GCAMB_PLAIN32 (else GCAMB_EINVAL).
+ */
+int gcamb_los_transfer(const gcamb_grid *g, const void *S, int M, int mode, void *Delta, void *stream);
+
+/*
+ * C_l from transfer functions, Eq. (1) with X = Y = T:
+ *   Delta[M][nk][nl]   device, d_dtype = GCAMB_F64 or GCAMB_F32
+ *   Pk[M][nk]          device double, P_R(k) per source
+ *   Cl[M][nl]          device double, C_l for l = lmin..lmax
+ * Summed in FP64 in increasing k (deterministic).
+ */
+int gcamb_cl(const gcamb_grid *g, const void *Delta, int d_dtype, const double *Pk, int M,
+             double *Cl, void *stream);
+
+/*
+ * Device workspace (bytes) that gcamb_los_cl needs for M sources in `mode`.
+ */
+int gcamb_los_cl_workspace(const gcamb_grid *g, int M, int mode, size_t *bytes);
+
+/*
+ * Fused, batched Eqs. (1)-(2) on the tensor cores for M sources sharing the
+ * grid: per k, the tau-contraction D_k[l][m] = sum_i (w_i j_l)(k,tau_i) S_m(k,tau_i)
+ * is a dense product over the active tau-blocks, computed from hi/lo splits
+ * of both operands (three products, FP32 accumulate); D_k is squared,
+ * weighted by 4 pi w_k P_m(k) and summed over k without being stored.
+ * Partial sums over k-chunks are FP32; the final sum over chunks is FP64 in
+ * a fixed order (deterministic).
+ *   S[M][nk][ntau]   device float
+ *   Pk[M][nk]        device double
+ *   Cl[M][nl]        device double
+ *   ws, ws_bytes     device workspace of at least gcamb_los_cl_workspace bytes
+ * mode: GCAMB_BF16X3 or GCAMB_TF32X3; requires gcamb_bessel_table(g, mode).
+ * Errors: GCAMB_EINVAL, GCAMB_ESTATE, GCAMB_EUNSUPPORTED (device is not
+ * sm_103), GCAMB_ECUDA; GCAMB_ETIMEOUT is reported by gcamb_sync.
+ */
+int gcamb_los_cl(const gcamb_grid *g, const float *S, const double *Pk, int M, int mode,
+                 double *Cl, void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * Waits for `stream` and reports any error the library's kernels raised on
+ * the device since the last gcamb_sync (GCAMB_ETIMEOUT for a bounded wait
+ * that gave up), or a CUDA error (GCAMB_ECUDA).  Clears the device flag.
+ */
+int gcamb_sync(void *stream);
+
+/*
+ * Throughput probe of the device's plain arithmetic pipes (no tensor cores):
+ *   what = 0: FP64 fused multiply-add, 1: FP32 fused multiply-add.
+ * Runs a fixed dependent-chain kernel over all SMs and writes the measured
+ * rate in FLOP/s (2 per FMA) to *flops (host).  Synchronous.
+ */
+int gcamb_probe_flops(int what, double *flops);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GCAMB_H */

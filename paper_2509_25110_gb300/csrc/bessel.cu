@@ -1,0 +1,284 @@
+// Spherical Bessel tables: w_i j_l(k (tau0 - tau_i)) over the active extents,
+// generated in FP64 per (k, tau) node by three-term recurrences in l.
+//
+// For x = k (tau0 - tau) the orders split at ls = min(floor(x), l_top):
+//   l <= ls  (x >= 1): forward recurrence from j_0 = sin x / x and
+//            j_1 = (sin x / x - cos x) / x; forward is stable while l < x.
+//   l >  ls: Miller's backward recurrence from f_{L+1} = 0, f_L = 1, with L
+//            the first order at which Watson's bound (A&S 9.1.63) puts
+//            |j_L(x)| below delta; the backward values are scaled to match
+//            the forward value at ls or ls-1 (the larger of the two), or to
+//            j_0 for x < 1.  A first backward pass finds the scale, a second
+//            writes the scaled values, so no per-thread order buffer is kept.
+// Recurrence: j_{l-1} + j_{l+1} = (2l+1)/x j_l (both directions).
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <mutex>
+
+#include "internal.h"
+
+namespace gcamb {
+
+// First order l >= lfrom whose start threshold exceeds x (|j_l(x)| < delta);
+// xs is increasing for l >= 1.
+__device__ __forceinline__ int miller_start(const double *__restrict__ xs, int nxs, int lfrom, double x) {
+  int lo = lfrom < 1 ? 1 : lfrom, hi = nxs - 1;
+  if (lo >= hi) return hi > lo ? hi : lo;
+  if (xs[hi] <= x) return hi;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (xs[mid] > x) hi = mid;
+    else lo = mid + 1;
+  }
+  return lo;
+}
+
+// Calls put(l, j_l(x)) for the orders l in [lmin, ltop] that are not below
+// the Miller start; orders not passed to put are zero to within delta.
+template <class Sink>
+__device__ __forceinline__ void bessel_orders(double x, int lmin, int ltop, const double *__restrict__ xs, int nxs,
+                                              Sink &put) {
+  if (ltop < lmin) return;
+  if (x == 0.0) {
+    if (lmin == 0) put(0, 1.0);
+    return;
+  }
+  if (x < 1e-150) {  // j_1 = x/3, j_l < 1e-300 for l >= 2
+    if (lmin == 0) put(0, 1.0);
+    if (lmin <= 1 && ltop >= 1) put(1, x / 3.0);
+    return;
+  }
+  const double inv = 1.0 / x;
+  int ls = 0;
+  double fa = 0.0, fb = 0.0;  // forward j_{ls-1}, j_{ls}
+  double j0 = 0.0;
+  if (x >= 1.0) {
+    ls = x >= (double)ltop ? ltop : (int)floor(x);
+    double s, c;
+    sincos(x, &s, &c);
+    double jm = s / x;
+    double j = (jm - c) / x;
+    if (lmin == 0) put(0, jm);
+    if (ls >= 1 && lmin <= 1) put(1, j);
+    double dl = 3.0;  // 2l+1 at l = 1
+    for (int l = 1; l < ls; ++l) {
+      const double jn = fma(dl * inv, j, -jm);
+      jm = j;
+      j = jn;
+      dl += 2.0;
+      if (l + 1 >= lmin) put(l + 1, j);
+    }
+    if (ls >= ltop) return;
+    fa = jm;
+    fb = j;
+  } else {
+    j0 = sin(x) / x;
+    if (lmin == 0) put(0, j0);
+  }
+  const int L = miller_start(xs, nxs, ls + 1, x);
+  const int lstop = x >= 1.0 ? ls - 1 : 0;  // pass 1 ends with f at this order
+  // pass 1: scale
+  double fh = 0.0, f = 1.0, dl = 2.0 * L + 1.0;
+  for (int l = L; l > lstop; --l) {
+    const double fm = fma(dl * inv, f, -fh);
+    fh = f;
+    f = fm;
+    dl -= 2.0;
+  }
+  double scale;
+  if (x >= 1.0) scale = (fabs(fb) >= fabs(fa)) ? fb / fh : fa / f;  // fh = f_ls, f = f_{ls-1}
+  else scale = j0 / f;                                                // f = f_0
+  // pass 2: scaled values above ls
+  const int lwrite_hi = L < ltop ? L : ltop;
+  fh = 0.0;
+  f = 1.0;
+  dl = 2.0 * L + 1.0;
+  for (int l = L; l > ls; --l) {
+    if (l <= lwrite_hi && l >= lmin) put(l, scale * f);
+    const double fm = fma(dl * inv, f, -fh);
+    fh = f;
+    f = fm;
+    dl -= 2.0;
+  }
+}
+
+__device__ __forceinline__ uint32_t tf32_rna(float v) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+  return r;
+}
+
+// Byte offset of (row r, column c) in a 128-row plane of 128-byte rows, in the
+// 128-byte swizzled order: 16-byte chunk index XOR (r % 8).
+__device__ __forceinline__ uint32_t sw128_offset(int r, int cbytes) {
+  return (uint32_t)r * 128u + ((uint32_t)((cbytes >> 4) ^ (r & 7)) << 4) + (uint32_t)(cbytes & 15);
+}
+
+template <int MODE>
+struct TableSink {
+  char *table;
+  const int64_t *off_q;
+  int lmin, kbi, c;
+  double w;
+  int cur_lt;
+  char *base;
+  __device__ __forceinline__ void operator()(int l, double v) {
+    const int t = l - lmin;
+    const int lt = t >> 7, r = t & 127;
+    if (lt != cur_lt) {
+      cur_lt = lt;
+      base = table + (size_t)(off_q[lt] + kbi) * TableSink::block_bytes();
+    }
+    const double wv = w * v;
+    if constexpr (MODE == GCAMB_PLAIN64) {
+      reinterpret_cast<double *>(base)[r * 64 + c] = wv;
+    } else if constexpr (MODE == GCAMB_PLAIN32) {
+      reinterpret_cast<float *>(base)[r * 64 + c] = (float)wv;
+    } else if constexpr (MODE == GCAMB_BF16X3) {
+      const __nv_bfloat16 hi = __double2bfloat16(wv);
+      const __nv_bfloat16 lo = __double2bfloat16(wv - (double)__bfloat162float(hi));
+      const uint32_t o = sw128_offset(r, c * 2);
+      *reinterpret_cast<__nv_bfloat16 *>(base + o) = hi;
+      *reinterpret_cast<__nv_bfloat16 *>(base + 16384 + o) = lo;
+    } else {  // TF32X3
+      const uint32_t hi = tf32_rna((float)wv);
+      const uint32_t lo = tf32_rna((float)(wv - (double)__uint_as_float(hi)));
+      const uint32_t o = sw128_offset(r, c * 4);
+      *reinterpret_cast<uint32_t *>(base + o) = hi;
+      *reinterpret_cast<uint32_t *>(base + 16384 + o) = lo;
+    }
+  }
+  static constexpr size_t block_bytes() {
+    return MODE == GCAMB_PLAIN64 ? 65536 : 32768;
+  }
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(128) bessel_table_kernel(const double *__restrict__ k, const double *__restrict__ tau,
+                                                           const double *__restrict__ wtau, double tau0, int ntau,
+                                                           int lmin, int lmax, int nlt,
+                                                           const int32_t *__restrict__ nkb,
+                                                           const int64_t *__restrict__ off,
+                                                           const double *__restrict__ xs, int nxs, void *table) {
+  constexpr int KB = (MODE == GCAMB_TF32X3) ? 32 : 64;
+  const int q = blockIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ntau) return;
+  const int32_t *nkb_q = nkb + (size_t)q * nlt;
+  const int kbi = i / KB;
+  int lt_last = -1;
+  while (lt_last + 1 < nlt && nkb_q[lt_last + 1] > kbi) ++lt_last;
+  if (lt_last < 0) return;
+  const int ltop = min(lmin + (lt_last + 1) * kTileL - 1, lmax);
+  const double x = k[q] * (tau0 - tau[i]);
+  TableSink<MODE> sink{static_cast<char *>(table), off + (size_t)q * nlt, lmin, kbi, i % KB, wtau[i], -1, nullptr};
+  bessel_orders(x, lmin, ltop, xs, nxs, sink);
+}
+
+struct DenseSink {
+  double *row;
+  __device__ __forceinline__ void operator()(int l, double v) { row[l] = v; }
+};
+
+__global__ void sph_bessel_kernel(const double *__restrict__ x, int n, int lmax, const double *__restrict__ xs, int nxs,
+                                  double *out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  DenseSink s{out + (size_t)i * (lmax + 1)};
+  bessel_orders(x[i], 0, lmax, xs, nxs, s);
+}
+
+int launch_bessel_table(gcamb_grid *g, int mode, cudaStream_t st) {
+  Table &t = g->tab[mode];
+  const ModeLayout lay = mode_layout(mode);
+  if (!t.d_data) {
+    t.lay = lay;
+    t.nkb.assign((size_t)g->nk * g->nlt, 0);
+    t.off.assign((size_t)g->nk * g->nlt, 0);
+    int64_t nb = 0;
+    for (int q = 0; q < g->nk; ++q)
+      for (int lt = 0; lt < g->nlt; ++lt) {
+        const size_t e = (size_t)q * g->nlt + lt;
+        t.nkb[e] = (g->ext[e] + lay.kb - 1) / lay.kb;
+        t.off[e] = nb;
+        nb += t.nkb[e];
+      }
+    t.nblocks = nb;
+    t.bytes = (size_t)nb * lay.block_bytes();
+    cudaError_t e;
+    if ((e = cudaMalloc(&t.d_data, std::max<size_t>(t.bytes, 256))) != cudaSuccess) {
+      t.d_data = nullptr;
+      cudaGetLastError();
+      return e == cudaErrorMemoryAllocation ? fail(GCAMB_ENOMEM, "bessel_table: device allocation")
+                                            : cuda_fail(e, "bessel_table: cudaMalloc");
+    }
+    if ((e = cudaMalloc(&t.d_nkb, t.nkb.size() * sizeof(int32_t))) != cudaSuccess) return cuda_fail(e, "bessel_table");
+    if ((e = cudaMalloc(&t.d_off, t.off.size() * sizeof(int64_t))) != cudaSuccess) return cuda_fail(e, "bessel_table");
+    if ((e = cudaMemcpy(t.d_nkb, t.nkb.data(), t.nkb.size() * sizeof(int32_t), cudaMemcpyHostToDevice)) != cudaSuccess)
+      return cuda_fail(e, "bessel_table");
+    if ((e = cudaMemcpy(t.d_off, t.off.data(), t.off.size() * sizeof(int64_t), cudaMemcpyHostToDevice)) != cudaSuccess)
+      return cuda_fail(e, "bessel_table");
+  }
+  cudaError_t e = cudaMemsetAsync(t.d_data, 0, t.bytes, st);
+  if (e != cudaSuccess) return cuda_fail(e, "bessel_table: memset");
+  dim3 grid((g->ntau + 127) / 128, g->nk);
+  switch (mode) {
+    case GCAMB_PLAIN64:
+      bessel_table_kernel<GCAMB_PLAIN64><<<grid, 128, 0, st>>>(g->d_k, g->d_tau, g->d_wtau, g->tau0, g->ntau, g->lmin,
+                                                               g->lmax, g->nlt, t.d_nkb, t.d_off, g->d_xstart, g->nxs,
+                                                               t.d_data);
+      break;
+    case GCAMB_PLAIN32:
+      bessel_table_kernel<GCAMB_PLAIN32><<<grid, 128, 0, st>>>(g->d_k, g->d_tau, g->d_wtau, g->tau0, g->ntau, g->lmin,
+                                                               g->lmax, g->nlt, t.d_nkb, t.d_off, g->d_xstart, g->nxs,
+                                                               t.d_data);
+      break;
+    case GCAMB_BF16X3:
+      bessel_table_kernel<GCAMB_BF16X3><<<grid, 128, 0, st>>>(g->d_k, g->d_tau, g->d_wtau, g->tau0, g->ntau, g->lmin,
+                                                              g->lmax, g->nlt, t.d_nkb, t.d_off, g->d_xstart, g->nxs,
+                                                              t.d_data);
+      break;
+    case GCAMB_TF32X3:
+      bessel_table_kernel<GCAMB_TF32X3><<<grid, 128, 0, st>>>(g->d_k, g->d_tau, g->d_wtau, g->tau0, g->ntau, g->lmin,
+                                                              g->lmax, g->nlt, t.d_nkb, t.d_off, g->d_xstart, g->nxs,
+                                                              t.d_data);
+      break;
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "bessel_table: launch");
+  t.built = true;
+  return GCAMB_OK;
+}
+
+// Start thresholds for the stand-alone entry point: delta = 1e-40, orders up to 24096.
+static std::mutex g_xs_mu;
+static double *g_xs_dev = nullptr;
+static int g_nxs = 0;
+
+int launch_sph_bessel(const double *x, int n, int lmax, double *out, cudaStream_t st) {
+  {
+    std::lock_guard<std::mutex> lk(g_xs_mu);
+    if (!g_xs_dev) {
+      const int cap = kMaxL + 4096;
+      std::vector<double> xs(cap + 1);
+      const double logdelta = std::log(1e-40);
+      for (int l = 0; l <= cap; ++l) xs[l] = watson_threshold(l, logdelta);
+      double *d = nullptr;
+      cudaError_t e = cudaMalloc(&d, xs.size() * sizeof(double));
+      if (e != cudaSuccess) return cuda_fail(e, "sph_bessel: cudaMalloc");
+      e = cudaMemcpy(d, xs.data(), xs.size() * sizeof(double), cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) return cuda_fail(e, "sph_bessel: upload");
+      g_xs_dev = d;
+      g_nxs = (int)xs.size();
+    }
+  }
+  cudaError_t e = cudaMemsetAsync(out, 0, (size_t)n * (lmax + 1) * sizeof(double), st);
+  if (e != cudaSuccess) return cuda_fail(e, "sph_bessel: memset");
+  sph_bessel_kernel<<<(n + 127) / 128, 128, 0, st>>>(x, n, lmax, g_xs_dev, g_nxs, out);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "sph_bessel: launch");
+  return GCAMB_OK;
+}
+
+}  // namespace gcamb

@@ -1,0 +1,104 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/gcamb.h"
+
+namespace gcamb {
+
+constexpr int kTileL = 128;      // multipoles per l-tile (UMMA M)
+constexpr int kMaxL = 20000;
+constexpr int kNumModes = 4;
+
+// Table layout of one mode: blocks of [planes][128 rows][kb cols], one block
+// per (k, l-tile, tau-block of kb nodes).  Rows are multipoles, columns tau.
+// Split modes store 128-byte rows in the 128-byte swizzled order the tensor
+// cores read (16-byte chunk index XOR row%8).
+struct ModeLayout {
+  int kb;        // tau nodes per block
+  int planes;    // 1 (plain) or 2 (hi, lo)
+  int esize;     // bytes per element
+  bool swizzle;  // 128B swizzle within each 8-row group
+  size_t block_bytes() const { return (size_t)planes * kTileL * kb * esize; }
+};
+
+inline ModeLayout mode_layout(int mode) {
+  switch (mode) {
+    case GCAMB_PLAIN64: return {64, 1, 8, false};
+    case GCAMB_PLAIN32: return {64, 1, 4, false};
+    case GCAMB_BF16X3: return {64, 2, 2, true};
+    case GCAMB_TF32X3: return {32, 2, 4, true};
+    default: return {0, 0, 0, false};
+  }
+}
+
+struct Table {
+  bool built = false;
+  ModeLayout lay{};
+  std::vector<int32_t> nkb;   // [nk][nlt] tau-blocks stored per (k, l-tile)
+  std::vector<int64_t> off;   // [nk][nlt] first block of the chunk
+  int64_t nblocks = 0;
+  void *d_data = nullptr;     // table blocks
+  int32_t *d_nkb = nullptr;
+  int64_t *d_off = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace gcamb
+
+struct gcamb_grid {
+  int nk = 0, ntau = 0, lmin = 0, lmax = 0, nl = 0, nlt = 0;
+  double tau0 = 0.0, eps_cut = 1e-30;
+  std::vector<double> k, tau, wtau, wk;
+  std::vector<int32_t> ext;       // [nk][nlt] active tau-prefix per (k, l-tile)
+  std::vector<double> xstart;     // [nxs] Miller start thresholds per order
+  int64_t active = 0;             // active (l,k,tau) entries
+  // device copies (made lazily)
+  double *d_k = nullptr, *d_tau = nullptr, *d_wtau = nullptr, *d_wk = nullptr;
+  double *d_xstart = nullptr;
+  int nxs = 0;
+  gcamb::Table tab[gcamb::kNumModes];
+};
+
+namespace gcamb {
+
+// Thread-local error text; returns the code for convenient `return fail(...)`.
+int fail(int code, const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+int *device_error_flag();  // device pointer of the mapped error word
+
+// Device-side error codes written to the flag word.
+constexpr int kDevErrTimeout = 1;
+
+int ensure_device_grid(gcamb_grid *g);
+
+// Bessel table construction (bessel.cu).
+int launch_bessel_table(gcamb_grid *g, int mode, cudaStream_t st);
+int launch_sph_bessel(const double *x, int n, int lmax, double *out, cudaStream_t st);
+
+// Plain FP64/FP32 path (plain.cu).
+int launch_los_plain(const gcamb_grid *g, const void *S, int M, int mode, void *Delta, cudaStream_t st);
+int launch_cl(const gcamb_grid *g, const void *Delta, int d_dtype, const double *Pk, int M, double *Cl,
+              cudaStream_t st);
+
+// Tensor-core batched path (tc.cu).
+size_t los_cl_workspace_bytes(const gcamb_grid *g, int M, int mode);
+int launch_los_cl(const gcamb_grid *g, const float *S, const double *Pk, int M, int mode, double *Cl,
+                  void *ws, size_t ws_bytes, cudaStream_t st);
+void drop_plans(const gcamb_grid *g);
+
+// Probes (probe.cu).
+int run_probe_flops(int what, double *flops);
+
+// Watson's bound (A&S 9.1.63) on log|j_l(x)| for x < l + 1/2.
+double log_watson_bound(int l, double x);
+// Smallest x > 0 at which the bound on |j_l| reaches `logeps` (0 for l == 0).
+double watson_threshold(int l, double logeps);
+
+}  // namespace gcamb

@@ -1,0 +1,245 @@
+"""Python binding of libgcamb.so (include/gcamb.h): argument marshalling only.
+
+Every function has the name of the C entry point without the `gcamb_` prefix.
+Device arrays are torch CUDA tensors (contiguous, stated dtype); streams
+default to torch's current stream.  Every step of the computation runs in the
+library's kernels; if the library is missing this module raises instead of
+falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgcamb.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ESTATE, EUNSUPPORTED, ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
+PLAIN64, PLAIN32, BF16X3, TF32X3 = 0, 1, 2, 3
+F64, F32 = 0, 1
+MODE_NAMES = {PLAIN64: "plain64", PLAIN32: "plain32", BF16X3: "bf16x3", TF32X3: "tf32x3"}
+INFO_N = 8
+
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_lib = None
+
+
+class GcambError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("gcamb error %d: %s" % (code, msg))
+        self.code = code
+
+
+def lib():
+    """Loads libgcamb.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libgcamb.so is not built; run paper_2509_25110_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    L.gcamb_version.restype = ctypes.c_char_p
+    L.gcamb_last_error.restype = ctypes.c_char_p
+    L.gcamb_grid_create.argtypes = [_dp, ctypes.c_int, _dp, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                    ctypes.c_int, ctypes.c_double, ctypes.POINTER(_vp)]
+    L.gcamb_grid_destroy.argtypes = [_vp]
+    L.gcamb_grid_info.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
+    L.gcamb_grid_extents.argtypes = [_vp, ctypes.POINTER(ctypes.c_int32)]
+    L.gcamb_grid_weights.argtypes = [_vp, _dp, _dp]
+    L.gcamb_bessel_table.argtypes = [_vp, ctypes.c_int, _vp]
+    L.gcamb_table_bytes.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
+    L.gcamb_sph_bessel.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp]
+    L.gcamb_los_transfer.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp]
+    L.gcamb_cl.argtypes = [_vp, _vp, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp]
+    L.gcamb_los_cl_workspace.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
+    L.gcamb_los_cl.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_size_t, _vp]
+    L.gcamb_sync.argtypes = [_vp]
+    L.gcamb_probe_flops.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc != OK:
+        raise GcambError(rc, lib().gcamb_last_error().decode())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return _vp(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return _vp(stream)
+    return _vp(stream.cuda_stream)
+
+
+def _dev(t, dtype, shape=None, name="tensor"):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise ValueError("%s must have dtype %s, got %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError("%s must have shape %s, got %s" % (name, tuple(shape), tuple(t.shape)))
+    return _vp(t.data_ptr())
+
+
+def version() -> str:
+    return lib().gcamb_version().decode()
+
+
+def last_error() -> str:
+    return lib().gcamb_last_error().decode()
+
+
+class Grid:
+    """Owning wrapper of a gcamb_grid handle."""
+
+    def __init__(self, handle, k, tau, tau0, lmin, lmax):
+        self.handle = handle
+        self.k = k
+        self.tau = tau
+        self.tau0 = tau0
+        self.lmin = lmin
+        self.lmax = lmax
+
+    @property
+    def nk(self):
+        return self.k.size
+
+    @property
+    def ntau(self):
+        return self.tau.size
+
+    @property
+    def nl(self):
+        return self.lmax - self.lmin + 1
+
+    def close(self):
+        if self.handle is not None:
+            grid_destroy(self)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def grid_create(k, tau, tau0, lmin, lmax, eps_cut=0.0) -> Grid:
+    k = np.ascontiguousarray(k, dtype=np.float64)
+    tau = np.ascontiguousarray(tau, dtype=np.float64)
+    h = _vp()
+    _check(lib().gcamb_grid_create(k.ctypes.data_as(_dp), k.size, tau.ctypes.data_as(_dp), tau.size, float(tau0),
+                                   int(lmin), int(lmax), float(eps_cut), ctypes.byref(h)))
+    return Grid(h, k.copy(), tau.copy(), float(tau0), int(lmin), int(lmax))
+
+
+def grid_destroy(g: Grid):
+    if g.handle is not None:
+        _check(lib().gcamb_grid_destroy(g.handle))
+        g.handle = None
+
+
+def grid_info(g: Grid) -> dict:
+    a = (ctypes.c_int64 * INFO_N)()
+    _check(lib().gcamb_grid_info(g.handle, a))
+    keys = ("nk", "ntau", "nl", "n_ltile", "active", "stored_plain64", "lmin", "lmax")
+    return dict(zip(keys, [int(v) for v in a]))
+
+
+def grid_extents(g: Grid) -> np.ndarray:
+    info = grid_info(g)
+    out = np.empty((info["nk"], info["n_ltile"]), dtype=np.int32)
+    _check(lib().gcamb_grid_extents(g.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+    return out
+
+
+def grid_weights(g: Grid):
+    wt = np.empty(g.ntau)
+    wk = np.empty(g.nk)
+    _check(lib().gcamb_grid_weights(g.handle, wt.ctypes.data_as(_dp), wk.ctypes.data_as(_dp)))
+    return wt, wk
+
+
+def bessel_table(g: Grid, mode: int, stream=None):
+    _check(lib().gcamb_bessel_table(g.handle, int(mode), _stream(stream)))
+
+
+def table_bytes(g: Grid, mode: int) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().gcamb_table_bytes(g.handle, int(mode), ctypes.byref(b)))
+    return int(b.value)
+
+
+def sph_bessel(x, lmax: int, out=None, stream=None):
+    """j_0..j_lmax at device FP64 x[n] -> out[n][lmax+1] (FP64)."""
+    import torch
+    n = x.numel()
+    if out is None:
+        out = torch.empty((n, lmax + 1), dtype=torch.float64, device=x.device)
+    _check(lib().gcamb_sph_bessel(_dev(x, torch.float64, name="x"), n, int(lmax),
+                                  _dev(out, torch.float64, (n, lmax + 1), "out"), _stream(stream)))
+    return out
+
+
+def los_transfer(g: Grid, S, mode: int, Delta=None, stream=None):
+    """Eq. (2): S[M][nk][ntau] -> Delta[M][nk][nl] (FP64 for PLAIN64, FP32 for PLAIN32)."""
+    import torch
+    dt = torch.float64 if mode == PLAIN64 else torch.float32
+    M = S.shape[0]
+    if Delta is None:
+        Delta = torch.empty((M, g.nk, g.nl), dtype=dt, device=S.device)
+    _check(lib().gcamb_los_transfer(g.handle, _dev(S, dt, (M, g.nk, g.ntau), "S"), M, int(mode),
+                                    _dev(Delta, dt, (M, g.nk, g.nl), "Delta"), _stream(stream)))
+    return Delta
+
+
+def cl(g: Grid, Delta, Pk, Cl=None, stream=None):
+    """Eq. (1): Delta[M][nk][nl], Pk[M][nk] -> Cl[M][nl] (FP64)."""
+    import torch
+    M = Delta.shape[0]
+    d_dtype = F64 if Delta.dtype == torch.float64 else F32
+    if Cl is None:
+        Cl = torch.empty((M, g.nl), dtype=torch.float64, device=Delta.device)
+    _check(lib().gcamb_cl(g.handle, _dev(Delta, Delta.dtype, (M, g.nk, g.nl), "Delta"), d_dtype,
+                          _dev(Pk, torch.float64, (M, g.nk), "Pk"), M, _dev(Cl, torch.float64, (M, g.nl), "Cl"),
+                          _stream(stream)))
+    return Cl
+
+
+def los_cl_workspace(g: Grid, M: int, mode: int) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().gcamb_los_cl_workspace(g.handle, int(M), int(mode), ctypes.byref(b)))
+    return int(b.value)
+
+
+def los_cl(g: Grid, S, Pk, mode: int, Cl=None, ws=None, stream=None):
+    """Fused batched Eqs. (1)-(2) on the tensor cores: S[M][nk][ntau] FP32 -> Cl[M][nl] FP64."""
+    import torch
+    M = S.shape[0]
+    need = los_cl_workspace(g, M, mode)
+    if ws is None:
+        ws = torch.empty(need, dtype=torch.uint8, device=S.device)
+    if Cl is None:
+        Cl = torch.empty((M, g.nl), dtype=torch.float64, device=S.device)
+    _check(lib().gcamb_los_cl(g.handle, _dev(S, torch.float32, (M, g.nk, g.ntau), "S"),
+                              _dev(Pk, torch.float64, (M, g.nk), "Pk"), M, int(mode),
+                              _dev(Cl, torch.float64, (M, g.nl), "Cl"), _dev(ws, torch.uint8, name="ws"),
+                              ws.numel(), _stream(stream)))
+    return Cl
+
+
+def sync(stream=None):
+    _check(lib().gcamb_sync(_stream(stream)))
+
+
+def probe_flops(what: int) -> float:
+    f = ctypes.c_double()
+    _check(lib().gcamb_probe_flops(int(what), ctypes.byref(f)))
+    return float(f.value)
