@@ -1,0 +1,379 @@
+#!/usr/bin/env python
+"""Benchmark of the batched split-precision line-of-sight path.
+
+Metric: C_l spectra per second at l_max = 2500 (batched split precision vs
+plain FP64, relative error <= 1e-5), on the batched workload: 256 sources
+sharing one grid, l = 2..2500, 2000 k log-spaced on [1e-4, 0.3] 1/Mpc, 1000
+tau uniform on [200, 14000] Mpc, synthetic sources (paper_2509_25110_gb300.synth).
+
+One step = one pass of the batched path over one batch of 256 sources:
+hi/lo split of the sources, the tensor-core tau-contraction + square + k-chunk
+sum, and the FP64 reduction to C_l (gcamb_los_cl).  The grid's Bessel table is
+built once per grid before the timed region (its build time is reported in
+`config`).  Inputs (2.0 GB of sources, a 3.3 GB table) are larger than L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--mode f16x3|bf16x3|tf32x3]
+  python bench.py --impl reference ...   (the FP64 CPU oracle, timed on the host)
+
+Under torchrun every rank runs its own batch (weak scaling, no collective on
+the data path); the timed region is bracketed by a barrier and the maximum
+over ranks is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "C_l spectra/sec at l_max=2500: batched split-precision vs plain FP64, rel err ≤1e-5"
+WORKLOAD = "batched_lmax2500"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=600)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="f16x3")
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--cpu-models", type=int, default=16)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nk", type=int, default=0,
+                    help="profiling case: the same k range with this many nodes (default: the workload's 2000)")
+    ap.add_argument("--kernel-only", action="store_true",
+                    help="profiling case: only warm-up + timed steps, one short line, no e2e/plain/CPU legs")
+    return ap.parse_args()
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id=None):
+        self.bus_id = (bus_id or "").lower()
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        time.sleep(0.25)
+
+    def stop(self):
+        if self.p is None:
+            return None
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        rows = [[c.strip() for c in r] for r in rows if len(r) >= 10]
+        if self.bus_id:
+            mine = [r for r in rows if self.bus_id[-12:] in r[1].lower()]
+            rows = mine or rows
+        if not rows:
+            return None
+        idx = rows[0][0]
+        rows = [r for r in rows if r[0] == idx]
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return float("nan")
+        sm = [num(r[2]) for r in rows]
+        smax = max(num(r[3]) for r in rows)
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[j] for r in rows for j in range(4) if r[6 + j].lower().startswith("active")})
+        loaded = [s for s in sm if s == s]
+        return {"sm_mhz": statistics.median(loaded) if loaded else None, "sm_max_mhz": smax,
+                "power_w_max": max(num(r[4]) for r in rows), "samples": len(rows), "reasons": reasons}
+
+
+# ------------------------------------------------------------------ reference arm
+
+def run_reference(args):
+    """The FP64 CPU oracle as it stands, on host cores, one bounded sample per step."""
+    import numpy as np
+
+    import oracle
+    from oracle import build as ob
+    from paper_2509_25110_gb300 import synth
+
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    ob.build()
+    wl = synth.workload(WORKLOAD)
+    p = synth.model_params(1, seed=0)
+    # per step: one source on a subset of k nodes (a fraction of a spectrum);
+    # sized so that warm-up + steps finish in about two minutes
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    nks = 64
+    while True:
+        qs = np.unique(np.linspace(0, wl.nk - 1, nks).astype(int))
+        S = synth.sources(wl.k[qs], wl.tau, p)
+        P = synth.primordial(wl.k[qs], p)
+        t0 = time.perf_counter()
+        oracle.los_cl(wl.k[qs], wl.tau, wl.tau0, wl.lmin, wl.lmax, S, P, want_delta=False)
+        dt = time.perf_counter() - t0
+        if dt <= budget or nks <= 4:
+            break
+        nks = max(4, int(nks * budget / dt * 0.8))
+    frac = qs.size / wl.nk
+    for _ in range(args.warmup):
+        oracle.los_cl(wl.k[qs], wl.tau, wl.tau0, wl.lmin, wl.lmax, S, P, want_delta=False)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.los_cl(wl.k[qs], wl.tau, wl.tau0, wl.lmin, wl.lmax, S, P, want_delta=False)
+    dt = time.perf_counter() - t0
+    value = frac * args.steps / dt
+    cores = oracle.num_threads()
+    sample = "1 source x %d of %d k nodes per step (%.4f spectra), all 1000 tau, l 2..2500" % (qs.size, wl.nk, frac)
+    line = {
+        "metric": METRIC, "value": value, "unit": "spectra/s", "impl": "reference", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "M": 256, "lmax": 2500, "nk": 2000, "ntau": 1000,
+                   "reference": "FP64 CPU oracle (oracle/gcamb_oracle.c), dense tau sums"},
+        "cpu_baseline": {"value": value, "unit": "spectra/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "spectra/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2509_25110_gb300 import build, gcamb, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    build.build()
+    mode = {"bf16x3": gcamb.BF16X3, "tf32x3": gcamb.TF32X3, "f16x3": gcamb.F16X3}[args.mode]
+    peaks, peak_src = load_peaks()
+
+    wl = synth.workload(WORKLOAD)
+    if args.nk:
+        wl.k = synth.log_grid(float(wl.k[0]), float(wl.k[-1]), args.nk)
+    M = wl.M
+    p = synth.model_params(M, seed=rank)
+    S = synth.sources_torch(wl.k, wl.tau, p, dev, torch.float32)
+    P = torch.as_tensor(synth.primordial(wl.k, p), device=dev)
+    g = gcamb.grid_create(wl.k, wl.tau, wl.tau0, wl.lmin, wl.lmax)
+    info = gcamb.grid_info(g)
+
+    def timed(fn):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        fn()
+        b.record()
+        b.synchronize()
+        return a.elapsed_time(b)
+
+    first_table_ms = timed(lambda: gcamb.bessel_table(g, mode))
+    table_ms = timed(lambda: gcamb.bessel_table(g, mode))
+    ws = torch.empty(gcamb.los_cl_workspace(g, M, mode), dtype=torch.uint8, device=dev)
+    C = torch.empty((M, wl.nl), dtype=torch.float64, device=dev)
+    first_call_ms = timed(lambda: gcamb.los_cl(g, S, P, mode, C, ws))
+    gcamb.sync()
+    for _ in range(max(3, args.warmup)):
+        gcamb.los_cl(g, S, P, mode, C, ws)
+    gcamb.sync()
+
+    # ---------------- timed region
+    bus = None
+    try:
+        bus = torch.cuda.get_device_properties(dev).pci_bus_id
+    except Exception:
+        pass
+    sampler = ClockSampler(bus)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    gcamb.profile_enable(True)
+    sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        gcamb.los_cl(g, S, P, mode, C, ws)
+    e1.record()
+    e1.synchronize()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    if world > 1:
+        dist.barrier()
+    gcamb.sync()
+    ms = e0.elapsed_time(e1)
+    if args.kernel_only:
+        gcamb.profile_enable(False)
+        print(json.dumps({"workload": WORKLOAD, "nk": wl.nk, "mode": args.mode, "steps": args.steps,
+                          "ms_per_step": ms / args.steps}), flush=True)
+        return
+    kern = {gcamb.K_NAMES[i]: gcamb.profile_read(i) for i in (gcamb.K_SPLIT, gcamb.K_WEIGHTS, gcamb.K_TC,
+                                                               gcamb.K_REDUCE)}
+    gcamb.profile_enable(False)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * M * args.steps / (ms * 1e-3)
+    launches = sum(n for _, n in kern.values())
+
+    # ---------------- roofline of the dominant kernel (tensor-core contraction)
+    tc_ms, tc_n = kern["los_cl_tc"]
+    tc_avg_s = tc_ms / max(1, tc_n) * 1e-3
+    pair = 8 if mode == gcamb.TF32X3 else 4            # bytes of one hi+lo table entry
+    alg_bytes = info["active"] * pair + M * wl.nk * wl.ntau * pair   # table entries + split sources, once each
+    alg_flops = 3 * 2 * info["active"] * M                             # three split products
+    achieved_gbs = alg_bytes / tc_avg_s / 1e9
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "los_cl_tc_traffic.txt")) as f:
+            tr = json.load(f)
+        import hashlib
+        src = open(os.path.join(ROOT, "paper_2509_25110_gb300", "csrc", "tc.cu"), "rb").read()
+        if tr.get("tc_cu_sha1") == hashlib.sha1(src).hexdigest() and tr.get("mode") == args.mode:
+            traffic = tr["dram_bytes_per_launch"]
+    except Exception:
+        pass
+    roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved_gbs / peaks["hbm_gbs"], "traffic": traffic,
+                "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src,
+                "kernel": "los_cl_tc_kernel", "kernel_ms": tc_avg_s * 1e3,
+                "algorithmic_bytes": alg_bytes,
+                "tensor_view": {"achieved_tflops": alg_flops / tc_avg_s / 1e12,
+                                "peak_tflops": peaks.get("bf16_tflops"),
+                                "frac": alg_flops / tc_avg_s / 1e12 / peaks.get("bf16_tflops", 1900.0)}}
+
+    # ---------------- end to end through the C ABI with host buffers
+    S_h = S.cpu().pin_memory()
+    P_h = P.cpu().pin_memory()
+    C_h = torch.empty((M, wl.nl), dtype=torch.float64).pin_memory()
+    S_d = torch.empty_like(S)
+    P_d = torch.empty_like(P)
+
+    def e2e_step():
+        S_d.copy_(S_h, non_blocking=True)
+        P_d.copy_(P_h, non_blocking=True)
+        gcamb.los_cl(g, S_d, P_d, mode, C, ws)
+        C_h.copy_(C, non_blocking=True)
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_ms = timed(lambda: [e2e_step() for _ in range(args.e2e_steps)])
+    gcamb.sync()
+    e2e = {"value": world * M * args.e2e_steps / (e2e_ms * 1e-3), "unit": "spectra/s",
+           "h2d_bytes_per_step": S_h.numel() * 4 + P_h.numel() * 8, "d2h_bytes_per_step": C_h.numel() * 8}
+
+    # ---------------- plain FP64 on the same grid (the metric's comparison), 4 sources
+    gcamb.bessel_table(g, gcamb.PLAIN64)
+    S64 = S[:4].double().contiguous()
+    D64 = torch.empty((4, wl.nk, wl.nl), dtype=torch.float64, device=dev)
+    C64 = torch.empty((4, wl.nl), dtype=torch.float64, device=dev)
+
+    def plain_step():
+        gcamb.los_transfer(g, S64, gcamb.PLAIN64, D64)
+        gcamb.cl(g, D64, P[:4].contiguous(), C64)
+    plain_step()
+    plain_ms = timed(lambda: [plain_step() for _ in range(3)]) / 3
+    gcamb.sync()
+    plain64_rate = 4 / (plain_ms * 1e-3)
+
+    # ---------------- CPU baseline: the oracle on a bounded sample (rank 0, N = 1)
+    cpu = None
+    err = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        from oracle import build as ob
+        ob.build()
+        mc = args.cpu_models
+        Sc = S[:mc].double().cpu().numpy()
+        Pc = P[:mc].cpu().numpy()
+        t0 = time.perf_counter()
+        _, Cr = oracle.los_cl(wl.k, wl.tau, wl.tau0, wl.lmin, wl.lmax, Sc, Pc, want_delta=False)
+        dt = time.perf_counter() - t0
+        cpu = {"value": mc / dt, "unit": "spectra/s", "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": "%d of the 256 sources, full grid (2000 k x 1000 tau, l 2..2500), %.1f s" % (mc, dt)}
+        rel = np.abs(C[:mc].cpu().numpy() / Cr - 1)
+        err = float(rel.max())
+
+    props = torch.cuda.get_device_properties(dev)
+    line = {
+        "metric": METRIC, "value": value, "unit": "spectra/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {gcamb.BF16X3: "bf16", gcamb.F16X3: "f16", gcamb.TF32X3: "tf32"}[mode], "data": "synthetic",
+        "config": {"workload": WORKLOAD, "M": M, "lmax": wl.lmax, "nk": wl.nk, "ntau": wl.ntau,
+                   "mode": args.mode, "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (sources 2.05 GB fp32, table %.2f GB)" % (gcamb.table_bytes(g, mode) / 1e9),
+                   "table": "resident, built once per grid: %.2f ms (first build %.2f ms), not in the step" % (
+                       table_ms, first_table_ms),
+                   "first_call_ms": first_call_ms, "max_rel_err_vs_oracle": err,
+                   "max_rel_err_sample": "%d sources" % args.cpu_models if err is not None else None,
+                   "plain64_spectra_per_s": plain64_rate, "speedup_vs_plain64": value / world / plain64_rate,
+                   "active_entries": info["active"], "kernel_ms": {k: (v[0] / max(1, v[1])) for k, v in kern.items()},
+                   "device": props.name},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": clocks,
+        "gpu_launches": launches,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -53,6 +53,7 @@ extern "C" {
 #define GCAMB_PLAIN32 1  /* FP32 table, FP32 sums */
 #define GCAMB_BF16X3  2  /* tensor cores: bf16 hi/lo split, hi*hi + hi*lo + lo*hi, FP32 accumulate */
 #define GCAMB_TF32X3  3  /* tensor cores: tf32 hi/lo split, same three products, FP32 accumulate */
+#define GCAMB_F16X3   4  /* tensor cores: fp16 hi/lo split of power-of-two scaled operands, FP32 accumulate */
 
 /* Element types of Delta arrays. */
 #define GCAMB_F64 0
@@ -168,13 +169,20 @@ int gcamb_los_cl_workspace(const gcamb_grid *g, int M, int mode, size_t *bytes);
  * is a dense product over the active tau-blocks, computed from hi/lo splits
  * of both operands (three products, FP32 accumulate); D_k is squared,
  * weighted by 4 pi w_k P_m(k) and summed over k without being stored.
- * Partial sums over k-chunks are FP32; the final sum over chunks is FP64 in
- * a fixed order (deterministic).
+ * hi*hi is accumulated apart from hi*lo + lo*hi (two TMEM accumulators), so
+ * the main chain takes a third of the accumulate steps.  Partial sums over
+ * k-chunks of at most 64 nodes are FP32; the final sum over chunks is FP64 in
+ * a fixed order (deterministic).  GCAMB_F16X3 scales the table by one power
+ * of two per grid and each (k, source) row of S by its own power of two so
+ * that both land in fp16's normal range; the scales are removed exactly.
  *   S[M][nk][ntau]   device float
- *   Pk[M][nk]        device double
+ *   Pk[M][nk]        device double, >= 0 (a power spectrum; the epilogue
+ *                    weights by sqrt(4 pi w_k P))
  *   Cl[M][nl]        device double
  *   ws, ws_bytes     device workspace of at least gcamb_los_cl_workspace bytes
- * mode: GCAMB_BF16X3 or GCAMB_TF32X3; requires gcamb_bessel_table(g, mode).
+ * mode: GCAMB_BF16X3, GCAMB_F16X3 or GCAMB_TF32X3; requires
+ * gcamb_bessel_table(g, mode).  For GCAMB_F16X3 the per-row scale is clamped
+ * to 2^-40..2^80, so rows whose largest |S| is below ~1e-20 lose precision.
  * Errors: GCAMB_EINVAL, GCAMB_ESTATE, GCAMB_EUNSUPPORTED (device is not
  * sm_103), GCAMB_ECUDA; GCAMB_ETIMEOUT is reported by gcamb_sync.
  */
@@ -187,6 +195,27 @@ int gcamb_los_cl(const gcamb_grid *g, const float *S, const double *Pk, int M, i
  * that gave up), or a CUDA error (GCAMB_ECUDA).  Clears the device flag.
  */
 int gcamb_sync(void *stream);
+
+/* Kernel identifiers of the event tracer. */
+#define GCAMB_K_TABLE     0  /* Bessel table generation */
+#define GCAMB_K_LOS_PLAIN 1  /* plain transfer, Eq. (2) */
+#define GCAMB_K_CL        2  /* Eq. (1) k-sum of stored transfers */
+#define GCAMB_K_SPLIT     3  /* hi/lo split of the sources (batched path) */
+#define GCAMB_K_WEIGHTS   4  /* 4 pi w_k P(k) weights (batched path) */
+#define GCAMB_K_TC        5  /* tensor-core contraction + square + k-chunk sum */
+#define GCAMB_K_REDUCE    6  /* FP64 sum of the k-chunk partials */
+#define GCAMB_K_COUNT     8
+
+/*
+ * Event tracer.  While enabled, every kernel the library launches is
+ * bracketed by CUDA events recorded on its launch stream.  Enabling clears
+ * the accumulators.  gcamb_profile_read waits for the recorded events and
+ * returns, for one kernel id, the summed device time in milliseconds and the
+ * number of launches (host double*, int64_t*).  Not thread-safe with respect
+ * to concurrent launches from several host threads.
+ */
+int gcamb_profile_enable(int on);
+int gcamb_profile_read(int kernel, double *total_ms, int64_t *launches);
 
 /*
  * Throughput probe of the device's plain arithmetic pipes (no tensor cores):

@@ -54,6 +54,60 @@ static int read_and_clear_flag() {
   return v;
 }
 
+// ------------------------------------------------------------ event tracer
+namespace {
+struct ProfRec {
+  int id;
+  cudaEvent_t a, b;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfRec> g_prof_pending;
+std::vector<cudaEvent_t> g_ev_pool;
+double g_prof_ms[GCAMB_K_COUNT];
+int64_t g_prof_n[GCAMB_K_COUNT];
+
+cudaEvent_t take_event() {
+  if (!g_ev_pool.empty()) {
+    cudaEvent_t e = g_ev_pool.back();
+    g_ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+void drain_pending() {
+  for (auto &r : g_prof_pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      g_prof_ms[r.id] += ms;
+      g_prof_n[r.id] += 1;
+    }
+    g_ev_pool.push_back(r.a);
+    g_ev_pool.push_back(r.b);
+  }
+  g_prof_pending.clear();
+}
+}  // namespace
+
+ProfScope::ProfScope(int id_, cudaStream_t st_) : id(id_), st(st_) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (!g_prof_on) return;
+  if (g_prof_pending.size() > 4096) drain_pending();
+  a = take_event();
+  b = take_event();
+  if (a && b) cudaEventRecord(a, st);
+}
+
+ProfScope::~ProfScope() {
+  if (!a || !b) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  cudaEventRecord(b, st);
+  g_prof_pending.push_back({id, a, b});
+}
+
 // log of Watson's bound on |j_l(x)| = sqrt(pi/(2x)) |J_nu(x)|, nu = l + 1/2:
 // |J_nu(nu z)| <= exp(-nu (alpha - tanh alpha)), z = sech(alpha) <= 1
 // (Abramowitz & Stegun 9.1.63).  Written with s = tanh(alpha) = sqrt(1 - z^2).
@@ -316,7 +370,8 @@ int gcamb_cl(const gcamb_grid *g, const void *Delta, int d_dtype, const double *
 
 int gcamb_los_cl_workspace(const gcamb_grid *g, int M, int mode, size_t *bytes) {
   if (!g || !bytes) return fail(GCAMB_EINVAL, "los_cl_workspace: NULL argument");
-  if (mode != GCAMB_BF16X3 && mode != GCAMB_TF32X3) return fail(GCAMB_EINVAL, "los_cl_workspace: bad mode");
+  if (mode != GCAMB_BF16X3 && mode != GCAMB_TF32X3 && mode != GCAMB_F16X3)
+    return fail(GCAMB_EINVAL, "los_cl_workspace: bad mode");
   if (M < 1) return fail(GCAMB_EINVAL, "los_cl_workspace: M must be >= 1");
   *bytes = los_cl_workspace_bytes(g, M, mode);
   return GCAMB_OK;
@@ -325,8 +380,8 @@ int gcamb_los_cl_workspace(const gcamb_grid *g, int M, int mode, size_t *bytes) 
 int gcamb_los_cl(const gcamb_grid *g, const float *S, const double *Pk, int M, int mode, double *Cl, void *ws,
                  size_t ws_bytes, void *stream) {
   if (!g) return fail(GCAMB_EINVAL, "los_cl: NULL grid");
-  if (mode != GCAMB_BF16X3 && mode != GCAMB_TF32X3)
-    return fail(GCAMB_EINVAL, "los_cl: mode must be GCAMB_BF16X3 or GCAMB_TF32X3");
+  if (mode != GCAMB_BF16X3 && mode != GCAMB_TF32X3 && mode != GCAMB_F16X3)
+    return fail(GCAMB_EINVAL, "los_cl: mode must be GCAMB_BF16X3, GCAMB_F16X3 or GCAMB_TF32X3");
   if (M < 0) return fail(GCAMB_EINVAL, "los_cl: M < 0");
   if (M == 0) return GCAMB_OK;
   if (!S || !Pk || !Cl) return fail(GCAMB_EINVAL, "los_cl: NULL pointer");
@@ -343,6 +398,27 @@ int gcamb_sync(void *stream) {
   int f = read_and_clear_flag();
   if (f == kDevErrTimeout) return fail(GCAMB_ETIMEOUT, "a device-side bounded wait gave up");
   if (f) return fail(GCAMB_ECUDA, "device error flag " + std::to_string(f));
+  return GCAMB_OK;
+}
+
+int gcamb_profile_enable(int on) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  drain_pending();
+  g_prof_on = on != 0;
+  for (int i = 0; i < GCAMB_K_COUNT; ++i) {
+    g_prof_ms[i] = 0.0;
+    g_prof_n[i] = 0;
+  }
+  return GCAMB_OK;
+}
+
+int gcamb_profile_read(int kernel, double *total_ms, int64_t *launches) {
+  if (kernel < 0 || kernel >= GCAMB_K_COUNT || !total_ms || !launches)
+    return fail(GCAMB_EINVAL, "profile_read: bad argument");
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  drain_pending();
+  *total_ms = g_prof_ms[kernel];
+  *launches = g_prof_n[kernel];
   return GCAMB_OK;
 }
 

@@ -12,6 +12,7 @@
 //            writes the scaled values, so no per-thread order buffer is kept.
 // Recurrence: j_{l-1} + j_{l+1} = (2l+1)/x j_l (both directions).
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <cmath>
 #include <mutex>
@@ -120,7 +121,7 @@ struct TableSink {
   char *table;
   const int64_t *off_q;
   int lmin, kbi, c;
-  double w;
+  double w;  // tau weight (times 2^scale for F16X3)
   int cur_lt;
   char *base;
   __device__ __forceinline__ void operator()(int l, double v) {
@@ -141,6 +142,12 @@ struct TableSink {
       const uint32_t o = sw128_offset(r, c * 2);
       *reinterpret_cast<__nv_bfloat16 *>(base + o) = hi;
       *reinterpret_cast<__nv_bfloat16 *>(base + 16384 + o) = lo;
+    } else if constexpr (MODE == GCAMB_F16X3) {
+      const __half hi = __double2half(wv);
+      const __half lo = __double2half(wv - (double)__half2float(hi));
+      const uint32_t o = sw128_offset(r, c * 2);
+      *reinterpret_cast<__half *>(base + o) = hi;
+      *reinterpret_cast<__half *>(base + 16384 + o) = lo;
     } else {  // TF32X3
       const uint32_t hi = tf32_rna((float)wv);
       const uint32_t lo = tf32_rna((float)(wv - (double)__uint_as_float(hi)));
@@ -160,7 +167,8 @@ __global__ void __launch_bounds__(128) bessel_table_kernel(const double *__restr
                                                            int lmin, int lmax, int nlt,
                                                            const int32_t *__restrict__ nkb,
                                                            const int64_t *__restrict__ off,
-                                                           const double *__restrict__ xs, int nxs, void *table) {
+                                                           const double *__restrict__ xs, int nxs, int scale_exp,
+                                                           void *table) {
   constexpr int KB = (MODE == GCAMB_TF32X3) ? 32 : 64;
   const int q = blockIdx.y;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -172,7 +180,8 @@ __global__ void __launch_bounds__(128) bessel_table_kernel(const double *__restr
   if (lt_last < 0) return;
   const int ltop = min(lmin + (lt_last + 1) * kTileL - 1, lmax);
   const double x = k[q] * (tau0 - tau[i]);
-  TableSink<MODE> sink{static_cast<char *>(table), off + (size_t)q * nlt, lmin, kbi, i % KB, wtau[i], -1, nullptr};
+  TableSink<MODE> sink{static_cast<char *>(table), off + (size_t)q * nlt, lmin, kbi, i % KB,
+                       ldexp(wtau[i], scale_exp), -1, nullptr};
   bessel_orders(x, lmin, ltop, xs, nxs, sink);
 }
 
@@ -205,6 +214,14 @@ int launch_bessel_table(gcamb_grid *g, int mode, cudaStream_t st) {
         nb += t.nkb[e];
       }
     t.nblocks = nb;
+    if (mode == GCAMB_F16X3) {
+      // |j_l| <= 1: scale so that max_i w_i j_l < 2^14, inside fp16's normal range
+      double wmax = 0.0;
+      for (double w : g->wtau) wmax = w > wmax ? w : wmax;
+      int e = 0;
+      if (wmax > 0.0) std::frexp(wmax, &e);  // wmax < 2^e
+      t.scale_exp = wmax > 0.0 ? 14 - e : 0;
+    }
     t.bytes = (size_t)nb * lay.block_bytes();
     cudaError_t e;
     if ((e = cudaMalloc(&t.d_data, std::max<size_t>(t.bytes, 256))) != cudaSuccess) {
@@ -223,26 +240,32 @@ int launch_bessel_table(gcamb_grid *g, int mode, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(t.d_data, 0, t.bytes, st);
   if (e != cudaSuccess) return cuda_fail(e, "bessel_table: memset");
   dim3 grid((g->ntau + 127) / 128, g->nk);
+  ProfScope prof(GCAMB_K_TABLE, st);
   switch (mode) {
     case GCAMB_PLAIN64:
       bessel_table_kernel<GCAMB_PLAIN64><<<grid, 128, 0, st>>>(g->d_k, g->d_tau, g->d_wtau, g->tau0, g->ntau, g->lmin,
                                                                g->lmax, g->nlt, t.d_nkb, t.d_off, g->d_xstart, g->nxs,
-                                                               t.d_data);
+                                                               t.scale_exp, t.d_data);
       break;
     case GCAMB_PLAIN32:
       bessel_table_kernel<GCAMB_PLAIN32><<<grid, 128, 0, st>>>(g->d_k, g->d_tau, g->d_wtau, g->tau0, g->ntau, g->lmin,
                                                                g->lmax, g->nlt, t.d_nkb, t.d_off, g->d_xstart, g->nxs,
-                                                               t.d_data);
+                                                               t.scale_exp, t.d_data);
       break;
     case GCAMB_BF16X3:
       bessel_table_kernel<GCAMB_BF16X3><<<grid, 128, 0, st>>>(g->d_k, g->d_tau, g->d_wtau, g->tau0, g->ntau, g->lmin,
                                                               g->lmax, g->nlt, t.d_nkb, t.d_off, g->d_xstart, g->nxs,
-                                                              t.d_data);
+                                                              t.scale_exp, t.d_data);
+      break;
+    case GCAMB_F16X3:
+      bessel_table_kernel<GCAMB_F16X3><<<grid, 128, 0, st>>>(g->d_k, g->d_tau, g->d_wtau, g->tau0, g->ntau, g->lmin,
+                                                             g->lmax, g->nlt, t.d_nkb, t.d_off, g->d_xstart, g->nxs,
+                                                             t.scale_exp, t.d_data);
       break;
     case GCAMB_TF32X3:
       bessel_table_kernel<GCAMB_TF32X3><<<grid, 128, 0, st>>>(g->d_k, g->d_tau, g->d_wtau, g->tau0, g->ntau, g->lmin,
                                                               g->lmax, g->nlt, t.d_nkb, t.d_off, g->d_xstart, g->nxs,
-                                                              t.d_data);
+                                                              t.scale_exp, t.d_data);
       break;
   }
   e = cudaGetLastError();

@@ -14,7 +14,7 @@ namespace gcamb {
 
 constexpr int kTileL = 128;      // multipoles per l-tile (UMMA M)
 constexpr int kMaxL = 20000;
-constexpr int kNumModes = 4;
+constexpr int kNumModes = 5;
 
 // Table layout of one mode: blocks of [planes][128 rows][kb cols], one block
 // per (k, l-tile, tau-block of kb nodes).  Rows are multipoles, columns tau.
@@ -34,6 +34,7 @@ inline ModeLayout mode_layout(int mode) {
     case GCAMB_PLAIN32: return {64, 1, 4, false};
     case GCAMB_BF16X3: return {64, 2, 2, true};
     case GCAMB_TF32X3: return {32, 2, 4, true};
+    case GCAMB_F16X3: return {64, 2, 2, true};
     default: return {0, 0, 0, false};
   }
 }
@@ -48,6 +49,7 @@ struct Table {
   int32_t *d_nkb = nullptr;
   int64_t *d_off = nullptr;
   size_t bytes = 0;
+  int scale_exp = 0;          // F16X3: entries are w_i j_l 2^scale_exp
 };
 
 }  // namespace gcamb
@@ -95,6 +97,15 @@ void drop_plans(const gcamb_grid *g);
 
 // Probes (probe.cu).
 int run_probe_flops(int what, double *flops);
+
+// Event tracer: brackets one kernel launch when profiling is on.
+struct ProfScope {
+  int id;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr, b = nullptr;
+  ProfScope(int id, cudaStream_t st);
+  ~ProfScope();
+};
 
 // Watson's bound (A&S 9.1.63) on log|j_l(x)| for x < l + 1/2.
 double log_watson_bound(int l, double x);

@@ -77,6 +77,7 @@ static int launch_plain_t(const gcamb_grid *g, const Table &t, const T *S, int M
   if (e != cudaSuccess) return cuda_fail(e, "los_transfer: smem attribute");
   dim3 grid(g->nlt, g->nk, (M + MC - 1) / MC);
   if (grid.z > 65535) return fail(GCAMB_EINVAL, "los_transfer: too many sources for one launch");
+  ProfScope prof(GCAMB_K_LOS_PLAIN, st);
   los_plain_kernel<T, MC><<<grid, 256, smem, st>>>(static_cast<const T *>(t.d_data), t.d_nkb, t.d_off, g->nk, g->nlt,
                                                    g->lmin, g->lmax, g->ntau, S, M, Delta);
   e = cudaGetLastError();
@@ -125,6 +126,7 @@ int launch_cl(const gcamb_grid *g, const void *Delta, int d_dtype, const double 
               cudaStream_t st) {
   if (M > 65535) return fail(GCAMB_EINVAL, "cl: too many sources for one launch");
   dim3 grid((g->nl + 255) / 256, M);
+  ProfScope prof(GCAMB_K_CL, st);
   if (d_dtype == GCAMB_F64)
     cl_kernel<double><<<grid, 256, 0, st>>>(static_cast<const double *>(Delta), Pk, g->d_wk, g->nk, g->nl, Cl);
   else

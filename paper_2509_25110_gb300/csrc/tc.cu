@@ -17,6 +17,7 @@
 // Every mbarrier wait is bounded (1 s); a timeout sets the device error flag,
 // the CTA drains its own copies and MMAs, frees TMEM and exits.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 #include <cmath>
@@ -124,9 +125,14 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   return d;
 }
 
-template <bool TF32>
+
+
+// Split modes of the batched path.
+enum TcMode { kBF16 = 0, kF16 = 1, kTF32 = 2 };
+
+template <int MODE>
 __device__ __forceinline__ void mma(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  if constexpr (TF32) {
+  if constexpr (MODE == kTF32) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtmem),
@@ -143,32 +149,49 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+template <int W>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, float (&v)[W]) {
+  uint32_t r[W];
+  if constexpr (W == 16) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+  } else {
+    static_assert(W == 8, "tmem_ld width");
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+  }
 #pragma unroll
-  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+  for (int j = 0; j < W; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Per k the accumulators are a pair: D_hh (hi*hi) and D_x (hi*lo + lo*hi).
+// Keeping the correction products out of D_hh leaves the main chain with a
+// third of the accumulate steps (the tensor core's FP32 accumulation error
+// grows with their number); D_x is ~2^-8 of D_hh, so its own rounding is
+// negligible.  The pairs are double-buffered across k when TMEM allows.
 template <int NT>
 struct TcCfg {
   static constexpr int kBBytes = 256 * NT;               // hi + lo planes of NT x 128 B
   static constexpr int kStageBytes = kABytes + kBBytes;
   static constexpr int kStages = (kSmemBudget / kStageBytes) > 4 ? 4 : (kSmemBudget / kStageBytes);
-  static constexpr int kTmemCols = 2 * NT < 32 ? 32 : 2 * NT;  // two accumulators of NT columns
+  static constexpr int kNBuf = (4 * NT <= 512) ? 2 : 1;
+  static constexpr int kTmemCols = kNBuf * 2 * NT < 32 ? 32 : kNBuf * 2 * NT;
   static constexpr int kSmemBytes = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
   static constexpr int kColsPerThread = NT / 2;
+  static constexpr int kChunk = NT >= 256 ? 8 : 16;      // TMEM load width (register budget)
 };
 
-template <int NT, bool TF32>
+template <int NT, int MODE>
 __global__ void __launch_bounds__(kThreads, 1) los_cl_tc_kernel(TcParams p) {
   using C = TcCfg<NT>;
   constexpr int S = C::kStages;
+  constexpr int NB = C::kNBuf;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + S * C::kStageBytes);
@@ -241,7 +264,7 @@ __global__ void __launch_bounds__(kThreads, 1) los_cl_tc_kernel(TcParams p) {
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------- MMA issuer
-      constexpr uint32_t fmt = TF32 ? 2u : 1u;
+      constexpr uint32_t fmt = MODE == kTF32 ? 2u : (MODE == kBF16 ? 1u : 0u);
       constexpr uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(NT >> 3) << 17) |
                                  ((uint32_t)(128 >> 4) << 24);
       int stage = 0;
@@ -251,10 +274,12 @@ __global__ void __launch_bounds__(kThreads, 1) los_cl_tc_kernel(TcParams p) {
       for (int q = it.qb; q < it.qe && ok; ++q) {
         const int nb = nkb_row[(size_t)q * p.nlt];
         if (nb == 0) continue;
-        const int buf = n & 1;
-        if (!mbar_wait(tempty0 + 8 * buf, (((uint32_t)n >> 1) & 1u) ^ 1u, abort_flag, p.err)) break;
+        const int buf = n % NB;
+        const uint32_t use = (uint32_t)(n / NB);
+        if (!mbar_wait(tempty0 + 8 * buf, (use & 1u) ^ 1u, abort_flag, p.err)) break;
         tc_fence_after();
-        const uint32_t d = tmem + (uint32_t)(buf * NT);
+        const uint32_t dhh = tmem + (uint32_t)(buf * 2 * NT);
+        const uint32_t dx = dhh + (uint32_t)NT;
         for (int kb = 0; kb < nb; ++kb) {
           if (!mbar_wait(full0 + 8 * stage, phase, abort_flag, p.err)) {
             ok = false;
@@ -267,9 +292,10 @@ __global__ void __launch_bounds__(kThreads, 1) los_cl_tc_kernel(TcParams p) {
           for (int kk = 0; kk < 4; ++kk) {
             const uint64_t ah = sw128_desc(sa + kk * 32), al = sw128_desc(sa + 16384 + kk * 32);
             const uint64_t bh = sw128_desc(sb + kk * 32), bl = sw128_desc(sb + NT * 128 + kk * 32);
-            mma<TF32>(d, ah, bh, idesc, (kb | kk) ? 1u : 0u);
-            mma<TF32>(d, ah, bl, idesc, 1u);
-            mma<TF32>(d, al, bh, idesc, 1u);
+            const uint32_t accum = (kb | kk) ? 1u : 0u;
+            mma<MODE>(dhh, ah, bh, idesc, accum);
+            mma<MODE>(dx, ah, bl, idesc, accum);
+            mma<MODE>(dx, al, bh, idesc, 1u);
           }
           mma_commit(empty0 + 8 * stage);
           if (++stage == S) {
@@ -286,7 +312,8 @@ __global__ void __launch_bounds__(kThreads, 1) los_cl_tc_kernel(TcParams p) {
       mbar_wait(drain, 0, nullptr, p.err);
     }
   } else {
-    // ---------------- epilogue
+    // ---------------- epilogue: acc += (sqrt(4 pi w_k P) (D_hh + D_x))^2
+    constexpr int CW = C::kChunk;
     const int sp = warp & 3;
     const int half = (warp - 2) >> 2;
     const int row = sp * 32 + lane;
@@ -298,22 +325,29 @@ __global__ void __launch_bounds__(kThreads, 1) los_cl_tc_kernel(TcParams p) {
     for (int q = it.qb; q < it.qe; ++q) {
       const int nb = nkb_row[(size_t)q * p.nlt];
       if (nb == 0) continue;
-      const int buf = n & 1;
-      if (!mbar_wait(tfull0 + 8 * buf, ((uint32_t)n >> 1) & 1u, abort_flag, p.err)) break;
+      const int buf = n % NB;
+      const uint32_t use = (uint32_t)(n / NB);
+      if (!mbar_wait(tfull0 + 8 * buf, use & 1u, abort_flag, p.err)) break;
       tc_fence_after();
       const float4 *w4 = reinterpret_cast<const float4 *>(p.wp + (size_t)q * p.mpad + it.mt * NT + col0);
-      const uint32_t taddr = tmem + ((uint32_t)(sp * 32) << 16) + (uint32_t)(buf * NT + col0);
+      const uint32_t taddr = tmem + ((uint32_t)(sp * 32) << 16) + (uint32_t)(buf * 2 * NT + col0);
 #pragma unroll
-      for (int c = 0; c < C::kColsPerThread / 16; ++c) {
-        float v[16];
-        tmem_ld16(taddr + c * 16, v);
+      for (int c = 0; c < C::kColsPerThread / CW; ++c) {
+        float vh[CW], vx[CW];
+        tmem_ld<CW>(taddr + c * CW, vh);
+        tmem_ld<CW>(taddr + NT + c * CW, vx);
+        tmem_wait_ld();
 #pragma unroll
-        for (int j4 = 0; j4 < 4; ++j4) {
-          const float4 w = __ldg(w4 + c * 4 + j4);
-          acc[c * 16 + 4 * j4 + 0] = fmaf(w.x, v[4 * j4 + 0] * v[4 * j4 + 0], acc[c * 16 + 4 * j4 + 0]);
-          acc[c * 16 + 4 * j4 + 1] = fmaf(w.y, v[4 * j4 + 1] * v[4 * j4 + 1], acc[c * 16 + 4 * j4 + 1]);
-          acc[c * 16 + 4 * j4 + 2] = fmaf(w.z, v[4 * j4 + 2] * v[4 * j4 + 2], acc[c * 16 + 4 * j4 + 2]);
-          acc[c * 16 + 4 * j4 + 3] = fmaf(w.w, v[4 * j4 + 3] * v[4 * j4 + 3], acc[c * 16 + 4 * j4 + 3]);
+        for (int j4 = 0; j4 < CW / 4; ++j4) {
+          const float4 w = __ldg(w4 + c * (CW / 4) + j4);
+          const float t0 = w.x * (vh[4 * j4 + 0] + vx[4 * j4 + 0]);
+          const float t1 = w.y * (vh[4 * j4 + 1] + vx[4 * j4 + 1]);
+          const float t2 = w.z * (vh[4 * j4 + 2] + vx[4 * j4 + 2]);
+          const float t3 = w.w * (vh[4 * j4 + 3] + vx[4 * j4 + 3]);
+          acc[c * CW + 4 * j4 + 0] = fmaf(t0, t0, acc[c * CW + 4 * j4 + 0]);
+          acc[c * CW + 4 * j4 + 1] = fmaf(t1, t1, acc[c * CW + 4 * j4 + 1]);
+          acc[c * CW + 4 * j4 + 2] = fmaf(t2, t2, acc[c * CW + 4 * j4 + 2]);
+          acc[c * CW + 4 * j4 + 3] = fmaf(t3, t3, acc[c * CW + 4 * j4 + 3]);
         }
       }
       tc_fence_before();
@@ -342,13 +376,18 @@ __device__ __forceinline__ uint32_t tf32_rna_u(float v) {
   return r;
 }
 
-// S[M][nk][ntau] fp32 -> split blocks [q][mt][kb]{hi plane, lo plane}, rows =
-// sources (NT per tile), 128-byte swizzled rows of KB tau (zero padded).
-template <bool TF32>
+__device__ __forceinline__ uint32_t sw_off(int n, int cbytes) {
+  return (uint32_t)n * 128u + ((uint32_t)((cbytes >> 4) ^ (n & 7)) << 4) + (uint32_t)(cbytes & 15);
+}
+
+// bf16 / tf32: S[M][nk][ntau] fp32 -> split blocks [q][mt][kb]{hi plane, lo
+// plane}; rows = sources (NT per tile), 128-byte swizzled rows of KB tau, zero
+// padded.  One thread per element.
+template <int MODE>
 __global__ void __launch_bounds__(256) split_sources_kernel(const float *__restrict__ S, int M, int nk, int ntau, int NT,
                                                             int n_mt, int nkbs, char *__restrict__ sp) {
-  constexpr int KB = TF32 ? 32 : 64;
-  constexpr int ES = TF32 ? 4 : 2;
+  constexpr int KB = MODE == kTF32 ? 32 : 64;
+  constexpr int ES = MODE == kTF32 ? 4 : 2;
   constexpr int ROWS = 256 / KB;  // rows per CTA
   const int qm = blockIdx.y;      // q * n_mt + mt
   const int q = qm / n_mt, mt = qm - q * n_mt;
@@ -361,8 +400,8 @@ __global__ void __launch_bounds__(256) split_sources_kernel(const float *__restr
   float v = 0.f;
   if (m < M && t < ntau) v = __ldg(S + ((size_t)m * nk + q) * ntau + t);
   char *blk = sp + (((size_t)qm * nkbs) + kb) * (size_t)(256 * NT);
-  const uint32_t o = (uint32_t)n * 128u + ((uint32_t)(((c * ES) >> 4) ^ (n & 7)) << 4) + (uint32_t)((c * ES) & 15);
-  if constexpr (TF32) {
+  const uint32_t o = sw_off(n, c * ES);
+  if constexpr (MODE == kTF32) {
     const uint32_t hi = tf32_rna_u(v);
     const uint32_t lo = tf32_rna_u(v - __uint_as_float(hi));
     *reinterpret_cast<uint32_t *>(blk + o) = hi;
@@ -375,12 +414,58 @@ __global__ void __launch_bounds__(256) split_sources_kernel(const float *__restr
   }
 }
 
-// wp[q][m] = 4 pi w_k P[m][q] (zero for padded sources).
+// wq[q][m] = sqrt(4 pi w_k P[m][q]) (zero for padded sources).
 __global__ void weights_kernel(const double *__restrict__ Pk, const double *__restrict__ wk, int M, int nk, int mpad,
-                               float *__restrict__ wp) {
+                               float *__restrict__ wq) {
   const int q = blockIdx.x;
   for (int m = threadIdx.x; m < mpad; m += blockDim.x)
-    wp[(size_t)q * mpad + m] = m < M ? (float)(4.0 * 3.14159265358979323846 * wk[q] * Pk[(size_t)m * nk + q]) : 0.f;
+    wq[(size_t)q * mpad + m] =
+        m < M ? (float)sqrt(4.0 * 3.14159265358979323846 * wk[q] * Pk[(size_t)m * nk + q]) : 0.f;
+}
+
+// fp16: one warp per (k, source) row.  The row is scaled by 2^s so that its
+// largest |S| lies in [2^13, 2^14) (fp16 keeps 11 significant bits only in
+// its normal range), split into fp16 hi/lo, and written like the bf16 path.
+// The weight absorbs the scales: wq = sqrt(4 pi w_k P) 2^-(sJ + s), where
+// 2^sJ is the table's scale, so (wq D')^2 is the unscaled contribution.
+__global__ void __launch_bounds__(256) split_sources_f16_kernel(const float *__restrict__ S,
+                                                                const double *__restrict__ Pk,
+                                                                const double *__restrict__ wk, int M, int nk,
+                                                                int ntau, int NT, int n_mt, int nkbs, int mpad,
+                                                                int sJ, char *__restrict__ sp,
+                                                                float *__restrict__ wq) {
+  const int lane = threadIdx.x & 31;
+  const size_t row = (size_t)blockIdx.x * 8 + (threadIdx.x >> 5);  // q * mpad + m
+  if (row >= (size_t)nk * mpad) return;
+  const int q = (int)(row / mpad), mfull = (int)(row - (size_t)q * mpad);
+  const int mt = mfull / NT, n = mfull - mt * NT;
+  const bool live = mfull < M;
+  const float *src = S + ((size_t)(live ? mfull : 0) * nk + q) * ntau;
+  float mx = 0.f;
+  if (live)
+    for (int t = lane; t < ntau; t += 32) mx = fmaxf(mx, fabsf(__ldg(src + t)));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  int s = 0;
+  if (mx > 0.f) {
+    int e;
+    frexpf(mx, &e);  // mx < 2^e
+    s = 14 - e;
+    s = s < -40 ? -40 : (s > 80 ? 80 : s);
+  }
+  char *base = sp + ((size_t)(q * n_mt + mt) * nkbs) * (size_t)(256 * NT);
+  for (int t = lane; t < nkbs * 64; t += 32) {
+    const float v = (live && t < ntau) ? ldexpf(__ldg(src + t), s) : 0.f;
+    const __half hi = __float2half_rn(v);
+    const __half lo = __float2half_rn(v - __half2float(hi));
+    char *blk = base + (size_t)(t >> 6) * (256 * NT);
+    const uint32_t o = sw_off(n, (t & 63) * 2);
+    *reinterpret_cast<__half *>(blk + o) = hi;
+    *reinterpret_cast<__half *>(blk + NT * 128 + o) = lo;
+  }
+  if (lane == 0)
+    wq[row] = live ? (float)ldexp(sqrt(4.0 * 3.14159265358979323846 * wk[q] * Pk[(size_t)mfull * nk + q]), -(sJ + s))
+                   : 0.f;
 }
 
 // C[m][l] = sum over the tile's items (fixed order) of the FP32 chunk sums, in FP64.
@@ -414,11 +499,16 @@ struct TcPlan {
 std::mutex g_plan_mu;
 std::vector<std::pair<const gcamb_grid *, TcPlan *>> g_plans;
 
+// Source-tile width: 64 for small batches, else 128 (double-buffered
+// accumulator pairs); GCAMB_TC_NT=64|128|256 overrides it.
 int pick_nt(int M, int *n_mt) {
-  if (M <= 64) { *n_mt = 1; return 64; }
-  if (M <= 128) { *n_mt = 1; return 128; }
-  *n_mt = (M + 255) / 256;
-  return 256;
+  int nt = M <= 64 ? 64 : 128;
+  if (const char *e = getenv("GCAMB_TC_NT")) {
+    const int v = atoi(e);
+    if (v == 64 || v == 128 || v == 256) nt = v;
+  }
+  *n_mt = (M + nt - 1) / nt;
+  return nt;
 }
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -488,8 +578,10 @@ void plan_layout(const gcamb_grid *g, int M, int mode, TcPlan &pl) {
 
 TcPlan *get_plan(const gcamb_grid *g, int M, int mode, int *rc) {
   std::lock_guard<std::mutex> lk(g_plan_mu);
+  int nmt = 0;
+  const int nt = pick_nt(M, &nmt);
   for (auto &e : g_plans)
-    if (e.first == g && e.second->M == M && e.second->mode == mode) return e.second;
+    if (e.first == g && e.second->M == M && e.second->mode == mode && e.second->NT == nt) return e.second;
   TcPlan *pl = new TcPlan();
   plan_layout(g, M, mode, *pl);
   cudaError_t e1 = cudaMalloc(&pl->d_items, std::max<size_t>(1, pl->items.size()) * sizeof(TcItem));
@@ -497,6 +589,7 @@ TcPlan *get_plan(const gcamb_grid *g, int M, int mode, int *rc) {
   cudaError_t e3 = cudaMalloc(&pl->d_tile_items, std::max<size_t>(1, pl->tile_items.size()) * sizeof(int));
   if (e1 || e2 || e3) {
     *rc = cuda_fail(e1 ? e1 : (e2 ? e2 : e3), "los_cl: plan allocation");
+    delete pl;
     return nullptr;
   }
   cudaMemcpy(pl->d_items, pl->items.data(), pl->items.size() * sizeof(TcItem), cudaMemcpyHostToDevice);
@@ -511,7 +604,7 @@ TcPlan *get_plan(const gcamb_grid *g, int M, int mode, int *rc) {
   return pl;
 }
 
-template <int NT, bool TF32>
+template <int NT, int MODE>
 int launch_tc(const gcamb_grid *g, const TcPlan &pl, const float *S, const double *Pk, double *Cl, char *ws,
               cudaStream_t st) {
   using Cfg = TcCfg<NT>;
@@ -519,34 +612,54 @@ int launch_tc(const gcamb_grid *g, const TcPlan &pl, const float *S, const doubl
   char *sp = ws + pl.off_sp;
   float *wp = reinterpret_cast<float *>(ws + pl.off_wp);
   float *part = reinterpret_cast<float *>(ws + pl.off_part);
-  {
-    constexpr int KB = TF32 ? 32 : 64;
-    dim3 grid(pl.nkbs * (NT / (256 / KB)), g->nk * pl.n_mt);
-    split_sources_kernel<TF32><<<grid, 256, 0, st>>>(S, pl.M, g->nk, g->ntau, NT, pl.n_mt, pl.nkbs, sp);
+  if constexpr (MODE == kF16) {
+    const size_t rows = (size_t)g->nk * pl.mpad;
+    ProfScope prof(GCAMB_K_SPLIT, st);
+    split_sources_f16_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, st>>>(
+        S, Pk, g->d_wk, pl.M, g->nk, g->ntau, NT, pl.n_mt, pl.nkbs, pl.mpad, t.scale_exp, sp, wp);
+  } else {
+    {
+      constexpr int KB = MODE == kTF32 ? 32 : 64;
+      dim3 grid(pl.nkbs * (NT / (256 / KB)), g->nk * pl.n_mt);
+      ProfScope prof(GCAMB_K_SPLIT, st);
+      split_sources_kernel<MODE><<<grid, 256, 0, st>>>(S, pl.M, g->nk, g->ntau, NT, pl.n_mt, pl.nkbs, sp);
+    }
+    ProfScope prof(GCAMB_K_WEIGHTS, st);
+    weights_kernel<<<g->nk, 256, 0, st>>>(Pk, g->d_wk, pl.M, g->nk, pl.mpad, wp);
   }
-  weights_kernel<<<g->nk, 256, 0, st>>>(Pk, g->d_wk, pl.M, g->nk, pl.mpad, wp);
   if (!pl.items.empty()) {
-    cudaError_t e = cudaFuncSetAttribute(los_cl_tc_kernel<NT, TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(los_cl_tc_kernel<NT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          Cfg::kSmemBytes);
     if (e != cudaSuccess) return cuda_fail(e, "los_cl: smem attribute");
     TcParams prm{static_cast<const char *>(t.d_data), t.d_off, t.d_nkb, sp, wp, pl.d_items, part,
                  device_error_flag(), g->nlt, pl.n_mt, pl.nkbs, pl.mpad};
     if (!prm.err) return fail(GCAMB_ECUDA, "los_cl: error flag allocation");
-    los_cl_tc_kernel<NT, TF32><<<(unsigned)pl.items.size(), kThreads, Cfg::kSmemBytes, st>>>(prm);
+    ProfScope prof(GCAMB_K_TC, st);
+    los_cl_tc_kernel<NT, MODE><<<(unsigned)pl.items.size(), kThreads, Cfg::kSmemBytes, st>>>(prm);
   }
   dim3 rgrid(NT, g->nlt * pl.n_mt);
+  ProfScope prof(GCAMB_K_REDUCE, st);
   reduce_kernel<<<rgrid, 128, 0, st>>>(part, pl.d_tile_ptr, pl.d_tile_items, NT, pl.n_mt, pl.M, g->lmin, g->lmax, Cl);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "los_cl: launch");
   return GCAMB_OK;
 }
 
+template <int MODE>
+int launch_mode(const gcamb_grid *g, const TcPlan &pl, const float *S, const double *Pk, double *Cl, char *w,
+                cudaStream_t st) {
+  switch (pl.NT) {
+    case 64: return launch_tc<64, MODE>(g, pl, S, Pk, Cl, w, st);
+    case 128: return launch_tc<128, MODE>(g, pl, S, Pk, Cl, w, st);
+    default: return launch_tc<256, MODE>(g, pl, S, Pk, Cl, w, st);
+  }
+}
+
 }  // namespace
 
 size_t los_cl_workspace_bytes(const gcamb_grid *g, int M, int mode) {
-  TcPlan pl;
   if (!g->tab[mode].built) {
-    // layout only depends on the table's block counts; estimate with the extents
+    // without the table: an upper bound from the extents
     TcPlan tmp;
     tmp.NT = pick_nt(M, &tmp.n_mt);
     const ModeLayout lay = mode_layout(mode);
@@ -554,7 +667,7 @@ size_t los_cl_workspace_bytes(const gcamb_grid *g, int M, int mode) {
     tmp.mpad = tmp.n_mt * tmp.NT;
     size_t sp_bytes = (size_t)g->nk * tmp.n_mt * tmp.nkbs * 256 * tmp.NT;
     size_t wp_bytes = (size_t)g->nk * tmp.mpad * sizeof(float);
-    size_t max_items = (size_t)g->nk * g->nlt * tmp.n_mt;  // upper bound
+    size_t max_items = (size_t)g->nk * g->nlt * tmp.n_mt;
     return align256(sp_bytes) + align256(wp_bytes) + align256(max_items * tmp.NT * 128 * sizeof(float));
   }
   int rc = 0;
@@ -569,11 +682,10 @@ int launch_los_cl(const gcamb_grid *g, const float *S, const double *Pk, int M, 
   if (!pl) return rc ? rc : fail(GCAMB_ECUDA, "los_cl: plan");
   if (ws_bytes < pl->ws_bytes) return fail(GCAMB_EINVAL, "los_cl: workspace too small");
   char *w = static_cast<char *>(ws);
-  const bool tf = mode == GCAMB_TF32X3;
-  switch (pl->NT) {
-    case 64: return tf ? launch_tc<64, true>(g, *pl, S, Pk, Cl, w, st) : launch_tc<64, false>(g, *pl, S, Pk, Cl, w, st);
-    case 128: return tf ? launch_tc<128, true>(g, *pl, S, Pk, Cl, w, st) : launch_tc<128, false>(g, *pl, S, Pk, Cl, w, st);
-    default: return tf ? launch_tc<256, true>(g, *pl, S, Pk, Cl, w, st) : launch_tc<256, false>(g, *pl, S, Pk, Cl, w, st);
+  switch (mode) {
+    case GCAMB_TF32X3: return launch_mode<kTF32>(g, *pl, S, Pk, Cl, w, st);
+    case GCAMB_F16X3: return launch_mode<kF16>(g, *pl, S, Pk, Cl, w, st);
+    default: return launch_mode<kBF16>(g, *pl, S, Pk, Cl, w, st);
   }
 }
 

@@ -17,10 +17,12 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgcamb.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ESTATE, EUNSUPPORTED, ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
-PLAIN64, PLAIN32, BF16X3, TF32X3 = 0, 1, 2, 3
+PLAIN64, PLAIN32, BF16X3, TF32X3, F16X3 = 0, 1, 2, 3, 4
 F64, F32 = 0, 1
-MODE_NAMES = {PLAIN64: "plain64", PLAIN32: "plain32", BF16X3: "bf16x3", TF32X3: "tf32x3"}
+MODE_NAMES = {PLAIN64: "plain64", PLAIN32: "plain32", BF16X3: "bf16x3", TF32X3: "tf32x3", F16X3: "f16x3"}
 INFO_N = 8
+K_TABLE, K_LOS_PLAIN, K_CL, K_SPLIT, K_WEIGHTS, K_TC, K_REDUCE = range(7)
+K_NAMES = ("bessel_table", "los_plain", "cl", "split_sources", "weights", "los_cl_tc", "reduce")
 
 _vp = ctypes.c_void_p
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -57,6 +59,8 @@ def lib():
     L.gcamb_los_cl_workspace.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
     L.gcamb_los_cl.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_size_t, _vp]
     L.gcamb_sync.argtypes = [_vp]
+    L.gcamb_profile_enable.argtypes = [ctypes.c_int]
+    L.gcamb_profile_read.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
     L.gcamb_probe_flops.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
     _lib = L
     return L
@@ -243,3 +247,16 @@ def probe_flops(what: int) -> float:
     f = ctypes.c_double()
     _check(lib().gcamb_probe_flops(int(what), ctypes.byref(f)))
     return float(f.value)
+
+
+def profile_enable(on: bool = True):
+    """Starts (clearing the accumulators) or stops the library's event tracer."""
+    _check(lib().gcamb_profile_enable(1 if on else 0))
+
+
+def profile_read(kernel: int):
+    """(total device ms, launches) of one kernel id since profile_enable."""
+    ms = ctypes.c_double()
+    n = ctypes.c_int64()
+    _check(lib().gcamb_profile_read(int(kernel), ctypes.byref(ms), ctypes.byref(n)))
+    return float(ms.value), int(n.value)
