@@ -190,6 +190,39 @@ int gcamb_los_cl(const gcamb_grid *g, const float *S, const double *Pk, int M, i
                  double *Cl, void *ws, size_t ws_bytes, void *stream);
 
 /*
+ * gcamb_los_cl without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that may not allocate device memory,
+ * such as a likelihood callback running inside a sampler or host framework
+ * that owns the device's memory budget, or code that cannot afford
+ * cudaMalloc's implicit device-wide synchronisation.
+ *
+ * Same arguments and result as gcamb_los_cl, without the workspace: every
+ * scratch byte (the work list, the split sources, the weights and the
+ * k-chunk partial sums) lives in one statically allocated 64 MiB device
+ * buffer inside the library, which every device that loads the library
+ * holds until the process exits.  The call makes no cudaMalloc, cudaFree or
+ * other allocating call.
+ *   status   device int, or NULL: set to GCAMB_ETIMEOUT if a bounded wait
+ *            on the device gave up (left untouched otherwise)
+ * Limits and behaviour:
+ *  - Problems whose scratch exceeds 64 MiB are rejected with GCAMB_EINVAL
+ *    (the message gives the bytes needed); use gcamb_los_cl for them.  The
+ *    split sources take about 4 bytes per (k, tau, source) with the sources
+ *    rounded up to a multiple of 64, so with 1000 tau nodes the limit is
+ *    roughly nk * M <= 15,000.
+ *  - The first call on a device looks up the buffer's device address
+ *    (cudaGetSymbolAddress) and caches it; make that first call before any
+ *    stream capture.
+ *  - All calls share the one buffer, and each call overwrites all of the
+ *    scratch it uses before reading it, so nothing has to start at zero.
+ *    Calls whose device work overlaps (on different streams, or from
+ *    different host threads) race on the buffer and give wrong results:
+ *    serialise them.
+ */
+int gcamb_los_cl_noalloc(const gcamb_grid *g, const float *S, const double *Pk, int M, int mode,
+                         double *Cl, int *status, void *stream);
+
+/*
  * Waits for `stream` and reports any error the library's kernels raised on
  * the device since the last gcamb_sync (GCAMB_ETIMEOUT for a bounded wait
  * that gave up), or a CUDA error (GCAMB_ECUDA).  Clears the device flag.

@@ -94,6 +94,9 @@ size_t los_cl_workspace_bytes(const gcamb_grid *g, int M, int mode);
 int launch_los_cl(const gcamb_grid *g, const float *S, const double *Pk, int M, int mode, double *Cl,
                   void *ws, size_t ws_bytes, cudaStream_t st);
 void drop_plans(const gcamb_grid *g);
+size_t los_cl_fixed_bytes(const gcamb_grid *g, int M, int mode);
+int launch_los_cl_fixed(const gcamb_grid *g, const float *S, const double *Pk, int M, int mode, double *Cl,
+                        char *scratch, size_t cap, int *status, cudaStream_t st);
 
 // Probes (probe.cu).
 int run_probe_flops(int what, double *flops);

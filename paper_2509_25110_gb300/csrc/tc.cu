@@ -22,6 +22,7 @@
 #include <algorithm>
 #include <cmath>
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include "internal.h"
@@ -606,7 +607,7 @@ TcPlan *get_plan(const gcamb_grid *g, int M, int mode, int *rc) {
 
 template <int NT, int MODE>
 int launch_tc(const gcamb_grid *g, const TcPlan &pl, const float *S, const double *Pk, double *Cl, char *ws,
-              cudaStream_t st) {
+              cudaStream_t st, int *err_word = nullptr, bool use_err_word = false) {
   using Cfg = TcCfg<NT>;
   const Table &t = g->tab[pl.mode];
   char *sp = ws + pl.off_sp;
@@ -632,8 +633,8 @@ int launch_tc(const gcamb_grid *g, const TcPlan &pl, const float *S, const doubl
                                          Cfg::kSmemBytes);
     if (e != cudaSuccess) return cuda_fail(e, "los_cl: smem attribute");
     TcParams prm{static_cast<const char *>(t.d_data), t.d_off, t.d_nkb, sp, wp, pl.d_items, part,
-                 device_error_flag(), g->nlt, pl.n_mt, pl.nkbs, pl.mpad};
-    if (!prm.err) return fail(GCAMB_ECUDA, "los_cl: error flag allocation");
+                 use_err_word ? err_word : device_error_flag(), g->nlt, pl.n_mt, pl.nkbs, pl.mpad};
+    if (!prm.err && !use_err_word) return fail(GCAMB_ECUDA, "los_cl: error flag allocation");
     ProfScope prof(GCAMB_K_TC, st);
     los_cl_tc_kernel<NT, MODE><<<(unsigned)pl.items.size(), kThreads, Cfg::kSmemBytes, st>>>(prm);
   }
@@ -647,11 +648,11 @@ int launch_tc(const gcamb_grid *g, const TcPlan &pl, const float *S, const doubl
 
 template <int MODE>
 int launch_mode(const gcamb_grid *g, const TcPlan &pl, const float *S, const double *Pk, double *Cl, char *w,
-                cudaStream_t st) {
+                cudaStream_t st, int *err_word = nullptr, bool use_err_word = false) {
   switch (pl.NT) {
-    case 64: return launch_tc<64, MODE>(g, pl, S, Pk, Cl, w, st);
-    case 128: return launch_tc<128, MODE>(g, pl, S, Pk, Cl, w, st);
-    default: return launch_tc<256, MODE>(g, pl, S, Pk, Cl, w, st);
+    case 64: return launch_tc<64, MODE>(g, pl, S, Pk, Cl, w, st, err_word, use_err_word);
+    case 128: return launch_tc<128, MODE>(g, pl, S, Pk, Cl, w, st, err_word, use_err_word);
+    default: return launch_tc<256, MODE>(g, pl, S, Pk, Cl, w, st, err_word, use_err_word);
   }
 }
 
@@ -687,6 +688,52 @@ int launch_los_cl(const gcamb_grid *g, const float *S, const double *Pk, int M, 
     case GCAMB_F16X3: return launch_mode<kF16>(g, *pl, S, Pk, Cl, w, st);
     default: return launch_mode<kBF16>(g, *pl, S, Pk, Cl, w, st);
   }
+}
+
+// Fixed-buffer variant for gcamb_los_cl_noalloc: the plan is computed on the
+// host and its arrays, the split sources, the weights and the chunk partials
+// all live in the caller's buffer `scratch` (no device allocation).
+size_t los_cl_fixed_bytes(const gcamb_grid *g, int M, int mode) {
+  TcPlan pl;
+  plan_layout(g, M, mode, pl);
+  return align256(pl.items.size() * sizeof(TcItem)) + align256(pl.tile_ptr.size() * sizeof(int)) +
+         align256(pl.tile_items.size() * sizeof(int)) + pl.ws_bytes;
+}
+
+int launch_los_cl_fixed(const gcamb_grid *g, const float *S, const double *Pk, int M, int mode, double *Cl,
+                        char *scratch, size_t cap, int *status, cudaStream_t st) {
+  TcPlan pl;
+  plan_layout(g, M, mode, pl);
+  const size_t b_items = align256(pl.items.size() * sizeof(TcItem));
+  const size_t b_ptr = align256(pl.tile_ptr.size() * sizeof(int));
+  const size_t b_ti = align256(pl.tile_items.size() * sizeof(int));
+  const size_t need = b_items + b_ptr + b_ti + pl.ws_bytes;
+  if (need > cap)
+    return fail(GCAMB_EINVAL, "los_cl_noalloc: needs " + std::to_string(need) + " bytes of scratch, the fixed buffer holds " +
+                                  std::to_string(cap) + "; use gcamb_los_cl with a caller workspace");
+  pl.d_items = reinterpret_cast<TcItem *>(scratch);
+  pl.d_tile_ptr = reinterpret_cast<int *>(scratch + b_items);
+  pl.d_tile_items = reinterpret_cast<int *>(scratch + b_items + b_ptr);
+  char *ws = scratch + b_items + b_ptr + b_ti;
+  cudaError_t e = cudaSuccess;
+  if (!pl.items.empty())
+    e = cudaMemcpyAsync(pl.d_items, pl.items.data(), pl.items.size() * sizeof(TcItem), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(pl.d_tile_ptr, pl.tile_ptr.data(), pl.tile_ptr.size() * sizeof(int), cudaMemcpyHostToDevice,
+                        st);
+  if (e == cudaSuccess && !pl.tile_items.empty())
+    e = cudaMemcpyAsync(pl.d_tile_items, pl.tile_items.data(), pl.tile_items.size() * sizeof(int),
+                        cudaMemcpyHostToDevice, st);
+  // copies from pageable memory return once the host data is staged, so the
+  // vectors may go out of scope when this function returns
+  if (e != cudaSuccess) return cuda_fail(e, "los_cl_noalloc: plan upload");
+  int rc;
+  switch (mode) {
+    case GCAMB_TF32X3: rc = launch_mode<kTF32>(g, pl, S, Pk, Cl, ws, st, status, true); break;
+    case GCAMB_F16X3: rc = launch_mode<kF16>(g, pl, S, Pk, Cl, ws, st, status, true); break;
+    default: rc = launch_mode<kBF16>(g, pl, S, Pk, Cl, ws, st, status, true); break;
+  }
+  return rc;
 }
 
 void drop_plans(const gcamb_grid *g) {

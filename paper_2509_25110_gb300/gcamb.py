@@ -59,6 +59,7 @@ def lib():
     L.gcamb_los_cl_workspace.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
     L.gcamb_los_cl.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_size_t, _vp]
     L.gcamb_sync.argtypes = [_vp]
+    L.gcamb_los_cl_noalloc.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]
     L.gcamb_profile_enable.argtypes = [ctypes.c_int]
     L.gcamb_profile_read.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
     L.gcamb_probe_flops.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
@@ -236,6 +237,20 @@ def los_cl(g: Grid, S, Pk, mode: int, Cl=None, ws=None, stream=None):
                               _dev(Pk, torch.float64, (M, g.nk), "Pk"), M, int(mode),
                               _dev(Cl, torch.float64, (M, g.nl), "Cl"), _dev(ws, torch.uint8, name="ws"),
                               ws.numel(), _stream(stream)))
+    return Cl
+
+
+def los_cl_noalloc(g: Grid, S, Pk, mode: int, Cl, status=None, stream=None):
+    """gcamb_los_cl without a workspace: the library's fixed 64 MiB device
+    buffer holds all scratch, and nothing is allocated by the call.  Cl must
+    be given (this function allocates nothing either); status, if given, is a
+    device int32 tensor of one element."""
+    import torch
+    M = S.shape[0]
+    st = _vp(None) if status is None else _dev(status, torch.int32, (1,), "status")
+    _check(lib().gcamb_los_cl_noalloc(g.handle, _dev(S, torch.float32, (M, g.nk, g.ntau), "S"),
+                                      _dev(Pk, torch.float64, (M, g.nk), "Pk"), M, int(mode),
+                                      _dev(Cl, torch.float64, (M, g.nl), "Cl"), st, _stream(stream)))
     return Cl
 
 
