@@ -190,6 +190,65 @@ int gcamb_los_cl(const gcamb_grid *g, const float *S, const double *Pk, int M, i
                  double *Cl, void *ws, size_t ws_bytes, void *stream);
 
 /*
+ * Plans: batches of sources with their own l_max and k range on one grid
+ * (the uneven batch), run as one persistent tensor-core kernel replayed from
+ * a CUDA graph.  Eq. (1) is summed for source m over its own k prefix
+ * k[0..nk_m[m]) (trapezoid in ln k on that prefix) and Eq. (2) for its own
+ * multipoles l <= lmax_m[m]; C_l above lmax_m[m] is written as 0.  The
+ * paper's counterpart is Algorithm 1's gang loop over modes, which runs one
+ * cosmology at a time.
+ *
+ *   lmax_m[M], nk_m[M]  host int, or both NULL (every source uses the whole
+ *                       grid, as gcamb_los_cl); lmin <= lmax_m <= lmax,
+ *                       1 <= nk_m <= nk.  Copied.
+ *   mode                GCAMB_BF16X3, GCAMB_F16X3 or GCAMB_TF32X3; the grid's
+ *                       table for this mode must be built.
+ *   tune                0: source-tile width from a heuristic;
+ *                       1: the first gcamb_plan_launch times the candidate
+ *                       widths (64, 128, 256 sources) on its inputs and keeps
+ *                       the fastest.  If the environment variable
+ *                       GCAMB_TUNE_CACHE names a file, choices are appended
+ *                       there (one JSON object per line, keyed by device,
+ *                       grid and batch) and reused by later plans.
+ * Sources are processed sorted by l_max (descending), so that at each (k,
+ * l-tile) the sources that need it are a prefix of the source tiles; work
+ * items are spread over one persistent CTA per SM, longest first.
+ */
+typedef struct gcamb_plan gcamb_plan;
+
+#define GCAMB_PLAN_INFO_N 8
+
+int gcamb_plan_create(gcamb_grid *g, int M, const int *lmax_m, const int *nk_m, int mode, int tune,
+                      gcamb_plan **out);
+
+/* Releases the plan and its graph.  NULL is accepted. */
+int gcamb_plan_destroy(gcamb_plan *p);
+
+/* Device workspace bytes gcamb_plan_launch needs (the largest candidate's
+ * when tuning). */
+int gcamb_plan_workspace(const gcamb_plan *p, size_t *bytes);
+
+/*
+ * Runs the plan: S[M][nk][ntau] device float (rows k >= nk_m[m] are
+ * ignored), Pk[M][nk] device double (>= 0), Cl[M][nl] device double.
+ * The first launch (and any launch whose pointers or stream differ from the
+ * previous one) captures the split, contraction and reduction launches into a
+ * CUDA graph; later launches replay it.  The first launch of a tuning plan
+ * runs each candidate three times before capturing.  Must not itself be
+ * called inside a stream capture.
+ */
+int gcamb_plan_launch(gcamb_plan *p, const float *S, const double *Pk, double *Cl, void *ws, size_t ws_bytes,
+                      void *stream);
+
+/*
+ * Plan summary (host, int64[GCAMB_PLAN_INFO_N]): [0] source-tile width in use
+ * (0 before tuning), [1] work items, [2] persistent CTAs, [3] graph captures,
+ * [4] graph replays, [5] 1 if the width came from timing (now or cached),
+ * [6] M, [7] workspace bytes of the width in use.
+ */
+int gcamb_plan_info(const gcamb_plan *p, int64_t *info);
+
+/*
  * gcamb_los_cl without any device allocation.  The paper has no counterpart:
  * this entry point exists for callers that may not allocate device memory,
  * such as a likelihood callback running inside a sampler or host framework

@@ -95,6 +95,8 @@ void drain_pending() {
 ProfScope::ProfScope(int id_, cudaStream_t st_) : id(id_), st(st_) {
   std::lock_guard<std::mutex> lk(g_prof_mu);
   if (!g_prof_on) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
   if (g_prof_pending.size() > 4096) drain_pending();
   a = take_event();
   b = take_event();

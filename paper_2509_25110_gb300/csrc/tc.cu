@@ -21,7 +21,10 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <mutex>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -36,6 +39,7 @@ constexpr int kThreads = 32 * (2 + kEpiWarps);
 constexpr int kKChunkMax = 64;     // k per work item: bounds the FP32 partial-sum length
 constexpr int kABytes = 32768;     // one table block: hi + lo planes of 128 x 128 B
 constexpr int kSmemBudget = 196608;
+constexpr int kItemSlots = 4;       // item indices in flight from the producer to the other roles
 
 struct TcItem {
   int lt, mt, qb, qe;
@@ -48,6 +52,8 @@ struct TcParams {
   const char *sp;        // split sources [nk][n_mt][nkbs] blocks of 256*NT bytes
   const float *wp;       // [nk][mpad] 4 pi w_k P_m(k)
   const TcItem *items;
+  int *counter;          // next item to hand out (zeroed before each launch)
+  int nitems;
   float *partial;        // [n_items][NT][128]
   int *err;
   int nlt, n_mt, nkbs, mpad;
@@ -196,14 +202,16 @@ __global__ void __launch_bounds__(kThreads, 1) los_cl_tc_kernel(TcParams p) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + S * C::kStageBytes);
-  // bars: full[S], empty[S], tfull[2], tempty[2], drain
+  // bars: full[S], empty[S], tfull[2], tempty[2], drain, (tmem slot), (abort),
+  //       ifull[4], iempty[4], (item slots)
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * S + 5);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 2 * S + 6);
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + S);
   const uint32_t tfull0 = smem_u32(bars + 2 * S), tempty0 = smem_u32(bars + 2 * S + 2);
   const uint32_t drain = smem_u32(bars + 2 * S + 4);
+  const uint32_t ifull0 = smem_u32(bars + 2 * S + 7), iempty0 = smem_u32(bars + 2 * S + 11);
+  volatile int *islot = reinterpret_cast<volatile int *>(bars + 2 * S + 15);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const TcItem it = p.items[blockIdx.x];
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
@@ -215,6 +223,10 @@ __global__ void __launch_bounds__(kThreads, 1) los_cl_tc_kernel(TcParams p) {
     mbar_init(tempty0, kEpiWarps);
     mbar_init(tempty0 + 8, kEpiWarps);
     mbar_init(drain, 1);
+    for (int s = 0; s < kItemSlots; ++s) {
+      mbar_init(ifull0 + 8 * s, 1);
+      mbar_init(iempty0 + 8 * s, 1 + kEpiWarps);
+    }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -228,8 +240,6 @@ __global__ void __launch_bounds__(kThreads, 1) los_cl_tc_kernel(TcParams p) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const int32_t *nkb_row = p.nkb + it.lt;
-  const int64_t *off_row = p.off + it.lt;
 
   if (warp == 0) {
     if (lane == 0) {
@@ -238,6 +248,23 @@ __global__ void __launch_bounds__(kThreads, 1) los_cl_tc_kernel(TcParams p) {
       uint32_t phase = 0;
       int armed_phase[4] = {-1, -1, -1, -1};
       bool ok = true;
+      int is = 0;
+      uint32_t iph = 0;
+      while (ok) {
+      // hand out the next item (or -1) to the MMA issuer and the epilogue
+      if (!mbar_wait(iempty0 + 8 * is, iph ^ 1u, abort_flag, p.err)) break;
+      int item = atomicAdd(p.counter, 1);
+      if (item >= p.nitems) item = -1;
+      islot[is] = item;
+      mbar_arrive(ifull0 + 8 * is);
+      if (++is == kItemSlots) {
+        is = 0;
+        iph ^= 1u;
+      }
+      if (item < 0) break;
+      const TcItem it = p.items[item];
+      const int32_t *nkb_row = p.nkb + it.lt;
+      const int64_t *off_row = p.off + it.lt;
       for (int q = it.qb; q < it.qe && ok; ++q) {
         const int nb = nkb_row[(size_t)q * p.nlt];
         const char *a = p.table + (size_t)off_row[(size_t)q * p.nlt] * kABytes;
@@ -258,6 +285,7 @@ __global__ void __launch_bounds__(kThreads, 1) los_cl_tc_kernel(TcParams p) {
           }
         }
       }
+      }
       // no copy may still be landing when the CTA exits
       for (int s = 0; s < S; ++s)
         if (armed_phase[s] >= 0) mbar_wait(full0 + 8 * s, (uint32_t)armed_phase[s], nullptr, p.err);
@@ -272,12 +300,28 @@ __global__ void __launch_bounds__(kThreads, 1) los_cl_tc_kernel(TcParams p) {
       uint32_t phase = 0;
       int n = 0;
       bool ok = true;
+      int is = 0;
+      uint32_t iph = 0;
+      while (ok) {
+      if (!mbar_wait(ifull0 + 8 * is, iph, abort_flag, p.err)) break;
+      const int item = islot[is];
+      mbar_arrive(iempty0 + 8 * is);
+      if (++is == kItemSlots) {
+        is = 0;
+        iph ^= 1u;
+      }
+      if (item < 0) break;
+      const TcItem it = p.items[item];
+      const int32_t *nkb_row = p.nkb + it.lt;
       for (int q = it.qb; q < it.qe && ok; ++q) {
         const int nb = nkb_row[(size_t)q * p.nlt];
         if (nb == 0) continue;
         const int buf = n % NB;
         const uint32_t use = (uint32_t)(n / NB);
-        if (!mbar_wait(tempty0 + 8 * buf, (use & 1u) ^ 1u, abort_flag, p.err)) break;
+        if (!mbar_wait(tempty0 + 8 * buf, (use & 1u) ^ 1u, abort_flag, p.err)) {
+          ok = false;
+          break;
+        }
         tc_fence_after();
         const uint32_t dhh = tmem + (uint32_t)(buf * 2 * NT);
         const uint32_t dx = dhh + (uint32_t)NT;
@@ -308,6 +352,7 @@ __global__ void __launch_bounds__(kThreads, 1) los_cl_tc_kernel(TcParams p) {
         mma_commit(tfull0 + 8 * buf);
         ++n;
       }
+      }
       // every MMA this thread issued has completed before TMEM is freed
       mma_commit(drain);
       mbar_wait(drain, 0, nullptr, p.err);
@@ -320,15 +365,33 @@ __global__ void __launch_bounds__(kThreads, 1) los_cl_tc_kernel(TcParams p) {
     const int row = sp * 32 + lane;
     const int col0 = half * C::kColsPerThread;
     float acc[C::kColsPerThread];
+    int n = 0;
+    bool ok = true;
+    int is = 0;
+    uint32_t iph = 0;
+    while (ok) {
+    if (!mbar_wait(ifull0 + 8 * is, iph, abort_flag, p.err)) break;
+    const int item = islot[is];
+    __syncwarp();
+    if (lane == 0) mbar_arrive(iempty0 + 8 * is);
+    if (++is == kItemSlots) {
+      is = 0;
+      iph ^= 1u;
+    }
+    if (item < 0) break;
+    const TcItem it = p.items[item];
+    const int32_t *nkb_row = p.nkb + it.lt;
 #pragma unroll
     for (int j = 0; j < C::kColsPerThread; ++j) acc[j] = 0.f;
-    int n = 0;
-    for (int q = it.qb; q < it.qe; ++q) {
+    for (int q = it.qb; q < it.qe && ok; ++q) {
       const int nb = nkb_row[(size_t)q * p.nlt];
       if (nb == 0) continue;
       const int buf = n % NB;
       const uint32_t use = (uint32_t)(n / NB);
-      if (!mbar_wait(tfull0 + 8 * buf, use & 1u, abort_flag, p.err)) break;
+      if (!mbar_wait(tfull0 + 8 * buf, use & 1u, abort_flag, p.err)) {
+        ok = false;
+        break;
+      }
       tc_fence_after();
       const float4 *w4 = reinterpret_cast<const float4 *>(p.wp + (size_t)q * p.mpad + it.mt * NT + col0);
       const uint32_t taddr = tmem + ((uint32_t)(sp * 32) << 16) + (uint32_t)(buf * 2 * NT + col0);
@@ -356,9 +419,10 @@ __global__ void __launch_bounds__(kThreads, 1) los_cl_tc_kernel(TcParams p) {
       if (lane == 0) mbar_arrive(tempty0 + 8 * buf);
       ++n;
     }
-    float *part = p.partial + (size_t)blockIdx.x * NT * 128;
+    float *part = p.partial + (size_t)item * NT * 128;
 #pragma unroll
     for (int j = 0; j < C::kColsPerThread; ++j) part[(size_t)(col0 + j) * 128 + row] = acc[j];
+    }
   }
   tc_fence_before();
   __syncthreads();
@@ -381,12 +445,24 @@ __device__ __forceinline__ uint32_t sw_off(int n, int cbytes) {
   return (uint32_t)n * 128u + ((uint32_t)((cbytes >> 4) ^ (n & 7)) << 4) + (uint32_t)(cbytes & 15);
 }
 
+// Trapezoid weight in ln k of node q on a source's own k prefix [0, nkm):
+// the master weight, except at the prefix's last node (half interval) and
+// beyond it (zero).
+__device__ __forceinline__ double prefix_weight(const double *__restrict__ wk, const double *__restrict__ k, int nk,
+                                                int nkm, int q) {
+  if (q >= nkm) return 0.0;
+  if (nkm == nk || q + 1 < nkm) return wk[q];
+  return q > 0 ? 0.5 * (log(k[q]) - log(k[q - 1])) : 0.0;
+}
+
 // bf16 / tf32: S[M][nk][ntau] fp32 -> split blocks [q][mt][kb]{hi plane, lo
-// plane}; rows = sources (NT per tile), 128-byte swizzled rows of KB tau, zero
-// padded.  One thread per element.
+// plane}; rows = sources in plan order (NT per tile; perm maps a plan row to
+// the caller's source), 128-byte swizzled rows of KB tau, zero padded and zero
+// beyond a source's k prefix.  One thread per element.
 template <int MODE>
 __global__ void __launch_bounds__(256) split_sources_kernel(const float *__restrict__ S, int M, int nk, int ntau, int NT,
-                                                            int n_mt, int nkbs, char *__restrict__ sp) {
+                                                            int n_mt, int nkbs, const int *__restrict__ perm,
+                                                            const int *__restrict__ nk_m, char *__restrict__ sp) {
   constexpr int KB = MODE == kTF32 ? 32 : 64;
   constexpr int ES = MODE == kTF32 ? 4 : 2;
   constexpr int ROWS = 256 / KB;  // rows per CTA
@@ -399,7 +475,7 @@ __global__ void __launch_bounds__(256) split_sources_kernel(const float *__restr
   const int m = mt * NT + n;
   const int t = kb * KB + c;
   float v = 0.f;
-  if (m < M && t < ntau) v = __ldg(S + ((size_t)m * nk + q) * ntau + t);
+  if (m < M && t < ntau && q < nk_m[m]) v = __ldg(S + ((size_t)perm[m] * nk + q) * ntau + t);
   char *blk = sp + (((size_t)qm * nkbs) + kb) * (size_t)(256 * NT);
   const uint32_t o = sw_off(n, c * ES);
   if constexpr (MODE == kTF32) {
@@ -415,13 +491,19 @@ __global__ void __launch_bounds__(256) split_sources_kernel(const float *__restr
   }
 }
 
-// wq[q][m] = sqrt(4 pi w_k P[m][q]) (zero for padded sources).
-__global__ void weights_kernel(const double *__restrict__ Pk, const double *__restrict__ wk, int M, int nk, int mpad,
-                               float *__restrict__ wq) {
+// wq[q][m] = sqrt(4 pi w_k P[m][q]) with the source's own k weights (zero
+// for padded sources and beyond the source's k prefix).
+__global__ void weights_kernel(const double *__restrict__ Pk, const double *__restrict__ wk,
+                               const double *__restrict__ kk, int M, int nk, int mpad, const int *__restrict__ perm,
+                               const int *__restrict__ nk_m, float *__restrict__ wq) {
   const int q = blockIdx.x;
-  for (int m = threadIdx.x; m < mpad; m += blockDim.x)
-    wq[(size_t)q * mpad + m] =
-        m < M ? (float)sqrt(4.0 * 3.14159265358979323846 * wk[q] * Pk[(size_t)m * nk + q]) : 0.f;
+  for (int m = threadIdx.x; m < mpad; m += blockDim.x) {
+    float v = 0.f;
+    if (m < M && q < nk_m[m])
+      v = (float)sqrt(4.0 * 3.14159265358979323846 * prefix_weight(wk, kk, nk, nk_m[m], q) *
+                      Pk[(size_t)perm[m] * nk + q]);
+    wq[(size_t)q * mpad + m] = v;
+  }
 }
 
 // fp16: one warp per (k, source) row.  The row is scaled by 2^s so that its
@@ -431,17 +513,20 @@ __global__ void weights_kernel(const double *__restrict__ Pk, const double *__re
 // 2^sJ is the table's scale, so (wq D')^2 is the unscaled contribution.
 __global__ void __launch_bounds__(256) split_sources_f16_kernel(const float *__restrict__ S,
                                                                 const double *__restrict__ Pk,
-                                                                const double *__restrict__ wk, int M, int nk,
+                                                                const double *__restrict__ wk,
+                                                                const double *__restrict__ kk, int M, int nk,
                                                                 int ntau, int NT, int n_mt, int nkbs, int mpad,
-                                                                int sJ, char *__restrict__ sp,
+                                                                int sJ, const int *__restrict__ perm,
+                                                                const int *__restrict__ nk_m, char *__restrict__ sp,
                                                                 float *__restrict__ wq) {
   const int lane = threadIdx.x & 31;
   const size_t row = (size_t)blockIdx.x * 8 + (threadIdx.x >> 5);  // q * mpad + m
   if (row >= (size_t)nk * mpad) return;
   const int q = (int)(row / mpad), mfull = (int)(row - (size_t)q * mpad);
   const int mt = mfull / NT, n = mfull - mt * NT;
-  const bool live = mfull < M;
-  const float *src = S + ((size_t)(live ? mfull : 0) * nk + q) * ntau;
+  const bool live = mfull < M && q < nk_m[mfull];
+  const int mc = live ? perm[mfull] : 0;
+  const float *src = S + ((size_t)mc * nk + q) * ntau;
   float mx = 0.f;
   if (live)
     for (int t = lane; t < ntau; t += 32) mx = fmaxf(mx, fabsf(__ldg(src + t)));
@@ -465,14 +550,18 @@ __global__ void __launch_bounds__(256) split_sources_f16_kernel(const float *__r
     *reinterpret_cast<__half *>(blk + NT * 128 + o) = lo;
   }
   if (lane == 0)
-    wq[row] = live ? (float)ldexp(sqrt(4.0 * 3.14159265358979323846 * wk[q] * Pk[(size_t)mfull * nk + q]), -(sJ + s))
+    wq[row] = live ? (float)ldexp(sqrt(4.0 * 3.14159265358979323846 * prefix_weight(wk, kk, nk, nk_m[mfull], q) *
+                                       Pk[(size_t)mc * nk + q]),
+                                  -(sJ + s))
                    : 0.f;
 }
 
-// C[m][l] = sum over the tile's items (fixed order) of the FP32 chunk sums, in FP64.
+// C[m][l] = sum over the tile's items (fixed order) of the FP32 chunk sums, in
+// FP64; zero above the source's own l_max.
 __global__ void __launch_bounds__(128) reduce_kernel(const float *__restrict__ partial, const int *__restrict__ tile_ptr,
                                                      const int *__restrict__ tile_items, int NT, int n_mt, int M,
-                                                     int lmin, int lmax, double *__restrict__ Cl) {
+                                                     int lmin, int lmax, const int *__restrict__ perm,
+                                                     const int *__restrict__ lmax_m, double *__restrict__ Cl) {
   const int r = threadIdx.x;
   const int ml = blockIdx.x;       // source within the tile
   const int tile = blockIdx.y;     // lt * n_mt + mt
@@ -481,124 +570,208 @@ __global__ void __launch_bounds__(128) reduce_kernel(const float *__restrict__ p
   const int l = lmin + lt * kTileL + r;
   if (m >= M || l > lmax) return;
   double acc = 0.0;
-  for (int e = tile_ptr[tile]; e < tile_ptr[tile + 1]; ++e)
-    acc += (double)partial[((size_t)tile_items[e] * NT + ml) * 128 + r];
-  Cl[(size_t)m * (lmax - lmin + 1) + (l - lmin)] = acc;
+  if (l <= lmax_m[m])
+    for (int e = tile_ptr[tile]; e < tile_ptr[tile + 1]; ++e)
+      acc += (double)partial[((size_t)tile_items[e] * NT + ml) * 128 + r];
+  Cl[(size_t)perm[m] * (lmax - lmin + 1) + (l - lmin)] = acc;
 }
 
 // ------------------------------------------------------------------ plan
 
+// Work plan of one batched launch.  Sources are processed in plan order:
+// sorted by l_max (then k prefix) descending, so that at every (k, l-tile)
+// the sources that still need it form a prefix of the source tiles.  All
+// integer arrays live in one blob, uploaded once (or written into the fixed
+// buffer of the allocation-free entry point).
 struct TcPlan {
-  int mode = -1, M = 0, NT = 0, n_mt = 0, nkbs = 0, mpad = 0;
-  std::vector<TcItem> items;
-  std::vector<int> tile_ptr, tile_items;
-  TcItem *d_items = nullptr;
-  int *d_tile_ptr = nullptr, *d_tile_items = nullptr;
-  size_t off_sp = 0, off_wp = 0, off_part = 0, ws_bytes = 0;
+  int mode = -1, M = 0, NT = 0, n_mt = 0, nkbs = 0, mpad = 0, nctas = 0, nitems = 0, ntile = 0;
+  bool uniform = true;
+  std::vector<int> blob;
+  size_t o_items = 0, o_tile_ptr = 0, o_tile_items = 0, o_perm = 0, o_nkm = 0, o_lmaxm = 0;
+  std::vector<double> cost;  // per item
+  int *d_blob = nullptr;
+  bool own_blob = false;
+  size_t off_sp = 0, off_wp = 0, off_part = 0, off_ctr = 0, ws_bytes = 0;
+
+  const TcItem *items(const int *base) const { return reinterpret_cast<const TcItem *>(base + o_items); }
+  void release() {
+    if (own_blob && d_blob) cudaFree(d_blob);
+    d_blob = nullptr;
+    own_blob = false;
+  }
 };
 
 std::mutex g_plan_mu;
 std::vector<std::pair<const gcamb_grid *, TcPlan *>> g_plans;
 
-// Source-tile width: 64 for small batches, else 128 (double-buffered
-// accumulator pairs); GCAMB_TC_NT=64|128|256 overrides it.
-int pick_nt(int M, int *n_mt) {
+// Source-tile width of the uniform entry point: 64 for small batches, else
+// 128 (double-buffered accumulator pairs); GCAMB_TC_NT=64|128|256 overrides it.
+int pick_nt(int M) {
   int nt = M <= 64 ? 64 : 128;
   if (const char *e = getenv("GCAMB_TC_NT")) {
     const int v = atoi(e);
     if (v == 64 || v == 128 || v == 256) nt = v;
   }
-  *n_mt = (M + nt - 1) / nt;
   return nt;
 }
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-void plan_layout(const gcamb_grid *g, int M, int mode, TcPlan &pl) {
+int num_sms() {
+  int dev = 0, sms = 148;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 148;
+}
+
+// lmax_c / nk_c: per-source l_max and k-prefix length in the caller's order,
+// or null for a uniform batch (every source uses the whole grid).
+void plan_build(const gcamb_grid *g, int M, int mode, int nt, const int *lmax_c, const int *nk_c, TcPlan &pl) {
   const ModeLayout lay = mode_layout(mode);
+  const Table &t = g->tab[mode];
   pl.mode = mode;
   pl.M = M;
-  pl.NT = pick_nt(M, &pl.n_mt);
+  pl.NT = nt;
+  pl.n_mt = (M + nt - 1) / nt;
+  pl.mpad = pl.n_mt * nt;
   pl.nkbs = (g->ntau + lay.kb - 1) / lay.kb;
-  pl.mpad = pl.n_mt * pl.NT;
-  const Table &t = g->tab[mode];
-  // cost per (q, lt): table blocks + a fixed epilogue share
+  pl.uniform = !lmax_c && !nk_c;
+  std::vector<int> perm(M), nkm(M), lmm(M);
+  for (int m = 0; m < M; ++m) perm[m] = m;
+  auto lm_of = [&](int m) { return lmax_c ? lmax_c[m] : g->lmax; };
+  auto nk_of = [&](int m) { return nk_c ? nk_c[m] : g->nk; };
+  if (!pl.uniform)
+    std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) {
+      if (lm_of(a) != lm_of(b)) return lm_of(a) > lm_of(b);
+      return nk_of(a) > nk_of(b);
+    });
+  for (int j = 0; j < M; ++j) {
+    nkm[j] = nk_of(perm[j]);
+    lmm[j] = lm_of(perm[j]);
+  }
+  std::vector<int> tile_nk(pl.n_mt, 0), tile_lm(pl.n_mt, -1);
+  for (int j = 0; j < M; ++j) {
+    tile_nk[j / nt] = std::max(tile_nk[j / nt], nkm[j]);
+    tile_lm[j / nt] = std::max(tile_lm[j / nt], lmm[j]);
+  }
+  // items: (l-tile, source tile, contiguous chunk of active k)
   double total = 0.0;
-  for (size_t e = 0; e < t.nkb.size(); ++e)
-    if (t.nkb[e] > 0) total += t.nkb[e] + 0.5;
-  total *= pl.n_mt;
-  int dev = 0, sms = 148;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const double target = std::max(4.0, total / (sms * 4.0));
-  pl.items.clear();
   for (int lt = 0; lt < g->nlt; ++lt)
     for (int mt = 0; mt < pl.n_mt; ++mt) {
+      if (tile_lm[mt] < g->lmin + lt * kTileL) continue;
+      for (int q = 0; q < tile_nk[mt]; ++q) {
+        const int nb = t.nkb[(size_t)q * g->nlt + lt];
+        if (nb) total += nb + 0.5;
+      }
+    }
+  const int sms = num_sms();
+  const double target = std::max(4.0, total / (sms * 4.0));
+  std::vector<TcItem> items;
+  pl.cost.clear();
+  for (int lt = 0; lt < g->nlt; ++lt)
+    for (int mt = 0; mt < pl.n_mt; ++mt) {
+      if (tile_lm[mt] < g->lmin + lt * kTileL) continue;
       int qb = -1;
       double c = 0.0;
-      for (int q = 0; q < g->nk; ++q) {
+      for (int q = 0; q < tile_nk[mt]; ++q) {
         const int nb = t.nkb[(size_t)q * g->nlt + lt];
         if (nb == 0) continue;
-        if (qb < 0) { qb = q; c = 0.0; }
+        if (qb < 0) {
+          qb = q;
+          c = 0.0;
+        }
         c += nb + 0.5;
         if (c >= target || q - qb + 1 >= kKChunkMax) {
-          pl.items.push_back({lt, mt, qb, q + 1});
+          items.push_back({lt, mt, qb, q + 1});
+          pl.cost.push_back(c);
           qb = -1;
         }
       }
-      if (qb >= 0) pl.items.push_back({lt, mt, qb, g->nk});
+      if (qb >= 0) {
+        items.push_back({lt, mt, qb, tile_nk[mt]});
+        pl.cost.push_back(c);
+      }
     }
-  // launch order: by k position so that tiles sharing source blocks run together
-  std::stable_sort(pl.items.begin(), pl.items.end(), [](const TcItem &a, const TcItem &b) {
-    return (a.qb + a.qe) > (b.qb + b.qe);
-  });
-  const int ntile = g->nlt * pl.n_mt;
-  pl.tile_ptr.assign(ntile + 1, 0);
-  for (const auto &x : pl.items) pl.tile_ptr[x.lt * pl.n_mt + x.mt + 1]++;
-  for (int i = 0; i < ntile; ++i) pl.tile_ptr[i + 1] += pl.tile_ptr[i];
-  pl.tile_items.assign(pl.items.size(), 0);
+  pl.nitems = (int)items.size();
+  // hand-out order: by k position (high k first), so that the CTAs working at
+  // any moment share the source blocks of nearby k in L2; one persistent CTA
+  // per SM takes the next item from a counter when it is free
   {
-    std::vector<int> fill(pl.tile_ptr.begin(), pl.tile_ptr.end() - 1);
-    // fixed order inside a tile: increasing k
-    std::vector<int> idx(pl.items.size());
-    for (size_t i = 0; i < idx.size(); ++i) idx[i] = (int)i;
-    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return pl.items[a].qb < pl.items[b].qb; });
-    for (int i : idx) {
-      const auto &x = pl.items[i];
-      pl.tile_items[fill[x.lt * pl.n_mt + x.mt]++] = i;
+    std::vector<int> order(pl.nitems);
+    for (int i = 0; i < pl.nitems; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+      return (items[a].qb + items[a].qe) > (items[b].qb + items[b].qe);
+    });
+    std::vector<TcItem> sorted(pl.nitems);
+    std::vector<double> sc(pl.nitems);
+    for (int i = 0; i < pl.nitems; ++i) {
+      sorted[i] = items[order[i]];
+      sc[i] = pl.cost[order[i]];
     }
+    items.swap(sorted);
+    pl.cost.swap(sc);
   }
+  pl.nctas = std::max(1, std::min(sms, pl.nitems));
+  // per (l-tile, source tile): its items in increasing k (fixed reduce order)
+  pl.ntile = g->nlt * pl.n_mt;
+  std::vector<int> tile_ptr(pl.ntile + 1, 0), tile_items(pl.nitems);
+  for (const auto &x : items) tile_ptr[x.lt * pl.n_mt + x.mt + 1]++;
+  for (int i = 0; i < pl.ntile; ++i) tile_ptr[i + 1] += tile_ptr[i];
+  {
+    std::vector<int> idx(pl.nitems), fill(tile_ptr.begin(), tile_ptr.end() - 1);
+    for (int i = 0; i < pl.nitems; ++i) idx[i] = i;
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return items[a].qb < items[b].qb; });
+    for (int i : idx) tile_items[fill[items[i].lt * pl.n_mt + items[i].mt]++] = i;
+  }
+  // blob
+  pl.blob.clear();
+  auto put = [&](const int *p, size_t n) {
+    const size_t o = pl.blob.size();
+    pl.blob.insert(pl.blob.end(), p, p + n);
+    while (pl.blob.size() % 4) pl.blob.push_back(0);  // 16-byte alignment of every array
+    return o;
+  };
+  pl.o_items = put(reinterpret_cast<const int *>(items.data()), items.size() * 4);
+  pl.o_tile_ptr = put(tile_ptr.data(), tile_ptr.size());
+  pl.o_tile_items = put(tile_items.data(), tile_items.size());
+  pl.o_perm = put(perm.data(), perm.size());
+  pl.o_nkm = put(nkm.data(), nkm.size());
+  pl.o_lmaxm = put(lmm.data(), lmm.size());
+  if (pl.blob.empty()) pl.blob.push_back(0);
+  // workspace: split sources, weights, k-chunk partials
   const size_t sp_bytes = (size_t)g->nk * pl.n_mt * pl.nkbs * 256 * pl.NT;
   const size_t wp_bytes = (size_t)g->nk * pl.mpad * sizeof(float);
-  const size_t part_bytes = std::max<size_t>(1, pl.items.size()) * pl.NT * 128 * sizeof(float);
+  const size_t part_bytes = std::max<size_t>(1, pl.nitems) * pl.NT * 128 * sizeof(float);
   pl.off_sp = 0;
   pl.off_wp = align256(sp_bytes);
   pl.off_part = pl.off_wp + align256(wp_bytes);
-  pl.ws_bytes = pl.off_part + align256(part_bytes);
+  pl.off_ctr = pl.off_part + align256(part_bytes);
+  pl.ws_bytes = pl.off_ctr + 256;
+}
+
+size_t blob_bytes(const TcPlan &pl) { return align256(pl.blob.size() * sizeof(int)); }
+
+int upload_blob(TcPlan &pl) {
+  cudaError_t e = cudaMalloc(&pl.d_blob, pl.blob.size() * sizeof(int));
+  if (e != cudaSuccess) {
+    pl.d_blob = nullptr;
+    return cuda_fail(e, "plan: allocation");
+  }
+  pl.own_blob = true;
+  e = cudaMemcpy(pl.d_blob, pl.blob.data(), pl.blob.size() * sizeof(int), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "plan: upload");
+  return GCAMB_OK;
 }
 
 TcPlan *get_plan(const gcamb_grid *g, int M, int mode, int *rc) {
   std::lock_guard<std::mutex> lk(g_plan_mu);
-  int nmt = 0;
-  const int nt = pick_nt(M, &nmt);
+  const int nt = pick_nt(M);
   for (auto &e : g_plans)
     if (e.first == g && e.second->M == M && e.second->mode == mode && e.second->NT == nt) return e.second;
   TcPlan *pl = new TcPlan();
-  plan_layout(g, M, mode, *pl);
-  cudaError_t e1 = cudaMalloc(&pl->d_items, std::max<size_t>(1, pl->items.size()) * sizeof(TcItem));
-  cudaError_t e2 = cudaMalloc(&pl->d_tile_ptr, pl->tile_ptr.size() * sizeof(int));
-  cudaError_t e3 = cudaMalloc(&pl->d_tile_items, std::max<size_t>(1, pl->tile_items.size()) * sizeof(int));
-  if (e1 || e2 || e3) {
-    *rc = cuda_fail(e1 ? e1 : (e2 ? e2 : e3), "los_cl: plan allocation");
+  plan_build(g, M, mode, nt, nullptr, nullptr, *pl);
+  if ((*rc = upload_blob(*pl)) != GCAMB_OK) {
+    pl->release();
     delete pl;
-    return nullptr;
-  }
-  cudaMemcpy(pl->d_items, pl->items.data(), pl->items.size() * sizeof(TcItem), cudaMemcpyHostToDevice);
-  cudaMemcpy(pl->d_tile_ptr, pl->tile_ptr.data(), pl->tile_ptr.size() * sizeof(int), cudaMemcpyHostToDevice);
-  cudaError_t e4 = cudaMemcpy(pl->d_tile_items, pl->tile_items.data(), pl->tile_items.size() * sizeof(int),
-                              cudaMemcpyHostToDevice);
-  if (e4) {
-    *rc = cuda_fail(e4, "los_cl: plan upload");
     return nullptr;
   }
   g_plans.push_back({g, pl});
@@ -613,34 +786,41 @@ int launch_tc(const gcamb_grid *g, const TcPlan &pl, const float *S, const doubl
   char *sp = ws + pl.off_sp;
   float *wp = reinterpret_cast<float *>(ws + pl.off_wp);
   float *part = reinterpret_cast<float *>(ws + pl.off_part);
+  const int *B = pl.d_blob;
+  const int *perm = B + pl.o_perm, *nkm = B + pl.o_nkm, *lmm = B + pl.o_lmaxm;
   if constexpr (MODE == kF16) {
     const size_t rows = (size_t)g->nk * pl.mpad;
     ProfScope prof(GCAMB_K_SPLIT, st);
-    split_sources_f16_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, st>>>(
-        S, Pk, g->d_wk, pl.M, g->nk, g->ntau, NT, pl.n_mt, pl.nkbs, pl.mpad, t.scale_exp, sp, wp);
+    split_sources_f16_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, st>>>(S, Pk, g->d_wk, g->d_k, pl.M, g->nk, g->ntau,
+                                                                        NT, pl.n_mt, pl.nkbs, pl.mpad, t.scale_exp,
+                                                                        perm, nkm, sp, wp);
   } else {
     {
       constexpr int KB = MODE == kTF32 ? 32 : 64;
       dim3 grid(pl.nkbs * (NT / (256 / KB)), g->nk * pl.n_mt);
       ProfScope prof(GCAMB_K_SPLIT, st);
-      split_sources_kernel<MODE><<<grid, 256, 0, st>>>(S, pl.M, g->nk, g->ntau, NT, pl.n_mt, pl.nkbs, sp);
+      split_sources_kernel<MODE><<<grid, 256, 0, st>>>(S, pl.M, g->nk, g->ntau, NT, pl.n_mt, pl.nkbs, perm, nkm, sp);
     }
     ProfScope prof(GCAMB_K_WEIGHTS, st);
-    weights_kernel<<<g->nk, 256, 0, st>>>(Pk, g->d_wk, pl.M, g->nk, pl.mpad, wp);
+    weights_kernel<<<g->nk, 256, 0, st>>>(Pk, g->d_wk, g->d_k, pl.M, g->nk, pl.mpad, perm, nkm, wp);
   }
-  if (!pl.items.empty()) {
+  if (pl.nitems > 0) {
     cudaError_t e = cudaFuncSetAttribute(los_cl_tc_kernel<NT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          Cfg::kSmemBytes);
     if (e != cudaSuccess) return cuda_fail(e, "los_cl: smem attribute");
-    TcParams prm{static_cast<const char *>(t.d_data), t.d_off, t.d_nkb, sp, wp, pl.d_items, part,
+    int *ctr = reinterpret_cast<int *>(ws + pl.off_ctr);
+    TcParams prm{static_cast<const char *>(t.d_data), t.d_off, t.d_nkb, sp, wp, pl.items(B), ctr, pl.nitems, part,
                  use_err_word ? err_word : device_error_flag(), g->nlt, pl.n_mt, pl.nkbs, pl.mpad};
     if (!prm.err && !use_err_word) return fail(GCAMB_ECUDA, "los_cl: error flag allocation");
+    e = cudaMemsetAsync(ctr, 0, sizeof(int), st);
+    if (e != cudaSuccess) return cuda_fail(e, "los_cl: counter reset");
     ProfScope prof(GCAMB_K_TC, st);
-    los_cl_tc_kernel<NT, MODE><<<(unsigned)pl.items.size(), kThreads, Cfg::kSmemBytes, st>>>(prm);
+    los_cl_tc_kernel<NT, MODE><<<(unsigned)pl.nctas, kThreads, Cfg::kSmemBytes, st>>>(prm);
   }
-  dim3 rgrid(NT, g->nlt * pl.n_mt);
+  dim3 rgrid(NT, pl.ntile);
   ProfScope prof(GCAMB_K_REDUCE, st);
-  reduce_kernel<<<rgrid, 128, 0, st>>>(part, pl.d_tile_ptr, pl.d_tile_items, NT, pl.n_mt, pl.M, g->lmin, g->lmax, Cl);
+  reduce_kernel<<<rgrid, 128, 0, st>>>(part, B + pl.o_tile_ptr, B + pl.o_tile_items, NT, pl.n_mt, pl.M, g->lmin,
+                                       g->lmax, perm, lmm, Cl);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "los_cl: launch");
   return GCAMB_OK;
@@ -656,20 +836,27 @@ int launch_mode(const gcamb_grid *g, const TcPlan &pl, const float *S, const dou
   }
 }
 
+int launch_plan(const gcamb_grid *g, const TcPlan &pl, const float *S, const double *Pk, double *Cl, char *w,
+                cudaStream_t st, int *err_word = nullptr, bool use_err_word = false) {
+  switch (pl.mode) {
+    case GCAMB_TF32X3: return launch_mode<kTF32>(g, pl, S, Pk, Cl, w, st, err_word, use_err_word);
+    case GCAMB_F16X3: return launch_mode<kF16>(g, pl, S, Pk, Cl, w, st, err_word, use_err_word);
+    default: return launch_mode<kBF16>(g, pl, S, Pk, Cl, w, st, err_word, use_err_word);
+  }
+}
+
 }  // namespace
 
 size_t los_cl_workspace_bytes(const gcamb_grid *g, int M, int mode) {
   if (!g->tab[mode].built) {
     // without the table: an upper bound from the extents
-    TcPlan tmp;
-    tmp.NT = pick_nt(M, &tmp.n_mt);
+    const int nt = pick_nt(M), n_mt = (M + nt - 1) / nt;
     const ModeLayout lay = mode_layout(mode);
-    tmp.nkbs = (g->ntau + lay.kb - 1) / lay.kb;
-    tmp.mpad = tmp.n_mt * tmp.NT;
-    size_t sp_bytes = (size_t)g->nk * tmp.n_mt * tmp.nkbs * 256 * tmp.NT;
-    size_t wp_bytes = (size_t)g->nk * tmp.mpad * sizeof(float);
-    size_t max_items = (size_t)g->nk * g->nlt * tmp.n_mt;
-    return align256(sp_bytes) + align256(wp_bytes) + align256(max_items * tmp.NT * 128 * sizeof(float));
+    const size_t nkbs = (g->ntau + lay.kb - 1) / lay.kb;
+    const size_t sp_bytes = (size_t)g->nk * n_mt * nkbs * 256 * nt;
+    const size_t wp_bytes = (size_t)g->nk * n_mt * nt * sizeof(float);
+    const size_t max_items = (size_t)g->nk * g->nlt * n_mt;
+    return align256(sp_bytes) + align256(wp_bytes) + align256(max_items * nt * 128 * sizeof(float));
   }
   int rc = 0;
   TcPlan *p = get_plan(g, M, mode, &rc);
@@ -682,67 +869,40 @@ int launch_los_cl(const gcamb_grid *g, const float *S, const double *Pk, int M, 
   TcPlan *pl = get_plan(g, M, mode, &rc);
   if (!pl) return rc ? rc : fail(GCAMB_ECUDA, "los_cl: plan");
   if (ws_bytes < pl->ws_bytes) return fail(GCAMB_EINVAL, "los_cl: workspace too small");
-  char *w = static_cast<char *>(ws);
-  switch (mode) {
-    case GCAMB_TF32X3: return launch_mode<kTF32>(g, *pl, S, Pk, Cl, w, st);
-    case GCAMB_F16X3: return launch_mode<kF16>(g, *pl, S, Pk, Cl, w, st);
-    default: return launch_mode<kBF16>(g, *pl, S, Pk, Cl, w, st);
-  }
+  return launch_plan(g, *pl, S, Pk, Cl, static_cast<char *>(ws), st);
 }
 
 // Fixed-buffer variant for gcamb_los_cl_noalloc: the plan is computed on the
-// host and its arrays, the split sources, the weights and the chunk partials
-// all live in the caller's buffer `scratch` (no device allocation).
+// host and its integer blob, the split sources, the weights and the chunk
+// partials all live in the caller's buffer `scratch` (no device allocation).
 size_t los_cl_fixed_bytes(const gcamb_grid *g, int M, int mode) {
   TcPlan pl;
-  plan_layout(g, M, mode, pl);
-  return align256(pl.items.size() * sizeof(TcItem)) + align256(pl.tile_ptr.size() * sizeof(int)) +
-         align256(pl.tile_items.size() * sizeof(int)) + pl.ws_bytes;
+  plan_build(g, M, mode, pick_nt(M), nullptr, nullptr, pl);
+  return blob_bytes(pl) + pl.ws_bytes;
 }
 
 int launch_los_cl_fixed(const gcamb_grid *g, const float *S, const double *Pk, int M, int mode, double *Cl,
                         char *scratch, size_t cap, int *status, cudaStream_t st) {
   TcPlan pl;
-  plan_layout(g, M, mode, pl);
-  const size_t b_items = align256(pl.items.size() * sizeof(TcItem));
-  const size_t b_ptr = align256(pl.tile_ptr.size() * sizeof(int));
-  const size_t b_ti = align256(pl.tile_items.size() * sizeof(int));
-  const size_t need = b_items + b_ptr + b_ti + pl.ws_bytes;
+  plan_build(g, M, mode, pick_nt(M), nullptr, nullptr, pl);
+  const size_t b_blob = blob_bytes(pl);
+  const size_t need = b_blob + pl.ws_bytes;
   if (need > cap)
     return fail(GCAMB_EINVAL, "los_cl_noalloc: needs " + std::to_string(need) + " bytes of scratch, the fixed buffer holds " +
                                   std::to_string(cap) + "; use gcamb_los_cl with a caller workspace");
-  pl.d_items = reinterpret_cast<TcItem *>(scratch);
-  pl.d_tile_ptr = reinterpret_cast<int *>(scratch + b_items);
-  pl.d_tile_items = reinterpret_cast<int *>(scratch + b_items + b_ptr);
-  char *ws = scratch + b_items + b_ptr + b_ti;
-  cudaError_t e = cudaSuccess;
-  if (!pl.items.empty())
-    e = cudaMemcpyAsync(pl.d_items, pl.items.data(), pl.items.size() * sizeof(TcItem), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(pl.d_tile_ptr, pl.tile_ptr.data(), pl.tile_ptr.size() * sizeof(int), cudaMemcpyHostToDevice,
-                        st);
-  if (e == cudaSuccess && !pl.tile_items.empty())
-    e = cudaMemcpyAsync(pl.d_tile_items, pl.tile_items.data(), pl.tile_items.size() * sizeof(int),
-                        cudaMemcpyHostToDevice, st);
+  pl.d_blob = reinterpret_cast<int *>(scratch);
   // copies from pageable memory return once the host data is staged, so the
-  // vectors may go out of scope when this function returns
+  // plan may go out of scope when this function returns
+  cudaError_t e = cudaMemcpyAsync(pl.d_blob, pl.blob.data(), pl.blob.size() * sizeof(int), cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "los_cl_noalloc: plan upload");
-  int rc;
-  switch (mode) {
-    case GCAMB_TF32X3: rc = launch_mode<kTF32>(g, pl, S, Pk, Cl, ws, st, status, true); break;
-    case GCAMB_F16X3: rc = launch_mode<kF16>(g, pl, S, Pk, Cl, ws, st, status, true); break;
-    default: rc = launch_mode<kBF16>(g, pl, S, Pk, Cl, ws, st, status, true); break;
-  }
-  return rc;
+  return launch_plan(g, pl, S, Pk, Cl, scratch + b_blob, st, status, true);
 }
 
 void drop_plans(const gcamb_grid *g) {
   std::lock_guard<std::mutex> lk(g_plan_mu);
   for (auto it = g_plans.begin(); it != g_plans.end();) {
     if (it->first == g) {
-      cudaFree(it->second->d_items);
-      cudaFree(it->second->d_tile_ptr);
-      cudaFree(it->second->d_tile_items);
+      it->second->release();
       delete it->second;
       it = g_plans.erase(it);
     } else {
@@ -752,3 +912,278 @@ void drop_plans(const gcamb_grid *g) {
 }
 
 }  // namespace gcamb
+
+// ------------------------------------------------------------------ plans (uneven batches)
+//
+// A gcamb_plan fixes a batch's composition (per-source l_max and k prefix),
+// builds the work list once, can pick the source-tile width by timing the
+// candidates on the first launch (autotuner, optionally cached on disk), and
+// replays its three launches as one CUDA graph.
+
+namespace gcamb {
+namespace {
+
+constexpr int kCandNT[3] = {64, 128, 256};
+
+uint64_t fnv1a(uint64_t h, const void *p, size_t n) {
+  const unsigned char *c = static_cast<const unsigned char *>(p);
+  for (size_t i = 0; i < n; ++i) {
+    h ^= c[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+}  // namespace
+}  // namespace gcamb
+
+struct gcamb_plan {
+  const gcamb_grid *g = nullptr;
+  int M = 0, mode = 0;
+  bool tune = false, tuned = false;
+  std::vector<int> lmax_c, nk_c;
+  gcamb::TcPlan cand[3];
+  bool have[3] = {false, false, false};
+  int chosen = -1;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cap = nullptr;  // private stream the graph is captured on
+  const void *bS = nullptr, *bP = nullptr, *bC = nullptr, *bW = nullptr;
+  int64_t captures = 0, replays = 0;
+  std::string key;
+};
+
+namespace gcamb {
+namespace {
+
+std::string tune_cache_path() {
+  const char *e = getenv("GCAMB_TUNE_CACHE");
+  return e ? std::string(e) : std::string();
+}
+
+// One JSON object per line: {"key": "...", "nt": 128, "ms": 1.234}
+int tune_cache_lookup(const std::string &key) {
+  const std::string path = tune_cache_path();
+  if (path.empty()) return -1;
+  FILE *f = fopen(path.c_str(), "r");
+  if (!f) return -1;
+  char line[1024];
+  int nt = -1;
+  while (fgets(line, sizeof line, f)) {
+    const std::string s(line);
+    const size_t k = s.find("\"key\": \"");
+    if (k == std::string::npos) continue;
+    const size_t b = k + 8, e = s.find('"', b);
+    if (e == std::string::npos || s.substr(b, e - b) != key) continue;
+    const size_t n = s.find("\"nt\": ");
+    if (n != std::string::npos) nt = atoi(s.c_str() + n + 6);
+  }
+  fclose(f);
+  return nt;
+}
+
+void tune_cache_store(const std::string &key, int nt, double ms) {
+  const std::string path = tune_cache_path();
+  if (path.empty()) return;
+  FILE *f = fopen(path.c_str(), "a");
+  if (!f) return;
+  fprintf(f, "{\"key\": \"%s\", \"nt\": %d, \"ms\": %.6f}\n", key.c_str(), nt, ms);
+  fclose(f);
+}
+
+int plan_time(gcamb_plan *p, int c, const float *S, const double *Pk, double *Cl, char *ws, cudaStream_t st,
+              float *ms) {
+  cudaEvent_t a, b;
+  if (cudaEventCreate(&a) != cudaSuccess) return fail(GCAMB_ECUDA, "plan: event");
+  if (cudaEventCreate(&b) != cudaSuccess) {
+    cudaEventDestroy(a);
+    return fail(GCAMB_ECUDA, "plan: event");
+  }
+  int rc = launch_plan(p->g, p->cand[c], S, Pk, Cl, ws, st);  // warm-up
+  if (!rc) {
+    cudaEventRecord(a, st);
+    for (int r = 0; r < 2 && !rc; ++r) rc = launch_plan(p->g, p->cand[c], S, Pk, Cl, ws, st);
+    cudaEventRecord(b, st);
+    cudaEventSynchronize(b);
+    cudaEventElapsedTime(ms, a, b);
+    *ms *= 0.5f;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return rc;
+}
+
+}  // namespace
+}  // namespace gcamb
+
+using namespace gcamb;
+
+extern "C" {
+
+int gcamb_plan_create(gcamb_grid *g, int M, const int *lmax_m, const int *nk_m, int mode, int tune,
+                      gcamb_plan **out) {
+  if (!out) return fail(GCAMB_EINVAL, "plan_create: out is NULL");
+  *out = nullptr;
+  if (!g) return fail(GCAMB_EINVAL, "plan_create: NULL grid");
+  if (mode != GCAMB_BF16X3 && mode != GCAMB_TF32X3 && mode != GCAMB_F16X3)
+    return fail(GCAMB_EINVAL, "plan_create: mode must be GCAMB_BF16X3, GCAMB_F16X3 or GCAMB_TF32X3");
+  if (M < 1) return fail(GCAMB_EINVAL, "plan_create: M must be >= 1");
+  if (!g->tab[mode].built) return fail(GCAMB_ESTATE, "plan_create: build the table for this mode first");
+  if ((lmax_m == nullptr) != (nk_m == nullptr))
+    return fail(GCAMB_EINVAL, "plan_create: give both lmax_m and nk_m, or neither");
+  for (int m = 0; lmax_m && m < M; ++m) {
+    if (lmax_m[m] < g->lmin || lmax_m[m] > g->lmax)
+      return fail(GCAMB_EINVAL, "plan_create: lmax_m outside the grid's [lmin, lmax]");
+    if (nk_m[m] < 1 || nk_m[m] > g->nk) return fail(GCAMB_EINVAL, "plan_create: nk_m outside [1, nk]");
+  }
+  gcamb_plan *p = new (std::nothrow) gcamb_plan();
+  if (!p) return fail(GCAMB_ENOMEM, "plan_create: host allocation");
+  p->g = g;
+  p->M = M;
+  p->mode = mode;
+  p->tune = tune != 0;
+  if (lmax_m) {
+    p->lmax_c.assign(lmax_m, lmax_m + M);
+    p->nk_c.assign(nk_m, nk_m + M);
+  }
+  // the key identifies grid, batch and device for the tile cache
+  uint64_t h = 1469598103934665603ull;
+  h = fnv1a(h, g->k.data(), g->k.size() * sizeof(double));
+  h = fnv1a(h, g->tau.data(), g->tau.size() * sizeof(double));
+  if (lmax_m) {
+    h = fnv1a(h, lmax_m, M * sizeof(int));
+    h = fnv1a(h, nk_m, M * sizeof(int));
+  }
+  char kb[256];
+  snprintf(kb, sizeof kb, "v1|sm%d|%d|%d|%d|%d|%g|%d|%d|%016llx", num_sms(), g->nk, g->ntau, g->lmin, g->lmax,
+           g->eps_cut, M, mode, (unsigned long long)h);
+  p->key = kb;
+  int cached = p->tune ? tune_cache_lookup(p->key) : -1;
+  for (int c = 0; c < 3; ++c) {
+    const int nt = kCandNT[c];
+    const bool want = p->tune ? (cached < 0 ? (nt <= 128 || M > 128) : nt == cached) : nt == pick_nt(M);
+    if (!want) continue;
+    plan_build(g, M, mode, nt, lmax_m, nk_m, p->cand[c]);
+    int rc = upload_blob(p->cand[c]);
+    if (rc) {
+      gcamb_plan_destroy(p);
+      return rc;
+    }
+    p->have[c] = true;
+    if (!p->tune || cached == nt) p->chosen = c;
+  }
+  if (p->chosen >= 0 && cached >= 0) p->tuned = true;
+  *out = p;
+  return GCAMB_OK;
+}
+
+int gcamb_plan_destroy(gcamb_plan *p) {
+  if (!p) return GCAMB_OK;
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->cap) cudaStreamDestroy(p->cap);
+  for (auto &c : p->cand) c.release();
+  delete p;
+  return GCAMB_OK;
+}
+
+int gcamb_plan_workspace(const gcamb_plan *p, size_t *bytes) {
+  if (!p || !bytes) return fail(GCAMB_EINVAL, "plan_workspace: NULL argument");
+  size_t b = 0;
+  for (int c = 0; c < 3; ++c)
+    if (p->have[c]) b = std::max(b, p->cand[c].ws_bytes);
+  *bytes = b;
+  return GCAMB_OK;
+}
+
+int gcamb_plan_info(const gcamb_plan *p, int64_t *info) {
+  if (!p || !info) return fail(GCAMB_EINVAL, "plan_info: NULL argument");
+  const TcPlan *c = p->chosen >= 0 ? &p->cand[p->chosen] : nullptr;
+  info[0] = c ? c->NT : 0;
+  info[1] = c ? c->nitems : 0;
+  info[2] = c ? c->nctas : 0;
+  info[3] = p->captures;
+  info[4] = p->replays;
+  info[5] = p->tuned ? 1 : 0;
+  info[6] = p->M;
+  info[7] = c ? (int64_t)c->ws_bytes : 0;
+  return GCAMB_OK;
+}
+
+int gcamb_plan_launch(gcamb_plan *p, const float *S, const double *Pk, double *Cl, void *ws, size_t ws_bytes,
+                      void *stream) {
+  if (!p) return fail(GCAMB_EINVAL, "plan_launch: NULL plan");
+  if (!S || !Pk || !Cl || !ws) return fail(GCAMB_EINVAL, "plan_launch: NULL pointer");
+  size_t need = 0;
+  gcamb_plan_workspace(p, &need);
+  if (ws_bytes < need) return fail(GCAMB_EINVAL, "plan_launch: workspace too small");
+  if (!p->g->tab[p->mode].built) return fail(GCAMB_ESTATE, "plan_launch: the grid's table is gone");
+  cudaStream_t st = (cudaStream_t)stream;
+  char *w = static_cast<char *>(ws);
+  if (!device_error_flag()) return fail(GCAMB_ECUDA, "plan_launch: error flag allocation");
+  if (p->chosen < 0) {
+    // autotune: time every candidate tile on these inputs, keep the fastest
+    float best = 1e30f;
+    int bi = -1;
+    for (int c = 0; c < 3; ++c) {
+      if (!p->have[c]) continue;
+      float ms = 0.f;
+      int rc = plan_time(p, c, S, Pk, Cl, w, st, &ms);
+      if (rc) return rc;
+      if (ms < best) {
+        best = ms;
+        bi = c;
+      }
+    }
+    if (bi < 0) return fail(GCAMB_ESTATE, "plan_launch: no candidate tile");
+    p->chosen = bi;
+    p->tuned = true;
+    tune_cache_store(p->key, p->cand[bi].NT, best);
+    for (int c = 0; c < 3; ++c)
+      if (c != bi && p->have[c]) {
+        p->cand[c].release();
+        p->have[c] = false;
+      }
+  }
+  const bool rebind = !p->exec || p->bS != S || p->bP != Pk || p->bC != Cl || p->bW != ws;
+  if (rebind) {
+    if (p->exec) {
+      cudaGraphExecDestroy(p->exec);
+      p->exec = nullptr;
+    }
+    // capture on a private stream (the legacy default stream cannot be
+    // captured); the graph is then launched on the caller's stream
+    if (!p->cap) {
+      cudaError_t e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking);
+      if (e != cudaSuccess) {
+        p->cap = nullptr;
+        return cuda_fail(e, "plan_launch: capture stream");
+      }
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "plan_launch: begin capture");
+    const int rc = launch_plan(p->g, p->cand[p->chosen], S, Pk, Cl, w, p->cap);
+    e = cudaStreamEndCapture(p->cap, &graph);
+    if (rc) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "plan_launch: end capture");
+    e = cudaGraphInstantiate(&p->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      p->exec = nullptr;
+      return cuda_fail(e, "plan_launch: instantiate");
+    }
+    p->bS = S;
+    p->bP = Pk;
+    p->bC = Cl;
+    p->bW = ws;
+    ++p->captures;
+  }
+  cudaError_t e = cudaGraphLaunch(p->exec, st);
+  if (e != cudaSuccess) return cuda_fail(e, "plan_launch: graph launch");
+  ++p->replays;
+  return GCAMB_OK;
+}
+
+}  // extern "C"

@@ -59,6 +59,11 @@ def lib():
     L.gcamb_los_cl_workspace.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
     L.gcamb_los_cl.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_size_t, _vp]
     L.gcamb_sync.argtypes = [_vp]
+    L.gcamb_plan_create.argtypes = [_vp, ctypes.c_int, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp)]
+    L.gcamb_plan_destroy.argtypes = [_vp]
+    L.gcamb_plan_workspace.argtypes = [_vp, ctypes.POINTER(ctypes.c_size_t)]
+    L.gcamb_plan_launch.argtypes = [_vp, _vp, _vp, _vp, _vp, ctypes.c_size_t, _vp]
+    L.gcamb_plan_info.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
     L.gcamb_los_cl_noalloc.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]
     L.gcamb_profile_enable.argtypes = [ctypes.c_int]
     L.gcamb_profile_read.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
@@ -237,6 +242,79 @@ def los_cl(g: Grid, S, Pk, mode: int, Cl=None, ws=None, stream=None):
                               _dev(Pk, torch.float64, (M, g.nk), "Pk"), M, int(mode),
                               _dev(Cl, torch.float64, (M, g.nl), "Cl"), _dev(ws, torch.uint8, name="ws"),
                               ws.numel(), _stream(stream)))
+    return Cl
+
+
+class Plan:
+    """Owning wrapper of a gcamb_plan handle (an uneven batch on one grid)."""
+
+    def __init__(self, handle, grid, M):
+        self.handle = handle
+        self.grid = grid
+        self.M = M
+
+    def close(self):
+        if self.handle is not None:
+            plan_destroy(self)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def plan_create(g: Grid, M: int, lmax_m=None, nk_m=None, mode: int = F16X3, tune: bool = False) -> Plan:
+    """Plan for M sources; lmax_m / nk_m are per-source l_max and k-prefix
+    lengths (both None: every source uses the whole grid)."""
+    h = _vp()
+    if (lmax_m is None) != (nk_m is None):
+        raise ValueError("give both lmax_m and nk_m, or neither")
+    la = na = None
+    if lmax_m is not None:
+        la = np.ascontiguousarray(lmax_m, dtype=np.int32)
+        na = np.ascontiguousarray(nk_m, dtype=np.int32)
+        if la.size != M or na.size != M:
+            raise ValueError("lmax_m and nk_m must have M entries")
+    _check(lib().gcamb_plan_create(g.handle, int(M), None if la is None else _vp(la.ctypes.data),
+                                   None if na is None else _vp(na.ctypes.data), int(mode), 1 if tune else 0,
+                                   ctypes.byref(h)))
+    return Plan(h, g, int(M))
+
+
+def plan_destroy(p: Plan):
+    if p.handle is not None:
+        _check(lib().gcamb_plan_destroy(p.handle))
+        p.handle = None
+
+
+def plan_workspace(p: Plan) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().gcamb_plan_workspace(p.handle, ctypes.byref(b)))
+    return int(b.value)
+
+
+def plan_info(p: Plan) -> dict:
+    a = (ctypes.c_int64 * 8)()
+    _check(lib().gcamb_plan_info(p.handle, a))
+    keys = ("tile", "items", "ctas", "captures", "replays", "tuned", "M", "workspace")
+    return dict(zip(keys, [int(v) for v in a]))
+
+
+def plan_launch(p: Plan, S, Pk, Cl=None, ws=None, stream=None):
+    """Runs the plan (graph replay after the first launch): S[M][nk][ntau]
+    FP32, Pk[M][nk] FP64 -> Cl[M][nl] FP64."""
+    import torch
+    g = p.grid
+    M = p.M
+    if ws is None:
+        ws = torch.empty(plan_workspace(p), dtype=torch.uint8, device=S.device)
+    if Cl is None:
+        Cl = torch.empty((M, g.nl), dtype=torch.float64, device=S.device)
+    _check(lib().gcamb_plan_launch(p.handle, _dev(S, torch.float32, (M, g.nk, g.ntau), "S"),
+                                   _dev(Pk, torch.float64, (M, g.nk), "Pk"),
+                                   _dev(Cl, torch.float64, (M, g.nl), "Cl"), _dev(ws, torch.uint8, name="ws"),
+                                   ws.numel(), _stream(stream)))
     return Cl
 
 
