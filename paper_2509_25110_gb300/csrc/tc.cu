@@ -455,70 +455,25 @@ __device__ __forceinline__ double prefix_weight(const double *__restrict__ wk, c
   return q > 0 ? 0.5 * (log(k[q]) - log(k[q - 1])) : 0.0;
 }
 
-// bf16 / tf32: S[M][nk][ntau] fp32 -> split blocks [q][mt][kb]{hi plane, lo
-// plane}; rows = sources in plan order (NT per tile; perm maps a plan row to
-// the caller's source), 128-byte swizzled rows of KB tau, zero padded and zero
-// beyond a source's k prefix.  One thread per element.
-template <int MODE>
-__global__ void __launch_bounds__(256) split_sources_kernel(const float *__restrict__ S, int M, int nk, int ntau, int NT,
-                                                            int n_mt, int nkbs, const int *__restrict__ perm,
-                                                            const int *__restrict__ nk_m, char *__restrict__ sp) {
-  constexpr int KB = MODE == kTF32 ? 32 : 64;
-  constexpr int ES = MODE == kTF32 ? 4 : 2;
-  constexpr int ROWS = 256 / KB;  // rows per CTA
-  const int qm = blockIdx.y;      // q * n_mt + mt
-  const int q = qm / n_mt, mt = qm - q * n_mt;
-  const int groups = NT / ROWS;
-  const int kb = blockIdx.x / groups, rg = blockIdx.x - kb * groups;
-  const int c = threadIdx.x % KB;
-  const int n = rg * ROWS + threadIdx.x / KB;
-  const int m = mt * NT + n;
-  const int t = kb * KB + c;
-  float v = 0.f;
-  if (m < M && t < ntau && q < nk_m[m]) v = __ldg(S + ((size_t)perm[m] * nk + q) * ntau + t);
-  char *blk = sp + (((size_t)qm * nkbs) + kb) * (size_t)(256 * NT);
-  const uint32_t o = sw_off(n, c * ES);
-  if constexpr (MODE == kTF32) {
-    const uint32_t hi = tf32_rna_u(v);
-    const uint32_t lo = tf32_rna_u(v - __uint_as_float(hi));
-    *reinterpret_cast<uint32_t *>(blk + o) = hi;
-    *reinterpret_cast<uint32_t *>(blk + NT * 128 + o) = lo;
-  } else {
-    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-    const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-    *reinterpret_cast<__nv_bfloat16 *>(blk + o) = hi;
-    *reinterpret_cast<__nv_bfloat16 *>(blk + NT * 128 + o) = lo;
-  }
-}
-
-// wq[q][m] = sqrt(4 pi w_k P[m][q]) with the source's own k weights (zero
-// for padded sources and beyond the source's k prefix).
-__global__ void weights_kernel(const double *__restrict__ Pk, const double *__restrict__ wk,
-                               const double *__restrict__ kk, int M, int nk, int mpad, const int *__restrict__ perm,
-                               const int *__restrict__ nk_m, float *__restrict__ wq) {
-  const int q = blockIdx.x;
-  for (int m = threadIdx.x; m < mpad; m += blockDim.x) {
-    float v = 0.f;
-    if (m < M && q < nk_m[m])
-      v = (float)sqrt(4.0 * 3.14159265358979323846 * prefix_weight(wk, kk, nk, nk_m[m], q) *
-                      Pk[(size_t)perm[m] * nk + q]);
-    wq[(size_t)q * mpad + m] = v;
-  }
-}
-
-// fp16: one warp per (k, source) row.  The row is scaled by 2^s so that its
-// largest |S| lies in [2^13, 2^14) (fp16 keeps 11 significant bits only in
-// its normal range), split into fp16 hi/lo, and written like the bf16 path.
-// The weight absorbs the scales: wq = sqrt(4 pi w_k P) 2^-(sJ + s), where
-// 2^sJ is the table's scale, so (wq D')^2 is the unscaled contribution.
-__global__ void __launch_bounds__(256) split_sources_f16_kernel(const float *__restrict__ S,
-                                                                const double *__restrict__ Pk,
-                                                                const double *__restrict__ wk,
-                                                                const double *__restrict__ kk, int M, int nk,
-                                                                int ntau, int NT, int n_mt, int nkbs, int mpad,
-                                                                int sJ, const int *__restrict__ perm,
-                                                                const int *__restrict__ nk_m, char *__restrict__ sp,
-                                                                float *__restrict__ wq) {
+// Split of the sources, all modes: one warp per (k, plan-order source) row.
+// S[perm[m]][q][*] (fp32) -> hi/lo planes of the source's row in every
+// tau-block [q][mt][kb]{hi, lo}[NT rows][128 B], 128-byte swizzled, zero
+// padded beyond ntau and beyond the source's k prefix.  Each lane converts
+// one 16-byte output chunk per plane at a time (8 bf16/fp16 or 4 tf32
+// elements), so loads are 32-byte (16-byte for tf32) contiguous runs and
+// stores whole 16-byte chunks.
+// fp16 rows are first scaled by 2^s so that their largest |S| lies in
+// [2^13, 2^14) (fp16 keeps 11 significant bits only in its normal range).
+// Lane 0 writes the row's epilogue weight wq = sqrt(4 pi w_k P) 2^-(sJ + s),
+// with the source's own k weights; (wq D')^2 is then the unscaled term.
+template <int MODE, int CACHE>
+__global__ void __launch_bounds__(256) split_rows_kernel(const float *__restrict__ S, const double *__restrict__ Pk,
+                                                         const double *__restrict__ wk, const double *__restrict__ kk,
+                                                         int M, int nk, int ntau, int NT, int n_mt, int nkbs,
+                                                         int mpad, int sJ, const int *__restrict__ perm,
+                                                         const int *__restrict__ nk_m, int vec,
+                                                         char *__restrict__ sp, float *__restrict__ wq) {
+  constexpr int EPC = MODE == kTF32 ? 4 : 8;  // elements per 16-byte chunk
   const int lane = threadIdx.x & 31;
   const size_t row = (size_t)blockIdx.x * 8 + (threadIdx.x >> 5);  // q * mpad + m
   if (row >= (size_t)nk * mpad) return;
@@ -527,33 +482,106 @@ __global__ void __launch_bounds__(256) split_sources_f16_kernel(const float *__r
   const bool live = mfull < M && q < nk_m[mfull];
   const int mc = live ? perm[mfull] : 0;
   const float *src = S + ((size_t)mc * nk + q) * ntau;
-  float mx = 0.f;
-  if (live)
-    for (int t = lane; t < ntau; t += 32) mx = fmaxf(mx, fabsf(__ldg(src + t)));
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   int s = 0;
-  if (mx > 0.f) {
-    int e;
-    frexpf(mx, &e);  // mx < 2^e
-    s = 14 - e;
-    s = s < -40 ? -40 : (s > 80 ? 80 : s);
+  const int nch = nkbs * 8;  // 16-byte chunks per row over all tau-blocks
+  // loads one chunk's fp32 values (zero beyond ntau and for dead rows)
+  auto load_chunk = [&](int ch, float *v) {
+    const int t0 = ch * EPC;
+    if (live && vec && t0 + EPC <= ntau) {
+      const float4 *s4 = reinterpret_cast<const float4 *>(src + t0);
+#pragma unroll
+      for (int u = 0; u < EPC / 4; ++u) {
+        const float4 f = __ldg(s4 + u);
+        v[4 * u + 0] = f.x;
+        v[4 * u + 1] = f.y;
+        v[4 * u + 2] = f.z;
+        v[4 * u + 3] = f.w;
+      }
+    } else {
+#pragma unroll
+      for (int u = 0; u < EPC; ++u) v[u] = (live && t0 + u < ntau) ? __ldg(src + t0 + u) : 0.f;
+    }
+  };
+  // fp16 with a short row: keep the row in registers between the max and the split
+  float cache[CACHE > 0 ? CACHE : 1][EPC];
+  if constexpr (CACHE > 0) {
+#pragma unroll
+    for (int j = 0; j < CACHE; ++j)
+      if (lane + 32 * j < nch) load_chunk(lane + 32 * j, cache[j]);
+  }
+  if constexpr (MODE == kF16) {
+    float mx = 0.f;
+    if constexpr (CACHE > 0) {
+#pragma unroll
+      for (int j = 0; j < CACHE; ++j)
+#pragma unroll
+        for (int u = 0; u < EPC; ++u)
+          if (lane + 32 * j < nch) mx = fmaxf(mx, fabsf(cache[j][u]));
+    } else if (live) {
+      for (int t = lane; t < ntau; t += 32) mx = fmaxf(mx, fabsf(__ldg(src + t)));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (mx > 0.f) {
+      int e;
+      frexpf(mx, &e);  // mx < 2^e
+      s = 14 - e;
+      s = s < -40 ? -40 : (s > 80 ? 80 : s);
+    }
   }
   char *base = sp + ((size_t)(q * n_mt + mt) * nkbs) * (size_t)(256 * NT);
-  for (int t = lane; t < nkbs * 64; t += 32) {
-    const float v = (live && t < ntau) ? ldexpf(__ldg(src + t), s) : 0.f;
-    const __half hi = __float2half_rn(v);
-    const __half lo = __float2half_rn(v - __half2float(hi));
-    char *blk = base + (size_t)(t >> 6) * (256 * NT);
-    const uint32_t o = sw_off(n, (t & 63) * 2);
-    *reinterpret_cast<__half *>(blk + o) = hi;
-    *reinterpret_cast<__half *>(blk + NT * 128 + o) = lo;
+#pragma unroll(CACHE > 0 ? CACHE : 1)
+  for (int j = 0; (CACHE > 0 ? j < CACHE : true); ++j) {
+    const int ch = lane + 32 * j;
+    if (ch >= nch) break;
+    float v[EPC];
+    if constexpr (CACHE > 0) {
+#pragma unroll
+      for (int u = 0; u < EPC; ++u) v[u] = cache[j][u];
+    } else {
+      load_chunk(ch, v);
+    }
+    uint4 hi, lo;
+    uint32_t *h = reinterpret_cast<uint32_t *>(&hi), *l = reinterpret_cast<uint32_t *>(&lo);
+    if constexpr (MODE == kTF32) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        h[u] = tf32_rna_u(v[u]);
+        l[u] = tf32_rna_u(v[u] - __uint_as_float(h[u]));
+      }
+    } else if constexpr (MODE == kF16) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float a = ldexpf(v[2 * u], s), b = ldexpf(v[2 * u + 1], s);
+        const __half2 hh = __floats2half2_rn(a, b);
+        const __half2 ll = __floats2half2_rn(a - __low2float(hh), b - __high2float(hh));
+        h[u] = *reinterpret_cast<const uint32_t *>(&hh);
+        l[u] = *reinterpret_cast<const uint32_t *>(&ll);
+      }
+    } else {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const __nv_bfloat162 hh = __floats2bfloat162_rn(v[2 * u], v[2 * u + 1]);
+        const __nv_bfloat162 ll =
+            __floats2bfloat162_rn(v[2 * u] - __low2float(hh), v[2 * u + 1] - __high2float(hh));
+        h[u] = *reinterpret_cast<const uint32_t *>(&hh);
+        l[u] = *reinterpret_cast<const uint32_t *>(&ll);
+      }
+    }
+    char *blk = base + (size_t)(ch >> 3) * (256 * NT);
+    const uint32_t o = sw_off(n, (ch & 7) * 16);
+    *reinterpret_cast<uint4 *>(blk + o) = hi;
+    *reinterpret_cast<uint4 *>(blk + NT * 128 + o) = lo;
   }
-  if (lane == 0)
-    wq[row] = live ? (float)ldexp(sqrt(4.0 * 3.14159265358979323846 * prefix_weight(wk, kk, nk, nk_m[mfull], q) *
-                                       Pk[(size_t)mc * nk + q]),
-                                  -(sJ + s))
-                   : 0.f;
+  if (lane == 0) {
+    float w = 0.f;
+    if (live) {
+      const double root = sqrt(4.0 * 3.14159265358979323846 * prefix_weight(wk, kk, nk, nk_m[mfull], q) *
+                               Pk[(size_t)mc * nk + q]);
+      w = (float)(MODE == kF16 ? ldexp(root, -(sJ + s)) : root);
+    }
+    wq[row] = w;
+  }
 }
 
 // C[m][l] = sum over the tile's items (fixed order) of the FP32 chunk sums, in
@@ -788,21 +816,17 @@ int launch_tc(const gcamb_grid *g, const TcPlan &pl, const float *S, const doubl
   float *part = reinterpret_cast<float *>(ws + pl.off_part);
   const int *B = pl.d_blob;
   const int *perm = B + pl.o_perm, *nkm = B + pl.o_nkm, *lmm = B + pl.o_lmaxm;
-  if constexpr (MODE == kF16) {
+  {
     const size_t rows = (size_t)g->nk * pl.mpad;
+    const int vec = (g->ntau % 4 == 0) && (reinterpret_cast<uintptr_t>(S) % 16 == 0);
+    const unsigned nblk = (unsigned)((rows + 7) / 8);
     ProfScope prof(GCAMB_K_SPLIT, st);
-    split_sources_f16_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, st>>>(S, Pk, g->d_wk, g->d_k, pl.M, g->nk, g->ntau,
-                                                                        NT, pl.n_mt, pl.nkbs, pl.mpad, t.scale_exp,
-                                                                        perm, nkm, sp, wp);
-  } else {
-    {
-      constexpr int KB = MODE == kTF32 ? 32 : 64;
-      dim3 grid(pl.nkbs * (NT / (256 / KB)), g->nk * pl.n_mt);
-      ProfScope prof(GCAMB_K_SPLIT, st);
-      split_sources_kernel<MODE><<<grid, 256, 0, st>>>(S, pl.M, g->nk, g->ntau, NT, pl.n_mt, pl.nkbs, perm, nkm, sp);
-    }
-    ProfScope prof(GCAMB_K_WEIGHTS, st);
-    weights_kernel<<<g->nk, 256, 0, st>>>(Pk, g->d_wk, g->d_k, pl.M, g->nk, pl.mpad, perm, nkm, wp);
+    if (MODE == kF16 && pl.nkbs * 8 <= 32 * 8)
+      split_rows_kernel<MODE, 8><<<nblk, 256, 0, st>>>(S, Pk, g->d_wk, g->d_k, pl.M, g->nk, g->ntau, NT, pl.n_mt,
+                                                       pl.nkbs, pl.mpad, t.scale_exp, perm, nkm, vec, sp, wp);
+    else
+      split_rows_kernel<MODE, 0><<<nblk, 256, 0, st>>>(S, Pk, g->d_wk, g->d_k, pl.M, g->nk, g->ntau, NT, pl.n_mt,
+                                                       pl.nkbs, pl.mpad, t.scale_exp, perm, nkm, vec, sp, wp);
   }
   if (pl.nitems > 0) {
     cudaError_t e = cudaFuncSetAttribute(los_cl_tc_kernel<NT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
