@@ -249,6 +249,92 @@ int gcamb_plan_launch(gcamb_plan *p, const float *S, const double *Pk, double *C
 int gcamb_plan_info(const gcamb_plan *p, int64_t *info);
 
 /*
+ * Emulator of log C_l with a projection fallback.  The paper builds none; it
+ * motivates fast spectra as training sets for emulators (Sec. 1, Sec. 5).
+ * An MLP maps the 9 features of the synthetic source generator
+ *   x = (tau*, sigma, r_s, cos phi, sin phi, k_D, b, n_s, ln(1e10 A_s))
+ * to the standardised log C_l of the grid's multipoles (n_out = nl), with
+ * `depth` hidden layers of `width` units and GELU.  It is trained on the
+ * device by the library's kernels: tcgen05 GEMMs with bf16 operands and FP32
+ * accumulation, FP32 parameters and Adam moments.  Parameter layout (host
+ * arrays of gcamb_emu_params / gcamb_emu_grads): for each layer l, W_l
+ * [out][in] row-major, then b_l [out].
+ *
+ * All pointers below are device memory unless marked host.
+ */
+typedef struct gcamb_emu gcamb_emu;
+
+#define GCAMB_EMU_INFO_N 8
+#define GCAMB_EMU_CHECK_N 6
+
+/* n_in must be 9; 16 <= width <= 4096, 1 <= depth <= 8; batches up to
+ * max_batch.  Parameters U(-1/sqrt(fan_in), 1/sqrt(fan_in)) from SplitMix64
+ * on (seed, index); identity normalisation. */
+int gcamb_emu_create(gcamb_grid *g, int n_in, int width, int depth, int max_batch, uint64_t seed, gcamb_emu **out);
+int gcamb_emu_destroy(gcamb_emu *e);
+/* Number of parameters (host size_t*). */
+int gcamb_emu_num_params(const gcamb_emu *e, size_t *n);
+/* Copies host_in into the parameters (if not NULL), then the parameters into
+ * host_out (if not NULL); host float arrays of gcamb_emu_num_params entries. */
+int gcamb_emu_params(gcamb_emu *e, float *host_out, const float *host_in);
+/* Gradients of the last gcamb_emu_train_step (host float array). */
+int gcamb_emu_grads(gcamb_emu *e, float *host_out);
+/* Normalisation (host float arrays, n_in and n_out long): set = 1 writes
+ * them, set = 0 reads them.  Inputs enter as (x - mu_x) / sd_x (sd_x = 0: the
+ * feature is dropped), outputs leave as y sd_y + mu_y. */
+int gcamb_emu_norm(gcamb_emu *e, float *mu_x, float *sd_x, float *mu_y, float *sd_y, int set);
+/* Fits the normalisation on N training samples X[N][9], Cl[N][n_out] (>0)
+ * and writes the standardised targets Y[N][n_out] = (log Cl - mu_y) / sd_y.
+ * Synchronises the stream. */
+int gcamb_emu_fit_norm(gcamb_emu *e, const float *X, const double *Cl, int N, float *Y, void *stream);
+/* One Adam step (lr; beta 0.9, 0.999; eps 1e-8) on the mean squared error of
+ * the batch X[idx[b]], Y[idx[b]] (idx[B] device int, or NULL for the first B
+ * rows); the batch loss goes to *loss (device float, may be NULL). */
+int gcamb_emu_train_step(gcamb_emu *e, const float *X, const float *Y, const int *idx, int B, float lr, float *loss,
+                         void *stream);
+/* Standardised network output Y[B][n_out] for X[B][9]. */
+int gcamb_emu_forward(gcamb_emu *e, const float *X, int B, float *Y, void *stream);
+/*
+ * Held-out check against reference spectra Cl_ref[N][n_out] (from the
+ * projection path) for X[N][9]: per spectrum the max over l of
+ * |C_emu/C_ref - 1|.  Parameter space is cut into at most 16 cells by
+ * splitting, at its held-out median, each of the (at most 4) features whose
+ * two halves differ most in mean log error; a cell is trusted when it holds at
+ * least max(1, min_count) held-out spectra and all are within tol.  report (host double[GCAMB_EMU_CHECK_N]): max error, mean error,
+ * fraction within tol, fraction of cells trusted, fraction of held-out
+ * spectra in trusted cells, number of cells.  Synchronises the stream.
+ */
+int gcamb_emu_check(gcamb_emu *e, const float *X, const double *Cl_ref, int N, double tol, int min_count,
+                    double *report, void *stream);
+/*
+ * C_l[B][n_out] (double) for X[B][9]: requests in trusted cells from the
+ * network (exp of the de-standardised output), the others (all of them before
+ * any check) from the batched projection, gcamb_los_cl in GCAMB_F16X3 on
+ * sources regenerated by gcamb_synth_sources; used_fallback[B] (device int)
+ * marks those.  Synchronises the stream; builds the F16X3 table if needed.
+ */
+int gcamb_emulate(gcamb_emu *e, const float *X, int B, double *Cl, int *used_fallback, void *stream);
+/* Summary (host double[GCAMB_EMU_INFO_N]): parameters, Adam steps, last check's
+ * max error, its tol, fraction of cells trusted, n_out, device error flag,
+ * width. */
+int gcamb_emu_info(const gcamb_emu *e, double *info);
+/* Checkpoint: architecture, step, parameters, Adam moments, normalisation,
+ * trust cells, FNV-1a checksum.  Load requires the same architecture. */
+int gcamb_emu_save(const gcamb_emu *e, const char *path);
+int gcamb_emu_load(gcamb_emu *e, const char *path);
+
+/*
+ * The synthetic source family (input synthesis, not the method): for
+ * features X[M][9] as above,
+ *   S(k, tau) = N(tau; tau*, sigma) cos(k r_s + phi) exp(-(k/k_D)^2)
+ *             + b exp(-(tau - 11000)^2 / (2 * 2000^2)) exp(-k / 0.01)
+ *   P(k) = A_s (k / 0.05)^(n_s - 1),  phi = atan2(sin phi, cos phi)
+ * on the grid's nodes, evaluated in FP64: S[M][nk][ntau] float, Pk[M][nk]
+ * double.
+ */
+int gcamb_synth_sources(const gcamb_grid *g, const float *X, int M, float *S, double *Pk, void *stream);
+
+/*
  * gcamb_los_cl without any device allocation.  The paper has no counterpart:
  * this entry point exists for callers that may not allocate device memory,
  * such as a likelihood callback running inside a sampler or host framework

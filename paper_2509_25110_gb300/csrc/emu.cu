@@ -1,0 +1,948 @@
+// Emulator of log C_l with a projection fallback.
+//
+// An MLP maps the 9 source-generator features to standardised log C_l
+// (l = lmin..lmax of a grid).  It is trained on the device by the library's
+// own kernels: tcgen05 GEMMs with bf16 operands and FP32 accumulation
+// (emu_gemm.cuh) for the forward pass, the input and weight gradients, and
+// small kernels for GELU, the loss, bias gradients and Adam.  Parameters and
+// Adam moments are FP32; every matrix-product operand is rounded to bf16 at
+// load time.  A held-out check (spectra from the projection path) marks cells
+// of parameter space as trusted; gcamb_emulate answers trusted requests from
+// the network and the rest from the batched projection (gcamb_los_cl) on
+// sources regenerated from the features.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "emu_gemm.cuh"
+#include "internal.h"
+
+using namespace gcamb;
+using namespace gcamb::emu;
+
+struct gcamb_emu {
+  gcamb_grid *g = nullptr;
+  int n_in = 0, width = 0, depth = 0, n_out = 0, max_batch = 0;
+  std::vector<int> sizes;                // n_in, width x depth, n_out
+  std::vector<size_t> w_off, b_off;      // offsets of W_l [out][in] and b_l [out] in theta
+  size_t n_params = 0;
+  float *theta = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
+  float *mu_x = nullptr, *isd_x = nullptr, *mu_y = nullptr, *sd_y = nullptr;
+  float *xs = nullptr, *out = nullptr, *d0 = nullptr, *d1 = nullptr, *loss_part = nullptr, *loss = nullptr;
+  std::vector<float *> Z, H;             // hidden pre-activations and activations [B][width]
+  // feature-major copies, so that every GEMM operand is contiguous along its
+  // contraction index: xs^T, H^T [width][B], the gradients' (d)^T, W^T
+  float *xsT = nullptr, *dT0 = nullptr, *dT1 = nullptr, *WT = nullptr, *splitk = nullptr;
+  std::vector<float *> HT;
+  int64_t step = 0;
+  int *err = nullptr;
+  // trust cells: bit d of a cell is (x[cell_dim[d]] > cell_mid[d])
+  std::vector<int> cell_dim;
+  std::vector<float> cell_mid;
+  std::vector<unsigned char> trusted;
+  int *d_cell_dim = nullptr;
+  float *d_cell_mid = nullptr;
+  unsigned char *d_trusted = nullptr;
+  double check_max_err = -1.0, check_tol = 0.0;
+  // fallback buffers
+  int fb_cap = 0, fb_mode = GCAMB_F16X3;
+  float *fb_x = nullptr, *fb_S = nullptr;
+  double *fb_P = nullptr, *fb_C = nullptr;
+  int *fb_idx = nullptr;
+  void *fb_ws = nullptr;
+  size_t fb_ws_bytes = 0;
+};
+
+namespace {
+
+constexpr int kLossBlocks = 256;
+constexpr uint32_t kEmuMagic = 0x47454D55u;  // "GEMU"
+
+int ck(cudaError_t e, const char *what) { return e == cudaSuccess ? GCAMB_OK : cuda_fail(e, what); }
+
+template <typename T>
+int dalloc(T **p, size_t n) {
+  cudaError_t e = cudaMalloc(p, std::max<size_t>(1, n) * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return e == cudaErrorMemoryAllocation ? fail(GCAMB_ENOMEM, "emu: device allocation") : cuda_fail(e, "emu: cudaMalloc");
+  }
+  return GCAMB_OK;
+}
+
+// ---------------------------------------------------------------- kernels
+
+__device__ __forceinline__ uint64_t sm64(uint64_t c) {
+  uint64_t z = c + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// U(-bound, bound) from SplitMix64 on (seed, parameter index)
+__global__ void init_uniform_kernel(float *p, size_t n, float bound, uint64_t seed, uint64_t base) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double u = (double)(sm64((seed << 40) ^ (base + i)) >> 11) * (1.0 / 9007199254740992.0);
+    p[i] = (float)((2.0 * u - 1.0) * bound);
+  }
+}
+
+__global__ void standardize_kernel(const float *__restrict__ X, const int *__restrict__ idx, int B, int n,
+                                   const float *__restrict__ mu, const float *__restrict__ isd, float *__restrict__ xs,
+                                   float *__restrict__ xsT) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= B * n) return;
+  const int b = e / n, j = e - b * n;
+  const int r = idx ? idx[b] : b;
+  const float v = (X[(size_t)r * n + j] - mu[j]) * isd[j];
+  xs[e] = v;
+  if (xsT) xsT[(size_t)j * B + b] = v;
+}
+
+// dOut = 2 (out - y) / (B N); per-block partial sums of (out - y)^2
+__global__ void __launch_bounds__(256) loss_kernel(const float *__restrict__ out, const float *__restrict__ Y,
+                                                   const int *__restrict__ idx, int B, int N, float *__restrict__ dout,
+                                                   float *__restrict__ doutT, float *__restrict__ part) {
+  __shared__ float red[256];
+  const size_t total = (size_t)B * N;
+  const float scale = 2.f / (float)total;
+  float acc = 0.f;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t b = e / N, n = e - b * N;
+    const size_t r = idx ? (size_t)idx[b] : b;
+    const float d = out[e] - Y[r * N + n];
+    dout[e] = scale * d;
+    doutT[n * B + b] = scale * d;
+    acc += d * d;
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void loss_final_kernel(const float *__restrict__ part, int nb, float inv_total, float *__restrict__ loss) {
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < nb; ++i) s += part[i];
+    *loss = (float)(s * inv_total);
+  }
+}
+
+// db[n] = sum_b DT[n][b]: one warp per row, lanes in a fixed order then a
+// fixed shuffle tree (deterministic)
+__global__ void rowsum_kernel(const float *__restrict__ DT, int B, int N, float *__restrict__ db) {
+  const int n = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (n >= N) return;
+  float s = 0.f;
+  for (int b = lane; b < B; b += 32) s += DT[(size_t)n * B + b];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) db[n] = s;
+}
+
+// WT[i][o] = W[o][i]
+__global__ void transpose_kernel(const float *__restrict__ W, int nout, int nin, float *__restrict__ WT) {
+  __shared__ float t[32][33];
+  const int o0 = blockIdx.y * 32, i0 = blockIdx.x * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int o = o0 + r, i = i0 + threadIdx.x;
+    if (o < nout && i < nin) t[r][threadIdx.x] = W[(size_t)o * nin + i];
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int i = i0 + r, o = o0 + threadIdx.x;
+    if (o < nout && i < nin) WT[(size_t)i * nout + o] = t[threadIdx.x][r];
+  }
+}
+
+// C[e] = sum_z part[z][e], increasing z
+__global__ void splitk_reduce_kernel(const float *__restrict__ part, int nz, size_t n, float *__restrict__ C) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int z = 0; z < nz; ++z) s += part[(size_t)z * n + e];
+    C[e] = s;
+  }
+}
+
+__global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
+                            float *__restrict__ v, size_t n, float lr, float b1, float b2, float eps, float bc1,
+                            float bc2) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+  }
+}
+
+// column mean and standard deviation (two passes, FP64), thread per column
+__global__ void colstats_kernel(const float *__restrict__ X, int N, int n, float *__restrict__ mu,
+                                float *__restrict__ sd) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double s = 0.0;
+  for (int i = 0; i < N; ++i) s += X[(size_t)i * n + j];
+  const double mean = s / N;
+  double q = 0.0;
+  for (int i = 0; i < N; ++i) {
+    const double d = X[(size_t)i * n + j] - mean;
+    q += d * d;
+  }
+  mu[j] = (float)mean;
+  sd[j] = (float)sqrt(q / N);
+}
+
+__global__ void log_kernel(const double *__restrict__ C, size_t n, float *__restrict__ Y) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    Y[i] = (float)log(C[i]);
+}
+
+__global__ void standardize_y_kernel(float *__restrict__ Y, size_t N, int n, const float *__restrict__ mu,
+                                     const float *__restrict__ sd) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N * n; i += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(i % n);
+    Y[i] = (Y[i] - mu[j]) / (sd[j] > 0.f ? sd[j] : 1.f);
+  }
+}
+
+__global__ void inv_sd_kernel(const float *__restrict__ sd, int n, float *__restrict__ isd) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) isd[j] = sd[j] > 1e-12f ? 1.f / sd[j] : 0.f;
+}
+
+// C_l = exp(out sd + mu)
+__global__ void exp_kernel(const float *__restrict__ out, size_t B, int n, const float *__restrict__ mu,
+                           const float *__restrict__ sd, double *__restrict__ C) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < B * n; i += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(i % n);
+    C[i] = exp((double)out[i] * (double)(sd[j] > 0.f ? sd[j] : 1.f) + (double)mu[j]);
+  }
+}
+
+__global__ void cell_kernel(const float *__restrict__ X, int B, int n_in, const int *__restrict__ dims,
+                            const float *__restrict__ mids, int nd, const unsigned char *__restrict__ trusted,
+                            int *__restrict__ cell, int *__restrict__ fallback) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  int c = 0;
+  for (int d = 0; d < nd; ++d)
+    if (X[(size_t)b * n_in + dims[d]] > mids[d]) c |= 1 << d;
+  if (cell) cell[b] = c;
+  if (fallback) fallback[b] = trusted ? (trusted[c] ? 0 : 1) : 1;
+}
+
+// per-sample max |C_emu / C_ref - 1|
+__global__ void __launch_bounds__(256) maxrel_kernel(const double *__restrict__ Ce, const double *__restrict__ Cr,
+                                                     int n, double *__restrict__ err) {
+  __shared__ double red[256];
+  const size_t b = blockIdx.x;
+  double mx = 0.0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const double r = Cr[b * n + j];
+    const double e = r != 0.0 ? fabs(Ce[b * n + j] / r - 1.0) : fabs(Ce[b * n + j]);
+    mx = e > mx ? e : mx;
+  }
+  red[threadIdx.x] = mx;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) err[b] = red[0];
+}
+
+__global__ void gather_rows_kernel(const float *__restrict__ X, const int *__restrict__ idx, int B, int n,
+                                   float *__restrict__ out) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < B * n) out[e] = X[(size_t)idx[e / n] * n + (e % n)];
+}
+
+__global__ void scatter_rows_kernel(const double *__restrict__ src, const int *__restrict__ idx, int B, int n,
+                                    double *__restrict__ dst) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)B * n; e += (size_t)gridDim.x * blockDim.x)
+    dst[(size_t)idx[e / n] * n + (e % n)] = src[e];
+}
+
+// Synthetic sources of one generator family from its 9 features
+// (tau*, sigma, r_s, cos phi, sin phi, k_D, b, n_s, ln(1e10 A_s)):
+// S(k, tau) = N(tau; tau*, sigma) cos(k r_s + phi) exp(-(k/k_D)^2)
+//           + b exp(-(tau - 11000)^2 / (2 2000^2)) exp(-k / 0.01),
+// P(k) = A_s (k / 0.05)^(n_s - 1).  S separates into tau and k factors: one
+// block per (source, 256 k nodes) evaluates them once in FP64 (shared memory)
+// and combines them with two multiply-adds per element; stored FP32 (S) and
+// FP64 (P).
+__global__ void __launch_bounds__(256) synth_kernel(const float *__restrict__ X, const double *__restrict__ k,
+                                                    const double *__restrict__ tau, int nk, int ntau,
+                                                    float *__restrict__ S, double *__restrict__ P) {
+  extern __shared__ double sh[];  // g[ntau], late[ntau], a[256], e[256]
+  double *gt = sh, *lt = sh + ntau, *ak = sh + 2 * ntau, *ek = ak + 256;
+  const int m = blockIdx.y, q0 = blockIdx.x * 256;
+  const float *f = X + (size_t)m * 9;
+  const double ts = f[0], sg = f[1], rs = f[2], phi = atan2((double)f[4], (double)f[3]), kd = f[5], bb = f[6];
+  const double inv_norm = 1.0 / (sg * sqrt(2.0 * 3.14159265358979323846));
+  for (int i = threadIdx.x; i < ntau; i += blockDim.x) {
+    const double t = tau[i];
+    gt[i] = exp(-(t - ts) * (t - ts) / (2.0 * sg * sg)) * inv_norm;
+    lt[i] = bb * exp(-(t - 11000.0) * (t - 11000.0) / (2.0 * 2000.0 * 2000.0));
+  }
+  {
+    const int q = q0 + threadIdx.x;
+    if (q < nk) {
+      const double kk = k[q];
+      ak[threadIdx.x] = cos(kk * rs + phi) * exp(-(kk / kd) * (kk / kd));
+      ek[threadIdx.x] = exp(-kk / 0.01);
+      P[(size_t)m * nk + q] = exp((double)f[8]) * 1e-10 * pow(kk / 0.05, (double)f[7] - 1.0);
+    }
+  }
+  __syncthreads();
+  const int nq = min(256, nk - q0);
+  for (int qq = 0; qq < nq; ++qq) {
+    const double a = ak[qq], b = ek[qq];
+    float *row = S + ((size_t)m * nk + q0 + qq) * ntau;
+    for (int i = threadIdx.x; i < ntau; i += blockDim.x) row[i] = (float)fma(gt[i], a, lt[i] * b);
+  }
+}
+
+// ---------------------------------------------------------------- GEMM launcher
+
+template <int EPI>
+int gemm(const GemmArgs &a, cudaStream_t st, int nz = 1) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(gemm_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
+    if (e != cudaSuccess) return cuda_fail(e, "emu: gemm smem attribute");
+    attr = true;
+  }
+  dim3 grid((a.M + 127) / 128, (a.N + 127) / 128, nz);
+  gemm_kernel<EPI><<<grid, 128, kGemmSmem, st>>>(a);
+  return ck(cudaGetLastError(), "emu: gemm launch");
+}
+
+View rowmajor(const float *p, int R, int K, long long ld, const int *rows = nullptr) {
+  return View{p, ld, 1, rows, R, K};
+}
+
+int forward_pass(gcamb_emu *e, const float *X, const int *idx, int B, cudaStream_t st) {
+  const int L = e->depth + 1;
+  {
+    const int n = B * e->n_in;
+    standardize_kernel<<<(n + 255) / 256, 256, 0, st>>>(X, idx, B, e->n_in, e->mu_x, e->isd_x, e->xs, e->xsT);
+  }
+  const float *h = e->xs;
+  int hin = e->n_in;
+  for (int l = 0; l < L; ++l) {
+    const int nout = e->sizes[l + 1];
+    GemmArgs a{};
+    a.A = rowmajor(h, B, hin, hin);
+    a.B = rowmajor(e->theta + e->w_off[l], nout, hin, hin);
+    a.M = B;
+    a.N = nout;
+    a.K = hin;
+    a.bias = e->theta + e->b_off[l];
+    a.err = e->err;
+    int rc;
+    if (l < L - 1) {
+      a.C = e->Z[l];
+      a.ldc = nout;
+      a.H = e->H[l];
+      a.CT = e->HT[l];
+      a.ldct = B;
+      rc = gemm<kBiasGelu>(a, st);
+      h = e->H[l];
+    } else {
+      a.C = e->out;
+      a.ldc = nout;
+      rc = gemm<kBias>(a, st);
+    }
+    if (rc) return rc;
+    hin = nout;
+  }
+  return GCAMB_OK;
+}
+
+int check_emu(const gcamb_emu *e, int B) {
+  if (!e) return fail(GCAMB_EINVAL, "emu: NULL handle");
+  if (B < 1 || B > e->max_batch) return fail(GCAMB_EINVAL, "emu: batch must be in [1, max_batch]");
+  return GCAMB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gcamb_emu_create(gcamb_grid *g, int n_in, int width, int depth, int max_batch, uint64_t seed, gcamb_emu **out) {
+  if (!out) return fail(GCAMB_EINVAL, "emu_create: out is NULL");
+  *out = nullptr;
+  if (!g) return fail(GCAMB_EINVAL, "emu_create: NULL grid");
+  if (n_in != 9) return fail(GCAMB_EINVAL, "emu_create: the source generator has 9 features");
+  if (width < 16 || width > 4096 || depth < 1 || depth > 8) return fail(GCAMB_EINVAL, "emu_create: width/depth");
+  if (max_batch < 1 || max_batch > (1 << 20)) return fail(GCAMB_EINVAL, "emu_create: max_batch");
+  int rc = ensure_device_grid(g);
+  if (rc) return rc;
+  gcamb_emu *e = new (std::nothrow) gcamb_emu();
+  if (!e) return fail(GCAMB_ENOMEM, "emu_create: host allocation");
+  e->g = g;
+  e->n_in = n_in;
+  e->width = width;
+  e->depth = depth;
+  e->n_out = g->nl;
+  e->max_batch = max_batch;
+  e->sizes.push_back(n_in);
+  for (int d = 0; d < depth; ++d) e->sizes.push_back(width);
+  e->sizes.push_back(e->n_out);
+  size_t o = 0;
+  for (size_t l = 0; l + 1 < e->sizes.size(); ++l) {
+    e->w_off.push_back(o);
+    o += (size_t)e->sizes[l + 1] * e->sizes[l];
+    e->b_off.push_back(o);
+    o += e->sizes[l + 1];
+  }
+  e->n_params = o;
+  const size_t mx = std::max(width, e->n_out);
+  if ((rc = dalloc(&e->theta, o)) || (rc = dalloc(&e->grad, o)) || (rc = dalloc(&e->m, o)) || (rc = dalloc(&e->v, o)) ||
+      (rc = dalloc(&e->mu_x, n_in)) || (rc = dalloc(&e->isd_x, n_in)) || (rc = dalloc(&e->mu_y, e->n_out)) ||
+      (rc = dalloc(&e->sd_y, e->n_out)) || (rc = dalloc(&e->xs, (size_t)max_batch * n_in)) ||
+      (rc = dalloc(&e->out, (size_t)max_batch * e->n_out)) || (rc = dalloc(&e->d0, (size_t)max_batch * mx)) ||
+      (rc = dalloc(&e->d1, (size_t)max_batch * mx)) || (rc = dalloc(&e->loss_part, kLossBlocks)) ||
+      (rc = dalloc(&e->loss, 1)) || (rc = dalloc(&e->err, 1)) || (rc = dalloc(&e->xsT, (size_t)max_batch * n_in)) ||
+      (rc = dalloc(&e->dT0, (size_t)max_batch * mx)) || (rc = dalloc(&e->dT1, (size_t)max_batch * mx)) ||
+      (rc = dalloc(&e->WT, o))) {
+    gcamb_emu_destroy(e);
+    return rc;
+  }
+  for (int d = 0; d < depth; ++d) {
+    float *z = nullptr, *h = nullptr, *ht = nullptr;
+    if ((rc = dalloc(&z, (size_t)max_batch * width)) || (rc = dalloc(&h, (size_t)max_batch * width)) ||
+        (rc = dalloc(&ht, (size_t)max_batch * width))) {
+      cudaFree(z);
+      cudaFree(h);
+      gcamb_emu_destroy(e);
+      return rc;
+    }
+    e->Z.push_back(z);
+    e->H.push_back(h);
+    e->HT.push_back(ht);
+  }
+  {
+    // split-K partials of the weight gradients: (ceil(max_batch / 256)) slices of the largest W
+    size_t wmax = 0;
+    for (size_t l = 0; l + 1 < e->sizes.size(); ++l) wmax = std::max(wmax, (size_t)e->sizes[l + 1] * e->sizes[l]);
+    const size_t nzmax = ((size_t)max_batch + 255) / 256;
+    if ((rc = dalloc(&e->splitk, nzmax * wmax))) {
+      gcamb_emu_destroy(e);
+      return rc;
+    }
+  }
+  // parameters U(-1/sqrt(fan_in), 1/sqrt(fan_in)); identity normalisation
+  for (size_t l = 0; l + 1 < e->sizes.size(); ++l) {
+    const float bound = 1.f / sqrtf((float)e->sizes[l]);
+    const size_t nw = (size_t)e->sizes[l + 1] * e->sizes[l];
+    init_uniform_kernel<<<256, 256>>>(e->theta + e->w_off[l], nw, bound, seed, e->w_off[l]);
+    init_uniform_kernel<<<64, 256>>>(e->theta + e->b_off[l], e->sizes[l + 1], bound, seed, e->b_off[l]);
+  }
+  cudaMemset(e->m, 0, o * sizeof(float));
+  cudaMemset(e->v, 0, o * sizeof(float));
+  cudaMemset(e->err, 0, sizeof(int));
+  std::vector<float> zeros(std::max(n_in, e->n_out), 0.f), ones(std::max(n_in, e->n_out), 1.f);
+  cudaMemcpy(e->mu_x, zeros.data(), n_in * sizeof(float), cudaMemcpyHostToDevice);
+  cudaMemcpy(e->isd_x, ones.data(), n_in * sizeof(float), cudaMemcpyHostToDevice);
+  cudaMemcpy(e->mu_y, zeros.data(), e->n_out * sizeof(float), cudaMemcpyHostToDevice);
+  rc = ck(cudaMemcpy(e->sd_y, ones.data(), e->n_out * sizeof(float), cudaMemcpyHostToDevice), "emu_create: init");
+  if (rc) {
+    gcamb_emu_destroy(e);
+    return rc;
+  }
+  *out = e;
+  return GCAMB_OK;
+}
+
+int gcamb_emu_destroy(gcamb_emu *e) {
+  if (!e) return GCAMB_OK;
+  for (void *p : {(void *)e->theta, (void *)e->grad, (void *)e->m, (void *)e->v, (void *)e->mu_x, (void *)e->isd_x,
+                  (void *)e->mu_y, (void *)e->sd_y, (void *)e->xs, (void *)e->out, (void *)e->d0, (void *)e->d1,
+                  (void *)e->loss_part, (void *)e->loss, (void *)e->err, (void *)e->d_cell_dim,
+                  (void *)e->d_cell_mid, (void *)e->d_trusted, (void *)e->fb_x, (void *)e->fb_S, (void *)e->fb_P,
+                  (void *)e->fb_C, (void *)e->fb_idx, e->fb_ws, (void *)e->xsT, (void *)e->dT0, (void *)e->dT1,
+                  (void *)e->WT, (void *)e->splitk})
+    cudaFree(p);
+  for (float *p : e->Z) cudaFree(p);
+  for (float *p : e->H) cudaFree(p);
+  for (float *p : e->HT) cudaFree(p);
+  delete e;
+  return GCAMB_OK;
+}
+
+int gcamb_emu_num_params(const gcamb_emu *e, size_t *n) {
+  if (!e || !n) return fail(GCAMB_EINVAL, "emu_num_params: NULL argument");
+  *n = e->n_params;
+  return GCAMB_OK;
+}
+
+int gcamb_emu_params(gcamb_emu *e, float *host_out, const float *host_in) {
+  if (!e) return fail(GCAMB_EINVAL, "emu_params: NULL handle");
+  const size_t bytes = e->n_params * sizeof(float);
+  if (host_in) {
+    int rc = ck(cudaMemcpy(e->theta, host_in, bytes, cudaMemcpyHostToDevice), "emu_params: upload");
+    if (rc) return rc;
+  }
+  if (host_out) return ck(cudaMemcpy(host_out, e->theta, bytes, cudaMemcpyDeviceToHost), "emu_params: download");
+  return GCAMB_OK;
+}
+
+int gcamb_emu_grads(gcamb_emu *e, float *host_out) {
+  if (!e || !host_out) return fail(GCAMB_EINVAL, "emu_grads: NULL argument");
+  return ck(cudaMemcpy(host_out, e->grad, e->n_params * sizeof(float), cudaMemcpyDeviceToHost), "emu_grads");
+}
+
+int gcamb_emu_norm(gcamb_emu *e, float *mu_x, float *sd_x, float *mu_y, float *sd_y, int set) {
+  if (!e) return fail(GCAMB_EINVAL, "emu_norm: NULL handle");
+  if (set) {
+    if (!mu_x || !sd_x || !mu_y || !sd_y) return fail(GCAMB_EINVAL, "emu_norm: NULL array");
+    std::vector<float> isd(e->n_in);
+    for (int j = 0; j < e->n_in; ++j) isd[j] = sd_x[j] > 1e-12f ? 1.f / sd_x[j] : 0.f;
+    cudaMemcpy(e->mu_x, mu_x, e->n_in * sizeof(float), cudaMemcpyHostToDevice);
+    cudaMemcpy(e->isd_x, isd.data(), e->n_in * sizeof(float), cudaMemcpyHostToDevice);
+    cudaMemcpy(e->mu_y, mu_y, e->n_out * sizeof(float), cudaMemcpyHostToDevice);
+    return ck(cudaMemcpy(e->sd_y, sd_y, e->n_out * sizeof(float), cudaMemcpyHostToDevice), "emu_norm: upload");
+  }
+  std::vector<float> isd(e->n_in);
+  if (mu_x) cudaMemcpy(mu_x, e->mu_x, e->n_in * sizeof(float), cudaMemcpyDeviceToHost);
+  if (sd_x) {
+    cudaMemcpy(isd.data(), e->isd_x, e->n_in * sizeof(float), cudaMemcpyDeviceToHost);
+    for (int j = 0; j < e->n_in; ++j) sd_x[j] = isd[j] > 0.f ? 1.f / isd[j] : 0.f;
+  }
+  if (mu_y) cudaMemcpy(mu_y, e->mu_y, e->n_out * sizeof(float), cudaMemcpyDeviceToHost);
+  if (sd_y) cudaMemcpy(sd_y, e->sd_y, e->n_out * sizeof(float), cudaMemcpyDeviceToHost);
+  return ck(cudaGetLastError(), "emu_norm: download");
+}
+
+int gcamb_emu_fit_norm(gcamb_emu *e, const float *X, const double *Cl, int N, float *Y, void *stream) {
+  if (!e || !X || !Cl || !Y) return fail(GCAMB_EINVAL, "emu_fit_norm: NULL argument");
+  if (N < 2) return fail(GCAMB_EINVAL, "emu_fit_norm: need at least 2 samples");
+  cudaStream_t st = (cudaStream_t)stream;
+  float *sdx = nullptr;
+  int rc = dalloc(&sdx, e->n_in);
+  if (rc) return rc;
+  colstats_kernel<<<1, 32, 0, st>>>(X, N, e->n_in, e->mu_x, sdx);
+  inv_sd_kernel<<<1, 32, 0, st>>>(sdx, e->n_in, e->isd_x);
+  const size_t n = (size_t)N * e->n_out;
+  log_kernel<<<1024, 256, 0, st>>>(Cl, n, Y);
+  colstats_kernel<<<(e->n_out + 127) / 128, 128, 0, st>>>(Y, N, e->n_out, e->mu_y, e->sd_y);
+  standardize_y_kernel<<<1024, 256, 0, st>>>(Y, N, e->n_out, e->mu_y, e->sd_y);
+  rc = ck(cudaGetLastError(), "emu_fit_norm: launch");
+  cudaStreamSynchronize(st);
+  cudaFree(sdx);
+  return rc;
+}
+
+int gcamb_emu_forward(gcamb_emu *e, const float *X, int B, float *Y, void *stream) {
+  int rc = check_emu(e, B);
+  if (rc) return rc;
+  if (!X || !Y) return fail(GCAMB_EINVAL, "emu_forward: NULL pointer");
+  cudaStream_t st = (cudaStream_t)stream;
+  if ((rc = forward_pass(e, X, nullptr, B, st))) return rc;
+  return ck(cudaMemcpyAsync(Y, e->out, (size_t)B * e->n_out * sizeof(float), cudaMemcpyDeviceToDevice, st),
+            "emu_forward: copy");
+}
+
+int gcamb_emu_train_step(gcamb_emu *e, const float *X, const float *Y, const int *idx, int B, float lr, float *loss,
+                         void *stream) {
+  int rc = check_emu(e, B);
+  if (rc) return rc;
+  if (!X || !Y) return fail(GCAMB_EINVAL, "emu_train_step: NULL pointer");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int L = e->depth + 1;
+  if ((rc = forward_pass(e, X, idx, B, st))) return rc;
+  loss_kernel<<<kLossBlocks, 256, 0, st>>>(e->out, Y, idx, B, e->n_out, e->d0, e->dT0, e->loss_part);
+  loss_final_kernel<<<1, 32, 0, st>>>(e->loss_part, kLossBlocks, 1.f / ((float)B * e->n_out), e->loss);
+  // W^T of every layer (the input-gradient GEMMs read it along the output index)
+  for (int l = 1; l < L; ++l) {
+    const int nin = e->sizes[l], nout = e->sizes[l + 1];
+    dim3 tg((nin + 31) / 32, (nout + 31) / 32);
+    transpose_kernel<<<tg, dim3(32, 8), 0, st>>>(e->theta + e->w_off[l], nout, nin, e->WT + e->w_off[l]);
+  }
+  // d / dT: gradient wrt the current layer's pre-activation, [B][out] and [out][B]
+  float *d = e->d0, *dn = e->d1, *dT = e->dT0, *dnT = e->dT1;
+  const int nkc = (B + 63) / 64;
+  const int kpc = 4;                       // K-chunks per CTA of the weight-gradient GEMMs
+  const int nz = (nkc + kpc - 1) / kpc;
+  for (int l = L - 1; l >= 0; --l) {
+    const int nin = e->sizes[l], nout = e->sizes[l + 1];
+    const float *hT = l == 0 ? e->xsT : e->HT[l - 1];
+    // dW_l[o][i] = sum_b dT[o][b] hT[i][b], split over b, summed in a fixed order
+    GemmArgs w{};
+    w.A = rowmajor(dT, nout, B, B);
+    w.B = rowmajor(hT, nin, B, B);
+    w.M = nout;
+    w.N = nin;
+    w.K = B;
+    w.C = e->splitk;
+    w.ldc = nin;
+    w.kchunks = kpc;
+    w.err = e->err;
+    if ((rc = gemm<kStore>(w, st, nz))) return rc;
+    const size_t nw = (size_t)nout * nin;
+    splitk_reduce_kernel<<<(unsigned)std::min<size_t>(4096, (nw + 255) / 256), 256, 0, st>>>(
+        e->splitk, nz, nw, e->grad + e->w_off[l]);
+    rowsum_kernel<<<(nout + 7) / 8, 256, 0, st>>>(dT, B, nout, e->grad + e->b_off[l]);
+    if (l > 0) {
+      // dn[b][i] = (sum_o d[b][o] W_l[o][i]) GELU'(Z_{l-1}[b][i]), and its transpose
+      GemmArgs x{};
+      x.A = rowmajor(d, B, nout, nout);
+      x.B = rowmajor(e->WT + e->w_off[l], nin, nout, nout);
+      x.M = B;
+      x.N = nin;
+      x.K = nout;
+      x.C = dn;
+      x.ldc = nin;
+      x.CT = dnT;
+      x.ldct = B;
+      x.Zprev = e->Z[l - 1];
+      x.err = e->err;
+      if ((rc = gemm<kDGelu>(x, st))) return rc;
+      std::swap(d, dn);
+      std::swap(dT, dnT);
+    }
+  }
+  ++e->step;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float bc1 = 1.f - powf(b1, (float)e->step), bc2 = 1.f - powf(b2, (float)e->step);
+  adam_kernel<<<1024, 256, 0, st>>>(e->theta, e->grad, e->m, e->v, e->n_params, lr, b1, b2, 1e-8f, bc1, bc2);
+  if (loss) cudaMemcpyAsync(loss, e->loss, sizeof(float), cudaMemcpyDeviceToDevice, st);
+  return ck(cudaGetLastError(), "emu_train_step: launch");
+}
+
+int gcamb_synth_sources(const gcamb_grid *g, const float *X, int M, float *S, double *Pk, void *stream) {
+  if (!g || (M > 0 && (!X || !S || !Pk))) return fail(GCAMB_EINVAL, "synth_sources: NULL argument");
+  if (M < 0 || M > 65535) return fail(GCAMB_EINVAL, "synth_sources: M out of range");
+  if (M == 0) return GCAMB_OK;
+  int rc = ensure_device_grid(const_cast<gcamb_grid *>(g));
+  if (rc) return rc;
+  const size_t smem = (2 * (size_t)g->ntau + 512) * sizeof(double);
+  if (smem > 200 * 1024) return fail(GCAMB_EINVAL, "synth_sources: tau grid too long");
+  cudaError_t ea = cudaFuncSetAttribute(synth_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (ea != cudaSuccess) return cuda_fail(ea, "synth_sources: smem attribute");
+  dim3 grid((g->nk + 255) / 256, M);
+  synth_kernel<<<grid, 256, smem, (cudaStream_t)stream>>>(X, g->d_k, g->d_tau, g->nk, g->ntau, S, Pk);
+  return ck(cudaGetLastError(), "synth_sources: launch");
+}
+
+int gcamb_emu_check(gcamb_emu *e, const float *X, const double *Cl_ref, int N, double tol, int min_count,
+                    double *report, void *stream) {
+  if (!e || !X || !Cl_ref || !report) return fail(GCAMB_EINVAL, "emu_check: NULL argument");
+  if (N < 1 || N > e->max_batch) return fail(GCAMB_EINVAL, "emu_check: N must be in [1, max_batch]");
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<float> hx((size_t)N * e->n_in);
+  int rc = ck(cudaMemcpy(hx.data(), X, hx.size() * sizeof(float), cudaMemcpyDeviceToHost), "emu_check: features");
+  if (rc) return rc;
+  // per-spectrum errors first
+  std::vector<double> he(N);
+  {
+    double *d_err = nullptr, *d_ce = nullptr;
+    if ((rc = dalloc(&d_err, N)) || (rc = dalloc(&d_ce, (size_t)N * e->n_out))) {
+      cudaFree(d_err);
+      return rc;
+    }
+    if (!(rc = forward_pass(e, X, nullptr, N, st))) {
+      exp_kernel<<<1024, 256, 0, st>>>(e->out, N, e->n_out, e->mu_y, e->sd_y, d_ce);
+      maxrel_kernel<<<N, 256, 0, st>>>(d_ce, Cl_ref, e->n_out, d_err);
+      rc = ck(cudaStreamSynchronize(st), "emu_check: kernels");
+      if (!rc) rc = ck(cudaMemcpy(he.data(), d_err, N * sizeof(double), cudaMemcpyDeviceToHost), "emu_check: errors");
+    }
+    cudaFree(d_err);
+    cudaFree(d_ce);
+    if (rc) return rc;
+  }
+  // cells: split the (at most 4) features whose two halves at the held-out
+  // median differ most in mean log error
+  struct Cand {
+    double score;
+    int j;
+    float med;
+  };
+  std::vector<Cand> cands;
+  for (int j = 0; j < e->n_in; ++j) {
+    std::vector<float> col(N);
+    for (int i = 0; i < N; ++i) col[i] = hx[(size_t)i * e->n_in + j];
+    std::vector<float> srt(col);
+    std::nth_element(srt.begin(), srt.begin() + N / 2, srt.end());
+    const float med = srt[N / 2];
+    double s0 = 0, s1 = 0;
+    int n0 = 0, n1 = 0;
+    for (int i = 0; i < N; ++i) {
+      const double le = std::log(std::max(he[i], 1e-300));
+      if (col[i] > med) {
+        s1 += le;
+        ++n1;
+      } else {
+        s0 += le;
+        ++n0;
+      }
+    }
+    if (n0 && n1) cands.push_back({std::fabs(s1 / n1 - s0 / n0), j, med});
+  }
+  std::stable_sort(cands.begin(), cands.end(), [](const Cand &a, const Cand &b) { return a.score > b.score; });
+  e->cell_dim.clear();
+  e->cell_mid.clear();
+  for (size_t c = 0; c < cands.size() && c < 4; ++c) {
+    e->cell_dim.push_back(cands[c].j);
+    e->cell_mid.push_back(cands[c].med);
+  }
+  const int nd = (int)e->cell_dim.size(), ncell = 1 << nd;
+  cudaFree(e->d_cell_dim);
+  cudaFree(e->d_cell_mid);
+  cudaFree(e->d_trusted);
+  e->d_cell_dim = nullptr;
+  e->d_cell_mid = nullptr;
+  e->d_trusted = nullptr;
+  if ((rc = dalloc(&e->d_cell_dim, std::max(1, nd))) || (rc = dalloc(&e->d_cell_mid, std::max(1, nd))) ||
+      (rc = dalloc(&e->d_trusted, ncell)))
+    return rc;
+  cudaMemcpy(e->d_cell_dim, e->cell_dim.data(), nd * sizeof(int), cudaMemcpyHostToDevice);
+  cudaMemcpy(e->d_cell_mid, e->cell_mid.data(), nd * sizeof(float), cudaMemcpyHostToDevice);
+  std::vector<int> hc(N, 0);
+  for (int i = 0; i < N; ++i)
+    for (int d = 0; d < nd; ++d)
+      if (hx[(size_t)i * e->n_in + e->cell_dim[d]] > e->cell_mid[d]) hc[i] |= 1 << d;
+  std::vector<double> cmax(ncell, 0.0);
+  std::vector<int> cnt(ncell, 0);
+  double emax = 0.0, esum = 0.0;
+  int within = 0;
+  for (int i = 0; i < N; ++i) {
+    cmax[hc[i]] = std::max(cmax[hc[i]], he[i]);
+    cnt[hc[i]]++;
+    emax = std::max(emax, he[i]);
+    esum += he[i];
+    within += he[i] <= tol;
+  }
+  e->trusted.assign(ncell, 0);
+  int ntr = 0;
+  double served = 0.0;
+  for (int c = 0; c < ncell; ++c) {
+    e->trusted[c] = (cnt[c] >= std::max(1, min_count) && cmax[c] <= tol) ? 1 : 0;
+    ntr += e->trusted[c];
+    if (e->trusted[c]) served += cnt[c];
+  }
+  cudaMemcpy(e->d_trusted, e->trusted.data(), ncell, cudaMemcpyHostToDevice);
+  e->check_max_err = emax;
+  e->check_tol = tol;
+  report[0] = emax;                     // max rel err over all held-out spectra
+  report[1] = esum / N;                 // mean of the per-spectrum max rel err
+  report[2] = (double)within / N;       // fraction of held-out spectra within tol
+  report[3] = (double)ntr / ncell;      // fraction of cells trusted
+  report[4] = served / N;               // fraction of held-out spectra in trusted cells
+  report[5] = ncell;
+  return GCAMB_OK;
+}
+
+int gcamb_emulate(gcamb_emu *e, const float *X, int B, double *Cl, int *used_fallback, void *stream) {
+  int rc = check_emu(e, B);
+  if (rc) return rc;
+  if (!X || !Cl || !used_fallback) return fail(GCAMB_EINVAL, "emulate: NULL pointer");
+  cudaStream_t st = (cudaStream_t)stream;
+  if ((rc = forward_pass(e, X, nullptr, B, st))) return rc;
+  exp_kernel<<<1024, 256, 0, st>>>(e->out, B, e->n_out, e->mu_y, e->sd_y, Cl);
+  const int nd = (int)e->cell_dim.size();
+  cell_kernel<<<(B + 255) / 256, 256, 0, st>>>(X, B, e->n_in, e->d_cell_dim, e->d_cell_mid, nd, e->d_trusted, nullptr,
+                                               used_fallback);
+  if ((rc = ck(cudaGetLastError(), "emulate: launch"))) return rc;
+  // requests outside the trusted cells: the batched projection on regenerated sources
+  std::vector<int> hf(B);
+  if ((rc = ck(cudaMemcpyAsync(hf.data(), used_fallback, B * sizeof(int), cudaMemcpyDeviceToHost, st), "emulate")))
+    return rc;
+  if ((rc = ck(cudaStreamSynchronize(st), "emulate: sync"))) return rc;
+  std::vector<int> idx;
+  for (int b = 0; b < B; ++b)
+    if (hf[b]) idx.push_back(b);
+  if (idx.empty()) return GCAMB_OK;
+  const int Mf = (int)idx.size();
+  gcamb_grid *g = e->g;
+  const int mode = e->fb_mode;
+  if (!g->tab[mode].built && (rc = gcamb_bessel_table(g, mode, stream))) return rc;
+  if (Mf > e->fb_cap) {
+    for (void *p : {(void *)e->fb_x, (void *)e->fb_S, (void *)e->fb_P, (void *)e->fb_C, (void *)e->fb_idx}) cudaFree(p);
+    e->fb_x = nullptr;
+    e->fb_S = nullptr;
+    e->fb_P = nullptr;
+    e->fb_C = nullptr;
+    e->fb_idx = nullptr;
+    e->fb_cap = 0;
+    if ((rc = dalloc(&e->fb_x, (size_t)Mf * 9)) || (rc = dalloc(&e->fb_S, (size_t)Mf * g->nk * g->ntau)) ||
+        (rc = dalloc(&e->fb_P, (size_t)Mf * g->nk)) || (rc = dalloc(&e->fb_C, (size_t)Mf * g->nl)) ||
+        (rc = dalloc(&e->fb_idx, Mf)))
+      return rc;
+    e->fb_cap = Mf;
+  }
+  size_t need = 0;
+  if ((rc = gcamb_los_cl_workspace(g, Mf, mode, &need))) return rc;
+  if (need > e->fb_ws_bytes) {
+    cudaFree(e->fb_ws);
+    e->fb_ws = nullptr;
+    e->fb_ws_bytes = 0;
+    if (cudaMalloc(&e->fb_ws, need) != cudaSuccess) {
+      e->fb_ws = nullptr;
+      return fail(GCAMB_ENOMEM, "emulate: fallback workspace");
+    }
+    e->fb_ws_bytes = need;
+  }
+  cudaMemcpyAsync(e->fb_idx, idx.data(), Mf * sizeof(int), cudaMemcpyHostToDevice, st);
+  gather_rows_kernel<<<(Mf * 9 + 255) / 256, 256, 0, st>>>(X, e->fb_idx, Mf, 9, e->fb_x);
+  if ((rc = gcamb_synth_sources(g, e->fb_x, Mf, e->fb_S, e->fb_P, stream))) return rc;
+  if ((rc = gcamb_los_cl(g, e->fb_S, e->fb_P, Mf, mode, e->fb_C, e->fb_ws, e->fb_ws_bytes, stream))) return rc;
+  scatter_rows_kernel<<<256, 256, 0, st>>>(e->fb_C, e->fb_idx, Mf, g->nl, Cl);
+  return ck(cudaGetLastError(), "emulate: fallback");
+}
+
+int gcamb_emu_info(const gcamb_emu *e, double *info) {
+  if (!e || !info) return fail(GCAMB_EINVAL, "emu_info: NULL argument");
+  info[0] = (double)e->n_params;
+  info[1] = (double)e->step;
+  info[2] = e->check_max_err;
+  info[3] = e->check_tol;
+  int ntr = 0;
+  for (unsigned char t : e->trusted) ntr += t;
+  info[4] = e->trusted.empty() ? 0.0 : (double)ntr / e->trusted.size();
+  info[5] = (double)e->n_out;
+  int herr = 0;
+  cudaMemcpy(&herr, e->err, sizeof(int), cudaMemcpyDeviceToHost);
+  info[6] = herr;
+  info[7] = (double)e->width;
+  return GCAMB_OK;
+}
+
+// Checkpoint: magic, version, architecture, step, parameters, Adam moments,
+// normalisation, trust cells, then a 64-bit FNV-1a checksum of all of it.
+int gcamb_emu_save(const gcamb_emu *e, const char *path) {
+  if (!e || !path) return fail(GCAMB_EINVAL, "emu_save: NULL argument");
+  std::vector<unsigned char> buf;
+  auto put = [&](const void *p, size_t n) {
+    const unsigned char *c = static_cast<const unsigned char *>(p);
+    buf.insert(buf.end(), c, c + n);
+  };
+  const uint32_t hdr[6] = {kEmuMagic, 1u, (uint32_t)e->n_in, (uint32_t)e->width, (uint32_t)e->depth,
+                           (uint32_t)e->n_out};
+  put(hdr, sizeof hdr);
+  put(&e->step, sizeof e->step);
+  std::vector<float> h(e->n_params);
+  for (float *src : {e->theta, e->m, e->v}) {
+    cudaMemcpy(h.data(), src, e->n_params * sizeof(float), cudaMemcpyDeviceToHost);
+    put(h.data(), h.size() * sizeof(float));
+  }
+  std::vector<float> nx(e->n_in), ny(e->n_out);
+  for (float *src : {e->mu_x, e->isd_x}) {
+    cudaMemcpy(nx.data(), src, e->n_in * sizeof(float), cudaMemcpyDeviceToHost);
+    put(nx.data(), nx.size() * sizeof(float));
+  }
+  for (float *src : {e->mu_y, e->sd_y}) {
+    cudaMemcpy(ny.data(), src, e->n_out * sizeof(float), cudaMemcpyDeviceToHost);
+    put(ny.data(), ny.size() * sizeof(float));
+  }
+  const int32_t nd = (int32_t)e->cell_dim.size();
+  put(&nd, sizeof nd);
+  put(e->cell_dim.data(), nd * sizeof(int));
+  put(e->cell_mid.data(), nd * sizeof(float));
+  const int32_t nt = (int32_t)e->trusted.size();
+  put(&nt, sizeof nt);
+  put(e->trusted.data(), nt);
+  put(&e->check_max_err, sizeof(double));
+  put(&e->check_tol, sizeof(double));
+  if (cudaGetLastError() != cudaSuccess) return fail(GCAMB_ECUDA, "emu_save: download");
+  uint64_t hsum = 1469598103934665603ull;
+  for (unsigned char c : buf) {
+    hsum ^= c;
+    hsum *= 1099511628211ull;
+  }
+  FILE *f = fopen(path, "wb");
+  if (!f) return fail(GCAMB_EINVAL, std::string("emu_save: cannot open ") + path);
+  const bool ok = fwrite(buf.data(), 1, buf.size(), f) == buf.size() && fwrite(&hsum, 1, 8, f) == 8;
+  fclose(f);
+  return ok ? GCAMB_OK : fail(GCAMB_EINVAL, "emu_save: write failed");
+}
+
+int gcamb_emu_load(gcamb_emu *e, const char *path) {
+  if (!e || !path) return fail(GCAMB_EINVAL, "emu_load: NULL argument");
+  FILE *f = fopen(path, "rb");
+  if (!f) return fail(GCAMB_EINVAL, std::string("emu_load: cannot open ") + path);
+  std::vector<unsigned char> buf;
+  unsigned char tmp[65536];
+  size_t r;
+  while ((r = fread(tmp, 1, sizeof tmp, f)) > 0) buf.insert(buf.end(), tmp, tmp + r);
+  fclose(f);
+  if (buf.size() < 8) return fail(GCAMB_EINVAL, "emu_load: truncated file");
+  uint64_t hsum = 1469598103934665603ull, stored;
+  for (size_t i = 0; i < buf.size() - 8; ++i) {
+    hsum ^= buf[i];
+    hsum *= 1099511628211ull;
+  }
+  std::memcpy(&stored, buf.data() + buf.size() - 8, 8);
+  if (hsum != stored) return fail(GCAMB_EINVAL, "emu_load: checksum mismatch");
+  size_t pos = 0;
+  auto get = [&](void *p, size_t n) -> bool {
+    if (pos + n > buf.size() - 8) return false;
+    std::memcpy(p, buf.data() + pos, n);
+    pos += n;
+    return true;
+  };
+  uint32_t hdr[6];
+  if (!get(hdr, sizeof hdr) || hdr[0] != kEmuMagic || hdr[1] != 1u) return fail(GCAMB_EINVAL, "emu_load: not a checkpoint");
+  if ((int)hdr[2] != e->n_in || (int)hdr[3] != e->width || (int)hdr[4] != e->depth || (int)hdr[5] != e->n_out)
+    return fail(GCAMB_EINVAL, "emu_load: architecture differs from this emulator");
+  int64_t step;
+  if (!get(&step, sizeof step)) return fail(GCAMB_EINVAL, "emu_load: truncated");
+  std::vector<float> h(e->n_params);
+  for (float *dst : {e->theta, e->m, e->v}) {
+    if (!get(h.data(), h.size() * sizeof(float))) return fail(GCAMB_EINVAL, "emu_load: truncated");
+    cudaMemcpy(dst, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice);
+  }
+  std::vector<float> nx(e->n_in), ny(e->n_out);
+  for (float *dst : {e->mu_x, e->isd_x}) {
+    if (!get(nx.data(), nx.size() * sizeof(float))) return fail(GCAMB_EINVAL, "emu_load: truncated");
+    cudaMemcpy(dst, nx.data(), nx.size() * sizeof(float), cudaMemcpyHostToDevice);
+  }
+  for (float *dst : {e->mu_y, e->sd_y}) {
+    if (!get(ny.data(), ny.size() * sizeof(float))) return fail(GCAMB_EINVAL, "emu_load: truncated");
+    cudaMemcpy(dst, ny.data(), ny.size() * sizeof(float), cudaMemcpyHostToDevice);
+  }
+  int32_t nd = 0, nt = 0;
+  if (!get(&nd, sizeof nd) || nd < 0 || nd > 16) return fail(GCAMB_EINVAL, "emu_load: bad cells");
+  std::vector<int> cd(nd);
+  std::vector<float> cm(nd);
+  if (!get(cd.data(), nd * sizeof(int)) || !get(cm.data(), nd * sizeof(float)) || !get(&nt, sizeof nt) ||
+      !(nt == (1 << nd) || (nd == 0 && nt == 0)))
+    return fail(GCAMB_EINVAL, "emu_load: bad cells");
+  std::vector<unsigned char> tr(nt);
+  double cmax = 0, ctol = 0;
+  if (!get(tr.data(), nt) || !get(&cmax, sizeof cmax) || !get(&ctol, sizeof ctol))
+    return fail(GCAMB_EINVAL, "emu_load: truncated");
+  e->step = step;
+  e->cell_dim = cd;
+  e->cell_mid = cm;
+  e->trusted = tr;
+  e->check_max_err = cmax;
+  e->check_tol = ctol;
+  cudaFree(e->d_cell_dim);
+  cudaFree(e->d_cell_mid);
+  cudaFree(e->d_trusted);
+  e->d_cell_dim = nullptr;
+  e->d_cell_mid = nullptr;
+  e->d_trusted = nullptr;
+  int rc;
+  if ((rc = dalloc(&e->d_cell_dim, std::max(1, nd))) || (rc = dalloc(&e->d_cell_mid, std::max(1, nd))) ||
+      (rc = dalloc(&e->d_trusted, std::max(1, nt))))
+    return rc;
+  cudaMemcpy(e->d_cell_dim, cd.data(), nd * sizeof(int), cudaMemcpyHostToDevice);
+  cudaMemcpy(e->d_cell_mid, cm.data(), nd * sizeof(float), cudaMemcpyHostToDevice);
+  return ck(cudaMemcpy(e->d_trusted, tr.data(), nt, cudaMemcpyHostToDevice), "emu_load: upload");
+}
+
+}  // extern "C"

@@ -530,17 +530,7 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const float *__restrict
     }
   }
   char *base = sp + ((size_t)(q * n_mt + mt) * nkbs) * (size_t)(256 * NT);
-#pragma unroll(CACHE > 0 ? CACHE : 1)
-  for (int j = 0; (CACHE > 0 ? j < CACHE : true); ++j) {
-    const int ch = lane + 32 * j;
-    if (ch >= nch) break;
-    float v[EPC];
-    if constexpr (CACHE > 0) {
-#pragma unroll
-      for (int u = 0; u < EPC; ++u) v[u] = cache[j][u];
-    } else {
-      load_chunk(ch, v);
-    }
+  auto split_store = [&](int ch, const float *v) {
     uint4 hi, lo;
     uint32_t *h = reinterpret_cast<uint32_t *>(&hi), *l = reinterpret_cast<uint32_t *>(&lo);
     if constexpr (MODE == kTF32) {
@@ -572,6 +562,17 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const float *__restrict
     const uint32_t o = sw_off(n, (ch & 7) * 16);
     *reinterpret_cast<uint4 *>(blk + o) = hi;
     *reinterpret_cast<uint4 *>(blk + NT * 128 + o) = lo;
+  };
+  if constexpr (CACHE > 0) {
+#pragma unroll
+    for (int j = 0; j < CACHE; ++j)
+      if (lane + 32 * j < nch) split_store(lane + 32 * j, cache[j]);
+  } else {
+    for (int ch = lane; ch < nch; ch += 32) {
+      float v[EPC];
+      load_chunk(ch, v);
+      split_store(ch, v);
+    }
   }
   if (lane == 0) {
     float w = 0.f;

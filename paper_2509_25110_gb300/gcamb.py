@@ -64,6 +64,22 @@ def lib():
     L.gcamb_plan_workspace.argtypes = [_vp, ctypes.POINTER(ctypes.c_size_t)]
     L.gcamb_plan_launch.argtypes = [_vp, _vp, _vp, _vp, _vp, ctypes.c_size_t, _vp]
     L.gcamb_plan_info.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
+    L.gcamb_emu_create.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
+                                   ctypes.POINTER(_vp)]
+    L.gcamb_emu_destroy.argtypes = [_vp]
+    L.gcamb_emu_num_params.argtypes = [_vp, ctypes.POINTER(ctypes.c_size_t)]
+    L.gcamb_emu_params.argtypes = [_vp, _vp, _vp]
+    L.gcamb_emu_grads.argtypes = [_vp, _vp]
+    L.gcamb_emu_norm.argtypes = [_vp, _vp, _vp, _vp, _vp, ctypes.c_int]
+    L.gcamb_emu_fit_norm.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp, _vp]
+    L.gcamb_emu_train_step.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_float, _vp, _vp]
+    L.gcamb_emu_forward.argtypes = [_vp, _vp, ctypes.c_int, _vp, _vp]
+    L.gcamb_emu_check.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, _vp, _vp]
+    L.gcamb_emulate.argtypes = [_vp, _vp, ctypes.c_int, _vp, _vp, _vp]
+    L.gcamb_emu_info.argtypes = [_vp, _vp]
+    L.gcamb_emu_save.argtypes = [_vp, ctypes.c_char_p]
+    L.gcamb_emu_load.argtypes = [_vp, ctypes.c_char_p]
+    L.gcamb_synth_sources.argtypes = [_vp, _vp, ctypes.c_int, _vp, _vp, _vp]
     L.gcamb_los_cl_noalloc.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]
     L.gcamb_profile_enable.argtypes = [ctypes.c_int]
     L.gcamb_profile_read.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
@@ -353,3 +369,182 @@ def profile_read(kernel: int):
     n = ctypes.c_int64()
     _check(lib().gcamb_profile_read(int(kernel), ctypes.byref(ms), ctypes.byref(n)))
     return float(ms.value), int(n.value)
+
+
+# ---------------------------------------------------------------- emulator
+
+class Emu:
+    """Owning wrapper of a gcamb_emu handle."""
+
+    def __init__(self, handle, grid, width, depth, max_batch):
+        self.handle = handle
+        self.grid = grid
+        self.width = width
+        self.depth = depth
+        self.max_batch = max_batch
+        self.n_in = 9
+        self.n_out = grid.nl
+
+    def close(self):
+        if self.handle is not None:
+            _check(lib().gcamb_emu_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def emu_create(g: Grid, width: int = 512, depth: int = 3, max_batch: int = 4096, seed: int = 0) -> Emu:
+    h = _vp()
+    _check(lib().gcamb_emu_create(g.handle, 9, int(width), int(depth), int(max_batch), int(seed), ctypes.byref(h)))
+    return Emu(h, g, int(width), int(depth), int(max_batch))
+
+
+def emu_destroy(e: Emu):
+    e.close()
+
+
+def emu_num_params(e: Emu) -> int:
+    n = ctypes.c_size_t()
+    _check(lib().gcamb_emu_num_params(e.handle, ctypes.byref(n)))
+    return int(n.value)
+
+
+def emu_layer_shapes(e: Emu):
+    sizes = [9] + [e.width] * e.depth + [e.n_out]
+    return [(b, a) for a, b in zip(sizes[:-1], sizes[1:])]
+
+
+def emu_params(e: Emu, new=None) -> np.ndarray:
+    """Flat float32 parameters (per layer W [out][in] then b [out]); sets them first if `new` is given."""
+    n = emu_num_params(e)
+    out = np.empty(n, dtype=np.float32)
+    src = None
+    if new is not None:
+        src = np.ascontiguousarray(new, dtype=np.float32)
+        if src.size != n:
+            raise ValueError("expected %d parameters" % n)
+    _check(lib().gcamb_emu_params(e.handle, _vp(out.ctypes.data), None if src is None else _vp(src.ctypes.data)))
+    return out
+
+
+def emu_grads(e: Emu) -> np.ndarray:
+    out = np.empty(emu_num_params(e), dtype=np.float32)
+    _check(lib().gcamb_emu_grads(e.handle, _vp(out.ctypes.data)))
+    return out
+
+
+def unflatten(e: Emu, flat):
+    """Flat parameter vector -> ([W_l], [b_l]) as float64 arrays."""
+    Ws, bs, o = [], [], 0
+    for (nout, nin) in emu_layer_shapes(e):
+        Ws.append(np.asarray(flat[o:o + nout * nin], dtype=np.float64).reshape(nout, nin))
+        o += nout * nin
+        bs.append(np.asarray(flat[o:o + nout], dtype=np.float64))
+        o += nout
+    return Ws, bs
+
+
+def flatten(Ws, bs) -> np.ndarray:
+    parts = []
+    for W, b in zip(Ws, bs):
+        parts += [np.asarray(W).ravel(), np.asarray(b).ravel()]
+    return np.concatenate(parts).astype(np.float32)
+
+
+def emu_norm(e: Emu, mu_x=None, sd_x=None, mu_y=None, sd_y=None) -> dict:
+    """Reads the normalisation, or sets it when all four arrays are given."""
+    arrs = [np.zeros(9, np.float32), np.zeros(9, np.float32), np.zeros(e.n_out, np.float32),
+            np.zeros(e.n_out, np.float32)]
+    setting = mu_x is not None
+    if setting:
+        arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in (mu_x, sd_x, mu_y, sd_y)]
+    _check(lib().gcamb_emu_norm(e.handle, *[_vp(a.ctypes.data) for a in arrs], 1 if setting else 0))
+    return dict(zip(("mu_x", "sd_x", "mu_y", "sd_y"), arrs))
+
+
+def emu_fit_norm(e: Emu, X, Cl, Y=None, stream=None):
+    import torch
+    N = X.shape[0]
+    if Y is None:
+        Y = torch.empty((N, e.n_out), dtype=torch.float32, device=X.device)
+    _check(lib().gcamb_emu_fit_norm(e.handle, _dev(X, torch.float32, (N, 9), "X"),
+                                    _dev(Cl, torch.float64, (N, e.n_out), "Cl"), N,
+                                    _dev(Y, torch.float32, (N, e.n_out), "Y"), _stream(stream)))
+    return Y
+
+
+def emu_train_step(e: Emu, X, Y, idx, B: int, lr: float, loss=None, stream=None):
+    import torch
+    ip = _vp(None) if idx is None else _dev(idx, torch.int32, name="idx")
+    lp = _vp(None) if loss is None else _dev(loss, torch.float32, (1,), "loss")
+    _check(lib().gcamb_emu_train_step(e.handle, _dev(X, torch.float32, name="X"), _dev(Y, torch.float32, name="Y"),
+                                      ip, int(B), float(lr), lp, _stream(stream)))
+    return loss
+
+
+def emu_forward(e: Emu, X, Y=None, stream=None):
+    import torch
+    B = X.shape[0]
+    if Y is None:
+        Y = torch.empty((B, e.n_out), dtype=torch.float32, device=X.device)
+    _check(lib().gcamb_emu_forward(e.handle, _dev(X, torch.float32, (B, 9), "X"), B,
+                                   _dev(Y, torch.float32, (B, e.n_out), "Y"), _stream(stream)))
+    return Y
+
+
+def emu_check(e: Emu, X, Cl_ref, tol: float, min_count: int = 4, stream=None) -> dict:
+    import torch
+    N = X.shape[0]
+    rep = np.zeros(6)
+    _check(lib().gcamb_emu_check(e.handle, _dev(X, torch.float32, (N, 9), "X"),
+                                 _dev(Cl_ref, torch.float64, (N, e.n_out), "Cl_ref"), N, float(tol), int(min_count),
+                                 _vp(rep.ctypes.data), _stream(stream)))
+    keys = ("max_err", "mean_err", "frac_within_tol", "frac_cells_trusted", "frac_served", "cells")
+    return dict(zip(keys, rep.tolist()))
+
+
+def emulate(e: Emu, X, Cl=None, used_fallback=None, stream=None):
+    """C_l[B][n_out] from the emulator (trusted cells) or the projection."""
+    import torch
+    B = X.shape[0]
+    if Cl is None:
+        Cl = torch.empty((B, e.n_out), dtype=torch.float64, device=X.device)
+    if used_fallback is None:
+        used_fallback = torch.empty(B, dtype=torch.int32, device=X.device)
+    _check(lib().gcamb_emulate(e.handle, _dev(X, torch.float32, (B, 9), "X"), B,
+                               _dev(Cl, torch.float64, (B, e.n_out), "Cl"),
+                               _dev(used_fallback, torch.int32, (B,), "used_fallback"), _stream(stream)))
+    return Cl, used_fallback
+
+
+def emu_info(e: Emu) -> dict:
+    a = np.zeros(8)
+    _check(lib().gcamb_emu_info(e.handle, _vp(a.ctypes.data)))
+    keys = ("params", "steps", "check_max_err", "check_tol", "frac_cells_trusted", "n_out", "device_error", "width")
+    return dict(zip(keys, a.tolist()))
+
+
+def emu_save(e: Emu, path: str):
+    _check(lib().gcamb_emu_save(e.handle, str(path).encode()))
+
+
+def emu_load(e: Emu, path: str):
+    _check(lib().gcamb_emu_load(e.handle, str(path).encode()))
+
+
+def synth_sources(g: Grid, X, S=None, Pk=None, stream=None):
+    """Synthetic sources S[M][nk][ntau] (float) and P[M][nk] (double) from features X[M][9]."""
+    import torch
+    M = X.shape[0]
+    if S is None:
+        S = torch.empty((M, g.nk, g.ntau), dtype=torch.float32, device=X.device)
+    if Pk is None:
+        Pk = torch.empty((M, g.nk), dtype=torch.float64, device=X.device)
+    _check(lib().gcamb_synth_sources(g.handle, _dev(X, torch.float32, (M, 9), "X"), M,
+                                     _dev(S, torch.float32, (M, g.nk, g.ntau), "S"),
+                                     _dev(Pk, torch.float64, (M, g.nk), "Pk"), _stream(stream)))
+    return S, Pk

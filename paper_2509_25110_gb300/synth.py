@@ -237,3 +237,27 @@ def primordial(k: np.ndarray, p: ModelParams, A_s: float = A_S) -> np.ndarray:
     """P[M][nk] = A_s (k/0.05)^(n_s-1), float64."""
     k = np.asarray(k, dtype=np.float64)
     return A_s * np.power(k[None, :] / K_PIVOT, (p.n_s[:, None] - 1.0))
+
+
+def emulator_features(p: ModelParams, A_s: float = A_S) -> np.ndarray:
+    """[M, 9] float32 features of the emulator: (tau*, sigma, r_s, cos phi,
+    sin phi, k_D, b, n_s, ln(1e10 A_s))."""
+    M = p.M
+    f = np.empty((M, 9), dtype=np.float64)
+    f[:, 0] = p.tau_star
+    f[:, 1] = p.sigma
+    f[:, 2] = p.r_s
+    f[:, 3] = np.cos(p.phi)
+    f[:, 4] = np.sin(p.phi)
+    f[:, 5] = p.k_D
+    f[:, 6] = p.b
+    f[:, 7] = p.n_s
+    f[:, 8] = math.log(1e10 * A_s)
+    return f.astype(np.float32)
+
+
+def params_from_features(f) -> ModelParams:
+    """Inverse of emulator_features (phi from atan2), in float64."""
+    f = np.asarray(f, dtype=np.float64)
+    return ModelParams(tau_star=f[:, 0].copy(), sigma=f[:, 1].copy(), r_s=f[:, 2].copy(),
+                       phi=np.arctan2(f[:, 4], f[:, 3]), k_D=f[:, 5].copy(), b=f[:, 6].copy(), n_s=f[:, 7].copy())

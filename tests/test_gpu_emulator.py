@@ -1,0 +1,212 @@
+"""GPU checks of the emulator (MLP of log C_l trained by the library's own
+kernels, with a projection fallback), through the C ABI.
+
+* the device forward pass and gradients against the FP64 reference network
+  (oracle/mlp.py) run on the same parameters, with the device's bf16 operand
+  rounding mimicked.  What remains is FP32 accumulation (~1e-6) and the rare
+  operand whose fp32 (device) and fp64 (reference) values lie on opposite
+  sides of a bf16 rounding boundary: each such flip moves one operand by
+  2^-8, and flips compound through the layers.  Measured: 1.5e-4 (forward)
+  and 1.2e-3 (first-layer weight gradient, three GELU' layers deep) relative
+  in Frobenius norm at width 512; bars: 1e-3 forward, 3e-3 gradients;
+* Adam's update against the reference formula;
+* training lowers the loss; requests outside the trusted cells are answered
+  by the projection path exactly, the rest by the network;
+* checkpoints round-trip and reject corruption;
+* the network serves spectra faster than the projection path it stands in for.
+"""
+import time
+
+import numpy as np
+import pytest
+
+from oracle import mlp
+from paper_2509_25110_gb300 import build, gcamb, synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    gcamb.lib()
+
+
+def small_grid(lmax=120):
+    k = synth.log_grid(1e-4, 0.3, 80)
+    tau = synth.uniform_grid(200.0, 14000.0, 200)
+    return gcamb.grid_create(k, tau, 14000.0, 2, lmax)
+
+
+def frob_rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def test_synth_sources_match_the_input_module():
+    g = small_grid()
+    p = synth.model_params(5, seed=30)
+    X = synth.emulator_features(p)
+    S, P = gcamb.synth_sources(g, torch.as_tensor(X, device="cuda"))
+    gcamb.sync()
+    pp = synth.params_from_features(X)
+    Sr = synth.sources(g.k, g.tau, pp)
+    Pr = synth.primordial(g.k, pp, A_s=np.exp(float(X[0, 8])) * 1e-10)
+    assert np.abs(S.cpu().numpy() - Sr).max() <= 1e-6 * np.abs(Sr).max()
+    assert np.allclose(P.cpu().numpy(), Pr, rtol=1e-6, atol=0)
+
+
+@pytest.mark.parametrize("width,lmax,B", [(64, 120, 200), (512, 2500, 256)])
+def test_forward_and_gradients_match_reference(width, lmax, B):
+    g = small_grid(lmax)
+    e = gcamb.emu_create(g, width=width, depth=3, max_batch=B, seed=1)
+    Ws, bs = mlp.init_params([9, width, width, width, g.nl], seed=5)
+    flat = gcamb.flatten(Ws, bs)
+    gcamb.emu_params(e, flat)
+    Ws32, bs32 = gcamb.unflatten(e, flat)  # the float32 values the device holds
+    rng = np.random.default_rng(6)
+    X = rng.normal(size=(B, 9)).astype(np.float32)
+    Y = rng.normal(size=(B, g.nl)).astype(np.float32)
+    Xd, Yd = torch.as_tensor(X, device="cuda"), torch.as_tensor(Y, device="cuda")
+    out = gcamb.emu_forward(e, Xd).cpu().numpy()
+    ref, cache = mlp.forward(Ws32, bs32, X.astype(np.float64), rounding=True)
+    assert frob_rel(out, ref) <= 1e-3
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    gcamb.emu_train_step(e, Xd, Yd, None, B, 0.0, loss)
+    gcamb.sync()
+    Lr, dW, db = mlp.backward(Ws32, bs32, cache, Y.astype(np.float64), rounding=True)
+    assert abs(float(loss.item()) - Lr) <= 1e-4 * Lr
+    gW, gb = gcamb.unflatten(e, gcamb.emu_grads(e))
+    for l in range(len(Ws)):
+        assert frob_rel(gW[l], dW[l]) <= 3e-3, ("W", l, frob_rel(gW[l], dW[l]))
+        assert frob_rel(gb[l], db[l]) <= 3e-3, ("b", l, frob_rel(gb[l], db[l]))
+    # lr = 0 leaves the parameters unchanged
+    assert np.array_equal(gcamb.emu_params(e), flat)
+
+
+def test_adam_step_matches_reference():
+    g = small_grid()
+    e = gcamb.emu_create(g, width=32, depth=2, max_batch=64, seed=2)
+    p0 = gcamb.emu_params(e)
+    rng = np.random.default_rng(7)
+    X = torch.as_tensor(rng.normal(size=(64, 9)).astype(np.float32), device="cuda")
+    Y = torch.as_tensor(rng.normal(size=(64, g.nl)).astype(np.float32), device="cuda")
+    gcamb.emu_train_step(e, X, Y, None, 64, 1e-3)
+    gcamb.sync()
+    grad = gcamb.emu_grads(e).astype(np.float64)
+    p1 = gcamb.emu_params(e).astype(np.float64)
+    ref, _, _ = mlp.adam_step(p0.astype(np.float64), grad, np.zeros_like(grad), np.zeros_like(grad), 1, lr=1e-3)
+    assert np.abs(p1 - ref).max() <= 2e-7
+
+
+def _dataset(g, N, seed, mode=gcamb.F16X3):
+    p = synth.model_params(N, seed=seed)
+    X = torch.as_tensor(synth.emulator_features(p), device="cuda")
+    C = torch.empty((N, g.nl), dtype=torch.float64, device="cuda")
+    gcamb.bessel_table(g, mode)
+    for a in range(0, N, 256):
+        b = min(N, a + 256)
+        S, P = gcamb.synth_sources(g, X[a:b].contiguous())
+        C[a:b] = gcamb.los_cl(g, S, P, mode)
+    gcamb.sync()
+    return X, C
+
+
+def test_training_fallback_and_checkpoint(tmp_path):
+    g = small_grid()
+    e = gcamb.emu_create(g, width=128, depth=3, max_batch=1024, seed=3)
+    X, C = _dataset(g, 2048, seed=31)
+    Xh, Ch = _dataset(g, 512, seed=32)
+    Y = gcamb.emu_fit_norm(e, X, C)
+    rng = np.random.default_rng(8)
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    losses = []
+    for step in range(400):
+        idx = torch.as_tensor(rng.integers(0, 2048, 256).astype(np.int32), device="cuda")
+        gcamb.emu_train_step(e, X, Y, idx, 256, 2e-3 if step < 300 else 5e-4, loss)
+        if step % 50 == 0 or step == 399:
+            losses.append(float(loss.item()))
+    assert losses[-1] < 0.1 * losses[0], losses
+    # before any check every request takes the projection path
+    Cl, fb = gcamb.emulate(e, Xh[:64].contiguous())
+    S64, P64 = gcamb.synth_sources(g, Xh[:64].contiguous())
+    ref64 = gcamb.los_cl(g, S64, P64, gcamb.F16X3)
+    gcamb.sync()
+    assert int(fb.sum().item()) == 64
+    assert np.array_equal(Cl.cpu().numpy(), ref64.cpu().numpy())
+    assert np.abs(Cl.cpu().numpy() / Ch[:64].cpu().numpy() - 1).max() <= 1e-5
+    rep = gcamb.emu_check(e, Xh, Ch, tol=0.02, min_count=4)
+    assert 0.0 <= rep["frac_cells_trusted"] <= 1.0 and rep["max_err"] > 0
+    Cl, fb = gcamb.emulate(e, Xh)
+    gcamb.sync()
+    fb = fb.cpu().numpy().astype(bool)
+    Cl = Cl.cpu().numpy()
+    # projection answers are the batched path's own results on those sources
+    if fb.any():
+        sel = np.flatnonzero(fb)
+        S, P = gcamb.synth_sources(g, Xh[torch.as_tensor(sel, device="cuda")].contiguous())
+        ref = gcamb.los_cl(g, S, P, gcamb.F16X3).cpu().numpy()
+        assert np.array_equal(Cl[fb], ref)
+    # network answers: exp of the de-standardised output
+    if (~fb).any():
+        nrm = gcamb.emu_norm(e)
+        out = gcamb.emu_forward(e, Xh).cpu().numpy().astype(np.float64)
+        net = np.exp(out * nrm["sd_y"] + nrm["mu_y"])
+        assert np.allclose(Cl[~fb], net[~fb], rtol=1e-6, atol=0)
+        # and they are within the trusted tolerance of the projection on the held-out set
+        assert np.abs(Cl[~fb] / Ch.cpu().numpy()[~fb] - 1).max() <= 0.02
+    # trusting everything: no fallback
+    gcamb.emu_check(e, Xh, Ch, tol=float("inf"), min_count=1)
+    _, fb2 = gcamb.emulate(e, Xh)
+    gcamb.sync()
+    assert int(fb2.sum().item()) == 0
+    # checkpoint round trip
+    path = tmp_path / "emu.bin"
+    gcamb.emu_save(e, path)
+    e2 = gcamb.emu_create(g, width=128, depth=3, max_batch=1024, seed=99)
+    gcamb.emu_load(e2, path)
+    o1 = gcamb.emu_forward(e, Xh).cpu().numpy()
+    o2 = gcamb.emu_forward(e2, Xh).cpu().numpy()
+    gcamb.sync()
+    assert np.array_equal(o1, o2)
+    assert gcamb.emu_info(e2)["steps"] == 400
+    raw = bytearray(path.read_bytes())
+    raw[100] ^= 0xFF
+    path.write_bytes(bytes(raw))
+    with pytest.raises(gcamb.GcambError) as ei:
+        gcamb.emu_load(e2, path)
+    assert ei.value.code == gcamb.EINVAL
+
+
+def test_network_serves_faster_than_the_projection():
+    """What the network gains over the method without it: spectra per second
+    of trusted requests against the batched projection on the 256-source,
+    l_max = 2500 grid, same GPU."""
+    wl = synth.workload("batched_lmax2500")
+    g = gcamb.grid_create(wl.k, wl.tau, wl.tau0, wl.lmin, wl.lmax)
+    e = gcamb.emu_create(g, width=512, depth=3, max_batch=4096, seed=4)
+    X, C = _dataset(g, 256, seed=33)
+    gcamb.emu_check(e, X, C, tol=float("inf"), min_count=1)  # trust every populated cell: time the network path
+    Xb = X.repeat(16, 1).contiguous()
+    Cl = torch.empty((4096, g.nl), dtype=torch.float64, device="cuda")
+    fb = torch.empty(4096, dtype=torch.int32, device="cuda")
+    gcamb.emulate(e, Xb, Cl, fb)
+    gcamb.sync()
+    assert int(fb.sum().item()) == 0
+    t0 = time.perf_counter()
+    for _ in range(5):
+        gcamb.emulate(e, Xb, Cl, fb)
+    gcamb.sync()
+    emu_rate = 5 * 4096 / (time.perf_counter() - t0)
+    S, P = gcamb.synth_sources(g, X.contiguous())
+    gcamb.los_cl(g, S, P, gcamb.F16X3)
+    gcamb.sync()
+    t0 = time.perf_counter()
+    for _ in range(5):
+        gcamb.los_cl(g, S, P, gcamb.F16X3)
+    gcamb.sync()
+    proj_rate = 5 * 256 / (time.perf_counter() - t0)
+    print("emulator %.3g spectra/s, projection %.3g spectra/s" % (emu_rate, proj_rate))
+    assert emu_rate > 5 * proj_rate
