@@ -50,6 +50,9 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nk", type=int, default=0,
                     help="profiling case: the same k range with this many nodes (default: the workload's 2000)")
+    ap.add_argument("--workload", default="batched", choices=["batched", "uneven", "emulator"],
+                    help="batched (the headline), uneven (1000 sources, l_max <= 6000, plan + graph), "
+                         "emulator (train on 100k spectra, serve)")
     ap.add_argument("--kernel-only", action="store_true",
                     help="profiling case: only warm-up + timed steps, one short line, no e2e/plain/CPU legs")
     return ap.parse_args()
@@ -174,12 +177,116 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ other workloads
+
+def _timed_region(fn, steps, dev):
+    import torch
+    bus = None
+    try:
+        bus = torch.cuda.get_device_properties(dev).pci_bus_id
+    except Exception:
+        pass
+    sampler = ClockSampler(bus)
+    torch.cuda.synchronize()
+    sampler.start()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        fn()
+    b.record()
+    b.synchronize()
+    return a.elapsed_time(b), sampler.stop()
+
+
+def run_uneven(args):
+    """1000 sources with l_max ~ U{1500..6000} and k prefixes of 1000..3000
+    nodes of a 3000-node linear grid, 1000 tau: one tuned plan, replayed from
+    its CUDA graph (one persistent tensor-core kernel per launch)."""
+    import numpy as np
+    import torch
+
+    from paper_2509_25110_gb300 import build, gcamb, synth
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    build.build()
+    mode = {"bf16x3": gcamb.BF16X3, "tf32x3": gcamb.TF32X3, "f16x3": gcamb.F16X3}[args.mode]
+    wl = synth.workload("uneven_lmax6000")
+    p = synth.model_params(wl.M, seed=0, lmax_range=(1500, 6000))
+    lm = p.lmax.astype(np.int32)
+    nkm = synth.uneven_nk(lm).astype(np.int32)
+    g = gcamb.grid_create(wl.k, wl.tau, wl.tau0, wl.lmin, wl.lmax)
+    t0 = time.perf_counter()
+    gcamb.bessel_table(g, mode)
+    torch.cuda.synchronize()
+    table_s = time.perf_counter() - t0
+    X = torch.as_tensor(synth.emulator_features(p), device=dev)
+    S, P = gcamb.synth_sources(g, X)
+    plan = gcamb.plan_create(g, wl.M, lm, nkm, mode, tune=True)
+    ws = torch.empty(gcamb.plan_workspace(plan), dtype=torch.uint8, device=dev)
+    C = torch.empty((wl.M, g.nl), dtype=torch.float64, device=dev)
+    t0 = time.perf_counter()
+    gcamb.plan_launch(plan, S, P, C, ws)  # tunes, then captures the graph
+    torch.cuda.synchronize()
+    first_s = time.perf_counter() - t0
+    for _ in range(max(3, args.warmup)):
+        gcamb.plan_launch(plan, S, P, C, ws)
+    steps = max(3, min(args.steps, 20))
+    ms, clocks = _timed_region(lambda: gcamb.plan_launch(plan, S, P, C, ws), steps, dev)
+    gcamb.sync()
+    info = gcamb.plan_info(plan)
+    line = {"metric": "C_l spectra/sec, uneven batch (1000 sources, l_max U{1500..6000})",
+            "value": wl.M * steps / (ms * 1e-3), "unit": "spectra/s", "n_gpus": 1, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {gcamb.BF16X3: "bf16", gcamb.F16X3: "f16", gcamb.TF32X3: "tf32"}[mode],
+            "data": "synthetic",
+            "config": {"workload": "uneven_lmax6000", "M": wl.M, "nk_master": wl.nk, "ntau": wl.ntau,
+                       "lmax": wl.lmax, "mode": args.mode, "tile": info["tile"], "items": info["items"],
+                       "ctas": info["ctas"], "graph_captures": info["captures"], "graph_replays": info["replays"],
+                       "table_build_s": table_s, "first_launch_s_incl_tuning": first_s,
+                       "table_gb": gcamb.table_bytes(g, mode) / 1e9},
+            "clocks": clocks, "gpu_launches": 3 * steps}
+    print(json.dumps(line), flush=True)
+
+
+def run_emulator(args):
+    """Trains the emulator on 100k spectra of the batched grid (l 2..2500) and
+    serves a held-out set; reports spectra/s and the held-out accuracy."""
+    import torch
+
+    from paper_2509_25110_gb300 import build, emulator, gcamb, synth
+    torch.cuda.set_device(0)
+    build.build()
+    wl = synth.workload(WORKLOAD)
+    g = gcamb.grid_create(wl.k, wl.tau, wl.tau0, wl.lmin, wl.lmax)
+    steps = args.steps if args.steps != 600 else 3000
+    e, rep, (Xh, Ch) = emulator.train(g, steps=steps, log=lambda m: print(m, file=sys.stderr, flush=True))
+    rates = emulator.serve_rates(e, g, Xh)
+    line = {"metric": "emulator C_l spectra/sec at l_max=2500 (trusted cells, projection fallback)",
+            "value": rates["emulate_spectra_per_s"], "unit": "spectra/s", "n_gpus": 1, "steps": steps,
+            "warmup": 0, "ms_per_step": rep["train_step_ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "emulator_lmax2500", "arch": "9-512-512-512-2499 GELU", "batch": rep["batch"],
+                       "n_train": rep["n_train"], "n_hold": rep["n_hold"], "train_steps": steps,
+                       "data_gen_s": rep["data_s"], "train_s": rep["train_s"], "check": rep["check"],
+                       "tol": rep["tol"], **rates,
+                       "gain_network_vs_projection": rates["network_spectra_per_s"] / rates["projection_spectra_per_s"],
+                       "final_loss": rep["loss_history"][-1][1]}}
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------------ our arm
 
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "uneven":
+        run_uneven(args)
+        return
+    if args.workload == "emulator":
+        run_emulator(args)
         return
     import numpy as np
     import torch

@@ -284,9 +284,12 @@ int gcamb_emu_grads(gcamb_emu *e, float *host_out);
  * feature is dropped), outputs leave as y sd_y + mu_y. */
 int gcamb_emu_norm(gcamb_emu *e, float *mu_x, float *sd_x, float *mu_y, float *sd_y, int set);
 /* Fits the normalisation on N training samples X[N][9], Cl[N][n_out] (>0)
- * and writes the standardised targets Y[N][n_out] = (log Cl - mu_y) / sd_y.
- * Synchronises the stream. */
-int gcamb_emu_fit_norm(gcamb_emu *e, const float *X, const double *Cl, int N, float *Y, void *stream);
+ * and writes the standardised targets Y[N][n_out] = (log Cl - mu_y) / sd_y:
+ * mu_y per multipole; sd_y per multipole (per_l = 1) or one scale for all,
+ * the root mean square of the per-multipole ones (per_l = 0, so that the loss
+ * weighs the error of log C_l, i.e. the relative error of C_l, alike at every
+ * l).  Synchronises the stream. */
+int gcamb_emu_fit_norm(gcamb_emu *e, const float *X, const double *Cl, int N, int per_l, float *Y, void *stream);
 /* One Adam step (lr; beta 0.9, 0.999; eps 1e-8) on the mean squared error of
  * the batch X[idx[b]], Y[idx[b]] (idx[B] device int, or NULL for the first B
  * rows); the batch loss goes to *loss (device float, may be NULL). */

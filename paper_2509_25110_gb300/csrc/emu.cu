@@ -526,7 +526,18 @@ int gcamb_emu_norm(gcamb_emu *e, float *mu_x, float *sd_x, float *mu_y, float *s
   return ck(cudaGetLastError(), "emu_norm: download");
 }
 
-int gcamb_emu_fit_norm(gcamb_emu *e, const float *X, const double *Cl, int N, float *Y, void *stream) {
+// Replaces every sd_y[j] by the root mean square of the per-l deviations, so
+// that the loss weighs each multipole's error in nats (log C_l) equally.
+__global__ void global_scale_kernel(float *__restrict__ sd, int n) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int j = 0; j < n; ++j) s += (double)sd[j] * sd[j];
+    const float r = (float)sqrt(s / n);
+    for (int j = 0; j < n; ++j) sd[j] = r;
+  }
+}
+
+int gcamb_emu_fit_norm(gcamb_emu *e, const float *X, const double *Cl, int N, int per_l, float *Y, void *stream) {
   if (!e || !X || !Cl || !Y) return fail(GCAMB_EINVAL, "emu_fit_norm: NULL argument");
   if (N < 2) return fail(GCAMB_EINVAL, "emu_fit_norm: need at least 2 samples");
   cudaStream_t st = (cudaStream_t)stream;
@@ -538,6 +549,7 @@ int gcamb_emu_fit_norm(gcamb_emu *e, const float *X, const double *Cl, int N, fl
   const size_t n = (size_t)N * e->n_out;
   log_kernel<<<1024, 256, 0, st>>>(Cl, n, Y);
   colstats_kernel<<<(e->n_out + 127) / 128, 128, 0, st>>>(Y, N, e->n_out, e->mu_y, e->sd_y);
+  if (!per_l) global_scale_kernel<<<1, 32, 0, st>>>(e->sd_y, e->n_out);
   standardize_y_kernel<<<1024, 256, 0, st>>>(Y, N, e->n_out, e->mu_y, e->sd_y);
   rc = ck(cudaGetLastError(), "emu_fit_norm: launch");
   cudaStreamSynchronize(st);

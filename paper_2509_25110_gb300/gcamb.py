@@ -71,7 +71,7 @@ def lib():
     L.gcamb_emu_params.argtypes = [_vp, _vp, _vp]
     L.gcamb_emu_grads.argtypes = [_vp, _vp]
     L.gcamb_emu_norm.argtypes = [_vp, _vp, _vp, _vp, _vp, ctypes.c_int]
-    L.gcamb_emu_fit_norm.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp, _vp]
+    L.gcamb_emu_fit_norm.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp]
     L.gcamb_emu_train_step.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_float, _vp, _vp]
     L.gcamb_emu_forward.argtypes = [_vp, _vp, ctypes.c_int, _vp, _vp]
     L.gcamb_emu_check.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, _vp, _vp]
@@ -466,13 +466,13 @@ def emu_norm(e: Emu, mu_x=None, sd_x=None, mu_y=None, sd_y=None) -> dict:
     return dict(zip(("mu_x", "sd_x", "mu_y", "sd_y"), arrs))
 
 
-def emu_fit_norm(e: Emu, X, Cl, Y=None, stream=None):
+def emu_fit_norm(e: Emu, X, Cl, Y=None, per_l=False, stream=None):
     import torch
     N = X.shape[0]
     if Y is None:
         Y = torch.empty((N, e.n_out), dtype=torch.float32, device=X.device)
     _check(lib().gcamb_emu_fit_norm(e.handle, _dev(X, torch.float32, (N, 9), "X"),
-                                    _dev(Cl, torch.float64, (N, e.n_out), "Cl"), N,
+                                    _dev(Cl, torch.float64, (N, e.n_out), "Cl"), N, 1 if per_l else 0,
                                     _dev(Y, torch.float32, (N, e.n_out), "Y"), _stream(stream)))
     return Y
 

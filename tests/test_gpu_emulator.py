@@ -119,7 +119,7 @@ def test_training_fallback_and_checkpoint(tmp_path):
     e = gcamb.emu_create(g, width=128, depth=3, max_batch=1024, seed=3)
     X, C = _dataset(g, 2048, seed=31)
     Xh, Ch = _dataset(g, 512, seed=32)
-    Y = gcamb.emu_fit_norm(e, X, C)
+    Y = gcamb.emu_fit_norm(e, X, C, per_l=True)
     rng = np.random.default_rng(8)
     loss = torch.zeros(1, dtype=torch.float32, device="cuda")
     losses = []
