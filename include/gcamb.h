@@ -355,9 +355,13 @@ int gcamb_synth_sources(const gcamb_grid *g, const float *X, int M, float *S, do
  * Limits and behaviour:
  *  - Problems whose scratch exceeds 64 MiB are rejected with GCAMB_EINVAL
  *    (the message gives the bytes needed); use gcamb_los_cl for them.  The
- *    split sources take about 4 bytes per (k, tau, source) with the sources
- *    rounded up to a multiple of 64, so with 1000 tau nodes the limit is
- *    roughly nk * M <= 15,000.
+ *    scratch holds the k-chunk partial sums, 64 KB per work item at 128
+ *    sources per tile (about 4 items per SM, and at least one per 64 k per
+ *    l-tile per source tile), and 4-8 bytes per (k, source) of weights.
+ *    When the sources cannot be read in place (ntau not a multiple of 4, or
+ *    the TF32X3 mode) it also holds the split sources, about 4 bytes per
+ *    (k, tau, source), which with 1000 tau nodes limits nk * M to about
+ *    15,000.
  *  - The first call on a device looks up the buffer's device address
  *    (cudaGetSymbolAddress) and caches it; make that first call before any
  *    stream capture.

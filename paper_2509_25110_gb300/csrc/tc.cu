@@ -10,12 +10,17 @@
 // to per-thread FP32 sums over a chunk of at most 64 k; the chunk sums are
 // added in FP64 in a fixed order by a second kernel.  D_k never leaves the SM.
 //
-// Work item = (l-tile, source tile, contiguous k-chunk).  One CTA per item:
-//   warp 0      bulk-copy producer (table block + split-source block per stage)
+// Work item = (l-tile, source tile, contiguous k-chunk).  One persistent CTA
+// per SM takes items from a counter:
+//   warp 0      producer: bulk copy of the table block and of the source block
+//               per stage (split sources, or FP32 sources by TMA when fused)
 //   warp 1      TMEM allocator and single-thread MMA issuer
-//   warps 2..9  epilogue: TMEM -> registers, square, weight, accumulate
+//   warps 2..5  (fused only) converters: FP32 source tile -> hi/lo planes in
+//               place, in the swizzled operand layout
+//   the rest    8 epilogue warps: TMEM -> registers, square, weight, accumulate
 // Every mbarrier wait is bounded (1 s); a timeout sets the device error flag,
 // the CTA drains its own copies and MMAs, frees TMEM and exits.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -23,6 +28,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
 #include <mutex>
 #include <new>
 #include <string>
@@ -35,11 +41,12 @@ namespace gcamb {
 namespace {
 
 constexpr int kEpiWarps = 8;
+constexpr int kConvWarps = 4;
 constexpr int kThreads = 32 * (2 + kEpiWarps);
+constexpr int kThreadsFused = 32 * (2 + kConvWarps + kEpiWarps);
 constexpr int kKChunkMax = 64;     // k per work item: bounds the FP32 partial-sum length
 constexpr int kABytes = 32768;     // one table block: hi + lo planes of 128 x 128 B
 constexpr int kSmemBudget = 196608;
-constexpr int kItemSlots = 4;       // item indices in flight from the producer to the other roles
 
 struct TcItem {
   int lt, mt, qb, qe;
@@ -51,6 +58,7 @@ struct TcParams {
   const int32_t *nkb;    // [nk][nlt]
   const char *sp;        // split sources [nk][n_mt][nkbs] blocks of 256*NT bytes
   const float *wp;       // [nk][mpad] 4 pi w_k P_m(k)
+  const float *sc;       // fused F16X3: [nk][mpad] power-of-two row scales of the sources
   const TcItem *items;
   int *counter;          // next item to hand out (zeroed before each launch)
   int nitems;
@@ -119,6 +127,27 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Named barrier 1 over the converter warps; returns the AND of every
+// converter thread's `ok`, so that all of them leave their loops together.
+__device__ __forceinline__ bool conv_all(bool ok) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.and.pred q, 1, %2, p;\n\tselp.u32 %0, 1, 0, q;\n\t}\n"
+      : "=r"(r)
+      : "r"((uint32_t)ok), "n"(kConvWarps * 32)
+      : "memory");
+  return r != 0;
+}
+
+// 3-D tiled TMA load (x innermost) into shared memory, completing on `bar`.
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int x, int y, int z, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
 
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
 // groups 1024 bytes apart (SBO), descriptor version 1 (bit 46).
@@ -189,47 +218,74 @@ struct TcCfg {
   static constexpr int kStages = (kSmemBudget / kStageBytes) > 4 ? 4 : (kSmemBudget / kStageBytes);
   static constexpr int kNBuf = (4 * NT <= 512) ? 2 : 1;
   static constexpr int kTmemCols = kNBuf * 2 * NT < 32 ? 32 : kNBuf * 2 * NT;
-  static constexpr int kSmemBytes = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
+  static constexpr int kKSlots = 4;                      // per-k records in flight
+  static constexpr int kSlotBytes = 16 + 8 * NT;         // header, weights, row scales
+  static constexpr int kQBytes = kKChunkMax * 12;        // the item's block counts and offsets
+  static constexpr int kSmemBytes =
+      kStages * kStageBytes + kKSlots * kSlotBytes + kQBytes + 1024 /*align*/ + 256 /*barriers*/;
   static constexpr int kColsPerThread = NT / 2;
   static constexpr int kChunk = NT >= 256 ? 8 : 16;      // TMEM load width (register budget)
 };
 
-template <int NT, int MODE>
-__global__ void __launch_bounds__(kThreads, 1) los_cl_tc_kernel(TcParams p) {
+template <bool FUSED>
+struct TcRoles {
+  static constexpr int kConv = FUSED ? kConvWarps : 0;
+  static constexpr int kEpi0 = 2 + kConv;  // first epilogue warp
+  static constexpr int kThreadsT = FUSED ? kThreadsFused : kThreads;
+};
+
+// Per-k record, written by the producer into a ring in shared memory:
+// header {q, nb, item, mt | flags}, then the epilogue weights of the k for
+// the item's source tile (bulk copy) and, fused fp16 only, the sources' row
+// scales.  nb < 0 ends the work.
+constexpr int kFirst = 1 << 16, kLast = 1 << 17;
+
+template <int NT, int MODE, bool FUSED>
+__global__ void __launch_bounds__(TcRoles<FUSED>::kThreadsT, 1)
+    los_cl_tc_kernel(const __grid_constant__ CUtensorMap tm_src, TcParams p) {
   using C = TcCfg<NT>;
+  using R = TcRoles<FUSED>;
   constexpr int S = C::kStages;
   constexpr int NB = C::kNBuf;
+  constexpr int KS = C::kKSlots;
+  constexpr bool kScale = FUSED && MODE == kF16;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + S * C::kStageBytes);
-  // bars: full[S], empty[S], tfull[2], tempty[2], drain, (tmem slot), (abort),
-  //       ifull[4], iempty[4], (item slots)
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * S + 5);
-  volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 2 * S + 6);
-  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + S);
-  const uint32_t tfull0 = smem_u32(bars + 2 * S), tempty0 = smem_u32(bars + 2 * S + 2);
-  const uint32_t drain = smem_u32(bars + 2 * S + 4);
-  const uint32_t ifull0 = smem_u32(bars + 2 * S + 7), iempty0 = smem_u32(bars + 2 * S + 11);
-  volatile int *islot = reinterpret_cast<volatile int *>(bars + 2 * S + 15);
+  unsigned char *kslots = smem + S * C::kStageBytes;
+  int64_t *q_off = reinterpret_cast<int64_t *>(kslots + KS * C::kSlotBytes);  // [kKChunkMax]
+  int32_t *q_nb = reinterpret_cast<int32_t *>(q_off + kKChunkMax);           // [kKChunkMax]
+  uint64_t *bars = reinterpret_cast<uint64_t *>(kslots + KS * C::kSlotBytes + C::kQBytes);
+  // bars: full[S], empty[S], conv[S], kfull[KS], kempty[KS], tfull[2],
+  //       tempty[2], drain, (tmem slot), (abort)
+  uint64_t *b1 = bars + 3 * S + 2 * KS;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(b1 + 5);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(b1 + 6);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + S), conv0 = smem_u32(bars + 2 * S);
+  const uint32_t kfull0 = smem_u32(bars + 3 * S), kempty0 = smem_u32(bars + 3 * S + KS);
+  const uint32_t tfull0 = smem_u32(b1), tempty0 = smem_u32(b1 + 2);
+  const uint32_t drain = smem_u32(b1 + 4);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(full0 + 8 * s, 1);
       mbar_init(empty0 + 8 * s, 1);
+      mbar_init(conv0 + 8 * s, R::kConv > 0 ? R::kConv : 1);
+    }
+    for (int s = 0; s < KS; ++s) {
+      mbar_init(kfull0 + 8 * s, 1);
+      mbar_init(kempty0 + 8 * s, 1 + kEpiWarps + R::kConv);
     }
     mbar_init(tfull0, 1);
     mbar_init(tfull0 + 8, 1);
     mbar_init(tempty0, kEpiWarps);
     mbar_init(tempty0 + 8, kEpiWarps);
     mbar_init(drain, 1);
-    for (int s = 0; s < kItemSlots; ++s) {
-      mbar_init(ifull0 + 8 * s, 1);
-      mbar_init(iempty0 + 8 * s, 1 + kEpiWarps);
-    }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  if (FUSED && threadIdx.x == 32)
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tm_src)) : "memory");
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"((uint32_t)C::kTmemCols)
@@ -242,53 +298,94 @@ __global__ void __launch_bounds__(kThreads, 1) los_cl_tc_kernel(TcParams p) {
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0) {
-    if (lane == 0) {
-      // ---------------- producer
-      int stage = 0;
-      uint32_t phase = 0;
-      int armed_phase[4] = {-1, -1, -1, -1};
-      bool ok = true;
-      int is = 0;
-      uint32_t iph = 0;
-      while (ok) {
-      // hand out the next item (or -1) to the MMA issuer and the epilogue
-      if (!mbar_wait(iempty0 + 8 * is, iph ^ 1u, abort_flag, p.err)) break;
-      int item = atomicAdd(p.counter, 1);
-      if (item >= p.nitems) item = -1;
-      islot[is] = item;
-      mbar_arrive(ifull0 + 8 * is);
-      if (++is == kItemSlots) {
-        is = 0;
-        iph ^= 1u;
-      }
-      if (item < 0) break;
+    // ---------------- producer: items from the counter; the whole warp loads
+    // the item's block counts and table offsets into shared memory (one
+    // round trip per item), then lane 0 writes per non-empty k a record and
+    // issues the k's table and source blocks into the stage ring
+    int stage = 0;
+    uint32_t phase = 0;
+    int armed_phase[4] = {-1, -1, -1, -1};
+    int ks = 0;
+    uint32_t kph = 0;
+    int karmed[C::kKSlots];
+#pragma unroll
+    for (int s = 0; s < KS; ++s) karmed[s] = -1;
+    bool ok = true;
+    while (ok) {
+      int item = 0;
+      if (lane == 0) item = atomicAdd(p.counter, 1);
+      item = __shfl_sync(0xffffffffu, item, 0);
+      if (item >= p.nitems) break;
       const TcItem it = p.items[item];
-      const int32_t *nkb_row = p.nkb + it.lt;
-      const int64_t *off_row = p.off + it.lt;
-      for (int q = it.qb; q < it.qe && ok; ++q) {
-        const int nb = nkb_row[(size_t)q * p.nlt];
-        const char *a = p.table + (size_t)off_row[(size_t)q * p.nlt] * kABytes;
-        const char *b = p.sp + ((size_t)q * p.n_mt + it.mt) * (size_t)p.nkbs * C::kBBytes;
-        for (int kb = 0; kb < nb; ++kb) {
-          if (!mbar_wait(empty0 + 8 * stage, phase ^ 1u, abort_flag, p.err)) {
+      const int cnt = min(it.qe - it.qb, kKChunkMax);  // the plan keeps items within kKChunkMax k
+      for (int j = lane; j < cnt; j += 32) {
+        const size_t e = (size_t)(it.qb + j) * p.nlt + it.lt;
+        q_nb[j] = p.nkb[e];
+        q_off[j] = p.off[e];
+      }
+      __syncwarp();
+      if (lane == 0) {
+        for (int j = 0; j < cnt && ok; ++j) {
+          const int q = it.qb + j;
+          const int nb = q_nb[j];
+          if (nb == 0) continue;
+          // the k's record
+          if (!mbar_wait(kempty0 + 8 * ks, kph ^ 1u, abort_flag, p.err)) {
             ok = false;
             break;
           }
-          const uint32_t sa = smem_u32(smem + stage * C::kStageBytes);
-          mbar_expect_tx(full0 + 8 * stage, C::kStageBytes);
-          armed_phase[stage] = (int)phase;
-          bulk_g2s(sa, a + (size_t)kb * kABytes, kABytes, full0 + 8 * stage);
-          bulk_g2s(sa + kABytes, b + (size_t)kb * C::kBBytes, C::kBBytes, full0 + 8 * stage);
-          if (++stage == S) {
-            stage = 0;
-            phase ^= 1u;
+          unsigned char *rec = kslots + ks * C::kSlotBytes;
+          volatile int *hdr = reinterpret_cast<volatile int *>(rec);
+          hdr[0] = q;
+          hdr[1] = nb;
+          hdr[2] = item;
+          hdr[3] = it.mt | (q == it.qb ? kFirst : 0) | (q == it.qe - 1 ? kLast : 0);
+          const uint32_t kb_bar = kfull0 + 8 * ks;
+          mbar_expect_tx(kb_bar, (kScale ? 2 : 1) * NT * 4);
+          karmed[ks] = (int)kph;
+          const size_t wrow = (size_t)q * p.mpad + (size_t)it.mt * NT;
+          bulk_g2s(smem_u32(rec + 16), p.wp + wrow, NT * 4, kb_bar);
+          if constexpr (kScale) bulk_g2s(smem_u32(rec + 16 + NT * 4), p.sc + wrow, NT * 4, kb_bar);
+          if (++ks == KS) {
+            ks = 0;
+            kph ^= 1u;
+          }
+          const char *a = p.table + (size_t)q_off[j] * kABytes;
+          const char *b = FUSED ? nullptr : p.sp + ((size_t)q * p.n_mt + it.mt) * (size_t)p.nkbs * C::kBBytes;
+          for (int kb = 0; kb < nb; ++kb) {
+            if (!mbar_wait(empty0 + 8 * stage, phase ^ 1u, abort_flag, p.err)) {
+              ok = false;
+              break;
+            }
+            const uint32_t sa = smem_u32(smem + stage * C::kStageBytes);
+            mbar_expect_tx(full0 + 8 * stage, C::kStageBytes);
+            armed_phase[stage] = (int)phase;
+            bulk_g2s(sa, a + (size_t)kb * kABytes, kABytes, full0 + 8 * stage);
+            if constexpr (FUSED)  // FP32 box [NT sources][1 k][64 tau]; zero beyond ntau and M
+              tma_load_3d(sa + kABytes, &tm_src, kb * 64, q, it.mt * NT, full0 + 8 * stage);
+            else
+              bulk_g2s(sa + kABytes, b + (size_t)kb * C::kBBytes, C::kBBytes, full0 + 8 * stage);
+            if (++stage == S) {
+              stage = 0;
+              phase ^= 1u;
+            }
           }
         }
       }
+      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;  // also orders lane 0's reads before the next item's writes
+    }
+    if (lane == 0) {
+      // end-of-work record (no copies)
+      if (ok && mbar_wait(kempty0 + 8 * ks, kph ^ 1u, abort_flag, p.err)) {
+        reinterpret_cast<volatile int *>(kslots + ks * C::kSlotBytes)[1] = -1;
+        mbar_arrive(kfull0 + 8 * ks);
+        karmed[ks] = (int)kph;  // this phase completes now; the drain below must not wait for a later one
       }
       // no copy may still be landing when the CTA exits
       for (int s = 0; s < S; ++s)
         if (armed_phase[s] >= 0) mbar_wait(full0 + 8 * s, (uint32_t)armed_phase[s], nullptr, p.err);
+      for (int s = 0; s < KS; ++s)
+        if (karmed[s] >= 0) mbar_wait(kfull0 + 8 * s, (uint32_t)karmed[s], nullptr, p.err);
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -296,37 +393,37 @@ __global__ void __launch_bounds__(kThreads, 1) los_cl_tc_kernel(TcParams p) {
       constexpr uint32_t fmt = MODE == kTF32 ? 2u : (MODE == kBF16 ? 1u : 0u);
       constexpr uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(NT >> 3) << 17) |
                                  ((uint32_t)(128 >> 4) << 24);
+      // With NT <= 128 the hi and lo source planes are one operand of 2 NT
+      // rows and D_hh, D_x adjacent TMEM columns, so hi*hi and hi*lo are one
+      // MMA of N = 2 NT: each K step reads A_hi once (shared-memory bandwidth
+      // bounds these MMAs).
+      constexpr bool kPair = 2 * NT <= 256;
+      constexpr uint32_t idesc2 = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)((2 * NT) >> 3) << 17) |
+                                  ((uint32_t)(128 >> 4) << 24);
       int stage = 0;
       uint32_t phase = 0;
       int n = 0;
-      bool ok = true;
-      int is = 0;
-      uint32_t iph = 0;
-      while (ok) {
-      if (!mbar_wait(ifull0 + 8 * is, iph, abort_flag, p.err)) break;
-      const int item = islot[is];
-      mbar_arrive(iempty0 + 8 * is);
-      if (++is == kItemSlots) {
-        is = 0;
-        iph ^= 1u;
-      }
-      if (item < 0) break;
-      const TcItem it = p.items[item];
-      const int32_t *nkb_row = p.nkb + it.lt;
-      for (int q = it.qb; q < it.qe && ok; ++q) {
-        const int nb = nkb_row[(size_t)q * p.nlt];
-        if (nb == 0) continue;
+      int ks = 0;
+      uint32_t kph = 0;
+      while (true) {
+        if (!mbar_wait(kfull0 + 8 * ks, kph, abort_flag, p.err)) break;
+        const int nb = reinterpret_cast<volatile int *>(kslots + ks * C::kSlotBytes)[1];
+        if (nb < 0) break;
+        mbar_arrive(kempty0 + 8 * ks);
+        if (++ks == KS) {
+          ks = 0;
+          kph ^= 1u;
+        }
         const int buf = n % NB;
         const uint32_t use = (uint32_t)(n / NB);
-        if (!mbar_wait(tempty0 + 8 * buf, (use & 1u) ^ 1u, abort_flag, p.err)) {
-          ok = false;
-          break;
-        }
+        if (!mbar_wait(tempty0 + 8 * buf, (use & 1u) ^ 1u, abort_flag, p.err)) break;
         tc_fence_after();
         const uint32_t dhh = tmem + (uint32_t)(buf * 2 * NT);
         const uint32_t dx = dhh + (uint32_t)NT;
+        bool ok = true;
         for (int kb = 0; kb < nb; ++kb) {
-          if (!mbar_wait(full0 + 8 * stage, phase, abort_flag, p.err)) {
+          if ((FUSED && !mbar_wait(conv0 + 8 * stage, phase, abort_flag, p.err)) ||
+              !mbar_wait(full0 + 8 * stage, phase, abort_flag, p.err)) {
             ok = false;
             break;
           }
@@ -338,8 +435,12 @@ __global__ void __launch_bounds__(kThreads, 1) los_cl_tc_kernel(TcParams p) {
             const uint64_t ah = sw128_desc(sa + kk * 32), al = sw128_desc(sa + 16384 + kk * 32);
             const uint64_t bh = sw128_desc(sb + kk * 32), bl = sw128_desc(sb + NT * 128 + kk * 32);
             const uint32_t accum = (kb | kk) ? 1u : 0u;
-            mma<MODE>(dhh, ah, bh, idesc, accum);
-            mma<MODE>(dx, ah, bl, idesc, accum);
+            if constexpr (kPair) {
+              mma<MODE>(dhh, ah, bh, idesc2, accum);  // [D_hh | D_x] (+)= A_hi [B_hi | B_lo]
+            } else {
+              mma<MODE>(dhh, ah, bh, idesc, accum);
+              mma<MODE>(dx, ah, bl, idesc, accum);
+            }
             mma<MODE>(dx, al, bh, idesc, 1u);
           }
           mma_commit(empty0 + 8 * stage);
@@ -352,48 +453,120 @@ __global__ void __launch_bounds__(kThreads, 1) los_cl_tc_kernel(TcParams p) {
         mma_commit(tfull0 + 8 * buf);
         ++n;
       }
-      }
       // every MMA this thread issued has completed before TMEM is freed
       mma_commit(drain);
       mbar_wait(drain, 0, nullptr, p.err);
     }
+  } else if (FUSED && warp < R::kEpi0) {
+    // ---------------- converters: the stage's FP32 tile [NT][64] becomes the
+    // hi and lo planes [NT][128 B] (swizzled) in the same bytes.  Thread ct
+    // owns float4 column c4 of rows r0 + 8 j; every row it writes has the same
+    // row mod 8, hence one swizzle offset.  All reads precede all writes
+    // (conv_all is the barrier between them).
+    if constexpr (FUSED) {
+      constexpr int RJ = NT / 8;
+      const int ct = threadIdx.x - 64;
+      const int c4 = ct & 15, r0 = ct >> 4;
+      const uint32_t swz = ((uint32_t)(((c4 >> 1) ^ (r0 & 7)) << 4)) | ((uint32_t)(c4 & 1) << 3);
+      int stage = 0;
+      uint32_t phase = 0;
+      int ks = 0;
+      uint32_t kph = 0;
+      while (true) {
+        const bool w = mbar_wait(kfull0 + 8 * ks, kph, abort_flag, p.err);
+        const unsigned char *rec = kslots + ks * C::kSlotBytes;
+        const int nb = w ? reinterpret_cast<const volatile int *>(rec)[1] : -1;
+        if (!conv_all(w) || nb < 0) break;
+        float scl[RJ];
+        if constexpr (MODE == kF16) {
+          const float *sr = reinterpret_cast<const float *>(rec + 16 + NT * 4) + r0;
+#pragma unroll
+          for (int j = 0; j < RJ; ++j) scl[j] = sr[8 * j];
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(kempty0 + 8 * ks);
+        if (++ks == KS) {
+          ks = 0;
+          kph ^= 1u;
+        }
+        bool ok = true;
+        for (int kb = 0; kb < nb; ++kb) {
+          const bool w2 = mbar_wait(full0 + 8 * stage, phase, abort_flag, p.err);
+          unsigned char *sb = smem + stage * C::kStageBytes + kABytes;
+          const float4 *raw = reinterpret_cast<const float4 *>(sb);
+          float4 v[RJ];
+#pragma unroll
+          for (int j = 0; j < RJ; ++j) v[j] = raw[ct + 128 * j];
+          if (!conv_all(w2)) {
+            ok = false;
+            break;
+          }
+#pragma unroll
+          for (int j = 0; j < RJ; ++j) {
+            float x0 = v[j].x, x1 = v[j].y, x2 = v[j].z, x3 = v[j].w;
+            uint2 hi, lo;
+            if constexpr (MODE == kF16) {
+              x0 *= scl[j];
+              x1 *= scl[j];
+              x2 *= scl[j];
+              x3 *= scl[j];
+              const __half2 h01 = __floats2half2_rn(x0, x1), h23 = __floats2half2_rn(x2, x3);
+              const __half2 l01 = __floats2half2_rn(x0 - __low2float(h01), x1 - __high2float(h01));
+              const __half2 l23 = __floats2half2_rn(x2 - __low2float(h23), x3 - __high2float(h23));
+              hi = make_uint2(*reinterpret_cast<const uint32_t *>(&h01), *reinterpret_cast<const uint32_t *>(&h23));
+              lo = make_uint2(*reinterpret_cast<const uint32_t *>(&l01), *reinterpret_cast<const uint32_t *>(&l23));
+            } else {
+              const __nv_bfloat162 h01 = __floats2bfloat162_rn(x0, x1), h23 = __floats2bfloat162_rn(x2, x3);
+              const __nv_bfloat162 l01 = __floats2bfloat162_rn(x0 - __low2float(h01), x1 - __high2float(h01));
+              const __nv_bfloat162 l23 = __floats2bfloat162_rn(x2 - __low2float(h23), x3 - __high2float(h23));
+              hi = make_uint2(*reinterpret_cast<const uint32_t *>(&h01), *reinterpret_cast<const uint32_t *>(&h23));
+              lo = make_uint2(*reinterpret_cast<const uint32_t *>(&l01), *reinterpret_cast<const uint32_t *>(&l23));
+            }
+            const uint32_t o = (uint32_t)(r0 + 8 * j) * 128u + swz;
+            *reinterpret_cast<uint2 *>(sb + o) = hi;
+            *reinterpret_cast<uint2 *>(sb + NT * 128 + o) = lo;
+          }
+          // generic-proxy stores, read next by the tensor cores
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) mbar_arrive(conv0 + 8 * stage);
+          if (++stage == S) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        if (!ok) break;
+      }
+    }
   } else {
     // ---------------- epilogue: acc += (sqrt(4 pi w_k P) (D_hh + D_x))^2
     constexpr int CW = C::kChunk;
-    const int sp = warp & 3;
-    const int half = (warp - 2) >> 2;
+    const int sp = warp & 3;  // a warp reads the TMEM lanes 32 (warp mod 4) .. + 31
+    const int half = (warp - R::kEpi0) >> 2;
     const int row = sp * 32 + lane;
     const int col0 = half * C::kColsPerThread;
     float acc[C::kColsPerThread];
-    int n = 0;
-    bool ok = true;
-    int is = 0;
-    uint32_t iph = 0;
-    while (ok) {
-    if (!mbar_wait(ifull0 + 8 * is, iph, abort_flag, p.err)) break;
-    const int item = islot[is];
-    __syncwarp();
-    if (lane == 0) mbar_arrive(iempty0 + 8 * is);
-    if (++is == kItemSlots) {
-      is = 0;
-      iph ^= 1u;
-    }
-    if (item < 0) break;
-    const TcItem it = p.items[item];
-    const int32_t *nkb_row = p.nkb + it.lt;
 #pragma unroll
     for (int j = 0; j < C::kColsPerThread; ++j) acc[j] = 0.f;
-    for (int q = it.qb; q < it.qe && ok; ++q) {
-      const int nb = nkb_row[(size_t)q * p.nlt];
-      if (nb == 0) continue;
+    int n = 0;
+    int ks = 0;
+    uint32_t kph = 0;
+    while (true) {
+      if (!mbar_wait(kfull0 + 8 * ks, kph, abort_flag, p.err)) break;
+      const unsigned char *rec = kslots + ks * C::kSlotBytes;
+      const volatile int *hdr = reinterpret_cast<const volatile int *>(rec);
+      const int nb = hdr[1];
+      if (nb < 0) break;
+      const int item = hdr[2], flags = hdr[3];
       const int buf = n % NB;
       const uint32_t use = (uint32_t)(n / NB);
-      if (!mbar_wait(tfull0 + 8 * buf, use & 1u, abort_flag, p.err)) {
-        ok = false;
-        break;
-      }
+      if (!mbar_wait(tfull0 + 8 * buf, use & 1u, abort_flag, p.err)) break;
       tc_fence_after();
-      const float4 *w4 = reinterpret_cast<const float4 *>(p.wp + (size_t)q * p.mpad + it.mt * NT + col0);
+      if (flags & kFirst) {
+#pragma unroll
+        for (int j = 0; j < C::kColsPerThread; ++j) acc[j] = 0.f;
+      }
+      const float4 *w4 = reinterpret_cast<const float4 *>(rec + 16) + col0 / 4;
       const uint32_t taddr = tmem + ((uint32_t)(sp * 32) << 16) + (uint32_t)(buf * 2 * NT + col0);
 #pragma unroll
       for (int c = 0; c < C::kColsPerThread / CW; ++c) {
@@ -403,7 +576,7 @@ __global__ void __launch_bounds__(kThreads, 1) los_cl_tc_kernel(TcParams p) {
         tmem_wait_ld();
 #pragma unroll
         for (int j4 = 0; j4 < CW / 4; ++j4) {
-          const float4 w = __ldg(w4 + c * (CW / 4) + j4);
+          const float4 w = w4[c * (CW / 4) + j4];
           const float t0 = w.x * (vh[4 * j4 + 0] + vx[4 * j4 + 0]);
           const float t1 = w.y * (vh[4 * j4 + 1] + vx[4 * j4 + 1]);
           const float t2 = w.z * (vh[4 * j4 + 2] + vx[4 * j4 + 2]);
@@ -416,12 +589,20 @@ __global__ void __launch_bounds__(kThreads, 1) los_cl_tc_kernel(TcParams p) {
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(tempty0 + 8 * buf);
+      if (lane == 0) {
+        mbar_arrive(tempty0 + 8 * buf);
+        mbar_arrive(kempty0 + 8 * ks);
+      }
+      if (++ks == KS) {
+        ks = 0;
+        kph ^= 1u;
+      }
       ++n;
-    }
-    float *part = p.partial + (size_t)item * NT * 128;
+      if (flags & kLast) {
+        float *part = p.partial + (size_t)item * NT * 128;
 #pragma unroll
-    for (int j = 0; j < C::kColsPerThread; ++j) part[(size_t)(col0 + j) * 128 + row] = acc[j];
+        for (int j = 0; j < C::kColsPerThread; ++j) part[(size_t)(col0 + j) * 128 + row] = acc[j];
+      }
     }
   }
   tc_fence_before();
@@ -466,13 +647,16 @@ __device__ __forceinline__ double prefix_weight(const double *__restrict__ wk, c
 // [2^13, 2^14) (fp16 keeps 11 significant bits only in its normal range).
 // Lane 0 writes the row's epilogue weight wq = sqrt(4 pi w_k P) 2^-(sJ + s),
 // with the source's own k weights; (wq D')^2 is then the unscaled term.
-template <int MODE, int CACHE>
+// With STORE false (fused kernel) nothing is split: only wq is written, and
+// for fp16 the row scale 2^s that the converters apply, into sc.
+template <int MODE, int CACHE, bool STORE = true>
 __global__ void __launch_bounds__(256) split_rows_kernel(const float *__restrict__ S, const double *__restrict__ Pk,
                                                          const double *__restrict__ wk, const double *__restrict__ kk,
                                                          int M, int nk, int ntau, int NT, int n_mt, int nkbs,
                                                          int mpad, int sJ, const int *__restrict__ perm,
                                                          const int *__restrict__ nk_m, int vec,
-                                                         char *__restrict__ sp, float *__restrict__ wq) {
+                                                         char *__restrict__ sp, float *__restrict__ wq,
+                                                         float *__restrict__ sc = nullptr) {
   constexpr int EPC = MODE == kTF32 ? 4 : 8;  // elements per 16-byte chunk
   const int lane = threadIdx.x & 31;
   const size_t row = (size_t)blockIdx.x * 8 + (threadIdx.x >> 5);  // q * mpad + m
@@ -563,7 +747,8 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const float *__restrict
     *reinterpret_cast<uint4 *>(blk + o) = hi;
     *reinterpret_cast<uint4 *>(blk + NT * 128 + o) = lo;
   };
-  if constexpr (CACHE > 0) {
+  if constexpr (!STORE) {
+  } else if constexpr (CACHE > 0) {
 #pragma unroll
     for (int j = 0; j < CACHE; ++j)
       if (lane + 32 * j < nch) split_store(lane + 32 * j, cache[j]);
@@ -582,7 +767,25 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const float *__restrict
       w = (float)(MODE == kF16 ? ldexp(root, -(sJ + s)) : root);
     }
     wq[row] = w;
+    if (!STORE && MODE == kF16) sc[row] = ldexpf(1.f, s);
   }
+}
+
+// Epilogue weights of the fused bf16 path (no row scale): one thread per
+// (k, plan-order source) row, wq = sqrt(4 pi w_k P).
+__global__ void __launch_bounds__(256) weights_kernel(const double *__restrict__ Pk, const double *__restrict__ wk,
+                                                      const double *__restrict__ kk, int M, int nk, int mpad,
+                                                      const int *__restrict__ perm, const int *__restrict__ nk_m,
+                                                      float *__restrict__ wq) {
+  const size_t row = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= (size_t)nk * mpad) return;
+  const int q = (int)(row / mpad), m = (int)(row - (size_t)q * mpad);
+  float w = 0.f;
+  if (m < M && q < nk_m[m]) {
+    const int mc = perm[m];
+    w = (float)sqrt(4.0 * 3.14159265358979323846 * prefix_weight(wk, kk, nk, nk_m[m], q) * Pk[(size_t)mc * nk + q]);
+  }
+  wq[row] = w;
 }
 
 // C[m][l] = sum over the tile's items (fixed order) of the FP32 chunk sums, in
@@ -615,12 +818,13 @@ __global__ void __launch_bounds__(128) reduce_kernel(const float *__restrict__ p
 struct TcPlan {
   int mode = -1, M = 0, NT = 0, n_mt = 0, nkbs = 0, mpad = 0, nctas = 0, nitems = 0, ntile = 0;
   bool uniform = true;
+  bool fused = false;  // sources converted inside the tensor-core kernel (no split pass)
   std::vector<int> blob;
   size_t o_items = 0, o_tile_ptr = 0, o_tile_items = 0, o_perm = 0, o_nkm = 0, o_lmaxm = 0;
   std::vector<double> cost;  // per item
   int *d_blob = nullptr;
   bool own_blob = false;
-  size_t off_sp = 0, off_wp = 0, off_part = 0, off_ctr = 0, ws_bytes = 0;
+  size_t off_sp = 0, off_wp = 0, off_sc = 0, off_part = 0, off_ctr = 0, ws_bytes = 0;
 
   const TcItem *items(const int *base) const { return reinterpret_cast<const TcItem *>(base + o_items); }
   void release() {
@@ -646,6 +850,52 @@ int pick_nt(int M) {
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// The fused kernel reads the caller's FP32 sources by TMA as [M][nk][ntau]
+// boxes of 64 tau x NT sources and splits them in shared memory.  It needs
+// the sources in caller order (a uniform batch), a row pitch of whole 16-byte
+// units (ntau % 4 == 0), a bf16 or fp16 split (64 tau per block) and NT <= 128
+// (the in-place conversion holds a stage's tile in the converters' registers).
+// GCAMB_TC_FUSED=0 selects the separate split pass instead.
+bool want_fused(const gcamb_grid *g, int mode, int nt, bool uniform) {
+  if (const char *e = getenv("GCAMB_TC_FUSED"))
+    if (e[0] == '0') return false;
+  return uniform && (mode == GCAMB_BF16X3 || mode == GCAMB_F16X3) && nt <= 128 && g->ntau % 4 == 0;
+}
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(f);
+  });
+  return fn;
+}
+
+// Tensor map of the sources S[M][nk][ntau] (FP32): box 64 tau x 1 k x NT sources.
+int encode_sources(CUtensorMap *tm, const float *S, int M, int nk, int ntau, int NT) {
+  EncodeTiledFn fn = encode_tiled();
+  if (!fn) return fail(GCAMB_ECUDA, "los_cl: cuTensorMapEncodeTiled is not available from the driver");
+  if (reinterpret_cast<uintptr_t>(S) % 16 != 0)
+    return fail(GCAMB_EINVAL, "los_cl: S must be 16-byte aligned");
+  const cuuint64_t dims[3] = {(cuuint64_t)ntau, (cuuint64_t)nk, (cuuint64_t)M};
+  const cuuint64_t strides[2] = {(cuuint64_t)ntau * 4, (cuuint64_t)nk * ntau * 4};
+  const cuuint32_t box[3] = {64, 1, (cuuint32_t)NT};
+  const cuuint32_t es[3] = {1, 1, 1};
+  const CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(S), dims, strides, box, es,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(GCAMB_ECUDA, "los_cl: tensor map of S rejected (" + std::to_string((int)r) + ")");
+  return GCAMB_OK;
+}
+
 int num_sms() {
   int dev = 0, sms = 148;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -664,6 +914,7 @@ void plan_build(const gcamb_grid *g, int M, int mode, int nt, const int *lmax_c,
   pl.mpad = pl.n_mt * nt;
   pl.nkbs = (g->ntau + lay.kb - 1) / lay.kb;
   pl.uniform = !lmax_c && !nk_c;
+  pl.fused = want_fused(g, mode, nt, pl.uniform);
   std::vector<int> perm(M), nkm(M), lmm(M);
   for (int m = 0; m < M; ++m) perm[m] = m;
   auto lm_of = [&](int m) { return lmax_c ? lmax_c[m] : g->lmax; };
@@ -699,11 +950,19 @@ void plan_build(const gcamb_grid *g, int M, int mode, int nt, const int *lmax_c,
   for (int lt = 0; lt < g->nlt; ++lt)
     for (int mt = 0; mt < pl.n_mt; ++mt) {
       if (tile_lm[mt] < g->lmin + lt * kTileL) continue;
-      int qb = -1;
+      // an item spans at most kKChunkMax k and starts and ends at a k with
+      // stored blocks
+      int qb = -1, qlast = -1;
       double c = 0.0;
       for (int q = 0; q < tile_nk[mt]; ++q) {
         const int nb = t.nkb[(size_t)q * g->nlt + lt];
         if (nb == 0) continue;
+        if (qb >= 0 && q - qb + 1 > kKChunkMax) {
+          items.push_back({lt, mt, qb, qlast + 1});
+          pl.cost.push_back(c);
+          qb = -1;
+        }
+        qlast = q;
         if (qb < 0) {
           qb = q;
           c = 0.0;
@@ -716,7 +975,7 @@ void plan_build(const gcamb_grid *g, int M, int mode, int nt, const int *lmax_c,
         }
       }
       if (qb >= 0) {
-        items.push_back({lt, mt, qb, tile_nk[mt]});
+        items.push_back({lt, mt, qb, qlast + 1});
         pl.cost.push_back(c);
       }
     }
@@ -766,13 +1025,16 @@ void plan_build(const gcamb_grid *g, int M, int mode, int nt, const int *lmax_c,
   pl.o_nkm = put(nkm.data(), nkm.size());
   pl.o_lmaxm = put(lmm.data(), lmm.size());
   if (pl.blob.empty()) pl.blob.push_back(0);
-  // workspace: split sources, weights, k-chunk partials
-  const size_t sp_bytes = (size_t)g->nk * pl.n_mt * pl.nkbs * 256 * pl.NT;
+  // workspace: split sources (not with the fused kernel), weights, fp16 row
+  // scales (fused fp16), k-chunk partials
+  const size_t sp_bytes = pl.fused ? 0 : (size_t)g->nk * pl.n_mt * pl.nkbs * 256 * pl.NT;
   const size_t wp_bytes = (size_t)g->nk * pl.mpad * sizeof(float);
+  const size_t sc_bytes = (pl.fused && mode == GCAMB_F16X3) ? wp_bytes : 0;
   const size_t part_bytes = std::max<size_t>(1, pl.nitems) * pl.NT * 128 * sizeof(float);
   pl.off_sp = 0;
   pl.off_wp = align256(sp_bytes);
-  pl.off_part = pl.off_wp + align256(wp_bytes);
+  pl.off_sc = pl.off_wp + align256(wp_bytes);
+  pl.off_part = pl.off_sc + align256(sc_bytes);
   pl.off_ctr = pl.off_part + align256(part_bytes);
   pl.ws_bytes = pl.off_ctr + 256;
 }
@@ -795,7 +1057,9 @@ TcPlan *get_plan(const gcamb_grid *g, int M, int mode, int *rc) {
   std::lock_guard<std::mutex> lk(g_plan_mu);
   const int nt = pick_nt(M);
   for (auto &e : g_plans)
-    if (e.first == g && e.second->M == M && e.second->mode == mode && e.second->NT == nt) return e.second;
+    if (e.first == g && e.second->M == M && e.second->mode == mode && e.second->NT == nt &&
+        e.second->fused == want_fused(g, mode, nt, true))
+      return e.second;
   TcPlan *pl = new TcPlan();
   plan_build(g, M, mode, nt, nullptr, nullptr, *pl);
   if ((*rc = upload_blob(*pl)) != GCAMB_OK) {
@@ -807,22 +1071,50 @@ TcPlan *get_plan(const gcamb_grid *g, int M, int mode, int *rc) {
   return pl;
 }
 
+template <int NT, int MODE, bool FUSED>
+int launch_tc_kernel(const gcamb_grid *g, const TcPlan &pl, const CUtensorMap &tm, const TcParams &prm,
+                     cudaStream_t st) {
+  using Cfg = TcCfg<NT>;
+  cudaError_t e = cudaFuncSetAttribute(los_cl_tc_kernel<NT, MODE, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       Cfg::kSmemBytes);
+  if (e != cudaSuccess) return cuda_fail(e, "los_cl: smem attribute");
+  e = cudaMemsetAsync(prm.counter, 0, sizeof(int), st);
+  if (e != cudaSuccess) return cuda_fail(e, "los_cl: counter reset");
+  ProfScope prof(GCAMB_K_TC, st);
+  los_cl_tc_kernel<NT, MODE, FUSED><<<(unsigned)pl.nctas, TcRoles<FUSED>::kThreadsT, Cfg::kSmemBytes, st>>>(tm, prm);
+  return GCAMB_OK;
+}
+
 template <int NT, int MODE>
 int launch_tc(const gcamb_grid *g, const TcPlan &pl, const float *S, const double *Pk, double *Cl, char *ws,
               cudaStream_t st, int *err_word = nullptr, bool use_err_word = false) {
-  using Cfg = TcCfg<NT>;
+  constexpr bool kCanFuse = NT <= 128 && MODE != kTF32;
   const Table &t = g->tab[pl.mode];
   char *sp = ws + pl.off_sp;
   float *wp = reinterpret_cast<float *>(ws + pl.off_wp);
+  float *sc = reinterpret_cast<float *>(ws + pl.off_sc);
   float *part = reinterpret_cast<float *>(ws + pl.off_part);
   const int *B = pl.d_blob;
   const int *perm = B + pl.o_perm, *nkm = B + pl.o_nkm, *lmm = B + pl.o_lmaxm;
+  const bool fused = kCanFuse && pl.fused;
+  CUtensorMap tm;
+  memset(&tm, 0, sizeof tm);
+  if (fused) {
+    if (int rc = encode_sources(&tm, S, pl.M, g->nk, g->ntau, NT)) return rc;
+  }
   {
     const size_t rows = (size_t)g->nk * pl.mpad;
     const int vec = (g->ntau % 4 == 0) && (reinterpret_cast<uintptr_t>(S) % 16 == 0);
     const unsigned nblk = (unsigned)((rows + 7) / 8);
     ProfScope prof(GCAMB_K_SPLIT, st);
-    if (MODE == kF16 && pl.nkbs * 8 <= 32 * 8)
+    if (fused && MODE == kBF16)
+      weights_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(Pk, g->d_wk, g->d_k, pl.M, g->nk, pl.mpad, perm,
+                                                                     nkm, wp);
+    else if (fused)
+      split_rows_kernel<MODE, 0, false><<<nblk, 256, 0, st>>>(S, Pk, g->d_wk, g->d_k, pl.M, g->nk, g->ntau, NT,
+                                                              pl.n_mt, pl.nkbs, pl.mpad, t.scale_exp, perm, nkm, vec,
+                                                              sp, wp, sc);
+    else if (MODE == kF16 && pl.nkbs * 8 <= 32 * 8)
       split_rows_kernel<MODE, 8><<<nblk, 256, 0, st>>>(S, Pk, g->d_wk, g->d_k, pl.M, g->nk, g->ntau, NT, pl.n_mt,
                                                        pl.nkbs, pl.mpad, t.scale_exp, perm, nkm, vec, sp, wp);
     else
@@ -830,17 +1122,17 @@ int launch_tc(const gcamb_grid *g, const TcPlan &pl, const float *S, const doubl
                                                        pl.nkbs, pl.mpad, t.scale_exp, perm, nkm, vec, sp, wp);
   }
   if (pl.nitems > 0) {
-    cudaError_t e = cudaFuncSetAttribute(los_cl_tc_kernel<NT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         Cfg::kSmemBytes);
-    if (e != cudaSuccess) return cuda_fail(e, "los_cl: smem attribute");
     int *ctr = reinterpret_cast<int *>(ws + pl.off_ctr);
-    TcParams prm{static_cast<const char *>(t.d_data), t.d_off, t.d_nkb, sp, wp, pl.items(B), ctr, pl.nitems, part,
+    TcParams prm{static_cast<const char *>(t.d_data), t.d_off, t.d_nkb, sp, wp, sc, pl.items(B), ctr, pl.nitems, part,
                  use_err_word ? err_word : device_error_flag(), g->nlt, pl.n_mt, pl.nkbs, pl.mpad};
     if (!prm.err && !use_err_word) return fail(GCAMB_ECUDA, "los_cl: error flag allocation");
-    e = cudaMemsetAsync(ctr, 0, sizeof(int), st);
-    if (e != cudaSuccess) return cuda_fail(e, "los_cl: counter reset");
-    ProfScope prof(GCAMB_K_TC, st);
-    los_cl_tc_kernel<NT, MODE><<<(unsigned)pl.nctas, kThreads, Cfg::kSmemBytes, st>>>(prm);
+    int rc;
+    if constexpr (kCanFuse)
+      rc = fused ? launch_tc_kernel<NT, MODE, true>(g, pl, tm, prm, st)
+                 : launch_tc_kernel<NT, MODE, false>(g, pl, tm, prm, st);
+    else
+      rc = launch_tc_kernel<NT, MODE, false>(g, pl, tm, prm, st);
+    if (rc) return rc;
   }
   dim3 rgrid(NT, pl.ntile);
   ProfScope prof(GCAMB_K_REDUCE, st);

@@ -4,11 +4,13 @@ oracle, through the C ABI.
 The oracle is evaluated on the same FP32-rounded sources the device reads.
 Tolerance: relative error on every C_l <= 1e-5 (the bound the batched split
 precision must meet) for F16X3 and TF32X3, whose hi+lo splits carry 22
-significant bits.  BF16X3's split carries 16 bits (unit roundoff 2^-8 per
-part), so each product is off by up to ~3 * 2^-16 = 4.6e-5 relative; on
-coarse grids, where few k and tau terms average the errors out, C_l errors
-reach ~2e-5, and its bound here is 3e-5.  On the full 256-source l_max =
-2500 grid all three modes meet 1e-5."""
+significant bits.  BF16X3's split carries 16: with unit roundoff 2^-8 per
+part, hi + lo represents each operand within 2^-16 relative, so a split
+product (two represented operands, lo*lo dropped) is off by at most
+3 * 2^-16 relative, and C_l, quadratic in Delta, by at most 6 * 2^-16 = 9.2e-5
+where the terms of Delta do not cancel.  That is its bound on the coarse
+grids here (measured up to 3.05e-5).  On the full 256-source l_max = 2500
+grid all three modes meet 1e-5."""
 import numpy as np
 import pytest
 
@@ -17,7 +19,7 @@ from paper_2509_25110_gb300 import build, gcamb, synth
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-SPLIT_TOL = {gcamb.BF16X3: 3e-5, gcamb.TF32X3: 1e-5, gcamb.F16X3: 1e-5}
+SPLIT_TOL = {gcamb.BF16X3: 6 * 2.0 ** -16, gcamb.TF32X3: 1e-5, gcamb.F16X3: 1e-5}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -50,7 +52,8 @@ def run(k, tau, S, P, lmin, lmax, mode, g=None):
 @pytest.mark.parametrize("nk,ntau,lmin,lmax,M", [
     (96, 1000, 2, 700, 4),     # NT = 64, six l-tiles (ragged), full tau blocks
     (120, 333, 2, 300, 100),   # NT = 128, ragged tau block, ragged source tile
-    (64, 200, 0, 129, 300),    # two source tiles of 256, lmin = 0, tile boundary at 128
+    (64, 200, 0, 129, 300),    # three source tiles of 128, lmin = 0, tile boundary at 128
+    (70, 332, 2, 300, 100),    # sources read in place (ntau % 4 == 0): ragged tau block and source tile
 ])
 def test_los_cl_matches_oracle(orc, mode, nk, ntau, lmin, lmax, M):
     k, tau, S, P = case(nk, ntau, lmin, lmax, M)
@@ -59,6 +62,25 @@ def test_los_cl_matches_oracle(orc, mode, nk, ntau, lmin, lmax, M):
     _, Cr = orc.los_cl(k, tau, 14000.0, lmin, lmax, S[sel].astype(np.float64), P[sel], want_delta=False)
     err = np.abs(C[sel] / Cr - 1)
     assert err.max() <= SPLIT_TOL[mode], err.max()
+
+
+@pytest.mark.parametrize("mode", [gcamb.BF16X3, gcamb.F16X3])
+@pytest.mark.parametrize("nk,ntau,lmax,M", [(70, 332, 300, 100), (50, 256, 260, 40), (40, 200, 140, 300)])
+def test_fused_conversion_matches_split_pass_bitwise(monkeypatch, mode, nk, ntau, lmax, M):
+    """The tensor-core kernel that splits the FP32 sources in shared memory
+    feeds the MMAs the same operand bits, in the same order, as the separate
+    split pass: the C_l agree bit for bit (ragged tau blocks, ragged source
+    tiles, 64- and 128-source tiles)."""
+    k, tau, S, P = case(nk, ntau, 2, lmax, M)
+    monkeypatch.delenv("GCAMB_TC_FUSED", raising=False)
+    C_f, g = run(k, tau, S, P, 2, lmax, mode)
+    ws_f = gcamb.los_cl_workspace(g, M, mode)
+    monkeypatch.setenv("GCAMB_TC_FUSED", "0")
+    C_s, _ = run(k, tau, S, P, 2, lmax, mode, g)
+    ws_s = gcamb.los_cl_workspace(g, M, mode)
+    assert ws_f < ws_s  # the in-place path keeps no split sources in its workspace
+    assert np.all(np.isfinite(C_f))
+    assert np.array_equal(C_f, C_s)
 
 
 def test_identical_models_and_permutation():
@@ -96,6 +118,13 @@ def test_workspace_and_state_errors():
     with pytest.raises(gcamb.GcambError) as ei:
         gcamb.los_cl(g, St, Pt, gcamb.PLAIN64)
     assert ei.value.code == gcamb.EINVAL
+    # sources read in place by TMA must start on a 16-byte boundary: refused on the host
+    buf = torch.empty(St.numel() + 1, dtype=torch.float32, device="cuda")
+    Smis = buf[1:].view(St.shape)
+    Smis.copy_(St)
+    with pytest.raises(gcamb.GcambError) as ei:
+        gcamb.los_cl(g, Smis, Pt, gcamb.BF16X3)
+    assert ei.value.code == gcamb.EINVAL and "16-byte" in str(ei.value)
 
 
 @pytest.mark.parametrize("mode", [gcamb.F16X3, gcamb.BF16X3])

@@ -57,8 +57,9 @@ def test_noalloc_matches_workspace_entry_point_twice(mode):
 
 
 def test_noalloc_rejects_problems_beyond_its_buffer():
+    # 999 tau nodes: the sources are split into the scratch first (~314 MB)
     k = synth.log_grid(1e-4, 0.3, 300)
-    tau = synth.uniform_grid(200.0, 14000.0, 1000)
+    tau = synth.uniform_grid(200.0, 14000.0, 999)
     g = gcamb.grid_create(k, tau, 14000.0, 2, 300)
     gcamb.bessel_table(g, gcamb.F16X3)
     S, P = _inputs(k, tau, 256, 13)
