@@ -6,13 +6,15 @@ plain FP64, relative error <= 1e-5), on the batched workload: 256 sources
 sharing one grid, l = 2..2500, 2000 k log-spaced on [1e-4, 0.3] 1/Mpc, 1000
 tau uniform on [200, 14000] Mpc, synthetic sources (paper_2509_25110_gb300.synth).
 
-One step = one pass of the batched path over one batch of 256 sources:
-hi/lo split of the sources, the tensor-core tau-contraction + square + k-chunk
-sum, and the FP64 reduction to C_l (gcamb_los_cl).  The grid's Bessel table is
+One step = one pass of the batched path over one batch of 256 sources
+(gcamb_los_cl): the epilogue weights (and, for fp16, the sources' row
+scales), the tensor-core kernel that splits the FP32 sources into hi/lo
+planes in shared memory and does the tau-contraction + square + k-chunk sum,
+and the FP64 reduction to C_l.  The grid's Bessel table is
 built once per grid before the timed region (its build time is reported in
 `config`).  Inputs (2.0 GB of sources, a 3.3 GB table) are larger than L2.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--mode f16x3|bf16x3|tf32x3]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--mode bf16x3|f16x3|tf32x3]
   python bench.py --impl reference ...   (the FP64 CPU oracle, timed on the host)
 
 Under torchrun every rank runs its own batch (weak scaling, no collective on
@@ -44,7 +46,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=600)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="f16x3")
+    ap.add_argument("--mode", default="bf16x3")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-models", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -381,7 +383,9 @@ def main():
     tc_ms, tc_n = kern["los_cl_tc"]
     tc_avg_s = tc_ms / max(1, tc_n) * 1e-3
     pair = 8 if mode == gcamb.TF32X3 else 4            # bytes of one hi+lo table entry
-    alg_bytes = info["active"] * pair + M * wl.nk * wl.ntau * pair   # table entries + split sources, once each
+    # active table entries (hi + lo) and the sources once (FP32, read by the
+    # fused kernel; the split pass's hi + lo planes for tf32x3: 8 bytes)
+    alg_bytes = info["active"] * pair + M * wl.nk * wl.ntau * pair
     alg_flops = 3 * 2 * info["active"] * M                             # three split products
     achieved_gbs = alg_bytes / tc_avg_s / 1e9
     traffic = None

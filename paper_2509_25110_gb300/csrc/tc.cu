@@ -224,7 +224,7 @@ struct TcCfg {
   static constexpr int kSmemBytes =
       kStages * kStageBytes + kKSlots * kSlotBytes + kQBytes + 1024 /*align*/ + 256 /*barriers*/;
   static constexpr int kColsPerThread = NT / 2;
-  static constexpr int kChunk = NT >= 256 ? 8 : 16;      // TMEM load width (register budget)
+  static constexpr int kChunk = NT >= 128 ? 8 : 16;      // TMEM load width (register budget)
 };
 
 template <bool FUSED>
@@ -647,16 +647,13 @@ __device__ __forceinline__ double prefix_weight(const double *__restrict__ wk, c
 // [2^13, 2^14) (fp16 keeps 11 significant bits only in its normal range).
 // Lane 0 writes the row's epilogue weight wq = sqrt(4 pi w_k P) 2^-(sJ + s),
 // with the source's own k weights; (wq D')^2 is then the unscaled term.
-// With STORE false (fused kernel) nothing is split: only wq is written, and
-// for fp16 the row scale 2^s that the converters apply, into sc.
-template <int MODE, int CACHE, bool STORE = true>
+template <int MODE, int CACHE>
 __global__ void __launch_bounds__(256) split_rows_kernel(const float *__restrict__ S, const double *__restrict__ Pk,
                                                          const double *__restrict__ wk, const double *__restrict__ kk,
                                                          int M, int nk, int ntau, int NT, int n_mt, int nkbs,
                                                          int mpad, int sJ, const int *__restrict__ perm,
                                                          const int *__restrict__ nk_m, int vec,
-                                                         char *__restrict__ sp, float *__restrict__ wq,
-                                                         float *__restrict__ sc = nullptr) {
+                                                         char *__restrict__ sp, float *__restrict__ wq) {
   constexpr int EPC = MODE == kTF32 ? 4 : 8;  // elements per 16-byte chunk
   const int lane = threadIdx.x & 31;
   const size_t row = (size_t)blockIdx.x * 8 + (threadIdx.x >> 5);  // q * mpad + m
@@ -701,6 +698,15 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const float *__restrict
 #pragma unroll
         for (int u = 0; u < EPC; ++u)
           if (lane + 32 * j < nch) mx = fmaxf(mx, fabsf(cache[j][u]));
+    } else if (live && vec) {
+      // 16-byte loads, eight in flight per lane
+      const float4 *s4 = reinterpret_cast<const float4 *>(src);
+      const int n4 = ntau >> 2;
+#pragma unroll 8
+      for (int c = lane; c < n4; c += 32) {
+        const float4 f = __ldg(s4 + c);
+        mx = fmaxf(mx, fmaxf(fmaxf(fabsf(f.x), fabsf(f.y)), fmaxf(fabsf(f.z), fabsf(f.w))));
+      }
     } else if (live) {
       for (int t = lane; t < ntau; t += 32) mx = fmaxf(mx, fabsf(__ldg(src + t)));
     }
@@ -747,8 +753,7 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const float *__restrict
     *reinterpret_cast<uint4 *>(blk + o) = hi;
     *reinterpret_cast<uint4 *>(blk + NT * 128 + o) = lo;
   };
-  if constexpr (!STORE) {
-  } else if constexpr (CACHE > 0) {
+  if constexpr (CACHE > 0) {
 #pragma unroll
     for (int j = 0; j < CACHE; ++j)
       if (lane + 32 * j < nch) split_store(lane + 32 * j, cache[j]);
@@ -767,7 +772,48 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const float *__restrict
       w = (float)(MODE == kF16 ? ldexp(root, -(sJ + s)) : root);
     }
     wq[row] = w;
-    if (!STORE && MODE == kF16) sc[row] = ldexpf(1.f, s);
+  }
+}
+
+// Row scales and epilogue weights of the fused fp16 path (a uniform batch,
+// sources in caller order): one warp per (source, k) row, taken in memory
+// order so that the 4 KB rows stream; 16-byte loads when vec.  Same scale
+// rule as the split pass: 2^s with the row's largest |S| in [2^13, 2^14),
+// s clamped to [-40, 80]; wq = sqrt(4 pi w_k P) 2^-(sJ + s).
+__global__ void __launch_bounds__(256) rowscale_kernel(const float *__restrict__ S, const double *__restrict__ Pk,
+                                                       const double *__restrict__ wk, int M, int nk, int ntau,
+                                                       int mpad, int sJ, int vec, float *__restrict__ wq,
+                                                       float *__restrict__ sc) {
+  const int lane = threadIdx.x & 31;
+  const size_t r = (size_t)blockIdx.x * 8 + (threadIdx.x >> 5);  // m * nk + q
+  if (r >= (size_t)M * nk) return;
+  const int m = (int)(r / nk), q = (int)(r - (size_t)m * nk);
+  const float *src = S + r * ntau;
+  float mx = 0.f;
+  if (vec) {
+    const float4 *s4 = reinterpret_cast<const float4 *>(src);
+    const int n4 = ntau >> 2;
+#pragma unroll 8
+    for (int c = lane; c < n4; c += 32) {
+      const float4 f = __ldg(s4 + c);
+      mx = fmaxf(mx, fmaxf(fmaxf(fabsf(f.x), fabsf(f.y)), fmaxf(fabsf(f.z), fabsf(f.w))));
+    }
+  } else {
+    for (int t = lane; t < ntau; t += 32) mx = fmaxf(mx, fabsf(__ldg(src + t)));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) {
+    int s = 0;
+    if (mx > 0.f) {
+      int e;
+      frexpf(mx, &e);
+      s = 14 - e;
+      s = s < -40 ? -40 : (s > 80 ? 80 : s);
+    }
+    const double root = sqrt(4.0 * 3.14159265358979323846 * wk[q] * Pk[r]);
+    wq[(size_t)q * mpad + m] = (float)ldexp(root, -(sJ + s));
+    sc[(size_t)q * mpad + m] = ldexpf(1.f, s);
   }
 }
 
@@ -1110,10 +1156,16 @@ int launch_tc(const gcamb_grid *g, const TcPlan &pl, const float *S, const doubl
     if (fused && MODE == kBF16)
       weights_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(Pk, g->d_wk, g->d_k, pl.M, g->nk, pl.mpad, perm,
                                                                      nkm, wp);
-    else if (fused)
-      split_rows_kernel<MODE, 0, false><<<nblk, 256, 0, st>>>(S, Pk, g->d_wk, g->d_k, pl.M, g->nk, g->ntau, NT,
-                                                              pl.n_mt, pl.nkbs, pl.mpad, t.scale_exp, perm, nkm, vec,
-                                                              sp, wp, sc);
+    else if (fused) {
+      // rows beyond M (the last tile's padding sources) get zero weights and scales
+      if (pl.mpad > pl.M) {
+        cudaError_t e = cudaMemsetAsync(wp, 0, (size_t)g->nk * pl.mpad * sizeof(float), st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(sc, 0, (size_t)g->nk * pl.mpad * sizeof(float), st);
+        if (e != cudaSuccess) return cuda_fail(e, "los_cl: weight reset");
+      }
+      rowscale_kernel<<<(unsigned)(((size_t)pl.M * g->nk + 7) / 8), 256, 0, st>>>(
+          S, Pk, g->d_wk, pl.M, g->nk, g->ntau, pl.mpad, t.scale_exp, vec, wp, sc);
+    }
     else if (MODE == kF16 && pl.nkbs * 8 <= 32 * 8)
       split_rows_kernel<MODE, 8><<<nblk, 256, 0, st>>>(S, Pk, g->d_wk, g->d_k, pl.M, g->nk, g->ntau, NT, pl.n_mt,
                                                        pl.nkbs, pl.mpad, t.scale_exp, perm, nkm, vec, sp, wp);
