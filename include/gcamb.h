@@ -351,7 +351,8 @@ int gcamb_synth_sources(const gcamb_grid *g, const float *X, int M, float *S, do
  * holds until the process exits.  The call makes no cudaMalloc, cudaFree or
  * other allocating call.
  *   status   device int, or NULL: set to GCAMB_ETIMEOUT if a bounded wait
- *            on the device gave up (left untouched otherwise)
+ *            on the device gave up (left untouched otherwise); with NULL
+ *            the timeout is reported by the next gcamb_sync instead
  * Limits and behaviour:
  *  - Problems whose scratch exceeds 64 MiB are rejected with GCAMB_EINVAL
  *    (the message gives the bytes needed); use gcamb_los_cl for them.  The
@@ -409,6 +410,18 @@ int gcamb_profile_read(int kernel, double *total_ms, int64_t *launches);
  * rate in FLOP/s (2 per FMA) to *flops (host).  Synchronous.
  */
 int gcamb_probe_flops(int what, double *flops);
+
+/*
+ * Self-test of the device-side failure path (no counterpart in the paper).
+ * Launches one thread that waits, with the bounded wait every tensor-core
+ * kernel of the library uses, on an mbarrier that nothing ever arrives on.
+ * After the wait limit (one second) it gives up and reports GCAMB_ETIMEOUT
+ * exactly as a stalled kernel would: in *status (device int) if status is not
+ * NULL, else through the library's error flag, so that the next
+ * gcamb_sync(stream) returns GCAMB_ETIMEOUT.  Nothing faults, traps or
+ * hangs; the CUDA context stays usable.  Asynchronous on `stream`.
+ */
+int gcamb_selftest_wait(int *status, void *stream);
 
 #ifdef __cplusplus
 }

@@ -429,4 +429,6 @@ int gcamb_probe_flops(int what, double *flops) {
   return run_probe_flops(what, flops);
 }
 
+int gcamb_selftest_wait(int *status, void *stream) { return run_wait_selftest(status, (cudaStream_t)stream); }
+
 }  // extern "C"

@@ -16,6 +16,8 @@
 
 #include <cstdint>
 
+#include "mbar.cuh"
+
 namespace gcamb {
 namespace emu {
 
@@ -41,36 +43,6 @@ struct GemmArgs {
   const float *Zprev;  // kDGelu: C *= GELU'(Zprev), [M][ldc]
   int *err;
 };
-
-__device__ __forceinline__ uint32_t e_smem(const void *p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ bool e_try(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ bool e_wait(uint32_t bar, uint32_t parity, int *err) {
-  uint64_t t0 = 0;
-  for (uint32_t n = 1;; ++n) {
-    if (e_try(bar, parity)) return true;
-    if ((n & 255u) == 0) {
-      uint64_t now;
-      asm volatile("mov.u64 %0, %globaltimer;" : "=l"(now));
-      if (t0 == 0) t0 = now;
-      else if (now - t0 > 1000000000ull) {
-        if (err) *reinterpret_cast<volatile int *>(err) = 1;
-        return false;
-      }
-    }
-  }
-}
 
 __device__ __forceinline__ uint64_t e_desc(uint32_t saddr) {
   return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
@@ -135,7 +107,7 @@ __global__ void __launch_bounds__(128, 1) gemm_kernel(GemmArgs a) {
   // [buf0: A 16 KB | B 16 KB][buf1: A | B][barriers]
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + 65536);
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 3);
-  const uint32_t done0 = e_smem(bars), fin = e_smem(bars + 2);
+  const uint32_t done0 = smem_u32(bars), fin = smem_u32(bars + 2);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i0 = blockIdx.x * 128, n0 = blockIdx.y * 128;
   if (threadIdx.x == 0) {
@@ -145,7 +117,7 @@ __global__ void __launch_bounds__(128, 1) gemm_kernel(GemmArgs a) {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(e_smem(tmem_slot))
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(smem_u32(tmem_slot))
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -164,7 +136,7 @@ __global__ void __launch_bounds__(128, 1) gemm_kernel(GemmArgs a) {
   for (int kc = 0; kc < nkc && ok; ++kc) {
     const int buf = kc & 1;
     bool w = true;
-    if (kc >= 2) w = e_wait(done0 + 8 * buf, (uint32_t)((kc - 2) >> 1) & 1u, a.err);
+    if (kc >= 2) w = mbar_wait(done0 + 8 * buf, (uint32_t)((kc - 2) >> 1) & 1u, nullptr, a.err);
     // every thread takes the same branch (no thread may be left at a barrier)
     if (!__syncthreads_and(w)) {
       ok = false;
@@ -178,7 +150,7 @@ __global__ void __launch_bounds__(128, 1) gemm_kernel(GemmArgs a) {
     __syncthreads();
     if (threadIdx.x == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t sa = e_smem(ta), sb = e_smem(tb);
+      const uint32_t sa = smem_u32(ta), sb = smem_u32(tb);
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk) {
         const uint64_t da = e_desc(sa + kk * 32), db = e_desc(sb + kk * 32);
@@ -195,7 +167,7 @@ __global__ void __launch_bounds__(128, 1) gemm_kernel(GemmArgs a) {
   // all MMAs done (also on the error path, before TMEM is freed)
   if (threadIdx.x == 0)
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(fin) : "memory");
-  const bool fin_ok = e_wait(fin, 0, a.err);
+  const bool fin_ok = mbar_wait(fin, 0, nullptr, a.err);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (ok && fin_ok) {
     const int i = i0 + warp * 32 + lane;

@@ -75,8 +75,9 @@ int fail(int code, const std::string &msg);
 int cuda_fail(cudaError_t e, const char *what);
 int *device_error_flag();  // device pointer of the mapped error word
 
-// Device-side error codes written to the flag word.
-constexpr int kDevErrTimeout = 1;
+// Device-side error code written to the flag word (or a caller's status
+// word) when a bounded wait gives up: the public status itself.
+constexpr int kDevErrTimeout = GCAMB_ETIMEOUT;
 
 int ensure_device_grid(gcamb_grid *g);
 
@@ -100,6 +101,7 @@ int launch_los_cl_fixed(const gcamb_grid *g, const float *S, const double *Pk, i
 
 // Probes (probe.cu).
 int run_probe_flops(int what, double *flops);
+int run_wait_selftest(int *status, cudaStream_t st);
 
 // Event tracer: brackets one kernel launch when profiling is on.
 struct ProfScope {

@@ -2,6 +2,7 @@
 // and FP32 CUDA-core kernels).  Eight independent FMA chains per thread keep
 // the pipe busy; the grid covers every SM several times over.
 #include "internal.h"
+#include "mbar.cuh"
 
 namespace gcamb {
 
@@ -55,6 +56,27 @@ static int probe_t(double *flops) {
 
 int run_probe_flops(int what, double *flops) {
   return what == 0 ? probe_t<double>(flops) : probe_t<float>(flops);
+}
+
+// One thread waits, with the kernels' bounded wait, on an mbarrier that no
+// one arrives on: after the wait limit it writes GCAMB_ETIMEOUT to *err and
+// the kernel ends.
+__global__ void wait_selftest_kernel(int *err) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_wait(smem_u32(&bar), 0, nullptr, err);
+  }
+}
+
+int run_wait_selftest(int *status, cudaStream_t st) {
+  int *err = status ? status : device_error_flag();
+  if (!err) return fail(GCAMB_ECUDA, "selftest_wait: error flag allocation");
+  wait_selftest_kernel<<<1, 32, 0, st>>>(err);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "selftest_wait: launch");
+  return GCAMB_OK;
 }
 
 }  // namespace gcamb

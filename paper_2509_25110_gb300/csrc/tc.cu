@@ -35,6 +35,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "mbar.cuh"
 
 namespace gcamb {
 
@@ -66,64 +67,6 @@ struct TcParams {
   int *err;
   int nlt, n_mt, nkbs, mpad;
 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ uint64_t globaltimer() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait.  abort_flag may be null (teardown drains wait on time only).
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *err) {
-  uint64_t t0 = 0;
-  for (uint32_t n = 1;; ++n) {
-    if (mbar_try(bar, parity)) return true;
-    if (abort_flag && *abort_flag) return false;
-    if ((n & 255u) == 0) {
-      const uint64_t now = globaltimer();
-      if (t0 == 0) t0 = now;
-      else if (now - t0 > 1000000000ull) {
-        if (abort_flag) *abort_flag = 1;
-        if (err) *reinterpret_cast<volatile int *>(err) = kDevErrTimeout;
-        return false;
-      }
-    }
-  }
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-               "l"(src), "r"(bytes), "r"(bar)
-               : "memory");
-}
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -1264,7 +1207,8 @@ int launch_los_cl_fixed(const gcamb_grid *g, const float *S, const double *Pk, i
   // plan may go out of scope when this function returns
   cudaError_t e = cudaMemcpyAsync(pl.d_blob, pl.blob.data(), pl.blob.size() * sizeof(int), cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "los_cl_noalloc: plan upload");
-  return launch_plan(g, pl, S, Pk, Cl, scratch + b_blob, st, status, true);
+  // without a status word a timeout is reported through the library's error flag
+  return launch_plan(g, pl, S, Pk, Cl, scratch + b_blob, st, status, status != nullptr);
 }
 
 void drop_plans(const gcamb_grid *g) {

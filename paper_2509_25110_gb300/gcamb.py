@@ -84,6 +84,7 @@ def lib():
     L.gcamb_profile_enable.argtypes = [ctypes.c_int]
     L.gcamb_profile_read.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
     L.gcamb_probe_flops.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    L.gcamb_selftest_wait.argtypes = [_vp, _vp]
     _lib = L
     return L
 
@@ -356,6 +357,16 @@ def probe_flops(what: int) -> float:
     f = ctypes.c_double()
     _check(lib().gcamb_probe_flops(int(what), ctypes.byref(f)))
     return float(f.value)
+
+
+def selftest_wait(status=None, stream=None):
+    """Device-side failure path self-test: a bounded wait on an mbarrier that
+    nothing arrives on gives up after one second and reports GCAMB_ETIMEOUT,
+    in `status` (device int32 tensor of one element) or, without it, through
+    the next sync()."""
+    import torch
+    st = _vp(None) if status is None else _dev(status, torch.int32, (1,), "status")
+    _check(lib().gcamb_selftest_wait(st, _stream(stream)))
 
 
 def profile_enable(on: bool = True):
