@@ -261,8 +261,11 @@ def run_emulator(args):
     build.build()
     wl = synth.workload(WORKLOAD)
     g = gcamb.grid_create(wl.k, wl.tau, wl.tau0, wl.lmin, wl.lmax)
-    steps = args.steps if args.steps != 600 else 3000
+    steps = args.steps if args.steps != 600 else 10000
     e, rep, (Xh, Ch) = emulator.train(g, steps=steps, log=lambda m: print(m, file=sys.stderr, flush=True))
+    acc = emulator.accuracy(e, Xh, Ch)
+    served = emulator.served_by_tolerance(e, Xh, Ch)
+    rep["check"] = gcamb.emu_check(e, Xh, Ch, tol=rep["tol"], min_count=32)  # the 1e-3 check serves below
     rates = emulator.serve_rates(e, g, Xh)
     line = {"metric": "emulator C_l spectra/sec at l_max=2500 (trusted cells, projection fallback)",
             "value": rates["emulate_spectra_per_s"], "unit": "spectra/s", "n_gpus": 1, "steps": steps,
@@ -271,7 +274,7 @@ def run_emulator(args):
             "config": {"workload": "emulator_lmax2500", "arch": "9-512-512-512-2499 GELU", "batch": rep["batch"],
                        "n_train": rep["n_train"], "n_hold": rep["n_hold"], "train_steps": steps,
                        "data_gen_s": rep["data_s"], "train_s": rep["train_s"], "check": rep["check"],
-                       "tol": rep["tol"], **rates,
+                       "tol": rep["tol"], "network_accuracy": acc, "served_fraction_by_tol": served, **rates,
                        "gain_network_vs_projection": rates["network_spectra_per_s"] / rates["projection_spectra_per_s"],
                        "final_loss": rep["loss_history"][-1][1]}}
     print(json.dumps(line), flush=True)
@@ -294,7 +297,7 @@ def main():
     import torch
     import torch.distributed as dist
 
-    from paper_2509_25110_gb300 import build, gcamb, synth
+    from paper_2509_25110_gb300 import build, gcamb, shard, synth
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -313,7 +316,7 @@ def main():
     if args.nk:
         wl.k = synth.log_grid(float(wl.k[0]), float(wl.k[-1]), args.nk)
     M = wl.M
-    p = synth.model_params(M, seed=rank)
+    p = shard.rank_params(M, rank)
     S = synth.sources_torch(wl.k, wl.tau, p, dev, torch.float32)
     P = torch.as_tensor(synth.primordial(wl.k, p), device=dev)
     g = gcamb.grid_create(wl.k, wl.tau, wl.tau0, wl.lmin, wl.lmax)
@@ -346,8 +349,7 @@ def main():
     except Exception:
         pass
     sampler = ClockSampler(bus)
-    if world > 1:
-        dist.barrier()
+    shard.barrier()
     torch.cuda.synchronize()
     gcamb.profile_enable(True)
     sampler.start()
@@ -360,8 +362,7 @@ def main():
     e1.synchronize()
     torch.cuda.synchronize()
     clocks = sampler.stop()
-    if world > 1:
-        dist.barrier()
+    shard.barrier()
     gcamb.sync()
     ms = e0.elapsed_time(e1)
     if args.kernel_only:
@@ -372,11 +373,8 @@ def main():
     kern = {gcamb.K_NAMES[i]: gcamb.profile_read(i) for i in (gcamb.K_SPLIT, gcamb.K_WEIGHTS, gcamb.K_TC,
                                                                gcamb.K_REDUCE)}
     gcamb.profile_enable(False)
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * M * args.steps / (ms * 1e-3)
+    ms = shard.max_over_ranks(ms, dev)
+    value = shard.job_rate(world, M, args.steps, ms)
     launches = sum(n for _, n in kern.values())
 
     # ---------------- roofline of the dominant kernel (tensor-core contraction)

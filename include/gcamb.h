@@ -281,10 +281,14 @@ int gcamb_emu_params(gcamb_emu *e, float *host_out, const float *host_in);
 int gcamb_emu_grads(gcamb_emu *e, float *host_out);
 /* Normalisation (host float arrays, n_in and n_out long): set = 1 writes
  * them, set = 0 reads them.  Inputs enter as (x - mu_x) / sd_x (sd_x = 0: the
- * feature is dropped), outputs leave as y sd_y + mu_y. */
+ * feature is dropped), outputs leave as log C_l = y sd_y + mu_y + (x_8 -
+ * mu_x[8]): C_l is proportional to A_s (Eq. 1 is linear in P), so the
+ * amplitude feature x_8 = ln(1e10 A_s) enters exactly, not through the
+ * network. */
 int gcamb_emu_norm(gcamb_emu *e, float *mu_x, float *sd_x, float *mu_y, float *sd_y, int set);
 /* Fits the normalisation on N training samples X[N][9], Cl[N][n_out] (>0)
- * and writes the standardised targets Y[N][n_out] = (log Cl - mu_y) / sd_y:
+ * and writes the standardised targets
+ * Y[N][n_out] = (log Cl - (x_8 - mu_x[8]) - mu_y) / sd_y:
  * mu_y per multipole; sd_y per multipole (per_l = 1) or one scale for all,
  * the root mean square of the per-multipole ones (per_l = 0, so that the loss
  * weighs the error of log C_l, i.e. the relative error of C_l, alike at every
@@ -311,7 +315,8 @@ int gcamb_emu_check(gcamb_emu *e, const float *X, const double *Cl_ref, int N, d
                     double *report, void *stream);
 /*
  * C_l[B][n_out] (double) for X[B][9]: requests in trusted cells from the
- * network (exp of the de-standardised output), the others (all of them before
+ * network (exp of the de-standardised output plus the amplitude term of
+ * gcamb_emu_norm), the others (all of them before
  * any check) from the batched projection, gcamb_los_cl in GCAMB_F16X3 on
  * sources regenerated by gcamb_synth_sources; used_fallback[B] (device int)
  * marks those.  Synchronises the stream; builds the F16X3 table if needed.

@@ -57,6 +57,9 @@ struct gcamb_emu {
   size_t fb_ws_bytes = 0;
 };
 
+// Column of the amplitude feature ln(1e10 A_s) in the 9-feature layout.
+static int amp_col(const gcamb_emu *e) { return e->n_in == 9 ? 8 : -1; }
+
 namespace {
 
 constexpr int kLossBlocks = 256;
@@ -202,9 +205,19 @@ __global__ void colstats_kernel(const float *__restrict__ X, int N, int n, float
   sd[j] = (float)sqrt(q / N);
 }
 
-__global__ void log_kernel(const double *__restrict__ C, size_t n, float *__restrict__ Y) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    Y[i] = (float)log(C[i]);
+// C_l is proportional to A_s (Eq. 1 is linear in P), so the amplitude
+// feature ln(1e10 A_s) (column amp of X, or none if amp < 0) enters log C_l
+// exactly as an additive term, relative to its training mean: the network
+// learns log C_l - (x_amp - mu_amp), and that term is added back on output.
+__device__ __forceinline__ double amp_shift(const float *__restrict__ X, int n_in, int amp,
+                                            const float *__restrict__ mu_x, size_t s) {
+  return amp < 0 ? 0.0 : (double)X[s * n_in + amp] - (double)mu_x[amp];
+}
+
+__global__ void log_kernel(const double *__restrict__ C, size_t N, int n, const float *__restrict__ X, int n_in,
+                           int amp, const float *__restrict__ mu_x, float *__restrict__ Y) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N * n; i += (size_t)gridDim.x * blockDim.x)
+    Y[i] = (float)(log(C[i]) - amp_shift(X, n_in, amp, mu_x, i / n));
 }
 
 __global__ void standardize_y_kernel(float *__restrict__ Y, size_t N, int n, const float *__restrict__ mu,
@@ -220,12 +233,14 @@ __global__ void inv_sd_kernel(const float *__restrict__ sd, int n, float *__rest
   if (j < n) isd[j] = sd[j] > 1e-12f ? 1.f / sd[j] : 0.f;
 }
 
-// C_l = exp(out sd + mu)
+// C_l = exp(out sd + mu + (x_amp - mu_amp))
 __global__ void exp_kernel(const float *__restrict__ out, size_t B, int n, const float *__restrict__ mu,
-                           const float *__restrict__ sd, double *__restrict__ C) {
+                           const float *__restrict__ sd, const float *__restrict__ X, int n_in, int amp,
+                           const float *__restrict__ mu_x, double *__restrict__ C) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < B * n; i += (size_t)gridDim.x * blockDim.x) {
     const int j = (int)(i % n);
-    C[i] = exp((double)out[i] * (double)(sd[j] > 0.f ? sd[j] : 1.f) + (double)mu[j]);
+    C[i] = exp((double)out[i] * (double)(sd[j] > 0.f ? sd[j] : 1.f) + (double)mu[j] +
+               amp_shift(X, n_in, amp, mu_x, i / n));
   }
 }
 
@@ -547,7 +562,7 @@ int gcamb_emu_fit_norm(gcamb_emu *e, const float *X, const double *Cl, int N, in
   colstats_kernel<<<1, 32, 0, st>>>(X, N, e->n_in, e->mu_x, sdx);
   inv_sd_kernel<<<1, 32, 0, st>>>(sdx, e->n_in, e->isd_x);
   const size_t n = (size_t)N * e->n_out;
-  log_kernel<<<1024, 256, 0, st>>>(Cl, n, Y);
+  log_kernel<<<1024, 256, 0, st>>>(Cl, (size_t)N, e->n_out, X, e->n_in, amp_col(e), e->mu_x, Y);
   colstats_kernel<<<(e->n_out + 127) / 128, 128, 0, st>>>(Y, N, e->n_out, e->mu_y, e->sd_y);
   if (!per_l) global_scale_kernel<<<1, 32, 0, st>>>(e->sd_y, e->n_out);
   standardize_y_kernel<<<1024, 256, 0, st>>>(Y, N, e->n_out, e->mu_y, e->sd_y);
@@ -666,7 +681,8 @@ int gcamb_emu_check(gcamb_emu *e, const float *X, const double *Cl_ref, int N, d
       return rc;
     }
     if (!(rc = forward_pass(e, X, nullptr, N, st))) {
-      exp_kernel<<<1024, 256, 0, st>>>(e->out, N, e->n_out, e->mu_y, e->sd_y, d_ce);
+      exp_kernel<<<1024, 256, 0, st>>>(e->out, N, e->n_out, e->mu_y, e->sd_y, X, e->n_in, amp_col(e), e->mu_x,
+                                       d_ce);
       maxrel_kernel<<<N, 256, 0, st>>>(d_ce, Cl_ref, e->n_out, d_err);
       rc = ck(cudaStreamSynchronize(st), "emu_check: kernels");
       if (!rc) rc = ck(cudaMemcpy(he.data(), d_err, N * sizeof(double), cudaMemcpyDeviceToHost), "emu_check: errors");
@@ -763,7 +779,7 @@ int gcamb_emulate(gcamb_emu *e, const float *X, int B, double *Cl, int *used_fal
   if (!X || !Cl || !used_fallback) return fail(GCAMB_EINVAL, "emulate: NULL pointer");
   cudaStream_t st = (cudaStream_t)stream;
   if ((rc = forward_pass(e, X, nullptr, B, st))) return rc;
-  exp_kernel<<<1024, 256, 0, st>>>(e->out, B, e->n_out, e->mu_y, e->sd_y, Cl);
+  exp_kernel<<<1024, 256, 0, st>>>(e->out, B, e->n_out, e->mu_y, e->sd_y, X, e->n_in, amp_col(e), e->mu_x, Cl);
   const int nd = (int)e->cell_dim.size();
   cell_kernel<<<(B + 255) / 256, 256, 0, st>>>(X, B, e->n_in, e->d_cell_dim, e->d_cell_mid, nd, e->d_trusted, nullptr,
                                                used_fallback);

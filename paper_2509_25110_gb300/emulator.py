@@ -43,7 +43,7 @@ def make_dataset(g, n, seed, mode=gcamb.F16X3, batch=256, first_model=0):
     return X, C
 
 
-def train(g, n_train=100_000, n_hold=4096, steps=3000, batch=4096, width=512, depth=3, lr0=2e-3, lr_min=1e-5,
+def train(g, n_train=100_000, n_hold=4096, steps=10000, batch=4096, width=512, depth=3, lr0=2e-3, lr_min=1e-5,
           tol=1e-3, min_count=32, seed=0, per_l=False, log=None, data=None):
     """Trains an emulator on grid g; returns (emu, report)."""
     import torch
@@ -83,6 +83,34 @@ def train(g, n_train=100_000, n_hold=4096, steps=3000, batch=4096, width=512, de
     rep["check"] = gcamb.emu_check(e, Xh, Ch, tol=tol, min_count=min_count)
     rep["tol"] = tol
     return e, rep, (Xh, Ch)
+
+
+def accuracy(e, Xh, Ch, lmin=2):
+    """Held-out accuracy of the network alone: |C_net / C_ref - 1| per
+    (spectrum, l), summarised (the amplitude term is zero on data of one A_s)."""
+    import torch
+    Y = gcamb.emu_forward(e, Xh)
+    nrm = gcamb.emu_norm(e)
+    gcamb.sync()
+    x8 = Xh[:, 8].double().cpu().numpy()[:, None] - float(nrm["mu_x"][8])
+    logc = Y.cpu().numpy().astype(np.float64) * nrm["sd_y"] + nrm["mu_y"] + x8
+    err = np.abs(np.exp(logc) / Ch.cpu().numpy() - 1.0)
+    per = err.max(axis=1)
+    l = np.arange(lmin, lmin + err.shape[1])
+    out = {"median": float(np.median(err)), "p99": float(np.quantile(err, 0.99)),
+           "spectrum_max_p50": float(np.median(per)), "spectrum_max_p90": float(np.quantile(per, 0.9)),
+           "frac_elements_within_1e-3": float((err <= 1e-3).mean())}
+    for a, b in ((2, 30), (30, 500), (500, 1500), (1500, 2501)):
+        sel = (l >= a) & (l < b)
+        if sel.any():
+            out["median_l%d-%d" % (a, b - 1)] = float(np.median(err[:, sel]))
+    return out
+
+
+def served_by_tolerance(e, Xh, Ch, tols=(1e-3, 3e-3, 1e-2, 3e-2, 1e-1), min_count=32):
+    """Fraction of held-out requests the network would serve at each tolerance
+    (the check is re-run per tolerance; the last one stays in force)."""
+    return {"%g" % t: gcamb.emu_check(e, Xh, Ch, tol=t, min_count=min_count)["frac_served"] for t in tols}
 
 
 def serve_rates(e, g, Xh, reps=5):

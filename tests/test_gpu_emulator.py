@@ -159,9 +159,19 @@ def test_training_fallback_and_checkpoint(tmp_path):
         assert np.abs(Cl[~fb] / Ch.cpu().numpy()[~fb] - 1).max() <= 0.02
     # trusting everything: no fallback
     gcamb.emu_check(e, Xh, Ch, tol=float("inf"), min_count=1)
-    _, fb2 = gcamb.emulate(e, Xh)
+    C1, fb2 = gcamb.emulate(e, Xh)
     gcamb.sync()
     assert int(fb2.sum().item()) == 0
+    # C_l is proportional to A_s: a request with ln(1e10 A_s) raised by 0.3
+    # gets the same spectrum times exp(0.3) (the amplitude enters exactly)
+    Xa = Xh.clone()
+    Xa[:, 8] += 0.3
+    Ca, fba = gcamb.emulate(e, Xa)
+    gcamb.sync()
+    assert int(fba.sum().item()) == 0
+    shift = (Xa[:, 8].double() - Xh[:, 8].double()).cpu().numpy()[:, None]
+    ratio = Ca.cpu().numpy() / C1.cpu().numpy()
+    np.testing.assert_allclose(ratio, np.broadcast_to(np.exp(shift), ratio.shape), rtol=1e-12, atol=0)
     # checkpoint round trip
     path = tmp_path / "emu.bin"
     gcamb.emu_save(e, path)
