@@ -116,6 +116,12 @@ __device__ __forceinline__ uint32_t sw128_offset(int r, int cbytes) {
   return (uint32_t)r * 128u + ((uint32_t)((cbytes >> 4) ^ (r & 7)) << 4) + (uint32_t)(cbytes & 15);
 }
 
+// The same for 64-byte rows in the 64-byte swizzled order: 16-byte chunk
+// index XOR ((r / 2) % 4) (address bits 7-8 into bits 4-5).
+__device__ __forceinline__ uint32_t sw64_offset(int r, int cbytes) {
+  return (uint32_t)r * 64u + ((uint32_t)((cbytes >> 4) ^ ((r >> 1) & 3)) << 4) + (uint32_t)(cbytes & 15);
+}
+
 template <int MODE>
 struct TableSink {
   char *table;
@@ -139,15 +145,15 @@ struct TableSink {
     } else if constexpr (MODE == GCAMB_BF16X3) {
       const __nv_bfloat16 hi = __double2bfloat16(wv);
       const __nv_bfloat16 lo = __double2bfloat16(wv - (double)__bfloat162float(hi));
-      const uint32_t o = sw128_offset(r, c * 2);
+      const uint32_t o = sw64_offset(r, c * 2);
       *reinterpret_cast<__nv_bfloat16 *>(base + o) = hi;
-      *reinterpret_cast<__nv_bfloat16 *>(base + 16384 + o) = lo;
+      *reinterpret_cast<__nv_bfloat16 *>(base + 8192 + o) = lo;
     } else if constexpr (MODE == GCAMB_F16X3) {
       const __half hi = __double2half(wv);
       const __half lo = __double2half(wv - (double)__half2float(hi));
-      const uint32_t o = sw128_offset(r, c * 2);
+      const uint32_t o = sw64_offset(r, c * 2);
       *reinterpret_cast<__half *>(base + o) = hi;
-      *reinterpret_cast<__half *>(base + 16384 + o) = lo;
+      *reinterpret_cast<__half *>(base + 8192 + o) = lo;
     } else {  // TF32X3
       const uint32_t hi = tf32_rna((float)wv);
       const uint32_t lo = tf32_rna((float)(wv - (double)__uint_as_float(hi)));
@@ -157,7 +163,7 @@ struct TableSink {
     }
   }
   static constexpr size_t block_bytes() {
-    return MODE == GCAMB_PLAIN64 ? 65536 : 32768;
+    return MODE == GCAMB_PLAIN64 ? 65536 : (MODE == GCAMB_BF16X3 || MODE == GCAMB_F16X3 ? 16384 : 32768);
   }
 };
 
@@ -169,7 +175,7 @@ __global__ void __launch_bounds__(128) bessel_table_kernel(const double *__restr
                                                            const int64_t *__restrict__ off,
                                                            const double *__restrict__ xs, int nxs, int scale_exp,
                                                            void *table) {
-  constexpr int KB = (MODE == GCAMB_TF32X3) ? 32 : 64;
+  constexpr int KB = (MODE == GCAMB_PLAIN64 || MODE == GCAMB_PLAIN32) ? 64 : 32;
   const int q = blockIdx.y;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ntau) return;

@@ -18,8 +18,10 @@ constexpr int kNumModes = 5;
 
 // Table layout of one mode: blocks of [planes][128 rows][kb cols], one block
 // per (k, l-tile, tau-block of kb nodes).  Rows are multipoles, columns tau.
-// Split modes store 128-byte rows in the 128-byte swizzled order the tensor
-// cores read (16-byte chunk index XOR row%8).
+// Split modes store their rows in the swizzled order the tensor cores read
+// K-major operands in: bf16/fp16 64-byte rows (32 tau) in the 64-byte
+// swizzle (16-byte chunk index XOR (row / 2) % 4), tf32 128-byte rows
+// (32 tau) in the 128-byte swizzle (chunk index XOR row % 8).
 struct ModeLayout {
   int kb;        // tau nodes per block
   int planes;    // 1 (plain) or 2 (hi, lo)
@@ -32,9 +34,9 @@ inline ModeLayout mode_layout(int mode) {
   switch (mode) {
     case GCAMB_PLAIN64: return {64, 1, 8, false};
     case GCAMB_PLAIN32: return {64, 1, 4, false};
-    case GCAMB_BF16X3: return {64, 2, 2, true};
+    case GCAMB_BF16X3: return {32, 2, 2, true};
     case GCAMB_TF32X3: return {32, 2, 4, true};
-    case GCAMB_F16X3: return {64, 2, 2, true};
+    case GCAMB_F16X3: return {32, 2, 2, true};
     default: return {0, 0, 0, false};
   }
 }

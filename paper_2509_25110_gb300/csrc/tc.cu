@@ -46,7 +46,6 @@ constexpr int kConvWarps = 4;
 constexpr int kThreads = 32 * (2 + kEpiWarps);
 constexpr int kThreadsFused = 32 * (2 + kConvWarps + kEpiWarps);
 constexpr int kKChunkMax = 64;     // k per work item: bounds the FP32 partial-sum length
-constexpr int kABytes = 32768;     // one table block: hi + lo planes of 128 x 128 B
 constexpr int kSmemBudget = 196608;
 
 struct TcItem {
@@ -92,15 +91,16 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map
       : "memory");
 }
 
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
-// groups 1024 bytes apart (SBO), descriptor version 1 (bit 46).
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+// Shared-memory matrix descriptor: K-major operand, 8-row groups `sbo` bytes
+// apart, swizzle `layout` (2: 128-byte, 4: 64-byte), descriptor version 1
+// (bit 46).
+__device__ __forceinline__ uint64_t op_desc(uint32_t saddr, uint32_t sbo, uint64_t layout) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
   d |= (uint64_t)1 << 16;            // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset
+  d |= (uint64_t)(sbo >> 4) << 32;   // stride byte offset
   d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;            // 128-byte swizzle
+  d |= layout << 61;
   return d;
 }
 
@@ -108,6 +108,20 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
 
 // Split modes of the batched path.
 enum TcMode { kBF16 = 0, kF16 = 1, kTF32 = 2 };
+
+// Operand geometry of a split mode: a tau-block is 32 nodes; its operand rows
+// are 64 bytes (bf16, fp16; 64-byte swizzle) or 128 bytes (tf32; 128-byte
+// swizzle); one K step of the MMA covers 32 bytes of a row.
+template <int MODE>
+struct TcGeom {
+  static constexpr int kRowB = MODE == kTF32 ? 128 : 64;
+  static constexpr int kKSteps = kRowB / 32;
+  static constexpr int kPlaneA = 128 * kRowB;          // one plane of a table block
+  static constexpr int kABytes = 2 * kPlaneA;          // table block: hi + lo planes
+  static constexpr uint32_t kSbo = 8 * kRowB;
+  static constexpr uint64_t kLayout = MODE == kTF32 ? 2 : 4;
+  __device__ static __forceinline__ uint64_t desc(uint32_t saddr) { return op_desc(saddr, kSbo, kLayout); }
+};
 
 template <int MODE>
 __device__ __forceinline__ void mma(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
@@ -154,18 +168,19 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 // third of the accumulate steps (the tensor core's FP32 accumulation error
 // grows with their number); D_x is ~2^-8 of D_hh, so its own rounding is
 // negligible.  The pairs are double-buffered across k when TMEM allows.
-template <int NT>
+template <int NT, int MODE>
 struct TcCfg {
-  static constexpr int kBBytes = 256 * NT;               // hi + lo planes of NT x 128 B
+  static constexpr int kABytes = TcGeom<MODE>::kABytes;
+  static constexpr int kBBytes = 2 * NT * TcGeom<MODE>::kRowB;  // hi + lo planes of NT rows
   static constexpr int kStageBytes = kABytes + kBBytes;
-  static constexpr int kStages = (kSmemBudget / kStageBytes) > 4 ? 4 : (kSmemBudget / kStageBytes);
+  static constexpr int kStages = (kSmemBudget / kStageBytes) > 8 ? 8 : (kSmemBudget / kStageBytes);
   static constexpr int kNBuf = (4 * NT <= 512) ? 2 : 1;
   static constexpr int kTmemCols = kNBuf * 2 * NT < 32 ? 32 : kNBuf * 2 * NT;
   static constexpr int kKSlots = 4;                      // per-k records in flight
   static constexpr int kSlotBytes = 16 + 8 * NT;         // header, weights, row scales
   static constexpr int kQBytes = kKChunkMax * 12;        // the item's block counts and offsets
   static constexpr int kSmemBytes =
-      kStages * kStageBytes + kKSlots * kSlotBytes + kQBytes + 1024 /*align*/ + 256 /*barriers*/;
+      kStages * kStageBytes + kKSlots * kSlotBytes + kQBytes + 1024 /*align*/ + 512 /*barriers*/;
   static constexpr int kColsPerThread = NT / 2;
   static constexpr int kChunk = NT >= 128 ? 8 : 16;      // TMEM load width (register budget)
 };
@@ -186,7 +201,8 @@ constexpr int kFirst = 1 << 16, kLast = 1 << 17;
 template <int NT, int MODE, bool FUSED>
 __global__ void __launch_bounds__(TcRoles<FUSED>::kThreadsT, 1)
     los_cl_tc_kernel(const __grid_constant__ CUtensorMap tm_src, TcParams p) {
-  using C = TcCfg<NT>;
+  using C = TcCfg<NT, MODE>;
+  using G = TcGeom<MODE>;
   using R = TcRoles<FUSED>;
   constexpr int S = C::kStages;
   constexpr int NB = C::kNBuf;
@@ -247,7 +263,9 @@ __global__ void __launch_bounds__(TcRoles<FUSED>::kThreadsT, 1)
     // issues the k's table and source blocks into the stage ring
     int stage = 0;
     uint32_t phase = 0;
-    int armed_phase[4] = {-1, -1, -1, -1};
+    int armed_phase[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) armed_phase[s] = -1;
     int ks = 0;
     uint32_t kph = 0;
     int karmed[C::kKSlots];
@@ -293,7 +311,7 @@ __global__ void __launch_bounds__(TcRoles<FUSED>::kThreadsT, 1)
             ks = 0;
             kph ^= 1u;
           }
-          const char *a = p.table + (size_t)q_off[j] * kABytes;
+          const char *a = p.table + (size_t)q_off[j] * C::kABytes;
           const char *b = FUSED ? nullptr : p.sp + ((size_t)q * p.n_mt + it.mt) * (size_t)p.nkbs * C::kBBytes;
           for (int kb = 0; kb < nb; ++kb) {
             if (!mbar_wait(empty0 + 8 * stage, phase ^ 1u, abort_flag, p.err)) {
@@ -303,11 +321,11 @@ __global__ void __launch_bounds__(TcRoles<FUSED>::kThreadsT, 1)
             const uint32_t sa = smem_u32(smem + stage * C::kStageBytes);
             mbar_expect_tx(full0 + 8 * stage, C::kStageBytes);
             armed_phase[stage] = (int)phase;
-            bulk_g2s(sa, a + (size_t)kb * kABytes, kABytes, full0 + 8 * stage);
-            if constexpr (FUSED)  // FP32 box [NT sources][1 k][64 tau]; zero beyond ntau and M
-              tma_load_3d(sa + kABytes, &tm_src, kb * 64, q, it.mt * NT, full0 + 8 * stage);
+            bulk_g2s(sa, a + (size_t)kb * C::kABytes, C::kABytes, full0 + 8 * stage);
+            if constexpr (FUSED)  // FP32 box [NT sources][1 k][32 tau]; zero beyond ntau and M
+              tma_load_3d(sa + C::kABytes, &tm_src, kb * 32, q, it.mt * NT, full0 + 8 * stage);
             else
-              bulk_g2s(sa + kABytes, b + (size_t)kb * C::kBBytes, C::kBBytes, full0 + 8 * stage);
+              bulk_g2s(sa + C::kABytes, b + (size_t)kb * C::kBBytes, C::kBBytes, full0 + 8 * stage);
             if (++stage == S) {
               stage = 0;
               phase ^= 1u;
@@ -372,11 +390,11 @@ __global__ void __launch_bounds__(TcRoles<FUSED>::kThreadsT, 1)
           }
           tc_fence_after();
           const uint32_t sa = smem_u32(smem + stage * C::kStageBytes);
-          const uint32_t sb = sa + kABytes;
+          const uint32_t sb = sa + C::kABytes;
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk) {
-            const uint64_t ah = sw128_desc(sa + kk * 32), al = sw128_desc(sa + 16384 + kk * 32);
-            const uint64_t bh = sw128_desc(sb + kk * 32), bl = sw128_desc(sb + NT * 128 + kk * 32);
+          for (int kk = 0; kk < G::kKSteps; ++kk) {
+            const uint64_t ah = G::desc(sa + kk * 32), al = G::desc(sa + G::kPlaneA + kk * 32);
+            const uint64_t bh = G::desc(sb + kk * 32), bl = G::desc(sb + NT * G::kRowB + kk * 32);
             const uint32_t accum = (kb | kk) ? 1u : 0u;
             if constexpr (kPair) {
               mma<MODE>(dhh, ah, bh, idesc2, accum);  // [D_hh | D_x] (+)= A_hi [B_hi | B_lo]
@@ -401,16 +419,16 @@ __global__ void __launch_bounds__(TcRoles<FUSED>::kThreadsT, 1)
       mbar_wait(drain, 0, nullptr, p.err);
     }
   } else if (FUSED && warp < R::kEpi0) {
-    // ---------------- converters: the stage's FP32 tile [NT][64] becomes the
-    // hi and lo planes [NT][128 B] (swizzled) in the same bytes.  Thread ct
-    // owns float4 column c4 of rows r0 + 8 j; every row it writes has the same
-    // row mod 8, hence one swizzle offset.  All reads precede all writes
-    // (conv_all is the barrier between them).
+    // ---------------- converters: the stage's FP32 tile [NT][32] becomes the
+    // hi and lo planes [NT][64 B] (64-byte swizzle) in the same bytes.  Thread
+    // ct owns float4 column c4 of rows r0 + 16 j; every row it writes has the
+    // same (row / 2) mod 4, hence one swizzle offset.  All reads precede all
+    // writes (conv_all is the barrier between them).
     if constexpr (FUSED) {
-      constexpr int RJ = NT / 8;
+      constexpr int RJ = NT / 16;
       const int ct = threadIdx.x - 64;
-      const int c4 = ct & 15, r0 = ct >> 4;
-      const uint32_t swz = ((uint32_t)(((c4 >> 1) ^ (r0 & 7)) << 4)) | ((uint32_t)(c4 & 1) << 3);
+      const int c4 = ct & 7, r0 = ct >> 3;
+      const uint32_t swz = ((uint32_t)(((c4 >> 1) ^ ((r0 >> 1) & 3)) << 4)) | ((uint32_t)(c4 & 1) << 3);
       int stage = 0;
       uint32_t phase = 0;
       int ks = 0;
@@ -424,7 +442,7 @@ __global__ void __launch_bounds__(TcRoles<FUSED>::kThreadsT, 1)
         if constexpr (MODE == kF16) {
           const float *sr = reinterpret_cast<const float *>(rec + 16 + NT * 4) + r0;
 #pragma unroll
-          for (int j = 0; j < RJ; ++j) scl[j] = sr[8 * j];
+          for (int j = 0; j < RJ; ++j) scl[j] = sr[16 * j];
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(kempty0 + 8 * ks);
@@ -435,7 +453,7 @@ __global__ void __launch_bounds__(TcRoles<FUSED>::kThreadsT, 1)
         bool ok = true;
         for (int kb = 0; kb < nb; ++kb) {
           const bool w2 = mbar_wait(full0 + 8 * stage, phase, abort_flag, p.err);
-          unsigned char *sb = smem + stage * C::kStageBytes + kABytes;
+          unsigned char *sb = smem + stage * C::kStageBytes + C::kABytes;
           const float4 *raw = reinterpret_cast<const float4 *>(sb);
           float4 v[RJ];
 #pragma unroll
@@ -465,9 +483,9 @@ __global__ void __launch_bounds__(TcRoles<FUSED>::kThreadsT, 1)
               hi = make_uint2(*reinterpret_cast<const uint32_t *>(&h01), *reinterpret_cast<const uint32_t *>(&h23));
               lo = make_uint2(*reinterpret_cast<const uint32_t *>(&l01), *reinterpret_cast<const uint32_t *>(&l23));
             }
-            const uint32_t o = (uint32_t)(r0 + 8 * j) * 128u + swz;
+            const uint32_t o = (uint32_t)(r0 + 16 * j) * 64u + swz;
             *reinterpret_cast<uint2 *>(sb + o) = hi;
-            *reinterpret_cast<uint2 *>(sb + NT * 128 + o) = lo;
+            *reinterpret_cast<uint2 *>(sb + NT * 64 + o) = lo;
           }
           // generic-proxy stores, read next by the tensor cores
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -565,8 +583,15 @@ __device__ __forceinline__ uint32_t tf32_rna_u(float v) {
   return r;
 }
 
+// Byte offset of (row n, byte c) in a plane of the mode's operand rows, in
+// its swizzled order (64-byte rows: chunk XOR (n / 2) % 4; 128-byte rows:
+// chunk XOR n % 8).
+template <int MODE>
 __device__ __forceinline__ uint32_t sw_off(int n, int cbytes) {
-  return (uint32_t)n * 128u + ((uint32_t)((cbytes >> 4) ^ (n & 7)) << 4) + (uint32_t)(cbytes & 15);
+  if constexpr (TcGeom<MODE>::kRowB == 64)
+    return (uint32_t)n * 64u + ((uint32_t)((cbytes >> 4) ^ ((n >> 1) & 3)) << 4) + (uint32_t)(cbytes & 15);
+  else
+    return (uint32_t)n * 128u + ((uint32_t)((cbytes >> 4) ^ (n & 7)) << 4) + (uint32_t)(cbytes & 15);
 }
 
 // Trapezoid weight in ln k of node q on a source's own k prefix [0, nkm):
@@ -607,7 +632,9 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const float *__restrict
   const int mc = live ? perm[mfull] : 0;
   const float *src = S + ((size_t)mc * nk + q) * ntau;
   int s = 0;
-  const int nch = nkbs * 8;  // 16-byte chunks per row over all tau-blocks
+  constexpr int CPR = TcGeom<MODE>::kRowB / 16;  // 16-byte chunks per row of a tau-block
+  constexpr int BB = 2 * TcGeom<MODE>::kRowB;    // bytes of one source row's hi + lo in a block
+  const int nch = nkbs * CPR;  // 16-byte chunks per row over all tau-blocks
   // loads one chunk's fp32 values (zero beyond ntau and for dead rows)
   auto load_chunk = [&](int ch, float *v) {
     const int t0 = ch * EPC;
@@ -662,7 +689,7 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const float *__restrict
       s = s < -40 ? -40 : (s > 80 ? 80 : s);
     }
   }
-  char *base = sp + ((size_t)(q * n_mt + mt) * nkbs) * (size_t)(256 * NT);
+  char *base = sp + ((size_t)(q * n_mt + mt) * nkbs) * (size_t)(BB * NT);
   auto split_store = [&](int ch, const float *v) {
     uint4 hi, lo;
     uint32_t *h = reinterpret_cast<uint32_t *>(&hi), *l = reinterpret_cast<uint32_t *>(&lo);
@@ -691,10 +718,10 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const float *__restrict
         l[u] = *reinterpret_cast<const uint32_t *>(&ll);
       }
     }
-    char *blk = base + (size_t)(ch >> 3) * (256 * NT);
-    const uint32_t o = sw_off(n, (ch & 7) * 16);
+    char *blk = base + (size_t)(ch / CPR) * (BB * NT);
+    const uint32_t o = sw_off<MODE>(n, (ch % CPR) * 16);
     *reinterpret_cast<uint4 *>(blk + o) = hi;
-    *reinterpret_cast<uint4 *>(blk + NT * 128 + o) = lo;
+    *reinterpret_cast<uint4 *>(blk + NT * TcGeom<MODE>::kRowB + o) = lo;
   };
   if constexpr (CACHE > 0) {
 #pragma unroll
@@ -840,9 +867,9 @@ int pick_nt(int M) {
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // The fused kernel reads the caller's FP32 sources by TMA as [M][nk][ntau]
-// boxes of 64 tau x NT sources and splits them in shared memory.  It needs
+// boxes of 32 tau x NT sources and splits them in shared memory.  It needs
 // the sources in caller order (a uniform batch), a row pitch of whole 16-byte
-// units (ntau % 4 == 0), a bf16 or fp16 split (64 tau per block) and NT <= 128
+// units (ntau % 4 == 0), a bf16 or fp16 split and NT <= 128
 // (the in-place conversion holds a stage's tile in the converters' registers).
 // GCAMB_TC_FUSED=0 selects the separate split pass instead.
 bool want_fused(const gcamb_grid *g, int mode, int nt, bool uniform) {
@@ -868,7 +895,7 @@ EncodeTiledFn encode_tiled() {
   return fn;
 }
 
-// Tensor map of the sources S[M][nk][ntau] (FP32): box 64 tau x 1 k x NT sources.
+// Tensor map of the sources S[M][nk][ntau] (FP32): box 32 tau x 1 k x NT sources.
 int encode_sources(CUtensorMap *tm, const float *S, int M, int nk, int ntau, int NT) {
   EncodeTiledFn fn = encode_tiled();
   if (!fn) return fail(GCAMB_ECUDA, "los_cl: cuTensorMapEncodeTiled is not available from the driver");
@@ -876,7 +903,7 @@ int encode_sources(CUtensorMap *tm, const float *S, int M, int nk, int ntau, int
     return fail(GCAMB_EINVAL, "los_cl: S must be 16-byte aligned");
   const cuuint64_t dims[3] = {(cuuint64_t)ntau, (cuuint64_t)nk, (cuuint64_t)M};
   const cuuint64_t strides[2] = {(cuuint64_t)ntau * 4, (cuuint64_t)nk * ntau * 4};
-  const cuuint32_t box[3] = {64, 1, (cuuint32_t)NT};
+  const cuuint32_t box[3] = {32, 1, (cuuint32_t)NT};
   const cuuint32_t es[3] = {1, 1, 1};
   const CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(S), dims, strides, box, es,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -1016,7 +1043,8 @@ void plan_build(const gcamb_grid *g, int M, int mode, int nt, const int *lmax_c,
   if (pl.blob.empty()) pl.blob.push_back(0);
   // workspace: split sources (not with the fused kernel), weights, fp16 row
   // scales (fused fp16), k-chunk partials
-  const size_t sp_bytes = pl.fused ? 0 : (size_t)g->nk * pl.n_mt * pl.nkbs * 256 * pl.NT;
+  const size_t row_b = mode == GCAMB_TF32X3 ? 128 : 64;  // operand row bytes of a 32-tau block
+  const size_t sp_bytes = pl.fused ? 0 : (size_t)g->nk * pl.n_mt * pl.nkbs * 2 * row_b * pl.NT;
   const size_t wp_bytes = (size_t)g->nk * pl.mpad * sizeof(float);
   const size_t sc_bytes = (pl.fused && mode == GCAMB_F16X3) ? wp_bytes : 0;
   const size_t part_bytes = std::max<size_t>(1, pl.nitems) * pl.NT * 128 * sizeof(float);
@@ -1063,7 +1091,7 @@ TcPlan *get_plan(const gcamb_grid *g, int M, int mode, int *rc) {
 template <int NT, int MODE, bool FUSED>
 int launch_tc_kernel(const gcamb_grid *g, const TcPlan &pl, const CUtensorMap &tm, const TcParams &prm,
                      cudaStream_t st) {
-  using Cfg = TcCfg<NT>;
+  using Cfg = TcCfg<NT, MODE>;
   cudaError_t e = cudaFuncSetAttribute(los_cl_tc_kernel<NT, MODE, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        Cfg::kSmemBytes);
   if (e != cudaSuccess) return cuda_fail(e, "los_cl: smem attribute");
@@ -1109,7 +1137,7 @@ int launch_tc(const gcamb_grid *g, const TcPlan &pl, const float *S, const doubl
       rowscale_kernel<<<(unsigned)(((size_t)pl.M * g->nk + 7) / 8), 256, 0, st>>>(
           S, Pk, g->d_wk, pl.M, g->nk, g->ntau, pl.mpad, t.scale_exp, vec, wp, sc);
     }
-    else if (MODE == kF16 && pl.nkbs * 8 <= 32 * 8)
+    else if (MODE == kF16 && pl.nkbs * (TcGeom<MODE>::kRowB / 16) <= 32 * 8)
       split_rows_kernel<MODE, 8><<<nblk, 256, 0, st>>>(S, Pk, g->d_wk, g->d_k, pl.M, g->nk, g->ntau, NT, pl.n_mt,
                                                        pl.nkbs, pl.mpad, t.scale_exp, perm, nkm, vec, sp, wp);
     else

@@ -50,7 +50,7 @@ def run(k, tau, S, P, lmin, lmax, mode, g=None):
 
 @pytest.mark.parametrize("mode", [gcamb.BF16X3, gcamb.F16X3, gcamb.TF32X3])
 @pytest.mark.parametrize("nk,ntau,lmin,lmax,M", [
-    (96, 1000, 2, 700, 4),     # NT = 64, six l-tiles (ragged), full tau blocks
+    (96, 1000, 2, 700, 4),     # NT = 64, six l-tiles (ragged), ragged last tau block
     (120, 333, 2, 300, 100),   # NT = 128, ragged tau block, ragged source tile
     (64, 200, 0, 129, 300),    # three source tiles of 128, lmin = 0, tile boundary at 128
     (70, 332, 2, 300, 100),    # sources read in place (ntau % 4 == 0): ragged tau block and source tile
