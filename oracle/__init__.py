@@ -51,6 +51,12 @@ def _load():
     lib.orc_cl.argtypes = [ctypes.c_int, _dp, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp]
     lib.orc_cl.restype = ctypes.c_int
     lib.orc_num_threads.restype = ctypes.c_int
+    lib.orc_eps_many.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _dp]
+    lib.orc_los_e.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _dp, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                              ctypes.c_int, _dp, _dp, _dp, ctypes.c_int]
+    lib.orc_los_e.restype = ctypes.c_int
+    lib.orc_cl_cross.argtypes = [ctypes.c_int, _dp, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp]
+    lib.orc_cl_cross.restype = ctypes.c_int
     _LIB = lib
     return lib
 
@@ -143,6 +149,50 @@ def cl_from_delta(k, delta, Pk, wk=None) -> np.ndarray:
     cl = np.empty((M, nl))
     _load().orc_cl(nk, _ptr(k), nl, M, _ptr(delta), _ptr(Pk),
                    _ptr(_f64(wk)) if wk is not None else None, _ptr(cl))
+    return cl[0] if single else cl
+
+
+def eps(x, lmax) -> np.ndarray:
+    """eps_l(x) = sqrt((l+2)!/(l-2)!) j_l(x)/x^2 (0 for l < 2; limit at x = 0)
+    for l = 0..lmax, shape [x.size][lmax + 1] (the kernel of Eq. 3)."""
+    xa = _f64(x).ravel()
+    out = np.empty((xa.size, lmax + 1))
+    _load().orc_eps_many(xa.size, _ptr(xa), int(lmax), _ptr(out))
+    return out
+
+
+def los_e(k, tau, tau0, lmin, lmax, SP, wtau=None, nthreads=0) -> np.ndarray:
+    """Dense FP64 Delta^E[M][nk][nl] of Eq. (3), S_P of shape [M][nk][ntau]."""
+    k = _f64(k)
+    tau = _f64(tau)
+    SP = _f64(SP)
+    single = SP.ndim == 2
+    if single:
+        SP = SP[None]
+    M, nk, ntau = SP.shape
+    assert nk == k.size and ntau == tau.size
+    d = np.empty((M, nk, lmax - lmin + 1))
+    rc = _load().orc_los_e(nk, _ptr(k), ntau, _ptr(tau), float(tau0), int(lmin), int(lmax), M, _ptr(SP),
+                           _ptr(_f64(wtau)) if wtau is not None else None, _ptr(d), int(nthreads))
+    if rc != 0:
+        raise ValueError("oracle rejected the arguments")
+    return d[0] if single else d
+
+
+def cl_cross(k, DX, DY, Pk, wk=None) -> np.ndarray:
+    """C^XY[M][nl] = 4 pi sum_k w_k P Delta^X Delta^Y (Eq. 1)."""
+    k = _f64(k)
+    DX = _f64(DX)
+    DY = _f64(DY)
+    single = DX.ndim == 2
+    if single:
+        DX, DY = DX[None], DY[None]
+    M, nk, nl = DX.shape
+    assert DY.shape == DX.shape
+    Pk = _f64(Pk).reshape(M, nk)
+    cl = np.empty((M, nl))
+    _load().orc_cl_cross(nk, _ptr(k), nl, M, _ptr(DX), _ptr(DY), _ptr(Pk),
+                         _ptr(_f64(wk)) if wk is not None else None, _ptr(cl))
     return cl[0] if single else cl
 
 
