@@ -149,6 +149,31 @@ int gcamb_sph_bessel(const double *x, int n, int lmax, double *out, void *stream
 int gcamb_los_transfer(const gcamb_grid *g, const void *S, int M, int mode, void *Delta, void *stream);
 
 /*
+ * E-mode polarisation transfer functions, Eq. (3) (Sec. 2.1), on the CUDA
+ * cores, with the flat-space kernel
+ *   eps_l(x) = sqrt((l+2)!/(l-2)!) j_l(x) / x^2   (l >= 2; 0 for l < 2):
+ *   DeltaE[m][k][l - lmin] = sum_i w_i S_P[m][k][i] eps_l(k (tau0 - tau_i)).
+ * It uses the same j_l table as gcamb_los_transfer (the x^-2 factor is
+ * applied to the source, the prefactor to the row).  Nodes with x below a
+ * small cut x_lo (x = 0 included; x_lo is 1e-12 or the largest x at which the
+ * table may hold j_2 as zero, at most 0.2) contribute to l = 2 only, through
+ * the power series of j_2(x)/x^2 (-> 1/15); for l >= 3 their terms are below
+ * c_l x_lo^(l-2)/(2l+1)!!.  GCAMB_EINVAL if eps_cut is so large that x_lo
+ * would exceed 0.2.  Arguments, layout, modes, dtypes and other errors as for
+ * gcamb_los_transfer.
+ */
+int gcamb_los_transfer_e(const gcamb_grid *g, const void *SP, int M, int mode, void *DeltaE, void *stream);
+
+/*
+ * Cross spectrum, Eq. (1) with X, Y in {T, E}:
+ *   C^XY[m][l] = 4 pi sum_k w_k P[m][k] DX[m][k][l] DY[m][k][l]
+ * DX, DY [M][nk][nl] device, both of d_dtype (GCAMB_F64 or GCAMB_F32);
+ * Pk[M][nk], Cl[M][nl] device double.  Summed in FP64 in increasing k.
+ */
+int gcamb_cl_cross(const gcamb_grid *g, const void *DX, const void *DY, int d_dtype, const double *Pk, int M,
+                   double *Cl, void *stream);
+
+/*
  * C_l from transfer functions, Eq. (1) with X = Y = T:
  *   Delta[M][nk][nl]   device, d_dtype = GCAMB_F64 or GCAMB_F32
  *   Pk[M][nk]          device double, P_R(k) per source

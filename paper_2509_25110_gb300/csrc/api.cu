@@ -358,6 +358,29 @@ int gcamb_los_transfer(const gcamb_grid *g, const void *S, int M, int mode, void
   return launch_los_plain(g, S, M, mode, Delta, (cudaStream_t)stream);
 }
 
+int gcamb_los_transfer_e(const gcamb_grid *g, const void *SP, int M, int mode, void *DeltaE, void *stream) {
+  if (!g) return fail(GCAMB_EINVAL, "los_transfer_e: NULL grid");
+  if (mode != GCAMB_PLAIN64 && mode != GCAMB_PLAIN32)
+    return fail(GCAMB_EINVAL, "los_transfer_e: mode must be GCAMB_PLAIN64 or GCAMB_PLAIN32");
+  if (M < 0) return fail(GCAMB_EINVAL, "los_transfer_e: M < 0");
+  if (M == 0) return GCAMB_OK;
+  if (!SP || !DeltaE) return fail(GCAMB_EINVAL, "los_transfer_e: NULL S_P or Delta_E");
+  if (!g->tab[mode].built) return fail(GCAMB_ESTATE, "los_transfer_e: build the table for this mode first");
+  return launch_los_plain(g, SP, M, mode, DeltaE, (cudaStream_t)stream, true);
+}
+
+int gcamb_cl_cross(const gcamb_grid *g, const void *DX, const void *DY, int d_dtype, const double *Pk, int M,
+                   double *Cl, void *stream) {
+  if (!g) return fail(GCAMB_EINVAL, "cl_cross: NULL grid");
+  if (d_dtype != GCAMB_F64 && d_dtype != GCAMB_F32) return fail(GCAMB_EINVAL, "cl_cross: d_dtype must be F64 or F32");
+  if (M < 0) return fail(GCAMB_EINVAL, "cl_cross: M < 0");
+  if (M == 0) return GCAMB_OK;
+  if (!DX || !DY || !Pk || !Cl) return fail(GCAMB_EINVAL, "cl_cross: NULL pointer");
+  int rc = ensure_device_grid(const_cast<gcamb_grid *>(g));
+  if (rc) return rc;
+  return launch_cl_cross(g, DX, DY, d_dtype, Pk, M, Cl, (cudaStream_t)stream);
+}
+
 int gcamb_cl(const gcamb_grid *g, const void *Delta, int d_dtype, const double *Pk, int M, double *Cl,
              void *stream) {
   if (!g) return fail(GCAMB_EINVAL, "cl: NULL grid");

@@ -88,7 +88,10 @@ int launch_bessel_table(gcamb_grid *g, int mode, cudaStream_t st);
 int launch_sph_bessel(const double *x, int n, int lmax, double *out, cudaStream_t st);
 
 // Plain FP64/FP32 path (plain.cu).
-int launch_los_plain(const gcamb_grid *g, const void *S, int M, int mode, void *Delta, cudaStream_t st);
+int launch_los_plain(const gcamb_grid *g, const void *S, int M, int mode, void *Delta, cudaStream_t st,
+                     bool emode = false);
+int launch_cl_cross(const gcamb_grid *g, const void *DX, const void *DY, int d_dtype, const double *Pk, int M,
+                    double *Cl, cudaStream_t st);
 int launch_cl(const gcamb_grid *g, const void *Delta, int d_dtype, const double *Pk, int M, double *Cl,
               cudaStream_t st);
 

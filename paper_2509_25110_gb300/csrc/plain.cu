@@ -2,6 +2,8 @@
 // cores (Algorithm 1's gang over k and vector loops over l and tau, here one
 // CTA per (l-tile, k, source chunk) and one warp per multipole row), and the
 // FP64 k-sum of Eq. (1).
+#include <cmath>
+
 #include "internal.h"
 
 namespace gcamb {
@@ -9,11 +11,23 @@ namespace gcamb {
 // One CTA: 128 multipoles x MC sources at one k.  The sources' tau-prefix is
 // staged in shared memory; each warp walks table rows (tau contiguous, read
 // coalesced), the lanes split tau and reduce by shuffles.
-template <typename T, int MC>
+//
+// E = true: E-mode polarisation, Eq. (3) with eps_l(x) = c_l j_l(x)/x^2,
+// c_l = sqrt((l+2)!/(l-2)!).  The j_l table is shared with temperature: the
+// staged source is S_P/x^2, the row sum is multiplied by c_l.  Nodes with
+// x < x_lo (x = 0 included) are left out of the table sum: there the table's
+// j_2 may be cut to zero (activity threshold, Miller start) although
+// j_2(x)/x^2 -> 1/15.  They add, to l = 2 only, the power series
+//   j_2(x)/x^2 = 1/15 - x^2/210 + x^4/7560 - x^6/498960 + O(x^8)
+// (from j_l(x) = x^l sum_n (-x^2/2)^n / (n! (2l+2n+1)!!)); for l >= 3 their
+// eps_l is below c_l x_lo^(l-2)/(2l+1)!!, and x_lo <= 0.2.
+template <typename T, int MC, bool E>
 __global__ void __launch_bounds__(256) los_plain_kernel(const T *__restrict__ table, const int32_t *__restrict__ nkb,
                                                         const int64_t *__restrict__ off, int nk, int nlt, int lmin,
                                                         int lmax, int ntau, const T *__restrict__ S, int M,
-                                                        T *__restrict__ Delta) {
+                                                        T *__restrict__ Delta, const double *__restrict__ kk,
+                                                        const double *__restrict__ tau, double tau0,
+                                                        const double *__restrict__ wtau, double x_lo) {
   constexpr int KB = 64;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *s = reinterpret_cast<T *>(smem_raw);  // [MC][ext]
@@ -27,7 +41,14 @@ __global__ void __launch_bounds__(256) los_plain_kernel(const T *__restrict__ ta
   const int mc = min(MC, M - m0);
   for (int idx = threadIdx.x; idx < MC * ext; idx += blockDim.x) {
     const int m = idx / ext, t = idx - m * ext;
-    s[idx] = (m < mc && t < ntau) ? S[((size_t)(m0 + m) * nk + q) * ntau + t] : T(0);
+    T v = (m < mc && t < ntau) ? S[((size_t)(m0 + m) * nk + q) * ntau + t] : T(0);
+    if constexpr (E) {
+      if (m < mc && t < ntau) {
+        const double x = kk[q] * (tau0 - tau[t]);
+        v = x >= x_lo ? (T)((double)v / (x * x)) : T(0);
+      }
+    }
+    s[idx] = v;
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -61,45 +82,80 @@ __global__ void __launch_bounds__(256) los_plain_kernel(const T *__restrict__ ta
   for (int idx = threadIdx.x; idx < MC * kTileL; idx += blockDim.x) {
     const int m = idx / kTileL, r = idx - m * kTileL;
     const int l = l0 + r;
-    if (m < mc && l <= lmax) Delta[((size_t)(m0 + m) * nk + q) * nl + (l - lmin)] = res[m][r];
+    if (m < mc && l <= lmax) {
+      T v = res[m][r];
+      if constexpr (E) {
+        const double c = l >= 2 ? sqrt((double)(l + 2) * (l + 1) * l * (l - 1)) : 0.0;
+        double d = c * (double)v;
+        if (l == 2) {  // the small-x nodes are the tail of the tau grid (x decreases with tau)
+          const T *src = S + ((size_t)(m0 + m) * nk + q) * ntau;
+          double tail = 0.0;
+          for (int i = ntau - 1; i >= 0; --i) {
+            const double x = kk[q] * (tau0 - tau[i]);
+            if (!(x < x_lo)) break;
+            const double x2 = x * x;
+            const double e2 = 1.0 / 15.0 - x2 * (1.0 / 210.0 - x2 * (1.0 / 7560.0 - x2 / 498960.0));
+            tail += wtau[i] * (double)src[i] * e2;
+          }
+          d += c * tail;
+        }
+        v = (T)d;
+      }
+      Delta[((size_t)(m0 + m) * nk + q) * nl + (l - lmin)] = v;
+    }
   }
 }
 
-template <typename T, int MC>
+template <typename T, int MC, bool E>
 static int launch_plain_t(const gcamb_grid *g, const Table &t, const T *S, int M, T *Delta, cudaStream_t st) {
   int max_ext = 0;
   for (int v : t.nkb) max_ext = max_ext > v ? max_ext : v;
   max_ext *= 64;
   const size_t smem = (size_t)MC * max_ext * sizeof(T);
   if (smem > 200 * 1024) return fail(GCAMB_EINVAL, "los_transfer: tau grid too long for the plain kernel");
-  cudaError_t e = cudaFuncSetAttribute(los_plain_kernel<T, MC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(los_plain_kernel<T, MC, E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)(smem > 0 ? smem : 16));
   if (e != cudaSuccess) return cuda_fail(e, "los_transfer: smem attribute");
   dim3 grid(g->nlt, g->nk, (M + MC - 1) / MC);
   if (grid.z > 65535) return fail(GCAMB_EINVAL, "los_transfer: too many sources for one launch");
   ProfScope prof(GCAMB_K_LOS_PLAIN, st);
-  los_plain_kernel<T, MC><<<grid, 256, smem, st>>>(static_cast<const T *>(t.d_data), t.d_nkb, t.d_off, g->nk, g->nlt,
-                                                   g->lmin, g->lmax, g->ntau, S, M, Delta);
+  // E-mode small-x cut: at least 1e-12 and every x the l = 2 row of the table
+  // may have cut (the activity threshold of the tile holding l = 2, the
+  // Miller start of j_2); at most 0.2 (eps_cut <= 1e-3 keeps it near 0.12).
+  double x_lo = 1e-12;
+  if (E && g->lmin <= 2) {
+    if (g->lmin >= 1) x_lo = fmax(x_lo, watson_threshold(g->lmin, std::log(g->eps_cut)));
+    if (g->nxs > 2) x_lo = fmax(x_lo, g->xstart[2]);
+    if (!(x_lo <= 0.2)) return fail(GCAMB_EINVAL, "los_transfer_e: eps_cut too large for the l = 2 limit");
+  }
+  los_plain_kernel<T, MC, E><<<grid, 256, smem, st>>>(static_cast<const T *>(t.d_data), t.d_nkb, t.d_off, g->nk,
+                                                      g->nlt, g->lmin, g->lmax, g->ntau, S, M, Delta, g->d_k,
+                                                      g->d_tau, g->tau0, g->d_wtau, x_lo);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "los_transfer: launch");
   return GCAMB_OK;
 }
 
-int launch_los_plain(const gcamb_grid *g, const void *S, int M, int mode, void *Delta, cudaStream_t st) {
+template <bool E>
+static int launch_los_plain_k(const gcamb_grid *g, const void *S, int M, int mode, void *Delta, cudaStream_t st) {
   const Table &t = g->tab[mode];
   if (mode == GCAMB_PLAIN64) {
     auto s = static_cast<const double *>(S);
     auto d = static_cast<double *>(Delta);
-    if (M >= 4) return launch_plain_t<double, 4>(g, t, s, M, d, st);
-    if (M >= 2) return launch_plain_t<double, 2>(g, t, s, M, d, st);
-    return launch_plain_t<double, 1>(g, t, s, M, d, st);
+    if (M >= 4) return launch_plain_t<double, 4, E>(g, t, s, M, d, st);
+    if (M >= 2) return launch_plain_t<double, 2, E>(g, t, s, M, d, st);
+    return launch_plain_t<double, 1, E>(g, t, s, M, d, st);
   }
   auto s = static_cast<const float *>(S);
   auto d = static_cast<float *>(Delta);
-  if (M >= 8) return launch_plain_t<float, 8>(g, t, s, M, d, st);
-  if (M >= 4) return launch_plain_t<float, 4>(g, t, s, M, d, st);
-  if (M >= 2) return launch_plain_t<float, 2>(g, t, s, M, d, st);
-  return launch_plain_t<float, 1>(g, t, s, M, d, st);
+  if (M >= 8) return launch_plain_t<float, 8, E>(g, t, s, M, d, st);
+  if (M >= 4) return launch_plain_t<float, 4, E>(g, t, s, M, d, st);
+  if (M >= 2) return launch_plain_t<float, 2, E>(g, t, s, M, d, st);
+  return launch_plain_t<float, 1, E>(g, t, s, M, d, st);
+}
+
+int launch_los_plain(const gcamb_grid *g, const void *S, int M, int mode, void *Delta, cudaStream_t st, bool emode) {
+  return emode ? launch_los_plain_k<true>(g, S, M, mode, Delta, st) : launch_los_plain_k<false>(g, S, M, mode, Delta, st);
 }
 
 // C_l[m][l] = 4 pi sum_k w_k P[m][k] Delta[m][k][l]^2 in FP64, increasing k.
@@ -120,6 +176,41 @@ __global__ void __launch_bounds__(256) cl_kernel(const TD *__restrict__ Delta, c
     acc = fma(f, v * v, acc);
   }
   Cl[(size_t)m * nl + l] = acc;
+}
+
+// C^XY_l[m] = 4 pi sum_k w_k P[m][k] DX[m][k][l] DY[m][k][l] in FP64, increasing k.
+template <typename TD>
+__global__ void __launch_bounds__(256) cl_cross_kernel(const TD *__restrict__ DX, const TD *__restrict__ DY,
+                                                       const double *__restrict__ Pk, const double *__restrict__ wk,
+                                                       int nk, int nl, double *__restrict__ Cl) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  const int m = blockIdx.y;
+  if (l >= nl) return;
+  const size_t base = (size_t)m * nk * nl + l;
+  const double *p = Pk + (size_t)m * nk;
+  const double four_pi = 4.0 * 3.14159265358979323846;
+  double acc = 0.0;
+  for (int q = 0; q < nk; ++q) {
+    const double f = four_pi * wk[q] * p[q];
+    acc = fma(f, (double)DX[base + (size_t)q * nl] * (double)DY[base + (size_t)q * nl], acc);
+  }
+  Cl[(size_t)m * nl + l] = acc;
+}
+
+int launch_cl_cross(const gcamb_grid *g, const void *DX, const void *DY, int d_dtype, const double *Pk, int M,
+                    double *Cl, cudaStream_t st) {
+  if (M > 65535) return fail(GCAMB_EINVAL, "cl_cross: too many sources for one launch");
+  dim3 grid((g->nl + 255) / 256, M);
+  ProfScope prof(GCAMB_K_CL, st);
+  if (d_dtype == GCAMB_F64)
+    cl_cross_kernel<double><<<grid, 256, 0, st>>>(static_cast<const double *>(DX), static_cast<const double *>(DY), Pk,
+                                                  g->d_wk, g->nk, g->nl, Cl);
+  else
+    cl_cross_kernel<float><<<grid, 256, 0, st>>>(static_cast<const float *>(DX), static_cast<const float *>(DY), Pk,
+                                                 g->d_wk, g->nk, g->nl, Cl);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "cl_cross: launch");
+  return GCAMB_OK;
 }
 
 int launch_cl(const gcamb_grid *g, const void *Delta, int d_dtype, const double *Pk, int M, double *Cl,

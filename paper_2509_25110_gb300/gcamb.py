@@ -56,6 +56,8 @@ def lib():
     L.gcamb_sph_bessel.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp]
     L.gcamb_los_transfer.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp]
     L.gcamb_cl.argtypes = [_vp, _vp, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp]
+    L.gcamb_los_transfer_e.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp]
+    L.gcamb_cl_cross.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp]
     L.gcamb_los_cl_workspace.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
     L.gcamb_los_cl.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_size_t, _vp]
     L.gcamb_sync.argtypes = [_vp]
@@ -225,6 +227,32 @@ def los_transfer(g: Grid, S, mode: int, Delta=None, stream=None):
     _check(lib().gcamb_los_transfer(g.handle, _dev(S, dt, (M, g.nk, g.ntau), "S"), M, int(mode),
                                     _dev(Delta, dt, (M, g.nk, g.nl), "Delta"), _stream(stream)))
     return Delta
+
+
+def los_transfer_e(g: Grid, SP, mode: int, DeltaE=None, stream=None):
+    """Eq. (3), E-mode: S_P[M][nk][ntau] -> Delta_E[M][nk][nl] (FP64 for PLAIN64, FP32 for PLAIN32)."""
+    import torch
+    dt = torch.float64 if mode == PLAIN64 else torch.float32
+    M = SP.shape[0]
+    if DeltaE is None:
+        DeltaE = torch.empty((M, g.nk, g.nl), dtype=dt, device=SP.device)
+    _check(lib().gcamb_los_transfer_e(g.handle, _dev(SP, dt, (M, g.nk, g.ntau), "S_P"), M, int(mode),
+                                      _dev(DeltaE, dt, (M, g.nk, g.nl), "Delta_E"), _stream(stream)))
+    return DeltaE
+
+
+def cl_cross(g: Grid, DX, DY, Pk, Cl=None, stream=None):
+    """Eq. (1) with X, Y in {T, E}: DX, DY [M][nk][nl], Pk [M][nk] -> C^XY [M][nl] (FP64)."""
+    import torch
+    M = DX.shape[0]
+    d_dtype = F64 if DX.dtype == torch.float64 else F32
+    if Cl is None:
+        Cl = torch.empty((M, g.nl), dtype=torch.float64, device=DX.device)
+    _check(lib().gcamb_cl_cross(g.handle, _dev(DX, DX.dtype, (M, g.nk, g.nl), "DX"),
+                                _dev(DY, DX.dtype, (M, g.nk, g.nl), "DY"), d_dtype,
+                                _dev(Pk, torch.float64, (M, g.nk), "Pk"), M, _dev(Cl, torch.float64, (M, g.nl), "Cl"),
+                                _stream(stream)))
+    return Cl
 
 
 def cl(g: Grid, Delta, Pk, Cl=None, stream=None):

@@ -35,6 +35,11 @@ TAU_L = 11000.0   # centre of the late-time term [Mpc]
 S_L = 2000.0      # width of the late-time term [Mpc]
 K_L = 0.01        # k-scale of the late-time term [1/Mpc]
 A_S = 2.1e-9      # primordial amplitude
+A_P = 0.3         # polarisation / temperature amplitude at recombination
+TAU_RE = 4700.0   # centre of the reionisation term of the polarisation source [Mpc]
+S_RE = 600.0      # its width [Mpc]
+K_RE = 0.005      # its k-scale [1/Mpc]
+B_RE = 0.02       # its amplitude
 K_PIVOT = 0.05    # pivot scale [1/Mpc]
 
 # Parameter slots drawn per model, in counter order.
@@ -230,6 +235,45 @@ def sources_torch(k, tau, p: ModelParams, device, dtype=None, nk_per_model=None)
         if nk_per_model is not None:
             s[int(nk_per_model[m]):] = 0.0
         out[m] = s.to(dtype)
+    return out
+
+
+def sources_pol(k: np.ndarray, tau: np.ndarray, p: ModelParams, dtype=np.float64) -> np.ndarray:
+    """Polarisation source S_P[M][nk][ntau] of the E-mode projection (Eq. 3),
+    in float64, returned in `dtype`: the visibility peak of `sources` a quarter
+    period out of phase (the quadrupole follows the velocity), plus a broad
+    reionisation term at late times and large scales,
+
+    S_P(k,tau) = A_P g(tau) sin(k r_s + phi) exp(-(k/k_D)^2)
+               + B_RE exp(-(tau-TAU_RE)^2 / (2 S_RE^2)) exp(-k/K_RE).
+    """
+    k = np.asarray(k, dtype=np.float64)
+    tau = np.asarray(tau, dtype=np.float64)
+    out = np.empty((p.M, k.size, tau.size), dtype=dtype)
+    re_tau = np.exp(-(tau - TAU_RE) ** 2 / (2.0 * S_RE ** 2))
+    re_k = B_RE * np.exp(-k / K_RE)
+    for m in range(p.M):
+        g = np.exp(-(tau - p.tau_star[m]) ** 2 / (2.0 * p.sigma[m] ** 2)) / (p.sigma[m] * math.sqrt(2.0 * math.pi))
+        ak = A_P * np.sin(k * p.r_s[m] + p.phi[m]) * np.exp(-(k / p.k_D[m]) ** 2)
+        out[m] = (ak[:, None] * g[None, :] + re_k[:, None] * re_tau[None, :]).astype(dtype)
+    return out
+
+
+def sources_pol_torch(k, tau, p: ModelParams, device, dtype=None):
+    """Same as `sources_pol`, evaluated with torch in float64 on `device` and
+    cast to `dtype` (default float32)."""
+    import torch
+    dtype = dtype or torch.float32
+    kt = torch.as_tensor(np.asarray(k, dtype=np.float64), device=device)
+    tt = torch.as_tensor(np.asarray(tau, dtype=np.float64), device=device)
+    out = torch.empty((p.M, kt.numel(), tt.numel()), dtype=dtype, device=device)
+    re_tau = torch.exp(-(tt - TAU_RE) ** 2 / (2.0 * S_RE ** 2))
+    re_k = B_RE * torch.exp(-kt / K_RE)
+    for m in range(p.M):
+        g = torch.exp(-(tt - float(p.tau_star[m])) ** 2 / (2.0 * float(p.sigma[m]) ** 2)) / (
+            float(p.sigma[m]) * math.sqrt(2.0 * math.pi))
+        ak = A_P * torch.sin(kt * float(p.r_s[m]) + float(p.phi[m])) * torch.exp(-(kt / float(p.k_D[m])) ** 2)
+        out[m] = (ak[:, None] * g[None, :] + re_k[:, None] * re_tau[None, :]).to(dtype)
     return out
 
 
