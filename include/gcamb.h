@@ -215,6 +215,29 @@ int gcamb_los_cl(const gcamb_grid *g, const float *S, const double *Pk, int M, i
                  double *Cl, void *ws, size_t ws_bytes, void *stream);
 
 /*
+ * Temperature and E-mode polarisation together, batched on the tensor cores:
+ * for M models sharing the grid, Eq. (2) for S_T and Eq. (3) for S_P (the
+ * E-mode kernel eps_l(x) = c_l j_l(x)/x^2 of gcamb_los_transfer_e, with its
+ * small-x treatment) and Eq. (1) for XY = TT, EE, TE, without storing Delta.
+ * The two sources of a model are adjacent operand rows of one product with
+ * the shared bf16 hi/lo table (the table is read once for both); the
+ * polarisation rows are scaled by 1/x^2 while they are split in shared
+ * memory, and the row sums by c_l (EE: c_l^2) in the FP64 reduce.
+ *   ST, SP[M][nk][ntau]   device float, 16-byte aligned, ntau % 4 == 0
+ *   Pk[M][nk]             device double, >= 0
+ *   ClTT, ClEE, ClTE[M][nl]  device double
+ *   ws, ws_bytes          device workspace of at least
+ *                         gcamb_los_cl_te_workspace bytes
+ * mode: GCAMB_BF16X3 (the only one); requires gcamb_bessel_table(g, mode).
+ * Errors: GCAMB_EINVAL (mode, pointers, alignment, workspace, eps_cut too
+ * large for the l = 2 limit), GCAMB_ESTATE (no table), GCAMB_EUNSUPPORTED
+ * (ntau % 4 != 0, or not sm_103), GCAMB_ECUDA; GCAMB_ETIMEOUT by gcamb_sync.
+ */
+int gcamb_los_cl_te_workspace(const gcamb_grid *g, int M, int mode, size_t *bytes);
+int gcamb_los_cl_te(const gcamb_grid *g, const float *ST, const float *SP, const double *Pk, int M, int mode,
+                    double *ClTT, double *ClEE, double *ClTE, void *ws, size_t ws_bytes, void *stream);
+
+/*
  * Plans: batches of sources with their own l_max and k range on one grid
  * (the uneven batch), run as one persistent tensor-core kernel replayed from
  * a CUDA graph.  Eq. (1) is summed for source m over its own k prefix

@@ -417,6 +417,35 @@ int gcamb_los_cl(const gcamb_grid *g, const float *S, const double *Pk, int M, i
   return launch_los_cl(g, S, Pk, M, mode, Cl, ws, ws_bytes, (cudaStream_t)stream);
 }
 
+static int te_check(const gcamb_grid *g, int M, int mode, const char *who) {
+  if (!g) return fail(GCAMB_EINVAL, std::string(who) + ": NULL grid");
+  if (mode != GCAMB_BF16X3) return fail(GCAMB_EINVAL, std::string(who) + ": mode must be GCAMB_BF16X3");
+  if (M < 0) return fail(GCAMB_EINVAL, std::string(who) + ": M < 0");
+  if (!g->tab[mode].built) return fail(GCAMB_ESTATE, std::string(who) + ": build the table for this mode first");
+  if (g->ntau % 4 != 0)
+    return fail(GCAMB_EUNSUPPORTED, std::string(who) + ": needs ntau % 4 == 0 (sources read by TMA in place)");
+  return GCAMB_OK;
+}
+
+int gcamb_los_cl_te_workspace(const gcamb_grid *g, int M, int mode, size_t *bytes) {
+  if (!bytes) return fail(GCAMB_EINVAL, "los_cl_te_workspace: bytes is NULL");
+  *bytes = 0;
+  if (int rc = te_check(g, M, mode, "los_cl_te_workspace")) return rc;
+  if (M == 0) return GCAMB_OK;
+  *bytes = los_cl_te_workspace_bytes(g, M);
+  return *bytes ? GCAMB_OK : fail(GCAMB_ECUDA, "los_cl_te_workspace: plan");
+}
+
+int gcamb_los_cl_te(const gcamb_grid *g, const float *ST, const float *SP, const double *Pk, int M, int mode,
+                    double *ClTT, double *ClEE, double *ClTE, void *ws, size_t ws_bytes, void *stream) {
+  if (int rc = te_check(g, M, mode, "los_cl_te")) return rc;
+  if (M == 0) return GCAMB_OK;
+  if (!ST || !SP || !Pk || !ClTT || !ClEE || !ClTE) return fail(GCAMB_EINVAL, "los_cl_te: NULL pointer");
+  if (!is_sm103()) return fail(GCAMB_EUNSUPPORTED, "los_cl_te: the tensor-core path needs an sm_103 device");
+  if (!ws) return fail(GCAMB_EINVAL, "los_cl_te: workspace missing");
+  return launch_los_cl_te(g, ST, SP, Pk, M, ClTT, ClEE, ClTE, ws, ws_bytes, (cudaStream_t)stream);
+}
+
 int gcamb_sync(void *stream) {
   cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "sync");

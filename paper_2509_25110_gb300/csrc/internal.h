@@ -90,6 +90,8 @@ int launch_sph_bessel(const double *x, int n, int lmax, double *out, cudaStream_
 // Plain FP64/FP32 path (plain.cu).
 int launch_los_plain(const gcamb_grid *g, const void *S, int M, int mode, void *Delta, cudaStream_t st,
                      bool emode = false);
+// E-mode small-x cut x_lo of the grid (plain.cu); -1 if it would exceed 0.2.
+int emode_x_lo(const gcamb_grid *g, double *x_lo);
 int launch_cl_cross(const gcamb_grid *g, const void *DX, const void *DY, int d_dtype, const double *Pk, int M,
                     double *Cl, cudaStream_t st);
 int launch_cl(const gcamb_grid *g, const void *Delta, int d_dtype, const double *Pk, int M, double *Cl,
@@ -97,6 +99,9 @@ int launch_cl(const gcamb_grid *g, const void *Delta, int d_dtype, const double 
 
 // Tensor-core batched path (tc.cu).
 size_t los_cl_workspace_bytes(const gcamb_grid *g, int M, int mode);
+size_t los_cl_te_workspace_bytes(const gcamb_grid *g, int M);
+int launch_los_cl_te(const gcamb_grid *g, const float *ST, const float *SP, const double *Pk, int M, double *ClTT,
+                     double *ClEE, double *ClTE, void *ws, size_t ws_bytes, cudaStream_t st);
 int launch_los_cl(const gcamb_grid *g, const float *S, const double *Pk, int M, int mode, double *Cl,
                   void *ws, size_t ws_bytes, cudaStream_t st);
 void drop_plans(const gcamb_grid *g);

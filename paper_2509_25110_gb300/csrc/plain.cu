@@ -106,6 +106,20 @@ __global__ void __launch_bounds__(256) los_plain_kernel(const T *__restrict__ ta
   }
 }
 
+// E-mode small-x cut: at least 1e-12 and every x at which the l = 2 row of
+// the table may hold zero (the activity threshold of the tile holding l = 2,
+// the Miller start of j_2); at most 0.2, where the four-term series of
+// j_2(x)/x^2 is still exact to 1e-12 (eps_cut <= 1e-3 keeps it near 0.12).
+int emode_x_lo(const gcamb_grid *g, double *x_lo) {
+  double x = 1e-12;
+  if (g->lmin <= 2) {
+    if (g->lmin >= 1) x = fmax(x, watson_threshold(g->lmin, std::log(g->eps_cut)));
+    if (g->nxs > 2) x = fmax(x, g->xstart[2]);
+  }
+  *x_lo = x;
+  return x <= 0.2 ? 0 : -1;
+}
+
 template <typename T, int MC, bool E>
 static int launch_plain_t(const gcamb_grid *g, const Table &t, const T *S, int M, T *Delta, cudaStream_t st) {
   int max_ext = 0;
@@ -119,15 +133,8 @@ static int launch_plain_t(const gcamb_grid *g, const Table &t, const T *S, int M
   dim3 grid(g->nlt, g->nk, (M + MC - 1) / MC);
   if (grid.z > 65535) return fail(GCAMB_EINVAL, "los_transfer: too many sources for one launch");
   ProfScope prof(GCAMB_K_LOS_PLAIN, st);
-  // E-mode small-x cut: at least 1e-12 and every x the l = 2 row of the table
-  // may have cut (the activity threshold of the tile holding l = 2, the
-  // Miller start of j_2); at most 0.2 (eps_cut <= 1e-3 keeps it near 0.12).
   double x_lo = 1e-12;
-  if (E && g->lmin <= 2) {
-    if (g->lmin >= 1) x_lo = fmax(x_lo, watson_threshold(g->lmin, std::log(g->eps_cut)));
-    if (g->nxs > 2) x_lo = fmax(x_lo, g->xstart[2]);
-    if (!(x_lo <= 0.2)) return fail(GCAMB_EINVAL, "los_transfer_e: eps_cut too large for the l = 2 limit");
-  }
+  if (E && emode_x_lo(g, &x_lo)) return fail(GCAMB_EINVAL, "los_transfer_e: eps_cut too large for the l = 2 limit");
   los_plain_kernel<T, MC, E><<<grid, 256, smem, st>>>(static_cast<const T *>(t.d_data), t.d_nkb, t.d_off, g->nk,
                                                       g->nlt, g->lmin, g->lmax, g->ntau, S, M, Delta, g->d_k,
                                                       g->d_tau, g->tau0, g->d_wtau, x_lo);

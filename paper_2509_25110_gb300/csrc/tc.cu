@@ -57,8 +57,13 @@ struct TcParams {
   const int64_t *off;    // [nk][nlt]
   const int32_t *nkb;    // [nk][nlt]
   const char *sp;        // split sources [nk][n_mt][nkbs] blocks of 256*NT bytes
-  const float *wp;       // [nk][mpad] 4 pi w_k P_m(k)
-  const float *sc;       // fused F16X3: [nk][mpad] power-of-two row scales of the sources
+  const float *wp;       // [nk][mpad] sqrt(4 pi w_k P_m(k))
+  const float *sc;       // fused F16X3: [nk][mpad] power-of-two row scales of the sources;
+                         // TE: [nk][mpad] small-x tail of Delta_E at l = 2
+  const float *dtau;     // TE: [nkbs * 32] tau0 - tau_i in FP32 (1 beyond ntau)
+  const double *kk;      // TE: the k grid
+  float xlo;             // TE: small-x cut of the E-mode source
+  int r2;                // TE: row of l = 2 in the first l-tile, or -1
   const TcItem *items;
   int *counter;          // next item to hand out (zeroed before each launch)
   int nitems;
@@ -151,6 +156,10 @@ __device__ __forceinline__ void tmem_ld(uint32_t taddr, float (&v)[W]) {
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
+  } else if constexpr (W == 4) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr));
   } else {
     static_assert(W == 8, "tmem_ld width");
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
@@ -195,12 +204,22 @@ struct TcRoles {
 // Per-k record, written by the producer into a ring in shared memory:
 // header {q, nb, item, mt | flags}, then the epilogue weights of the k for
 // the item's source tile (bulk copy) and, fused fp16 only, the sources' row
-// scales.  nb < 0 ends the work.
-constexpr int kFirst = 1 << 16, kLast = 1 << 17;
+// scales; TE: the NT/2 models' weights and small-x tails.  nb < 0 ends the
+// work.  kL2: the item's l-tile is the first (it may hold l = 2).
+constexpr int kFirst = 1 << 16, kLast = 1 << 17, kL2 = 1 << 18;
 
-template <int NT, int MODE, bool FUSED>
+// TE (temperature and E-mode together, fused bf16 only): a source tile holds
+// NT/2 models, their FP32 temperature sources in operand rows 0 .. NT/2-1 and
+// their polarisation sources in rows NT/2 .. NT-1 (one TMA box from each).
+// The converters scale the E rows by 1/x^2 (0 below the small-x cut), so
+// that the shared table of w_i j_l gives D_E' = sum_i w_i j_l S_P / x^2; the
+// epilogue adds the l = 2 small-x tail and accumulates, per model,
+// (w D_T)^2, (w D_E')^2 and w^2 D_T D_E'; the reduce applies c_l^2 and c_l.
+template <int NT, int MODE, bool FUSED, bool TE = false>
 __global__ void __launch_bounds__(TcRoles<FUSED>::kThreadsT, 1)
-    los_cl_tc_kernel(const __grid_constant__ CUtensorMap tm_src, TcParams p) {
+    los_cl_tc_kernel(const __grid_constant__ CUtensorMap tm_src, const __grid_constant__ CUtensorMap tm_src2,
+                     TcParams p) {
+  static_assert(!TE || (FUSED && MODE == kBF16 && NT <= 128), "TE: fused bf16, NT <= 128");
   using C = TcCfg<NT, MODE>;
   using G = TcGeom<MODE>;
   using R = TcRoles<FUSED>;
@@ -245,6 +264,8 @@ __global__ void __launch_bounds__(TcRoles<FUSED>::kThreadsT, 1)
   }
   if (FUSED && threadIdx.x == 32)
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tm_src)) : "memory");
+  if (TE && threadIdx.x == 33)
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tm_src2)) : "memory");
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"((uint32_t)C::kTmemCols)
@@ -300,13 +321,21 @@ __global__ void __launch_bounds__(TcRoles<FUSED>::kThreadsT, 1)
           hdr[0] = q;
           hdr[1] = nb;
           hdr[2] = item;
-          hdr[3] = it.mt | (q == it.qb ? kFirst : 0) | (q == it.qe - 1 ? kLast : 0);
+          hdr[3] = it.mt | (q == it.qb ? kFirst : 0) | (q == it.qe - 1 ? kLast : 0) | (TE && it.lt == 0 ? kL2 : 0);
           const uint32_t kb_bar = kfull0 + 8 * ks;
-          mbar_expect_tx(kb_bar, (kScale ? 2 : 1) * NT * 4);
           karmed[ks] = (int)kph;
-          const size_t wrow = (size_t)q * p.mpad + (size_t)it.mt * NT;
-          bulk_g2s(smem_u32(rec + 16), p.wp + wrow, NT * 4, kb_bar);
-          if constexpr (kScale) bulk_g2s(smem_u32(rec + 16 + NT * 4), p.sc + wrow, NT * 4, kb_bar);
+          if constexpr (TE) {
+            // NT/2 models: weights, then the l = 2 tails
+            mbar_expect_tx(kb_bar, NT * 4);
+            const size_t wrow = (size_t)q * p.mpad + (size_t)it.mt * (NT / 2);
+            bulk_g2s(smem_u32(rec + 16), p.wp + wrow, NT * 2, kb_bar);
+            bulk_g2s(smem_u32(rec + 16 + NT * 2), p.sc + wrow, NT * 2, kb_bar);
+          } else {
+            mbar_expect_tx(kb_bar, (kScale ? 2 : 1) * NT * 4);
+            const size_t wrow = (size_t)q * p.mpad + (size_t)it.mt * NT;
+            bulk_g2s(smem_u32(rec + 16), p.wp + wrow, NT * 4, kb_bar);
+            if constexpr (kScale) bulk_g2s(smem_u32(rec + 16 + NT * 4), p.sc + wrow, NT * 4, kb_bar);
+          }
           if (++ks == KS) {
             ks = 0;
             kph ^= 1u;
@@ -322,7 +351,11 @@ __global__ void __launch_bounds__(TcRoles<FUSED>::kThreadsT, 1)
             mbar_expect_tx(full0 + 8 * stage, C::kStageBytes);
             armed_phase[stage] = (int)phase;
             bulk_g2s(sa, a + (size_t)kb * C::kABytes, C::kABytes, full0 + 8 * stage);
-            if constexpr (FUSED)  // FP32 box [NT sources][1 k][32 tau]; zero beyond ntau and M
+            if constexpr (TE) {  // FP32 boxes [NT/2 models][1 k][32 tau] of S_T and S_P
+              tma_load_3d(sa + C::kABytes, &tm_src, kb * 32, q, it.mt * (NT / 2), full0 + 8 * stage);
+              tma_load_3d(sa + C::kABytes + (NT / 2) * 128, &tm_src2, kb * 32, q, it.mt * (NT / 2),
+                          full0 + 8 * stage);
+            } else if constexpr (FUSED)  // FP32 box [NT sources][1 k][32 tau]; zero beyond ntau and M
               tma_load_3d(sa + C::kABytes, &tm_src, kb * 32, q, it.mt * NT, full0 + 8 * stage);
             else
               bulk_g2s(sa + C::kABytes, b + (size_t)kb * C::kBBytes, C::kBBytes, full0 + 8 * stage);
@@ -444,6 +477,8 @@ __global__ void __launch_bounds__(TcRoles<FUSED>::kThreadsT, 1)
 #pragma unroll
           for (int j = 0; j < RJ; ++j) scl[j] = sr[16 * j];
         }
+        float kq = 0.f;  // TE: this k, for x = k (tau0 - tau)
+        if constexpr (TE) kq = (float)p.kk[reinterpret_cast<const volatile int *>(rec)[0]];
         __syncwarp();
         if (lane == 0) mbar_arrive(kempty0 + 8 * ks);
         if (++ks == KS) {
@@ -458,6 +493,17 @@ __global__ void __launch_bounds__(TcRoles<FUSED>::kThreadsT, 1)
           float4 v[RJ];
 #pragma unroll
           for (int j = 0; j < RJ; ++j) v[j] = raw[ct + 128 * j];
+          // TE: 1/x^2 of this thread's four tau nodes (0 below the small-x cut)
+          float f[4] = {1.f, 1.f, 1.f, 1.f};
+          if constexpr (TE) {
+            const float4 dt = __ldg(reinterpret_cast<const float4 *>(p.dtau) + kb * 8 + c4);
+            const float d4[4] = {dt.x, dt.y, dt.z, dt.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const float x = kq * d4[u];
+              f[u] = x >= p.xlo ? 1.f / (x * x) : 0.f;
+            }
+          }
           if (!conv_all(w2)) {
             ok = false;
             break;
@@ -465,6 +511,14 @@ __global__ void __launch_bounds__(TcRoles<FUSED>::kThreadsT, 1)
 #pragma unroll
           for (int j = 0; j < RJ; ++j) {
             float x0 = v[j].x, x1 = v[j].y, x2 = v[j].z, x3 = v[j].w;
+            if constexpr (TE) {
+              if (j >= RJ / 2) {  // rows NT/2 .. NT-1: polarisation sources
+                x0 *= f[0];
+                x1 *= f[1];
+                x2 *= f[2];
+                x3 *= f[3];
+              }
+            }
             uint2 hi, lo;
             if constexpr (MODE == kF16) {
               x0 *= scl[j];
@@ -497,6 +551,80 @@ __global__ void __launch_bounds__(TcRoles<FUSED>::kThreadsT, 1)
           }
         }
         if (!ok) break;
+      }
+    }
+  } else if constexpr (TE) {
+    // ---------------- epilogue (TE): per model j of the thread's quarter,
+    // t = w (D_T), e = w (D_E' + tail at l = 2); tt += t^2, ee += e^2, te += t e
+    constexpr int H = NT / 2, MPT = NT / 4;
+    constexpr int CWE = NT >= 128 ? 4 : 8;
+    const int sp = warp & 3;
+    const int half = (warp - R::kEpi0) >> 2;
+    const int row = sp * 32 + lane;
+    const int j0 = half * MPT;
+    float att[MPT], aee[MPT], ate[MPT];
+#pragma unroll
+    for (int j = 0; j < MPT; ++j) att[j] = aee[j] = ate[j] = 0.f;
+    int n = 0;
+    int ks = 0;
+    uint32_t kph = 0;
+    while (true) {
+      if (!mbar_wait(kfull0 + 8 * ks, kph, abort_flag, p.err)) break;
+      const unsigned char *rec = kslots + ks * C::kSlotBytes;
+      const volatile int *hdr = reinterpret_cast<const volatile int *>(rec);
+      const int nb = hdr[1];
+      if (nb < 0) break;
+      const int item = hdr[2], flags = hdr[3];
+      const int buf = n % NB;
+      const uint32_t use = (uint32_t)(n / NB);
+      if (!mbar_wait(tfull0 + 8 * buf, use & 1u, abort_flag, p.err)) break;
+      tc_fence_after();
+      if (flags & kFirst) {
+#pragma unroll
+        for (int j = 0; j < MPT; ++j) att[j] = aee[j] = ate[j] = 0.f;
+      }
+      const float *wr = reinterpret_cast<const float *>(rec + 16);
+      const float *cr = wr + H;
+      const float cm = ((flags & kL2) && row == p.r2) ? 1.f : 0.f;
+      const uint32_t taddr = tmem + ((uint32_t)(sp * 32) << 16) + (uint32_t)(buf * 2 * NT);
+#pragma unroll
+      for (int c = 0; c < MPT / CWE; ++c) {
+        const int jc = j0 + c * CWE;
+        float th[CWE], tx[CWE], eh[CWE], ex[CWE];
+        tmem_ld<CWE>(taddr + jc, th);
+        tmem_ld<CWE>(taddr + NT + jc, tx);
+        tmem_ld<CWE>(taddr + H + jc, eh);
+        tmem_ld<CWE>(taddr + NT + H + jc, ex);
+        tmem_wait_ld();
+#pragma unroll
+        for (int u = 0; u < CWE; ++u) {
+          const float w = wr[jc + u];
+          const float t = w * (th[u] + tx[u]);
+          const float e = w * fmaf(cm, cr[jc + u], eh[u] + ex[u]);
+          att[c * CWE + u] = fmaf(t, t, att[c * CWE + u]);
+          aee[c * CWE + u] = fmaf(e, e, aee[c * CWE + u]);
+          ate[c * CWE + u] = fmaf(t, e, ate[c * CWE + u]);
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(tempty0 + 8 * buf);
+        mbar_arrive(kempty0 + 8 * ks);
+      }
+      if (++ks == KS) {
+        ks = 0;
+        kph ^= 1u;
+      }
+      ++n;
+      if (flags & kLast) {
+        float *part = p.partial + (size_t)item * 3 * H * 128;
+#pragma unroll
+        for (int j = 0; j < MPT; ++j) {
+          part[(size_t)(j0 + j) * 128 + row] = att[j];
+          part[(size_t)(H + j0 + j) * 128 + row] = aee[j];
+          part[(size_t)(2 * H + j0 + j) * 128 + row] = ate[j];
+        }
       }
     }
   } else {
@@ -824,6 +952,75 @@ __global__ void __launch_bounds__(128) reduce_kernel(const float *__restrict__ p
   Cl[(size_t)perm[m] * (lmax - lmin + 1) + (l - lmin)] = acc;
 }
 
+// TE inputs per (k, model) row, models in caller order: the epilogue weight
+// wq = sqrt(4 pi w_k P) and the small-x tail of Delta_E at l = 2,
+//   tail = sum over the last nodes with x = k (tau0 - tau_i) < x_lo of
+//          w_i S_P[m][k][i] j_2(x)/x^2,
+// with j_2(x)/x^2 = 1/15 - x^2/210 + x^4/7560 - x^6/498960 (x <= 0.2).  x is
+// formed exactly as the converters form it (FP32 k times FP32 tau0 - tau_i),
+// so every node is either in the table sum or in the tail.
+__global__ void __launch_bounds__(256) te_weights_kernel(const double *__restrict__ Pk, const double *__restrict__ wk,
+                                                         const double *__restrict__ kk,
+                                                         const double *__restrict__ wtau,
+                                                         const float *__restrict__ dtau, float xlo,
+                                                         const float *__restrict__ SP, int M, int nk, int ntau,
+                                                         int mpad, float *__restrict__ wq, float *__restrict__ tail) {
+  const size_t row = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= (size_t)nk * mpad) return;
+  const int q = (int)(row / mpad), m = (int)(row - (size_t)q * mpad);
+  float w = 0.f, t = 0.f;
+  if (m < M) {
+    w = (float)sqrt(4.0 * 3.14159265358979323846 * wk[q] * Pk[(size_t)m * nk + q]);
+    const float kq = (float)kk[q];
+    const float *src = SP + ((size_t)m * nk + q) * ntau;
+    double acc = 0.0;
+    for (int i = ntau - 1; i >= 0; --i) {
+      const float x = kq * dtau[i];
+      if (!(x < xlo)) break;
+      const double x2 = (double)x * (double)x;
+      acc += wtau[i] * (double)src[i] * (1.0 / 15.0 - x2 * (1.0 / 210.0 - x2 * (1.0 / 7560.0 - x2 / 498960.0)));
+    }
+    t = (float)acc;
+  }
+  wq[row] = w;
+  tail[row] = t;
+}
+
+// tau0 - tau_i in FP32 for the converters, 1 on the padding of the last block.
+__global__ void __launch_bounds__(256) te_dtau_kernel(const double *__restrict__ tau, double tau0, int ntau, int npad,
+                                                      float *__restrict__ dtau) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < npad) dtau[i] = i < ntau ? (float)(tau0 - tau[i]) : 1.f;
+}
+
+// TE reduce: per (model, l) the FP64 fixed-order sums of the three chunk
+// partials; C^EE = c_l^2 sum, C^TE = c_l sum, c_l^2 = (l+2)(l+1)l(l-1).
+__global__ void __launch_bounds__(128) reduce_te_kernel(const float *__restrict__ partial,
+                                                        const int *__restrict__ tile_ptr,
+                                                        const int *__restrict__ tile_items, int H, int n_mt, int M,
+                                                        int lmin, int lmax, double *__restrict__ ClTT,
+                                                        double *__restrict__ ClEE, double *__restrict__ ClTE) {
+  const int r = threadIdx.x;
+  const int ml = blockIdx.x;
+  const int tile = blockIdx.y;
+  const int lt = tile / n_mt, mt = tile - lt * n_mt;
+  const int m = mt * H + ml;
+  const int l = lmin + lt * kTileL + r;
+  if (m >= M || l > lmax) return;
+  double tt = 0.0, ee = 0.0, te = 0.0;
+  for (int e = tile_ptr[tile]; e < tile_ptr[tile + 1]; ++e) {
+    const float *pp = partial + (size_t)tile_items[e] * 3 * H * 128 + (size_t)ml * 128 + r;
+    tt += (double)pp[0];
+    ee += (double)pp[(size_t)H * 128];
+    te += (double)pp[(size_t)2 * H * 128];
+  }
+  const double c2 = l >= 2 ? (double)(l + 2) * (l + 1) * l * (l - 1) : 0.0;
+  const size_t o = (size_t)m * (lmax - lmin + 1) + (l - lmin);
+  ClTT[o] = tt;
+  ClEE[o] = c2 * ee;
+  ClTE[o] = sqrt(c2) * te;
+}
+
 // ------------------------------------------------------------------ plan
 
 // Work plan of one batched launch.  Sources are processed in plan order:
@@ -835,6 +1032,7 @@ struct TcPlan {
   int mode = -1, M = 0, NT = 0, n_mt = 0, nkbs = 0, mpad = 0, nctas = 0, nitems = 0, ntile = 0;
   bool uniform = true;
   bool fused = false;  // sources converted inside the tensor-core kernel (no split pass)
+  bool te = false;     // temperature + E-mode: NT models per tile, 2 NT operand rows
   std::vector<int> blob;
   size_t o_items = 0, o_tile_ptr = 0, o_tile_items = 0, o_perm = 0, o_nkm = 0, o_lmaxm = 0;
   std::vector<double> cost;  // per item
@@ -920,17 +1118,22 @@ int num_sms() {
 
 // lmax_c / nk_c: per-source l_max and k-prefix length in the caller's order,
 // or null for a uniform batch (every source uses the whole grid).
-void plan_build(const gcamb_grid *g, int M, int mode, int nt, const int *lmax_c, const int *nk_c, TcPlan &pl) {
+//
+// te: a temperature + E-mode plan (uniform, fused bf16): nt models per tile,
+// each with a temperature and a polarisation operand row.
+void plan_build(const gcamb_grid *g, int M, int mode, int nt, const int *lmax_c, const int *nk_c, TcPlan &pl,
+                bool te = false) {
   const ModeLayout lay = mode_layout(mode);
   const Table &t = g->tab[mode];
   pl.mode = mode;
   pl.M = M;
   pl.NT = nt;
+  pl.te = te;
   pl.n_mt = (M + nt - 1) / nt;
   pl.mpad = pl.n_mt * nt;
   pl.nkbs = (g->ntau + lay.kb - 1) / lay.kb;
   pl.uniform = !lmax_c && !nk_c;
-  pl.fused = want_fused(g, mode, nt, pl.uniform);
+  pl.fused = te || want_fused(g, mode, nt, pl.uniform);
   std::vector<int> perm(M), nkm(M), lmm(M);
   for (int m = 0; m < M; ++m) perm[m] = m;
   auto lm_of = [&](int m) { return lmax_c ? lmax_c[m] : g->lmax; };
@@ -1043,11 +1246,14 @@ void plan_build(const gcamb_grid *g, int M, int mode, int nt, const int *lmax_c,
   if (pl.blob.empty()) pl.blob.push_back(0);
   // workspace: split sources (not with the fused kernel), weights, fp16 row
   // scales (fused fp16), k-chunk partials
+  // (te: tau0 - tau in the split-source slot, the l = 2 tails in the scale
+  // slot, three partials per model)
   const size_t row_b = mode == GCAMB_TF32X3 ? 128 : 64;  // operand row bytes of a 32-tau block
-  const size_t sp_bytes = pl.fused ? 0 : (size_t)g->nk * pl.n_mt * pl.nkbs * 2 * row_b * pl.NT;
+  const size_t sp_bytes = te ? (size_t)pl.nkbs * 32 * sizeof(float)
+                             : (pl.fused ? 0 : (size_t)g->nk * pl.n_mt * pl.nkbs * 2 * row_b * pl.NT);
   const size_t wp_bytes = (size_t)g->nk * pl.mpad * sizeof(float);
-  const size_t sc_bytes = (pl.fused && mode == GCAMB_F16X3) ? wp_bytes : 0;
-  const size_t part_bytes = std::max<size_t>(1, pl.nitems) * pl.NT * 128 * sizeof(float);
+  const size_t sc_bytes = (te || (pl.fused && mode == GCAMB_F16X3)) ? wp_bytes : 0;
+  const size_t part_bytes = std::max<size_t>(1, pl.nitems) * (te ? 3 : 1) * pl.NT * 128 * sizeof(float);
   pl.off_sp = 0;
   pl.off_wp = align256(sp_bytes);
   pl.off_sc = pl.off_wp + align256(wp_bytes);
@@ -1074,7 +1280,7 @@ TcPlan *get_plan(const gcamb_grid *g, int M, int mode, int *rc) {
   std::lock_guard<std::mutex> lk(g_plan_mu);
   const int nt = pick_nt(M);
   for (auto &e : g_plans)
-    if (e.first == g && e.second->M == M && e.second->mode == mode && e.second->NT == nt &&
+    if (e.first == g && !e.second->te && e.second->M == M && e.second->mode == mode && e.second->NT == nt &&
         e.second->fused == want_fused(g, mode, nt, true))
       return e.second;
   TcPlan *pl = new TcPlan();
@@ -1088,17 +1294,18 @@ TcPlan *get_plan(const gcamb_grid *g, int M, int mode, int *rc) {
   return pl;
 }
 
-template <int NT, int MODE, bool FUSED>
-int launch_tc_kernel(const gcamb_grid *g, const TcPlan &pl, const CUtensorMap &tm, const TcParams &prm,
-                     cudaStream_t st) {
+template <int NT, int MODE, bool FUSED, bool TE = false>
+int launch_tc_kernel(const gcamb_grid *g, const TcPlan &pl, const CUtensorMap &tm, const CUtensorMap &tm2,
+                     const TcParams &prm, cudaStream_t st) {
   using Cfg = TcCfg<NT, MODE>;
-  cudaError_t e = cudaFuncSetAttribute(los_cl_tc_kernel<NT, MODE, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       Cfg::kSmemBytes);
+  cudaError_t e = cudaFuncSetAttribute(los_cl_tc_kernel<NT, MODE, FUSED, TE>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmemBytes);
   if (e != cudaSuccess) return cuda_fail(e, "los_cl: smem attribute");
   e = cudaMemsetAsync(prm.counter, 0, sizeof(int), st);
   if (e != cudaSuccess) return cuda_fail(e, "los_cl: counter reset");
   ProfScope prof(GCAMB_K_TC, st);
-  los_cl_tc_kernel<NT, MODE, FUSED><<<(unsigned)pl.nctas, TcRoles<FUSED>::kThreadsT, Cfg::kSmemBytes, st>>>(tm, prm);
+  los_cl_tc_kernel<NT, MODE, FUSED, TE>
+      <<<(unsigned)pl.nctas, TcRoles<FUSED>::kThreadsT, Cfg::kSmemBytes, st>>>(tm, tm2, prm);
   return GCAMB_OK;
 }
 
@@ -1146,15 +1353,16 @@ int launch_tc(const gcamb_grid *g, const TcPlan &pl, const float *S, const doubl
   }
   if (pl.nitems > 0) {
     int *ctr = reinterpret_cast<int *>(ws + pl.off_ctr);
-    TcParams prm{static_cast<const char *>(t.d_data), t.d_off, t.d_nkb, sp, wp, sc, pl.items(B), ctr, pl.nitems, part,
-                 use_err_word ? err_word : device_error_flag(), g->nlt, pl.n_mt, pl.nkbs, pl.mpad};
+    TcParams prm{static_cast<const char *>(t.d_data), t.d_off, t.d_nkb, sp, wp, sc, nullptr, nullptr, 0.f, -1,
+                 pl.items(B), ctr, pl.nitems, part, use_err_word ? err_word : device_error_flag(), g->nlt, pl.n_mt,
+                 pl.nkbs, pl.mpad};
     if (!prm.err && !use_err_word) return fail(GCAMB_ECUDA, "los_cl: error flag allocation");
     int rc;
     if constexpr (kCanFuse)
-      rc = fused ? launch_tc_kernel<NT, MODE, true>(g, pl, tm, prm, st)
-                 : launch_tc_kernel<NT, MODE, false>(g, pl, tm, prm, st);
+      rc = fused ? launch_tc_kernel<NT, MODE, true>(g, pl, tm, tm, prm, st)
+                 : launch_tc_kernel<NT, MODE, false>(g, pl, tm, tm, prm, st);
     else
-      rc = launch_tc_kernel<NT, MODE, false>(g, pl, tm, prm, st);
+      rc = launch_tc_kernel<NT, MODE, false>(g, pl, tm, tm, prm, st);
     if (rc) return rc;
   }
   dim3 rgrid(NT, pl.ntile);
@@ -1185,7 +1393,97 @@ int launch_plan(const gcamb_grid *g, const TcPlan &pl, const float *S, const dou
   }
 }
 
+// Models per tile of a temperature + E-mode batch (operand rows = twice
+// that): 32 for small batches, else 64; GCAMB_TC_NT=64|128 (operand rows)
+// overrides it.
+int pick_h_te(int M) {
+  int h = 2 * M <= 64 ? 32 : 64;
+  if (const char *e = getenv("GCAMB_TC_NT")) {
+    const int v = atoi(e);
+    if (v == 64 || v == 128) h = v / 2;
+  }
+  return h;
+}
+
+TcPlan *get_plan_te(const gcamb_grid *g, int M, int *rc) {
+  std::lock_guard<std::mutex> lk(g_plan_mu);
+  const int h = pick_h_te(M);
+  for (auto &e : g_plans)
+    if (e.first == g && e.second->te && e.second->M == M && e.second->NT == h) return e.second;
+  TcPlan *pl = new TcPlan();
+  plan_build(g, M, GCAMB_BF16X3, h, nullptr, nullptr, *pl, true);
+  if ((*rc = upload_blob(*pl)) != GCAMB_OK) {
+    pl->release();
+    delete pl;
+    return nullptr;
+  }
+  g_plans.push_back({g, pl});
+  return pl;
+}
+
+// Temperature + E-mode batch: tau0 - tau in FP32, weights and l = 2 tails,
+// the tensor-core kernel over NT = 2 H operand rows per tile, the TE reduce.
+template <int NT>
+int launch_tc_te(const gcamb_grid *g, const TcPlan &pl, const float *ST, const float *SP, const double *Pk,
+                 double *ClTT, double *ClEE, double *ClTE, char *ws, double xlo, cudaStream_t st) {
+  constexpr int H = NT / 2;
+  const Table &t = g->tab[GCAMB_BF16X3];
+  float *dt = reinterpret_cast<float *>(ws + pl.off_sp);
+  float *wp = reinterpret_cast<float *>(ws + pl.off_wp);
+  float *tail = reinterpret_cast<float *>(ws + pl.off_sc);
+  float *part = reinterpret_cast<float *>(ws + pl.off_part);
+  const int *B = pl.d_blob;
+  CUtensorMap tm1, tm2;
+  memset(&tm1, 0, sizeof tm1);
+  memset(&tm2, 0, sizeof tm2);
+  if (int rc = encode_sources(&tm1, ST, pl.M, g->nk, g->ntau, H)) return rc;
+  if (int rc = encode_sources(&tm2, SP, pl.M, g->nk, g->ntau, H)) return rc;
+  const float xlof = (float)xlo;
+  {
+    ProfScope prof(GCAMB_K_SPLIT, st);
+    const int npad = pl.nkbs * 32;
+    te_dtau_kernel<<<(npad + 255) / 256, 256, 0, st>>>(g->d_tau, g->tau0, g->ntau, npad, dt);
+    const size_t rows = (size_t)g->nk * pl.mpad;
+    te_weights_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(Pk, g->d_wk, g->d_k, g->d_wtau, dt, xlof, SP,
+                                                                      pl.M, g->nk, g->ntau, pl.mpad, wp, tail);
+  }
+  if (pl.nitems > 0) {
+    int *ctr = reinterpret_cast<int *>(ws + pl.off_ctr);
+    const int r2 = (g->lmin <= 2 && g->lmax >= 2) ? 2 - g->lmin : -1;
+    TcParams prm{static_cast<const char *>(t.d_data), t.d_off, t.d_nkb, nullptr, wp, tail, dt, g->d_k, xlof, r2,
+                 pl.items(B), ctr, pl.nitems, part, device_error_flag(), g->nlt, pl.n_mt, pl.nkbs, pl.mpad};
+    if (!prm.err) return fail(GCAMB_ECUDA, "los_cl_te: error flag allocation");
+    if (int rc = launch_tc_kernel<NT, kBF16, true, true>(g, pl, tm1, tm2, prm, st)) return rc;
+  }
+  dim3 rgrid(H, pl.ntile);
+  ProfScope prof(GCAMB_K_REDUCE, st);
+  reduce_te_kernel<<<rgrid, 128, 0, st>>>(part, B + pl.o_tile_ptr, B + pl.o_tile_items, H, pl.n_mt, pl.M, g->lmin,
+                                          g->lmax, ClTT, ClEE, ClTE);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "los_cl_te: launch");
+  return GCAMB_OK;
+}
+
 }  // namespace
+
+size_t los_cl_te_workspace_bytes(const gcamb_grid *g, int M) {
+  int rc = 0;
+  TcPlan *p = get_plan_te(g, M, &rc);
+  return p ? p->ws_bytes : 0;
+}
+
+int launch_los_cl_te(const gcamb_grid *g, const float *ST, const float *SP, const double *Pk, int M, double *ClTT,
+                     double *ClEE, double *ClTE, void *ws, size_t ws_bytes, cudaStream_t st) {
+  double xlo = 0.0;
+  if (emode_x_lo(g, &xlo)) return fail(GCAMB_EINVAL, "los_cl_te: eps_cut too large for the l = 2 limit");
+  int rc = 0;
+  TcPlan *pl = get_plan_te(g, M, &rc);
+  if (!pl) return rc ? rc : fail(GCAMB_ECUDA, "los_cl_te: plan");
+  if (ws_bytes < pl->ws_bytes) return fail(GCAMB_EINVAL, "los_cl_te: workspace too small");
+  char *w = static_cast<char *>(ws);
+  return pl->NT == 32 ? launch_tc_te<64>(g, *pl, ST, SP, Pk, ClTT, ClEE, ClTE, w, xlo, st)
+                      : launch_tc_te<128>(g, *pl, ST, SP, Pk, ClTT, ClEE, ClTE, w, xlo, st);
+}
 
 size_t los_cl_workspace_bytes(const gcamb_grid *g, int M, int mode) {
   if (!g->tab[mode].built) {

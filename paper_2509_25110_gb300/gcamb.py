@@ -60,6 +60,9 @@ def lib():
     L.gcamb_cl_cross.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp]
     L.gcamb_los_cl_workspace.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
     L.gcamb_los_cl.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_size_t, _vp]
+    L.gcamb_los_cl_te_workspace.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
+    L.gcamb_los_cl_te.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp,
+                                  ctypes.c_size_t, _vp]
     L.gcamb_sync.argtypes = [_vp]
     L.gcamb_plan_create.argtypes = [_vp, ctypes.c_int, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp)]
     L.gcamb_plan_destroy.argtypes = [_vp]
@@ -288,6 +291,31 @@ def los_cl(g: Grid, S, Pk, mode: int, Cl=None, ws=None, stream=None):
                               _dev(Cl, torch.float64, (M, g.nl), "Cl"), _dev(ws, torch.uint8, name="ws"),
                               ws.numel(), _stream(stream)))
     return Cl
+
+
+def los_cl_te_workspace(g: Grid, M: int, mode: int = BF16X3) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().gcamb_los_cl_te_workspace(g.handle, M, int(mode), ctypes.byref(b)))
+    return b.value
+
+
+def los_cl_te(g: Grid, ST, SP, Pk, mode: int = BF16X3, out=None, ws=None, stream=None):
+    """Batched temperature + E-mode on the tensor cores (Eqs. 1-3):
+    ST, SP[M][nk][ntau] FP32 -> (C^TT, C^EE, C^TE), each [M][nl] FP64."""
+    import torch
+    M = ST.shape[0]
+    if ws is None:
+        ws = torch.empty(max(1, los_cl_te_workspace(g, M, mode)), dtype=torch.uint8, device=ST.device)
+    if out is None:
+        out = tuple(torch.empty((M, g.nl), dtype=torch.float64, device=ST.device) for _ in range(3))
+    tt, ee, te = out
+    _check(lib().gcamb_los_cl_te(g.handle, _dev(ST, torch.float32, (M, g.nk, g.ntau), "ST"),
+                                 _dev(SP, torch.float32, (M, g.nk, g.ntau), "SP"),
+                                 _dev(Pk, torch.float64, (M, g.nk), "Pk"), M, int(mode),
+                                 _dev(tt, torch.float64, (M, g.nl), "ClTT"), _dev(ee, torch.float64, (M, g.nl), "ClEE"),
+                                 _dev(te, torch.float64, (M, g.nl), "ClTE"), _dev(ws, torch.uint8, name="ws"),
+                                 ws.numel(), _stream(stream)))
+    return tt, ee, te
 
 
 class Plan:
