@@ -52,7 +52,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nk", type=int, default=0,
                     help="profiling case: the same k range with this many nodes (default: the workload's 2000)")
-    ap.add_argument("--workload", default="batched", choices=["batched", "uneven", "emulator"],
+    ap.add_argument("--workload", default="batched", choices=["batched", "uneven", "emulator", "te"],
                     help="batched (the headline), uneven (1000 sources, l_max <= 6000, plan + graph), "
                          "emulator (train on 100k spectra, serve)")
     ap.add_argument("--kernel-only", action="store_true",
@@ -179,6 +179,22 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def committed_traffic(name, mode):
+    """DRAM bytes per launch of the tensor-core kernel from the committed ncu
+    summary `profiles/<name>`, or None once tc.cu has changed since it was
+    taken (the summary records tc.cu's SHA-1)."""
+    try:
+        import hashlib
+        with open(os.path.join(ROOT, "profiles", name)) as f:
+            tr = json.load(f)
+        src = open(os.path.join(ROOT, "paper_2509_25110_gb300", "csrc", "tc.cu"), "rb").read()
+        if tr.get("tc_cu_sha1") == hashlib.sha1(src).hexdigest() and tr.get("mode") == mode:
+            return tr["dram_bytes_per_launch"]
+    except Exception:
+        pass
+    return None
+
+
 # ------------------------------------------------------------------ other workloads
 
 def _timed_region(fn, steps, dev):
@@ -280,6 +296,108 @@ def run_emulator(args):
     print(json.dumps(line), flush=True)
 
 
+def run_te(args):
+    """Temperature + E-mode on the 256-model, l_max = 2500 grid: C^TT, C^EE and
+    C^TE per model from one tensor-core kernel (gcamb_los_cl_te), against the
+    temperature-only batch on the same grid and the plain FP64 path."""
+    import numpy as np
+    import torch
+
+    from paper_2509_25110_gb300 import build, gcamb, synth
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    build.build()
+    peaks, peak_src = load_peaks()
+    wl = synth.workload(WORKLOAD)
+    if args.nk:
+        wl.k = synth.log_grid(float(wl.k[0]), float(wl.k[-1]), args.nk)
+    M = wl.M
+    p = synth.model_params(M, seed=0)
+    ST = synth.sources_torch(wl.k, wl.tau, p, dev, torch.float32)
+    SP = synth.sources_pol_torch(wl.k, wl.tau, p, dev, torch.float32)
+    P = torch.as_tensor(synth.primordial(wl.k, p), device=dev)
+    g = gcamb.grid_create(wl.k, wl.tau, wl.tau0, wl.lmin, wl.lmax)
+    info = gcamb.grid_info(g)
+    gcamb.bessel_table(g, gcamb.BF16X3)
+    ws = torch.empty(gcamb.los_cl_te_workspace(g, M), dtype=torch.uint8, device=dev)
+    out = tuple(torch.empty((M, wl.nl), dtype=torch.float64, device=dev) for _ in range(3))
+    for _ in range(max(3, args.warmup)):
+        gcamb.los_cl_te(g, ST, SP, P, out=out, ws=ws)
+    gcamb.sync()
+    steps = args.steps
+    gcamb.profile_enable(True)
+    ms, clocks = _timed_region(lambda: gcamb.los_cl_te(g, ST, SP, P, out=out, ws=ws), steps, dev)
+    gcamb.sync()
+    kern = {gcamb.K_NAMES[i]: gcamb.profile_read(i) for i in (gcamb.K_SPLIT, gcamb.K_TC, gcamb.K_REDUCE)}
+    gcamb.profile_enable(False)
+    tc_ms, tc_n = kern["los_cl_tc"]
+    tc_avg_s = tc_ms / max(1, tc_n) * 1e-3
+    # the table (hi + lo, 4 bytes an active entry) once, both FP32 sources once
+    alg_bytes = info["active"] * 4 + 2 * M * wl.nk * wl.ntau * 4
+    alg_flops = 3 * 2 * info["active"] * 2 * M
+    achieved = alg_bytes / tc_avg_s / 1e9
+    # the temperature-only batch on the same grid and sources
+    wsT = torch.empty(gcamb.los_cl_workspace(g, M, gcamb.BF16X3), dtype=torch.uint8, device=dev)
+    CT = torch.empty((M, wl.nl), dtype=torch.float64, device=dev)
+    for _ in range(3):
+        gcamb.los_cl(g, ST, P, gcamb.BF16X3, CT, wsT)
+    t_ms, _ = _timed_region(lambda: gcamb.los_cl(g, ST, P, gcamb.BF16X3, CT, wsT), steps, dev)
+    gcamb.sync()
+    # plain FP64 TT, EE, TE of 4 models on the same grid
+    gcamb.bessel_table(g, gcamb.PLAIN64)
+    S64, P64 = ST[:4].double().contiguous(), P[:4].contiguous()
+    E64 = SP[:4].double().contiguous()
+
+    def plain_step():
+        DT = gcamb.los_transfer(g, S64, gcamb.PLAIN64)
+        DE = gcamb.los_transfer_e(g, E64, gcamb.PLAIN64)
+        gcamb.cl(g, DT, P64)
+        gcamb.cl_cross(g, DE, DE, P64)
+        gcamb.cl_cross(g, DT, DE, P64)
+    plain_step()
+    plain_ms, _ = _timed_region(plain_step, 2, dev)
+    plain_rate = 4 / (plain_ms / 2 * 1e-3)
+    gcamb.sync()
+    # the oracle on one model: accuracy and the CPU baseline
+    cpu = None
+    err = None
+    if not args.no_cpu_baseline:
+        import oracle
+        from oracle import build as ob
+        ob.build()
+        Sc, Ec, Pc = ST[:1].double().cpu().numpy(), SP[:1].double().cpu().numpy(), P[:1].cpu().numpy()
+        t0 = time.perf_counter()
+        DT, TT = oracle.los_cl(wl.k, wl.tau, wl.tau0, wl.lmin, wl.lmax, Sc, Pc)
+        DE = oracle.los_e(wl.k, wl.tau, wl.tau0, wl.lmin, wl.lmax, Ec)
+        EE = oracle.cl_cross(wl.k, DE, DE, Pc)
+        TE = oracle.cl_cross(wl.k, DT, DE, Pc)
+        dt = time.perf_counter() - t0
+        cpu = {"value": 1 / dt, "unit": "models/s (TT, EE, TE)", "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": "1 of the 256 models, full grid, %.1f s" % dt}
+        tt, ee, te = (x[:1].cpu().numpy() for x in out)
+        nz = EE > 0
+        err = {"TT": float(np.max(np.abs(tt / TT - 1))), "EE": float(np.max(np.abs(ee[nz] / EE[nz] - 1))),
+               "TE_on_sqrt_TT_EE": float(np.max(np.abs(te - TE)[nz] / np.sqrt(TT * EE)[nz]))}
+    line = {"metric": "TT+EE+TE spectrum sets/sec at l_max=2500, batched split precision (bf16x3)",
+            "value": M * steps / (ms * 1e-3), "unit": "models/s", "n_gpus": 1, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "batched_te_lmax2500", "M": M, "lmax": wl.lmax, "nk": wl.nk, "ntau": wl.ntau,
+                       "l2": "inputs larger than L2 (two 2.05 GB fp32 sources)",
+                       "tt_only_ms_per_step": t_ms / steps, "te_over_tt_only_time": ms / t_ms,
+                       "plain64_models_per_s": plain_rate, "speedup_vs_plain64": M * steps / (ms * 1e-3) / plain_rate,
+                       "max_err_vs_oracle": err,
+                       "kernel_ms": {k: (v[0] / max(1, v[1])) for k, v in kern.items()}},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": achieved / peaks["hbm_gbs"],
+                         "traffic": committed_traffic("los_cl_tc_te_traffic.txt", "te_bf16x3"), "peak_source": peak_src,
+                         "kernel": "los_cl_tc_kernel (TE)", "kernel_ms": tc_avg_s * 1e3, "algorithmic_bytes": alg_bytes,
+                         "tensor_view": {"achieved_tflops": alg_flops / tc_avg_s / 1e12,
+                                         "frac": alg_flops / tc_avg_s / 1e12 / peaks.get("bf16_tflops", 1900.0)}},
+            "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": 4 * steps}
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------------ our arm
 
 def main():
@@ -292,6 +410,9 @@ def main():
         return
     if args.workload == "emulator":
         run_emulator(args)
+        return
+    if args.workload == "te":
+        run_te(args)
         return
     import numpy as np
     import torch
@@ -386,16 +507,7 @@ def main():
     alg_bytes = info["active"] * pair + M * wl.nk * wl.ntau * pair
     alg_flops = 3 * 2 * info["active"] * M                             # three split products
     achieved_gbs = alg_bytes / tc_avg_s / 1e9
-    traffic = None
-    try:
-        with open(os.path.join(ROOT, "profiles", "los_cl_tc_traffic.txt")) as f:
-            tr = json.load(f)
-        import hashlib
-        src = open(os.path.join(ROOT, "paper_2509_25110_gb300", "csrc", "tc.cu"), "rb").read()
-        if tr.get("tc_cu_sha1") == hashlib.sha1(src).hexdigest() and tr.get("mode") == args.mode:
-            traffic = tr["dram_bytes_per_launch"]
-    except Exception:
-        pass
+    traffic = committed_traffic("los_cl_tc_traffic.txt", args.mode)
     roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved_gbs / peaks["hbm_gbs"], "traffic": traffic,
                 "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src,

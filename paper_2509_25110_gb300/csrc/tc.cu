@@ -43,8 +43,6 @@ namespace {
 
 constexpr int kEpiWarps = 8;
 constexpr int kConvWarps = 4;
-constexpr int kThreads = 32 * (2 + kEpiWarps);
-constexpr int kThreadsFused = 32 * (2 + kConvWarps + kEpiWarps);
 constexpr int kKChunkMax = 64;     // k per work item: bounds the FP32 partial-sum length
 constexpr int kSmemBudget = 196608;
 
@@ -60,9 +58,7 @@ struct TcParams {
   const float *wp;       // [nk][mpad] sqrt(4 pi w_k P_m(k))
   const float *sc;       // fused F16X3: [nk][mpad] power-of-two row scales of the sources;
                          // TE: [nk][mpad] small-x tail of Delta_E at l = 2
-  const float *dtau;     // TE: [nkbs * 32] tau0 - tau_i in FP32 (1 beyond ntau)
-  const double *kk;      // TE: the k grid
-  float xlo;             // TE: small-x cut of the E-mode source
+  const float *ix2;      // TE: [nk][nkbs * 32] 1/x^2 of each node (0 below the small-x cut and beyond ntau)
   int r2;                // TE: row of l = 2 in the first l-tile, or -1
   const TcItem *items;
   int *counter;          // next item to hand out (zeroed before each launch)
@@ -188,17 +184,19 @@ struct TcCfg {
   static constexpr int kKSlots = 4;                      // per-k records in flight
   static constexpr int kSlotBytes = 16 + 8 * NT;         // header, weights, row scales
   static constexpr int kQBytes = kKChunkMax * 12;        // the item's block counts and offsets
+  static constexpr int kFBytes = kStages * 128;          // TE: 1/x^2 of each stage's 32 nodes
   static constexpr int kSmemBytes =
-      kStages * kStageBytes + kKSlots * kSlotBytes + kQBytes + 1024 /*align*/ + 512 /*barriers*/;
+      kStages * kStageBytes + kFBytes + kKSlots * kSlotBytes + kQBytes + 1024 /*align*/ + 512 /*barriers*/;
   static constexpr int kColsPerThread = NT / 2;
   static constexpr int kChunk = NT >= 128 ? 8 : 16;      // TMEM load width (register budget)
 };
 
-template <bool FUSED>
+template <bool FUSED, bool TE = false>
 struct TcRoles {
   static constexpr int kConv = FUSED ? kConvWarps : 0;
   static constexpr int kEpi0 = 2 + kConv;  // first epilogue warp
-  static constexpr int kThreadsT = FUSED ? kThreadsFused : kThreads;
+  static constexpr int kEpi = kEpiWarps;
+  static constexpr int kThreadsT = 32 * (2 + kConv + kEpi);
 };
 
 // Per-k record, written by the producer into a ring in shared memory:
@@ -216,20 +214,21 @@ constexpr int kFirst = 1 << 16, kLast = 1 << 17, kL2 = 1 << 18;
 // epilogue adds the l = 2 small-x tail and accumulates, per model,
 // (w D_T)^2, (w D_E')^2 and w^2 D_T D_E'; the reduce applies c_l^2 and c_l.
 template <int NT, int MODE, bool FUSED, bool TE = false>
-__global__ void __launch_bounds__(TcRoles<FUSED>::kThreadsT, 1)
+__global__ void __launch_bounds__(TcRoles<FUSED, TE>::kThreadsT, 1)
     los_cl_tc_kernel(const __grid_constant__ CUtensorMap tm_src, const __grid_constant__ CUtensorMap tm_src2,
                      TcParams p) {
   static_assert(!TE || (FUSED && MODE == kBF16 && NT <= 128), "TE: fused bf16, NT <= 128");
   using C = TcCfg<NT, MODE>;
   using G = TcGeom<MODE>;
-  using R = TcRoles<FUSED>;
+  using R = TcRoles<FUSED, TE>;
   constexpr int S = C::kStages;
   constexpr int NB = C::kNBuf;
   constexpr int KS = C::kKSlots;
   constexpr bool kScale = FUSED && MODE == kF16;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  unsigned char *kslots = smem + S * C::kStageBytes;
+  unsigned char *fbuf = smem + S * C::kStageBytes;  // TE: [S][32] floats
+  unsigned char *kslots = fbuf + C::kFBytes;
   int64_t *q_off = reinterpret_cast<int64_t *>(kslots + KS * C::kSlotBytes);  // [kKChunkMax]
   int32_t *q_nb = reinterpret_cast<int32_t *>(q_off + kKChunkMax);           // [kKChunkMax]
   uint64_t *bars = reinterpret_cast<uint64_t *>(kslots + KS * C::kSlotBytes + C::kQBytes);
@@ -252,12 +251,12 @@ __global__ void __launch_bounds__(TcRoles<FUSED>::kThreadsT, 1)
     }
     for (int s = 0; s < KS; ++s) {
       mbar_init(kfull0 + 8 * s, 1);
-      mbar_init(kempty0 + 8 * s, 1 + kEpiWarps + R::kConv);
+      mbar_init(kempty0 + 8 * s, 1 + R::kEpi + R::kConv);
     }
     mbar_init(tfull0, 1);
     mbar_init(tfull0 + 8, 1);
-    mbar_init(tempty0, kEpiWarps);
-    mbar_init(tempty0 + 8, kEpiWarps);
+    mbar_init(tempty0, R::kEpi);
+    mbar_init(tempty0 + 8, R::kEpi);
     mbar_init(drain, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -348,9 +347,11 @@ __global__ void __launch_bounds__(TcRoles<FUSED>::kThreadsT, 1)
               break;
             }
             const uint32_t sa = smem_u32(smem + stage * C::kStageBytes);
-            mbar_expect_tx(full0 + 8 * stage, C::kStageBytes);
+            mbar_expect_tx(full0 + 8 * stage, C::kStageBytes + (TE ? 128 : 0));
             armed_phase[stage] = (int)phase;
             bulk_g2s(sa, a + (size_t)kb * C::kABytes, C::kABytes, full0 + 8 * stage);
+            if constexpr (TE)  // the block's 32 values of 1/x^2
+              bulk_g2s(smem_u32(fbuf + stage * 128), p.ix2 + ((size_t)q * p.nkbs + kb) * 32, 128, full0 + 8 * stage);
             if constexpr (TE) {  // FP32 boxes [NT/2 models][1 k][32 tau] of S_T and S_P
               tma_load_3d(sa + C::kABytes, &tm_src, kb * 32, q, it.mt * (NT / 2), full0 + 8 * stage);
               tma_load_3d(sa + C::kABytes + (NT / 2) * 128, &tm_src2, kb * 32, q, it.mt * (NT / 2),
@@ -477,8 +478,6 @@ __global__ void __launch_bounds__(TcRoles<FUSED>::kThreadsT, 1)
 #pragma unroll
           for (int j = 0; j < RJ; ++j) scl[j] = sr[16 * j];
         }
-        float kq = 0.f;  // TE: this k, for x = k (tau0 - tau)
-        if constexpr (TE) kq = (float)p.kk[reinterpret_cast<const volatile int *>(rec)[0]];
         __syncwarp();
         if (lane == 0) mbar_arrive(kempty0 + 8 * ks);
         if (++ks == KS) {
@@ -493,17 +492,9 @@ __global__ void __launch_bounds__(TcRoles<FUSED>::kThreadsT, 1)
           float4 v[RJ];
 #pragma unroll
           for (int j = 0; j < RJ; ++j) v[j] = raw[ct + 128 * j];
-          // TE: 1/x^2 of this thread's four tau nodes (0 below the small-x cut)
-          float f[4] = {1.f, 1.f, 1.f, 1.f};
-          if constexpr (TE) {
-            const float4 dt = __ldg(reinterpret_cast<const float4 *>(p.dtau) + kb * 8 + c4);
-            const float d4[4] = {dt.x, dt.y, dt.z, dt.w};
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const float x = kq * d4[u];
-              f[u] = x >= p.xlo ? 1.f / (x * x) : 0.f;
-            }
-          }
+          // TE: 1/x^2 of this thread's four tau nodes (copied with the stage)
+          float4 f = make_float4(1.f, 1.f, 1.f, 1.f);
+          if constexpr (TE) f = reinterpret_cast<const float4 *>(fbuf + stage * 128)[c4];
           if (!conv_all(w2)) {
             ok = false;
             break;
@@ -513,10 +504,10 @@ __global__ void __launch_bounds__(TcRoles<FUSED>::kThreadsT, 1)
             float x0 = v[j].x, x1 = v[j].y, x2 = v[j].z, x3 = v[j].w;
             if constexpr (TE) {
               if (j >= RJ / 2) {  // rows NT/2 .. NT-1: polarisation sources
-                x0 *= f[0];
-                x1 *= f[1];
-                x2 *= f[2];
-                x3 *= f[3];
+                x0 *= f.x;
+                x1 *= f.y;
+                x2 *= f.z;
+                x3 *= f.w;
               }
             }
             uint2 hi, lo;
@@ -556,8 +547,8 @@ __global__ void __launch_bounds__(TcRoles<FUSED>::kThreadsT, 1)
   } else if constexpr (TE) {
     // ---------------- epilogue (TE): per model j of the thread's quarter,
     // t = w (D_T), e = w (D_E' + tail at l = 2); tt += t^2, ee += e^2, te += t e
-    constexpr int H = NT / 2, MPT = NT / 4;
-    constexpr int CWE = NT >= 128 ? 4 : 8;
+    constexpr int H = NT / 2, MPT = H / 2;
+    constexpr int CWE = NT >= 128 ? 4 : 8;  // TMEM load width (register budget)
     const int sp = warp & 3;
     const int half = (warp - R::kEpi0) >> 2;
     const int row = sp * 32 + lane;
@@ -585,6 +576,7 @@ __global__ void __launch_bounds__(TcRoles<FUSED>::kThreadsT, 1)
       }
       const float *wr = reinterpret_cast<const float *>(rec + 16);
       const float *cr = wr + H;
+      // the small-x tail at l = 2: lane r2 of the first l-tile only
       const float cm = ((flags & kL2) && row == p.r2) ? 1.f : 0.f;
       const uint32_t taddr = tmem + ((uint32_t)(sp * 32) << 16) + (uint32_t)(buf * 2 * NT);
 #pragma unroll
@@ -952,17 +944,34 @@ __global__ void __launch_bounds__(128) reduce_kernel(const float *__restrict__ p
   Cl[(size_t)perm[m] * (lmax - lmin + 1) + (l - lmin)] = acc;
 }
 
+// 1/x^2 of every node, x = k (tau0 - tau_i), in FP32 for the converters:
+// 0 below the small-x cut x_lo and on the padding beyond ntau (whose
+// sources are zero).  [nk][npad], npad = 32 * the tau-blocks.
+__global__ void __launch_bounds__(256) te_ix2_kernel(const double *__restrict__ kk, const double *__restrict__ tau,
+                                                     double tau0, double xlo, int nk, int ntau, int npad,
+                                                     float *__restrict__ ix2) {
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (size_t)nk * npad) return;
+  const int q = (int)(e / npad), i = (int)(e - (size_t)q * npad);
+  float v = 0.f;
+  if (i < ntau) {
+    const double x = kk[q] * (tau0 - tau[i]);
+    if (x >= xlo) v = (float)(1.0 / (x * x));
+  }
+  ix2[e] = v;
+}
+
 // TE inputs per (k, model) row, models in caller order: the epilogue weight
 // wq = sqrt(4 pi w_k P) and the small-x tail of Delta_E at l = 2,
-//   tail = sum over the last nodes with x = k (tau0 - tau_i) < x_lo of
-//          w_i S_P[m][k][i] j_2(x)/x^2,
-// with j_2(x)/x^2 = 1/15 - x^2/210 + x^4/7560 - x^6/498960 (x <= 0.2).  x is
-// formed exactly as the converters form it (FP32 k times FP32 tau0 - tau_i),
-// so every node is either in the table sum or in the tail.
+//   tail = sum over the nodes with x = k (tau0 - tau_i) < x_lo (the last
+//          ones: x falls with tau) of w_i S_P[m][k][i] j_2(x)/x^2,
+// with j_2(x)/x^2 = 1/15 - x^2/210 + x^4/7560 - x^6/498960 (x <= 0.2).  The
+// test x < x_lo is the one te_ix2_kernel makes, so every node is either in
+// the table sum or in the tail.
 __global__ void __launch_bounds__(256) te_weights_kernel(const double *__restrict__ Pk, const double *__restrict__ wk,
                                                          const double *__restrict__ kk,
+                                                         const double *__restrict__ tau, double tau0, double xlo,
                                                          const double *__restrict__ wtau,
-                                                         const float *__restrict__ dtau, float xlo,
                                                          const float *__restrict__ SP, int M, int nk, int ntau,
                                                          int mpad, float *__restrict__ wq, float *__restrict__ tail) {
   const size_t row = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -971,26 +980,18 @@ __global__ void __launch_bounds__(256) te_weights_kernel(const double *__restric
   float w = 0.f, t = 0.f;
   if (m < M) {
     w = (float)sqrt(4.0 * 3.14159265358979323846 * wk[q] * Pk[(size_t)m * nk + q]);
-    const float kq = (float)kk[q];
     const float *src = SP + ((size_t)m * nk + q) * ntau;
     double acc = 0.0;
     for (int i = ntau - 1; i >= 0; --i) {
-      const float x = kq * dtau[i];
-      if (!(x < xlo)) break;
-      const double x2 = (double)x * (double)x;
+      const double x = kk[q] * (tau0 - tau[i]);
+      if (x >= xlo) break;
+      const double x2 = x * x;
       acc += wtau[i] * (double)src[i] * (1.0 / 15.0 - x2 * (1.0 / 210.0 - x2 * (1.0 / 7560.0 - x2 / 498960.0)));
     }
     t = (float)acc;
   }
   wq[row] = w;
   tail[row] = t;
-}
-
-// tau0 - tau_i in FP32 for the converters, 1 on the padding of the last block.
-__global__ void __launch_bounds__(256) te_dtau_kernel(const double *__restrict__ tau, double tau0, int ntau, int npad,
-                                                      float *__restrict__ dtau) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < npad) dtau[i] = i < ntau ? (float)(tau0 - tau[i]) : 1.f;
 }
 
 // TE reduce: per (model, l) the FP64 fixed-order sums of the three chunk
@@ -1038,6 +1039,7 @@ struct TcPlan {
   std::vector<double> cost;  // per item
   int *d_blob = nullptr;
   bool own_blob = false;
+  float *d_ix2 = nullptr;  // te: 1/x^2 per node [nk][nkbs * 32], built with the plan
   size_t off_sp = 0, off_wp = 0, off_sc = 0, off_part = 0, off_ctr = 0, ws_bytes = 0;
 
   const TcItem *items(const int *base) const { return reinterpret_cast<const TcItem *>(base + o_items); }
@@ -1045,6 +1047,8 @@ struct TcPlan {
     if (own_blob && d_blob) cudaFree(d_blob);
     d_blob = nullptr;
     own_blob = false;
+    if (d_ix2) cudaFree(d_ix2);
+    d_ix2 = nullptr;
   }
 };
 
@@ -1246,11 +1250,9 @@ void plan_build(const gcamb_grid *g, int M, int mode, int nt, const int *lmax_c,
   if (pl.blob.empty()) pl.blob.push_back(0);
   // workspace: split sources (not with the fused kernel), weights, fp16 row
   // scales (fused fp16), k-chunk partials
-  // (te: tau0 - tau in the split-source slot, the l = 2 tails in the scale
-  // slot, three partials per model)
+  // (te: the l = 2 tails in the scale slot, three partials per model)
   const size_t row_b = mode == GCAMB_TF32X3 ? 128 : 64;  // operand row bytes of a 32-tau block
-  const size_t sp_bytes = te ? (size_t)pl.nkbs * 32 * sizeof(float)
-                             : (pl.fused ? 0 : (size_t)g->nk * pl.n_mt * pl.nkbs * 2 * row_b * pl.NT);
+  const size_t sp_bytes = pl.fused ? 0 : (size_t)g->nk * pl.n_mt * pl.nkbs * 2 * row_b * pl.NT;
   const size_t wp_bytes = (size_t)g->nk * pl.mpad * sizeof(float);
   const size_t sc_bytes = (te || (pl.fused && mode == GCAMB_F16X3)) ? wp_bytes : 0;
   const size_t part_bytes = std::max<size_t>(1, pl.nitems) * (te ? 3 : 1) * pl.NT * 128 * sizeof(float);
@@ -1305,7 +1307,7 @@ int launch_tc_kernel(const gcamb_grid *g, const TcPlan &pl, const CUtensorMap &t
   if (e != cudaSuccess) return cuda_fail(e, "los_cl: counter reset");
   ProfScope prof(GCAMB_K_TC, st);
   los_cl_tc_kernel<NT, MODE, FUSED, TE>
-      <<<(unsigned)pl.nctas, TcRoles<FUSED>::kThreadsT, Cfg::kSmemBytes, st>>>(tm, tm2, prm);
+      <<<(unsigned)pl.nctas, TcRoles<FUSED, TE>::kThreadsT, Cfg::kSmemBytes, st>>>(tm, tm2, prm);
   return GCAMB_OK;
 }
 
@@ -1353,7 +1355,7 @@ int launch_tc(const gcamb_grid *g, const TcPlan &pl, const float *S, const doubl
   }
   if (pl.nitems > 0) {
     int *ctr = reinterpret_cast<int *>(ws + pl.off_ctr);
-    TcParams prm{static_cast<const char *>(t.d_data), t.d_off, t.d_nkb, sp, wp, sc, nullptr, nullptr, 0.f, -1,
+    TcParams prm{static_cast<const char *>(t.d_data), t.d_off, t.d_nkb, sp, wp, sc, nullptr, -1,
                  pl.items(B), ctr, pl.nitems, part, use_err_word ? err_word : device_error_flag(), g->nlt, pl.n_mt,
                  pl.nkbs, pl.mpad};
     if (!prm.err && !use_err_word) return fail(GCAMB_ECUDA, "los_cl: error flag allocation");
@@ -1405,6 +1407,23 @@ int pick_h_te(int M) {
   return h;
 }
 
+// The grid's 1/x^2 per node for the converters of a TE plan (once per plan).
+int build_ix2(const gcamb_grid *g, TcPlan &pl) {
+  double xlo = 0.0;
+  if (emode_x_lo(g, &xlo)) return fail(GCAMB_EINVAL, "los_cl_te: eps_cut too large for the l = 2 limit");
+  const int npad = pl.nkbs * 32;
+  const size_t n = (size_t)g->nk * npad;
+  cudaError_t e = cudaMalloc(&pl.d_ix2, n * sizeof(float));
+  if (e != cudaSuccess) {
+    pl.d_ix2 = nullptr;
+    return cuda_fail(e, "los_cl_te: 1/x^2 table allocation");
+  }
+  te_ix2_kernel<<<(unsigned)((n + 255) / 256), 256>>>(g->d_k, g->d_tau, g->tau0, xlo, g->nk, g->ntau, npad, pl.d_ix2);
+  e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "los_cl_te: 1/x^2 table");
+  return GCAMB_OK;
+}
+
 TcPlan *get_plan_te(const gcamb_grid *g, int M, int *rc) {
   std::lock_guard<std::mutex> lk(g_plan_mu);
   const int h = pick_h_te(M);
@@ -1412,7 +1431,8 @@ TcPlan *get_plan_te(const gcamb_grid *g, int M, int *rc) {
     if (e.first == g && e.second->te && e.second->M == M && e.second->NT == h) return e.second;
   TcPlan *pl = new TcPlan();
   plan_build(g, M, GCAMB_BF16X3, h, nullptr, nullptr, *pl, true);
-  if ((*rc = upload_blob(*pl)) != GCAMB_OK) {
+  if ((*rc = upload_blob(*pl)) == GCAMB_OK) *rc = build_ix2(g, *pl);
+  if (*rc != GCAMB_OK) {
     pl->release();
     delete pl;
     return nullptr;
@@ -1421,14 +1441,15 @@ TcPlan *get_plan_te(const gcamb_grid *g, int M, int *rc) {
   return pl;
 }
 
-// Temperature + E-mode batch: tau0 - tau in FP32, weights and l = 2 tails,
-// the tensor-core kernel over NT = 2 H operand rows per tile, the TE reduce.
+// Temperature + E-mode batch: weights and l = 2 tails,
+// the tensor-core kernel over NT = 2 H operand rows per tile, the TE reduce
+// (1/x^2 per node was built with the plan).
 template <int NT>
 int launch_tc_te(const gcamb_grid *g, const TcPlan &pl, const float *ST, const float *SP, const double *Pk,
                  double *ClTT, double *ClEE, double *ClTE, char *ws, double xlo, cudaStream_t st) {
   constexpr int H = NT / 2;
   const Table &t = g->tab[GCAMB_BF16X3];
-  float *dt = reinterpret_cast<float *>(ws + pl.off_sp);
+  const float *ix2 = pl.d_ix2;
   float *wp = reinterpret_cast<float *>(ws + pl.off_wp);
   float *tail = reinterpret_cast<float *>(ws + pl.off_sc);
   float *part = reinterpret_cast<float *>(ws + pl.off_part);
@@ -1438,19 +1459,17 @@ int launch_tc_te(const gcamb_grid *g, const TcPlan &pl, const float *ST, const f
   memset(&tm2, 0, sizeof tm2);
   if (int rc = encode_sources(&tm1, ST, pl.M, g->nk, g->ntau, H)) return rc;
   if (int rc = encode_sources(&tm2, SP, pl.M, g->nk, g->ntau, H)) return rc;
-  const float xlof = (float)xlo;
   {
     ProfScope prof(GCAMB_K_SPLIT, st);
-    const int npad = pl.nkbs * 32;
-    te_dtau_kernel<<<(npad + 255) / 256, 256, 0, st>>>(g->d_tau, g->tau0, g->ntau, npad, dt);
     const size_t rows = (size_t)g->nk * pl.mpad;
-    te_weights_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(Pk, g->d_wk, g->d_k, g->d_wtau, dt, xlof, SP,
-                                                                      pl.M, g->nk, g->ntau, pl.mpad, wp, tail);
+    te_weights_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(Pk, g->d_wk, g->d_k, g->d_tau, g->tau0, xlo,
+                                                                      g->d_wtau, SP, pl.M, g->nk, g->ntau, pl.mpad, wp,
+                                                                      tail);
   }
   if (pl.nitems > 0) {
     int *ctr = reinterpret_cast<int *>(ws + pl.off_ctr);
     const int r2 = (g->lmin <= 2 && g->lmax >= 2) ? 2 - g->lmin : -1;
-    TcParams prm{static_cast<const char *>(t.d_data), t.d_off, t.d_nkb, nullptr, wp, tail, dt, g->d_k, xlof, r2,
+    TcParams prm{static_cast<const char *>(t.d_data), t.d_off, t.d_nkb, nullptr, wp, tail, ix2, r2,
                  pl.items(B), ctr, pl.nitems, part, device_error_flag(), g->nlt, pl.n_mt, pl.nkbs, pl.mpad};
     if (!prm.err) return fail(GCAMB_ECUDA, "los_cl_te: error flag allocation");
     if (int rc = launch_tc_kernel<NT, kBF16, true, true>(g, pl, tm1, tm2, prm, st)) return rc;
