@@ -394,7 +394,7 @@ def run_te(args):
                          "kernel": "los_cl_tc_kernel (TE)", "kernel_ms": tc_avg_s * 1e3, "algorithmic_bytes": alg_bytes,
                          "tensor_view": {"achieved_tflops": alg_flops / tc_avg_s / 1e12,
                                          "frac": alg_flops / tc_avg_s / 1e12 / peaks.get("bf16_tflops", 1900.0)}},
-            "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": 4 * steps}
+            "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": 3 * steps}
     print(json.dumps(line), flush=True)
 
 
