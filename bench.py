@@ -377,7 +377,10 @@ def run_te(args):
         tt, ee, te = (x[:1].cpu().numpy() for x in out)
         nz = EE > 0
         err = {"TT": float(np.max(np.abs(tt / TT - 1))), "EE": float(np.max(np.abs(ee[nz] / EE[nz] - 1))),
-               "TE_on_sqrt_TT_EE": float(np.max(np.abs(te - TE)[nz] / np.sqrt(TT * EE)[nz]))}
+               "TE_on_sqrt_TT_EE": float(np.max(np.abs(te - TE)[nz] / np.sqrt(TT * EE)[nz])),
+               "max_dcl_over_sigma_cv": {"TT": float(oracle.cosmic_variance_ratio(tt, TT).max()),
+                                         "EE": float(oracle.cosmic_variance_ratio(ee, EE).max()),
+                                         "TE": float(oracle.cosmic_variance_ratio_te(te, TT, EE, TE).max())}}
     line = {"metric": "TT+EE+TE spectrum sets/sec at l_max=2500, batched split precision (bf16x3)",
             "value": M * steps / (ms * 1e-3), "unit": "models/s", "n_gpus": 1, "steps": steps,
             "warmup": args.warmup, "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",

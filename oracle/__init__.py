@@ -1,4 +1,4 @@
-"""FP64 CPU oracle for the line-of-sight projection (arXiv 2509.25110, Eqs. 1-2).
+"""FP64 CPU oracle for the line-of-sight projection (arXiv 2509.25110, Eqs. 1-3).
 
 TEST INFRASTRUCTURE ONLY: imported by the tests, by the package smoke check
 and by the benchmark's CPU-baseline leg, never by the product path.  It shares
@@ -13,6 +13,10 @@ Pins (tests/test_oracle_*.py): closed forms of j_0, j_1, j_2; the addition
 sum rule; 50-digit mpmath values; the trapezoid's exactness on linear
 integrands and its error bound; a delta-function source; linearity; the
 Sachs-Wolfe plateau C_l = 2 pi A / (l (l+1)); brute force on tiny grids.
+E-mode and cross spectra: eps_2 in closed form, mpmath eps_l, its x -> 0
+limit, a delta source, the scale-invariant C^EE and C^TE closed forms,
+Cauchy-Schwarz; the cross-spectrum cosmic variance against its auto form
+and a Monte Carlo of the full-sky estimator.
 """
 from __future__ import annotations
 
@@ -197,8 +201,20 @@ def cl_cross(k, DX, DY, Pk, wk=None) -> np.ndarray:
 
 
 def cosmic_variance_ratio(cl_test, cl_ref, lmin=2) -> np.ndarray:
-    """|Delta C_l| / sigma_CV with sigma_CV = sqrt(2/(2l+1)) |C_l| (Sec. 4.6)."""
+    """|Delta C_l| / sigma_CV with sigma_CV = sqrt(2/(2l+1)) |C_l| (Sec. 4.6),
+    the auto spectra TT, EE."""
     cl_ref = np.asarray(cl_ref, dtype=np.float64)
     l = lmin + np.arange(cl_ref.shape[-1])
     sig = np.sqrt(2.0 / (2.0 * l + 1.0)) * np.abs(cl_ref)
     return np.abs(np.asarray(cl_test, dtype=np.float64) - cl_ref) / sig
+
+
+def cosmic_variance_ratio_te(te_test, tt_ref, ee_ref, te_ref, lmin=2) -> np.ndarray:
+    """|Delta C^TE_l| / sigma_CV^TE with the cross-spectrum cosmic variance of
+    Sec. 4.6, sigma_CV^TE = sqrt(((C^TE)^2 + C^TT C^EE) / (2l+1))."""
+    tt = np.asarray(tt_ref, dtype=np.float64)
+    ee = np.asarray(ee_ref, dtype=np.float64)
+    te = np.asarray(te_ref, dtype=np.float64)
+    l = lmin + np.arange(te.shape[-1])
+    sig = np.sqrt((te * te + tt * ee) / (2.0 * l + 1.0))
+    return np.abs(np.asarray(te_test, dtype=np.float64) - te) / sig

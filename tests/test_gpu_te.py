@@ -164,7 +164,12 @@ def test_te_full_grid_sampled(orc):
     ms = [0, 131, 255]
     sub = synth.Workload("sub", wl.k, wl.tau, wl.tau0, wl.lmin, wl.lmax, len(ms))
     ref = oracle_te(orc, sub, ST[ms].cpu().numpy(), SP[ms].cpu().numpy(), P[ms].cpu().numpy())
-    check((tt[ms].cpu().numpy(), ee[ms].cpu().numpy(), te[ms].cpu().numpy()), ref, 1e-5)
+    got = (tt[ms].cpu().numpy(), ee[ms].cpu().numpy(), te[ms].cpu().numpy())
+    check(got, ref, 1e-5)
+    # the paper's validation: |Delta C_l| / sigma_CV (Sec. 4.6), here far below 1
+    assert orc.cosmic_variance_ratio(got[0], ref[0]).max() < 1e-3
+    assert orc.cosmic_variance_ratio(got[1], ref[1]).max() < 1e-3
+    assert orc.cosmic_variance_ratio_te(got[2], ref[0], ref[1], ref[2]).max() < 1e-3
 
 
 def test_te_errors():

@@ -121,3 +121,32 @@ def test_cross_spectrum_properties(orc):
     assert np.allclose(orc.cl_cross(k, dE, dT, P), te, rtol=1e-13, atol=0)  # symmetric (to rounding)
     # linearity in S_P (on the scale of the sums: random terms cancel)
     assert np.abs(orc.los_e(k, tau, tau0, 2, 120, 2.5 * SP) - 2.5 * dE).max() <= 1e-13 * np.abs(2.5 * dE).max()
+
+
+def test_cosmic_variance_te_reduces_to_the_auto_form(orc):
+    """Fully correlated fields (TE^2 = TT EE, here TT = EE = TE) give the auto
+    spectrum's sigma_CV = sqrt(2/(2l+1)) |C|."""
+    rng = np.random.default_rng(5)
+    c = rng.uniform(1e-12, 1e-9, 50)
+    d = 1e-3 * c
+    r_te = orc.cosmic_variance_ratio_te(c + d, c, c, c)
+    r_auto = orc.cosmic_variance_ratio(c + d, c)
+    assert np.allclose(r_te, r_auto, rtol=1e-12, atol=0)
+
+
+def test_cosmic_variance_te_monte_carlo(orc):
+    """sigma_CV^TE is the standard deviation of the full-sky estimator
+    (1/(2l+1)) sum_m a^T_lm a^E_lm of jointly Gaussian (T, E) with covariance
+    [[TT, TE], [TE, EE]]: drawn here as real pairs, 2l+1 per estimate."""
+    rng = np.random.default_rng(6)
+    tt, ee, te = 2.0, 0.5, 0.6
+    L = np.linalg.cholesky(np.array([[tt, te], [te, ee]]))
+    for l in (2, 7):
+        n = 2 * l + 1
+        z = rng.normal(size=(200000, n, 2)) @ L.T
+        est = (z[..., 0] * z[..., 1]).mean(axis=1)
+        sig_mc = est.std()
+        # a unit deviation of C^TE measured in sigma_CV^TE units
+        ratio = orc.cosmic_variance_ratio_te(np.array([te + 1.0]), np.array([tt]), np.array([ee]), np.array([te]),
+                                             lmin=l)[0]
+        assert 1.0 / ratio == pytest.approx(sig_mc, rel=0.01)
