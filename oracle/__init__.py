@@ -61,6 +61,10 @@ def _load():
     lib.orc_los_e.restype = ctypes.c_int
     lib.orc_cl_cross.argtypes = [ctypes.c_int, _dp, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp]
     lib.orc_cl_cross.restype = ctypes.c_int
+    lib.orc_tensor_kernels_many.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _dp, _dp, _dp]
+    lib.orc_los_tensor.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _dp, ctypes.c_double, ctypes.c_int,
+                                   ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp, ctypes.c_int]
+    lib.orc_los_tensor.restype = ctypes.c_int
     _LIB = lib
     return lib
 
@@ -181,6 +185,35 @@ def los_e(k, tau, tau0, lmin, lmax, SP, wtau=None, nthreads=0) -> np.ndarray:
     if rc != 0:
         raise ValueError("oracle rejected the arguments")
     return d[0] if single else d
+
+
+def tensor_kernels(x, lmax):
+    """Tensor-mode kernels (t_l, e_l, b_l)(x) for l = 0..lmax, each of shape
+    [x.size][lmax + 1] (zero below l = 2; limits at x = 0)."""
+    xa = _f64(x).ravel()
+    t, e, b = (np.empty((xa.size, lmax + 1)) for _ in range(3))
+    _load().orc_tensor_kernels_many(xa.size, _ptr(xa), int(lmax), _ptr(t), _ptr(e), _ptr(b))
+    return t, e, b
+
+
+def los_tensor(k, tau, tau0, lmin, lmax, ST, SP, wtau=None, nthreads=0):
+    """Dense FP64 tensor transfer functions (DT, DE, DB), each [M][nk][nl],
+    from tensor sources ST, SP of shape [M][nk][ntau]."""
+    k = _f64(k)
+    tau = _f64(tau)
+    ST, SP = _f64(ST), _f64(SP)
+    single = ST.ndim == 2
+    if single:
+        ST, SP = ST[None], SP[None]
+    M, nk, ntau = ST.shape
+    assert SP.shape == ST.shape and nk == k.size and ntau == tau.size
+    out = [np.empty((M, nk, lmax - lmin + 1)) for _ in range(3)]
+    rc = _load().orc_los_tensor(nk, _ptr(k), ntau, _ptr(tau), float(tau0), int(lmin), int(lmax), M, _ptr(ST),
+                                _ptr(SP), _ptr(_f64(wtau)) if wtau is not None else None, _ptr(out[0]),
+                                _ptr(out[1]), _ptr(out[2]), int(nthreads))
+    if rc != 0:
+        raise ValueError("oracle rejected the arguments")
+    return tuple(o[0] for o in out) if single else tuple(out)
 
 
 def cl_cross(k, DX, DY, Pk, wk=None) -> np.ndarray:

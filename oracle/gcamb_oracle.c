@@ -22,6 +22,20 @@
  *       eps_l(x) = sqrt((l+2)! / (l-2)!) j_l(x) / x^2     (l >= 2; 0 below),
  * with its limit at x = 0: sqrt(24) / 15 for l = 2 and 0 above.
  *
+ * Tensor modes (the second projection the paper runs, Sec. 3.1 and 3.3; it
+ * says only that equations like Eqs. (2)-(3) hold for tensors and B modes,
+ * Sec. 2.1).  This oracle takes the flat-space line-of-sight kernels of
+ * tensor perturbations:
+ *       T: t_l(x) = sqrt((l+2)!/(l-2)!) j_l(x) / x^2            (= eps_l)
+ *       E: e_l(x) = -j_l + j_l'' + 2 j_l / x^2 + 4 j_l' / x
+ *       B: b_l(x) = 2 j_l' + 4 j_l / x
+ * (l >= 2; 0 below), evaluated through the Bessel equation and
+ * j_l' = j_{l-1} - (l+1) j_l / x as
+ *       e_l = (l (l-1) / x^2 - 2) j_l + 2 j_{l-1} / x,
+ *       b_l = 2 j_{l-1} - 2 (l-1) j_l / x,
+ * with their limits at x = 0: e_2 = 4/5, all others 0.  Each projection is
+ * the dense sum of Eq. (2) with the tensor sources S_T^t, S_P^t.
+ *
  * The paper fixes neither the Bessel kernel's evaluation nor the quadrature
  * (it names phi_l only as "related to spherical Bessel functions", Sec. 2.1,
  * and evaluates it inside the line-of-sight loop, Sec. 3.2 / Algorithm 1).
@@ -324,6 +338,84 @@ int orc_los_e(int nk, const double *k, int ntau, const double *tau, double tau0,
             }
         }
         free(el);
+    }
+    free(wtau);
+    return 0;
+}
+
+/* Tensor kernels t_l, e_l, b_l at one x for l = 0..lmax (zero below l = 2). */
+void orc_tensor_kernels(int lmax, double x, double *t, double *e, double *b)
+{
+    double *jl = (double *)malloc(sizeof(double) * (size_t)(lmax + 1));
+    orc_sph_bessel(lmax, x, jl);
+    for (int l = 0; l <= lmax; ++l) {
+        t[l] = e[l] = b[l] = 0.0;
+        if (l < 2) continue;
+        double c = sqrt((double)(l + 2) * (double)(l + 1) * (double)l * (double)(l - 1));
+        if (x == 0.0) {
+            if (l == 2) {
+                t[l] = c / 15.0;
+                e[l] = 0.8;
+            }
+            continue;
+        }
+        t[l] = c * jl[l] / (x * x);
+        e[l] = ((double)l * (double)(l - 1) / (x * x) - 2.0) * jl[l] + 2.0 * jl[l - 1] / x;
+        b[l] = 2.0 * jl[l - 1] - 2.0 * (double)(l - 1) * jl[l] / x;
+    }
+    free(jl);
+}
+
+void orc_tensor_kernels_many(int n, const double *x, int lmax, double *t, double *e, double *b)
+{
+    for (int i = 0; i < n; ++i) {
+        size_t o = (size_t)i * (lmax + 1);
+        orc_tensor_kernels(lmax, x[i], t + o, e + o, b + o);
+    }
+}
+
+/* Tensor transfer functions DT, DE, DB [M][q][l - lmin] = sum_i w_i S[m][q][i]
+ * kernel_l(k_q (tau0 - tau_i)), S = ST for t_l and SP for e_l, b_l; dense
+ * over the tau nodes.  wtau_in NULL = trapezoid.  Returns 0 or -1. */
+int orc_los_tensor(int nk, const double *k, int ntau, const double *tau, double tau0,
+                   int lmin, int lmax, int M, const double *ST, const double *SP,
+                   const double *wtau_in, double *DT, double *DE, double *DB, int nthreads)
+{
+    if (nk < 0 || ntau < 0 || lmin < 0 || lmax < lmin || M < 0 || !DT || !DE || !DB) return -1;
+    const int nl = lmax - lmin + 1;
+    double *wtau = (double *)malloc(sizeof(double) * (size_t)(ntau > 0 ? ntau : 1));
+    if (wtau_in) memcpy(wtau, wtau_in, sizeof(double) * (size_t)ntau);
+    else orc_trapz_weights(ntau, tau, wtau);
+    int nt = 1;
+#ifdef _OPENMP
+    nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#endif
+    #pragma omp parallel num_threads(nt)
+    {
+        double *kt = (double *)malloc(sizeof(double) * 3 * (size_t)(lmax + 1));
+        double *ke = kt + (lmax + 1), *kb = ke + (lmax + 1);
+        #pragma omp for schedule(static)
+        for (int q = 0; q < nk; ++q) {
+            for (int m = 0; m < M; ++m) {
+                size_t o = ((size_t)m * nk + q) * nl;
+                memset(DT + o, 0, sizeof(double) * (size_t)nl);
+                memset(DE + o, 0, sizeof(double) * (size_t)nl);
+                memset(DB + o, 0, sizeof(double) * (size_t)nl);
+            }
+            for (int i = 0; i < ntau; ++i) {
+                orc_tensor_kernels(lmax, k[q] * (tau0 - tau[i]), kt, ke, kb);
+                for (int m = 0; m < M; ++m) {
+                    size_t s = ((size_t)m * nk + q) * ntau + i, o = ((size_t)m * nk + q) * nl;
+                    double wt = wtau[i] * ST[s], wp = wtau[i] * SP[s];
+                    for (int l = lmin; l <= lmax; ++l) {
+                        DT[o + l - lmin] += wt * kt[l];
+                        DE[o + l - lmin] += wp * ke[l];
+                        DB[o + l - lmin] += wp * kb[l];
+                    }
+                }
+            }
+        }
+        free(kt);
     }
     free(wtau);
     return 0;
