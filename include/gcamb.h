@@ -165,6 +165,29 @@ int gcamb_los_transfer(const gcamb_grid *g, const void *S, int M, int mode, void
 int gcamb_los_transfer_e(const gcamb_grid *g, const void *SP, int M, int mode, void *DeltaE, void *stream);
 
 /*
+ * Tensor modes on the CUDA cores: the projection the paper runs a second time
+ * for tensor perturbations (Sec. 3.1, 3.3; Sec. 2.1 says equations like
+ * Eqs. (2)-(3) hold for them), with the flat-space line-of-sight kernels
+ *   T: t_l(x) = sqrt((l+2)!/(l-2)!) j_l(x) / x^2        (source ST)
+ *   E: e_l(x) = -j_l + j_l'' + 2 j_l/x^2 + 4 j_l'/x
+ *             = (l (l-1)/x^2 - 2) j_l + 2 j_(l-1)/x     (source SP)
+ *   B: b_l(x) = 2 j_l' + 4 j_l/x = 2 j_(l-1) - 2 (l-1) j_l/x   (source SP)
+ * (l >= 2; 0 below).  The shared j_l table gives the sums D_p[l] =
+ * sum_i w_i j_l S_P x^-p (p = 0, 1, 2) and the kernels combine rows l and
+ * l-1 (for l = lmin >= 2, row l-1 from j_(l-1) = (2l+1)/x j_l - j_(l+1)).
+ * Nodes below the small cut x_lo of gcamb_los_transfer_e take the power
+ * series of the kernels for l = 2..5 (e_2 -> 4/5, t_2 -> sqrt(24)/15).
+ *   ST, SP                [M][nk][ntau] device, FP64 (PLAIN64) or FP32 (PLAIN32)
+ *   DeltaT, DeltaE, DeltaB [M][nk][nl] device, same dtype; DeltaT is also used
+ *                         as scratch (the three must not overlap)
+ * C_l (TT, EE, BB, TE of the tensor spectrum) follow from gcamb_cl and
+ * gcamb_cl_cross with the tensor P(k).  Errors: as gcamb_los_transfer_e, and
+ * GCAMB_EINVAL for lmin >= 2 with lmax == lmin.
+ */
+int gcamb_los_transfer_tensor(const gcamb_grid *g, const void *ST, const void *SP, int M, int mode, void *DeltaT,
+                              void *DeltaE, void *DeltaB, void *stream);
+
+/*
  * Cross spectrum, Eq. (1) with X, Y in {T, E}:
  *   C^XY[m][l] = 4 pi sum_k w_k P[m][k] DX[m][k][l] DY[m][k][l]
  * DX, DY [M][nk][nl] device, both of d_dtype (GCAMB_F64 or GCAMB_F32);

@@ -369,6 +369,20 @@ int gcamb_los_transfer_e(const gcamb_grid *g, const void *SP, int M, int mode, v
   return launch_los_plain(g, SP, M, mode, DeltaE, (cudaStream_t)stream, true);
 }
 
+int gcamb_los_transfer_tensor(const gcamb_grid *g, const void *ST, const void *SP, int M, int mode, void *DeltaT,
+                              void *DeltaE, void *DeltaB, void *stream) {
+  if (!g) return fail(GCAMB_EINVAL, "los_transfer_tensor: NULL grid");
+  if (mode != GCAMB_PLAIN64 && mode != GCAMB_PLAIN32)
+    return fail(GCAMB_EINVAL, "los_transfer_tensor: mode must be GCAMB_PLAIN64 or GCAMB_PLAIN32");
+  if (M < 0) return fail(GCAMB_EINVAL, "los_transfer_tensor: M < 0");
+  if (M == 0) return GCAMB_OK;
+  if (!ST || !SP || !DeltaT || !DeltaE || !DeltaB) return fail(GCAMB_EINVAL, "los_transfer_tensor: NULL pointer");
+  if (DeltaT == DeltaE || DeltaT == DeltaB || DeltaE == DeltaB)
+    return fail(GCAMB_EINVAL, "los_transfer_tensor: the three outputs must be distinct");
+  if (!g->tab[mode].built) return fail(GCAMB_ESTATE, "los_transfer_tensor: build the table for this mode first");
+  return launch_los_tensor(g, ST, SP, M, mode, DeltaT, DeltaE, DeltaB, (cudaStream_t)stream);
+}
+
 int gcamb_cl_cross(const gcamb_grid *g, const void *DX, const void *DY, int d_dtype, const double *Pk, int M,
                    double *Cl, void *stream) {
   if (!g) return fail(GCAMB_EINVAL, "cl_cross: NULL grid");

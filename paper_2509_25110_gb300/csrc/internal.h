@@ -90,6 +90,8 @@ int launch_sph_bessel(const double *x, int n, int lmax, double *out, cudaStream_
 // Plain FP64/FP32 path (plain.cu).
 int launch_los_plain(const gcamb_grid *g, const void *S, int M, int mode, void *Delta, cudaStream_t st,
                      bool emode = false);
+int launch_los_tensor(const gcamb_grid *g, const void *ST, const void *SP, int M, int mode, void *DT, void *DE,
+                      void *DB, cudaStream_t st);
 // E-mode small-x cut x_lo of the grid (plain.cu); -1 if it would exceed 0.2.
 int emode_x_lo(const gcamb_grid *g, double *x_lo);
 int launch_cl_cross(const gcamb_grid *g, const void *DX, const void *DY, int d_dtype, const double *Pk, int M,

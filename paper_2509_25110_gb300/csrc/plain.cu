@@ -21,7 +21,12 @@ namespace gcamb {
 //   j_2(x)/x^2 = 1/15 - x^2/210 + x^4/7560 - x^6/498960 + O(x^8)
 // (from j_l(x) = x^l sum_n (-x^2/2)^n / (n! (2l+2n+1)!!)); for l >= 3 their
 // eps_l is below c_l x_lo^(l-2)/(2l+1)!!, and x_lo <= 0.2.
-template <typename T, int MC, bool E>
+//
+// XP: the staged source is S x^-XP for x >= x_lo and 0 below (XP >= 0), or
+// S itself (XP < 0, temperature); E: the E-mode epilogue above (XP = 2).
+// XP = 0, 1, 2 without E give the raw sums D_XP[l] = sum_i w_i j_l S x^-XP of
+// the tensor-mode kernels.
+template <typename T, int MC, int XP, bool E>
 __global__ void __launch_bounds__(256) los_plain_kernel(const T *__restrict__ table, const int32_t *__restrict__ nkb,
                                                         const int64_t *__restrict__ off, int nk, int nlt, int lmin,
                                                         int lmax, int ntau, const T *__restrict__ S, int M,
@@ -42,10 +47,11 @@ __global__ void __launch_bounds__(256) los_plain_kernel(const T *__restrict__ ta
   for (int idx = threadIdx.x; idx < MC * ext; idx += blockDim.x) {
     const int m = idx / ext, t = idx - m * ext;
     T v = (m < mc && t < ntau) ? S[((size_t)(m0 + m) * nk + q) * ntau + t] : T(0);
-    if constexpr (E) {
+    if constexpr (XP >= 0) {
       if (m < mc && t < ntau) {
         const double x = kk[q] * (tau0 - tau[t]);
-        v = x >= x_lo ? (T)((double)v / (x * x)) : T(0);
+        const double f = XP == 2 ? 1.0 / (x * x) : (XP == 1 ? 1.0 / x : 1.0);
+        v = x >= x_lo ? (T)((double)v * f) : T(0);
       }
     }
     s[idx] = v;
@@ -120,49 +126,173 @@ int emode_x_lo(const gcamb_grid *g, double *x_lo) {
   return x <= 0.2 ? 0 : -1;
 }
 
-template <typename T, int MC, bool E>
+template <typename T, int MC, int XP, bool E>
 static int launch_plain_t(const gcamb_grid *g, const Table &t, const T *S, int M, T *Delta, cudaStream_t st) {
   int max_ext = 0;
   for (int v : t.nkb) max_ext = max_ext > v ? max_ext : v;
   max_ext *= 64;
   const size_t smem = (size_t)MC * max_ext * sizeof(T);
   if (smem > 200 * 1024) return fail(GCAMB_EINVAL, "los_transfer: tau grid too long for the plain kernel");
-  cudaError_t e = cudaFuncSetAttribute(los_plain_kernel<T, MC, E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)(smem > 0 ? smem : 16));
+  cudaError_t e = cudaFuncSetAttribute(los_plain_kernel<T, MC, XP, E>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(smem > 0 ? smem : 16));
   if (e != cudaSuccess) return cuda_fail(e, "los_transfer: smem attribute");
   dim3 grid(g->nlt, g->nk, (M + MC - 1) / MC);
   if (grid.z > 65535) return fail(GCAMB_EINVAL, "los_transfer: too many sources for one launch");
   ProfScope prof(GCAMB_K_LOS_PLAIN, st);
   double x_lo = 1e-12;
-  if (E && emode_x_lo(g, &x_lo)) return fail(GCAMB_EINVAL, "los_transfer_e: eps_cut too large for the l = 2 limit");
-  los_plain_kernel<T, MC, E><<<grid, 256, smem, st>>>(static_cast<const T *>(t.d_data), t.d_nkb, t.d_off, g->nk,
-                                                      g->nlt, g->lmin, g->lmax, g->ntau, S, M, Delta, g->d_k,
-                                                      g->d_tau, g->tau0, g->d_wtau, x_lo);
+  if (XP >= 0 && emode_x_lo(g, &x_lo))
+    return fail(GCAMB_EINVAL, "los_transfer: eps_cut too large for the l = 2 limit of the polarisation kernels");
+  los_plain_kernel<T, MC, XP, E><<<grid, 256, smem, st>>>(static_cast<const T *>(t.d_data), t.d_nkb, t.d_off,
+                                                          g->nk, g->nlt, g->lmin, g->lmax, g->ntau, S, M, Delta,
+                                                          g->d_k, g->d_tau, g->tau0, g->d_wtau, x_lo);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "los_transfer: launch");
   return GCAMB_OK;
 }
 
-template <bool E>
+template <int XP, bool E>
 static int launch_los_plain_k(const gcamb_grid *g, const void *S, int M, int mode, void *Delta, cudaStream_t st) {
   const Table &t = g->tab[mode];
   if (mode == GCAMB_PLAIN64) {
     auto s = static_cast<const double *>(S);
     auto d = static_cast<double *>(Delta);
-    if (M >= 4) return launch_plain_t<double, 4, E>(g, t, s, M, d, st);
-    if (M >= 2) return launch_plain_t<double, 2, E>(g, t, s, M, d, st);
-    return launch_plain_t<double, 1, E>(g, t, s, M, d, st);
+    if (M >= 4) return launch_plain_t<double, 4, XP, E>(g, t, s, M, d, st);
+    if (M >= 2) return launch_plain_t<double, 2, XP, E>(g, t, s, M, d, st);
+    return launch_plain_t<double, 1, XP, E>(g, t, s, M, d, st);
   }
   auto s = static_cast<const float *>(S);
   auto d = static_cast<float *>(Delta);
-  if (M >= 8) return launch_plain_t<float, 8, E>(g, t, s, M, d, st);
-  if (M >= 4) return launch_plain_t<float, 4, E>(g, t, s, M, d, st);
-  if (M >= 2) return launch_plain_t<float, 2, E>(g, t, s, M, d, st);
-  return launch_plain_t<float, 1, E>(g, t, s, M, d, st);
+  if (M >= 8) return launch_plain_t<float, 8, XP, E>(g, t, s, M, d, st);
+  if (M >= 4) return launch_plain_t<float, 4, XP, E>(g, t, s, M, d, st);
+  if (M >= 2) return launch_plain_t<float, 2, XP, E>(g, t, s, M, d, st);
+  return launch_plain_t<float, 1, XP, E>(g, t, s, M, d, st);
 }
 
 int launch_los_plain(const gcamb_grid *g, const void *S, int M, int mode, void *Delta, cudaStream_t st, bool emode) {
-  return emode ? launch_los_plain_k<true>(g, S, M, mode, Delta, st) : launch_los_plain_k<false>(g, S, M, mode, Delta, st);
+  return emode ? launch_los_plain_k<2, true>(g, S, M, mode, Delta, st)
+               : launch_los_plain_k<-1, false>(g, S, M, mode, Delta, st);
+}
+
+// Tensor modes: power series of the tensor kernels at small x for the nodes
+// below the cut, from j_l(x) = x^l s_l(x^2),
+// s_l(y) = sum_n (-y/2)^n / (n! (2l+2n+1)!!) (seven terms: exact to rounding
+// for x <= 0.2):
+//   e_l = x^(l-2) [l (l-1) s_l - 2 x^2 s_l + 2 s_(l-1)],
+//   b_l = 2 x^(l-1) [s_(l-1) - (l-1) s_l].
+__device__ __forceinline__ double sph_series(int l, double y) {
+  double df = 1.0;  // (2l+1)!!
+  for (int j = 3; j <= 2 * l + 1; j += 2) df *= j;
+  double term = 1.0 / df, sum = term;
+  for (int n = 0; n < 6; ++n) {
+    term *= (-0.5 * y) / ((n + 1) * (2.0 * l + 2 * n + 3));
+    sum += term;
+  }
+  return sum;
+}
+
+// Combines the raw tensor sums, in place: D0 -> Delta_E, D1 -> Delta_B
+// (D2 read only), one CTA per (source, k) row walking l in chunks.
+//   Delta_E[l] = l (l-1) D2[l] - 2 D0[l] + 2 D1[l-1] + tail_e(l)
+//   Delta_B[l] = 2 D0[l-1] - 2 (l-1) D1[l] + tail_b(l)
+// Row l-1 of the first multipole (lmin >= 2) comes from the recurrence
+// j_(l-1) = (2l+1)/x j_l - j_(l+1):  D1[l-1] = (2l+1) D2[l] - D1[l+1],
+// D0[l-1] = (2l+1) D1[l] - D0[l+1] (all three sums leave out the same nodes).
+// The tails add, for l = 2..5, the series terms of the nodes below the cut.
+template <typename T>
+__global__ void __launch_bounds__(256) tensor_combine_kernel(T *__restrict__ DE, T *__restrict__ DB,
+                                                             const T *__restrict__ D2, const T *__restrict__ SP,
+                                                             const double *__restrict__ kk,
+                                                             const double *__restrict__ tau, double tau0,
+                                                             const double *__restrict__ wtau, double x_lo, int nk,
+                                                             int ntau, int lmin, int lmax) {
+  __shared__ double carry[2];
+  const int nl = lmax - lmin + 1;
+  const size_t row = blockIdx.x;  // m * nk + q
+  const int q = (int)(row % nk);
+  T *e = DE + row * nl;
+  T *b = DB + row * nl;
+  const T *d2 = D2 + row * nl;
+  const T *src = SP + row * ntau;
+  for (int base = 0; base < nl; base += blockDim.x) {
+    const int idx = base + threadIdx.x;
+    const int l = lmin + idx;
+    double d0 = 0, d1 = 0, dd2 = 0, p0 = 0, p1 = 0;
+    if (idx < nl) {
+      d0 = (double)e[idx];
+      d1 = (double)b[idx];
+      dd2 = (double)d2[idx];
+      if (idx == 0) {
+        if (l >= 2 && nl > 1) {
+          p1 = (2.0 * l + 1.0) * dd2 - (double)b[1];
+          p0 = (2.0 * l + 1.0) * d1 - (double)e[1];
+        }
+      } else if (threadIdx.x == 0) {
+        p0 = carry[0];
+        p1 = carry[1];
+      } else {
+        p0 = (double)e[idx - 1];
+        p1 = (double)b[idx - 1];
+      }
+    }
+    __syncthreads();  // every read of this chunk (and of the carry) precedes its writes
+    if (threadIdx.x == blockDim.x - 1) {
+      carry[0] = d0;
+      carry[1] = d1;
+    }
+    if (idx < nl) {
+      double ve = 0.0, vb = 0.0;
+      if (l >= 2) {
+        ve = (double)l * (l - 1) * dd2 - 2.0 * d0 + 2.0 * p1;
+        vb = 2.0 * p0 - 2.0 * (l - 1) * d1;
+        if (l <= 5) {
+          for (int i = ntau - 1; i >= 0; --i) {
+            const double x = kk[q] * (tau0 - tau[i]);
+            if (x >= x_lo) break;
+            const double y = x * x, sl = sph_series(l, y), sm = sph_series(l - 1, y);
+            const double xl2 = l == 2 ? 1.0 : pow(x, l - 2);
+            const double ws = wtau[i] * (double)src[i];
+            ve += ws * xl2 * ((double)l * (l - 1) * sl - 2.0 * y * sl + 2.0 * sm);
+            vb += ws * 2.0 * xl2 * x * (sm - (l - 1) * sl);
+          }
+        }
+      }
+      e[idx] = (T)ve;
+      b[idx] = (T)vb;
+    }
+    __syncthreads();  // the carry is read by the next chunk
+  }
+}
+
+int launch_los_tensor(const gcamb_grid *g, const void *ST, const void *SP, int M, int mode, void *DT, void *DE,
+                      void *DB, cudaStream_t st) {
+  if (g->lmin >= 2 && g->lmax == g->lmin)
+    return fail(GCAMB_EINVAL, "los_transfer_tensor: needs lmax > lmin when lmin >= 2 (the kernels take j_(l-1))");
+  double x_lo = 1e-12;
+  if (emode_x_lo(g, &x_lo)) return fail(GCAMB_EINVAL, "los_transfer_tensor: eps_cut too large for the l = 2 limit");
+  // raw sums of the polarisation source: D0 -> DE, D1 -> DB, D2 -> DT
+  int rc = launch_los_plain_k<0, false>(g, SP, M, mode, DE, st);
+  if (!rc) rc = launch_los_plain_k<1, false>(g, SP, M, mode, DB, st);
+  if (!rc) rc = launch_los_plain_k<2, false>(g, SP, M, mode, DT, st);
+  if (rc) return rc;
+  const unsigned rows = (unsigned)((size_t)M * g->nk);
+  if ((size_t)M * g->nk > 0x7fffffffULL) return fail(GCAMB_EINVAL, "los_transfer_tensor: too many rows");
+  {
+    ProfScope prof(GCAMB_K_LOS_PLAIN, st);
+    if (mode == GCAMB_PLAIN64)
+      tensor_combine_kernel<double><<<rows, 256, 0, st>>>(static_cast<double *>(DE), static_cast<double *>(DB),
+                                                          static_cast<const double *>(DT),
+                                                          static_cast<const double *>(SP), g->d_k, g->d_tau,
+                                                          g->tau0, g->d_wtau, x_lo, g->nk, g->ntau, g->lmin, g->lmax);
+    else
+      tensor_combine_kernel<float><<<rows, 256, 0, st>>>(static_cast<float *>(DE), static_cast<float *>(DB),
+                                                         static_cast<const float *>(DT),
+                                                         static_cast<const float *>(SP), g->d_k, g->d_tau, g->tau0,
+                                                         g->d_wtau, x_lo, g->nk, g->ntau, g->lmin, g->lmax);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "los_transfer_tensor: launch");
+  }
+  // temperature: t_l = c_l j_l / x^2, the E-mode kernel of Eq. (3), into DT
+  return launch_los_plain_k<2, true>(g, ST, M, mode, DT, st);
 }
 
 // C_l[m][l] = 4 pi sum_k w_k P[m][k] Delta[m][k][l]^2 in FP64, increasing k.

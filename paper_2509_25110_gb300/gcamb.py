@@ -60,6 +60,7 @@ def lib():
     L.gcamb_cl_cross.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp]
     L.gcamb_los_cl_workspace.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
     L.gcamb_los_cl.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_size_t, _vp]
+    L.gcamb_los_transfer_tensor.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp]
     L.gcamb_los_cl_te_workspace.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
     L.gcamb_los_cl_te.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp,
                                   ctypes.c_size_t, _vp]
@@ -242,6 +243,23 @@ def los_transfer_e(g: Grid, SP, mode: int, DeltaE=None, stream=None):
     _check(lib().gcamb_los_transfer_e(g.handle, _dev(SP, dt, (M, g.nk, g.ntau), "S_P"), M, int(mode),
                                       _dev(DeltaE, dt, (M, g.nk, g.nl), "Delta_E"), _stream(stream)))
     return DeltaE
+
+
+def los_transfer_tensor(g: Grid, ST, SP, mode: int, out=None, stream=None):
+    """Tensor modes: ST, SP[M][nk][ntau] -> (Delta_T, Delta_E, Delta_B), each
+    [M][nk][nl] (FP64 for PLAIN64, FP32 for PLAIN32)."""
+    import torch
+    dt = torch.float64 if mode == PLAIN64 else torch.float32
+    M = ST.shape[0]
+    if out is None:
+        out = tuple(torch.empty((M, g.nk, g.nl), dtype=dt, device=ST.device) for _ in range(3))
+    DT, DE, DB = out
+    _check(lib().gcamb_los_transfer_tensor(g.handle, _dev(ST, dt, (M, g.nk, g.ntau), "ST"),
+                                           _dev(SP, dt, (M, g.nk, g.ntau), "SP"), M, int(mode),
+                                           _dev(DT, dt, (M, g.nk, g.nl), "Delta_T"),
+                                           _dev(DE, dt, (M, g.nk, g.nl), "Delta_E"),
+                                           _dev(DB, dt, (M, g.nk, g.nl), "Delta_B"), _stream(stream)))
+    return DT, DE, DB
 
 
 def cl_cross(g: Grid, DX, DY, Pk, Cl=None, stream=None):

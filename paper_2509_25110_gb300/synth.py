@@ -175,6 +175,8 @@ def workload(name: str, M: Optional[int] = None) -> Workload:
     plain_lmax5000     : 1 model, l 2..5000, 3000 k log 1e-5..1.0, 2000 tau dense near tau*
     batched_lmax2500   : 256 models, l 2..2500, 2000 k log 1e-4..0.3, 1000 tau uniform
     uneven_lmax6000    : 1000 models on a 3000-point linear k grid, 1000 tau uniform
+    tensor_lmax1500    : 1 model, l 2..1500, 1000 k log 1e-4..3000/tau0, 1000 tau uniform
+                         (tensor modes: l_max and k tau0 <= 3000 as in the paper's runs)
     """
     tau0 = 14000.0
     if name == "plain_lmax500":
@@ -183,6 +185,8 @@ def workload(name: str, M: Optional[int] = None) -> Workload:
         wl = Workload(name, log_grid(1e-5, 1.0, 3000), dense_tau_grid(), tau0, 2, 5000, 1)
     elif name == "batched_lmax2500":
         wl = Workload(name, log_grid(1e-4, 0.3, 2000), uniform_grid(200.0, 14000.0, 1000), tau0, 2, 2500, 256)
+    elif name == "tensor_lmax1500":
+        wl = Workload(name, log_grid(1e-4, 3000.0 / tau0, 1000), uniform_grid(200.0, 14000.0, 1000), tau0, 2, 1500, 1)
     elif name == "uneven_lmax6000":
         wl = Workload(name, master_linear_k(), uniform_grid(200.0, 14000.0, 1000), tau0, 2, 6000, 1000)
     else:
@@ -275,6 +279,37 @@ def sources_pol_torch(k, tau, p: ModelParams, device, dtype=None):
         ak = A_P * torch.sin(kt * float(p.r_s[m]) + float(p.phi[m])) * torch.exp(-(kt / float(p.k_D[m])) ** 2)
         out[m] = (ak[:, None] * g[None, :] + re_k[:, None] * re_tau[None, :]).to(dtype)
     return out
+
+
+def sources_tensor(k: np.ndarray, tau: np.ndarray, p: ModelParams, dtype=np.float64):
+    """Tensor-mode sources (ST, SP), each [M][nk][ntau] in float64, returned in
+    `dtype`: the gravitational-wave amplitude at recombination,
+    h(k) = sin(k tau*) / (k tau*), times the visibility peak g(tau), plus a
+    late term (temperature) and the reionisation term (polarisation):
+
+    ST(k,tau) = h(k) [g(tau) + b 1e-3 exp(-(tau-TAU_L)^2 / (2 S_L^2))],
+    SP(k,tau) = h(k) [A_P g(tau) + B_RE exp(-(tau-TAU_RE)^2 / (2 S_RE^2))].
+    """
+    k = np.asarray(k, dtype=np.float64)
+    tau = np.asarray(tau, dtype=np.float64)
+    ST = np.empty((p.M, k.size, tau.size), dtype=dtype)
+    SP = np.empty_like(ST)
+    late = np.exp(-(tau - TAU_L) ** 2 / (2.0 * S_L ** 2))
+    re = np.exp(-(tau - TAU_RE) ** 2 / (2.0 * S_RE ** 2))
+    for m in range(p.M):
+        g = np.exp(-(tau - p.tau_star[m]) ** 2 / (2.0 * p.sigma[m] ** 2)) / (p.sigma[m] * math.sqrt(2.0 * math.pi))
+        u = k * p.tau_star[m]
+        h = np.sin(u) / u
+        ST[m] = (h[:, None] * (g + 1e-3 * p.b[m] * late)[None, :]).astype(dtype)
+        SP[m] = (h[:, None] * (A_P * g + B_RE * re)[None, :]).astype(dtype)
+    return ST, SP
+
+
+def primordial_tensor(k: np.ndarray, p: ModelParams, r: float = 0.1, A_s: float = A_S) -> np.ndarray:
+    """P_t[M][nk] = r A_s (k/0.05)^n_t, n_t = -r/8 (the single-field
+    consistency relation), float64."""
+    k = np.asarray(k, dtype=np.float64)
+    return np.broadcast_to(r * A_s * np.power(k / K_PIVOT, -r / 8.0), (p.M, k.size)).copy()
 
 
 def primordial(k: np.ndarray, p: ModelParams, A_s: float = A_S) -> np.ndarray:
