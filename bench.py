@@ -52,7 +52,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nk", type=int, default=0,
                     help="profiling case: the same k range with this many nodes (default: the workload's 2000)")
-    ap.add_argument("--workload", default="batched", choices=["batched", "uneven", "emulator", "te"],
+    ap.add_argument("--workload", default="batched", choices=["batched", "uneven", "emulator", "te", "tensor"],
                     help="batched (the headline), uneven (1000 sources, l_max <= 6000, plan + graph), "
                          "emulator (train on 100k spectra, serve)")
     ap.add_argument("--kernel-only", action="store_true",
@@ -401,6 +401,93 @@ def run_te(args):
     print(json.dumps(line), flush=True)
 
 
+def run_tensor(args):
+    """Tensor modes on the plain path: the l_max = 1500, k tau0 <= 3000 tensor
+    grid of the paper's runs, 4 models a step, Delta_T, Delta_E, Delta_B
+    (gcamb_los_transfer_tensor) and C^TT, C^EE, C^BB, C^TE, in FP64 and FP32."""
+    import numpy as np
+    import torch
+
+    from paper_2509_25110_gb300 import build, gcamb, synth
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    build.build()
+    wl = synth.workload("tensor_lmax1500")
+    M = 4
+    p = synth.model_params(M, seed=0)
+    ST, SP = synth.sources_tensor(wl.k, wl.tau, p)
+    Pt = torch.as_tensor(synth.primordial_tensor(wl.k, p), device=dev)
+    g = gcamb.grid_create(wl.k, wl.tau, wl.tau0, wl.lmin, wl.lmax)
+    info = gcamb.grid_info(g)
+    res = {}
+    for name, mode, dt in (("plain64", gcamb.PLAIN64, torch.float64), ("plain32", gcamb.PLAIN32, torch.float32)):
+        gcamb.bessel_table(g, mode)
+        STd, SPd = (torch.as_tensor(a, dtype=dt, device=dev) for a in (ST, SP))
+        out = tuple(torch.empty((M, wl.nk, wl.nl), dtype=dt, device=dev) for _ in range(3))
+        cls = tuple(torch.empty((M, wl.nl), dtype=torch.float64, device=dev) for _ in range(4))
+
+        def step():
+            DT, DE, DB = gcamb.los_transfer_tensor(g, STd, SPd, mode, out=out)
+            gcamb.cl(g, DT, Pt, cls[0])
+            gcamb.cl(g, DE, Pt, cls[1])
+            gcamb.cl(g, DB, Pt, cls[2])
+            gcamb.cl_cross(g, DT, DE, Pt, cls[3])
+        for _ in range(max(3, args.warmup)):
+            step()
+        gcamb.sync()
+        steps = max(3, min(args.steps, 20))
+        gcamb.profile_enable(True)
+        ms, clocks = _timed_region(step, steps, dev)
+        gcamb.sync()
+        kms, kn = gcamb.profile_read(gcamb.K_LOS_PLAIN)
+        gcamb.profile_enable(False)
+        # four plain launches a step (D0, D1, D2 of S_P; the temperature), each
+        # 2 flop per stored (l, k, tau) table entry per model
+        flops = 4 * 2.0 * info["stored_plain64"] * M
+        peak = gcamb.probe_flops(0 if mode == gcamb.PLAIN64 else 1)
+        res[name] = {"models_per_s": M * steps / (ms * 1e-3), "ms_per_step": ms / steps,
+                     "projection_ms": kms / steps, "achieved_tflops": flops / (kms / steps * 1e-3) / 1e12,
+                     "peak_tflops": peak / 1e12, "clocks": clocks,
+                     "cls": [c.cpu().numpy() for c in cls]}
+    # the oracle on one model: accuracy and the CPU baseline
+    cpu = None
+    err = None
+    if not args.no_cpu_baseline:
+        import oracle
+        from oracle import build as ob
+        ob.build()
+        t0 = time.perf_counter()
+        R = oracle.los_tensor(wl.k, wl.tau, wl.tau0, wl.lmin, wl.lmax, ST[:1], SP[:1])
+        P1 = Pt[:1].cpu().numpy()
+        ref = [oracle.cl_cross(wl.k, R[0], R[0], P1), oracle.cl_cross(wl.k, R[1], R[1], P1),
+               oracle.cl_cross(wl.k, R[2], R[2], P1), oracle.cl_cross(wl.k, R[0], R[1], P1)]
+        dt = time.perf_counter() - t0
+        cpu = {"value": 1 / dt, "unit": "models/s (tensor TT, EE, BB, TE)", "cores": oracle.num_threads(),
+               "kind": "oracle", "sample": "1 of the 4 models, full tensor grid, %.1f s" % dt}
+        err = {}
+        for name in res:
+            c = [x[:1] for x in res[name]["cls"]]
+            err[name] = {key: float(np.max(np.abs(c[i] / ref[i] - 1)[ref[i] > 0])) for i, key in
+                         enumerate(("TT", "EE", "BB"))}
+            err[name]["TE_on_sqrt_TT_EE"] = float(np.max(np.abs(c[3] - ref[3])[ref[0] > 0] /
+                                                         np.sqrt(ref[0] * ref[1])[ref[0] > 0]))
+    r64 = res["plain64"]
+    line = {"metric": "tensor TT+EE+BB+TE spectrum sets/sec at l_max=1500 (plain FP64)",
+            "value": r64["models_per_s"], "unit": "models/s", "n_gpus": 1, "steps": max(3, min(args.steps, 20)),
+            "warmup": args.warmup, "ms_per_step": r64["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "tensor_lmax1500", "M": M, "lmax": wl.lmax, "nk": wl.nk, "ntau": wl.ntau,
+                       "stored_entries": info["stored_plain64"],
+                       "plain32": {k: v for k, v in res["plain32"].items() if k not in ("cls", "clocks")},
+                       "max_err_vs_oracle": err},
+            "roofline": {"bound": "alu", "achieved": r64["achieved_tflops"], "peak": r64["peak_tflops"],
+                         "unit": "TFLOP/s", "frac": r64["achieved_tflops"] / r64["peak_tflops"], "traffic": None,
+                         "peak_source": "FP64 FMA probe (gcamb_probe_flops)", "kernel": "los_plain_kernel<double>",
+                         "kernel_ms": r64["projection_ms"]},
+            "cpu_baseline": cpu, "clocks": r64["clocks"], "gpu_launches": 9 * max(3, min(args.steps, 20))}
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------------ our arm
 
 def main():
@@ -416,6 +503,9 @@ def main():
         return
     if args.workload == "te":
         run_te(args)
+        return
+    if args.workload == "tensor":
+        run_tensor(args)
         return
     import numpy as np
     import torch
