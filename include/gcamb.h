@@ -188,6 +188,22 @@ int gcamb_los_transfer_tensor(const gcamb_grid *g, const void *ST, const void *S
                               void *DeltaE, void *DeltaB, void *stream);
 
 /*
+ * Source interpolation onto the grid's k nodes (the step that prepares the
+ * sources before the projection, Sec. 3.3): the natural cubic spline in k of
+ * every (source, tau) column (second derivatives zero at both ends), solved
+ * and evaluated in FP64.
+ *   k_in[nk_in]          host, strictly increasing, nk_in >= 2; the grid's k
+ *                        range must lie inside [k_in[0], k_in[nk_in-1]]
+ *   S_in[M][nk_in][ntau] device, dtype GCAMB_F64 or GCAMB_F32 (ntau: the grid's)
+ *   S_out[M][nk][ntau]   device, same dtype
+ *   ws, ws_bytes         device workspace of gcamb_interp_sources_workspace bytes
+ * Errors: GCAMB_EINVAL (arguments), GCAMB_ECUDA.
+ */
+int gcamb_interp_sources_workspace(const gcamb_grid *g, int M, int nk_in, size_t *bytes);
+int gcamb_interp_sources(const gcamb_grid *g, const double *k_in, int nk_in, const void *S_in, int M, int dtype,
+                         void *S_out, void *ws, size_t ws_bytes, void *stream);
+
+/*
  * Cross spectrum, Eq. (1) with X, Y in {T, E}:
  *   C^XY[m][l] = 4 pi sum_k w_k P[m][k] DX[m][k][l] DY[m][k][l]
  * DX, DY [M][nk][nl] device, both of d_dtype (GCAMB_F64 or GCAMB_F32);
@@ -466,6 +482,7 @@ int gcamb_sync(void *stream);
 #define GCAMB_K_WEIGHTS   4  /* 4 pi w_k P(k) weights (batched path) */
 #define GCAMB_K_TC        5  /* tensor-core contraction + square + k-chunk sum */
 #define GCAMB_K_REDUCE    6  /* FP64 sum of the k-chunk partials */
+#define GCAMB_K_INTERP    7  /* source interpolation onto the transfer k grid */
 #define GCAMB_K_COUNT     8
 
 /*

@@ -92,6 +92,10 @@ int launch_los_plain(const gcamb_grid *g, const void *S, int M, int mode, void *
                      bool emode = false);
 int launch_los_tensor(const gcamb_grid *g, const void *ST, const void *SP, int M, int mode, void *DT, void *DE,
                       void *DB, cudaStream_t st);
+// Source interpolation onto the grid's k nodes (interp.cu).
+size_t interp_workspace_bytes(int M, int nk_in, int ntau, int nk_out);
+int launch_interp_sources(const double *k_in, int nk_in, const void *S_in, int M, int ntau, int dtype,
+                          const gcamb_grid *g, void *S_out, void *ws, size_t ws_bytes, cudaStream_t st);
 // E-mode small-x cut x_lo of the grid (plain.cu); -1 if it would exceed 0.2.
 int emode_x_lo(const gcamb_grid *g, double *x_lo);
 int launch_cl_cross(const gcamb_grid *g, const void *DX, const void *DY, int d_dtype, const double *Pk, int M,

@@ -21,8 +21,8 @@ PLAIN64, PLAIN32, BF16X3, TF32X3, F16X3 = 0, 1, 2, 3, 4
 F64, F32 = 0, 1
 MODE_NAMES = {PLAIN64: "plain64", PLAIN32: "plain32", BF16X3: "bf16x3", TF32X3: "tf32x3", F16X3: "f16x3"}
 INFO_N = 8
-K_TABLE, K_LOS_PLAIN, K_CL, K_SPLIT, K_WEIGHTS, K_TC, K_REDUCE = range(7)
-K_NAMES = ("bessel_table", "los_plain", "cl", "split_sources", "weights", "los_cl_tc", "reduce")
+K_TABLE, K_LOS_PLAIN, K_CL, K_SPLIT, K_WEIGHTS, K_TC, K_REDUCE, K_INTERP = range(8)
+K_NAMES = ("bessel_table", "los_plain", "cl", "split_sources", "weights", "los_cl_tc", "reduce", "interp_sources")
 
 _vp = ctypes.c_void_p
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -60,6 +60,9 @@ def lib():
     L.gcamb_cl_cross.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp]
     L.gcamb_los_cl_workspace.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
     L.gcamb_los_cl.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_size_t, _vp]
+    L.gcamb_interp_sources_workspace.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
+    L.gcamb_interp_sources.argtypes = [_vp, _vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp,
+                                       ctypes.c_size_t, _vp]
     L.gcamb_los_transfer_tensor.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp]
     L.gcamb_los_cl_te_workspace.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
     L.gcamb_los_cl_te.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp,
@@ -260,6 +263,26 @@ def los_transfer_tensor(g: Grid, ST, SP, mode: int, out=None, stream=None):
                                            _dev(DE, dt, (M, g.nk, g.nl), "Delta_E"),
                                            _dev(DB, dt, (M, g.nk, g.nl), "Delta_B"), _stream(stream)))
     return DT, DE, DB
+
+
+def interp_sources(g: Grid, k_in, S_in, S_out=None, ws=None, stream=None):
+    """Natural cubic spline in k of S_in[M][nk_in][ntau] (FP64 or FP32) from
+    the nodes k_in onto the grid's k: -> S_out[M][nk][ntau], same dtype."""
+    import torch
+    k_in = np.ascontiguousarray(k_in, dtype=np.float64)
+    M = S_in.shape[0]
+    dt = S_in.dtype
+    if S_out is None:
+        S_out = torch.empty((M, g.nk, g.ntau), dtype=dt, device=S_in.device)
+    if ws is None:
+        b = ctypes.c_size_t()
+        _check(lib().gcamb_interp_sources_workspace(g.handle, M, k_in.size, ctypes.byref(b)))
+        ws = torch.empty(max(1, b.value), dtype=torch.uint8, device=S_in.device)
+    _check(lib().gcamb_interp_sources(g.handle, k_in.ctypes.data_as(_dp), k_in.size,
+                                      _dev(S_in, dt, (M, k_in.size, g.ntau), "S_in"), M,
+                                      F64 if dt == torch.float64 else F32, _dev(S_out, dt, (M, g.nk, g.ntau), "S_out"),
+                                      _dev(ws, torch.uint8, name="ws"), ws.numel(), _stream(stream)))
+    return S_out
 
 
 def cl_cross(g: Grid, DX, DY, Pk, Cl=None, stream=None):
