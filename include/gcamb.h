@@ -191,7 +191,7 @@ int gcamb_los_transfer_tensor(const gcamb_grid *g, const void *ST, const void *S
  * Source interpolation onto the grid's k nodes (the step that prepares the
  * sources before the projection, Sec. 3.3): the natural cubic spline in k of
  * every (source, tau) column (second derivatives zero at both ends), solved
- * and evaluated in FP64.
+ * and evaluated in the sources' precision (FP64 or FP32).
  *   k_in[nk_in]          host, strictly increasing, nk_in >= 2; the grid's k
  *                        range must lie inside [k_in[0], k_in[nk_in-1]]
  *   S_in[M][nk_in][ntau] device, dtype GCAMB_F64 or GCAMB_F32 (ntau: the grid's)

@@ -5,11 +5,15 @@
 //   h_(j-1) M_(j-1) + 2 (h_(j-1) + h_j) M_j + h_j M_(j+1)
 //       = 6 [(y_(j+1) - y_j)/h_j - (y_j - y_(j-1))/h_(j-1)],   0 < j < n-1,
 // with M_0 = M_(n-1) = 0; on [k_j, k_(j+1)], t = (k - k_j)/h_j,
-//   y = (1-t) y_j + t y_(j+1) + h_j^2/6 [((1-t)^3 - (1-t)) M_j + (t^3 - t) M_(j+1)].
-// The elimination coefficients depend on the k nodes only and are formed on
-// the host; one thread per (source, tau) column runs the forward sweep and
-// the back substitution in FP64 (reads along k are coalesced across tau),
-// then one thread per output element evaluates the spline.
+//   y = (1-t) y_j + t y_(j+1) + h_j^2/6 [((1-t)^3 - (1-t)) M_j + (t^3 - t) M_(j+1)]
+// (the cubic factors are evaluated in their factored forms, which do not
+// cancel next to a node).
+// The elimination coefficients and 1/h depend on the k nodes only and are
+// formed on the host; one thread per (source, tau) column runs the forward
+// sweep and the back substitution (reads along k are coalesced across tau),
+// then one thread per output element evaluates the spline.  The arithmetic
+// is that of the sources: FP64 for FP64 sources, FP32 for FP32 sources (the
+// GPU's FP64 rate would make the FP32 case ALU-bound).
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -20,77 +24,138 @@ namespace gcamb {
 
 namespace {
 
-// Per column: d'_j = (r_j - a_j d'_(j-1)) * inv_j, M_j = d'_j - c'_j M_(j+1).
-template <typename T>
-__global__ void __launch_bounds__(256) spline_solve_kernel(const T *__restrict__ y, const double *__restrict__ h,
-                                                           const double *__restrict__ cp,
-                                                           const double *__restrict__ inv, int n, int ntau, int M,
-                                                           double *__restrict__ Md) {
+// Node coefficients of one precision: h, 1/h, c', 1/den (each [n]).
+template <typename A>
+struct NodeCoef {
+  const A *h, *ih, *cp, *inv;
+};
+
+// Per column: d'_j = (r_j - h_(j-1) d'_(j-1)) / den_j, M_j = d'_j - c'_j M_(j+1).
+template <typename T, typename A>
+__global__ void __launch_bounds__(256) spline_solve_kernel(const T *__restrict__ y, NodeCoef<A> c, int n, int ntau,
+                                                           int M, A *__restrict__ Md) {
   const size_t col = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // m * ntau + tau
   if (col >= (size_t)M * ntau) return;
   const size_t m = col / ntau, t = col - m * ntau;
   const T *yc = y + m * (size_t)n * ntau + t;
-  double *mc = Md + m * (size_t)n * ntau + t;
-  mc[0] = 0.0;
-  mc[(size_t)(n - 1) * ntau] = 0.0;
+  A *mc = Md + m * (size_t)n * ntau + t;
+  mc[0] = A(0);
+  mc[(size_t)(n - 1) * ntau] = A(0);
   if (n < 3) return;
-  double y0 = (double)yc[0], y1 = (double)yc[ntau];
-  double dprev = 0.0;
+  A y0 = (A)yc[0], y1 = (A)yc[ntau];
+  A s0 = (y1 - y0) * c.ih[0];  // slope of the previous interval
+  A dprev = A(0);
+#pragma unroll 8
   for (int j = 1; j < n - 1; ++j) {
-    const double y2 = (double)yc[(size_t)(j + 1) * ntau];
-    const double r = 6.0 * ((y2 - y1) / h[j] - (y1 - y0) / h[j - 1]);
-    const double d = (r - (j > 1 ? h[j - 1] * dprev : 0.0)) * inv[j];
+    const A y2 = (A)yc[(size_t)(j + 1) * ntau];
+    const A s1 = (y2 - y1) * c.ih[j];
+    const A r = A(6) * (s1 - s0);
+    const A d = (r - (j > 1 ? c.h[j - 1] * dprev : A(0))) * c.inv[j];
     mc[(size_t)j * ntau] = d;
     dprev = d;
-    y0 = y1;
     y1 = y2;
+    s0 = s1;
   }
-  double next = 0.0;  // M_(n-1)
+  A next = A(0);  // M_(n-1)
+#pragma unroll 8
   for (int j = n - 2; j >= 1; --j) {
-    const double v = mc[(size_t)j * ntau] - cp[j] * next;
+    const A v = mc[(size_t)j * ntau] - c.cp[j] * next;
     mc[(size_t)j * ntau] = v;
     next = v;
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) spline_eval_kernel(const T *__restrict__ y, const double *__restrict__ Md,
-                                                          const int *__restrict__ jq, const double *__restrict__ tq,
-                                                          const double *__restrict__ hq, int n, int nq, int ntau,
-                                                          int M, T *__restrict__ out) {
-  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // (m * nq + q) * ntau + tau
-  if (e >= (size_t)M * nq * ntau) return;
-  const size_t t = e % ntau, mq = e / ntau;
-  const size_t q = mq % nq, m = mq / nq;
-  const int j = jq[q];
-  const double s = tq[q], h = hq[q], u = 1.0 - s;
-  const size_t i0 = (m * (size_t)n + j) * ntau + t, i1 = i0 + ntau;
-  const double v = u * (double)y[i0] + s * (double)y[i1] +
-                   h * h / 6.0 * ((u * u * u - u) * Md[i0] + (s * s * s - s) * Md[i1]);
-  out[e] = (T)v;
+// Blocks: x = (block of kQB output nodes) * ntc + (tau chunk of 256),
+// y = source; tau is the fastest index, so loads and stores are coalesced.
+// Each thread walks kQB consecutive output nodes of its column and reloads
+// the interval's y and M only when the interval changes.
+constexpr int kQB = 64;
+
+template <typename T, typename A>
+__global__ void __launch_bounds__(256) spline_eval_kernel(const T *__restrict__ y, const A *__restrict__ Md,
+                                                          const int *__restrict__ jq, const A *__restrict__ tq,
+                                                          const A *__restrict__ hq, int n, int nq, int ntau, int ntc,
+                                                          T *__restrict__ out) {
+  const int qb = (int)(blockIdx.x / (unsigned)ntc);
+  const int t = (int)(blockIdx.x - (unsigned)qb * ntc) * 256 + threadIdx.x;
+  if (t >= ntau) return;
+  const size_t m = blockIdx.y;
+  const int q0 = qb * kQB, q1 = min(nq, q0 + kQB);
+  int jc = -1;
+  A y0 = A(0), y1 = A(0), m0 = A(0), m1 = A(0);
+  for (int q = q0; q < q1; ++q) {
+    const int j = jq[q];
+    if (j != jc) {
+      const size_t i0 = (m * (size_t)n + j) * ntau + t, i1 = i0 + ntau;
+      y0 = (A)y[i0];
+      y1 = (A)y[i1];
+      m0 = Md[i0];
+      m1 = Md[i1];
+      jc = j;
+    }
+    const A s = tq[q], h = hq[q], u = A(1) - s;
+    // u^3 - u = -s u (1 + u) and s^3 - s = -s u (1 + s): no cancellation near the nodes
+    const A su = s * u;
+    const A v = u * y0 + s * y1 - h * h / A(6) * su * ((A(1) + u) * m0 + (A(1) + s) * m1);
+    out[(m * nq + q) * (size_t)ntau + t] = (T)v;
+  }
 }
 
 size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// Workspace regions (each 256-byte aligned): node coefficients in FP64
+// [4][n] and FP32 [4][n]; each output node's t and h in FP64 [2][nq] and FP32
+// [2][nq]; its interval [nq] (int); the second derivatives [M][n][ntau] in the
+// arithmetic's precision (sized for FP64).
+struct InterpLayout {
+  size_t c64, c32, q64, q32, qj, md, total;
+  InterpLayout(int M, int n, int ntau, int nq) {
+    c64 = 0;
+    c32 = c64 + a256((size_t)n * 4 * sizeof(double));
+    q64 = c32 + a256((size_t)n * 4 * sizeof(float));
+    q32 = q64 + a256((size_t)nq * 2 * sizeof(double));
+    qj = q32 + a256((size_t)nq * 2 * sizeof(float));
+    md = qj + a256((size_t)nq * sizeof(int));
+    total = md + a256((size_t)M * n * ntau * sizeof(double));
+  }
+};
+
+template <typename T, typename A>
+int launch_interp_t(const InterpLayout &L, char *w, int n, int nq, int ntau, int M, const T *S_in, T *S_out,
+                    cudaStream_t st) {
+  const A *c = reinterpret_cast<const A *>(w + (sizeof(A) == 8 ? L.c64 : L.c32));
+  const A *qd = reinterpret_cast<const A *>(w + (sizeof(A) == 8 ? L.q64 : L.q32));
+  NodeCoef<A> nc{c, c + n, c + 2 * n, c + 3 * n};
+  A *Md = reinterpret_cast<A *>(w + L.md);
+  const size_t cols = (size_t)M * ntau;
+  const int ntc = (ntau + 255) / 256, nqb = (nq + kQB - 1) / kQB;
+  spline_solve_kernel<T, A><<<(unsigned)((cols + 255) / 256), 256, 0, st>>>(S_in, nc, n, ntau, M, Md);
+  spline_eval_kernel<T, A><<<dim3((unsigned)((size_t)nqb * ntc), (unsigned)M), 256, 0, st>>>(
+      S_in, Md, reinterpret_cast<const int *>(w + L.qj), qd, qd + nq, n, nq, ntau, ntc, S_out);
+  return GCAMB_OK;
+}
+
 }  // namespace
 
-// Workspace: [h, c', 1/den] (3 nk_in doubles) | [t, h] of each output node
-// (2 nk_out doubles) | interval of each output node (nk_out ints) |
-// second derivatives [M][nk_in][ntau] (doubles), each region 256-byte aligned.
 size_t interp_workspace_bytes(int M, int nk_in, int ntau, int nk_out) {
-  return a256((size_t)nk_in * 3 * sizeof(double)) + a256((size_t)nk_out * 2 * sizeof(double)) +
-         a256((size_t)nk_out * sizeof(int)) + a256((size_t)M * nk_in * ntau * sizeof(double));
+  return InterpLayout(M, nk_in, ntau, nk_out).total;
 }
 
 int launch_interp_sources(const double *k_in, int nk_in, const void *S_in, int M, int ntau, int dtype,
                           const gcamb_grid *g, void *S_out, void *ws, size_t ws_bytes, cudaStream_t st) {
   const int n = nk_in, nq = g->nk;
-  if (ws_bytes < interp_workspace_bytes(M, n, ntau, nq)) return fail(GCAMB_EINVAL, "interp_sources: workspace too small");
+  const InterpLayout L(M, n, ntau, nq);
+  if (ws_bytes < L.total) return fail(GCAMB_EINVAL, "interp_sources: workspace too small");
+  if ((size_t)nq * ((ntau + 255) / 256) > 0x7fffffffULL || M > 65535 || (size_t)M * ntau / 256 > 0x7fffffffULL)
+    return fail(GCAMB_EINVAL, "interp_sources: too many sources or nodes for one launch");
   // elimination coefficients (nodes only) and each output node's interval
-  std::vector<double> host(3 * (size_t)n, 0.0), qd(2 * (size_t)nq);
+  std::vector<double> c64(4 * (size_t)n, 0.0), q64(2 * (size_t)nq);
   std::vector<int> qj(nq);
-  double *h = host.data(), *cp = h + n, *inv = cp + n;
-  for (int j = 0; j + 1 < n; ++j) h[j] = k_in[j + 1] - k_in[j];
+  double *h = c64.data(), *ih = h + n, *cp = ih + n, *inv = cp + n;
+  for (int j = 0; j + 1 < n; ++j) {
+    h[j] = k_in[j + 1] - k_in[j];
+    ih[j] = 1.0 / h[j];
+  }
   for (int j = 1; j < n - 1; ++j) {
     const double b = 2.0 * (h[j - 1] + h[j]);
     const double den = b - (j > 1 ? h[j - 1] * cp[j - 1] : 0.0);
@@ -102,36 +167,25 @@ int launch_interp_sources(const double *k_in, int nk_in, const void *S_in, int M
     int j = (int)(std::upper_bound(k_in, k_in + n, k) - k_in) - 1;
     j = j < 0 ? 0 : (j > n - 2 ? n - 2 : j);
     qj[q] = j;
-    qd[q] = (k - k_in[j]) / h[j];
-    qd[nq + q] = h[j];
+    q64[q] = (k - k_in[j]) / h[j];
+    q64[nq + q] = h[j];
   }
+  std::vector<float> c32(c64.begin(), c64.end()), q32(q64.begin(), q64.end());
   char *w = static_cast<char *>(ws);
-  const size_t o1 = a256((size_t)n * 3 * sizeof(double));
-  const size_t o2 = o1 + a256((size_t)nq * 2 * sizeof(double));
-  const size_t o3 = o2 + a256((size_t)nq * sizeof(int));
-  double *d_h = reinterpret_cast<double *>(w);
-  double *d_t = reinterpret_cast<double *>(w + o1);
-  double *d_hq = d_t + nq;
-  int *d_j = reinterpret_cast<int *>(w + o2);
-  double *d_M = reinterpret_cast<double *>(w + o3);
   // pageable copies return once the host data is staged
-  cudaError_t e = cudaMemcpyAsync(d_h, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(d_j, qj.data(), qj.size() * sizeof(int), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(d_t, qd.data(), qd.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+  cudaError_t e = cudaMemcpyAsync(w + L.c64, c64.data(), c64.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(w + L.c32, c32.data(), c32.size() * sizeof(float), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(w + L.q64, q64.data(), q64.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(w + L.q32, q32.data(), q32.size() * sizeof(float), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(w + L.qj, qj.data(), qj.size() * sizeof(int), cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "interp_sources: coefficient upload");
-  const size_t cols = (size_t)M * ntau, outs = (size_t)M * nq * ntau;
   ProfScope prof(GCAMB_K_INTERP, st);
-  if (dtype == GCAMB_F64) {
-    spline_solve_kernel<double><<<(unsigned)((cols + 255) / 256), 256, 0, st>>>(
-        static_cast<const double *>(S_in), d_h, d_h + n, d_h + 2 * n, n, ntau, M, d_M);
-    spline_eval_kernel<double><<<(unsigned)((outs + 255) / 256), 256, 0, st>>>(
-        static_cast<const double *>(S_in), d_M, d_j, d_t, d_hq, n, nq, ntau, M, static_cast<double *>(S_out));
-  } else {
-    spline_solve_kernel<float><<<(unsigned)((cols + 255) / 256), 256, 0, st>>>(
-        static_cast<const float *>(S_in), d_h, d_h + n, d_h + 2 * n, n, ntau, M, d_M);
-    spline_eval_kernel<float><<<(unsigned)((outs + 255) / 256), 256, 0, st>>>(
-        static_cast<const float *>(S_in), d_M, d_j, d_t, d_hq, n, nq, ntau, M, static_cast<float *>(S_out));
-  }
+  if (dtype == GCAMB_F64)
+    launch_interp_t<double, double>(L, w, n, nq, ntau, M, static_cast<const double *>(S_in),
+                                    static_cast<double *>(S_out), st);
+  else
+    launch_interp_t<float, float>(L, w, n, nq, ntau, M, static_cast<const float *>(S_in), static_cast<float *>(S_out),
+                                  st);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "interp_sources: launch");
   return GCAMB_OK;

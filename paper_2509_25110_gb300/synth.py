@@ -44,6 +44,8 @@ K_PIVOT = 0.05    # pivot scale [1/Mpc]
 
 # Parameter slots drawn per model, in counter order.
 SLOT_TAU_STAR, SLOT_SIGMA, SLOT_RS, SLOT_PHI, SLOT_KD, SLOT_B, SLOT_NS, SLOT_LMAX = range(8)
+SLOT_AF, SLOT_OMEGA, SLOT_PHIF = 8, 9, 10   # primordial features
+FEATURE_RANGES = {"A_f": (0.0, 0.05), "omega": (10.0, 50.0), "phi_f": (0.0, 2.0 * math.pi)}
 PARAM_RANGES = {
     "tau_star": (270.0, 300.0),
     "sigma": (15.0, 25.0),
@@ -175,6 +177,8 @@ def workload(name: str, M: Optional[int] = None) -> Workload:
     plain_lmax5000     : 1 model, l 2..5000, 3000 k log 1e-5..1.0, 2000 tau dense near tau*
     batched_lmax2500   : 256 models, l 2..2500, 2000 k log 1e-4..0.3, 1000 tau uniform
     uneven_lmax6000    : 1000 models on a 3000-point linear k grid, 1000 tau uniform
+    features_lmax2500  : 256 models, l 2..2500, 8000 k log 1e-4..0.3 (sources made on
+                         1000 k and interpolated), 1000 tau uniform, log-oscillating P(k)
     tensor_lmax1500    : 1 model, l 2..1500, 1000 k log 1e-4..3000/tau0, 1000 tau uniform
                          (tensor modes: l_max and k tau0 <= 3000 as in the paper's runs)
     """
@@ -185,6 +189,8 @@ def workload(name: str, M: Optional[int] = None) -> Workload:
         wl = Workload(name, log_grid(1e-5, 1.0, 3000), dense_tau_grid(), tau0, 2, 5000, 1)
     elif name == "batched_lmax2500":
         wl = Workload(name, log_grid(1e-4, 0.3, 2000), uniform_grid(200.0, 14000.0, 1000), tau0, 2, 2500, 256)
+    elif name == "features_lmax2500":
+        wl = Workload(name, log_grid(1e-4, 0.3, 8000), uniform_grid(200.0, 14000.0, 1000), tau0, 2, 2500, 256)
     elif name == "tensor_lmax1500":
         wl = Workload(name, log_grid(1e-4, 3000.0 / tau0, 1000), uniform_grid(200.0, 14000.0, 1000), tau0, 2, 1500, 1)
     elif name == "uneven_lmax6000":
@@ -310,6 +316,25 @@ def primordial_tensor(k: np.ndarray, p: ModelParams, r: float = 0.1, A_s: float 
     consistency relation), float64."""
     k = np.asarray(k, dtype=np.float64)
     return np.broadcast_to(r * A_s * np.power(k / K_PIVOT, -r / 8.0), (p.M, k.size)).copy()
+
+
+def feature_params(M: int, seed: int = 0, first_model: int = 0) -> dict:
+    """Per-model parameters of a logarithmic primordial oscillation (the
+    resonant features of Sec. 5): amplitude A_f, log-frequency omega, phase."""
+    out = {n: np.empty(M) for n in FEATURE_RANGES}
+    for i in range(M):
+        for n, slot in (("A_f", SLOT_AF), ("omega", SLOT_OMEGA), ("phi_f", SLOT_PHIF)):
+            lo, hi = FEATURE_RANGES[n]
+            out[n][i] = lo + (hi - lo) * uniform(seed, first_model + i, slot)
+    return out
+
+
+def primordial_features(k: np.ndarray, p: ModelParams, f: dict, A_s: float = A_S) -> np.ndarray:
+    """P[M][nk] = A_s (k/0.05)^(n_s-1) [1 + A_f sin(omega ln(k/0.05) + phi_f)]."""
+    k = np.asarray(k, dtype=np.float64)
+    lk = np.log(k / K_PIVOT)[None, :]
+    base = A_s * np.exp((p.n_s[:, None] - 1.0) * lk)
+    return base * (1.0 + f["A_f"][:, None] * np.sin(f["omega"][:, None] * lk + f["phi_f"][:, None]))
 
 
 def primordial(k: np.ndarray, p: ModelParams, A_s: float = A_S) -> np.ndarray:
