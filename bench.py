@@ -53,7 +53,7 @@ def parse_args():
     ap.add_argument("--nk", type=int, default=0,
                     help="profiling case: the same k range with this many nodes (default: the workload's 2000)")
     ap.add_argument("--workload", default="batched",
-                    choices=["batched", "uneven", "emulator", "te", "tensor", "features"],
+                    choices=["batched", "uneven", "emulator", "te", "tensor", "features", "lsampled"],
                     help="batched (the headline), uneven (1000 sources, l_max <= 6000, plan + graph), "
                          "emulator (train on 100k spectra, serve)")
     ap.add_argument("--kernel-only", action="store_true",
@@ -565,6 +565,78 @@ def run_features(args):
     print(json.dumps(line), flush=True)
 
 
+def run_lsampled(args):
+    """l-sampling (the accuracy settings of Sec. 3.1, Table 1): the 256-model
+    l_max = 2500 batch computed on sampled multipoles (l_sample_boost 1, 3
+    and 20) and splined to every l (gcamb_cl_interp), against every l
+    computed (boost 50).  Reports the throughput and the spline's deviation
+    from the every-l result, also in units of the cosmic variance (Sec. 4.6).
+    The k grid resolves the projection's oscillations in k (linear above
+    0.01), so that C_l is smooth in l."""
+    import numpy as np
+    import torch
+
+    from paper_2509_25110_gb300 import build, gcamb, synth
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    build.build()
+    wl = synth.workload("lsampled_lmax2500")
+    M = wl.M
+    p = synth.model_params(M, seed=0)
+    S = synth.sources_torch(wl.k, wl.tau, p, dev, torch.float32)
+    P = torch.as_tensor(synth.primordial(wl.k, p), device=dev)
+    gd = gcamb.grid_create(wl.k, wl.tau, wl.tau0, wl.lmin, wl.lmax)
+    gcamb.bessel_table(gd, gcamb.BF16X3)
+    Cd = gcamb.los_cl(gd, S, P, gcamb.BF16X3)
+    for _ in range(3):
+        gcamb.los_cl(gd, S, P, gcamb.BF16X3, Cd)
+    steps = max(3, min(args.steps, 100))
+    ms_dense, _ = _timed_region(lambda: gcamb.los_cl(gd, S, P, gcamb.BF16X3, Cd), steps, dev)
+    gcamb.sync()
+    Cd_h = Cd.cpu().numpy()
+    l = np.arange(wl.lmin, wl.lmax + 1, dtype=np.float64)
+    out = {}
+    clocks = None
+    for boost in (1.0, 3.0, 20.0):
+        lv = gcamb.l_sampling(wl.lmin, wl.lmax, boost)
+        g = gcamb.grid_create_lsampled(wl.k, wl.tau, wl.tau0, lv)
+        gcamb.bessel_table(g, gcamb.BF16X3)
+        ws = torch.empty(gcamb.los_cl_workspace(g, M, gcamb.BF16X3), dtype=torch.uint8, device=dev)
+        Cs = torch.empty((M, g.nl), dtype=torch.float64, device=dev)
+        Cf = torch.empty((M, wl.nl), dtype=torch.float64, device=dev)
+
+        def step():
+            gcamb.los_cl(g, S, P, gcamb.BF16X3, Cs, ws)
+            gcamb.cl_interp(g, Cs, Cf)
+        for _ in range(max(3, args.warmup)):
+            step()
+        gcamb.sync()
+        gcamb.profile_enable(True)
+        ms, clocks = _timed_region(step, steps, dev)
+        gcamb.sync()
+        kern = {gcamb.K_NAMES[i]: gcamb.profile_read(i) for i in (gcamb.K_TC, gcamb.K_REDUCE, gcamb.K_INTERP)}
+        gcamb.profile_enable(False)
+        Cf_h = Cf.cpu().numpy()
+        rel = np.abs(Cf_h / Cd_h - 1)
+        cv = np.abs(Cf_h - Cd_h) / (np.sqrt(2.0 / (2.0 * l + 1.0)) * np.abs(Cd_h))
+        out["boost_%g" % boost] = {"n_l": int(lv.size), "spectra_per_s": M * steps / (ms * 1e-3),
+                                   "ms_per_step": ms / steps, "speedup_vs_every_l": ms_dense / ms,
+                                   "max_rel_dev_from_every_l": float(rel.max()),
+                                   "median_rel_dev": float(np.median(rel)),
+                                   "max_dcl_over_sigma_cv": float(cv.max()),
+                                   "kernel_ms": {k: v[0] / max(1, v[1]) for k, v in kern.items()}}
+        g.close()
+    b1 = out["boost_1"]
+    line = {"metric": "C_l spectra/sec at l_max=2500, l_sample_boost=1 (sampled l + spline), BF16X3",
+            "value": b1["spectra_per_s"], "unit": "spectra/s", "n_gpus": 1, "steps": steps, "warmup": args.warmup,
+            "ms_per_step": b1["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "lsampled_lmax2500", "M": M, "lmax": wl.lmax, "nk": wl.nk,
+                       "ntau": wl.ntau, "every_l_spectra_per_s": M * steps / (ms_dense * 1e-3), **out},
+            "clocks": clocks, "gpu_launches": 5 * steps}
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------------ our arm
 
 def main():
@@ -586,6 +658,9 @@ def main():
         return
     if args.workload == "features":
         run_features(args)
+        return
+    if args.workload == "lsampled":
+        run_lsampled(args)
         return
     import numpy as np
     import torch

@@ -188,6 +188,33 @@ int gcamb_los_transfer_tensor(const gcamb_grid *g, const void *ST, const void *S
                               void *DeltaE, void *DeltaB, void *stream);
 
 /*
+ * Sampled multipoles (the output l-sampling of the paper's accuracy settings,
+ * Sec. 3.1, Table 1: l_sample_boost = 50 computes every l).
+ *
+ * gcamb_grid_create_lsampled: as gcamb_grid_create, with the table rows,
+ * transfer functions and C_l rows on the listed multipoles lval[0..nl)
+ * (strictly increasing, 0..20000) instead of every l; lmin = lval[0],
+ * lmax = lval[nl-1], and the row index r of every output holds l = lval[r].
+ * Every path accepts such a grid except the tensor modes (GCAMB_EUNSUPPORTED:
+ * they combine rows l and l-1).
+ *
+ * gcamb_l_sampling: a list for such a grid (host; lval NULL returns the
+ * count in *n): every l below 20 boost, then steps of round(l / (20 boost)),
+ * at most ceil(50 / boost); boost >= 50 keeps every l; lmax is always listed.
+ *
+ * gcamb_cl_interp: C_l of every multipole lmin..lmax from the sampled rows:
+ * the natural cubic spline in l of l (l+1) C_l through the samples (FP64);
+ * sampled multipoles are copied.  Cl_s [M][nl] device, Cl [M][lmax-lmin+1]
+ * device, ws of gcamb_cl_interp_workspace bytes.
+ */
+int gcamb_grid_create_lsampled(const double *k, int nk, const double *tau, int ntau, double tau0, const int *lval,
+                               int nl, double eps_cut, gcamb_grid **out);
+int gcamb_l_sampling(int lmin, int lmax, double boost, int *lval, int *n);
+int gcamb_cl_interp_workspace(const gcamb_grid *g, int M, size_t *bytes);
+int gcamb_cl_interp(const gcamb_grid *g, const double *Cl_s, int M, double *Cl, void *ws, size_t ws_bytes,
+                    void *stream);
+
+/*
  * Source interpolation onto the grid's k nodes (the step that prepares the
  * sources before the projection, Sec. 3.3): the natural cubic spline in k of
  * every (source, tau) column (second derivatives zero at both ends), solved
@@ -482,7 +509,7 @@ int gcamb_sync(void *stream);
 #define GCAMB_K_WEIGHTS   4  /* 4 pi w_k P(k) weights (batched path) */
 #define GCAMB_K_TC        5  /* tensor-core contraction + square + k-chunk sum */
 #define GCAMB_K_REDUCE    6  /* FP64 sum of the k-chunk partials */
-#define GCAMB_K_INTERP    7  /* source interpolation onto the transfer k grid */
+#define GCAMB_K_INTERP    7  /* splines: sources onto the transfer k grid, C_l onto every l */
 #define GCAMB_K_COUNT     8
 
 /*

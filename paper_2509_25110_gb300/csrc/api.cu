@@ -151,6 +151,13 @@ int ensure_device_grid(gcamb_grid *g) {
   if ((e = up(&g->d_wtau, g->wtau)) != cudaSuccess) return cuda_fail(e, "grid upload");
   if ((e = up(&g->d_wk, g->wk)) != cudaSuccess) return cuda_fail(e, "grid upload");
   if ((e = up(&g->d_xstart, g->xstart)) != cudaSuccess) return cuda_fail(e, "grid upload");
+  auto upi = [](int **dst, const std::vector<int> &src) -> cudaError_t {
+    cudaError_t e = cudaMalloc(dst, std::max<size_t>(1, src.size()) * sizeof(int));
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(*dst, src.data(), src.size() * sizeof(int), cudaMemcpyHostToDevice);
+  };
+  if ((e = upi(&g->d_lrow, g->lrow)) != cudaSuccess) return cuda_fail(e, "grid upload");
+  if ((e = upi(&g->d_rowof, g->rowof)) != cudaSuccess) return cuda_fail(e, "grid upload");
   return GCAMB_OK;
 }
 
@@ -182,14 +189,56 @@ const char *gcamb_version(void) { return "gcamb-gb300 0.1 (sm_103a)"; }
 
 const char *gcamb_last_error(void) { return t_err.c_str(); }
 
+static int grid_build(const double *k, int nk, const double *tau, int ntau, double tau0, std::vector<int> lrow,
+                      bool sampled, double eps_cut, gcamb_grid **out);
+
 int gcamb_grid_create(const double *k, int nk, const double *tau, int ntau, double tau0, int lmin, int lmax,
                       double eps_cut, gcamb_grid **out) {
   if (!out) return fail(GCAMB_EINVAL, "grid_create: out is NULL");
   *out = nullptr;
+  if (lmin < 0 || lmax < lmin || lmax > kMaxL) return fail(GCAMB_EINVAL, "grid_create: need 0 <= lmin <= lmax <= 20000");
+  std::vector<int> lrow(lmax - lmin + 1);
+  for (int r = 0; r <= lmax - lmin; ++r) lrow[r] = lmin + r;
+  return grid_build(k, nk, tau, ntau, tau0, std::move(lrow), false, eps_cut, out);
+}
+
+int gcamb_grid_create_lsampled(const double *k, int nk, const double *tau, int ntau, double tau0, const int *lval,
+                               int nl, double eps_cut, gcamb_grid **out) {
+  if (!out) return fail(GCAMB_EINVAL, "grid_create_lsampled: out is NULL");
+  *out = nullptr;
+  if (!lval || nl < 1) return fail(GCAMB_EINVAL, "grid_create_lsampled: need a list of at least one multipole");
+  for (int r = 0; r < nl; ++r) {
+    if (lval[r] < 0 || lval[r] > kMaxL) return fail(GCAMB_EINVAL, "grid_create_lsampled: need 0 <= l <= 20000");
+    if (r && lval[r] <= lval[r - 1]) return fail(GCAMB_EINVAL, "grid_create_lsampled: l must be strictly increasing");
+  }
+  return grid_build(k, nk, tau, ntau, tau0, std::vector<int>(lval, lval + nl), true, eps_cut, out);
+}
+
+int gcamb_l_sampling(int lmin, int lmax, double boost, int *lval, int *n) {
+  if (!n) return fail(GCAMB_EINVAL, "l_sampling: n is NULL");
+  if (lmin < 0 || lmax < lmin || lmax > kMaxL || !(boost > 0.0))
+    return fail(GCAMB_EINVAL, "l_sampling: need 0 <= lmin <= lmax <= 20000 and boost > 0");
+  // every l below 20 boost, then steps of round(l / (20 boost)), at most
+  // ceil(50 / boost); boost >= 50 keeps every l; lmax is always a sample
+  const int cap = std::max(1, (int)std::ceil(50.0 / boost));
+  int cnt = 0;
+  for (int l = lmin; l <= lmax;) {
+    if (lval) lval[cnt] = l;
+    ++cnt;
+    if (l == lmax) break;
+    int step = boost >= 50.0 ? 1 : std::max(1, std::min(cap, (int)std::lround(l / (20.0 * boost))));
+    l = std::min(lmax, l + step);
+  }
+  *n = cnt;
+  return GCAMB_OK;
+}
+
+static int grid_build(const double *k, int nk, const double *tau, int ntau, double tau0, std::vector<int> lrow,
+                      bool sampled, double eps_cut, gcamb_grid **out) {
+  const int lmin = lrow.front(), lmax = lrow.back();
   if (!k || !tau) return fail(GCAMB_EINVAL, "grid_create: k or tau is NULL");
   if (nk < 1 || ntau < 1) return fail(GCAMB_EINVAL, "grid_create: nk and ntau must be >= 1");
   if (nk > (1 << 24) || ntau > (1 << 20)) return fail(GCAMB_EINVAL, "grid_create: grid too large");
-  if (lmin < 0 || lmax < lmin || lmax > kMaxL) return fail(GCAMB_EINVAL, "grid_create: need 0 <= lmin <= lmax <= 20000");
   if (!(eps_cut >= 0.0) || eps_cut > 1e-3) return fail(GCAMB_EINVAL, "grid_create: eps_cut must be in [0, 1e-3]");
   if (eps_cut == 0.0) eps_cut = 1e-30;
   eps_cut = std::max(eps_cut, 1e-200);
@@ -210,8 +259,12 @@ int gcamb_grid_create(const double *k, int nk, const double *tau, int ntau, doub
   g->ntau = ntau;
   g->lmin = lmin;
   g->lmax = lmax;
-  g->nl = lmax - lmin + 1;
+  g->nl = (int)lrow.size();
   g->nlt = (g->nl + kTileL - 1) / kTileL;
+  g->lsampled = sampled;
+  g->rowof.assign((size_t)(lmax - lmin + 1), -1);
+  for (int r = 0; r < g->nl; ++r) g->rowof[lrow[r] - lmin] = r;
+  g->lrow = std::move(lrow);
   g->tau0 = tau0;
   g->eps_cut = eps_cut;
   g->k.assign(k, k + nk);
@@ -238,20 +291,20 @@ int gcamb_grid_create(const double *k, int nk, const double *tau, int ntau, doub
   };
   g->ext.assign((size_t)nk * g->nlt, 0);
   for (int lt = 0; lt < g->nlt; ++lt) {
-    const int l0 = lmin + lt * kTileL;
+    const int l0 = g->lrow[(size_t)lt * kTileL];  // the tile's lowest multipole
     const double xe = watson_threshold(l0, logeps);
     for (int q = 0; q < nk; ++q) g->ext[(size_t)q * g->nlt + lt] = (l0 == 0) ? ntau : prefix(q, xe);
   }
   // Active (l, k, tau) entries with the per-l prefix.
   {
     std::vector<double> xe(g->nl);
-    for (int l = lmin; l <= lmax; ++l) xe[l - lmin] = watson_threshold(l, logeps);
+    for (int r = 0; r < g->nl; ++r) xe[r] = watson_threshold(g->lrow[r], logeps);
     int64_t act = 0;
     for (int q = 0; q < nk; ++q) {
       int i = ntau;  // boundary moves towards 0 as l grows
-      for (int l = lmin; l <= lmax; ++l) {
-        if (l == 0) { act += ntau; continue; }
-        while (i > 0 && g->k[q] * (tau0 - g->tau[i - 1]) < xe[l - lmin]) --i;
+      for (int r = 0; r < g->nl; ++r) {
+        if (g->lrow[r] == 0) { act += ntau; continue; }
+        while (i > 0 && g->k[q] * (tau0 - g->tau[i - 1]) < xe[r]) --i;
         act += i;
       }
     }
@@ -286,6 +339,8 @@ int gcamb_grid_destroy(gcamb_grid *g) {
   cudaFree(g->d_wtau);
   cudaFree(g->d_wk);
   cudaFree(g->d_xstart);
+  cudaFree(g->d_lrow);
+  cudaFree(g->d_rowof);
   delete g;
   return GCAMB_OK;
 }

@@ -122,6 +122,8 @@ __device__ __forceinline__ uint32_t sw64_offset(int r, int cbytes) {
   return (uint32_t)r * 64u + ((uint32_t)((cbytes >> 4) ^ ((r >> 1) & 3)) << 4) + (uint32_t)(cbytes & 15);
 }
 
+// Writes w_i j_l into row (l - lmin), or, on a grid of sampled multipoles,
+// into row rowof[l - lmin] (orders that are not sampled are skipped).
 template <int MODE>
 struct TableSink {
   char *table;
@@ -130,8 +132,10 @@ struct TableSink {
   double w;  // tau weight (times 2^scale for F16X3)
   int cur_lt;
   char *base;
+  const int *rowof;  // null: every order is a row
   __device__ __forceinline__ void operator()(int l, double v) {
-    const int t = l - lmin;
+    const int t = rowof ? rowof[l - lmin] : l - lmin;
+    if (t < 0) return;
     const int lt = t >> 7, r = t & 127;
     if (lt != cur_lt) {
       cur_lt = lt;
@@ -174,7 +178,8 @@ __global__ void __launch_bounds__(128) bessel_table_kernel(const double *__restr
                                                            const int32_t *__restrict__ nkb,
                                                            const int64_t *__restrict__ off,
                                                            const double *__restrict__ xs, int nxs, int scale_exp,
-                                                           void *table) {
+                                                           const int *__restrict__ lrow,
+                                                           const int *__restrict__ rowof, int nl, void *table) {
   constexpr int KB = (MODE == GCAMB_PLAIN64 || MODE == GCAMB_PLAIN32) ? 64 : 32;
   const int q = blockIdx.y;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -184,10 +189,11 @@ __global__ void __launch_bounds__(128) bessel_table_kernel(const double *__restr
   int lt_last = -1;
   while (lt_last + 1 < nlt && nkb_q[lt_last + 1] > kbi) ++lt_last;
   if (lt_last < 0) return;
-  const int ltop = min(lmin + (lt_last + 1) * kTileL - 1, lmax);
+  // the highest multipole of the last tile this node is active in
+  const int ltop = lrow ? lrow[min((lt_last + 1) * kTileL, nl) - 1] : min(lmin + (lt_last + 1) * kTileL - 1, lmax);
   const double x = k[q] * (tau0 - tau[i]);
   TableSink<MODE> sink{static_cast<char *>(table), off + (size_t)q * nlt, lmin, kbi, i % KB,
-                       ldexp(wtau[i], scale_exp), -1, nullptr};
+                       ldexp(wtau[i], scale_exp), -1, nullptr, rowof};
   bessel_orders(x, lmin, ltop, xs, nxs, sink);
 }
 
@@ -251,27 +257,32 @@ int launch_bessel_table(gcamb_grid *g, int mode, cudaStream_t st) {
     case GCAMB_PLAIN64:
       bessel_table_kernel<GCAMB_PLAIN64><<<grid, 128, 0, st>>>(g->d_k, g->d_tau, g->d_wtau, g->tau0, g->ntau, g->lmin,
                                                                g->lmax, g->nlt, t.d_nkb, t.d_off, g->d_xstart, g->nxs,
-                                                               t.scale_exp, t.d_data);
+                                                               t.scale_exp, g->lsampled ? g->d_lrow : nullptr,
+                                                               g->lsampled ? g->d_rowof : nullptr, g->nl, t.d_data);
       break;
     case GCAMB_PLAIN32:
       bessel_table_kernel<GCAMB_PLAIN32><<<grid, 128, 0, st>>>(g->d_k, g->d_tau, g->d_wtau, g->tau0, g->ntau, g->lmin,
                                                                g->lmax, g->nlt, t.d_nkb, t.d_off, g->d_xstart, g->nxs,
-                                                               t.scale_exp, t.d_data);
+                                                               t.scale_exp, g->lsampled ? g->d_lrow : nullptr,
+                                                               g->lsampled ? g->d_rowof : nullptr, g->nl, t.d_data);
       break;
     case GCAMB_BF16X3:
       bessel_table_kernel<GCAMB_BF16X3><<<grid, 128, 0, st>>>(g->d_k, g->d_tau, g->d_wtau, g->tau0, g->ntau, g->lmin,
                                                               g->lmax, g->nlt, t.d_nkb, t.d_off, g->d_xstart, g->nxs,
-                                                              t.scale_exp, t.d_data);
+                                                              t.scale_exp, g->lsampled ? g->d_lrow : nullptr,
+                                                               g->lsampled ? g->d_rowof : nullptr, g->nl, t.d_data);
       break;
     case GCAMB_F16X3:
       bessel_table_kernel<GCAMB_F16X3><<<grid, 128, 0, st>>>(g->d_k, g->d_tau, g->d_wtau, g->tau0, g->ntau, g->lmin,
                                                              g->lmax, g->nlt, t.d_nkb, t.d_off, g->d_xstart, g->nxs,
-                                                             t.scale_exp, t.d_data);
+                                                             t.scale_exp, g->lsampled ? g->d_lrow : nullptr,
+                                                               g->lsampled ? g->d_rowof : nullptr, g->nl, t.d_data);
       break;
     case GCAMB_TF32X3:
       bessel_table_kernel<GCAMB_TF32X3><<<grid, 128, 0, st>>>(g->d_k, g->d_tau, g->d_wtau, g->tau0, g->ntau, g->lmin,
                                                               g->lmax, g->nlt, t.d_nkb, t.d_off, g->d_xstart, g->nxs,
-                                                              t.scale_exp, t.d_data);
+                                                              t.scale_exp, g->lsampled ? g->d_lrow : nullptr,
+                                                               g->lsampled ? g->d_rowof : nullptr, g->nl, t.d_data);
       break;
   }
   e = cudaGetLastError();

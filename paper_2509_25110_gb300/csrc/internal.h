@@ -58,6 +58,11 @@ struct Table {
 
 struct gcamb_grid {
   int nk = 0, ntau = 0, lmin = 0, lmax = 0, nl = 0, nlt = 0;
+  // multipole of each table row (output index): lmin + r, or the caller's
+  // sampled list; rowof[l - lmin] is the row of l or -1 (sampled grids)
+  std::vector<int> lrow, rowof;
+  bool lsampled = false;
+  int *d_lrow = nullptr, *d_rowof = nullptr;
   double tau0 = 0.0, eps_cut = 1e-30;
   std::vector<double> k, tau, wtau, wk;
   std::vector<int32_t> ext;       // [nk][nlt] active tau-prefix per (k, l-tile)

@@ -191,11 +191,213 @@ int launch_interp_sources(const double *k_in, int nk_in, const void *S_in, int M
   return GCAMB_OK;
 }
 
+namespace {
+
+// C_l on every multipole from a grid of sampled multipoles: the natural cubic
+// spline in l of D_l = l (l+1) C_l through the sampled rows; sampled
+// multipoles are copied.  The elimination coefficients depend on the sampled
+// multipoles only and come from the host (no divisions on the device); one
+// thread per model runs the FP64 sweep over the nl samples ...
+__global__ void cl_spline_solve_kernel(const double *__restrict__ Cs, const int *__restrict__ lrow,
+                                       const double *__restrict__ h, const double *__restrict__ ih,
+                                       const double *__restrict__ cp, const double *__restrict__ inv, int nl, int M,
+                                       double *__restrict__ Md) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= M) return;
+  const double *c = Cs + (size_t)m * nl;
+  double *mm = Md + (size_t)m * nl;
+  mm[0] = 0.0;
+  mm[nl - 1] = 0.0;
+  if (nl < 3) return;
+  auto D = [&](int j) { const double l = __ldg(lrow + j); return l * (l + 1.0) * __ldg(c + j); };
+  double y1 = D(1);
+  double s0 = (y1 - D(0)) * ih[0];
+  double dprev = 0.0;
+#pragma unroll 8
+  for (int j = 1; j < nl - 1; ++j) {
+    const double y2 = D(j + 1);
+    const double s1 = (y2 - y1) * ih[j];
+    const double d = (6.0 * (s1 - s0) - (j > 1 ? h[j - 1] * dprev : 0.0)) * inv[j];
+    mm[j] = d;
+    dprev = d;
+    y1 = y2;
+    s0 = s1;
+  }
+  double next = 0.0;
+#pragma unroll 8
+  for (int j = nl - 2; j >= 1; --j) {
+    const double v = mm[j] - cp[j] * next;
+    mm[j] = v;
+    next = v;
+  }
+}
+
+// ... and one thread per (model, l) evaluates, with each output multipole's
+// bracketing samples (lo, lo+1) and position s from the host.
+__global__ void cl_spline_eval_kernel(const double *__restrict__ Cs, const double *__restrict__ Md,
+                                      const int *__restrict__ lrow, const int *__restrict__ rowof,
+                                      const int *__restrict__ jl, const double *__restrict__ sl, int nl, int lmin,
+                                      int nout, int M, double *__restrict__ out) {
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (size_t)M * nout) return;
+  const int m = (int)(e / nout), i = (int)(e - (size_t)m * nout);
+  const int l = lmin + i;
+  const double *c = Cs + (size_t)m * nl;
+  const int own = rowof[i];
+  if (own >= 0) {
+    out[e] = c[own];
+    return;
+  }
+  const int lo = jl[i];
+  const double l0 = lrow[lo], l1 = lrow[lo + 1], h = l1 - l0;
+  const double s = sl[i], u = 1.0 - s, su = s * u;
+  const double y0 = l0 * (l0 + 1.0) * c[lo], y1 = l1 * (l1 + 1.0) * c[lo + 1];
+  const double *mm = Md + (size_t)m * nl;
+  const double d = u * y0 + s * y1 - h * h / 6.0 * su * ((1.0 + u) * mm[lo] + (1.0 + s) * mm[lo + 1]);
+  out[e] = d / ((double)l * (l + 1.0));
+}
+
+// The same in one block per model for up to kSmemSamples samples: the
+// model's D_l and the coefficients are staged in shared memory, thread 0
+// sweeps there (no global-memory latency in the chain), then the block
+// evaluates the model's multipoles.
+constexpr int kSmemSamples = 4000;
+
+__global__ void __launch_bounds__(256) cl_spline_block_kernel(const double *__restrict__ Cs,
+                                                              const int *__restrict__ lrow,
+                                                              const int *__restrict__ rowof,
+                                                              const double *__restrict__ coef,
+                                                              const int *__restrict__ jl,
+                                                              const double *__restrict__ sl, int nl, int lmin,
+                                                              int nout, double *__restrict__ out) {
+  extern __shared__ double sh[];
+  double *y = sh, *mm = y + nl, *h = mm + nl, *ih = h + nl, *cp = ih + nl, *inv = cp + nl;
+  const int m = blockIdx.x;
+  const double *c = Cs + (size_t)m * nl;
+  for (int j = threadIdx.x; j < nl; j += blockDim.x) {
+    const double l = lrow[j];
+    y[j] = l * (l + 1.0) * c[j];
+    h[j] = coef[j];
+    ih[j] = coef[nl + j];
+    cp[j] = coef[2 * nl + j];
+    inv[j] = coef[3 * nl + j];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mm[0] = 0.0;
+    mm[nl - 1] = 0.0;
+    if (nl >= 3) {
+      double s0 = (y[1] - y[0]) * ih[0], dprev = 0.0;
+      for (int j = 1; j < nl - 1; ++j) {
+        const double s1 = (y[j + 1] - y[j]) * ih[j];
+        const double d = (6.0 * (s1 - s0) - (j > 1 ? h[j - 1] * dprev : 0.0)) * inv[j];
+        mm[j] = d;
+        dprev = d;
+        s0 = s1;
+      }
+      double next = 0.0;
+      for (int j = nl - 2; j >= 1; --j) {
+        next = mm[j] - cp[j] * next;
+        mm[j] = next;
+      }
+    }
+  }
+  __syncthreads();
+  double *o = out + (size_t)m * nout;
+  for (int i = threadIdx.x; i < nout; i += blockDim.x) {
+    const int own = rowof[i];
+    if (own >= 0) {
+      o[i] = c[own];
+      continue;
+    }
+    const int l = lmin + i, lo = jl[i];
+    const double hh = h[lo], s = sl[i], u = 1.0 - s, su = s * u;
+    const double d = u * y[lo] + s * y[lo + 1] - hh * hh / 6.0 * su * ((1.0 + u) * mm[lo] + (1.0 + s) * mm[lo + 1]);
+    o[i] = d / ((double)l * (l + 1.0));
+  }
+}
+
+size_t al(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+// Workspace: [h, 1/h, c', 1/den] (4 nl doubles) | [s] (nout doubles) |
+// [lo] (nout ints) | second derivatives [M][nl] (doubles).
+size_t cl_interp_workspace_bytes(const gcamb_grid *g, int M) {
+  const size_t nout = (size_t)(g->lmax - g->lmin + 1);
+  return al(4 * (size_t)g->nl * sizeof(double)) + al(nout * sizeof(double)) + al(nout * sizeof(int)) +
+         al((size_t)M * g->nl * sizeof(double));
+}
+
 }  // namespace gcamb
 
 using namespace gcamb;
 
 extern "C" {
+
+int gcamb_cl_interp_workspace(const gcamb_grid *g, int M, size_t *bytes) {
+  if (!g || !bytes || M < 0) return fail(GCAMB_EINVAL, "cl_interp_workspace: bad argument");
+  *bytes = cl_interp_workspace_bytes(g, M);
+  return GCAMB_OK;
+}
+
+int gcamb_cl_interp(const gcamb_grid *g, const double *Cl_s, int M, double *Cl, void *ws, size_t ws_bytes,
+                    void *stream) {
+  if (!g) return fail(GCAMB_EINVAL, "cl_interp: NULL grid");
+  if (M < 0) return fail(GCAMB_EINVAL, "cl_interp: M < 0");
+  if (M == 0) return GCAMB_OK;
+  if (!Cl_s || !Cl || !ws) return fail(GCAMB_EINVAL, "cl_interp: NULL pointer");
+  if (ws_bytes < cl_interp_workspace_bytes(g, M)) return fail(GCAMB_EINVAL, "cl_interp: workspace too small");
+  if (int rc = ensure_device_grid(const_cast<gcamb_grid *>(g))) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nl = g->nl, nout = g->lmax - g->lmin + 1;
+  std::vector<double> coef(4 * (size_t)nl, 0.0), sv(nout, 0.0);
+  std::vector<int> jv(nout, 0);
+  double *h = coef.data(), *ih = h + nl, *cp = ih + nl, *inv = cp + nl;
+  for (int j = 0; j + 1 < nl; ++j) {
+    h[j] = (double)(g->lrow[j + 1] - g->lrow[j]);
+    ih[j] = 1.0 / h[j];
+  }
+  for (int j = 1; j < nl - 1; ++j) {
+    const double den = 2.0 * (h[j - 1] + h[j]) - (j > 1 ? h[j - 1] * cp[j - 1] : 0.0);
+    inv[j] = 1.0 / den;
+    cp[j] = (j < nl - 2 ? h[j] : 0.0) * inv[j];
+  }
+  for (int i = 0, j = 0; i < nout && nl > 1; ++i) {
+    const int l = g->lmin + i;
+    while (j + 2 < nl && g->lrow[j + 1] <= l) ++j;
+    jv[i] = j;
+    sv[i] = (l - g->lrow[j]) * ih[j];
+  }
+  char *w = static_cast<char *>(ws);
+  const size_t o1 = al(4 * (size_t)nl * sizeof(double)), o2 = o1 + al((size_t)nout * sizeof(double));
+  const size_t o3 = o2 + al((size_t)nout * sizeof(int));
+  double *d_coef = reinterpret_cast<double *>(w);
+  double *d_s = reinterpret_cast<double *>(w + o1);
+  int *d_j = reinterpret_cast<int *>(w + o2);
+  double *Md = reinterpret_cast<double *>(w + o3);
+  // pageable copies return once the host data is staged
+  cudaError_t e = cudaMemcpyAsync(d_coef, coef.data(), coef.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_s, sv.data(), sv.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_j, jv.data(), jv.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "cl_interp: coefficient upload");
+  ProfScope prof(GCAMB_K_INTERP, st);
+  if (nl <= kSmemSamples) {
+    const size_t smem = (size_t)6 * nl * sizeof(double);
+    e = cudaFuncSetAttribute(cl_spline_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cl_interp: smem attribute");
+    cl_spline_block_kernel<<<M, 256, smem, st>>>(Cl_s, g->d_lrow, g->d_rowof, d_coef, d_j, d_s, nl, g->lmin, nout, Cl);
+  } else {
+    cl_spline_solve_kernel<<<(M + 127) / 128, 128, 0, st>>>(Cl_s, g->d_lrow, d_coef, d_coef + nl, d_coef + 2 * nl,
+                                                            d_coef + 3 * nl, nl, M, Md);
+    const size_t n = (size_t)M * nout;
+    cl_spline_eval_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(Cl_s, Md, g->d_lrow, g->d_rowof, d_j, d_s, nl,
+                                                                       g->lmin, nout, M, Cl);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "cl_interp: launch");
+  return GCAMB_OK;
+}
 
 int gcamb_interp_sources_workspace(const gcamb_grid *g, int M, int nk_in, size_t *bytes) {
   if (!g || !bytes) return fail(GCAMB_EINVAL, "interp_sources_workspace: NULL argument");

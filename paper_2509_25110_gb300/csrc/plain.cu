@@ -28,8 +28,9 @@ namespace gcamb {
 // the tensor-mode kernels.
 template <typename T, int MC, int XP, bool E>
 __global__ void __launch_bounds__(256) los_plain_kernel(const T *__restrict__ table, const int32_t *__restrict__ nkb,
-                                                        const int64_t *__restrict__ off, int nk, int nlt, int lmin,
-                                                        int lmax, int ntau, const T *__restrict__ S, int M,
+                                                        const int64_t *__restrict__ off, int nk, int nlt, int nl,
+                                                        const int *__restrict__ lrow, int ntau,
+                                                        const T *__restrict__ S, int M,
                                                         T *__restrict__ Delta, const double *__restrict__ kk,
                                                         const double *__restrict__ tau, double tau0,
                                                         const double *__restrict__ wtau, double x_lo) {
@@ -38,8 +39,7 @@ __global__ void __launch_bounds__(256) los_plain_kernel(const T *__restrict__ ta
   T *s = reinterpret_cast<T *>(smem_raw);  // [MC][ext]
   __shared__ T res[MC][kTileL];
   const int lt = blockIdx.x, q = blockIdx.y, m0 = blockIdx.z * MC;
-  const int nl = lmax - lmin + 1;
-  const int l0 = lmin + lt * kTileL;
+  const int row0 = lt * kTileL;  // first row (output index) of the tile
   const size_t e_idx = (size_t)q * nlt + lt;
   const int nb = nkb[e_idx];
   const int ext = nb * KB;
@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(256) los_plain_kernel(const T *__restrict__ ta
     T acc[MC];
 #pragma unroll
     for (int m = 0; m < MC; ++m) acc[m] = T(0);
-    if (l0 + r <= lmax) {
+    if (row0 + r < nl) {
       const T *row = chunk + r * KB + lane;
       for (int b = 0; b < nb; ++b) {
         const T ja = __ldg(row + (size_t)b * kTileL * KB);
@@ -87,10 +87,11 @@ __global__ void __launch_bounds__(256) los_plain_kernel(const T *__restrict__ ta
   __syncthreads();
   for (int idx = threadIdx.x; idx < MC * kTileL; idx += blockDim.x) {
     const int m = idx / kTileL, r = idx - m * kTileL;
-    const int l = l0 + r;
-    if (m < mc && l <= lmax) {
+    const int orow = row0 + r;
+    if (m < mc && orow < nl) {
       T v = res[m][r];
       if constexpr (E) {
+        const int l = lrow[orow];
         const double c = l >= 2 ? sqrt((double)(l + 2) * (l + 1) * l * (l - 1)) : 0.0;
         double d = c * (double)v;
         if (l == 2) {  // the small-x nodes are the tail of the tau grid (x decreases with tau)
@@ -107,7 +108,7 @@ __global__ void __launch_bounds__(256) los_plain_kernel(const T *__restrict__ ta
         }
         v = (T)d;
       }
-      Delta[((size_t)(m0 + m) * nk + q) * nl + (l - lmin)] = v;
+      Delta[((size_t)(m0 + m) * nk + q) * nl + orow] = v;
     }
   }
 }
@@ -143,7 +144,7 @@ static int launch_plain_t(const gcamb_grid *g, const Table &t, const T *S, int M
   if (XP >= 0 && emode_x_lo(g, &x_lo))
     return fail(GCAMB_EINVAL, "los_transfer: eps_cut too large for the l = 2 limit of the polarisation kernels");
   los_plain_kernel<T, MC, XP, E><<<grid, 256, smem, st>>>(static_cast<const T *>(t.d_data), t.d_nkb, t.d_off,
-                                                          g->nk, g->nlt, g->lmin, g->lmax, g->ntau, S, M, Delta,
+                                                          g->nk, g->nlt, g->nl, g->d_lrow, g->ntau, S, M, Delta,
                                                           g->d_k, g->d_tau, g->tau0, g->d_wtau, x_lo);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "los_transfer: launch");
@@ -265,6 +266,8 @@ __global__ void __launch_bounds__(256) tensor_combine_kernel(T *__restrict__ DE,
 
 int launch_los_tensor(const gcamb_grid *g, const void *ST, const void *SP, int M, int mode, void *DT, void *DE,
                       void *DB, cudaStream_t st) {
+  if (g->lsampled)
+    return fail(GCAMB_EUNSUPPORTED, "los_transfer_tensor: the kernels take row l-1: needs a grid of every multipole");
   if (g->lmin >= 2 && g->lmax == g->lmin)
     return fail(GCAMB_EINVAL, "los_transfer_tensor: needs lmax > lmin when lmin >= 2 (the kernels take j_(l-1))");
   double x_lo = 1e-12;

@@ -924,24 +924,26 @@ __global__ void __launch_bounds__(256) weights_kernel(const double *__restrict__
   wq[row] = w;
 }
 
-// C[m][l] = sum over the tile's items (fixed order) of the FP32 chunk sums, in
-// FP64; zero above the source's own l_max.
+// C[m][row] = sum over the tile's items (fixed order) of the FP32 chunk sums,
+// in FP64; zero above the source's own l_max.  row: output index, whose
+// multipole is lrow[row].
 __global__ void __launch_bounds__(128) reduce_kernel(const float *__restrict__ partial, const int *__restrict__ tile_ptr,
                                                      const int *__restrict__ tile_items, int NT, int n_mt, int M,
-                                                     int lmin, int lmax, const int *__restrict__ perm,
-                                                     const int *__restrict__ lmax_m, double *__restrict__ Cl) {
+                                                     int nl, const int *__restrict__ lrow,
+                                                     const int *__restrict__ perm, const int *__restrict__ lmax_m,
+                                                     double *__restrict__ Cl) {
   const int r = threadIdx.x;
   const int ml = blockIdx.x;       // source within the tile
   const int tile = blockIdx.y;     // lt * n_mt + mt
   const int lt = tile / n_mt, mt = tile - lt * n_mt;
   const int m = mt * NT + ml;
-  const int l = lmin + lt * kTileL + r;
-  if (m >= M || l > lmax) return;
+  const int row = lt * kTileL + r;
+  if (m >= M || row >= nl) return;
   double acc = 0.0;
-  if (l <= lmax_m[m])
+  if (lrow[row] <= lmax_m[m])
     for (int e = tile_ptr[tile]; e < tile_ptr[tile + 1]; ++e)
       acc += (double)partial[((size_t)tile_items[e] * NT + ml) * 128 + r];
-  Cl[(size_t)perm[m] * (lmax - lmin + 1) + (l - lmin)] = acc;
+  Cl[(size_t)perm[m] * nl + row] = acc;
 }
 
 // 1/x^2 of every node, x = k (tau0 - tau_i), in FP32 for the converters:
@@ -999,15 +1001,17 @@ __global__ void __launch_bounds__(256) te_weights_kernel(const double *__restric
 __global__ void __launch_bounds__(128) reduce_te_kernel(const float *__restrict__ partial,
                                                         const int *__restrict__ tile_ptr,
                                                         const int *__restrict__ tile_items, int H, int n_mt, int M,
-                                                        int lmin, int lmax, double *__restrict__ ClTT,
-                                                        double *__restrict__ ClEE, double *__restrict__ ClTE) {
+                                                        int nl, const int *__restrict__ lrow,
+                                                        double *__restrict__ ClTT, double *__restrict__ ClEE,
+                                                        double *__restrict__ ClTE) {
   const int r = threadIdx.x;
   const int ml = blockIdx.x;
   const int tile = blockIdx.y;
   const int lt = tile / n_mt, mt = tile - lt * n_mt;
   const int m = mt * H + ml;
-  const int l = lmin + lt * kTileL + r;
-  if (m >= M || l > lmax) return;
+  const int row = lt * kTileL + r;
+  if (m >= M || row >= nl) return;
+  const int l = lrow[row];
   double tt = 0.0, ee = 0.0, te = 0.0;
   for (int e = tile_ptr[tile]; e < tile_ptr[tile + 1]; ++e) {
     const float *pp = partial + (size_t)tile_items[e] * 3 * H * 128 + (size_t)ml * 128 + r;
@@ -1016,7 +1020,7 @@ __global__ void __launch_bounds__(128) reduce_te_kernel(const float *__restrict_
     te += (double)pp[(size_t)2 * H * 128];
   }
   const double c2 = l >= 2 ? (double)(l + 2) * (l + 1) * l * (l - 1) : 0.0;
-  const size_t o = (size_t)m * (lmax - lmin + 1) + (l - lmin);
+  const size_t o = (size_t)m * nl + row;
   ClTT[o] = tt;
   ClEE[o] = c2 * ee;
   ClTE[o] = sqrt(c2) * te;
@@ -1160,7 +1164,7 @@ void plan_build(const gcamb_grid *g, int M, int mode, int nt, const int *lmax_c,
   double total = 0.0;
   for (int lt = 0; lt < g->nlt; ++lt)
     for (int mt = 0; mt < pl.n_mt; ++mt) {
-      if (tile_lm[mt] < g->lmin + lt * kTileL) continue;
+      if (tile_lm[mt] < g->lrow[(size_t)lt * kTileL]) continue;
       for (int q = 0; q < tile_nk[mt]; ++q) {
         const int nb = t.nkb[(size_t)q * g->nlt + lt];
         if (nb) total += nb + 0.5;
@@ -1172,7 +1176,7 @@ void plan_build(const gcamb_grid *g, int M, int mode, int nt, const int *lmax_c,
   pl.cost.clear();
   for (int lt = 0; lt < g->nlt; ++lt)
     for (int mt = 0; mt < pl.n_mt; ++mt) {
-      if (tile_lm[mt] < g->lmin + lt * kTileL) continue;
+      if (tile_lm[mt] < g->lrow[(size_t)lt * kTileL]) continue;
       // an item spans at most kKChunkMax k and starts and ends at a k with
       // stored blocks
       int qb = -1, qlast = -1;
@@ -1369,8 +1373,8 @@ int launch_tc(const gcamb_grid *g, const TcPlan &pl, const float *S, const doubl
   }
   dim3 rgrid(NT, pl.ntile);
   ProfScope prof(GCAMB_K_REDUCE, st);
-  reduce_kernel<<<rgrid, 128, 0, st>>>(part, B + pl.o_tile_ptr, B + pl.o_tile_items, NT, pl.n_mt, pl.M, g->lmin,
-                                       g->lmax, perm, lmm, Cl);
+  reduce_kernel<<<rgrid, 128, 0, st>>>(part, B + pl.o_tile_ptr, B + pl.o_tile_items, NT, pl.n_mt, pl.M, g->nl,
+                                       g->d_lrow, perm, lmm, Cl);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "los_cl: launch");
   return GCAMB_OK;
@@ -1468,7 +1472,10 @@ int launch_tc_te(const gcamb_grid *g, const TcPlan &pl, const float *ST, const f
   }
   if (pl.nitems > 0) {
     int *ctr = reinterpret_cast<int *>(ws + pl.off_ctr);
-    const int r2 = (g->lmin <= 2 && g->lmax >= 2) ? 2 - g->lmin : -1;
+    // the row of l = 2 if the first l-tile holds it (TMEM lane of the epilogue)
+    const int r2 = (g->lmin <= 2 && g->lmax >= 2 && g->rowof[2 - g->lmin] >= 0 && g->rowof[2 - g->lmin] < kTileL)
+                       ? g->rowof[2 - g->lmin]
+                       : -1;
     TcParams prm{static_cast<const char *>(t.d_data), t.d_off, t.d_nkb, nullptr, wp, tail, ix2, r2,
                  pl.items(B), ctr, pl.nitems, part, device_error_flag(), g->nlt, pl.n_mt, pl.nkbs, pl.mpad};
     if (!prm.err) return fail(GCAMB_ECUDA, "los_cl_te: error flag allocation");
@@ -1476,8 +1483,8 @@ int launch_tc_te(const gcamb_grid *g, const TcPlan &pl, const float *ST, const f
   }
   dim3 rgrid(H, pl.ntile);
   ProfScope prof(GCAMB_K_REDUCE, st);
-  reduce_te_kernel<<<rgrid, 128, 0, st>>>(part, B + pl.o_tile_ptr, B + pl.o_tile_items, H, pl.n_mt, pl.M, g->lmin,
-                                          g->lmax, ClTT, ClEE, ClTE);
+  reduce_te_kernel<<<rgrid, 128, 0, st>>>(part, B + pl.o_tile_ptr, B + pl.o_tile_items, H, pl.n_mt, pl.M, g->nl,
+                                          g->d_lrow, ClTT, ClEE, ClTE);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "los_cl_te: launch");
   return GCAMB_OK;
@@ -1707,6 +1714,7 @@ int gcamb_plan_create(gcamb_grid *g, int M, const int *lmax_m, const int *nk_m, 
   uint64_t h = 1469598103934665603ull;
   h = fnv1a(h, g->k.data(), g->k.size() * sizeof(double));
   h = fnv1a(h, g->tau.data(), g->tau.size() * sizeof(double));
+  h = fnv1a(h, g->lrow.data(), g->lrow.size() * sizeof(int));
   if (lmax_m) {
     h = fnv1a(h, lmax_m, M * sizeof(int));
     h = fnv1a(h, nk_m, M * sizeof(int));

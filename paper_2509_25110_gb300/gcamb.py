@@ -22,7 +22,7 @@ F64, F32 = 0, 1
 MODE_NAMES = {PLAIN64: "plain64", PLAIN32: "plain32", BF16X3: "bf16x3", TF32X3: "tf32x3", F16X3: "f16x3"}
 INFO_N = 8
 K_TABLE, K_LOS_PLAIN, K_CL, K_SPLIT, K_WEIGHTS, K_TC, K_REDUCE, K_INTERP = range(8)
-K_NAMES = ("bessel_table", "los_plain", "cl", "split_sources", "weights", "los_cl_tc", "reduce", "interp_sources")
+K_NAMES = ("bessel_table", "los_plain", "cl", "split_sources", "weights", "los_cl_tc", "reduce", "interp")
 
 _vp = ctypes.c_void_p
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -60,6 +60,13 @@ def lib():
     L.gcamb_cl_cross.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp]
     L.gcamb_los_cl_workspace.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
     L.gcamb_los_cl.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_size_t, _vp]
+    L.gcamb_grid_create_lsampled.argtypes = [_dp, ctypes.c_int, _dp, ctypes.c_int, ctypes.c_double,
+                                             ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_double,
+                                             ctypes.POINTER(_vp)]
+    L.gcamb_l_sampling.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_int),
+                                   ctypes.POINTER(ctypes.c_int)]
+    L.gcamb_cl_interp_workspace.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
+    L.gcamb_cl_interp.argtypes = [_vp, _vp, ctypes.c_int, _vp, _vp, ctypes.c_size_t, _vp]
     L.gcamb_interp_sources_workspace.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
     L.gcamb_interp_sources.argtypes = [_vp, _vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp,
                                        ctypes.c_size_t, _vp]
@@ -136,13 +143,15 @@ def last_error() -> str:
 class Grid:
     """Owning wrapper of a gcamb_grid handle."""
 
-    def __init__(self, handle, k, tau, tau0, lmin, lmax):
+    def __init__(self, handle, k, tau, tau0, lmin, lmax, l=None):
         self.handle = handle
         self.k = k
         self.tau = tau
         self.tau0 = tau0
         self.lmin = lmin
         self.lmax = lmax
+        # multipole of each output row: every l, or a sampled list
+        self.l = np.arange(lmin, lmax + 1) if l is None else np.asarray(l, dtype=np.int64)
 
     @property
     def nk(self):
@@ -154,7 +163,7 @@ class Grid:
 
     @property
     def nl(self):
-        return self.lmax - self.lmin + 1
+        return self.l.size
 
     def close(self):
         if self.handle is not None:
@@ -174,6 +183,45 @@ def grid_create(k, tau, tau0, lmin, lmax, eps_cut=0.0) -> Grid:
     _check(lib().gcamb_grid_create(k.ctypes.data_as(_dp), k.size, tau.ctypes.data_as(_dp), tau.size, float(tau0),
                                    int(lmin), int(lmax), float(eps_cut), ctypes.byref(h)))
     return Grid(h, k.copy(), tau.copy(), float(tau0), int(lmin), int(lmax))
+
+
+def grid_create_lsampled(k, tau, tau0, lval, eps_cut=0.0) -> Grid:
+    """A grid whose rows are the listed multipoles lval (strictly increasing)."""
+    k = np.ascontiguousarray(k, dtype=np.float64)
+    tau = np.ascontiguousarray(tau, dtype=np.float64)
+    lv = np.ascontiguousarray(lval, dtype=np.int32)
+    h = _vp()
+    _check(lib().gcamb_grid_create_lsampled(k.ctypes.data_as(_dp), k.size, tau.ctypes.data_as(_dp), tau.size,
+                                            float(tau0), lv.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), lv.size,
+                                            float(eps_cut), ctypes.byref(h)))
+    return Grid(h, k.copy(), tau.copy(), float(tau0), int(lv[0]), int(lv[-1]), l=lv.astype(np.int64))
+
+
+def l_sampling(lmin, lmax, boost) -> np.ndarray:
+    """The sampled multipoles of gcamb_l_sampling (boost >= 50: every l)."""
+    n = ctypes.c_int()
+    _check(lib().gcamb_l_sampling(int(lmin), int(lmax), float(boost), None, ctypes.byref(n)))
+    out = np.empty(n.value, dtype=np.int32)
+    _check(lib().gcamb_l_sampling(int(lmin), int(lmax), float(boost), out.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                  ctypes.byref(n)))
+    return out
+
+
+def cl_interp(g: Grid, Cl_s, Cl=None, ws=None, stream=None):
+    """C_l[M][lmax-lmin+1] on every multipole from Cl_s[M][nl] on the grid's
+    sampled rows (natural cubic spline in l of l (l+1) C_l)."""
+    import torch
+    M = Cl_s.shape[0]
+    if Cl is None:
+        Cl = torch.empty((M, g.lmax - g.lmin + 1), dtype=torch.float64, device=Cl_s.device)
+    if ws is None:
+        b = ctypes.c_size_t()
+        _check(lib().gcamb_cl_interp_workspace(g.handle, M, ctypes.byref(b)))
+        ws = torch.empty(b.value, dtype=torch.uint8, device=Cl_s.device)
+    _check(lib().gcamb_cl_interp(g.handle, _dev(Cl_s, torch.float64, (M, g.nl), "Cl_s"), M,
+                                 _dev(Cl, torch.float64, (M, g.lmax - g.lmin + 1), "Cl"),
+                                 _dev(ws, torch.uint8, name="ws"), ws.numel(), _stream(stream)))
+    return Cl
 
 
 def grid_destroy(g: Grid):

@@ -179,6 +179,9 @@ def workload(name: str, M: Optional[int] = None) -> Workload:
     uneven_lmax6000    : 1000 models on a 3000-point linear k grid, 1000 tau uniform
     features_lmax2500  : 256 models, l 2..2500, 8000 k log 1e-4..0.3 (sources made on
                          1000 k and interpolated), 1000 tau uniform, log-oscillating P(k)
+    lsampled_lmax2500  : 256 models, l 2..2500, 400 k log 1e-4..0.01 then 1800 k linear to
+                         0.3 (dk = 1.6e-4 < 2 pi / tau0: the projection's oscillations in k
+                         are resolved, so C_l is smooth in l), 1000 tau uniform
     tensor_lmax1500    : 1 model, l 2..1500, 1000 k log 1e-4..3000/tau0, 1000 tau uniform
                          (tensor modes: l_max and k tau0 <= 3000 as in the paper's runs)
     """
@@ -191,6 +194,9 @@ def workload(name: str, M: Optional[int] = None) -> Workload:
         wl = Workload(name, log_grid(1e-4, 0.3, 2000), uniform_grid(200.0, 14000.0, 1000), tau0, 2, 2500, 256)
     elif name == "features_lmax2500":
         wl = Workload(name, log_grid(1e-4, 0.3, 8000), uniform_grid(200.0, 14000.0, 1000), tau0, 2, 2500, 256)
+    elif name == "lsampled_lmax2500":
+        k = np.concatenate([np.geomspace(1e-4, 0.01, 401)[:-1], np.linspace(0.01, 0.3, 1800)])
+        wl = Workload(name, k, uniform_grid(200.0, 14000.0, 1000), tau0, 2, 2500, 256)
     elif name == "tensor_lmax1500":
         wl = Workload(name, log_grid(1e-4, 3000.0 / tau0, 1000), uniform_grid(200.0, 14000.0, 1000), tau0, 2, 1500, 1)
     elif name == "uneven_lmax6000":
