@@ -61,6 +61,10 @@ def _load():
     lib.orc_los_e.restype = ctypes.c_int
     lib.orc_cl_cross.argtypes = [ctypes.c_int, _dp, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp]
     lib.orc_cl_cross.restype = ctypes.c_int
+    lib.orc_hyper_bessel_many.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_int, ctypes.c_int, _dp]
+    lib.orc_los_curved.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _dp, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, ctypes.c_int]
+    lib.orc_los_curved.restype = ctypes.c_int
     lib.orc_tensor_kernels_many.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _dp, _dp, _dp]
     lib.orc_los_tensor.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _dp, ctypes.c_double, ctypes.c_int,
                                    ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp, ctypes.c_int]
@@ -182,6 +186,34 @@ def los_e(k, tau, tau0, lmin, lmax, SP, wtau=None, nthreads=0) -> np.ndarray:
     d = np.empty((M, nk, lmax - lmin + 1))
     rc = _load().orc_los_e(nk, _ptr(k), ntau, _ptr(tau), float(tau0), int(lmin), int(lmax), M, _ptr(SP),
                            _ptr(_f64(wtau)) if wtau is not None else None, _ptr(d), int(nthreads))
+    if rc != 0:
+        raise ValueError("oracle rejected the arguments")
+    return d[0] if single else d
+
+
+def hyper_bessel(beta, chi, lmax, closed) -> np.ndarray:
+    """Phi^beta_l(chi), l = 0..lmax, for arrays beta, chi of one shape n ->
+    [n][lmax + 1]; closed = True for K > 0 (integer beta)."""
+    b = _f64(np.broadcast_to(beta, np.broadcast(beta, chi).shape)).ravel()
+    c = _f64(np.broadcast_to(chi, b.shape)).ravel()
+    out = np.empty((b.size, lmax + 1))
+    _load().orc_hyper_bessel_many(b.size, _ptr(b), _ptr(c), int(lmax), int(bool(closed)), _ptr(out))
+    return out
+
+
+def los_curved(q, tau, tau0, K, lmin, lmax, S, wtau=None, nthreads=0) -> np.ndarray:
+    """Dense FP64 curved-space transfer functions [M][nq][nl] (Eq. 2 with
+    phi_l the hyperspherical Bessel function of curvature K != 0)."""
+    q = _f64(q)
+    tau = _f64(tau)
+    S = _f64(S)
+    single = S.ndim == 2
+    if single:
+        S = S[None]
+    M, nq, ntau = S.shape
+    d = np.empty((M, nq, lmax - lmin + 1))
+    rc = _load().orc_los_curved(nq, _ptr(q), ntau, _ptr(tau), float(tau0), float(K), int(lmin), int(lmax), M,
+                                _ptr(S), _ptr(_f64(wtau)) if wtau is not None else None, _ptr(d), int(nthreads))
     if rc != 0:
         raise ValueError("oracle rejected the arguments")
     return d[0] if single else d

@@ -36,6 +36,21 @@
  * with their limits at x = 0: e_2 = 4/5, all others 0.  Each projection is
  * the dense sum of Eq. (2) with the tensor sources S_T^t, S_P^t.
  *
+ * Non-flat space (the curved-space kernels the paper names as next, Sec. 2.1
+ * and 5): phi_l becomes the hyperspherical Bessel function Phi^beta_l(chi)
+ * of curvature K, beta = q / sqrt|K|, chi = sqrt|K| (tau0 - tau), with
+ * (open, K < 0: sh = sinh, ct = coth, s_l = sqrt(beta^2 + l^2);
+ *  closed, K > 0: sh = sin, ct = cot, s_l = sqrt(beta^2 - l^2), beta an
+ *  integer, Phi_l = 0 for l >= beta)
+ *       Phi_0 = sin(beta chi) / (beta sh(chi)),
+ *       Phi_1 = Phi_0 (ct(chi) - beta cot(beta chi)) / s_1
+ *             = (sin(beta chi) ct(chi) - beta cos(beta chi)) / (beta sh(chi) s_1),
+ *       s_(l+1) Phi_(l+1) = (2l+1) ct(chi) Phi_l - s_l Phi_(l-1),
+ * which tends to j_l(q r) as K -> 0.  This oracle runs the recurrence
+ * downwards from far above the order range and the turning point (Miller;
+ * in closed space from l = beta - 1 with Phi_beta = 0, which is exact) and
+ * normalises to the larger of the closed forms of Phi_0, Phi_1.
+ *
  * The paper fixes neither the Bessel kernel's evaluation nor the quadrature
  * (it names phi_l only as "related to spherical Bessel functions", Sec. 2.1,
  * and evaluates it inside the line-of-sight loop, Sec. 3.2 / Algorithm 1).
@@ -338,6 +353,98 @@ int orc_los_e(int nk, const double *k, int ntau, const double *tau, double tau0,
             }
         }
         free(el);
+    }
+    free(wtau);
+    return 0;
+}
+
+/* Hyperspherical Bessel Phi^beta_l(chi), l = 0..lmax, open (closed = 0) or
+ * closed (closed = 1) space; see the header. */
+void orc_hyper_bessel(int lmax, double beta, double chi, int closed, double *out)
+{
+    for (int l = 0; l <= lmax; ++l) out[l] = 0.0;
+    if (chi == 0.0) {
+        out[0] = 1.0;
+        return;
+    }
+    const double sh = closed ? sin(chi) : sinh(chi);
+    const double ct = closed ? cos(chi) / sin(chi) : cosh(chi) / sinh(chi);
+    const double p0 = sin(beta * chi) / (beta * sh);
+    const double s1 = closed ? sqrt(beta * beta - 1.0) : sqrt(beta * beta + 1.0);
+    const double p1 = (sin(beta * chi) * ct - beta * cos(beta * chi)) / (beta * sh * s1);
+    /* start far above the order range and the classical turning order
+     * beta |sh(chi)|; above it the decaying solution falls by about
+     * tanh(chi/2) per order in open space (the recurrence's roots tend to
+     * (cosh chi -+ 1)/sinh chi), so the start also clears
+     * 46 / -ln tanh(chi/2) orders (a factor e^-46); in closed space at most
+     * l = beta - 1, where Phi_beta = 0 makes the start exact */
+    const double turn = beta * fabs(sh);
+    const double hi = lmax > turn ? (double)lmax : turn;
+    double extra = 0.0;
+    if (!closed) extra = fmin(46.0 / -log(tanh(0.5 * chi)), 1e6);
+    int top = (int)(hi + 60.0 + 8.0 * sqrt(hi) + extra) + 10;
+    if (closed && top > (int)llround(beta) - 1) top = (int)llround(beta) - 1;
+    if (top < 1) {
+        if (lmax >= 0) out[0] = p0;
+        return;
+    }
+    /* downward: s_l Phi_(l-1) = (2l+1) ct Phi_l - s_(l+1) Phi_(l+1) */
+    int n = top + 1;
+    double *f = (double *)malloc(sizeof(double) * (size_t)(n + 1));
+    f[n] = 0.0;
+    f[top] = 1e-300;
+    for (int l = top; l >= 1; --l) {
+        const double sl = closed ? sqrt(beta * beta - (double)l * l) : sqrt(beta * beta + (double)l * l);
+        const double sl1 = closed ? sqrt(fmax(beta * beta - (double)(l + 1) * (l + 1), 0.0))
+                                  : sqrt(beta * beta + (double)(l + 1) * (l + 1));
+        f[l - 1] = ((2.0 * l + 1.0) * ct * f[l] - sl1 * f[l + 1]) / sl;
+        if (fabs(f[l - 1]) > 1e250) {  /* rescale what is still needed: the outputs and f[l], f[l+1] */
+            const int hi2 = (l + 1 > lmax ? l + 1 : lmax);
+            for (int j = l - 1; j <= hi2 && j <= n; ++j) f[j] *= 1e-250;
+        }
+    }
+    const double norm = fabs(p0) >= fabs(p1) ? p0 / f[0] : p1 / f[1];
+    for (int l = 0; l <= lmax && l <= top; ++l) out[l] = f[l] * norm;
+    free(f);
+}
+
+void orc_hyper_bessel_many(int n, const double *beta, const double *chi, int lmax, int closed, double *out)
+{
+    for (int i = 0; i < n; ++i) orc_hyper_bessel(lmax, beta[i], chi[i], closed, out + (size_t)i * (lmax + 1));
+}
+
+/* Curved-space transfer functions Delta[M][q][l - lmin] = sum_i w_i S[m][q][i]
+ * Phi^(q/sqrt|K|)_l(sqrt|K| (tau0 - tau_i)), K != 0; dense over the nodes. */
+int orc_los_curved(int nq, const double *q, int ntau, const double *tau, double tau0, double K,
+                   int lmin, int lmax, int M, const double *S, const double *wtau_in, double *Delta, int nthreads)
+{
+    if (nq < 0 || ntau < 0 || lmin < 0 || lmax < lmin || M < 0 || !Delta || K == 0.0) return -1;
+    const int nl = lmax - lmin + 1;
+    const int closed = K > 0.0;
+    const double rk = sqrt(fabs(K));
+    double *wtau = (double *)malloc(sizeof(double) * (size_t)(ntau > 0 ? ntau : 1));
+    if (wtau_in) memcpy(wtau, wtau_in, sizeof(double) * (size_t)ntau);
+    else orc_trapz_weights(ntau, tau, wtau);
+    int nt = 1;
+#ifdef _OPENMP
+    nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#endif
+    #pragma omp parallel num_threads(nt)
+    {
+        double *ph = (double *)malloc(sizeof(double) * (size_t)(lmax + 1));
+        #pragma omp for schedule(dynamic)
+        for (int j = 0; j < nq; ++j) {
+            for (int m = 0; m < M; ++m) memset(Delta + ((size_t)m * nq + j) * nl, 0, sizeof(double) * (size_t)nl);
+            for (int i = 0; i < ntau; ++i) {
+                orc_hyper_bessel(lmax, q[j] / rk, rk * (tau0 - tau[i]), closed, ph);
+                for (int m = 0; m < M; ++m) {
+                    const double ws = wtau[i] * S[((size_t)m * nq + j) * ntau + i];
+                    double *d = Delta + ((size_t)m * nq + j) * nl;
+                    for (int l = lmin; l <= lmax; ++l) d[l - lmin] += ws * ph[l];
+                }
+            }
+        }
+        free(ph);
     }
     free(wtau);
     return 0;
