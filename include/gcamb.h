@@ -188,6 +188,24 @@ int gcamb_los_transfer_tensor(const gcamb_grid *g, const void *ST, const void *S
                               void *DeltaE, void *DeltaB, void *stream);
 
 /*
+ * Curved space (the non-flat integration the paper names as its next step,
+ * Sec. 2.1, 5): as gcamb_grid_create, with curvature K [Mpc^-2] != 0 and
+ * the wavenumbers q[nq] of the curved-space modes; the kernel phi_l of
+ * Eq. (2) becomes the hyperspherical Bessel function Phi^beta_l(chi),
+ * beta = q / sqrt|K|, chi = sqrt|K| (tau0 - tau) (open space for K < 0,
+ * closed for K > 0, where every beta must be an integer >= 3 and Phi_l = 0
+ * for l >= beta).  Eq. (1)'s measure is unchanged (trapezoid in ln q).
+ * gcamb_bessel_table evaluates Phi by its three-term recurrence (forward
+ * below the turning order beta |sh chi|, Miller's downward recurrence above)
+ * and, on the first build, finds each (q, l-tile) tau-prefix on the device
+ * from where some |Phi_l| of the tile reaches eps_cut.  The temperature
+ * paths (plain, batched, plans, emulator) take such grids; the E-mode and
+ * tensor kernels are flat-space only (GCAMB_EUNSUPPORTED).
+ */
+int gcamb_grid_create_curved(const double *q, int nq, const double *tau, int ntau, double tau0, int lmin, int lmax,
+                             double K, double eps_cut, gcamb_grid **out);
+
+/*
  * Sampled multipoles (the output l-sampling of the paper's accuracy settings,
  * Sec. 3.1, Table 1: l_sample_boost = 50 computes every l).
  *

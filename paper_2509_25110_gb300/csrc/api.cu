@@ -190,7 +190,7 @@ const char *gcamb_version(void) { return "gcamb-gb300 0.1 (sm_103a)"; }
 const char *gcamb_last_error(void) { return t_err.c_str(); }
 
 static int grid_build(const double *k, int nk, const double *tau, int ntau, double tau0, std::vector<int> lrow,
-                      bool sampled, double eps_cut, gcamb_grid **out);
+                      bool sampled, double eps_cut, gcamb_grid **out, double K = 0.0);
 
 int gcamb_grid_create(const double *k, int nk, const double *tau, int ntau, double tau0, int lmin, int lmax,
                       double eps_cut, gcamb_grid **out) {
@@ -214,6 +214,26 @@ int gcamb_grid_create_lsampled(const double *k, int nk, const double *tau, int n
   return grid_build(k, nk, tau, ntau, tau0, std::vector<int>(lval, lval + nl), true, eps_cut, out);
 }
 
+int gcamb_grid_create_curved(const double *q, int nq, const double *tau, int ntau, double tau0, int lmin, int lmax,
+                             double K, double eps_cut, gcamb_grid **out) {
+  if (!out) return fail(GCAMB_EINVAL, "grid_create_curved: out is NULL");
+  *out = nullptr;
+  if (!(K != 0.0) || !std::isfinite(K)) return fail(GCAMB_EINVAL, "grid_create_curved: K must be finite and nonzero");
+  if (lmin < 0 || lmax < lmin || lmax > kMaxL)
+    return fail(GCAMB_EINVAL, "grid_create_curved: need 0 <= lmin <= lmax <= 20000");
+  if (K > 0.0 && q) {
+    const double rk = std::sqrt(K);
+    for (int j = 0; j < nq; ++j) {
+      const double b = q[j] / rk;
+      if (!(std::fabs(b - std::nearbyint(b)) <= 1e-6 * std::max(1.0, b)) || b < 3.0)
+        return fail(GCAMB_EINVAL, "grid_create_curved: closed space needs integer beta = q / sqrt(K) >= 3");
+    }
+  }
+  std::vector<int> lrow(lmax - lmin + 1);
+  for (int r = 0; r <= lmax - lmin; ++r) lrow[r] = lmin + r;
+  return grid_build(q, nq, tau, ntau, tau0, std::move(lrow), false, eps_cut, out, K);
+}
+
 int gcamb_l_sampling(int lmin, int lmax, double boost, int *lval, int *n) {
   if (!n) return fail(GCAMB_EINVAL, "l_sampling: n is NULL");
   if (lmin < 0 || lmax < lmin || lmax > kMaxL || !(boost > 0.0))
@@ -234,7 +254,7 @@ int gcamb_l_sampling(int lmin, int lmax, double boost, int *lval, int *n) {
 }
 
 static int grid_build(const double *k, int nk, const double *tau, int ntau, double tau0, std::vector<int> lrow,
-                      bool sampled, double eps_cut, gcamb_grid **out) {
+                      bool sampled, double eps_cut, gcamb_grid **out, double K) {
   const int lmin = lrow.front(), lmax = lrow.back();
   if (!k || !tau) return fail(GCAMB_EINVAL, "grid_create: k or tau is NULL");
   if (nk < 1 || ntau < 1) return fail(GCAMB_EINVAL, "grid_create: nk and ntau must be >= 1");
@@ -265,6 +285,12 @@ static int grid_build(const double *k, int nk, const double *tau, int ntau, doub
   g->rowof.assign((size_t)(lmax - lmin + 1), -1);
   for (int r = 0; r < g->nl; ++r) g->rowof[lrow[r] - lmin] = r;
   g->lrow = std::move(lrow);
+  if (K != 0.0) {
+    g->curved = K < 0.0 ? 1 : 2;
+    g->K = K;
+    g->rk = std::sqrt(std::fabs(K));
+    g->ext_ready = false;  // the tau-prefixes come from the first table build
+  }
   g->tau0 = tau0;
   g->eps_cut = eps_cut;
   g->k.assign(k, k + nk);
@@ -293,7 +319,8 @@ static int grid_build(const double *k, int nk, const double *tau, int ntau, doub
   for (int lt = 0; lt < g->nlt; ++lt) {
     const int l0 = g->lrow[(size_t)lt * kTileL];  // the tile's lowest multipole
     const double xe = watson_threshold(l0, logeps);
-    for (int q = 0; q < nk; ++q) g->ext[(size_t)q * g->nlt + lt] = (l0 == 0) ? ntau : prefix(q, xe);
+    for (int q = 0; q < nk; ++q)
+      g->ext[(size_t)q * g->nlt + lt] = (l0 == 0 || g->curved) ? ntau : prefix(q, xe);
   }
   // Active (l, k, tau) entries with the per-l prefix.
   {
@@ -415,6 +442,7 @@ int gcamb_los_transfer(const gcamb_grid *g, const void *S, int M, int mode, void
 
 int gcamb_los_transfer_e(const gcamb_grid *g, const void *SP, int M, int mode, void *DeltaE, void *stream) {
   if (!g) return fail(GCAMB_EINVAL, "los_transfer_e: NULL grid");
+  if (g->curved) return fail(GCAMB_EUNSUPPORTED, "los_transfer_e: the E-mode kernel is flat-space only");
   if (mode != GCAMB_PLAIN64 && mode != GCAMB_PLAIN32)
     return fail(GCAMB_EINVAL, "los_transfer_e: mode must be GCAMB_PLAIN64 or GCAMB_PLAIN32");
   if (M < 0) return fail(GCAMB_EINVAL, "los_transfer_e: M < 0");
@@ -427,6 +455,7 @@ int gcamb_los_transfer_e(const gcamb_grid *g, const void *SP, int M, int mode, v
 int gcamb_los_transfer_tensor(const gcamb_grid *g, const void *ST, const void *SP, int M, int mode, void *DeltaT,
                               void *DeltaE, void *DeltaB, void *stream) {
   if (!g) return fail(GCAMB_EINVAL, "los_transfer_tensor: NULL grid");
+  if (g->curved) return fail(GCAMB_EUNSUPPORTED, "los_transfer_tensor: the tensor kernels are flat-space only");
   if (mode != GCAMB_PLAIN64 && mode != GCAMB_PLAIN32)
     return fail(GCAMB_EINVAL, "los_transfer_tensor: mode must be GCAMB_PLAIN64 or GCAMB_PLAIN32");
   if (M < 0) return fail(GCAMB_EINVAL, "los_transfer_tensor: M < 0");
@@ -488,6 +517,7 @@ int gcamb_los_cl(const gcamb_grid *g, const float *S, const double *Pk, int M, i
 
 static int te_check(const gcamb_grid *g, int M, int mode, const char *who) {
   if (!g) return fail(GCAMB_EINVAL, std::string(who) + ": NULL grid");
+  if (g->curved) return fail(GCAMB_EUNSUPPORTED, std::string(who) + ": the E-mode kernel is flat-space only");
   if (mode != GCAMB_BF16X3) return fail(GCAMB_EINVAL, std::string(who) + ": mode must be GCAMB_BF16X3");
   if (M < 0) return fail(GCAMB_EINVAL, std::string(who) + ": M < 0");
   if (!g->tab[mode].built) return fail(GCAMB_ESTATE, std::string(who) + ": build the table for this mode first");

@@ -16,6 +16,7 @@
 
 #include <cmath>
 #include <mutex>
+#include <vector>
 
 #include "internal.h"
 
@@ -104,6 +105,117 @@ __device__ __forceinline__ void bessel_orders(double x, int lmin, int ltop, cons
   }
 }
 
+// Calls put(l, Phi^beta_l(chi)) for l in [lmin, ltop]: the hyperspherical
+// Bessel functions of open (closed = false: sh = sinh, ct = coth,
+// s_l = sqrt(beta^2 + l^2)) or closed space (sh = sin, ct = cot,
+// s_l = sqrt(beta^2 - l^2), integer beta, Phi_l = 0 for l >= beta), with
+//   Phi_0 = sin(beta chi) / (beta sh),
+//   Phi_1 = (sin(beta chi) ct - beta cos(beta chi)) / (beta sh s_1),
+//   s_(l+1) Phi_(l+1) = (2l+1) ct Phi_l - s_l Phi_(l-1).
+// Forward from Phi_0, Phi_1 below the turning order beta |sh| (where the
+// solutions oscillate); above it Miller's downward recurrence, started past
+// max(ltop, turning order) + 60 + 8 sqrt(.) and, in open space, past the
+// tail that falls by tanh(chi/2) per order (46 / -ln tanh(chi/2) orders);
+// in closed space at most at beta - 1 (exact: Phi_beta = 0).  The downward
+// pass rescales by 1e-250 on overflow and counts it; the second pass writes
+// scale * f for the orders within one rescale of the match and 0 above.
+template <class Sink>
+__device__ void hyper_orders(double beta, double chi, bool closed, int lmin, int ltop, Sink &put) {
+  if (ltop < lmin) return;
+  if (chi == 0.0) {
+    if (lmin == 0) put(0, 1.0);
+    return;
+  }
+  double sh, ch;
+  if (closed) {
+    sincos(chi, &sh, &ch);
+  } else {
+    sh = sinh(chi);
+    ch = cosh(chi);
+  }
+  const double ct = ch / sh, b2 = beta * beta, sg = closed ? -1.0 : 1.0;
+  auto sl = [&](int l) {
+    const double v = fma(sg * (double)l, (double)l, b2);
+    return v > 0.0 ? sqrt(v) : 0.0;
+  };
+  const int lcap = closed ? (int)llrint(beta) - 1 : 0x3fffffff;
+  const int lt = min(ltop, lcap);
+  if (lt < lmin) return;
+  double sb, cb;
+  sincos(beta * chi, &sb, &cb);
+  const double p0 = sb / (beta * sh);
+  const double p1 = (sb * ct - beta * cb) / (beta * sh * sl(1));
+  const double turn = beta * fabs(sh);
+  const int ls = (int)fmin(floor(turn), (double)lt);
+  double fa = 0.0, fb = 0.0;  // forward Phi_(ls-1), Phi_ls
+  if (ls >= 1) {
+    double pm = p0, p = p1, sc = sl(1);
+    if (lmin == 0) put(0, p0);
+    if (lmin <= 1) put(1, p1);
+    for (int l = 1; l < ls; ++l) {
+      const double sn = sl(l + 1);
+      const double pn = ((2.0 * l + 1.0) * ct * p - sc * pm) / sn;
+      pm = p;
+      p = pn;
+      sc = sn;
+      if (l + 1 >= lmin) put(l + 1, p);
+    }
+    if (ls >= lt) return;
+    fa = pm;
+    fb = p;
+  }
+  const double hi = fmax((double)lt, turn);
+  double extra = 0.0;
+  if (!closed) {
+    const double th = tanh(0.5 * chi);
+    extra = th < 1.0 ? fmin(46.0 / -log(th), 1e6) : 1e6;
+  }
+  const int L = (int)fmin(hi + 60.0 + 8.0 * sqrt(hi) + extra + 10.0, (double)lcap);
+  const int lend = ls >= 1 ? ls : 1;
+  // pass 1: down to f_(lend-1), counting rescales
+  double fh = 0.0, f = 1.0, s_up = sl(L + 1);
+  int R = 0;
+  for (int l = L; l >= lend; --l) {
+    const double s_l = sl(l);
+    const double fm = ((2.0 * l + 1.0) * ct * f - s_up * fh) / s_l;
+    fh = f;
+    f = fm;
+    s_up = s_l;
+    if (fabs(f) > 1e250) {
+      f *= 1e-250;
+      fh *= 1e-250;
+      ++R;
+    }
+  }
+  double scale;  // fh = f_lend, f = f_(lend-1)
+  if (ls >= 1) scale = fabs(fb) >= fabs(fa) ? fb / fh : fa / f;
+  else scale = fabs(p1) > fabs(p0) ? p1 / fh : p0 / f;
+  const double scale2 = scale * 1e-250;
+  // pass 2: the orders above the match (all of them when ls = 0)
+  const int lbot = ls >= 1 ? ls + 1 : 0;
+  fh = 0.0;
+  f = 1.0;
+  s_up = sl(L + 1);
+  int r = 0;
+  for (int l = L;; --l) {
+    if (l <= lt && l >= lmin) {
+      const int d = R - r;
+      put(l, d == 0 ? scale * f : (d == 1 ? scale2 * f : 0.0));
+    }
+    if (l <= lbot) break;
+    const double s_l = sl(l);
+    const double fm = ((2.0 * l + 1.0) * ct * f - s_up * fh) / s_l;
+    fh = f;
+    f = fm;
+    s_up = s_l;
+    if (fabs(f) > 1e250) {
+      f *= 1e-250;
+      fh *= 1e-250;
+      ++r;
+    }
+  }
+}
+
 __device__ __forceinline__ uint32_t tf32_rna(float v) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
@@ -179,7 +291,8 @@ __global__ void __launch_bounds__(128) bessel_table_kernel(const double *__restr
                                                            const int64_t *__restrict__ off,
                                                            const double *__restrict__ xs, int nxs, int scale_exp,
                                                            const int *__restrict__ lrow,
-                                                           const int *__restrict__ rowof, int nl, void *table) {
+                                                           const int *__restrict__ rowof, int nl, int curved,
+                                                           double rk, void *table) {
   constexpr int KB = (MODE == GCAMB_PLAIN64 || MODE == GCAMB_PLAIN32) ? 64 : 32;
   const int q = blockIdx.y;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -191,10 +304,72 @@ __global__ void __launch_bounds__(128) bessel_table_kernel(const double *__restr
   if (lt_last < 0) return;
   // the highest multipole of the last tile this node is active in
   const int ltop = lrow ? lrow[min((lt_last + 1) * kTileL, nl) - 1] : min(lmin + (lt_last + 1) * kTileL - 1, lmax);
-  const double x = k[q] * (tau0 - tau[i]);
   TableSink<MODE> sink{static_cast<char *>(table), off + (size_t)q * nlt, lmin, kbi, i % KB,
                        ldexp(wtau[i], scale_exp), -1, nullptr, rowof};
-  bessel_orders(x, lmin, ltop, xs, nxs, sink);
+  if (curved)  // hyperspherical: beta = q / sqrt|K|, chi = sqrt|K| (tau0 - tau)
+    hyper_orders(k[q] / rk, rk * (tau0 - tau[i]), curved == 2, lmin, ltop, sink);
+  else
+    bessel_orders(k[q] * (tau0 - tau[i]), lmin, ltop, xs, nxs, sink);
+}
+
+// Activity of one node on a curved grid: the highest l-tile in which some
+// |Phi_l| reaches eps; the node then belongs to the tau-prefix of that tile
+// and of every tile below it.
+struct ActSink {
+  int lmin;
+  const int *rowof;
+  double eps;
+  int ltmax;
+  __device__ __forceinline__ void operator()(int l, double v) {
+    if (fabs(v) >= eps) {
+      const int row = rowof ? rowof[l - lmin] : l - lmin;
+      if (row >= 0) ltmax = max(ltmax, row >> 7);
+    }
+  }
+};
+
+__global__ void __launch_bounds__(128) curved_activity_kernel(const double *__restrict__ k,
+                                                              const double *__restrict__ tau, double tau0, int ntau,
+                                                              int lmin, int lmax, int nlt, double rk, int closed,
+                                                              double eps, const int *__restrict__ rowof, int *ext) {
+  const int q = blockIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ntau) return;
+  ActSink a{lmin, rowof, eps, -1};
+  hyper_orders(k[q] / rk, rk * (tau0 - tau[i]), closed != 0, lmin, lmax, a);
+  for (int t = 0; t <= a.ltmax && t < nlt; ++t) atomicMax(ext + (size_t)q * nlt + t, i + 1);
+}
+
+// The tau-prefixes of a curved grid, from the activity of every node (run
+// once, before the first table is laid out).
+int curved_extents(gcamb_grid *g, cudaStream_t st) {
+  const size_t n = (size_t)g->nk * g->nlt;
+  int *d_ext = nullptr;
+  cudaError_t e = cudaMalloc(&d_ext, n * sizeof(int));
+  if (e != cudaSuccess) return cuda_fail(e, "bessel_table: curved extents");
+  e = cudaMemsetAsync(d_ext, 0, n * sizeof(int), st);
+  if (e == cudaSuccess) {
+    dim3 grid((g->ntau + 127) / 128, g->nk);
+    curved_activity_kernel<<<grid, 128, 0, st>>>(g->d_k, g->d_tau, g->tau0, g->ntau, g->lmin, g->lmax, g->nlt, g->rk,
+                                                 g->curved == 2, g->eps_cut, g->lsampled ? g->d_rowof : nullptr,
+                                                 d_ext);
+    e = cudaGetLastError();
+  }
+  std::vector<int> h(n);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), d_ext, n * sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(d_ext);
+  if (e != cudaSuccess) return cuda_fail(e, "bessel_table: curved extents");
+  int64_t act = 0;
+  for (int q = 0; q < g->nk; ++q)
+    for (int t = 0; t < g->nlt; ++t) {
+      const int v = h[(size_t)q * g->nlt + t];
+      g->ext[(size_t)q * g->nlt + t] = v;
+      act += (int64_t)v * std::min(kTileL, g->nl - t * kTileL);
+    }
+  g->active = act;  // rows of a tile times its prefix (no per-l cut on curved grids)
+  g->ext_ready = true;
+  return GCAMB_OK;
 }
 
 struct DenseSink {
@@ -213,6 +388,9 @@ __global__ void sph_bessel_kernel(const double *__restrict__ x, int n, int lmax,
 int launch_bessel_table(gcamb_grid *g, int mode, cudaStream_t st) {
   Table &t = g->tab[mode];
   const ModeLayout lay = mode_layout(mode);
+  if (g->curved && !g->ext_ready) {
+    if (int rc = curved_extents(g, st)) return rc;
+  }
   if (!t.d_data) {
     t.lay = lay;
     t.nkb.assign((size_t)g->nk * g->nlt, 0);
@@ -258,31 +436,36 @@ int launch_bessel_table(gcamb_grid *g, int mode, cudaStream_t st) {
       bessel_table_kernel<GCAMB_PLAIN64><<<grid, 128, 0, st>>>(g->d_k, g->d_tau, g->d_wtau, g->tau0, g->ntau, g->lmin,
                                                                g->lmax, g->nlt, t.d_nkb, t.d_off, g->d_xstart, g->nxs,
                                                                t.scale_exp, g->lsampled ? g->d_lrow : nullptr,
-                                                               g->lsampled ? g->d_rowof : nullptr, g->nl, t.d_data);
+                                                               g->lsampled ? g->d_rowof : nullptr, g->nl, g->curved, g->rk,
+                                                               t.d_data);
       break;
     case GCAMB_PLAIN32:
       bessel_table_kernel<GCAMB_PLAIN32><<<grid, 128, 0, st>>>(g->d_k, g->d_tau, g->d_wtau, g->tau0, g->ntau, g->lmin,
                                                                g->lmax, g->nlt, t.d_nkb, t.d_off, g->d_xstart, g->nxs,
                                                                t.scale_exp, g->lsampled ? g->d_lrow : nullptr,
-                                                               g->lsampled ? g->d_rowof : nullptr, g->nl, t.d_data);
+                                                               g->lsampled ? g->d_rowof : nullptr, g->nl, g->curved, g->rk,
+                                                               t.d_data);
       break;
     case GCAMB_BF16X3:
       bessel_table_kernel<GCAMB_BF16X3><<<grid, 128, 0, st>>>(g->d_k, g->d_tau, g->d_wtau, g->tau0, g->ntau, g->lmin,
                                                               g->lmax, g->nlt, t.d_nkb, t.d_off, g->d_xstart, g->nxs,
                                                               t.scale_exp, g->lsampled ? g->d_lrow : nullptr,
-                                                               g->lsampled ? g->d_rowof : nullptr, g->nl, t.d_data);
+                                                               g->lsampled ? g->d_rowof : nullptr, g->nl, g->curved, g->rk,
+                                                               t.d_data);
       break;
     case GCAMB_F16X3:
       bessel_table_kernel<GCAMB_F16X3><<<grid, 128, 0, st>>>(g->d_k, g->d_tau, g->d_wtau, g->tau0, g->ntau, g->lmin,
                                                              g->lmax, g->nlt, t.d_nkb, t.d_off, g->d_xstart, g->nxs,
                                                              t.scale_exp, g->lsampled ? g->d_lrow : nullptr,
-                                                               g->lsampled ? g->d_rowof : nullptr, g->nl, t.d_data);
+                                                               g->lsampled ? g->d_rowof : nullptr, g->nl, g->curved, g->rk,
+                                                               t.d_data);
       break;
     case GCAMB_TF32X3:
       bessel_table_kernel<GCAMB_TF32X3><<<grid, 128, 0, st>>>(g->d_k, g->d_tau, g->d_wtau, g->tau0, g->ntau, g->lmin,
                                                               g->lmax, g->nlt, t.d_nkb, t.d_off, g->d_xstart, g->nxs,
                                                               t.scale_exp, g->lsampled ? g->d_lrow : nullptr,
-                                                               g->lsampled ? g->d_rowof : nullptr, g->nl, t.d_data);
+                                                               g->lsampled ? g->d_rowof : nullptr, g->nl, g->curved, g->rk,
+                                                               t.d_data);
       break;
   }
   e = cudaGetLastError();

@@ -63,6 +63,12 @@ struct gcamb_grid {
   std::vector<int> lrow, rowof;
   bool lsampled = false;
   int *d_lrow = nullptr, *d_rowof = nullptr;
+  // curvature: 0 flat (j_l), 1 open (K < 0), 2 closed (K > 0): hyperspherical
+  // Bessel functions with beta = k / rk, chi = rk (tau0 - tau), rk = sqrt|K|;
+  // the tau-prefixes of a curved grid come from a device pass (ext_ready)
+  int curved = 0;
+  double K = 0.0, rk = 0.0;
+  bool ext_ready = true;
   double tau0 = 0.0, eps_cut = 1e-30;
   std::vector<double> k, tau, wtau, wk;
   std::vector<int32_t> ext;       // [nk][nlt] active tau-prefix per (k, l-tile)

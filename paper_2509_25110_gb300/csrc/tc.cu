@@ -1715,6 +1715,7 @@ int gcamb_plan_create(gcamb_grid *g, int M, const int *lmax_m, const int *nk_m, 
   h = fnv1a(h, g->k.data(), g->k.size() * sizeof(double));
   h = fnv1a(h, g->tau.data(), g->tau.size() * sizeof(double));
   h = fnv1a(h, g->lrow.data(), g->lrow.size() * sizeof(int));
+  h = fnv1a(h, &g->K, sizeof(double));
   if (lmax_m) {
     h = fnv1a(h, lmax_m, M * sizeof(int));
     h = fnv1a(h, nk_m, M * sizeof(int));

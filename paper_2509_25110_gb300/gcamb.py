@@ -60,6 +60,8 @@ def lib():
     L.gcamb_cl_cross.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp]
     L.gcamb_los_cl_workspace.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
     L.gcamb_los_cl.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_size_t, _vp]
+    L.gcamb_grid_create_curved.argtypes = [_dp, ctypes.c_int, _dp, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                           ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.POINTER(_vp)]
     L.gcamb_grid_create_lsampled.argtypes = [_dp, ctypes.c_int, _dp, ctypes.c_int, ctypes.c_double,
                                              ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_double,
                                              ctypes.POINTER(_vp)]
@@ -183,6 +185,19 @@ def grid_create(k, tau, tau0, lmin, lmax, eps_cut=0.0) -> Grid:
     _check(lib().gcamb_grid_create(k.ctypes.data_as(_dp), k.size, tau.ctypes.data_as(_dp), tau.size, float(tau0),
                                    int(lmin), int(lmax), float(eps_cut), ctypes.byref(h)))
     return Grid(h, k.copy(), tau.copy(), float(tau0), int(lmin), int(lmax))
+
+
+def grid_create_curved(q, tau, tau0, lmin, lmax, K, eps_cut=0.0) -> Grid:
+    """A curved-space grid (K [Mpc^-2] < 0 open, > 0 closed): the kernel is
+    the hyperspherical Bessel function of beta = q / sqrt|K|."""
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    tau = np.ascontiguousarray(tau, dtype=np.float64)
+    h = _vp()
+    _check(lib().gcamb_grid_create_curved(q.ctypes.data_as(_dp), q.size, tau.ctypes.data_as(_dp), tau.size,
+                                          float(tau0), int(lmin), int(lmax), float(K), float(eps_cut), ctypes.byref(h)))
+    g = Grid(h, q.copy(), tau.copy(), float(tau0), int(lmin), int(lmax))
+    g.K = float(K)
+    return g
 
 
 def grid_create_lsampled(k, tau, tau0, lval, eps_cut=0.0) -> Grid:
