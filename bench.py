@@ -53,7 +53,7 @@ def parse_args():
     ap.add_argument("--nk", type=int, default=0,
                     help="profiling case: the same k range with this many nodes (default: the workload's 2000)")
     ap.add_argument("--workload", default="batched",
-                    choices=["batched", "uneven", "emulator", "te", "tensor", "features", "lsampled"],
+                    choices=["batched", "uneven", "emulator", "te", "tensor", "features", "lsampled", "curved"],
                     help="batched (the headline), uneven (1000 sources, l_max <= 6000, plan + graph), "
                          "emulator (train on 100k spectra, serve)")
     ap.add_argument("--kernel-only", action="store_true",
@@ -637,6 +637,80 @@ def run_lsampled(args):
     print(json.dumps(line), flush=True)
 
 
+def run_curved(args):
+    """Curved space (Sec. 5): the 256-model l_max = 2500 batch in an open
+    universe with Omega_K = 0.01 (K = -Omega_K (H0/c)^2, h = 0.7: -5.45e-10
+    Mpc^-2), hyperspherical Bessel table, BF16X3; also the flat batch on the
+    same grid, and the table builds."""
+    import numpy as np
+    import torch
+
+    from paper_2509_25110_gb300 import build, gcamb, synth
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    build.build()
+    peaks, peak_src = load_peaks()
+    K = -0.01 * (0.7 / 2997.92458) ** 2
+    wl = synth.workload(WORKLOAD)
+    M = wl.M
+    p = synth.model_params(M, seed=0)
+    S = synth.sources_torch(wl.k, wl.tau, p, dev, torch.float32)
+    P = torch.as_tensor(synth.primordial(wl.k, p), device=dev)
+    out = {}
+    clocks = None
+    for name, mk in (("flat", lambda: gcamb.grid_create(wl.k, wl.tau, wl.tau0, wl.lmin, wl.lmax)),
+                     ("open", lambda: gcamb.grid_create_curved(wl.k, wl.tau, wl.tau0, wl.lmin, wl.lmax, K))):
+        g = mk()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        gcamb.bessel_table(g, gcamb.BF16X3)
+        torch.cuda.synchronize()
+        table_s = time.perf_counter() - t0
+        info = gcamb.grid_info(g)
+        ws = torch.empty(gcamb.los_cl_workspace(g, M, gcamb.BF16X3), dtype=torch.uint8, device=dev)
+        C = torch.empty((M, wl.nl), dtype=torch.float64, device=dev)
+        for _ in range(max(3, args.warmup)):
+            gcamb.los_cl(g, S, P, gcamb.BF16X3, C, ws)
+        gcamb.sync()
+        steps = max(3, min(args.steps, 200))
+        gcamb.profile_enable(True)
+        ms, clocks = _timed_region(lambda: gcamb.los_cl(g, S, P, gcamb.BF16X3, C, ws), steps, dev)
+        gcamb.sync()
+        tc_ms, tc_n = gcamb.profile_read(gcamb.K_TC)
+        gcamb.profile_enable(False)
+        tc_s = tc_ms / max(1, tc_n) * 1e-3
+        alg = info["active"] * 4 + M * wl.nk * wl.ntau * 4
+        out[name] = {"spectra_per_s": M * steps / (ms * 1e-3), "ms_per_step": ms / steps, "kernel_ms": tc_s * 1e3,
+                     "table_build_s": table_s, "table_gb": gcamb.table_bytes(g, gcamb.BF16X3) / 1e9,
+                     "stored_entries": info["active"], "hbm_frac": alg / tc_s / 1e9 / peaks["hbm_gbs"],
+                     "C": C[:2].cpu().numpy()}
+        g.close()
+    cpu = None
+    err = None
+    if not args.no_cpu_baseline:
+        import oracle
+        from oracle import build as ob
+        ob.build()
+        t0 = time.perf_counter()
+        Dr = oracle.los_curved(wl.k, wl.tau, wl.tau0, K, wl.lmin, wl.lmax, S[:1].double().cpu().numpy())
+        Cr = oracle.cl_from_delta(wl.k, Dr, P[:1].cpu().numpy())
+        dt = time.perf_counter() - t0
+        cpu = {"value": 1 / dt, "unit": "spectra/s", "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": "1 of the 256 models, full curved grid, %.1f s" % dt}
+        err = float(np.max(np.abs(out["open"]["C"][:1] / Cr - 1)))
+    o = out["open"]
+    line = {"metric": "C_l spectra/sec at l_max=2500 in an open universe (Omega_K = 0.01), BF16X3",
+            "value": o["spectra_per_s"], "unit": "spectra/s", "n_gpus": 1, "steps": max(3, min(args.steps, 200)),
+            "warmup": args.warmup, "ms_per_step": o["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "batched_lmax2500, open space", "K_per_Mpc2": K, "M": M, "lmax": wl.lmax,
+                       "nk": wl.nk, "ntau": wl.ntau, "max_rel_err_vs_oracle": err,
+                       "open": {k: v for k, v in o.items() if k != "C"},
+                       "flat": {k: v for k, v in out["flat"].items() if k != "C"}},
+            "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": 3 * max(3, min(args.steps, 200))}
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------------ our arm
 
 def main():
@@ -661,6 +735,9 @@ def main():
         return
     if args.workload == "lsampled":
         run_lsampled(args)
+        return
+    if args.workload == "curved":
+        run_curved(args)
         return
     import numpy as np
     import torch
