@@ -188,6 +188,31 @@ int gcamb_los_transfer_tensor(const gcamb_grid *g, const void *ST, const void *S
                               void *DeltaE, void *DeltaB, void *stream);
 
 /*
+ * Kernel grids.  By default a grid's table holds w_i j_l (Eq. 2).  Before its
+ * first table, a flat grid can be switched to one of the other kernels of the
+ * line-of-sight projection, evaluated in FP64 while the table is built:
+ *   GCAMB_KERNEL_EPS       c_l j_l(x) / x^2, c_l = sqrt((l+2)!/(l-2)!): the
+ *                          E-mode kernel of Eq. (3) and the tensor T kernel
+ *   GCAMB_KERNEL_TENSOR_E  (l(l-1)/x^2 - 2) j_l + 2 j_(l-1)/x (tensor E)
+ *   GCAMB_KERNEL_TENSOR_B  2 j_(l-1) - 2 (l-1) j_l / x      (tensor B)
+ * (zero below l = 2; the power series below the small-x cut of
+ * gcamb_los_transfer_e; every tau node stays in the first l-tile when
+ * lmin <= 5, since the l = 2 kernels do not vanish at x = 0).  Every path
+ * that reads the table then projects with that kernel: gcamb_los_transfer,
+ * gcamb_cl, gcamb_los_cl (the batched tensor-core path: one kernel grid per
+ * field, no cancellation between j_l and j_(l-1) in split precision), plans,
+ * sampled grids.  gcamb_los_transfer_e, gcamb_los_transfer_tensor and
+ * gcamb_los_cl_te, which derive their kernels from j_l, reject kernel grids.
+ * Errors: GCAMB_ESTATE (a table exists), GCAMB_EUNSUPPORTED (curved grid),
+ * GCAMB_EINVAL.
+ */
+#define GCAMB_KERNEL_J 0
+#define GCAMB_KERNEL_EPS 1
+#define GCAMB_KERNEL_TENSOR_E 2
+#define GCAMB_KERNEL_TENSOR_B 3
+int gcamb_grid_set_kernel(gcamb_grid *g, int kernel);
+
+/*
  * Curved space (the non-flat integration the paper names as its next step,
  * Sec. 2.1, 5): as gcamb_grid_create, with curvature K [Mpc^-2] != 0 and
  * the wavenumbers q[nq] of the curved-space modes; the kernel phi_l of

@@ -234,6 +234,18 @@ int gcamb_grid_create_curved(const double *q, int nq, const double *tau, int nta
   return grid_build(q, nq, tau, ntau, tau0, std::move(lrow), false, eps_cut, out, K);
 }
 
+int gcamb_grid_set_kernel(gcamb_grid *g, int kernel) {
+  if (!g) return fail(GCAMB_EINVAL, "grid_set_kernel: NULL grid");
+  if (kernel < GCAMB_KERNEL_J || kernel > GCAMB_KERNEL_TENSOR_B) return fail(GCAMB_EINVAL, "grid_set_kernel: unknown kernel");
+  for (const auto &t : g->tab)
+    if (t.d_data) return fail(GCAMB_ESTATE, "grid_set_kernel: the grid already has a table");
+  if (g->curved && kernel) return fail(GCAMB_EUNSUPPORTED, "grid_set_kernel: kernel grids are flat-space only");
+  g->kernel = kernel;
+  if (kernel && g->lmin <= 5)  // the l = 2 kernels do not vanish at x = 0: keep every node in the first tile
+    for (int q = 0; q < g->nk; ++q) g->ext[(size_t)q * g->nlt] = g->ntau;
+  return GCAMB_OK;
+}
+
 int gcamb_l_sampling(int lmin, int lmax, double boost, int *lval, int *n) {
   if (!n) return fail(GCAMB_EINVAL, "l_sampling: n is NULL");
   if (lmin < 0 || lmax < lmin || lmax > kMaxL || !(boost > 0.0))
@@ -443,6 +455,7 @@ int gcamb_los_transfer(const gcamb_grid *g, const void *S, int M, int mode, void
 int gcamb_los_transfer_e(const gcamb_grid *g, const void *SP, int M, int mode, void *DeltaE, void *stream) {
   if (!g) return fail(GCAMB_EINVAL, "los_transfer_e: NULL grid");
   if (g->curved) return fail(GCAMB_EUNSUPPORTED, "los_transfer_e: the E-mode kernel is flat-space only");
+  if (g->kernel) return fail(GCAMB_EUNSUPPORTED, "los_transfer_e: needs a j_l grid (use gcamb_los_transfer on a kernel grid)");
   if (mode != GCAMB_PLAIN64 && mode != GCAMB_PLAIN32)
     return fail(GCAMB_EINVAL, "los_transfer_e: mode must be GCAMB_PLAIN64 or GCAMB_PLAIN32");
   if (M < 0) return fail(GCAMB_EINVAL, "los_transfer_e: M < 0");
@@ -456,6 +469,7 @@ int gcamb_los_transfer_tensor(const gcamb_grid *g, const void *ST, const void *S
                               void *DeltaE, void *DeltaB, void *stream) {
   if (!g) return fail(GCAMB_EINVAL, "los_transfer_tensor: NULL grid");
   if (g->curved) return fail(GCAMB_EUNSUPPORTED, "los_transfer_tensor: the tensor kernels are flat-space only");
+  if (g->kernel) return fail(GCAMB_EUNSUPPORTED, "los_transfer_tensor: needs a j_l grid");
   if (mode != GCAMB_PLAIN64 && mode != GCAMB_PLAIN32)
     return fail(GCAMB_EINVAL, "los_transfer_tensor: mode must be GCAMB_PLAIN64 or GCAMB_PLAIN32");
   if (M < 0) return fail(GCAMB_EINVAL, "los_transfer_tensor: M < 0");
@@ -518,6 +532,7 @@ int gcamb_los_cl(const gcamb_grid *g, const float *S, const double *Pk, int M, i
 static int te_check(const gcamb_grid *g, int M, int mode, const char *who) {
   if (!g) return fail(GCAMB_EINVAL, std::string(who) + ": NULL grid");
   if (g->curved) return fail(GCAMB_EUNSUPPORTED, std::string(who) + ": the E-mode kernel is flat-space only");
+  if (g->kernel) return fail(GCAMB_EUNSUPPORTED, std::string(who) + ": needs a j_l grid");
   if (mode != GCAMB_BF16X3) return fail(GCAMB_EINVAL, std::string(who) + ": mode must be GCAMB_BF16X3");
   if (M < 0) return fail(GCAMB_EINVAL, std::string(who) + ": M < 0");
   if (!g->tab[mode].built) return fail(GCAMB_ESTATE, std::string(who) + ": build the table for this mode first");

@@ -283,6 +283,65 @@ struct TableSink {
   }
 };
 
+// Kernel grids: turns the stream put(l, j_l(x)) into put(l, kernel_l(x)) for
+//   1: c_l j_l / x^2                          (scalar E, tensor T)
+//   2: (l (l-1) / x^2 - 2) j_l + 2 j_(l-1) / x (tensor E)
+//   3: 2 j_(l-1) - 2 (l-1) j_l / x            (tensor B)
+// (l >= 2).  bessel_orders passes the orders ascending below the match and
+// descending above it; each kernel value is formed when j_l and j_(l-1) are
+// both at hand, the last forward value being kept across the jump.
+template <class Inner>
+struct KernelSink {
+  Inner &out;
+  int kern, lmin;
+  double ix, ix2;
+  int pl, fl;
+  double pv, fv;
+  __device__ __forceinline__ void emit(int l, double jl, double jm) {
+    if (l < lmin || l < 2) return;
+    const double dl = (double)l;
+    double v;
+    if (kern == 1) v = sqrt((dl + 2.0) * (dl + 1.0) * dl * (dl - 1.0)) * jl * ix2;
+    else if (kern == 2) v = (dl * (dl - 1.0) * ix2 - 2.0) * jl + 2.0 * jm * ix;
+    else v = 2.0 * jm - 2.0 * (dl - 1.0) * jl * ix;
+    out(l, v);
+  }
+  __device__ __forceinline__ void operator()(int l, double v) {
+    if (l == pl + 1) {
+      emit(l, v, pv);
+    } else if (l == pl - 1) {
+      emit(pl, pv, v);
+      if (l - 1 == fl) emit(l, v, fv);
+    } else {
+      fl = pl;
+      fv = pv;
+    }
+    pl = l;
+    pv = v;
+  }
+};
+
+// The kernels at x below the small-x cut (x <= 0.2), from the power series
+// j_l = x^l s_l(x^2), s_l(y) = sum_n (-y/2)^n / (n! (2l+2n+1)!!), for l = 2..5
+// (every other kernel value there is below c_l x^(l-2) / (2l+1)!!).
+__device__ double small_x_kernel(int kern, int l, double x) {
+  auto sser = [](int ll, double y) {
+    double df = 1.0;
+    for (int j = 3; j <= 2 * ll + 1; j += 2) df *= j;
+    double term = 1.0 / df, sum = term;
+    for (int n = 0; n < 6; ++n) {
+      term *= (-0.5 * y) / ((n + 1) * (2.0 * ll + 2 * n + 3));
+      sum += term;
+    }
+    return sum;
+  };
+  const double y = x * x, sl = sser(l, y), sm = sser(l - 1, y), dl = (double)l;
+  const double xl2 = l == 2 ? 1.0 : pow(x, l - 2);
+  if (kern == 1) return sqrt((dl + 2.0) * (dl + 1.0) * dl * (dl - 1.0)) * xl2 * sl;
+  if (kern == 2) return xl2 * (dl * (dl - 1.0) * sl - 2.0 * y * sl + 2.0 * sm);
+  return 2.0 * xl2 * x * (sm - (dl - 1.0) * sl);
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(128) bessel_table_kernel(const double *__restrict__ k, const double *__restrict__ tau,
                                                            const double *__restrict__ wtau, double tau0, int ntau,
@@ -292,7 +351,7 @@ __global__ void __launch_bounds__(128) bessel_table_kernel(const double *__restr
                                                            const double *__restrict__ xs, int nxs, int scale_exp,
                                                            const int *__restrict__ lrow,
                                                            const int *__restrict__ rowof, int nl, int curved,
-                                                           double rk, void *table) {
+                                                           double rk, int kern, double x_lo, void *table) {
   constexpr int KB = (MODE == GCAMB_PLAIN64 || MODE == GCAMB_PLAIN32) ? 64 : 32;
   const int q = blockIdx.y;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -306,10 +365,19 @@ __global__ void __launch_bounds__(128) bessel_table_kernel(const double *__restr
   const int ltop = lrow ? lrow[min((lt_last + 1) * kTileL, nl) - 1] : min(lmin + (lt_last + 1) * kTileL - 1, lmax);
   TableSink<MODE> sink{static_cast<char *>(table), off + (size_t)q * nlt, lmin, kbi, i % KB,
                        ldexp(wtau[i], scale_exp), -1, nullptr, rowof};
-  if (curved)  // hyperspherical: beta = q / sqrt|K|, chi = sqrt|K| (tau0 - tau)
+  if (curved) {  // hyperspherical: beta = q / sqrt|K|, chi = sqrt|K| (tau0 - tau)
     hyper_orders(k[q] / rk, rk * (tau0 - tau[i]), curved == 2, lmin, ltop, sink);
-  else
+  } else if (kern) {
+    const double x = k[q] * (tau0 - tau[i]);
+    if (x < x_lo) {
+      for (int l = max(lmin, 2); l <= min(ltop, 5); ++l) sink(l, small_x_kernel(kern, l, x));
+    } else {
+      KernelSink<TableSink<MODE>> ks{sink, kern, lmin, 1.0 / x, 1.0 / (x * x), -10, -10, 0.0, 0.0};
+      bessel_orders(x, lmin > 0 ? lmin - 1 : 0, ltop, xs, nxs, ks);
+    }
+  } else {
     bessel_orders(k[q] * (tau0 - tau[i]), lmin, ltop, xs, nxs, sink);
+  }
 }
 
 // Activity of one node on a curved grid: the highest l-tile in which some
@@ -410,7 +478,8 @@ int launch_bessel_table(gcamb_grid *g, int mode, cudaStream_t st) {
       for (double w : g->wtau) wmax = w > wmax ? w : wmax;
       int e = 0;
       if (wmax > 0.0) std::frexp(wmax, &e);  // wmax < 2^e
-      t.scale_exp = wmax > 0.0 ? 14 - e : 0;
+      // kernel grids: |kernel_l| < 4 (t_l <= c_2/15, |e_l|, |b_l| <= 4 max|j|)
+      t.scale_exp = wmax > 0.0 ? 14 - e - (g->kernel ? 2 : 0) : 0;
     }
     t.bytes = (size_t)nb * lay.block_bytes();
     cudaError_t e;
@@ -427,6 +496,8 @@ int launch_bessel_table(gcamb_grid *g, int mode, cudaStream_t st) {
     if ((e = cudaMemcpy(t.d_off, t.off.data(), t.off.size() * sizeof(int64_t), cudaMemcpyHostToDevice)) != cudaSuccess)
       return cuda_fail(e, "bessel_table");
   }
+  double x_lo = 0.0;
+  if (g->kernel && emode_x_lo(g, &x_lo)) return fail(GCAMB_EINVAL, "bessel_table: eps_cut too large for the kernel's limits");
   cudaError_t e = cudaMemsetAsync(t.d_data, 0, t.bytes, st);
   if (e != cudaSuccess) return cuda_fail(e, "bessel_table: memset");
   dim3 grid((g->ntau + 127) / 128, g->nk);
@@ -437,35 +508,35 @@ int launch_bessel_table(gcamb_grid *g, int mode, cudaStream_t st) {
                                                                g->lmax, g->nlt, t.d_nkb, t.d_off, g->d_xstart, g->nxs,
                                                                t.scale_exp, g->lsampled ? g->d_lrow : nullptr,
                                                                g->lsampled ? g->d_rowof : nullptr, g->nl, g->curved, g->rk,
-                                                               t.d_data);
+                                                               g->kernel, x_lo, t.d_data);
       break;
     case GCAMB_PLAIN32:
       bessel_table_kernel<GCAMB_PLAIN32><<<grid, 128, 0, st>>>(g->d_k, g->d_tau, g->d_wtau, g->tau0, g->ntau, g->lmin,
                                                                g->lmax, g->nlt, t.d_nkb, t.d_off, g->d_xstart, g->nxs,
                                                                t.scale_exp, g->lsampled ? g->d_lrow : nullptr,
                                                                g->lsampled ? g->d_rowof : nullptr, g->nl, g->curved, g->rk,
-                                                               t.d_data);
+                                                               g->kernel, x_lo, t.d_data);
       break;
     case GCAMB_BF16X3:
       bessel_table_kernel<GCAMB_BF16X3><<<grid, 128, 0, st>>>(g->d_k, g->d_tau, g->d_wtau, g->tau0, g->ntau, g->lmin,
                                                               g->lmax, g->nlt, t.d_nkb, t.d_off, g->d_xstart, g->nxs,
                                                               t.scale_exp, g->lsampled ? g->d_lrow : nullptr,
                                                                g->lsampled ? g->d_rowof : nullptr, g->nl, g->curved, g->rk,
-                                                               t.d_data);
+                                                               g->kernel, x_lo, t.d_data);
       break;
     case GCAMB_F16X3:
       bessel_table_kernel<GCAMB_F16X3><<<grid, 128, 0, st>>>(g->d_k, g->d_tau, g->d_wtau, g->tau0, g->ntau, g->lmin,
                                                              g->lmax, g->nlt, t.d_nkb, t.d_off, g->d_xstart, g->nxs,
                                                              t.scale_exp, g->lsampled ? g->d_lrow : nullptr,
                                                                g->lsampled ? g->d_rowof : nullptr, g->nl, g->curved, g->rk,
-                                                               t.d_data);
+                                                               g->kernel, x_lo, t.d_data);
       break;
     case GCAMB_TF32X3:
       bessel_table_kernel<GCAMB_TF32X3><<<grid, 128, 0, st>>>(g->d_k, g->d_tau, g->d_wtau, g->tau0, g->ntau, g->lmin,
                                                               g->lmax, g->nlt, t.d_nkb, t.d_off, g->d_xstart, g->nxs,
                                                               t.scale_exp, g->lsampled ? g->d_lrow : nullptr,
                                                                g->lsampled ? g->d_rowof : nullptr, g->nl, g->curved, g->rk,
-                                                               t.d_data);
+                                                               g->kernel, x_lo, t.d_data);
       break;
   }
   e = cudaGetLastError();

@@ -66,6 +66,7 @@ struct gcamb_grid {
   // curvature: 0 flat (j_l), 1 open (K < 0), 2 closed (K > 0): hyperspherical
   // Bessel functions with beta = k / rk, chi = rk (tau0 - tau), rk = sqrt|K|;
   // the tau-prefixes of a curved grid come from a device pass (ext_ready)
+  int kernel = 0;  // 0: j_l; GCAMB_KERNEL_* (flat grids): the table holds that kernel
   int curved = 0;
   double K = 0.0, rk = 0.0;
   bool ext_ready = true;

@@ -60,6 +60,7 @@ def lib():
     L.gcamb_cl_cross.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp]
     L.gcamb_los_cl_workspace.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
     L.gcamb_los_cl.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_size_t, _vp]
+    L.gcamb_grid_set_kernel.argtypes = [_vp, ctypes.c_int]
     L.gcamb_grid_create_curved.argtypes = [_dp, ctypes.c_int, _dp, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                            ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.POINTER(_vp)]
     L.gcamb_grid_create_lsampled.argtypes = [_dp, ctypes.c_int, _dp, ctypes.c_int, ctypes.c_double,
@@ -185,6 +186,17 @@ def grid_create(k, tau, tau0, lmin, lmax, eps_cut=0.0) -> Grid:
     _check(lib().gcamb_grid_create(k.ctypes.data_as(_dp), k.size, tau.ctypes.data_as(_dp), tau.size, float(tau0),
                                    int(lmin), int(lmax), float(eps_cut), ctypes.byref(h)))
     return Grid(h, k.copy(), tau.copy(), float(tau0), int(lmin), int(lmax))
+
+
+KERNEL_J, KERNEL_EPS, KERNEL_TENSOR_E, KERNEL_TENSOR_B = 0, 1, 2, 3
+
+
+def grid_set_kernel(g: Grid, kernel: int):
+    """Switch a flat grid's table (before it is built) from j_l to another
+    kernel of the projection (KERNEL_EPS, KERNEL_TENSOR_E, KERNEL_TENSOR_B)."""
+    _check(lib().gcamb_grid_set_kernel(g.handle, int(kernel)))
+    g.kernel = int(kernel)
+    return g
 
 
 def grid_create_curved(q, tau, tau0, lmin, lmax, K, eps_cut=0.0) -> Grid:
