@@ -472,6 +472,48 @@ def run_tensor(args):
                          enumerate(("TT", "EE", "BB"))}
             err[name]["TE_on_sqrt_TT_EE"] = float(np.max(np.abs(c[3] - ref[3])[ref[0] > 0] /
                                                          np.sqrt(ref[0] * ref[1])[ref[0] > 0]))
+    # batched tensor-core path: one kernel grid per field (c_l j_l/x^2 for T,
+    # e_l for E, b_l for B), 256 models, C^TT, C^EE, C^BB
+    Mb = 256
+    pb = synth.model_params(Mb, seed=0)
+    STb, SPb = (torch.as_tensor(a, dtype=torch.float32, device=dev)
+                for a in synth.sources_tensor(wl.k, wl.tau, pb))
+    Pb = torch.as_tensor(synth.primordial_tensor(wl.k, pb), device=dev)
+    refb = None
+    if not args.no_cpu_baseline:
+        R1 = oracle.los_tensor(wl.k, wl.tau, wl.tau0, wl.lmin, wl.lmax, STb[:1].double().cpu().numpy(),
+                               SPb[:1].double().cpu().numpy())
+        P1b = Pb[:1].cpu().numpy()
+        refb = {"TT": oracle.cl_cross(wl.k, R1[0], R1[0], P1b), "EE": oracle.cl_cross(wl.k, R1[1], R1[1], P1b),
+                "BB": oracle.cl_cross(wl.k, R1[2], R1[2], P1b)}
+    batched = {}
+    for mname, bmode in (("bf16x3", gcamb.BF16X3), ("f16x3", gcamb.F16X3)):
+        grids = {}
+        for name, kern in (("TT", gcamb.KERNEL_EPS), ("EE", gcamb.KERNEL_TENSOR_E), ("BB", gcamb.KERNEL_TENSOR_B)):
+            gk = gcamb.grid_set_kernel(gcamb.grid_create(wl.k, wl.tau, wl.tau0, wl.lmin, wl.lmax), kern)
+            gcamb.bessel_table(gk, bmode)
+            grids[name] = (gk, torch.empty(gcamb.los_cl_workspace(gk, Mb, bmode), dtype=torch.uint8, device=dev),
+                           torch.empty((Mb, wl.nl), dtype=torch.float64, device=dev), STb if name == "TT" else SPb)
+
+        def bstep():
+            for gk, wsk, Ck, Sk in grids.values():
+                gcamb.los_cl(gk, Sk, Pb, bmode, Ck, wsk)
+        for _ in range(3):
+            bstep()
+        gcamb.sync()
+        bsteps = max(3, min(args.steps, 50))
+        bms, _ = _timed_region(bstep, bsteps, dev)
+        gcamb.sync()
+        b = {"models_per_s": Mb * bsteps / (bms * 1e-3), "ms_per_step": bms / bsteps, "M": Mb}
+        if refb is not None:
+            b["max_rel_err_vs_oracle"] = {k: float(np.max(np.abs(grids[k][2][:1].cpu().numpy() / v - 1)))
+                                          for k, v in refb.items()}
+            b["max_dcl_over_sigma_cv"] = {k: float(oracle.cosmic_variance_ratio(grids[k][2][:1].cpu().numpy(),
+                                                                                v).max())
+                                          for k, v in refb.items()}
+        batched[mname] = b
+        for gk, *_ in grids.values():
+            gk.close()
     r64 = res["plain64"]
     line = {"metric": "tensor TT+EE+BB+TE spectrum sets/sec at l_max=1500 (plain FP64)",
             "value": r64["models_per_s"], "unit": "models/s", "n_gpus": 1, "steps": max(3, min(args.steps, 20)),
@@ -480,6 +522,7 @@ def run_tensor(args):
             "config": {"workload": "tensor_lmax1500", "M": M, "lmax": wl.lmax, "nk": wl.nk, "ntau": wl.ntau,
                        "stored_entries": info["stored_plain64"],
                        "plain32": {k: v for k, v in res["plain32"].items() if k not in ("cls", "clocks")},
+                       "batched_tt_ee_bb": batched,
                        "max_err_vs_oracle": err},
             "roofline": {"bound": "alu", "achieved": r64["achieved_tflops"], "peak": r64["peak_tflops"],
                          "unit": "TFLOP/s", "frac": r64["achieved_tflops"] / r64["peak_tflops"], "traffic": None,
