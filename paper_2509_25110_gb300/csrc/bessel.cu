@@ -119,8 +119,12 @@ __device__ __forceinline__ void bessel_orders(double x, int lmin, int ltop, cons
 // in closed space at most at beta - 1 (exact: Phi_beta = 0).  The downward
 // pass rescales by 1e-250 on overflow and counts it; the second pass writes
 // scale * f for the orders within one rescale of the match and 0 above.
+//
+// S, IS (optional): s_l and 1/s_l for l = 0..nS-1 (the block's q), staged in
+// shared memory; orders beyond nS fall back to the square root and division.
 template <class Sink>
-__device__ void hyper_orders(double beta, double chi, bool closed, int lmin, int ltop, Sink &put) {
+__device__ void hyper_orders(double beta, double chi, bool closed, int lmin, int ltop, Sink &put,
+                             const double *S = nullptr, const double *IS = nullptr, int nS = 0) {
   if (ltop < lmin) return;
   if (chi == 0.0) {
     if (lmin == 0) put(0, 1.0);
@@ -135,9 +139,11 @@ __device__ void hyper_orders(double beta, double chi, bool closed, int lmin, int
   }
   const double ct = ch / sh, b2 = beta * beta, sg = closed ? -1.0 : 1.0;
   auto sl = [&](int l) {
+    if (l < nS) return S[l];
     const double v = fma(sg * (double)l, (double)l, b2);
     return v > 0.0 ? sqrt(v) : 0.0;
   };
+  auto isl = [&](int l) { return l < nS ? IS[l] : 1.0 / sl(l); };
   const int lcap = closed ? (int)llrint(beta) - 1 : 0x3fffffff;
   const int lt = min(ltop, lcap);
   if (lt < lmin) return;
@@ -154,7 +160,7 @@ __device__ void hyper_orders(double beta, double chi, bool closed, int lmin, int
     if (lmin <= 1) put(1, p1);
     for (int l = 1; l < ls; ++l) {
       const double sn = sl(l + 1);
-      const double pn = ((2.0 * l + 1.0) * ct * p - sc * pm) / sn;
+      const double pn = ((2.0 * l + 1.0) * ct * p - sc * pm) * isl(l + 1);
       pm = p;
       p = pn;
       sc = sn;
@@ -177,7 +183,7 @@ __device__ void hyper_orders(double beta, double chi, bool closed, int lmin, int
   int R = 0;
   for (int l = L; l >= lend; --l) {
     const double s_l = sl(l);
-    const double fm = ((2.0 * l + 1.0) * ct * f - s_up * fh) / s_l;
+    const double fm = ((2.0 * l + 1.0) * ct * f - s_up * fh) * isl(l);
     fh = f;
     f = fm;
     s_up = s_l;
@@ -204,7 +210,7 @@ __device__ void hyper_orders(double beta, double chi, bool closed, int lmin, int
     }
     if (l <= lbot) break;
     const double s_l = sl(l);
-    const double fm = ((2.0 * l + 1.0) * ct * f - s_up * fh) / s_l;
+    const double fm = ((2.0 * l + 1.0) * ct * f - s_up * fh) * isl(l);
     fh = f;
     f = fm;
     s_up = s_l;
@@ -351,10 +357,25 @@ __global__ void __launch_bounds__(128) bessel_table_kernel(const double *__restr
                                                            const double *__restrict__ xs, int nxs, int scale_exp,
                                                            const int *__restrict__ lrow,
                                                            const int *__restrict__ rowof, int nl, int curved,
-                                                           double rk, int kern, double x_lo, void *table) {
+                                                           double rk, int kern, double x_lo, int ns, void *table) {
   constexpr int KB = (MODE == GCAMB_PLAIN64 || MODE == GCAMB_PLAIN32) ? 64 : 32;
   const int q = blockIdx.y;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  // curved grids: s_l and 1/s_l of this block's q, for l < ns (dynamic shared memory)
+  extern __shared__ double s_stage[];
+  const double *s_sh = nullptr, *is_sh = nullptr;
+  if (curved && ns > 0) {
+    const double b2 = (k[q] / rk) * (k[q] / rk), sg = curved == 2 ? -1.0 : 1.0;
+    for (int l = threadIdx.x; l < ns; l += blockDim.x) {
+      const double v = fma(sg * (double)l, (double)l, b2);
+      const double sv = v > 0.0 ? sqrt(v) : 0.0;
+      s_stage[l] = sv;
+      s_stage[ns + l] = sv > 0.0 ? 1.0 / sv : 0.0;
+    }
+    __syncthreads();
+    s_sh = s_stage;
+    is_sh = s_stage + ns;
+  }
   if (i >= ntau) return;
   const int32_t *nkb_q = nkb + (size_t)q * nlt;
   const int kbi = i / KB;
@@ -366,7 +387,7 @@ __global__ void __launch_bounds__(128) bessel_table_kernel(const double *__restr
   TableSink<MODE> sink{static_cast<char *>(table), off + (size_t)q * nlt, lmin, kbi, i % KB,
                        ldexp(wtau[i], scale_exp), -1, nullptr, rowof};
   if (curved) {  // hyperspherical: beta = q / sqrt|K|, chi = sqrt|K| (tau0 - tau)
-    hyper_orders(k[q] / rk, rk * (tau0 - tau[i]), curved == 2, lmin, ltop, sink);
+    hyper_orders(k[q] / rk, rk * (tau0 - tau[i]), curved == 2, lmin, ltop, sink, s_sh, is_sh, ns);
   } else if (kern) {
     const double x = k[q] * (tau0 - tau[i]);
     if (x < x_lo) {
@@ -399,13 +420,43 @@ struct ActSink {
 __global__ void __launch_bounds__(128) curved_activity_kernel(const double *__restrict__ k,
                                                               const double *__restrict__ tau, double tau0, int ntau,
                                                               int lmin, int lmax, int nlt, double rk, int closed,
-                                                              double eps, const int *__restrict__ rowof, int *ext) {
+                                                              double eps, const int *__restrict__ rowof, int ns,
+                                                              int *ext) {
   const int q = blockIdx.y;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  extern __shared__ double s_stage[];
+  if (ns > 0) {
+    const double b2 = (k[q] / rk) * (k[q] / rk), sg = closed ? -1.0 : 1.0;
+    for (int l = threadIdx.x; l < ns; l += blockDim.x) {
+      const double v = fma(sg * (double)l, (double)l, b2);
+      const double sv = v > 0.0 ? sqrt(v) : 0.0;
+      s_stage[l] = sv;
+      s_stage[ns + l] = sv > 0.0 ? 1.0 / sv : 0.0;
+    }
+    __syncthreads();
+  }
   if (i >= ntau) return;
   ActSink a{lmin, rowof, eps, -1};
-  hyper_orders(k[q] / rk, rk * (tau0 - tau[i]), closed != 0, lmin, lmax, a);
+  hyper_orders(k[q] / rk, rk * (tau0 - tau[i]), closed != 0, lmin, lmax, a, s_stage, s_stage + ns, ns);
   for (int t = 0; t <= a.ltmax && t < nlt; ++t) atomicMax(ext + (size_t)q * nlt + t, i + 1);
+}
+
+// Orders of s_l to stage for a curved grid: every order the recurrence can
+// reach below l_max (the Miller start is at most l_max + 60 + 8 sqrt(l_max)
+// + the open-space tail + 10, and the forward part stops at l_max), if 2 of
+// them fit in 160 KB of shared memory; else 0 (computed on the fly).
+int curved_stage_orders(const gcamb_grid *g) {
+  double chimax = 0.0;
+  for (double t : g->tau) chimax = std::max(chimax, g->rk * (g->tau0 - t));
+  double extra = 0.0;
+  if (g->curved == 1 && chimax > 0.0) {
+    const double th = std::tanh(0.5 * chimax);
+    extra = th < 1.0 ? std::min(46.0 / -std::log(th), 1e6) : 1e6;
+  }
+  const double hi = (double)g->lmax;
+  const double nsd = hi + 60.0 + 8.0 * std::sqrt(hi) + extra + 16.0;
+  if (nsd * 2 * sizeof(double) > 160.0 * 1024) return 0;
+  return (int)nsd;
 }
 
 // The tau-prefixes of a curved grid, from the activity of every node (run
@@ -418,10 +469,16 @@ int curved_extents(gcamb_grid *g, cudaStream_t st) {
   e = cudaMemsetAsync(d_ext, 0, n * sizeof(int), st);
   if (e == cudaSuccess) {
     dim3 grid((g->ntau + 127) / 128, g->nk);
-    curved_activity_kernel<<<grid, 128, 0, st>>>(g->d_k, g->d_tau, g->tau0, g->ntau, g->lmin, g->lmax, g->nlt, g->rk,
-                                                 g->curved == 2, g->eps_cut, g->lsampled ? g->d_rowof : nullptr,
-                                                 d_ext);
-    e = cudaGetLastError();
+    const int ns = curved_stage_orders(g);
+    const size_t smem = (size_t)2 * ns * sizeof(double);
+    if (smem > 48 * 1024)
+      e = cudaFuncSetAttribute(curved_activity_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) {
+      curved_activity_kernel<<<grid, 128, smem, st>>>(g->d_k, g->d_tau, g->tau0, g->ntau, g->lmin, g->lmax, g->nlt,
+                                                      g->rk, g->curved == 2, g->eps_cut,
+                                                      g->lsampled ? g->d_rowof : nullptr, ns, d_ext);
+      e = cudaGetLastError();
+    }
   }
   std::vector<int> h(n);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), d_ext, n * sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -501,42 +558,55 @@ int launch_bessel_table(gcamb_grid *g, int mode, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(t.d_data, 0, t.bytes, st);
   if (e != cudaSuccess) return cuda_fail(e, "bessel_table: memset");
   dim3 grid((g->ntau + 127) / 128, g->nk);
+  // curved grids: s_l, 1/s_l staged per block (the block's q)
+  const int ns = g->curved ? curved_stage_orders(g) : 0;
+  const size_t tsmem = (size_t)2 * ns * sizeof(double);
+  if (tsmem > 48 * 1024) {
+    switch (mode) {
+      case GCAMB_PLAIN64: e = cudaFuncSetAttribute(bessel_table_kernel<GCAMB_PLAIN64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsmem); break;
+      case GCAMB_PLAIN32: e = cudaFuncSetAttribute(bessel_table_kernel<GCAMB_PLAIN32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsmem); break;
+      case GCAMB_BF16X3: e = cudaFuncSetAttribute(bessel_table_kernel<GCAMB_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsmem); break;
+      case GCAMB_F16X3: e = cudaFuncSetAttribute(bessel_table_kernel<GCAMB_F16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsmem); break;
+      default: e = cudaFuncSetAttribute(bessel_table_kernel<GCAMB_TF32X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsmem); break;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "bessel_table: smem attribute");
+  }
   ProfScope prof(GCAMB_K_TABLE, st);
   switch (mode) {
     case GCAMB_PLAIN64:
-      bessel_table_kernel<GCAMB_PLAIN64><<<grid, 128, 0, st>>>(g->d_k, g->d_tau, g->d_wtau, g->tau0, g->ntau, g->lmin,
+      bessel_table_kernel<GCAMB_PLAIN64><<<grid, 128, tsmem, st>>>(g->d_k, g->d_tau, g->d_wtau, g->tau0, g->ntau, g->lmin,
                                                                g->lmax, g->nlt, t.d_nkb, t.d_off, g->d_xstart, g->nxs,
                                                                t.scale_exp, g->lsampled ? g->d_lrow : nullptr,
                                                                g->lsampled ? g->d_rowof : nullptr, g->nl, g->curved, g->rk,
-                                                               g->kernel, x_lo, t.d_data);
+                                                               g->kernel, x_lo, ns, t.d_data);
       break;
     case GCAMB_PLAIN32:
-      bessel_table_kernel<GCAMB_PLAIN32><<<grid, 128, 0, st>>>(g->d_k, g->d_tau, g->d_wtau, g->tau0, g->ntau, g->lmin,
+      bessel_table_kernel<GCAMB_PLAIN32><<<grid, 128, tsmem, st>>>(g->d_k, g->d_tau, g->d_wtau, g->tau0, g->ntau, g->lmin,
                                                                g->lmax, g->nlt, t.d_nkb, t.d_off, g->d_xstart, g->nxs,
                                                                t.scale_exp, g->lsampled ? g->d_lrow : nullptr,
                                                                g->lsampled ? g->d_rowof : nullptr, g->nl, g->curved, g->rk,
-                                                               g->kernel, x_lo, t.d_data);
+                                                               g->kernel, x_lo, ns, t.d_data);
       break;
     case GCAMB_BF16X3:
-      bessel_table_kernel<GCAMB_BF16X3><<<grid, 128, 0, st>>>(g->d_k, g->d_tau, g->d_wtau, g->tau0, g->ntau, g->lmin,
+      bessel_table_kernel<GCAMB_BF16X3><<<grid, 128, tsmem, st>>>(g->d_k, g->d_tau, g->d_wtau, g->tau0, g->ntau, g->lmin,
                                                               g->lmax, g->nlt, t.d_nkb, t.d_off, g->d_xstart, g->nxs,
                                                               t.scale_exp, g->lsampled ? g->d_lrow : nullptr,
                                                                g->lsampled ? g->d_rowof : nullptr, g->nl, g->curved, g->rk,
-                                                               g->kernel, x_lo, t.d_data);
+                                                               g->kernel, x_lo, ns, t.d_data);
       break;
     case GCAMB_F16X3:
-      bessel_table_kernel<GCAMB_F16X3><<<grid, 128, 0, st>>>(g->d_k, g->d_tau, g->d_wtau, g->tau0, g->ntau, g->lmin,
+      bessel_table_kernel<GCAMB_F16X3><<<grid, 128, tsmem, st>>>(g->d_k, g->d_tau, g->d_wtau, g->tau0, g->ntau, g->lmin,
                                                              g->lmax, g->nlt, t.d_nkb, t.d_off, g->d_xstart, g->nxs,
                                                              t.scale_exp, g->lsampled ? g->d_lrow : nullptr,
                                                                g->lsampled ? g->d_rowof : nullptr, g->nl, g->curved, g->rk,
-                                                               g->kernel, x_lo, t.d_data);
+                                                               g->kernel, x_lo, ns, t.d_data);
       break;
     case GCAMB_TF32X3:
-      bessel_table_kernel<GCAMB_TF32X3><<<grid, 128, 0, st>>>(g->d_k, g->d_tau, g->d_wtau, g->tau0, g->ntau, g->lmin,
+      bessel_table_kernel<GCAMB_TF32X3><<<grid, 128, tsmem, st>>>(g->d_k, g->d_tau, g->d_wtau, g->tau0, g->ntau, g->lmin,
                                                               g->lmax, g->nlt, t.d_nkb, t.d_off, g->d_xstart, g->nxs,
                                                               t.scale_exp, g->lsampled ? g->d_lrow : nullptr,
                                                                g->lsampled ? g->d_rowof : nullptr, g->nl, g->curved, g->rk,
-                                                               g->kernel, x_lo, t.d_data);
+                                                               g->kernel, x_lo, ns, t.d_data);
       break;
   }
   e = cudaGetLastError();
