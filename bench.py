@@ -261,6 +261,7 @@ def run_uneven(args):
             "data": "synthetic",
             "config": {"workload": "uneven_lmax6000", "M": wl.M, "nk_master": wl.nk, "ntau": wl.ntau,
                        "lmax": wl.lmax, "mode": args.mode, "tile": info["tile"], "items": info["items"],
+                       "sources_read_in_place": bool(info["fused"]),
                        "ctas": info["ctas"], "graph_captures": info["captures"], "graph_replays": info["replays"],
                        "table_build_s": table_s, "first_launch_s_incl_tuning": first_s,
                        "table_gb": gcamb.table_bytes(g, mode) / 1e9},

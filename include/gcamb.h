@@ -373,7 +373,7 @@ int gcamb_los_cl_te(const gcamb_grid *g, const float *ST, const float *SP, const
  */
 typedef struct gcamb_plan gcamb_plan;
 
-#define GCAMB_PLAN_INFO_N 8
+#define GCAMB_PLAN_INFO_N 9
 
 int gcamb_plan_create(gcamb_grid *g, int M, const int *lmax_m, const int *nk_m, int mode, int tune,
                       gcamb_plan **out);
@@ -401,7 +401,8 @@ int gcamb_plan_launch(gcamb_plan *p, const float *S, const double *Pk, double *C
  * Plan summary (host, int64[GCAMB_PLAN_INFO_N]): [0] source-tile width in use
  * (0 before tuning), [1] work items, [2] persistent CTAs, [3] graph captures,
  * [4] graph replays, [5] 1 if the width came from timing (now or cached),
- * [6] M, [7] workspace bytes of the width in use.
+ * [6] M, [7] workspace bytes of the width in use, [8] 1 if the sources are
+ * read in place (fused kernel, no split pass: uniform batches only).
  */
 int gcamb_plan_info(const gcamb_plan *p, int64_t *info);
 

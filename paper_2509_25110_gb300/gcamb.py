@@ -484,9 +484,9 @@ def plan_workspace(p: Plan) -> int:
 
 
 def plan_info(p: Plan) -> dict:
-    a = (ctypes.c_int64 * 8)()
+    a = (ctypes.c_int64 * 9)()
     _check(lib().gcamb_plan_info(p.handle, a))
-    keys = ("tile", "items", "ctas", "captures", "replays", "tuned", "M", "workspace")
+    keys = ("tile", "items", "ctas", "captures", "replays", "tuned", "M", "workspace", "fused")
     return dict(zip(keys, [int(v) for v in a]))
 
 

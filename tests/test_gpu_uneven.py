@@ -160,3 +160,4 @@ def test_uneven_lmax6000_full_size_sampled(orc):
         err = np.abs(C[m, :L - wl.lmin + 1] / cr - 1)
         assert err.max() <= TOL, (m, L, q, err.max())
         assert np.all(C[m, L - wl.lmin + 1:] == 0.0)
+
