@@ -347,6 +347,22 @@ int gcamb_los_cl_te(const gcamb_grid *g, const float *ST, const float *SP, const
                     double *ClTT, double *ClEE, double *ClTE, void *ws, size_t ws_bytes, void *stream);
 
 /*
+ * Two fields batched together on the tensor cores, each with its own kernel
+ * grid (gcamb_grid_set_kernel; e.g. the tensor T and E kernels): for M
+ * models, C^XX, C^YY and C^XY of Eq. (1) with Delta_X from the sources SX
+ * and gx's table, Delta_Y from SY and gy's table, without storing Delta.
+ * Each stage carries a block of both tables; the epilogue accumulates the
+ * three spectra per model (the kernels' own factors are in the tables: no
+ * c_l here).  gx and gy must share k, tau, tau0, the multipoles and the
+ * table layout (the same grid arguments and kernels with the same
+ * activity); both need gcamb_bessel_table(., GCAMB_BF16X3).  Arguments and
+ * errors as for gcamb_los_cl_te; workspace from gcamb_los_cl_te_workspace(gx).
+ */
+int gcamb_los_cl_pair(const gcamb_grid *gx, const gcamb_grid *gy, const float *SX, const float *SY, const double *Pk,
+                      int M, int mode, double *ClXX, double *ClYY, double *ClXY, void *ws, size_t ws_bytes,
+                      void *stream);
+
+/*
  * Plans: batches of sources with their own l_max and k range on one grid
  * (the uneven batch), run as one persistent tensor-core kernel replayed from
  * a CUDA graph.  Eq. (1) is summed for source m over its own k prefix

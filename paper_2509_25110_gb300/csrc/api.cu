@@ -544,6 +544,11 @@ static int te_check(const gcamb_grid *g, int M, int mode, const char *who) {
 int gcamb_los_cl_te_workspace(const gcamb_grid *g, int M, int mode, size_t *bytes) {
   if (!bytes) return fail(GCAMB_EINVAL, "los_cl_te_workspace: bytes is NULL");
   *bytes = 0;
+  if (g && g->kernel && !g->curved && mode == GCAMB_BF16X3 && M >= 0 && g->tab[mode].built && g->ntau % 4 == 0) {
+    // a kernel grid: the workspace of gcamb_los_cl_pair
+    *bytes = M ? los_cl_te_workspace_bytes(g, M) : 0;
+    return (*bytes || !M) ? GCAMB_OK : fail(GCAMB_ECUDA, "los_cl_te_workspace: plan");
+  }
   if (int rc = te_check(g, M, mode, "los_cl_te_workspace")) return rc;
   if (M == 0) return GCAMB_OK;
   *bytes = los_cl_te_workspace_bytes(g, M);
@@ -558,6 +563,21 @@ int gcamb_los_cl_te(const gcamb_grid *g, const float *ST, const float *SP, const
   if (!is_sm103()) return fail(GCAMB_EUNSUPPORTED, "los_cl_te: the tensor-core path needs an sm_103 device");
   if (!ws) return fail(GCAMB_EINVAL, "los_cl_te: workspace missing");
   return launch_los_cl_te(g, ST, SP, Pk, M, ClTT, ClEE, ClTE, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+int gcamb_los_cl_pair(const gcamb_grid *gx, const gcamb_grid *gy, const float *SX, const float *SY, const double *Pk,
+                      int M, int mode, double *ClXX, double *ClYY, double *ClXY, void *ws, size_t ws_bytes,
+                      void *stream) {
+  if (!gx || !gy) return fail(GCAMB_EINVAL, "los_cl_pair: NULL grid");
+  if (mode != GCAMB_BF16X3) return fail(GCAMB_EINVAL, "los_cl_pair: mode must be GCAMB_BF16X3");
+  if (M < 0) return fail(GCAMB_EINVAL, "los_cl_pair: M < 0");
+  if (!gx->tab[mode].built || !gy->tab[mode].built)
+    return fail(GCAMB_ESTATE, "los_cl_pair: build both grids' tables for this mode first");
+  if (gx->ntau % 4 != 0) return fail(GCAMB_EUNSUPPORTED, "los_cl_pair: needs ntau % 4 == 0");
+  if (M == 0) return GCAMB_OK;
+  if (!SX || !SY || !Pk || !ClXX || !ClYY || !ClXY || !ws) return fail(GCAMB_EINVAL, "los_cl_pair: NULL pointer");
+  if (!is_sm103()) return fail(GCAMB_EUNSUPPORTED, "los_cl_pair: the tensor-core path needs an sm_103 device");
+  return launch_los_cl_pair(gx, gy, SX, SY, Pk, M, ClXX, ClYY, ClXY, ws, ws_bytes, (cudaStream_t)stream);
 }
 
 int gcamb_sync(void *stream) {

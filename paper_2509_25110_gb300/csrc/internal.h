@@ -118,6 +118,9 @@ int launch_cl(const gcamb_grid *g, const void *Delta, int d_dtype, const double 
 // Tensor-core batched path (tc.cu).
 size_t los_cl_workspace_bytes(const gcamb_grid *g, int M, int mode);
 size_t los_cl_te_workspace_bytes(const gcamb_grid *g, int M);
+int launch_los_cl_pair(const gcamb_grid *gx, const gcamb_grid *gy, const float *SX, const float *SY,
+                       const double *Pk, int M, double *ClXX, double *ClYY, double *ClXY, void *ws, size_t ws_bytes,
+                       cudaStream_t st);
 int launch_los_cl_te(const gcamb_grid *g, const float *ST, const float *SP, const double *Pk, int M, double *ClTT,
                      double *ClEE, double *ClTE, void *ws, size_t ws_bytes, cudaStream_t st);
 int launch_los_cl(const gcamb_grid *g, const float *S, const double *Pk, int M, int mode, double *Cl,

@@ -52,6 +52,7 @@ struct TcItem {
 
 struct TcParams {
   const char *table;
+  const char *table2;    // pair: the second field's table (same layout)
   const int64_t *off;    // [nk][nlt]
   const int32_t *nkb;    // [nk][nlt]
   const char *sp;        // split sources [nk][n_mt][nkbs] blocks of 256*NT bytes
@@ -173,11 +174,11 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 // third of the accumulate steps (the tensor core's FP32 accumulation error
 // grows with their number); D_x is ~2^-8 of D_hh, so its own rounding is
 // negligible.  The pairs are double-buffered across k when TMEM allows.
-template <int NT, int MODE>
+template <int NT, int MODE, int NA = 1>
 struct TcCfg {
   static constexpr int kABytes = TcGeom<MODE>::kABytes;
   static constexpr int kBBytes = 2 * NT * TcGeom<MODE>::kRowB;  // hi + lo planes of NT rows
-  static constexpr int kStageBytes = kABytes + kBBytes;
+  static constexpr int kStageBytes = NA * kABytes + kBBytes;     // NA table blocks (pair: 2)
   static constexpr int kStages = (kSmemBudget / kStageBytes) > 8 ? 8 : (kSmemBudget / kStageBytes);
   static constexpr int kNBuf = (4 * NT <= 512) ? 2 : 1;
   static constexpr int kTmemCols = kNBuf * 2 * NT < 32 ? 32 : kNBuf * 2 * NT;
@@ -191,7 +192,7 @@ struct TcCfg {
   static constexpr int kChunk = NT >= 128 ? 8 : 16;      // TMEM load width (register budget)
 };
 
-template <bool FUSED, bool TE = false>
+template <bool FUSED, int TE = 0>
 struct TcRoles {
   static constexpr int kConv = FUSED ? kConvWarps : 0;
   static constexpr int kEpi0 = 2 + kConv;  // first epilogue warp
@@ -206,19 +207,25 @@ struct TcRoles {
 // work.  kL2: the item's l-tile is the first (it may hold l = 2).
 constexpr int kFirst = 1 << 16, kLast = 1 << 17, kL2 = 1 << 18;
 
-// TE (temperature and E-mode together, fused bf16 only): a source tile holds
+// TE = 2 (pair): two fields X, Y of kernel grids with the same layout (for
+// instance the tensor T and E kernels): each stage holds a block of both
+// tables; the X rows are multiplied by the first, the Y rows by the second
+// (six MMAs of N = NT/2 per K step), into the TMEM layout of TE = 1, and the
+// sources are split without scaling.  The epilogue is that of TE = 1.
+//
+// TE = 1 (temperature and E-mode together, fused bf16 only): a source tile holds
 // NT/2 models, their FP32 temperature sources in operand rows 0 .. NT/2-1 and
 // their polarisation sources in rows NT/2 .. NT-1 (one TMA box from each).
 // The converters scale the E rows by 1/x^2 (0 below the small-x cut), so
 // that the shared table of w_i j_l gives D_E' = sum_i w_i j_l S_P / x^2; the
 // epilogue adds the l = 2 small-x tail and accumulates, per model,
 // (w D_T)^2, (w D_E')^2 and w^2 D_T D_E'; the reduce applies c_l^2 and c_l.
-template <int NT, int MODE, bool FUSED, bool TE = false>
+template <int NT, int MODE, bool FUSED, int TE = 0>
 __global__ void __launch_bounds__(TcRoles<FUSED, TE>::kThreadsT, 1)
     los_cl_tc_kernel(const __grid_constant__ CUtensorMap tm_src, const __grid_constant__ CUtensorMap tm_src2,
                      TcParams p) {
   static_assert(!TE || (FUSED && MODE == kBF16 && NT <= 128), "TE: fused bf16, NT <= 128");
-  using C = TcCfg<NT, MODE>;
+  using C = TcCfg<NT, MODE, TE == 2 ? 2 : 1>;
   using G = TcGeom<MODE>;
   using R = TcRoles<FUSED, TE>;
   constexpr int S = C::kStages;
@@ -347,19 +354,23 @@ __global__ void __launch_bounds__(TcRoles<FUSED, TE>::kThreadsT, 1)
               break;
             }
             const uint32_t sa = smem_u32(smem + stage * C::kStageBytes);
-            mbar_expect_tx(full0 + 8 * stage, C::kStageBytes + (TE ? 128 : 0));
+            mbar_expect_tx(full0 + 8 * stage, C::kStageBytes + (TE == 1 ? 128 : 0));
             armed_phase[stage] = (int)phase;
             bulk_g2s(sa, a + (size_t)kb * C::kABytes, C::kABytes, full0 + 8 * stage);
-            if constexpr (TE)  // the block's 32 values of 1/x^2
+            if constexpr (TE == 2)  // the second field's table block
+              bulk_g2s(sa + C::kABytes, p.table2 + (size_t)q_off[j] * C::kABytes + (size_t)kb * C::kABytes,
+                       C::kABytes, full0 + 8 * stage);
+            if constexpr (TE == 1)  // the block's 32 values of 1/x^2
               bulk_g2s(smem_u32(fbuf + stage * 128), p.ix2 + ((size_t)q * p.nkbs + kb) * 32, 128, full0 + 8 * stage);
-            if constexpr (TE) {  // FP32 boxes [NT/2 models][1 k][32 tau] of S_T and S_P
-              tma_load_3d(sa + C::kABytes, &tm_src, kb * 32, q, it.mt * (NT / 2), full0 + 8 * stage);
-              tma_load_3d(sa + C::kABytes + (NT / 2) * 128, &tm_src2, kb * 32, q, it.mt * (NT / 2),
+            constexpr int kBOff = (TE == 2 ? 2 : 1) * C::kABytes;  // the source region of the stage
+            if constexpr (TE) {  // FP32 boxes [NT/2 models][1 k][32 tau] of the two fields
+              tma_load_3d(sa + kBOff, &tm_src, kb * 32, q, it.mt * (NT / 2), full0 + 8 * stage);
+              tma_load_3d(sa + kBOff + (NT / 2) * 128, &tm_src2, kb * 32, q, it.mt * (NT / 2),
                           full0 + 8 * stage);
             } else if constexpr (FUSED)  // FP32 box [NT sources][1 k][32 tau]; zero beyond ntau and M
-              tma_load_3d(sa + C::kABytes, &tm_src, kb * 32, q, it.mt * NT, full0 + 8 * stage);
+              tma_load_3d(sa + kBOff, &tm_src, kb * 32, q, it.mt * NT, full0 + 8 * stage);
             else
-              bulk_g2s(sa + C::kABytes, b + (size_t)kb * C::kBBytes, C::kBBytes, full0 + 8 * stage);
+              bulk_g2s(sa + kBOff, b + (size_t)kb * C::kBBytes, C::kBBytes, full0 + 8 * stage);
             if (++stage == S) {
               stage = 0;
               phase ^= 1u;
@@ -424,12 +435,30 @@ __global__ void __launch_bounds__(TcRoles<FUSED, TE>::kThreadsT, 1)
           }
           tc_fence_after();
           const uint32_t sa = smem_u32(smem + stage * C::kStageBytes);
-          const uint32_t sb = sa + C::kABytes;
+          const uint32_t sb = sa + (TE == 2 ? 2 : 1) * C::kABytes;
 #pragma unroll
           for (int kk = 0; kk < G::kKSteps; ++kk) {
             const uint64_t ah = G::desc(sa + kk * 32), al = G::desc(sa + G::kPlaneA + kk * 32);
             const uint64_t bh = G::desc(sb + kk * 32), bl = G::desc(sb + NT * G::kRowB + kk * 32);
             const uint32_t accum = (kb | kk) ? 1u : 0u;
+            if constexpr (TE == 2) {
+              // X rows [0, NT/2) times table 1, Y rows [NT/2, NT) times table 2;
+              // row NT/2 starts on a whole 8-row swizzle atom
+              constexpr int H = NT / 2;
+              constexpr uint32_t idescH = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(H >> 3) << 17) |
+                                          ((uint32_t)(128 >> 4) << 24);
+              const uint32_t sa2 = sa + C::kABytes;
+              const uint64_t ah2 = G::desc(sa2 + kk * 32), al2 = G::desc(sa2 + G::kPlaneA + kk * 32);
+              const uint64_t bhY = G::desc(sb + H * G::kRowB + kk * 32);
+              const uint64_t blY = G::desc(sb + NT * G::kRowB + H * G::kRowB + kk * 32);
+              mma<MODE>(dhh, ah, bh, idescH, accum);       // D_X hh
+              mma<MODE>(dhh + H, ah2, bhY, idescH, accum);  // D_Y hh
+              mma<MODE>(dx, ah, bl, idescH, accum);        // D_X x
+              mma<MODE>(dx, al, bh, idescH, 1u);
+              mma<MODE>(dx + H, ah2, blY, idescH, accum);  // D_Y x
+              mma<MODE>(dx + H, al2, bhY, idescH, 1u);
+              continue;
+            }
             if constexpr (kPair) {
               mma<MODE>(dhh, ah, bh, idesc2, accum);  // [D_hh | D_x] (+)= A_hi [B_hi | B_lo]
             } else {
@@ -487,14 +516,14 @@ __global__ void __launch_bounds__(TcRoles<FUSED, TE>::kThreadsT, 1)
         bool ok = true;
         for (int kb = 0; kb < nb; ++kb) {
           const bool w2 = mbar_wait(full0 + 8 * stage, phase, abort_flag, p.err);
-          unsigned char *sb = smem + stage * C::kStageBytes + C::kABytes;
+          unsigned char *sb = smem + stage * C::kStageBytes + (TE == 2 ? 2 : 1) * C::kABytes;
           const float4 *raw = reinterpret_cast<const float4 *>(sb);
           float4 v[RJ];
 #pragma unroll
           for (int j = 0; j < RJ; ++j) v[j] = raw[ct + 128 * j];
           // TE: 1/x^2 of this thread's four tau nodes (copied with the stage)
           float4 f = make_float4(1.f, 1.f, 1.f, 1.f);
-          if constexpr (TE) f = reinterpret_cast<const float4 *>(fbuf + stage * 128)[c4];
+          if constexpr (TE == 1) f = reinterpret_cast<const float4 *>(fbuf + stage * 128)[c4];
           if (!conv_all(w2)) {
             ok = false;
             break;
@@ -502,7 +531,7 @@ __global__ void __launch_bounds__(TcRoles<FUSED, TE>::kThreadsT, 1)
 #pragma unroll
           for (int j = 0; j < RJ; ++j) {
             float x0 = v[j].x, x1 = v[j].y, x2 = v[j].z, x3 = v[j].w;
-            if constexpr (TE) {
+            if constexpr (TE == 1) {
               if (j >= RJ / 2) {  // rows NT/2 .. NT-1: polarisation sources
                 x0 *= f.x;
                 x1 *= f.y;
@@ -1001,7 +1030,7 @@ __global__ void __launch_bounds__(256) te_weights_kernel(const double *__restric
 __global__ void __launch_bounds__(128) reduce_te_kernel(const float *__restrict__ partial,
                                                         const int *__restrict__ tile_ptr,
                                                         const int *__restrict__ tile_items, int H, int n_mt, int M,
-                                                        int nl, const int *__restrict__ lrow,
+                                                        int nl, const int *__restrict__ lrow, int scale_cl,
                                                         double *__restrict__ ClTT, double *__restrict__ ClEE,
                                                         double *__restrict__ ClTE) {
   const int r = threadIdx.x;
@@ -1019,7 +1048,8 @@ __global__ void __launch_bounds__(128) reduce_te_kernel(const float *__restrict_
     ee += (double)pp[(size_t)H * 128];
     te += (double)pp[(size_t)2 * H * 128];
   }
-  const double c2 = l >= 2 ? (double)(l + 2) * (l + 1) * l * (l - 1) : 0.0;
+  // E-mode (scale_cl): C^EE = c_l^2 sum, C^TE = c_l sum; pairs of kernel grids: none
+  const double c2 = !scale_cl ? 1.0 : (l >= 2 ? (double)(l + 2) * (l + 1) * l * (l - 1) : 0.0);
   const size_t o = (size_t)m * nl + row;
   ClTT[o] = tt;
   ClEE[o] = c2 * ee;
@@ -1303,10 +1333,10 @@ TcPlan *get_plan(const gcamb_grid *g, int M, int mode, int *rc) {
   return pl;
 }
 
-template <int NT, int MODE, bool FUSED, bool TE = false>
+template <int NT, int MODE, bool FUSED, int TE = 0>
 int launch_tc_kernel(const gcamb_grid *g, const TcPlan &pl, const CUtensorMap &tm, const CUtensorMap &tm2,
                      const TcParams &prm, cudaStream_t st) {
-  using Cfg = TcCfg<NT, MODE>;
+  using Cfg = TcCfg<NT, MODE, TE == 2 ? 2 : 1>;
   cudaError_t e = cudaFuncSetAttribute(los_cl_tc_kernel<NT, MODE, FUSED, TE>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmemBytes);
   if (e != cudaSuccess) return cuda_fail(e, "los_cl: smem attribute");
@@ -1362,7 +1392,7 @@ int launch_tc(const gcamb_grid *g, const TcPlan &pl, const float *S, const doubl
   }
   if (pl.nitems > 0) {
     int *ctr = reinterpret_cast<int *>(ws + pl.off_ctr);
-    TcParams prm{static_cast<const char *>(t.d_data), t.d_off, t.d_nkb, sp, wp, sc, nullptr, -1,
+    TcParams prm{static_cast<const char *>(t.d_data), nullptr, t.d_off, t.d_nkb, sp, wp, sc, nullptr, -1,
                  pl.items(B), ctr, pl.nitems, part, use_err_word ? err_word : device_error_flag(), g->nlt, pl.n_mt,
                  pl.nkbs, pl.mpad};
     if (!prm.err && !use_err_word) return fail(GCAMB_ECUDA, "los_cl: error flag allocation");
@@ -1479,21 +1509,78 @@ int launch_tc_te(const gcamb_grid *g, const TcPlan &pl, const float *ST, const f
     const int r2 = (g->lmin <= 2 && g->lmax >= 2 && g->rowof[2 - g->lmin] >= 0 && g->rowof[2 - g->lmin] < kTileL)
                        ? g->rowof[2 - g->lmin]
                        : -1;
-    TcParams prm{static_cast<const char *>(t.d_data), t.d_off, t.d_nkb, nullptr, wp, tail, ix2, r2,
+    TcParams prm{static_cast<const char *>(t.d_data), nullptr, t.d_off, t.d_nkb, nullptr, wp, tail, ix2, r2,
                  pl.items(B), ctr, pl.nitems, part, device_error_flag(), g->nlt, pl.n_mt, pl.nkbs, pl.mpad};
     if (!prm.err) return fail(GCAMB_ECUDA, "los_cl_te: error flag allocation");
-    if (int rc = launch_tc_kernel<NT, kBF16, true, true>(g, pl, tm1, tm2, prm, st)) return rc;
+    if (int rc = launch_tc_kernel<NT, kBF16, true, 1>(g, pl, tm1, tm2, prm, st)) return rc;
   }
   dim3 rgrid(H, pl.ntile);
   ProfScope prof(GCAMB_K_REDUCE, st);
   reduce_te_kernel<<<rgrid, 128, 0, st>>>(part, B + pl.o_tile_ptr, B + pl.o_tile_items, H, pl.n_mt, pl.M, g->nl,
-                                          g->d_lrow, ClTT, ClEE, ClTE);
+                                          g->d_lrow, 1, ClTT, ClEE, ClTE);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "los_cl_te: launch");
   return GCAMB_OK;
 }
 
+// A pair of kernel grids X, Y with the same layout: C^XX, C^YY, C^XY of the
+// sources SX (with X's table) and SY (with Y's table), e.g. tensor T and E.
+template <int NT>
+int launch_tc_pair(const gcamb_grid *gx, const gcamb_grid *gy, const TcPlan &pl, const float *SX, const float *SY,
+                   const double *Pk, double *ClXX, double *ClYY, double *ClXY, char *ws, cudaStream_t st) {
+  constexpr int H = NT / 2;
+  const Table &tx = gx->tab[GCAMB_BF16X3], &ty = gy->tab[GCAMB_BF16X3];
+  float *wp = reinterpret_cast<float *>(ws + pl.off_wp);
+  float *tail = reinterpret_cast<float *>(ws + pl.off_sc);
+  float *part = reinterpret_cast<float *>(ws + pl.off_part);
+  const int *B = pl.d_blob;
+  CUtensorMap tm1, tm2;
+  memset(&tm1, 0, sizeof tm1);
+  memset(&tm2, 0, sizeof tm2);
+  if (int rc = encode_sources(&tm1, SX, pl.M, gx->nk, gx->ntau, H)) return rc;
+  if (int rc = encode_sources(&tm2, SY, pl.M, gx->nk, gx->ntau, H)) return rc;
+  {
+    ProfScope prof(GCAMB_K_SPLIT, st);
+    const size_t rows = (size_t)gx->nk * pl.mpad;
+    // weights; no small-x tails (the kernel tables hold the series): x_lo < 0
+    te_weights_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(Pk, gx->d_wk, gx->d_k, gx->d_tau, gx->tau0, -1.0,
+                                                                      gx->d_wtau, SY, pl.M, gx->nk, gx->ntau, pl.mpad,
+                                                                      wp, tail);
+  }
+  if (pl.nitems > 0) {
+    int *ctr = reinterpret_cast<int *>(ws + pl.off_ctr);
+    TcParams prm{static_cast<const char *>(tx.d_data), static_cast<const char *>(ty.d_data), tx.d_off, tx.d_nkb,
+                 nullptr, wp, tail, nullptr, -1, pl.items(B), ctr, pl.nitems, part, device_error_flag(), gx->nlt,
+                 pl.n_mt, pl.nkbs, pl.mpad};
+    if (!prm.err) return fail(GCAMB_ECUDA, "los_cl_pair: error flag allocation");
+    if (int rc = launch_tc_kernel<NT, kBF16, true, 2>(gx, pl, tm1, tm2, prm, st)) return rc;
+  }
+  dim3 rgrid(H, pl.ntile);
+  ProfScope prof(GCAMB_K_REDUCE, st);
+  reduce_te_kernel<<<rgrid, 128, 0, st>>>(part, B + pl.o_tile_ptr, B + pl.o_tile_items, H, pl.n_mt, pl.M, gx->nl,
+                                          gx->d_lrow, 0, ClXX, ClYY, ClXY);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "los_cl_pair: launch");
+  return GCAMB_OK;
+}
+
 }  // namespace
+
+int launch_los_cl_pair(const gcamb_grid *gx, const gcamb_grid *gy, const float *SX, const float *SY,
+                       const double *Pk, int M, double *ClXX, double *ClYY, double *ClXY, void *ws, size_t ws_bytes,
+                       cudaStream_t st) {
+  const Table &tx = gx->tab[GCAMB_BF16X3], &ty = gy->tab[GCAMB_BF16X3];
+  if (gx->k != gy->k || gx->tau != gy->tau || gx->tau0 != gy->tau0 || gx->lrow != gy->lrow || tx.nkb != ty.nkb ||
+      tx.off != ty.off)
+    return fail(GCAMB_EINVAL, "los_cl_pair: the two grids must share k, tau, tau0, the multipoles and the table layout");
+  int rc = 0;
+  TcPlan *pl = get_plan_te(gx, M, &rc);
+  if (!pl) return rc ? rc : fail(GCAMB_ECUDA, "los_cl_pair: plan");
+  if (ws_bytes < pl->ws_bytes) return fail(GCAMB_EINVAL, "los_cl_pair: workspace too small");
+  char *w = static_cast<char *>(ws);
+  return pl->NT == 32 ? launch_tc_pair<64>(gx, gy, *pl, SX, SY, Pk, ClXX, ClYY, ClXY, w, st)
+                      : launch_tc_pair<128>(gx, gy, *pl, SX, SY, Pk, ClXX, ClYY, ClXY, w, st);
+}
 
 size_t los_cl_te_workspace_bytes(const gcamb_grid *g, int M) {
   int rc = 0;

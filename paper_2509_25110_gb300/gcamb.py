@@ -74,6 +74,8 @@ def lib():
     L.gcamb_interp_sources.argtypes = [_vp, _vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp,
                                        ctypes.c_size_t, _vp]
     L.gcamb_los_transfer_tensor.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp]
+    L.gcamb_los_cl_pair.argtypes = [_vp, _vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp,
+                                    ctypes.c_size_t, _vp]
     L.gcamb_los_cl_te_workspace.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
     L.gcamb_los_cl_te.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp,
                                   ctypes.c_size_t, _vp]
@@ -432,6 +434,25 @@ def los_cl_te(g: Grid, ST, SP, Pk, mode: int = BF16X3, out=None, ws=None, stream
                                  _dev(te, torch.float64, (M, g.nl), "ClTE"), _dev(ws, torch.uint8, name="ws"),
                                  ws.numel(), _stream(stream)))
     return tt, ee, te
+
+
+def los_cl_pair(gx: Grid, gy: Grid, SX, SY, Pk, out=None, ws=None, stream=None):
+    """Two fields on kernel grids with the same layout (e.g. tensor T and E),
+    batched on the tensor cores: -> (C^XX, C^YY, C^XY), each [M][nl] FP64."""
+    import torch
+    M = SX.shape[0]
+    if ws is None:
+        ws = torch.empty(max(1, los_cl_te_workspace(gx, M)), dtype=torch.uint8, device=SX.device)
+    if out is None:
+        out = tuple(torch.empty((M, gx.nl), dtype=torch.float64, device=SX.device) for _ in range(3))
+    xx, yy, xy = out
+    _check(lib().gcamb_los_cl_pair(gx.handle, gy.handle, _dev(SX, torch.float32, (M, gx.nk, gx.ntau), "SX"),
+                                   _dev(SY, torch.float32, (M, gx.nk, gx.ntau), "SY"),
+                                   _dev(Pk, torch.float64, (M, gx.nk), "Pk"), M, BF16X3,
+                                   _dev(xx, torch.float64, (M, gx.nl), "ClXX"), _dev(yy, torch.float64, (M, gx.nl), "ClYY"),
+                                   _dev(xy, torch.float64, (M, gx.nl), "ClXY"), _dev(ws, torch.uint8, name="ws"),
+                                   ws.numel(), _stream(stream)))
+    return xx, yy, xy
 
 
 class Plan:

@@ -131,3 +131,42 @@ def test_kernel_grid_rules():
         gcamb.grid_set_kernel(gc, gcamb.KERNEL_EPS)
     assert ei.value.code == gcamb.EUNSUPPORTED
     gcamb.sync()
+
+
+def test_pair_gives_tensor_te(orc):
+    """gcamb_los_cl_pair on the tensor T and E kernel grids: C^TT, C^EE and
+    C^TE of the tensor sources from one launch, against the oracle (the split
+    bound, C^TE with |Delta_T| A_E + |Delta_E| A_T)."""
+    k = synth.log_grid(1e-4, 3000.0 / 14000.0, 120)
+    tau = synth.uniform_grid(200.0, 14000.0, 400)
+    M, lmax = 70, 800
+    p = synth.model_params(M, seed=74)
+    ST, SP = synth.sources_tensor(k, tau, p, np.float32)
+    P = synth.primordial_tensor(k, p)
+    gT = kgrid(k, tau, 2, lmax, gcamb.KERNEL_EPS)
+    gE = kgrid(k, tau, 2, lmax, gcamb.KERNEL_TENSOR_E)
+    gcamb.bessel_table(gT, gcamb.BF16X3)
+    gcamb.bessel_table(gE, gcamb.BF16X3)
+    tt, ee, te = (x.cpu().numpy() for x in gcamb.los_cl_pair(gT, gE, dev(ST, torch.float32), dev(SP, torch.float32),
+                                                               dev(P)))
+    gcamb.sync()
+    sub = [0, 35, 69]
+    DT, DE, _ = orc.los_tensor(k, tau, 14000.0, 2, lmax, ST[sub].astype(np.float64), SP[sub].astype(np.float64))
+    w = orc.trapz_weights(tau)
+    x = (k[:, None] * (14000.0 - tau[None, :])).ravel()
+    kt, ke, _ = (np.abs(a).reshape(k.size, tau.size, -1)[:, :, 2:] for a in orc.tensor_kernels(x, lmax))
+    AT = np.einsum("mki,kil->mkl", np.abs(ST[sub].astype(np.float64)) * w, kt)
+    AE = np.einsum("mki,kil->mkl", np.abs(SP[sub].astype(np.float64)) * w, ke)
+    f = 4.0 * np.pi * orc.lnk_weights(k)[None, :, None] * P[sub][:, :, None]
+    u = 3 * 2.0 ** -16 + tau.size * 2.0 ** -24
+    for name, c, DX, DY, AX, AY in (("TT", tt, DT, DT, AT, AT), ("EE", ee, DE, DE, AE, AE), ("TE", te, DT, DE, AT, AE)):
+        ref = orc.cl_cross(k, DX, DY, P[sub])
+        bound = u * (f * (np.abs(DX) * AY + np.abs(DY) * AX)).sum(axis=1)
+        assert np.all(np.abs(c[sub] - ref) <= bound), (name, np.max(np.abs(c[sub] - ref) / bound))
+    # grids of another layout are rejected
+    gB = kgrid(k, tau, 2, lmax - 1, gcamb.KERNEL_TENSOR_B)
+    gcamb.bessel_table(gB, gcamb.BF16X3)
+    with pytest.raises(gcamb.GcambError) as ei:
+        gcamb.los_cl_pair(gT, gB, dev(ST, torch.float32), dev(SP, torch.float32), dev(P))
+    assert ei.value.code == gcamb.EINVAL
+    gcamb.sync()
