@@ -513,6 +513,32 @@ def run_tensor(args):
                                                                                 v).max())
                                           for k, v in refb.items()}
         batched[mname] = b
+        if bmode == gcamb.BF16X3:
+            # TT, EE and TE from one launch on the T and E kernel grids, BB from the B grid
+            gT, gE, gB = grids["TT"][0], grids["EE"][0], grids["BB"][0]
+            wsp = torch.empty(gcamb.los_cl_te_workspace(gT, Mb), dtype=torch.uint8, device=dev)
+            outp = tuple(torch.empty((Mb, wl.nl), dtype=torch.float64, device=dev) for _ in range(3))
+
+            def pstep():
+                gcamb.los_cl_pair(gT, gE, STb, SPb, Pb, out=outp, ws=wsp)
+                gcamb.los_cl(gB, SPb, Pb, bmode, grids["BB"][2], grids["BB"][1])
+            for _ in range(3):
+                pstep()
+            gcamb.sync()
+            pms, _ = _timed_region(pstep, bsteps, dev)
+            gcamb.sync()
+            pb_ = {"models_per_s": Mb * bsteps / (pms * 1e-3), "ms_per_step": pms / bsteps,
+                   "spectra": "TT, EE, TE (pair) + BB"}
+            if refb is not None:
+                te_ref = oracle.cl_cross(wl.k, R1[0], R1[1], P1b)
+                tt1, ee1, te1 = (x[:1].cpu().numpy() for x in outp)
+                pb_["max_rel_err_vs_oracle"] = {"TT": float(np.max(np.abs(tt1 / refb["TT"] - 1))),
+                                                "EE": float(np.max(np.abs(ee1 / refb["EE"] - 1))),
+                                                "TE_on_sqrt_TT_EE": float(np.max(np.abs(te1 - te_ref) /
+                                                                                 np.sqrt(refb["TT"] * refb["EE"])))}
+                pb_["max_dcl_over_sigma_cv_TE"] = float(oracle.cosmic_variance_ratio_te(te1, refb["TT"], refb["EE"],
+                                                                                        te_ref).max())
+            batched["bf16x3_pair_tt_ee_te_plus_bb"] = pb_
         for gk, *_ in grids.values():
             gk.close()
     r64 = res["plain64"]
