@@ -389,7 +389,7 @@ int gcamb_los_cl_pair(const gcamb_grid *gx, const gcamb_grid *gy, const float *S
  */
 typedef struct gcamb_plan gcamb_plan;
 
-#define GCAMB_PLAN_INFO_N 9
+#define GCAMB_PLAN_INFO_N 10
 
 int gcamb_plan_create(gcamb_grid *g, int M, const int *lmax_m, const int *nk_m, int mode, int tune,
                       gcamb_plan **out);
@@ -418,7 +418,9 @@ int gcamb_plan_launch(gcamb_plan *p, const float *S, const double *Pk, double *C
  * (0 before tuning), [1] work items, [2] persistent CTAs, [3] graph captures,
  * [4] graph replays, [5] 1 if the width came from timing (now or cached),
  * [6] M, [7] workspace bytes of the width in use, [8] 1 if the sources are
- * read in place (fused kernel, no split pass: uniform batches only).
+ * read in place (fused kernel, no split pass: uniform batches only), [9]
+ * multipole tiles per work item (2 when adjacent 128-multipole tiles share
+ * each loaded and split source block: the in-place kernel; else 1).
  */
 int gcamb_plan_info(const gcamb_plan *p, int64_t *info);
 

@@ -174,30 +174,43 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 // third of the accumulate steps (the tensor core's FP32 accumulation error
 // grows with their number); D_x is ~2^-8 of D_hh, so its own rounding is
 // negligible.  The pairs are double-buffered across k when TMEM allows.
-template <int NT, int MODE, int NA = 1>
+//
+// LP = 2: an item covers two adjacent l-tiles; a stage holds the table block
+// of each and one source block, which both multiply (the sources are loaded
+// and split once for the two tiles).  Each tile has its own accumulator pair
+// and barriers; 16 epilogue warps, 8 per tile.
+template <int NT, int MODE, int NA = 1, int LP = 1>
 struct TcCfg {
   static constexpr int kABytes = TcGeom<MODE>::kABytes;
   static constexpr int kBBytes = 2 * NT * TcGeom<MODE>::kRowB;  // hi + lo planes of NT rows
-  static constexpr int kStageBytes = NA * kABytes + kBBytes;     // NA table blocks (pair: 2)
+  static constexpr int kStageBytes = NA * kABytes + kBBytes;     // NA table blocks (pair, LP = 2: 2)
   static constexpr int kStages = (kSmemBudget / kStageBytes) > 8 ? 8 : (kSmemBudget / kStageBytes);
-  static constexpr int kNBuf = (4 * NT <= 512) ? 2 : 1;
-  static constexpr int kTmemCols = kNBuf * 2 * NT < 32 ? 32 : kNBuf * 2 * NT;
+  static constexpr int kNBuf = (LP * 4 * NT <= 512) ? 2 : 1;
+  static constexpr int kTB = kNBuf * LP;                 // accumulator pairs (TMEM) and their barrier pairs
+  static constexpr int kTmemCols = kTB * 2 * NT < 32 ? 32 : kTB * 2 * NT;
   static constexpr int kKSlots = 4;                      // per-k records in flight
   static constexpr int kSlotBytes = 16 + 8 * NT;         // header, weights, row scales
-  static constexpr int kQBytes = kKChunkMax * 12;        // the item's block counts and offsets
+  static constexpr int kQBytes = kKChunkMax * 12 * LP;   // the item's block counts and offsets
   static constexpr int kFBytes = kStages * 128;          // TE: 1/x^2 of each stage's 32 nodes
   static constexpr int kSmemBytes =
       kStages * kStageBytes + kFBytes + kKSlots * kSlotBytes + kQBytes + 1024 /*align*/ + 512 /*barriers*/;
   static constexpr int kColsPerThread = NT / 2;
-  static constexpr int kChunk = NT >= 128 ? 8 : 16;      // TMEM load width (register budget)
+  // TMEM load width (register budget: 22 warps leave 88 registers a thread)
+  static constexpr int kChunk = NT >= 128 ? (LP == 2 ? 4 : 8) : 16;
 };
 
-template <bool FUSED, int TE = 0>
+// Warp roles.  LP = 2 keeps each role in whole warpgroups (warps 2, 3 idle)
+// so that the warpgroups can trade registers: launched at 80 a thread (24
+// warps), the producer/MMA and converter warpgroups drop to 64 and the four
+// epilogue warpgroups take 88 (8 x 64 + 16 x 88 = 24 x 80).
+template <bool FUSED, int TE = 0, int LP = 1>
 struct TcRoles {
   static constexpr int kConv = FUSED ? kConvWarps : 0;
-  static constexpr int kEpi0 = 2 + kConv;  // first epilogue warp
-  static constexpr int kEpi = kEpiWarps;
-  static constexpr int kThreadsT = 32 * (2 + kConv + kEpi);
+  static constexpr int kConv0 = LP == 2 ? 4 : 2;  // first converter warp
+  static constexpr int kEpi0 = kConv0 + kConv;    // first epilogue warp
+  static constexpr int kEpi = kEpiWarps * LP;
+  static constexpr int kThreadsT = 32 * (kEpi0 + kEpi);
+  static constexpr int kRegLow = 64, kRegHigh = 88;  // LP = 2 split
 };
 
 // Per-k record, written by the producer into a ring in shared memory:
@@ -220,34 +233,38 @@ constexpr int kFirst = 1 << 16, kLast = 1 << 17, kL2 = 1 << 18;
 // that the shared table of w_i j_l gives D_E' = sum_i w_i j_l S_P / x^2; the
 // epilogue adds the l = 2 small-x tail and accumulates, per model,
 // (w D_T)^2, (w D_E')^2 and w^2 D_T D_E'; the reduce applies c_l^2 and c_l.
-template <int NT, int MODE, bool FUSED, int TE = 0>
-__global__ void __launch_bounds__(TcRoles<FUSED, TE>::kThreadsT, 1)
+template <int NT, int MODE, bool FUSED, int TE = 0, int LP = 1>
+__global__ void __launch_bounds__(TcRoles<FUSED, TE, LP>::kThreadsT, 1)
     los_cl_tc_kernel(const __grid_constant__ CUtensorMap tm_src, const __grid_constant__ CUtensorMap tm_src2,
                      TcParams p) {
   static_assert(!TE || (FUSED && MODE == kBF16 && NT <= 128), "TE: fused bf16, NT <= 128");
-  using C = TcCfg<NT, MODE, TE == 2 ? 2 : 1>;
+  static_assert(LP == 1 || (LP == 2 && !TE && FUSED && MODE != kTF32 && NT <= 128),
+                "LP = 2: fused bf16/fp16 without TE, NT <= 128");
+  using C = TcCfg<NT, MODE, (TE == 2 || LP == 2) ? 2 : 1, LP>;
   using G = TcGeom<MODE>;
-  using R = TcRoles<FUSED, TE>;
+  using R = TcRoles<FUSED, TE, LP>;
   constexpr int S = C::kStages;
   constexpr int NB = C::kNBuf;
+  constexpr int TB = C::kTB;
   constexpr int KS = C::kKSlots;
   constexpr bool kScale = FUSED && MODE == kF16;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   unsigned char *fbuf = smem + S * C::kStageBytes;  // TE: [S][32] floats
   unsigned char *kslots = fbuf + C::kFBytes;
-  int64_t *q_off = reinterpret_cast<int64_t *>(kslots + KS * C::kSlotBytes);  // [kKChunkMax]
-  int32_t *q_nb = reinterpret_cast<int32_t *>(q_off + kKChunkMax);           // [kKChunkMax]
+  int64_t *q_off = reinterpret_cast<int64_t *>(kslots + KS * C::kSlotBytes);  // [LP][kKChunkMax]
+  int32_t *q_nb = reinterpret_cast<int32_t *>(q_off + LP * kKChunkMax);      // [LP][kKChunkMax]
   uint64_t *bars = reinterpret_cast<uint64_t *>(kslots + KS * C::kSlotBytes + C::kQBytes);
-  // bars: full[S], empty[S], conv[S], kfull[KS], kempty[KS], tfull[2],
-  //       tempty[2], drain, (tmem slot), (abort)
+  // bars: full[S], empty[S], conv[S], kfull[KS], kempty[KS], tfull[TB],
+  //       tempty[TB], drain, (tmem slot), (abort); accumulator pair
+  //       buf * LP + tile sits at TMEM column (buf * LP + tile) * 2 NT
   uint64_t *b1 = bars + 3 * S + 2 * KS;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(b1 + 5);
-  volatile int *abort_flag = reinterpret_cast<volatile int *>(b1 + 6);
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(b1 + 2 * TB + 1);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(b1 + 2 * TB + 2);
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + S), conv0 = smem_u32(bars + 2 * S);
   const uint32_t kfull0 = smem_u32(bars + 3 * S), kempty0 = smem_u32(bars + 3 * S + KS);
-  const uint32_t tfull0 = smem_u32(b1), tempty0 = smem_u32(b1 + 2);
-  const uint32_t drain = smem_u32(b1 + 4);
+  const uint32_t tfull0 = smem_u32(b1), tempty0 = smem_u32(b1 + TB);
+  const uint32_t drain = smem_u32(b1 + 2 * TB);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
@@ -260,10 +277,10 @@ __global__ void __launch_bounds__(TcRoles<FUSED, TE>::kThreadsT, 1)
       mbar_init(kfull0 + 8 * s, 1);
       mbar_init(kempty0 + 8 * s, 1 + R::kEpi + R::kConv);
     }
-    mbar_init(tfull0, 1);
-    mbar_init(tfull0 + 8, 1);
-    mbar_init(tempty0, R::kEpi);
-    mbar_init(tempty0 + 8, R::kEpi);
+    for (int b = 0; b < TB; ++b) {
+      mbar_init(tfull0 + 8 * b, 1);
+      mbar_init(tempty0 + 8 * b, kEpiWarps);  // the 8 epilogue warps of the pair's tile
+    }
     mbar_init(drain, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -283,229 +300,524 @@ __global__ void __launch_bounds__(TcRoles<FUSED, TE>::kThreadsT, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  if (warp == 0) {
-    // ---------------- producer: items from the counter; the whole warp loads
-    // the item's block counts and table offsets into shared memory (one
-    // round trip per item), then lane 0 writes per non-empty k a record and
-    // issues the k's table and source blocks into the stage ring
-    int stage = 0;
-    uint32_t phase = 0;
-    int armed_phase[S];
+  // Roles.  Each register change sits in its warpgroups' own branch, so that
+  // the code it covers is compiled to its budget.
+  if (warp < R::kEpi0) {
+    if constexpr (LP == 2) {
+      static_assert(R::kThreadsT == 768 && R::kEpi0 == 8, "LP = 2 register split: 6 warpgroups");
+      asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(R::kRegLow));
+    }
+    if (warp == 0) {
+      // ---------------- producer: items from the counter; the whole warp loads
+      // the item's block counts and table offsets into shared memory (one
+      // round trip per item), then lane 0 writes per non-empty k a record and
+      // issues the k's table and source blocks into the stage ring
+      int stage = 0;
+      uint32_t phase = 0;
+      int armed_phase[S];
 #pragma unroll
-    for (int s = 0; s < S; ++s) armed_phase[s] = -1;
-    int ks = 0;
-    uint32_t kph = 0;
-    int karmed[C::kKSlots];
+      for (int s = 0; s < S; ++s) armed_phase[s] = -1;
+      int ks = 0;
+      uint32_t kph = 0;
+      int karmed[C::kKSlots];
 #pragma unroll
-    for (int s = 0; s < KS; ++s) karmed[s] = -1;
-    bool ok = true;
-    while (ok) {
-      int item = 0;
-      if (lane == 0) item = atomicAdd(p.counter, 1);
-      item = __shfl_sync(0xffffffffu, item, 0);
-      if (item >= p.nitems) break;
-      const TcItem it = p.items[item];
-      const int cnt = min(it.qe - it.qb, kKChunkMax);  // the plan keeps items within kKChunkMax k
-      for (int j = lane; j < cnt; j += 32) {
-        const size_t e = (size_t)(it.qb + j) * p.nlt + it.lt;
-        q_nb[j] = p.nkb[e];
-        q_off[j] = p.off[e];
+      for (int s = 0; s < KS; ++s) karmed[s] = -1;
+      bool ok = true;
+      while (ok) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(p.counter, 1);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= p.nitems) break;
+        const TcItem it = p.items[item];
+        const int cnt = min(it.qe - it.qb, kKChunkMax);  // the plan keeps items within kKChunkMax k
+        for (int j = lane; j < cnt; j += 32) {
+          const size_t e = (size_t)(it.qb + j) * p.nlt + it.lt;
+          q_nb[j] = p.nkb[e];
+          q_off[j] = p.off[e];
+          if constexpr (LP == 2) {  // the pair's second tile (none past the last)
+            const bool has2 = it.lt + 1 < p.nlt;
+            q_nb[kKChunkMax + j] = has2 ? p.nkb[e + 1] : 0;
+            q_off[kKChunkMax + j] = has2 ? p.off[e + 1] : 0;
+          }
+        }
+        __syncwarp();
+        if (lane == 0) {
+          for (int j = 0; j < cnt && ok; ++j) {
+            const int q = it.qb + j;
+            const int nb0 = q_nb[j];
+            const int nb1 = LP == 2 ? q_nb[kKChunkMax + j] : 0;
+            const int nb = max(nb0, nb1);
+            if (nb == 0) continue;
+            // the k's record
+            if (!mbar_wait(kempty0 + 8 * ks, kph ^ 1u, abort_flag, p.err)) {
+              ok = false;
+              break;
+            }
+            unsigned char *rec = kslots + ks * C::kSlotBytes;
+            volatile int *hdr = reinterpret_cast<volatile int *>(rec);
+            hdr[0] = q;
+            hdr[1] = LP == 2 ? (nb0 | (nb1 << 16)) : nb;  // LP = 2: both tiles' block counts (< 2^15 each)
+            hdr[2] = item;
+            hdr[3] = it.mt | (q == it.qb ? kFirst : 0) | (q == it.qe - 1 ? kLast : 0) | (TE && it.lt == 0 ? kL2 : 0);
+            const uint32_t kb_bar = kfull0 + 8 * ks;
+            karmed[ks] = (int)kph;
+            if constexpr (TE) {
+              // NT/2 models: weights, then the l = 2 tails
+              mbar_expect_tx(kb_bar, NT * 4);
+              const size_t wrow = (size_t)q * p.mpad + (size_t)it.mt * (NT / 2);
+              bulk_g2s(smem_u32(rec + 16), p.wp + wrow, NT * 2, kb_bar);
+              bulk_g2s(smem_u32(rec + 16 + NT * 2), p.sc + wrow, NT * 2, kb_bar);
+            } else {
+              mbar_expect_tx(kb_bar, (kScale ? 2 : 1) * NT * 4);
+              const size_t wrow = (size_t)q * p.mpad + (size_t)it.mt * NT;
+              bulk_g2s(smem_u32(rec + 16), p.wp + wrow, NT * 4, kb_bar);
+              if constexpr (kScale) bulk_g2s(smem_u32(rec + 16 + NT * 4), p.sc + wrow, NT * 4, kb_bar);
+            }
+            if (++ks == KS) {
+              ks = 0;
+              kph ^= 1u;
+            }
+            const char *a = p.table + (size_t)q_off[j] * C::kABytes;
+            const char *b = FUSED ? nullptr : p.sp + ((size_t)q * p.n_mt + it.mt) * (size_t)p.nkbs * C::kBBytes;
+            for (int kb = 0; kb < nb; ++kb) {
+              if (!mbar_wait(empty0 + 8 * stage, phase ^ 1u, abort_flag, p.err)) {
+                ok = false;
+                break;
+              }
+              const uint32_t sa = smem_u32(smem + stage * C::kStageBytes);
+              armed_phase[stage] = (int)phase;
+              if constexpr (LP == 2) {
+                // the tiles' blocks while each has some, then the source block
+                const bool u0 = kb < nb0, u1 = kb < nb1;
+                mbar_expect_tx(full0 + 8 * stage, (u0 ? C::kABytes : 0) + (u1 ? C::kABytes : 0) + C::kBBytes);
+                if (u0) bulk_g2s(sa, a + (size_t)kb * C::kABytes, C::kABytes, full0 + 8 * stage);
+                if (u1)
+                  bulk_g2s(sa + C::kABytes, p.table + ((size_t)q_off[kKChunkMax + j] + kb) * C::kABytes, C::kABytes,
+                           full0 + 8 * stage);
+                tma_load_3d(sa + 2 * C::kABytes, &tm_src, kb * 32, q, it.mt * NT, full0 + 8 * stage);
+                if (++stage == S) {
+                  stage = 0;
+                  phase ^= 1u;
+                }
+                continue;
+              }
+              mbar_expect_tx(full0 + 8 * stage, C::kStageBytes + (TE == 1 ? 128 : 0));
+              bulk_g2s(sa, a + (size_t)kb * C::kABytes, C::kABytes, full0 + 8 * stage);
+              if constexpr (TE == 2)  // the second field's table block
+                bulk_g2s(sa + C::kABytes, p.table2 + (size_t)q_off[j] * C::kABytes + (size_t)kb * C::kABytes,
+                         C::kABytes, full0 + 8 * stage);
+              if constexpr (TE == 1)  // the block's 32 values of 1/x^2
+                bulk_g2s(smem_u32(fbuf + stage * 128), p.ix2 + ((size_t)q * p.nkbs + kb) * 32, 128, full0 + 8 * stage);
+              constexpr int kBOff = (TE == 2 ? 2 : 1) * C::kABytes;  // the source region of the stage
+              if constexpr (TE) {  // FP32 boxes [NT/2 models][1 k][32 tau] of the two fields
+                tma_load_3d(sa + kBOff, &tm_src, kb * 32, q, it.mt * (NT / 2), full0 + 8 * stage);
+                tma_load_3d(sa + kBOff + (NT / 2) * 128, &tm_src2, kb * 32, q, it.mt * (NT / 2),
+                            full0 + 8 * stage);
+              } else if constexpr (FUSED)  // FP32 box [NT sources][1 k][32 tau]; zero beyond ntau and M
+                tma_load_3d(sa + kBOff, &tm_src, kb * 32, q, it.mt * NT, full0 + 8 * stage);
+              else
+                bulk_g2s(sa + kBOff, b + (size_t)kb * C::kBBytes, C::kBBytes, full0 + 8 * stage);
+              if (++stage == S) {
+                stage = 0;
+                phase ^= 1u;
+              }
+            }
+          }
+        }
+        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;  // also orders lane 0's reads before the next item's writes
       }
-      __syncwarp();
       if (lane == 0) {
-        for (int j = 0; j < cnt && ok; ++j) {
-          const int q = it.qb + j;
-          const int nb = q_nb[j];
-          if (nb == 0) continue;
-          // the k's record
-          if (!mbar_wait(kempty0 + 8 * ks, kph ^ 1u, abort_flag, p.err)) {
-            ok = false;
-            break;
-          }
-          unsigned char *rec = kslots + ks * C::kSlotBytes;
-          volatile int *hdr = reinterpret_cast<volatile int *>(rec);
-          hdr[0] = q;
-          hdr[1] = nb;
-          hdr[2] = item;
-          hdr[3] = it.mt | (q == it.qb ? kFirst : 0) | (q == it.qe - 1 ? kLast : 0) | (TE && it.lt == 0 ? kL2 : 0);
-          const uint32_t kb_bar = kfull0 + 8 * ks;
-          karmed[ks] = (int)kph;
-          if constexpr (TE) {
-            // NT/2 models: weights, then the l = 2 tails
-            mbar_expect_tx(kb_bar, NT * 4);
-            const size_t wrow = (size_t)q * p.mpad + (size_t)it.mt * (NT / 2);
-            bulk_g2s(smem_u32(rec + 16), p.wp + wrow, NT * 2, kb_bar);
-            bulk_g2s(smem_u32(rec + 16 + NT * 2), p.sc + wrow, NT * 2, kb_bar);
-          } else {
-            mbar_expect_tx(kb_bar, (kScale ? 2 : 1) * NT * 4);
-            const size_t wrow = (size_t)q * p.mpad + (size_t)it.mt * NT;
-            bulk_g2s(smem_u32(rec + 16), p.wp + wrow, NT * 4, kb_bar);
-            if constexpr (kScale) bulk_g2s(smem_u32(rec + 16 + NT * 4), p.sc + wrow, NT * 4, kb_bar);
-          }
+        // end-of-work record (no copies)
+        if (ok && mbar_wait(kempty0 + 8 * ks, kph ^ 1u, abort_flag, p.err)) {
+          reinterpret_cast<volatile int *>(kslots + ks * C::kSlotBytes)[1] = -1;
+          mbar_arrive(kfull0 + 8 * ks);
+          karmed[ks] = (int)kph;  // this phase completes now; the drain below must not wait for a later one
+        }
+        // no copy may still be landing when the CTA exits
+        for (int s = 0; s < S; ++s)
+          if (armed_phase[s] >= 0) mbar_wait(full0 + 8 * s, (uint32_t)armed_phase[s], nullptr, p.err);
+        for (int s = 0; s < KS; ++s)
+          if (karmed[s] >= 0) mbar_wait(kfull0 + 8 * s, (uint32_t)karmed[s], nullptr, p.err);
+      }
+    } else if (warp == 1) {
+      if (lane == 0) {
+        // ---------------- MMA issuer
+        constexpr uint32_t fmt = MODE == kTF32 ? 2u : (MODE == kBF16 ? 1u : 0u);
+        constexpr uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(NT >> 3) << 17) |
+                                   ((uint32_t)(128 >> 4) << 24);
+        // With NT <= 128 the hi and lo source planes are one operand of 2 NT
+        // rows and D_hh, D_x adjacent TMEM columns, so hi*hi and hi*lo are one
+        // MMA of N = 2 NT: each K step reads A_hi once (shared-memory bandwidth
+        // bounds these MMAs).
+        constexpr bool kPair = 2 * NT <= 256;
+        constexpr uint32_t idesc2 = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)((2 * NT) >> 3) << 17) |
+                                    ((uint32_t)(128 >> 4) << 24);
+        int stage = 0;
+        uint32_t phase = 0;
+        int n = 0;
+        int ks = 0;
+        uint32_t kph = 0;
+        int nt2[2] = {0, 0};  // LP = 2: k's accumulated so far per tile
+        while (true) {
+          if (!mbar_wait(kfull0 + 8 * ks, kph, abort_flag, p.err)) break;
+          const int hv = reinterpret_cast<volatile int *>(kslots + ks * C::kSlotBytes)[1];
+          if (hv < 0) break;
+          mbar_arrive(kempty0 + 8 * ks);
           if (++ks == KS) {
             ks = 0;
             kph ^= 1u;
           }
-          const char *a = p.table + (size_t)q_off[j] * C::kABytes;
-          const char *b = FUSED ? nullptr : p.sp + ((size_t)q * p.n_mt + it.mt) * (size_t)p.nkbs * C::kBBytes;
+          if constexpr (LP == 2) {
+            // per tile: its block count, its accumulator pair (waited for just
+            // before the tile's first MMA of this k)
+            const int nbt[2] = {hv & 0xFFFF, hv >> 16};
+            const int nb = max(nbt[0], nbt[1]);
+            uint32_t dt[2];
+            int bt[2];
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+              bt[t] = (nt2[t] % NB) * LP + t;
+              dt[t] = tmem + (uint32_t)(bt[t] * 2 * NT);
+            }
+            bool ok = true;
+            for (int kb = 0; kb < nb && ok; ++kb) {
+              if (!mbar_wait(conv0 + 8 * stage, phase, abort_flag, p.err) ||
+                  !mbar_wait(full0 + 8 * stage, phase, abort_flag, p.err)) {
+                ok = false;
+                break;
+              }
+              tc_fence_after();
+              const uint32_t sa = smem_u32(smem + stage * C::kStageBytes);
+              const uint32_t sb = sa + 2 * C::kABytes;
+#pragma unroll
+              for (int t = 0; t < 2; ++t) {
+                if (kb >= nbt[t]) continue;
+                if (kb == 0) {
+                  if (!mbar_wait(tempty0 + 8 * bt[t], ((uint32_t)(nt2[t] / NB) & 1u) ^ 1u, abort_flag, p.err)) {
+                    ok = false;
+                    break;
+                  }
+                  tc_fence_after();
+                }
+                const uint32_t at = sa + t * C::kABytes;
+#pragma unroll
+                for (int kk = 0; kk < G::kKSteps; ++kk) {
+                  const uint64_t ah = G::desc(at + kk * 32), al = G::desc(at + G::kPlaneA + kk * 32);
+                  const uint64_t bh = G::desc(sb + kk * 32);
+                  const uint32_t accum = (kb | kk) ? 1u : 0u;
+                  mma<MODE>(dt[t], ah, bh, idesc2, accum);  // [D_hh | D_x] (+)= A_hi [B_hi | B_lo]
+                  mma<MODE>(dt[t] + NT, al, bh, idesc, 1u);
+                }
+              }
+              if (!ok) break;
+              mma_commit(empty0 + 8 * stage);
+              if (++stage == S) {
+                stage = 0;
+                phase ^= 1u;
+              }
+            }
+            if (!ok) break;
+#pragma unroll
+            for (int t = 0; t < 2; ++t)
+              if (nbt[t] > 0) {
+                mma_commit(tfull0 + 8 * bt[t]);
+                ++nt2[t];
+              }
+            continue;
+          }
+          const int nb = hv;
+          const int buf = n % NB;
+          const uint32_t use = (uint32_t)(n / NB);
+          if (!mbar_wait(tempty0 + 8 * buf, (use & 1u) ^ 1u, abort_flag, p.err)) break;
+          tc_fence_after();
+          const uint32_t dhh = tmem + (uint32_t)(buf * 2 * NT);
+          const uint32_t dx = dhh + (uint32_t)NT;
+          bool ok = true;
           for (int kb = 0; kb < nb; ++kb) {
-            if (!mbar_wait(empty0 + 8 * stage, phase ^ 1u, abort_flag, p.err)) {
+            if ((FUSED && !mbar_wait(conv0 + 8 * stage, phase, abort_flag, p.err)) ||
+                !mbar_wait(full0 + 8 * stage, phase, abort_flag, p.err)) {
               ok = false;
               break;
             }
+            tc_fence_after();
             const uint32_t sa = smem_u32(smem + stage * C::kStageBytes);
-            mbar_expect_tx(full0 + 8 * stage, C::kStageBytes + (TE == 1 ? 128 : 0));
-            armed_phase[stage] = (int)phase;
-            bulk_g2s(sa, a + (size_t)kb * C::kABytes, C::kABytes, full0 + 8 * stage);
-            if constexpr (TE == 2)  // the second field's table block
-              bulk_g2s(sa + C::kABytes, p.table2 + (size_t)q_off[j] * C::kABytes + (size_t)kb * C::kABytes,
-                       C::kABytes, full0 + 8 * stage);
-            if constexpr (TE == 1)  // the block's 32 values of 1/x^2
-              bulk_g2s(smem_u32(fbuf + stage * 128), p.ix2 + ((size_t)q * p.nkbs + kb) * 32, 128, full0 + 8 * stage);
-            constexpr int kBOff = (TE == 2 ? 2 : 1) * C::kABytes;  // the source region of the stage
-            if constexpr (TE) {  // FP32 boxes [NT/2 models][1 k][32 tau] of the two fields
-              tma_load_3d(sa + kBOff, &tm_src, kb * 32, q, it.mt * (NT / 2), full0 + 8 * stage);
-              tma_load_3d(sa + kBOff + (NT / 2) * 128, &tm_src2, kb * 32, q, it.mt * (NT / 2),
-                          full0 + 8 * stage);
-            } else if constexpr (FUSED)  // FP32 box [NT sources][1 k][32 tau]; zero beyond ntau and M
-              tma_load_3d(sa + kBOff, &tm_src, kb * 32, q, it.mt * NT, full0 + 8 * stage);
-            else
-              bulk_g2s(sa + kBOff, b + (size_t)kb * C::kBBytes, C::kBBytes, full0 + 8 * stage);
+            const uint32_t sb = sa + (TE == 2 ? 2 : 1) * C::kABytes;
+#pragma unroll
+            for (int kk = 0; kk < G::kKSteps; ++kk) {
+              const uint64_t ah = G::desc(sa + kk * 32), al = G::desc(sa + G::kPlaneA + kk * 32);
+              const uint64_t bh = G::desc(sb + kk * 32), bl = G::desc(sb + NT * G::kRowB + kk * 32);
+              const uint32_t accum = (kb | kk) ? 1u : 0u;
+              if constexpr (TE == 2) {
+                // X rows [0, NT/2) times table 1, Y rows [NT/2, NT) times table 2;
+                // row NT/2 starts on a whole 8-row swizzle atom
+                constexpr int H = NT / 2;
+                constexpr uint32_t idescH = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(H >> 3) << 17) |
+                                            ((uint32_t)(128 >> 4) << 24);
+                const uint32_t sa2 = sa + C::kABytes;
+                const uint64_t ah2 = G::desc(sa2 + kk * 32), al2 = G::desc(sa2 + G::kPlaneA + kk * 32);
+                const uint64_t bhY = G::desc(sb + H * G::kRowB + kk * 32);
+                const uint64_t blY = G::desc(sb + NT * G::kRowB + H * G::kRowB + kk * 32);
+                mma<MODE>(dhh, ah, bh, idescH, accum);       // D_X hh
+                mma<MODE>(dhh + H, ah2, bhY, idescH, accum);  // D_Y hh
+                mma<MODE>(dx, ah, bl, idescH, accum);        // D_X x
+                mma<MODE>(dx, al, bh, idescH, 1u);
+                mma<MODE>(dx + H, ah2, blY, idescH, accum);  // D_Y x
+                mma<MODE>(dx + H, al2, bhY, idescH, 1u);
+                continue;
+              }
+              if constexpr (kPair) {
+                mma<MODE>(dhh, ah, bh, idesc2, accum);  // [D_hh | D_x] (+)= A_hi [B_hi | B_lo]
+              } else {
+                mma<MODE>(dhh, ah, bh, idesc, accum);
+                mma<MODE>(dx, ah, bl, idesc, accum);
+              }
+              mma<MODE>(dx, al, bh, idesc, 1u);
+            }
+            mma_commit(empty0 + 8 * stage);
             if (++stage == S) {
               stage = 0;
               phase ^= 1u;
             }
           }
+          if (!ok) break;
+          mma_commit(tfull0 + 8 * buf);
+          ++n;
+        }
+        // every MMA this thread issued has completed before TMEM is freed
+        mma_commit(drain);
+        mbar_wait(drain, 0, nullptr, p.err);
+      }
+    } else if (warp < R::kConv0) {
+      // LP = 2: warps 2, 3 have no role
+    } else if (FUSED) {
+      // ---------------- converters: the stage's FP32 tile [NT][32] becomes the
+      // hi and lo planes [NT][64 B] (64-byte swizzle) in the same bytes.  Thread
+      // ct owns float4 column c4 of rows r0 + 16 j; every row it writes has the
+      // same (row / 2) mod 4, hence one swizzle offset.  All reads precede all
+      // writes (conv_all is the barrier between them).
+      if constexpr (FUSED) {
+        constexpr int RJ = NT / 16;
+        const int ct = threadIdx.x - 32 * R::kConv0;
+        const int c4 = ct & 7, r0 = ct >> 3;
+        const uint32_t swz = ((uint32_t)(((c4 >> 1) ^ ((r0 >> 1) & 3)) << 4)) | ((uint32_t)(c4 & 1) << 3);
+        int stage = 0;
+        uint32_t phase = 0;
+        int ks = 0;
+        uint32_t kph = 0;
+        while (true) {
+          const bool w = mbar_wait(kfull0 + 8 * ks, kph, abort_flag, p.err);
+          const unsigned char *rec = kslots + ks * C::kSlotBytes;
+          int nb = w ? reinterpret_cast<const volatile int *>(rec)[1] : -1;
+          if (!conv_all(w) || nb < 0) break;
+          if constexpr (LP == 2) nb = max(nb & 0xFFFF, nb >> 16);  // stages of the k: the longer tile's
+          float scl[RJ];
+          if constexpr (MODE == kF16) {
+            const float *sr = reinterpret_cast<const float *>(rec + 16 + NT * 4) + r0;
+#pragma unroll
+            for (int j = 0; j < RJ; ++j) scl[j] = sr[16 * j];
+          }
+          __syncwarp();
+          if (lane == 0) mbar_arrive(kempty0 + 8 * ks);
+          if (++ks == KS) {
+            ks = 0;
+            kph ^= 1u;
+          }
+          bool ok = true;
+          for (int kb = 0; kb < nb; ++kb) {
+            const bool w2 = mbar_wait(full0 + 8 * stage, phase, abort_flag, p.err);
+            unsigned char *sb = smem + stage * C::kStageBytes + ((TE == 2 || LP == 2) ? 2 : 1) * C::kABytes;
+            const float4 *raw = reinterpret_cast<const float4 *>(sb);
+            float4 v[RJ];
+#pragma unroll
+            for (int j = 0; j < RJ; ++j) v[j] = raw[ct + 128 * j];
+            // TE: 1/x^2 of this thread's four tau nodes (copied with the stage)
+            float4 f = make_float4(1.f, 1.f, 1.f, 1.f);
+            if constexpr (TE == 1) f = reinterpret_cast<const float4 *>(fbuf + stage * 128)[c4];
+            if (!conv_all(w2)) {
+              ok = false;
+              break;
+            }
+#pragma unroll
+            for (int j = 0; j < RJ; ++j) {
+              float x0 = v[j].x, x1 = v[j].y, x2 = v[j].z, x3 = v[j].w;
+              if constexpr (TE == 1) {
+                if (j >= RJ / 2) {  // rows NT/2 .. NT-1: polarisation sources
+                  x0 *= f.x;
+                  x1 *= f.y;
+                  x2 *= f.z;
+                  x3 *= f.w;
+                }
+              }
+              uint2 hi, lo;
+              if constexpr (MODE == kF16) {
+                x0 *= scl[j];
+                x1 *= scl[j];
+                x2 *= scl[j];
+                x3 *= scl[j];
+                const __half2 h01 = __floats2half2_rn(x0, x1), h23 = __floats2half2_rn(x2, x3);
+                const __half2 l01 = __floats2half2_rn(x0 - __low2float(h01), x1 - __high2float(h01));
+                const __half2 l23 = __floats2half2_rn(x2 - __low2float(h23), x3 - __high2float(h23));
+                hi = make_uint2(*reinterpret_cast<const uint32_t *>(&h01), *reinterpret_cast<const uint32_t *>(&h23));
+                lo = make_uint2(*reinterpret_cast<const uint32_t *>(&l01), *reinterpret_cast<const uint32_t *>(&l23));
+              } else {
+                const __nv_bfloat162 h01 = __floats2bfloat162_rn(x0, x1), h23 = __floats2bfloat162_rn(x2, x3);
+                const __nv_bfloat162 l01 = __floats2bfloat162_rn(x0 - __low2float(h01), x1 - __high2float(h01));
+                const __nv_bfloat162 l23 = __floats2bfloat162_rn(x2 - __low2float(h23), x3 - __high2float(h23));
+                hi = make_uint2(*reinterpret_cast<const uint32_t *>(&h01), *reinterpret_cast<const uint32_t *>(&h23));
+                lo = make_uint2(*reinterpret_cast<const uint32_t *>(&l01), *reinterpret_cast<const uint32_t *>(&l23));
+              }
+              const uint32_t o = (uint32_t)(r0 + 16 * j) * 64u + swz;
+              *reinterpret_cast<uint2 *>(sb + o) = hi;
+              *reinterpret_cast<uint2 *>(sb + NT * 64 + o) = lo;
+            }
+            // generic-proxy stores, read next by the tensor cores
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(conv0 + 8 * stage);
+            if (++stage == S) {
+              stage = 0;
+              phase ^= 1u;
+            }
+          }
+          if (!ok) break;
         }
       }
-      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;  // also orders lane 0's reads before the next item's writes
     }
-    if (lane == 0) {
-      // end-of-work record (no copies)
-      if (ok && mbar_wait(kempty0 + 8 * ks, kph ^ 1u, abort_flag, p.err)) {
-        reinterpret_cast<volatile int *>(kslots + ks * C::kSlotBytes)[1] = -1;
-        mbar_arrive(kfull0 + 8 * ks);
-        karmed[ks] = (int)kph;  // this phase completes now; the drain below must not wait for a later one
-      }
-      // no copy may still be landing when the CTA exits
-      for (int s = 0; s < S; ++s)
-        if (armed_phase[s] >= 0) mbar_wait(full0 + 8 * s, (uint32_t)armed_phase[s], nullptr, p.err);
-      for (int s = 0; s < KS; ++s)
-        if (karmed[s] >= 0) mbar_wait(kfull0 + 8 * s, (uint32_t)karmed[s], nullptr, p.err);
-    }
-  } else if (warp == 1) {
-    if (lane == 0) {
-      // ---------------- MMA issuer
-      constexpr uint32_t fmt = MODE == kTF32 ? 2u : (MODE == kBF16 ? 1u : 0u);
-      constexpr uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(NT >> 3) << 17) |
-                                 ((uint32_t)(128 >> 4) << 24);
-      // With NT <= 128 the hi and lo source planes are one operand of 2 NT
-      // rows and D_hh, D_x adjacent TMEM columns, so hi*hi and hi*lo are one
-      // MMA of N = 2 NT: each K step reads A_hi once (shared-memory bandwidth
-      // bounds these MMAs).
-      constexpr bool kPair = 2 * NT <= 256;
-      constexpr uint32_t idesc2 = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)((2 * NT) >> 3) << 17) |
-                                  ((uint32_t)(128 >> 4) << 24);
-      int stage = 0;
-      uint32_t phase = 0;
+  } else {
+    if constexpr (LP == 2) asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(R::kRegHigh));
+    if constexpr (TE) {
+      // ---------------- epilogue (TE): per model j of the thread's quarter,
+      // t = w (D_T), e = w (D_E' + tail at l = 2); tt += t^2, ee += e^2, te += t e
+      constexpr int H = NT / 2, MPT = H / 2;
+      constexpr int CWE = NT >= 128 ? 4 : 8;  // TMEM load width (register budget)
+      const int sp = warp & 3;
+      const int half = (warp - R::kEpi0) >> 2;
+      const int row = sp * 32 + lane;
+      const int j0 = half * MPT;
+      float att[MPT], aee[MPT], ate[MPT];
+#pragma unroll
+      for (int j = 0; j < MPT; ++j) att[j] = aee[j] = ate[j] = 0.f;
       int n = 0;
       int ks = 0;
       uint32_t kph = 0;
       while (true) {
         if (!mbar_wait(kfull0 + 8 * ks, kph, abort_flag, p.err)) break;
-        const int nb = reinterpret_cast<volatile int *>(kslots + ks * C::kSlotBytes)[1];
+        const unsigned char *rec = kslots + ks * C::kSlotBytes;
+        const volatile int *hdr = reinterpret_cast<const volatile int *>(rec);
+        const int nb = hdr[1];
         if (nb < 0) break;
-        mbar_arrive(kempty0 + 8 * ks);
+        const int item = hdr[2], flags = hdr[3];
+        const int buf = n % NB;
+        const uint32_t use = (uint32_t)(n / NB);
+        if (!mbar_wait(tfull0 + 8 * buf, use & 1u, abort_flag, p.err)) break;
+        tc_fence_after();
+        if (flags & kFirst) {
+#pragma unroll
+          for (int j = 0; j < MPT; ++j) att[j] = aee[j] = ate[j] = 0.f;
+        }
+        const float *wr = reinterpret_cast<const float *>(rec + 16);
+        const float *cr = wr + H;
+        // the small-x tail at l = 2: lane r2 of the first l-tile only
+        const float cm = ((flags & kL2) && row == p.r2) ? 1.f : 0.f;
+        const uint32_t taddr = tmem + ((uint32_t)(sp * 32) << 16) + (uint32_t)(buf * 2 * NT);
+#pragma unroll
+        for (int c = 0; c < MPT / CWE; ++c) {
+          const int jc = j0 + c * CWE;
+          float th[CWE], tx[CWE], eh[CWE], ex[CWE];
+          tmem_ld<CWE>(taddr + jc, th);
+          tmem_ld<CWE>(taddr + NT + jc, tx);
+          tmem_ld<CWE>(taddr + H + jc, eh);
+          tmem_ld<CWE>(taddr + NT + H + jc, ex);
+          tmem_wait_ld();
+#pragma unroll
+          for (int u = 0; u < CWE; ++u) {
+            const float w = wr[jc + u];
+            const float t = w * (th[u] + tx[u]);
+            const float e = w * fmaf(cm, cr[jc + u], eh[u] + ex[u]);
+            att[c * CWE + u] = fmaf(t, t, att[c * CWE + u]);
+            aee[c * CWE + u] = fmaf(e, e, aee[c * CWE + u]);
+            ate[c * CWE + u] = fmaf(t, e, ate[c * CWE + u]);
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(tempty0 + 8 * buf);
+          mbar_arrive(kempty0 + 8 * ks);
+        }
         if (++ks == KS) {
           ks = 0;
           kph ^= 1u;
         }
-        const int buf = n % NB;
-        const uint32_t use = (uint32_t)(n / NB);
-        if (!mbar_wait(tempty0 + 8 * buf, (use & 1u) ^ 1u, abort_flag, p.err)) break;
-        tc_fence_after();
-        const uint32_t dhh = tmem + (uint32_t)(buf * 2 * NT);
-        const uint32_t dx = dhh + (uint32_t)NT;
-        bool ok = true;
-        for (int kb = 0; kb < nb; ++kb) {
-          if ((FUSED && !mbar_wait(conv0 + 8 * stage, phase, abort_flag, p.err)) ||
-              !mbar_wait(full0 + 8 * stage, phase, abort_flag, p.err)) {
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-          const uint32_t sa = smem_u32(smem + stage * C::kStageBytes);
-          const uint32_t sb = sa + (TE == 2 ? 2 : 1) * C::kABytes;
+        ++n;
+        if (flags & kLast) {
+          float *part = p.partial + (size_t)item * 3 * H * 128;
 #pragma unroll
-          for (int kk = 0; kk < G::kKSteps; ++kk) {
-            const uint64_t ah = G::desc(sa + kk * 32), al = G::desc(sa + G::kPlaneA + kk * 32);
-            const uint64_t bh = G::desc(sb + kk * 32), bl = G::desc(sb + NT * G::kRowB + kk * 32);
-            const uint32_t accum = (kb | kk) ? 1u : 0u;
-            if constexpr (TE == 2) {
-              // X rows [0, NT/2) times table 1, Y rows [NT/2, NT) times table 2;
-              // row NT/2 starts on a whole 8-row swizzle atom
-              constexpr int H = NT / 2;
-              constexpr uint32_t idescH = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(H >> 3) << 17) |
-                                          ((uint32_t)(128 >> 4) << 24);
-              const uint32_t sa2 = sa + C::kABytes;
-              const uint64_t ah2 = G::desc(sa2 + kk * 32), al2 = G::desc(sa2 + G::kPlaneA + kk * 32);
-              const uint64_t bhY = G::desc(sb + H * G::kRowB + kk * 32);
-              const uint64_t blY = G::desc(sb + NT * G::kRowB + H * G::kRowB + kk * 32);
-              mma<MODE>(dhh, ah, bh, idescH, accum);       // D_X hh
-              mma<MODE>(dhh + H, ah2, bhY, idescH, accum);  // D_Y hh
-              mma<MODE>(dx, ah, bl, idescH, accum);        // D_X x
-              mma<MODE>(dx, al, bh, idescH, 1u);
-              mma<MODE>(dx + H, ah2, blY, idescH, accum);  // D_Y x
-              mma<MODE>(dx + H, al2, bhY, idescH, 1u);
-              continue;
-            }
-            if constexpr (kPair) {
-              mma<MODE>(dhh, ah, bh, idesc2, accum);  // [D_hh | D_x] (+)= A_hi [B_hi | B_lo]
-            } else {
-              mma<MODE>(dhh, ah, bh, idesc, accum);
-              mma<MODE>(dx, ah, bl, idesc, accum);
-            }
-            mma<MODE>(dx, al, bh, idesc, 1u);
-          }
-          mma_commit(empty0 + 8 * stage);
-          if (++stage == S) {
-            stage = 0;
-            phase ^= 1u;
+          for (int j = 0; j < MPT; ++j) {
+            part[(size_t)(j0 + j) * 128 + row] = att[j];
+            part[(size_t)(H + j0 + j) * 128 + row] = aee[j];
+            part[(size_t)(2 * H + j0 + j) * 128 + row] = ate[j];
           }
         }
-        if (!ok) break;
-        mma_commit(tfull0 + 8 * buf);
-        ++n;
       }
-      // every MMA this thread issued has completed before TMEM is freed
-      mma_commit(drain);
-      mbar_wait(drain, 0, nullptr, p.err);
-    }
-  } else if (FUSED && warp < R::kEpi0) {
-    // ---------------- converters: the stage's FP32 tile [NT][32] becomes the
-    // hi and lo planes [NT][64 B] (64-byte swizzle) in the same bytes.  Thread
-    // ct owns float4 column c4 of rows r0 + 16 j; every row it writes has the
-    // same (row / 2) mod 4, hence one swizzle offset.  All reads precede all
-    // writes (conv_all is the barrier between them).
-    if constexpr (FUSED) {
-      constexpr int RJ = NT / 16;
-      const int ct = threadIdx.x - 64;
-      const int c4 = ct & 7, r0 = ct >> 3;
-      const uint32_t swz = ((uint32_t)(((c4 >> 1) ^ ((r0 >> 1) & 3)) << 4)) | ((uint32_t)(c4 & 1) << 3);
-      int stage = 0;
-      uint32_t phase = 0;
+    } else {
+      // ---------------- epilogue: acc += (sqrt(4 pi w_k P) (D_hh + D_x))^2
+      // (LP = 2: warps 8 t .. 8 t + 7 of the epilogue serve tile t)
+      constexpr int CW = C::kChunk;
+      const int sp = warp & 3;  // a warp reads the TMEM lanes 32 (warp mod 4) .. + 31
+      const int grp = (warp - R::kEpi0) >> 2;
+      const int half = grp & 1, tile = grp >> 1;
+      const int row = sp * 32 + lane;
+      const int col0 = half * C::kColsPerThread;
+      float acc[C::kColsPerThread];
+#pragma unroll
+      for (int j = 0; j < C::kColsPerThread; ++j) acc[j] = 0.f;
+      int n = 0;
       int ks = 0;
       uint32_t kph = 0;
       while (true) {
-        const bool w = mbar_wait(kfull0 + 8 * ks, kph, abort_flag, p.err);
+        if (!mbar_wait(kfull0 + 8 * ks, kph, abort_flag, p.err)) break;
         const unsigned char *rec = kslots + ks * C::kSlotBytes;
-        const int nb = w ? reinterpret_cast<const volatile int *>(rec)[1] : -1;
-        if (!conv_all(w) || nb < 0) break;
-        float scl[RJ];
-        if constexpr (MODE == kF16) {
-          const float *sr = reinterpret_cast<const float *>(rec + 16 + NT * 4) + r0;
+        const volatile int *hdr = reinterpret_cast<const volatile int *>(rec);
+        const int hv = hdr[1];
+        if (hv < 0) break;
+        const int item = hdr[2], flags = hdr[3];
+        if (flags & kFirst) {
 #pragma unroll
-          for (int j = 0; j < RJ; ++j) scl[j] = sr[16 * j];
+          for (int j = 0; j < C::kColsPerThread; ++j) acc[j] = 0.f;
+        }
+        // this tile's blocks at this k (LP = 2: none when only the other tile has some)
+        const int nbt = LP == 2 ? ((hv >> (16 * tile)) & 0xFFFF) : hv;
+        if (nbt > 0) {
+          const int bt = (n % NB) * LP + tile;
+          const uint32_t use = (uint32_t)(n / NB);
+          if (!mbar_wait(tfull0 + 8 * bt, use & 1u, abort_flag, p.err)) break;
+          tc_fence_after();
+          const float4 *w4 = reinterpret_cast<const float4 *>(rec + 16) + col0 / 4;
+          const uint32_t taddr = tmem + ((uint32_t)(sp * 32) << 16) + (uint32_t)(bt * 2 * NT + col0);
+#pragma unroll
+          for (int c = 0; c < C::kColsPerThread / CW; ++c) {
+            float vh[CW], vx[CW];
+            tmem_ld<CW>(taddr + c * CW, vh);
+            tmem_ld<CW>(taddr + NT + c * CW, vx);
+            tmem_wait_ld();
+#pragma unroll
+            for (int j4 = 0; j4 < CW / 4; ++j4) {
+              const float4 w = w4[c * (CW / 4) + j4];
+              const float t0 = w.x * (vh[4 * j4 + 0] + vx[4 * j4 + 0]);
+              const float t1 = w.y * (vh[4 * j4 + 1] + vx[4 * j4 + 1]);
+              const float t2 = w.z * (vh[4 * j4 + 2] + vx[4 * j4 + 2]);
+              const float t3 = w.w * (vh[4 * j4 + 3] + vx[4 * j4 + 3]);
+              acc[c * CW + 4 * j4 + 0] = fmaf(t0, t0, acc[c * CW + 4 * j4 + 0]);
+              acc[c * CW + 4 * j4 + 1] = fmaf(t1, t1, acc[c * CW + 4 * j4 + 1]);
+              acc[c * CW + 4 * j4 + 2] = fmaf(t2, t2, acc[c * CW + 4 * j4 + 2]);
+              acc[c * CW + 4 * j4 + 3] = fmaf(t3, t3, acc[c * CW + 4 * j4 + 3]);
+            }
+          }
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(tempty0 + 8 * bt);
+          ++n;
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(kempty0 + 8 * ks);
@@ -513,205 +825,12 @@ __global__ void __launch_bounds__(TcRoles<FUSED, TE>::kThreadsT, 1)
           ks = 0;
           kph ^= 1u;
         }
-        bool ok = true;
-        for (int kb = 0; kb < nb; ++kb) {
-          const bool w2 = mbar_wait(full0 + 8 * stage, phase, abort_flag, p.err);
-          unsigned char *sb = smem + stage * C::kStageBytes + (TE == 2 ? 2 : 1) * C::kABytes;
-          const float4 *raw = reinterpret_cast<const float4 *>(sb);
-          float4 v[RJ];
+        if (flags & kLast) {
+          // k-chunk sums of (item, tile): partial index item * LP + tile
+          float *part = p.partial + ((size_t)item * LP + tile) * NT * 128;
 #pragma unroll
-          for (int j = 0; j < RJ; ++j) v[j] = raw[ct + 128 * j];
-          // TE: 1/x^2 of this thread's four tau nodes (copied with the stage)
-          float4 f = make_float4(1.f, 1.f, 1.f, 1.f);
-          if constexpr (TE == 1) f = reinterpret_cast<const float4 *>(fbuf + stage * 128)[c4];
-          if (!conv_all(w2)) {
-            ok = false;
-            break;
-          }
-#pragma unroll
-          for (int j = 0; j < RJ; ++j) {
-            float x0 = v[j].x, x1 = v[j].y, x2 = v[j].z, x3 = v[j].w;
-            if constexpr (TE == 1) {
-              if (j >= RJ / 2) {  // rows NT/2 .. NT-1: polarisation sources
-                x0 *= f.x;
-                x1 *= f.y;
-                x2 *= f.z;
-                x3 *= f.w;
-              }
-            }
-            uint2 hi, lo;
-            if constexpr (MODE == kF16) {
-              x0 *= scl[j];
-              x1 *= scl[j];
-              x2 *= scl[j];
-              x3 *= scl[j];
-              const __half2 h01 = __floats2half2_rn(x0, x1), h23 = __floats2half2_rn(x2, x3);
-              const __half2 l01 = __floats2half2_rn(x0 - __low2float(h01), x1 - __high2float(h01));
-              const __half2 l23 = __floats2half2_rn(x2 - __low2float(h23), x3 - __high2float(h23));
-              hi = make_uint2(*reinterpret_cast<const uint32_t *>(&h01), *reinterpret_cast<const uint32_t *>(&h23));
-              lo = make_uint2(*reinterpret_cast<const uint32_t *>(&l01), *reinterpret_cast<const uint32_t *>(&l23));
-            } else {
-              const __nv_bfloat162 h01 = __floats2bfloat162_rn(x0, x1), h23 = __floats2bfloat162_rn(x2, x3);
-              const __nv_bfloat162 l01 = __floats2bfloat162_rn(x0 - __low2float(h01), x1 - __high2float(h01));
-              const __nv_bfloat162 l23 = __floats2bfloat162_rn(x2 - __low2float(h23), x3 - __high2float(h23));
-              hi = make_uint2(*reinterpret_cast<const uint32_t *>(&h01), *reinterpret_cast<const uint32_t *>(&h23));
-              lo = make_uint2(*reinterpret_cast<const uint32_t *>(&l01), *reinterpret_cast<const uint32_t *>(&l23));
-            }
-            const uint32_t o = (uint32_t)(r0 + 16 * j) * 64u + swz;
-            *reinterpret_cast<uint2 *>(sb + o) = hi;
-            *reinterpret_cast<uint2 *>(sb + NT * 64 + o) = lo;
-          }
-          // generic-proxy stores, read next by the tensor cores
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          __syncwarp();
-          if (lane == 0) mbar_arrive(conv0 + 8 * stage);
-          if (++stage == S) {
-            stage = 0;
-            phase ^= 1u;
-          }
+          for (int j = 0; j < C::kColsPerThread; ++j) part[(size_t)(col0 + j) * 128 + row] = acc[j];
         }
-        if (!ok) break;
-      }
-    }
-  } else if constexpr (TE) {
-    // ---------------- epilogue (TE): per model j of the thread's quarter,
-    // t = w (D_T), e = w (D_E' + tail at l = 2); tt += t^2, ee += e^2, te += t e
-    constexpr int H = NT / 2, MPT = H / 2;
-    constexpr int CWE = NT >= 128 ? 4 : 8;  // TMEM load width (register budget)
-    const int sp = warp & 3;
-    const int half = (warp - R::kEpi0) >> 2;
-    const int row = sp * 32 + lane;
-    const int j0 = half * MPT;
-    float att[MPT], aee[MPT], ate[MPT];
-#pragma unroll
-    for (int j = 0; j < MPT; ++j) att[j] = aee[j] = ate[j] = 0.f;
-    int n = 0;
-    int ks = 0;
-    uint32_t kph = 0;
-    while (true) {
-      if (!mbar_wait(kfull0 + 8 * ks, kph, abort_flag, p.err)) break;
-      const unsigned char *rec = kslots + ks * C::kSlotBytes;
-      const volatile int *hdr = reinterpret_cast<const volatile int *>(rec);
-      const int nb = hdr[1];
-      if (nb < 0) break;
-      const int item = hdr[2], flags = hdr[3];
-      const int buf = n % NB;
-      const uint32_t use = (uint32_t)(n / NB);
-      if (!mbar_wait(tfull0 + 8 * buf, use & 1u, abort_flag, p.err)) break;
-      tc_fence_after();
-      if (flags & kFirst) {
-#pragma unroll
-        for (int j = 0; j < MPT; ++j) att[j] = aee[j] = ate[j] = 0.f;
-      }
-      const float *wr = reinterpret_cast<const float *>(rec + 16);
-      const float *cr = wr + H;
-      // the small-x tail at l = 2: lane r2 of the first l-tile only
-      const float cm = ((flags & kL2) && row == p.r2) ? 1.f : 0.f;
-      const uint32_t taddr = tmem + ((uint32_t)(sp * 32) << 16) + (uint32_t)(buf * 2 * NT);
-#pragma unroll
-      for (int c = 0; c < MPT / CWE; ++c) {
-        const int jc = j0 + c * CWE;
-        float th[CWE], tx[CWE], eh[CWE], ex[CWE];
-        tmem_ld<CWE>(taddr + jc, th);
-        tmem_ld<CWE>(taddr + NT + jc, tx);
-        tmem_ld<CWE>(taddr + H + jc, eh);
-        tmem_ld<CWE>(taddr + NT + H + jc, ex);
-        tmem_wait_ld();
-#pragma unroll
-        for (int u = 0; u < CWE; ++u) {
-          const float w = wr[jc + u];
-          const float t = w * (th[u] + tx[u]);
-          const float e = w * fmaf(cm, cr[jc + u], eh[u] + ex[u]);
-          att[c * CWE + u] = fmaf(t, t, att[c * CWE + u]);
-          aee[c * CWE + u] = fmaf(e, e, aee[c * CWE + u]);
-          ate[c * CWE + u] = fmaf(t, e, ate[c * CWE + u]);
-        }
-      }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) {
-        mbar_arrive(tempty0 + 8 * buf);
-        mbar_arrive(kempty0 + 8 * ks);
-      }
-      if (++ks == KS) {
-        ks = 0;
-        kph ^= 1u;
-      }
-      ++n;
-      if (flags & kLast) {
-        float *part = p.partial + (size_t)item * 3 * H * 128;
-#pragma unroll
-        for (int j = 0; j < MPT; ++j) {
-          part[(size_t)(j0 + j) * 128 + row] = att[j];
-          part[(size_t)(H + j0 + j) * 128 + row] = aee[j];
-          part[(size_t)(2 * H + j0 + j) * 128 + row] = ate[j];
-        }
-      }
-    }
-  } else {
-    // ---------------- epilogue: acc += (sqrt(4 pi w_k P) (D_hh + D_x))^2
-    constexpr int CW = C::kChunk;
-    const int sp = warp & 3;  // a warp reads the TMEM lanes 32 (warp mod 4) .. + 31
-    const int half = (warp - R::kEpi0) >> 2;
-    const int row = sp * 32 + lane;
-    const int col0 = half * C::kColsPerThread;
-    float acc[C::kColsPerThread];
-#pragma unroll
-    for (int j = 0; j < C::kColsPerThread; ++j) acc[j] = 0.f;
-    int n = 0;
-    int ks = 0;
-    uint32_t kph = 0;
-    while (true) {
-      if (!mbar_wait(kfull0 + 8 * ks, kph, abort_flag, p.err)) break;
-      const unsigned char *rec = kslots + ks * C::kSlotBytes;
-      const volatile int *hdr = reinterpret_cast<const volatile int *>(rec);
-      const int nb = hdr[1];
-      if (nb < 0) break;
-      const int item = hdr[2], flags = hdr[3];
-      const int buf = n % NB;
-      const uint32_t use = (uint32_t)(n / NB);
-      if (!mbar_wait(tfull0 + 8 * buf, use & 1u, abort_flag, p.err)) break;
-      tc_fence_after();
-      if (flags & kFirst) {
-#pragma unroll
-        for (int j = 0; j < C::kColsPerThread; ++j) acc[j] = 0.f;
-      }
-      const float4 *w4 = reinterpret_cast<const float4 *>(rec + 16) + col0 / 4;
-      const uint32_t taddr = tmem + ((uint32_t)(sp * 32) << 16) + (uint32_t)(buf * 2 * NT + col0);
-#pragma unroll
-      for (int c = 0; c < C::kColsPerThread / CW; ++c) {
-        float vh[CW], vx[CW];
-        tmem_ld<CW>(taddr + c * CW, vh);
-        tmem_ld<CW>(taddr + NT + c * CW, vx);
-        tmem_wait_ld();
-#pragma unroll
-        for (int j4 = 0; j4 < CW / 4; ++j4) {
-          const float4 w = w4[c * (CW / 4) + j4];
-          const float t0 = w.x * (vh[4 * j4 + 0] + vx[4 * j4 + 0]);
-          const float t1 = w.y * (vh[4 * j4 + 1] + vx[4 * j4 + 1]);
-          const float t2 = w.z * (vh[4 * j4 + 2] + vx[4 * j4 + 2]);
-          const float t3 = w.w * (vh[4 * j4 + 3] + vx[4 * j4 + 3]);
-          acc[c * CW + 4 * j4 + 0] = fmaf(t0, t0, acc[c * CW + 4 * j4 + 0]);
-          acc[c * CW + 4 * j4 + 1] = fmaf(t1, t1, acc[c * CW + 4 * j4 + 1]);
-          acc[c * CW + 4 * j4 + 2] = fmaf(t2, t2, acc[c * CW + 4 * j4 + 2]);
-          acc[c * CW + 4 * j4 + 3] = fmaf(t3, t3, acc[c * CW + 4 * j4 + 3]);
-        }
-      }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) {
-        mbar_arrive(tempty0 + 8 * buf);
-        mbar_arrive(kempty0 + 8 * ks);
-      }
-      if (++ks == KS) {
-        ks = 0;
-        kph ^= 1u;
-      }
-      ++n;
-      if (flags & kLast) {
-        float *part = p.partial + (size_t)item * NT * 128;
-#pragma unroll
-        for (int j = 0; j < C::kColsPerThread; ++j) part[(size_t)(col0 + j) * 128 + row] = acc[j];
       }
     }
   }
@@ -764,6 +883,8 @@ __device__ __forceinline__ double prefix_weight(const double *__restrict__ wk, c
 // [2^13, 2^14) (fp16 keeps 11 significant bits only in its normal range).
 // Lane 0 writes the row's epilogue weight wq = sqrt(4 pi w_k P) 2^-(sJ + s),
 // with the source's own k weights; (wq D')^2 is then the unscaled term.
+// Every epilogue weight forms 4 pi w_k P in FP64 and takes its square root in
+// FP32 (wq within 2^-24 relative; the same expression on every path).
 template <int MODE, int CACHE>
 __global__ void __launch_bounds__(256) split_rows_kernel(const float *__restrict__ S, const double *__restrict__ Pk,
                                                          const double *__restrict__ wk, const double *__restrict__ kk,
@@ -886,9 +1007,9 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const float *__restrict
   if (lane == 0) {
     float w = 0.f;
     if (live) {
-      const double root = sqrt(4.0 * 3.14159265358979323846 * prefix_weight(wk, kk, nk, nk_m[mfull], q) *
-                               Pk[(size_t)mc * nk + q]);
-      w = (float)(MODE == kF16 ? ldexp(root, -(sJ + s)) : root);
+      const float root = sqrtf((float)(4.0 * 3.14159265358979323846 * prefix_weight(wk, kk, nk, nk_m[mfull], q) *
+                                       Pk[(size_t)mc * nk + q]));
+      w = MODE == kF16 ? ldexpf(root, -(sJ + s)) : root;
     }
     wq[row] = w;
   }
@@ -930,8 +1051,8 @@ __global__ void __launch_bounds__(256) rowscale_kernel(const float *__restrict__
       s = 14 - e;
       s = s < -40 ? -40 : (s > 80 ? 80 : s);
     }
-    const double root = sqrt(4.0 * 3.14159265358979323846 * wk[q] * Pk[r]);
-    wq[(size_t)q * mpad + m] = (float)ldexp(root, -(sJ + s));
+    const float root = sqrtf((float)(4.0 * 3.14159265358979323846 * wk[q] * Pk[r]));
+    wq[(size_t)q * mpad + m] = ldexpf(root, -(sJ + s));
     sc[(size_t)q * mpad + m] = ldexpf(1.f, s);
   }
 }
@@ -948,13 +1069,29 @@ __global__ void __launch_bounds__(256) weights_kernel(const double *__restrict__
   float w = 0.f;
   if (m < M && q < nk_m[m]) {
     const int mc = perm[m];
-    w = (float)sqrt(4.0 * 3.14159265358979323846 * prefix_weight(wk, kk, nk, nk_m[m], q) * Pk[(size_t)mc * nk + q]);
+    w = sqrtf((float)(4.0 * 3.14159265358979323846 * prefix_weight(wk, kk, nk, nk_m[m], q) * Pk[(size_t)mc * nk + q]));
   }
   wq[row] = w;
 }
 
-// C[m][row] = sum over the tile's items (fixed order) of the FP32 chunk sums,
-// in FP64; zero above the source's own l_max.  row: output index, whose
+// Sum of FP32 values as an unevaluated pair hi + lo of FP32 numbers: each
+// add is Knuth's TwoSum (s = hi + v and its exact rounding error), the
+// errors gathered in lo; read out once as (double) hi + lo.  The result is
+// within ~n^2 2^-48 of the exact sum (n terms), at FP32-pipe cost (this
+// GPU's FP64 pipe runs at a small fraction of its FP32 rate).
+struct PairSum {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    const float s = hi + v;
+    const float b = s - hi;
+    lo += (hi - (s - b)) + (v - b);
+    hi = s;
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// C[m][row] = sum over the tile's items (fixed order) of the FP32 chunk sums
+// (PairSum); zero above the source's own l_max.  row: output index, whose
 // multipole is lrow[row].
 __global__ void __launch_bounds__(128) reduce_kernel(const float *__restrict__ partial, const int *__restrict__ tile_ptr,
                                                      const int *__restrict__ tile_items, int NT, int n_mt, int M,
@@ -968,11 +1105,21 @@ __global__ void __launch_bounds__(128) reduce_kernel(const float *__restrict__ p
   const int m = mt * NT + ml;
   const int row = lt * kTileL + r;
   if (m >= M || row >= nl) return;
-  double acc = 0.0;
-  if (lrow[row] <= lmax_m[m])
-    for (int e = tile_ptr[tile]; e < tile_ptr[tile + 1]; ++e)
-      acc += (double)partial[((size_t)tile_items[e] * NT + ml) * 128 + r];
-  Cl[(size_t)perm[m] * nl + row] = acc;
+  PairSum acc;
+  if (lrow[row] <= lmax_m[m]) {
+    // sequential order; the loads of eight items are issued together
+    const int e1 = tile_ptr[tile + 1];
+    int e = tile_ptr[tile];
+    for (; e + 8 <= e1; e += 8) {
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = partial[((size_t)tile_items[e + u] * NT + ml) * 128 + r];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc.add(v[u]);
+    }
+    for (; e < e1; ++e) acc.add(partial[((size_t)tile_items[e] * NT + ml) * 128 + r]);
+  }
+  Cl[(size_t)perm[m] * nl + row] = acc.value();
 }
 
 // 1/x^2 of every node, x = k (tau0 - tau_i), in FP32 for the converters:
@@ -1010,7 +1157,7 @@ __global__ void __launch_bounds__(256) te_weights_kernel(const double *__restric
   const int q = (int)(row / mpad), m = (int)(row - (size_t)q * mpad);
   float w = 0.f, t = 0.f;
   if (m < M) {
-    w = (float)sqrt(4.0 * 3.14159265358979323846 * wk[q] * Pk[(size_t)m * nk + q]);
+    w = sqrtf((float)(4.0 * 3.14159265358979323846 * wk[q] * Pk[(size_t)m * nk + q]));
     const float *src = SP + ((size_t)m * nk + q) * ntau;
     double acc = 0.0;
     for (int i = ntau - 1; i >= 0; --i) {
@@ -1041,19 +1188,19 @@ __global__ void __launch_bounds__(128) reduce_te_kernel(const float *__restrict_
   const int row = lt * kTileL + r;
   if (m >= M || row >= nl) return;
   const int l = lrow[row];
-  double tt = 0.0, ee = 0.0, te = 0.0;
+  PairSum tt, ee, te;
   for (int e = tile_ptr[tile]; e < tile_ptr[tile + 1]; ++e) {
     const float *pp = partial + (size_t)tile_items[e] * 3 * H * 128 + (size_t)ml * 128 + r;
-    tt += (double)pp[0];
-    ee += (double)pp[(size_t)H * 128];
-    te += (double)pp[(size_t)2 * H * 128];
+    tt.add(pp[0]);
+    ee.add(pp[(size_t)H * 128]);
+    te.add(pp[(size_t)2 * H * 128]);
   }
   // E-mode (scale_cl): C^EE = c_l^2 sum, C^TE = c_l sum; pairs of kernel grids: none
   const double c2 = !scale_cl ? 1.0 : (l >= 2 ? (double)(l + 2) * (l + 1) * l * (l - 1) : 0.0);
   const size_t o = (size_t)m * nl + row;
-  ClTT[o] = tt;
-  ClEE[o] = c2 * ee;
-  ClTE[o] = sqrt(c2) * te;
+  ClTT[o] = tt.value();
+  ClEE[o] = c2 * ee.value();
+  ClTE[o] = sqrt(c2) * te.value();
 }
 
 // ------------------------------------------------------------------ plan
@@ -1068,6 +1215,7 @@ struct TcPlan {
   bool uniform = true;
   bool fused = false;  // sources converted inside the tensor-core kernel (no split pass)
   bool te = false;     // temperature + E-mode: NT models per tile, 2 NT operand rows
+  int lp = 1;          // l-tiles per item (2: adjacent tiles share the item's source blocks)
   std::vector<int> blob;
   size_t o_items = 0, o_tile_ptr = 0, o_tile_items = 0, o_perm = 0, o_nkm = 0, o_lmaxm = 0;
   std::vector<double> cost;  // per item
@@ -1112,6 +1260,15 @@ bool want_fused(const gcamb_grid *g, int mode, int nt, bool uniform) {
   if (const char *e = getenv("GCAMB_TC_FUSED"))
     if (e[0] == '0') return false;
   return uniform && (mode == GCAMB_BF16X3 || mode == GCAMB_F16X3) && nt <= 128 && g->ntau % 4 == 0;
+}
+
+// l-tiles per item of a fused plan (not TE): 2, so that each source block is
+// loaded and split once for two tiles; GCAMB_TC_LP=1 selects one tile per item.
+int want_lp(bool fused, bool te) {
+  if (!fused || te) return 1;
+  if (const char *e = getenv("GCAMB_TC_LP"))
+    if (e[0] == '1') return 1;
+  return 2;
 }
 
 using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -1184,6 +1341,8 @@ void plan_build(const gcamb_grid *g, int M, int mode, int nt, const int *lmax_c,
   // plan's: measured on the 1000-source batch, the split-source kernel plus
   // the pass beat the fused kernel (48.0k against 43.8k spectra/s)
   pl.fused = te || want_fused(g, mode, nt, pl.uniform);
+  pl.lp = pl.nkbs < 32768 ? want_lp(pl.fused, te) : 1;  // LP = 2 records pack two block counts in 16 bits
+  const int lp = pl.lp;
   for (int j = 0; j < M; ++j) {
     nkm[j] = nk_of(perm[j]);
     lmm[j] = lm_of(perm[j]);
@@ -1193,21 +1352,26 @@ void plan_build(const gcamb_grid *g, int M, int mode, int nt, const int *lmax_c,
     tile_nk[j / nt] = std::max(tile_nk[j / nt], nkm[j]);
     tile_lm[j / nt] = std::max(tile_lm[j / nt], lmm[j]);
   }
-  // items: (l-tile, source tile, contiguous chunk of active k)
+  // items: (l-tile, source tile, contiguous chunk of active k); lp = 2:
+  // (first of two adjacent l-tiles, ...), active where either tile is, the
+  // cost weighing the stages (the longer tile) and the second tile's MMAs
+  auto kcost = [&](int q, int lt) -> double {
+    const int a = t.nkb[(size_t)q * g->nlt + lt];
+    const int b = (lp == 2 && lt + 1 < g->nlt) ? t.nkb[(size_t)q * g->nlt + lt + 1] : 0;
+    if (a == 0 && b == 0) return 0.0;
+    return std::max(a, b) + 0.5 * std::min(a, b) + 0.5;
+  };
   double total = 0.0;
-  for (int lt = 0; lt < g->nlt; ++lt)
+  for (int lt = 0; lt < g->nlt; lt += lp)
     for (int mt = 0; mt < pl.n_mt; ++mt) {
       if (tile_lm[mt] < g->lrow[(size_t)lt * kTileL]) continue;
-      for (int q = 0; q < tile_nk[mt]; ++q) {
-        const int nb = t.nkb[(size_t)q * g->nlt + lt];
-        if (nb) total += nb + 0.5;
-      }
+      for (int q = 0; q < tile_nk[mt]; ++q) total += kcost(q, lt);
     }
   const int sms = num_sms();
   const double target = std::max(4.0, total / (sms * 4.0));
   std::vector<TcItem> items;
   pl.cost.clear();
-  for (int lt = 0; lt < g->nlt; ++lt)
+  for (int lt = 0; lt < g->nlt; lt += lp)
     for (int mt = 0; mt < pl.n_mt; ++mt) {
       if (tile_lm[mt] < g->lrow[(size_t)lt * kTileL]) continue;
       // an item spans at most kKChunkMax k and starts and ends at a k with
@@ -1215,8 +1379,8 @@ void plan_build(const gcamb_grid *g, int M, int mode, int nt, const int *lmax_c,
       int qb = -1, qlast = -1;
       double c = 0.0;
       for (int q = 0; q < tile_nk[mt]; ++q) {
-        const int nb = t.nkb[(size_t)q * g->nlt + lt];
-        if (nb == 0) continue;
+        const double kc = kcost(q, lt);
+        if (kc == 0.0) continue;
         if (qb >= 0 && q - qb + 1 > kKChunkMax) {
           items.push_back({lt, mt, qb, qlast + 1});
           pl.cost.push_back(c);
@@ -1227,7 +1391,7 @@ void plan_build(const gcamb_grid *g, int M, int mode, int nt, const int *lmax_c,
           qb = q;
           c = 0.0;
         }
-        c += nb + 0.5;
+        c += kc;
         if (c >= target || q - qb + 1 >= kKChunkMax) {
           items.push_back({lt, mt, qb, q + 1});
           pl.cost.push_back(c);
@@ -1259,16 +1423,21 @@ void plan_build(const gcamb_grid *g, int M, int mode, int nt, const int *lmax_c,
     pl.cost.swap(sc);
   }
   pl.nctas = std::max(1, std::min(sms, pl.nitems));
-  // per (l-tile, source tile): its items in increasing k (fixed reduce order)
+  // per (l-tile, source tile): its items' partials in increasing k (fixed
+  // reduce order); item i writes partial i * lp + s for its tile lt + s
   pl.ntile = g->nlt * pl.n_mt;
-  std::vector<int> tile_ptr(pl.ntile + 1, 0), tile_items(pl.nitems);
-  for (const auto &x : items) tile_ptr[x.lt * pl.n_mt + x.mt + 1]++;
+  std::vector<int> tile_ptr(pl.ntile + 1, 0);
+  for (const auto &x : items)
+    for (int sub = 0; sub < lp && x.lt + sub < g->nlt; ++sub) tile_ptr[(x.lt + sub) * pl.n_mt + x.mt + 1]++;
   for (int i = 0; i < pl.ntile; ++i) tile_ptr[i + 1] += tile_ptr[i];
+  std::vector<int> tile_items(tile_ptr[pl.ntile]);
   {
     std::vector<int> idx(pl.nitems), fill(tile_ptr.begin(), tile_ptr.end() - 1);
     for (int i = 0; i < pl.nitems; ++i) idx[i] = i;
     std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return items[a].qb < items[b].qb; });
-    for (int i : idx) tile_items[fill[items[i].lt * pl.n_mt + items[i].mt]++] = i;
+    for (int i : idx)
+      for (int sub = 0; sub < lp && items[i].lt + sub < g->nlt; ++sub)
+        tile_items[fill[(items[i].lt + sub) * pl.n_mt + items[i].mt]++] = i * lp + sub;
   }
   // blob
   pl.blob.clear();
@@ -1292,7 +1461,7 @@ void plan_build(const gcamb_grid *g, int M, int mode, int nt, const int *lmax_c,
   const size_t sp_bytes = pl.fused ? 0 : (size_t)g->nk * pl.n_mt * pl.nkbs * 2 * row_b * pl.NT;
   const size_t wp_bytes = (size_t)g->nk * pl.mpad * sizeof(float);
   const size_t sc_bytes = (te || (pl.fused && mode == GCAMB_F16X3)) ? wp_bytes : 0;
-  const size_t part_bytes = std::max<size_t>(1, pl.nitems) * (te ? 3 : 1) * pl.NT * 128 * sizeof(float);
+  const size_t part_bytes = std::max<size_t>(1, pl.nitems) * lp * (te ? 3 : 1) * pl.NT * 128 * sizeof(float);
   pl.off_sp = 0;
   pl.off_wp = align256(sp_bytes);
   pl.off_sc = pl.off_wp + align256(wp_bytes);
@@ -1320,7 +1489,8 @@ TcPlan *get_plan(const gcamb_grid *g, int M, int mode, int *rc) {
   const int nt = pick_nt(M);
   for (auto &e : g_plans)
     if (e.first == g && !e.second->te && e.second->M == M && e.second->mode == mode && e.second->NT == nt &&
-        e.second->fused == want_fused(g, mode, nt, true))
+        e.second->fused == want_fused(g, mode, nt, true) &&
+        e.second->lp == (e.second->nkbs < 32768 ? want_lp(e.second->fused, false) : 1))
       return e.second;
   TcPlan *pl = new TcPlan();
   plan_build(g, M, mode, nt, nullptr, nullptr, *pl);
@@ -1333,18 +1503,18 @@ TcPlan *get_plan(const gcamb_grid *g, int M, int mode, int *rc) {
   return pl;
 }
 
-template <int NT, int MODE, bool FUSED, int TE = 0>
+template <int NT, int MODE, bool FUSED, int TE = 0, int LP = 1>
 int launch_tc_kernel(const gcamb_grid *g, const TcPlan &pl, const CUtensorMap &tm, const CUtensorMap &tm2,
                      const TcParams &prm, cudaStream_t st) {
-  using Cfg = TcCfg<NT, MODE, TE == 2 ? 2 : 1>;
-  cudaError_t e = cudaFuncSetAttribute(los_cl_tc_kernel<NT, MODE, FUSED, TE>,
+  using Cfg = TcCfg<NT, MODE, (TE == 2 || LP == 2) ? 2 : 1, LP>;
+  cudaError_t e = cudaFuncSetAttribute(los_cl_tc_kernel<NT, MODE, FUSED, TE, LP>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmemBytes);
   if (e != cudaSuccess) return cuda_fail(e, "los_cl: smem attribute");
   e = cudaMemsetAsync(prm.counter, 0, sizeof(int), st);
   if (e != cudaSuccess) return cuda_fail(e, "los_cl: counter reset");
   ProfScope prof(GCAMB_K_TC, st);
-  los_cl_tc_kernel<NT, MODE, FUSED, TE>
-      <<<(unsigned)pl.nctas, TcRoles<FUSED, TE>::kThreadsT, Cfg::kSmemBytes, st>>>(tm, tm2, prm);
+  los_cl_tc_kernel<NT, MODE, FUSED, TE, LP>
+      <<<(unsigned)pl.nctas, TcRoles<FUSED, TE, LP>::kThreadsT, Cfg::kSmemBytes, st>>>(tm, tm2, prm);
   return GCAMB_OK;
 }
 
@@ -1398,8 +1568,9 @@ int launch_tc(const gcamb_grid *g, const TcPlan &pl, const float *S, const doubl
     if (!prm.err && !use_err_word) return fail(GCAMB_ECUDA, "los_cl: error flag allocation");
     int rc;
     if constexpr (kCanFuse)
-      rc = fused ? launch_tc_kernel<NT, MODE, true>(g, pl, tm, tm, prm, st)
-                 : launch_tc_kernel<NT, MODE, false>(g, pl, tm, tm, prm, st);
+      rc = !fused         ? launch_tc_kernel<NT, MODE, false>(g, pl, tm, tm, prm, st)
+           : pl.lp == 2 ? launch_tc_kernel<NT, MODE, true, 0, 2>(g, pl, tm, tm, prm, st)
+                        : launch_tc_kernel<NT, MODE, true>(g, pl, tm, tm, prm, st);
     else
       rc = launch_tc_kernel<NT, MODE, false>(g, pl, tm, tm, prm, st);
     if (rc) return rc;
@@ -1609,7 +1780,7 @@ size_t los_cl_workspace_bytes(const gcamb_grid *g, int M, int mode) {
     const size_t nkbs = (g->ntau + lay.kb - 1) / lay.kb;
     const size_t sp_bytes = (size_t)g->nk * n_mt * nkbs * 256 * nt;
     const size_t wp_bytes = (size_t)g->nk * n_mt * nt * sizeof(float);
-    const size_t max_items = (size_t)g->nk * g->nlt * n_mt;
+    const size_t max_items = (size_t)g->nk * (g->nlt + 1) * n_mt;  // partials: LP = 2 pads an odd tile count
     return align256(sp_bytes) + align256(wp_bytes) + align256(max_items * nt * 128 * sizeof(float));
   }
   int rc = 0;
@@ -1863,6 +2034,7 @@ int gcamb_plan_info(const gcamb_plan *p, int64_t *info) {
   info[6] = p->M;
   info[7] = c ? (int64_t)c->ws_bytes : 0;
   info[8] = c && c->fused ? 1 : 0;
+  info[9] = c ? c->lp : 0;
   return GCAMB_OK;
 }
 

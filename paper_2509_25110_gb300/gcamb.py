@@ -505,9 +505,9 @@ def plan_workspace(p: Plan) -> int:
 
 
 def plan_info(p: Plan) -> dict:
-    a = (ctypes.c_int64 * 9)()
+    a = (ctypes.c_int64 * 10)()
     _check(lib().gcamb_plan_info(p.handle, a))
-    keys = ("tile", "items", "ctas", "captures", "replays", "tuned", "M", "workspace", "fused")
+    keys = ("tile", "items", "ctas", "captures", "replays", "tuned", "M", "workspace", "fused", "lp")
     return dict(zip(keys, [int(v) for v in a]))
 
 

@@ -70,9 +70,11 @@ def test_fused_conversion_matches_split_pass_bitwise(monkeypatch, mode, nk, ntau
     """The tensor-core kernel that splits the FP32 sources in shared memory
     feeds the MMAs the same operand bits, in the same order, as the separate
     split pass: the C_l agree bit for bit (ragged tau blocks, ragged source
-    tiles, 64- and 128-source tiles)."""
+    tiles, 64- and 128-source tiles).  One multipole tile per work item, as
+    in the split pass's plan, so that the k-chunks are the same."""
     k, tau, S, P = case(nk, ntau, 2, lmax, M)
     monkeypatch.delenv("GCAMB_TC_FUSED", raising=False)
+    monkeypatch.setenv("GCAMB_TC_LP", "1")
     C_f, g = run(k, tau, S, P, 2, lmax, mode)
     ws_f = gcamb.los_cl_workspace(g, M, mode)
     monkeypatch.setenv("GCAMB_TC_FUSED", "0")
@@ -81,6 +83,37 @@ def test_fused_conversion_matches_split_pass_bitwise(monkeypatch, mode, nk, ntau
     assert ws_f < ws_s  # the in-place path keeps no split sources in its workspace
     assert np.all(np.isfinite(C_f))
     assert np.array_equal(C_f, C_s)
+
+
+@pytest.mark.parametrize("mode", [gcamb.BF16X3, gcamb.F16X3])
+@pytest.mark.parametrize("nk,ntau,lmin,lmax,M", [
+    (70, 332, 2, 300, 100),    # three l-tiles: the last pair has one tile; 128-source tile
+    (50, 256, 2, 520, 40),     # five l-tiles, 64-source tiles (double-buffered pairs)
+    (60, 200, 2, 100, 130),    # one l-tile; two source tiles, the second ragged
+    (96, 1000, 0, 1200, 256),  # ten l-tiles, lmin = 0, ragged last tau block
+])
+def test_paired_l_tiles_match_single_tiles(monkeypatch, mode, nk, ntau, lmin, lmax, M):
+    """Two adjacent 128-multipole tiles per work item (each loaded and split
+    source block multiplies both tables) against one tile per item.  Each
+    (k, l-tile) product D_k is the same sequence of MMAs on the same operand
+    bits and each k's term (w (D_hh + D_x))^2 the same FP32 value; only the
+    k-chunks over which the epilogue sums the terms in FP32 differ.  A chunk
+    sum of at most 64 positive terms is within 63 * 2^-24 of exact (relative),
+    so the two C_l agree within 2 * 64 * 2^-24.  The uniform plan of the same
+    batch runs the paired kernel and gives the paired result bit for bit."""
+    k, tau, S, P = case(nk, ntau, lmin, lmax, M)
+    monkeypatch.setenv("GCAMB_TC_LP", "1")
+    C1, g = run(k, tau, S, P, lmin, lmax, mode)
+    monkeypatch.delenv("GCAMB_TC_LP", raising=False)
+    C2, _ = run(k, tau, S, P, lmin, lmax, mode, g)
+    assert np.all(np.isfinite(C2)) and np.all(C1 > 0)
+    assert (np.abs(C2 - C1) / C1).max() <= 2 * 64 * 2.0 ** -24
+    plan = gcamb.plan_create(g, M, mode=mode)
+    info = gcamb.plan_info(plan)
+    assert info["fused"] == 1 and info["lp"] == 2
+    C3 = gcamb.plan_launch(plan, torch.as_tensor(S, device="cuda"), torch.as_tensor(P, device="cuda")).cpu().numpy()
+    gcamb.sync()
+    assert np.array_equal(C3, C2)
 
 
 def test_identical_models_and_permutation():
