@@ -983,6 +983,9 @@ def main():
         err = float(rel.max())
 
     props = torch.cuda.get_device_properties(dev)
+    # the work plan of the timed launches (a uniform plan of the same batch:
+    # the same plan builder, items and tiles)
+    pinfo = gcamb.plan_info(gcamb.plan_create(g, M, mode=mode))
     line = {
         "metric": METRIC, "value": value, "unit": "spectra/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -996,6 +999,7 @@ def main():
                    "max_rel_err_sample": "%d sources" % args.cpu_models if err is not None else None,
                    "plain64_spectra_per_s": plain64_rate, "speedup_vs_plain64": value / world / plain64_rate,
                    "active_entries": info["active"], "kernel_ms": {k: (v[0] / max(1, v[1])) for k, v in kern.items()},
+                   "work_items": pinfo["items"], "l_tiles_per_item": pinfo["lp"], "ctas": pinfo["ctas"],
                    "device": props.name},
         "roofline": roofline,
         "cpu_baseline": cpu,
