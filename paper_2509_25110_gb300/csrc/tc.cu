@@ -7,17 +7,21 @@
 // Algorithm 1 window).  Both operands are split into hi + lo parts (bf16 or
 // tf32) and D_k accumulates hi*hi + hi*lo + lo*hi in FP32 in tensor memory.
 // The epilogue squares D_k, weights it by 4 pi w_k P_m(k) (Eq. 1) and adds it
-// to per-thread FP32 sums over a chunk of at most 64 k; the chunk sums are
-// added in FP64 in a fixed order by a second kernel.  D_k never leaves the SM.
+// to per-thread FP32 sums over a chunk of at most 64 k; a second kernel adds
+// the chunk sums in a fixed order (TwoSum pairs, read out in FP64).  D_k
+// never leaves the SM.
 //
-// Work item = (l-tile, source tile, contiguous k-chunk).  One persistent CTA
-// per SM takes items from a counter:
-//   warp 0      producer: bulk copy of the table block and of the source block
-//               per stage (split sources, or FP32 sources by TMA when fused)
+// Work item = (l-tile, source tile, contiguous k-chunk); with LP = 2 (fused
+// uniform batches) two adjacent l-tiles that share each source block.  One
+// persistent CTA per SM takes items from a counter:
+//   warp 0      producer: bulk copy of the table block(s) and of the source
+//               block per stage (split sources, or FP32 sources by TMA when fused)
 //   warp 1      TMEM allocator and single-thread MMA issuer
-//   warps 2..5  (fused only) converters: FP32 source tile -> hi/lo planes in
+//   (LP = 2: warps 2, 3 idle, so that every role is whole warpgroups)
+//   4 warps     (fused only) converters: FP32 source tile -> hi/lo planes in
 //               place, in the swizzled operand layout
-//   the rest    8 epilogue warps: TMEM -> registers, square, weight, accumulate
+//   the rest    8 epilogue warps per tile: TMEM -> registers, square, weight,
+//               accumulate
 // Every mbarrier wait is bounded (1 s); a timeout sets the device error flag,
 // the CTA drains its own copies and MMAs, frees TMEM and exits.
 #include <cuda.h>
