@@ -50,8 +50,11 @@ constexpr int kConvWarps = 4;
 constexpr int kKChunkMax = 64;     // k per work item: bounds the FP32 partial-sum length
 constexpr int kSmemBudget = 196608;
 
+// Work item: first l-tile, source tile, k range [qb, qe), and its number of
+// l-tiles (LP = 2 plans: 2, or 1 where the source tile's l_max stops before
+// the second tile or no tile follows).
 struct TcItem {
-  int lt, mt, qb, qe;
+  int lt, mt, qb, qe, ntl, pad[3];
 };
 
 struct TcParams {
@@ -210,7 +213,7 @@ struct TcCfg {
 template <bool FUSED, int TE = 0, int LP = 1>
 struct TcRoles {
   static constexpr int kConv = FUSED ? kConvWarps : 0;
-  static constexpr int kConv0 = LP == 2 ? 4 : 2;  // first converter warp
+  static constexpr int kConv0 = (LP == 2 && FUSED) ? 4 : 2;  // first converter warp (or epilogue warp)
   static constexpr int kEpi0 = kConv0 + kConv;    // first epilogue warp
   static constexpr int kEpi = kEpiWarps * LP;
   static constexpr int kThreadsT = 32 * (kEpi0 + kEpi);
@@ -242,8 +245,7 @@ __global__ void __launch_bounds__(TcRoles<FUSED, TE, LP>::kThreadsT, 1)
     los_cl_tc_kernel(const __grid_constant__ CUtensorMap tm_src, const __grid_constant__ CUtensorMap tm_src2,
                      TcParams p) {
   static_assert(!TE || (FUSED && MODE == kBF16 && NT <= 128), "TE: fused bf16, NT <= 128");
-  static_assert(LP == 1 || (LP == 2 && !TE && FUSED && MODE != kTF32 && NT <= 128),
-                "LP = 2: fused bf16/fp16 without TE, NT <= 128");
+  static_assert(LP == 1 || (LP == 2 && !TE && MODE != kTF32 && NT <= 128), "LP = 2: bf16/fp16 without TE, NT <= 128");
   using C = TcCfg<NT, MODE, (TE == 2 || LP == 2) ? 2 : 1, LP>;
   using G = TcGeom<MODE>;
   using R = TcRoles<FUSED, TE, LP>;
@@ -307,7 +309,7 @@ __global__ void __launch_bounds__(TcRoles<FUSED, TE, LP>::kThreadsT, 1)
   // Roles.  Each register change sits in its warpgroups' own branch, so that
   // the code it covers is compiled to its budget.
   if (warp < R::kEpi0) {
-    if constexpr (LP == 2) {
+    if constexpr (LP == 2 && FUSED) {
       static_assert(R::kThreadsT == 768 && R::kEpi0 == 8, "LP = 2 register split: 6 warpgroups");
       asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(R::kRegLow));
     }
@@ -339,7 +341,7 @@ __global__ void __launch_bounds__(TcRoles<FUSED, TE, LP>::kThreadsT, 1)
           q_nb[j] = p.nkb[e];
           q_off[j] = p.off[e];
           if constexpr (LP == 2) {  // the pair's second tile (none past the last)
-            const bool has2 = it.lt + 1 < p.nlt;
+            const bool has2 = it.ntl == 2;
             q_nb[kKChunkMax + j] = has2 ? p.nkb[e + 1] : 0;
             q_off[kKChunkMax + j] = has2 ? p.off[e + 1] : 0;
           }
@@ -398,7 +400,10 @@ __global__ void __launch_bounds__(TcRoles<FUSED, TE, LP>::kThreadsT, 1)
                 if (u1)
                   bulk_g2s(sa + C::kABytes, p.table + ((size_t)q_off[kKChunkMax + j] + kb) * C::kABytes, C::kABytes,
                            full0 + 8 * stage);
-                tma_load_3d(sa + 2 * C::kABytes, &tm_src, kb * 32, q, it.mt * NT, full0 + 8 * stage);
+                if constexpr (FUSED)
+                  tma_load_3d(sa + 2 * C::kABytes, &tm_src, kb * 32, q, it.mt * NT, full0 + 8 * stage);
+                else
+                  bulk_g2s(sa + 2 * C::kABytes, b + (size_t)kb * C::kBBytes, C::kBBytes, full0 + 8 * stage);
                 if (++stage == S) {
                   stage = 0;
                   phase ^= 1u;
@@ -485,7 +490,7 @@ __global__ void __launch_bounds__(TcRoles<FUSED, TE, LP>::kThreadsT, 1)
             }
             bool ok = true;
             for (int kb = 0; kb < nb && ok; ++kb) {
-              if (!mbar_wait(conv0 + 8 * stage, phase, abort_flag, p.err) ||
+              if ((FUSED && !mbar_wait(conv0 + 8 * stage, phase, abort_flag, p.err)) ||
                   !mbar_wait(full0 + 8 * stage, phase, abort_flag, p.err)) {
                 ok = false;
                 break;
@@ -688,7 +693,7 @@ __global__ void __launch_bounds__(TcRoles<FUSED, TE, LP>::kThreadsT, 1)
       }
     }
   } else {
-    if constexpr (LP == 2) asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(R::kRegHigh));
+    if constexpr (LP == 2 && FUSED) asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(R::kRegHigh));
     if constexpr (TE) {
       // ---------------- epilogue (TE): per model j of the thread's quarter,
       // t = w (D_T), e = w (D_E' + tail at l = 2); tt += t^2, ee += e^2, te += t e
@@ -1266,10 +1271,11 @@ bool want_fused(const gcamb_grid *g, int mode, int nt, bool uniform) {
   return uniform && (mode == GCAMB_BF16X3 || mode == GCAMB_F16X3) && nt <= 128 && g->ntau % 4 == 0;
 }
 
-// l-tiles per item of a fused plan (not TE): 2, so that each source block is
-// loaded and split once for two tiles; GCAMB_TC_LP=1 selects one tile per item.
-int want_lp(bool fused, bool te) {
-  if (!fused || te) return 1;
+// l-tiles per item (not TE; bf16/fp16 with NT <= 128): 2, so that each source
+// block is loaded (and, fused, split) once for two tiles; GCAMB_TC_LP=1
+// selects one tile per item.
+int want_lp(int mode, int nt, bool te) {
+  if (te || mode == GCAMB_TF32X3 || nt > 128) return 1;
   if (const char *e = getenv("GCAMB_TC_LP"))
     if (e[0] == '1') return 1;
   return 2;
@@ -1345,7 +1351,7 @@ void plan_build(const gcamb_grid *g, int M, int mode, int nt, const int *lmax_c,
   // plan's: measured on the 1000-source batch, the split-source kernel plus
   // the pass beat the fused kernel (48.0k against 43.8k spectra/s)
   pl.fused = te || want_fused(g, mode, nt, pl.uniform);
-  pl.lp = pl.nkbs < 32768 ? want_lp(pl.fused, te) : 1;  // LP = 2 records pack two block counts in 16 bits
+  pl.lp = pl.nkbs < 32768 ? want_lp(mode, nt, te) : 1;  // LP = 2 records pack two block counts in 16 bits
   const int lp = pl.lp;
   for (int j = 0; j < M; ++j) {
     nkm[j] = nk_of(perm[j]);
@@ -1359,9 +1365,13 @@ void plan_build(const gcamb_grid *g, int M, int mode, int nt, const int *lmax_c,
   // items: (l-tile, source tile, contiguous chunk of active k); lp = 2:
   // (first of two adjacent l-tiles, ...), active where either tile is, the
   // cost weighing the stages (the longer tile) and the second tile's MMAs
-  auto kcost = [&](int q, int lt) -> double {
+  // l-tiles of the item that starts at tile lt for source tile mt
+  auto ntl_of = [&](int lt, int mt) {
+    return (lp == 2 && lt + 1 < g->nlt && tile_lm[mt] >= g->lrow[(size_t)(lt + 1) * kTileL]) ? 2 : 1;
+  };
+  auto kcost = [&](int q, int lt, int ntl) -> double {
     const int a = t.nkb[(size_t)q * g->nlt + lt];
-    const int b = (lp == 2 && lt + 1 < g->nlt) ? t.nkb[(size_t)q * g->nlt + lt + 1] : 0;
+    const int b = ntl == 2 ? t.nkb[(size_t)q * g->nlt + lt + 1] : 0;
     if (a == 0 && b == 0) return 0.0;
     return std::max(a, b) + 0.5 * std::min(a, b) + 0.5;
   };
@@ -1369,7 +1379,7 @@ void plan_build(const gcamb_grid *g, int M, int mode, int nt, const int *lmax_c,
   for (int lt = 0; lt < g->nlt; lt += lp)
     for (int mt = 0; mt < pl.n_mt; ++mt) {
       if (tile_lm[mt] < g->lrow[(size_t)lt * kTileL]) continue;
-      for (int q = 0; q < tile_nk[mt]; ++q) total += kcost(q, lt);
+      for (int q = 0; q < tile_nk[mt]; ++q) total += kcost(q, lt, ntl_of(lt, mt));
     }
   const int sms = num_sms();
   const double target = std::max(4.0, total / (sms * 4.0));
@@ -1380,13 +1390,14 @@ void plan_build(const gcamb_grid *g, int M, int mode, int nt, const int *lmax_c,
       if (tile_lm[mt] < g->lrow[(size_t)lt * kTileL]) continue;
       // an item spans at most kKChunkMax k and starts and ends at a k with
       // stored blocks
+      const int ntl = ntl_of(lt, mt);
       int qb = -1, qlast = -1;
       double c = 0.0;
       for (int q = 0; q < tile_nk[mt]; ++q) {
-        const double kc = kcost(q, lt);
+        const double kc = kcost(q, lt, ntl);
         if (kc == 0.0) continue;
         if (qb >= 0 && q - qb + 1 > kKChunkMax) {
-          items.push_back({lt, mt, qb, qlast + 1});
+          items.push_back({lt, mt, qb, qlast + 1, ntl, {0, 0, 0}});
           pl.cost.push_back(c);
           qb = -1;
         }
@@ -1397,13 +1408,13 @@ void plan_build(const gcamb_grid *g, int M, int mode, int nt, const int *lmax_c,
         }
         c += kc;
         if (c >= target || q - qb + 1 >= kKChunkMax) {
-          items.push_back({lt, mt, qb, q + 1});
+          items.push_back({lt, mt, qb, q + 1, ntl, {0, 0, 0}});
           pl.cost.push_back(c);
           qb = -1;
         }
       }
       if (qb >= 0) {
-        items.push_back({lt, mt, qb, qlast + 1});
+        items.push_back({lt, mt, qb, qlast + 1, ntl, {0, 0, 0}});
         pl.cost.push_back(c);
       }
     }
@@ -1432,7 +1443,7 @@ void plan_build(const gcamb_grid *g, int M, int mode, int nt, const int *lmax_c,
   pl.ntile = g->nlt * pl.n_mt;
   std::vector<int> tile_ptr(pl.ntile + 1, 0);
   for (const auto &x : items)
-    for (int sub = 0; sub < lp && x.lt + sub < g->nlt; ++sub) tile_ptr[(x.lt + sub) * pl.n_mt + x.mt + 1]++;
+    for (int sub = 0; sub < x.ntl; ++sub) tile_ptr[(x.lt + sub) * pl.n_mt + x.mt + 1]++;
   for (int i = 0; i < pl.ntile; ++i) tile_ptr[i + 1] += tile_ptr[i];
   std::vector<int> tile_items(tile_ptr[pl.ntile]);
   {
@@ -1440,7 +1451,7 @@ void plan_build(const gcamb_grid *g, int M, int mode, int nt, const int *lmax_c,
     for (int i = 0; i < pl.nitems; ++i) idx[i] = i;
     std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return items[a].qb < items[b].qb; });
     for (int i : idx)
-      for (int sub = 0; sub < lp && items[i].lt + sub < g->nlt; ++sub)
+      for (int sub = 0; sub < items[i].ntl; ++sub)
         tile_items[fill[(items[i].lt + sub) * pl.n_mt + items[i].mt]++] = i * lp + sub;
   }
   // blob
@@ -1451,7 +1462,7 @@ void plan_build(const gcamb_grid *g, int M, int mode, int nt, const int *lmax_c,
     while (pl.blob.size() % 4) pl.blob.push_back(0);  // 16-byte alignment of every array
     return o;
   };
-  pl.o_items = put(reinterpret_cast<const int *>(items.data()), items.size() * 4);
+  pl.o_items = put(reinterpret_cast<const int *>(items.data()), items.size() * (sizeof(TcItem) / sizeof(int)));
   pl.o_tile_ptr = put(tile_ptr.data(), tile_ptr.size());
   pl.o_tile_items = put(tile_items.data(), tile_items.size());
   pl.o_perm = put(perm.data(), perm.size());
@@ -1494,7 +1505,7 @@ TcPlan *get_plan(const gcamb_grid *g, int M, int mode, int *rc) {
   for (auto &e : g_plans)
     if (e.first == g && !e.second->te && e.second->M == M && e.second->mode == mode && e.second->NT == nt &&
         e.second->fused == want_fused(g, mode, nt, true) &&
-        e.second->lp == (e.second->nkbs < 32768 ? want_lp(e.second->fused, false) : 1))
+        e.second->lp == (e.second->nkbs < 32768 ? want_lp(mode, nt, false) : 1))
       return e.second;
   TcPlan *pl = new TcPlan();
   plan_build(g, M, mode, nt, nullptr, nullptr, *pl);
@@ -1572,9 +1583,10 @@ int launch_tc(const gcamb_grid *g, const TcPlan &pl, const float *S, const doubl
     if (!prm.err && !use_err_word) return fail(GCAMB_ECUDA, "los_cl: error flag allocation");
     int rc;
     if constexpr (kCanFuse)
-      rc = !fused         ? launch_tc_kernel<NT, MODE, false>(g, pl, tm, tm, prm, st)
-           : pl.lp == 2 ? launch_tc_kernel<NT, MODE, true, 0, 2>(g, pl, tm, tm, prm, st)
-                        : launch_tc_kernel<NT, MODE, true>(g, pl, tm, tm, prm, st);
+      rc = fused ? (pl.lp == 2 ? launch_tc_kernel<NT, MODE, true, 0, 2>(g, pl, tm, tm, prm, st)
+                               : launch_tc_kernel<NT, MODE, true>(g, pl, tm, tm, prm, st))
+                 : (pl.lp == 2 ? launch_tc_kernel<NT, MODE, false, 0, 2>(g, pl, tm, tm, prm, st)
+                               : launch_tc_kernel<NT, MODE, false>(g, pl, tm, tm, prm, st));
     else
       rc = launch_tc_kernel<NT, MODE, false>(g, pl, tm, tm, prm, st);
     if (rc) return rc;

@@ -116,6 +116,26 @@ def test_paired_l_tiles_match_single_tiles(monkeypatch, mode, nk, ntau, lmin, lm
     assert np.array_equal(C3, C2)
 
 
+@pytest.mark.parametrize("mode", [gcamb.BF16X3, gcamb.F16X3])
+@pytest.mark.parametrize("nk,ntau,lmin,lmax,M", [
+    (70, 333, 2, 300, 100),   # split pass (ntau % 4 != 0), three l-tiles, 128-source tile
+    (50, 256, 2, 520, 40),    # five l-tiles, 64-source tiles
+])
+def test_split_pass_paired_l_tiles_match_single_tiles(monkeypatch, mode, nk, ntau, lmin, lmax, M):
+    """The split-pass kernel (sources split by a separate pass) with two
+    l-tiles per item against one tile per item: the bound of the fused test."""
+    k, tau, S, P = case(nk, ntau, lmin, lmax, M)
+    monkeypatch.setenv("GCAMB_TC_FUSED", "0")
+    monkeypatch.setenv("GCAMB_TC_LP", "1")
+    C1, g = run(k, tau, S, P, lmin, lmax, mode)
+    monkeypatch.delenv("GCAMB_TC_LP", raising=False)
+    C2, _ = run(k, tau, S, P, lmin, lmax, mode, g)
+    assert np.all(np.isfinite(C2)) and np.all(C1 > 0)
+    assert (np.abs(C2 - C1) / C1).max() <= 2 * 64 * 2.0 ** -24
+    info = gcamb.plan_info(gcamb.plan_create(g, M, mode=mode))
+    assert info["fused"] == 0 and info["lp"] == 2
+
+
 def test_identical_models_and_permutation():
     k, tau, S, P = case(64, 300, 2, 400, 5)
     Srep = np.repeat(S[:1], 70, axis=0)

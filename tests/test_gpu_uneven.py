@@ -32,14 +32,14 @@ def uneven_batch(M, nk, lmax_lo, lmax_hi, seed):
     return p, lm, nkm
 
 
-def check_against_oracle(orc, k, tau, tau0, lmin, C, S, P, lm, nkm, sel):
+def check_against_oracle(orc, k, tau, tau0, lmin, C, S, P, lm, nkm, sel, tol=TOL):
     for m in sel:
         q = int(nkm[m])
         L = int(lm[m])
         _, cr = orc.los_cl(k[:q], tau, tau0, lmin, L, S[m, :q].astype(np.float64), P[m, :q], want_delta=False)
         got = C[m, :L - lmin + 1]
         err = np.abs(got / cr - 1)
-        assert err.max() <= TOL, (m, L, q, err.max())
+        assert err.max() <= tol, (m, L, q, err.max())
         assert np.all(C[m, L - lmin + 1:] == 0.0)
 
 
@@ -59,6 +59,42 @@ def test_uneven_batch_matches_oracle(orc):
     order = np.argsort(lm)
     sel = sorted({int(order[0]), int(order[-1]), int(order[M // 2]), 3, 17, 44})
     check_against_oracle(orc, k, tau, 14000.0, lmin, C, S, P, lm, nkm, sel)
+
+
+@pytest.mark.parametrize("mode", [gcamb.BF16X3, gcamb.F16X3])
+def test_uneven_paired_l_tiles_match_single_tiles(monkeypatch, orc, mode):
+    """An uneven plan with two adjacent l-tiles per work item (the split
+    sources loaded once for both tables; a source tile whose largest l_max
+    stops before the second tile gets one-tile items) against the same plan
+    with one tile per item.  Each (k, l-tile) product is the same MMA
+    sequence; only the k-chunks of the FP32 sums differ, so the C_l agree
+    within 2 * 64 * 2^-24 relative, and exactly where a source's l_max ends.
+    Against the oracle: 1e-5 for F16X3, BF16X3's bound on coarse grids
+    6 * 2^-16 (its 16-bit split; see the batched tests)."""
+    nk, ntau, lmin, lmax, M = 60, 200, 2, 700, 300
+    k = synth.master_linear_k(nk, 0.05)
+    tau = synth.uniform_grid(200.0, 14000.0, ntau)
+    p, lm, nkm = uneven_batch(M, nk, 100, lmax, seed=24)
+    S = torch.as_tensor(synth.sources(k, tau, p).astype(np.float32), device="cuda")
+    P = torch.as_tensor(synth.primordial(k, p), device="cuda")
+    g = gcamb.grid_create(k, tau, 14000.0, lmin, lmax)
+    gcamb.bessel_table(g, mode)
+    monkeypatch.setenv("GCAMB_TC_LP", "1")
+    plan1 = gcamb.plan_create(g, M, lm, nkm, mode)
+    assert gcamb.plan_info(plan1)["lp"] == 1
+    C1 = gcamb.plan_launch(plan1, S, P).cpu().numpy()
+    monkeypatch.delenv("GCAMB_TC_LP", raising=False)
+    plan2 = gcamb.plan_create(g, M, lm, nkm, mode)
+    info = gcamb.plan_info(plan2)
+    assert info["lp"] == 2 and info["fused"] == 0
+    C2 = gcamb.plan_launch(plan2, S, P).cpu().numpy()
+    gcamb.sync()
+    live = C1 != 0
+    assert np.array_equal(live, C2 != 0)
+    assert (np.abs(C2[live] - C1[live]) / np.abs(C1[live])).max() <= 2 * 64 * 2.0 ** -24
+    sel = [int(np.argmin(lm)), int(np.argmax(lm)), 5, 150]
+    check_against_oracle(orc, k, tau, 14000.0, lmin, C2, S.cpu().numpy(), P.cpu().numpy(), lm, nkm, sel,
+                         tol=TOL if mode == gcamb.F16X3 else 6 * 2.0 ** -16)
 
 
 def test_uniform_plan_equals_los_cl():
