@@ -151,6 +151,7 @@ int ensure_device_grid(gcamb_grid *g) {
   if ((e = up(&g->d_wtau, g->wtau)) != cudaSuccess) return cuda_fail(e, "grid upload");
   if ((e = up(&g->d_wk, g->wk)) != cudaSuccess) return cuda_fail(e, "grid upload");
   if ((e = up(&g->d_xstart, g->xstart)) != cudaSuccess) return cuda_fail(e, "grid upload");
+  if (!g->xthr.empty() && (e = up(&g->d_xthr, g->xthr)) != cudaSuccess) return cuda_fail(e, "grid upload");
   auto upi = [](int **dst, const std::vector<int> &src) -> cudaError_t {
     cudaError_t e = cudaMalloc(dst, std::max<size_t>(1, src.size()) * sizeof(int));
     if (e != cudaSuccess) return e;
@@ -338,6 +339,7 @@ static int grid_build(const double *k, int nk, const double *tau, int ntau, doub
   {
     std::vector<double> xe(g->nl);
     for (int r = 0; r < g->nl; ++r) xe[r] = watson_threshold(g->lrow[r], logeps);
+    if (!g->curved) g->xthr = xe;
     int64_t act = 0;
     for (int q = 0; q < nk; ++q) {
       int i = ntau;  // boundary moves towards 0 as l grows
@@ -378,6 +380,7 @@ int gcamb_grid_destroy(gcamb_grid *g) {
   cudaFree(g->d_wtau);
   cudaFree(g->d_wk);
   cudaFree(g->d_xstart);
+  cudaFree(g->d_xthr);
   cudaFree(g->d_lrow);
   cudaFree(g->d_rowof);
   delete g;

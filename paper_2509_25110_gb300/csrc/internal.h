@@ -74,10 +74,14 @@ struct gcamb_grid {
   std::vector<double> k, tau, wtau, wk;
   std::vector<int32_t> ext;       // [nk][nlt] active tau-prefix per (k, l-tile)
   std::vector<double> xstart;     // [nxs] Miller start thresholds per order
+  // [nl] per row: Watson threshold below which |j_l| < eps_cut (flat grids;
+  // empty on curved ones)
+  std::vector<double> xthr;
   int64_t active = 0;             // active (l,k,tau) entries
   // device copies (made lazily)
   double *d_k = nullptr, *d_tau = nullptr, *d_wtau = nullptr, *d_wk = nullptr;
   double *d_xstart = nullptr;
+  double *d_xthr = nullptr;
   int nxs = 0;
   gcamb::Table tab[gcamb::kNumModes];
 };

@@ -8,9 +8,52 @@
 
 namespace gcamb {
 
+// Sum over the warp of each of the V values v[0..V) (V = 1, 2, 4, 8): every
+// step of the first log2(V) halves the values a lane holds (a lane keeps one
+// half, sends the other to its partner and adds what it receives), then plain
+// shuffle adds finish; lane L returns the total of value L >> (5 - log2 V).
+// (V - 1) + (5 - log2 V) adds a lane instead of 5 V.
+template <typename T, int N, int V>
+__device__ __forceinline__ void halve_lanes(T (&v)[V], int lane, int o) {
+  const bool up = (lane & o) != 0;
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    const T send = up ? v[j] : v[j + N];
+    const T keep = up ? v[j + N] : v[j];
+    v[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+  }
+}
+
+template <typename T, int V>
+__device__ __forceinline__ T reduce_lanes(T (&v)[V], int lane) {
+  static_assert(V == 1 || V == 2 || V == 4 || V == 8, "reduce_lanes: V in {1, 2, 4, 8}");
+  int o = 16;
+  if constexpr (V >= 8) {
+    halve_lanes<T, 4>(v, lane, o);
+    o >>= 1;
+  }
+  if constexpr (V >= 4) {
+    halve_lanes<T, 2>(v, lane, o);
+    o >>= 1;
+  }
+  if constexpr (V >= 2) {
+    halve_lanes<T, 1>(v, lane, o);
+    o >>= 1;
+  }
+  T t = v[0];
+  for (; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  return t;
+}
+
 // One CTA: 128 multipoles x MC sources at one k.  The sources' tau-prefix is
 // staged in shared memory; each warp walks table rows (tau contiguous, read
 // coalesced), the lanes split tau and reduce by shuffles.
+//
+// xthr (temperature on flat j_l grids, else null): per row the Watson
+// threshold below which |j_l| < eps_cut.  The tile's tau-prefix is that of
+// its lowest multipole; a row stops at the first 64-node block whose first
+// node has x below its own threshold (x falls along tau, so every later node
+// is below it too): the terms left out are below eps_cut |w S| each.
 //
 // E = true: E-mode polarisation, Eq. (3) with eps_l(x) = c_l j_l(x)/x^2,
 // c_l = sqrt((l+2)!/(l-2)!).  The j_l table is shared with temperature: the
@@ -33,7 +76,8 @@ __global__ void __launch_bounds__(256) los_plain_kernel(const T *__restrict__ ta
                                                         const T *__restrict__ S, int M,
                                                         T *__restrict__ Delta, const double *__restrict__ kk,
                                                         const double *__restrict__ tau, double tau0,
-                                                        const double *__restrict__ wtau, double x_lo) {
+                                                        const double *__restrict__ wtau, double x_lo,
+                                                        const double *__restrict__ xthr) {
   constexpr int KB = 64;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *s = reinterpret_cast<T *>(smem_raw);  // [MC][ext]
@@ -64,8 +108,17 @@ __global__ void __launch_bounds__(256) los_plain_kernel(const T *__restrict__ ta
 #pragma unroll
     for (int m = 0; m < MC; ++m) acc[m] = T(0);
     if (row0 + r < nl) {
+      int nbr = nb;  // blocks this row needs
+      if (xthr) {
+        const double xe = xthr[row0 + r], kq = kk[q];
+        nbr = 0;
+        for (int b0 = 0; b0 < nb; b0 += 32) {
+          const int b = b0 + lane;
+          nbr += __popc(__ballot_sync(0xffffffffu, b < nb && kq * (tau0 - tau[b * KB]) >= xe));
+        }
+      }
       const T *row = chunk + r * KB + lane;
-      for (int b = 0; b < nb; ++b) {
+      for (int b = 0; b < nbr; ++b) {
         const T ja = __ldg(row + (size_t)b * kTileL * KB);
         const T jb = __ldg(row + (size_t)b * kTileL * KB + 32);
         const int t = b * KB + lane;
@@ -76,13 +129,9 @@ __global__ void __launch_bounds__(256) los_plain_kernel(const T *__restrict__ ta
         }
       }
     }
-#pragma unroll
-    for (int m = 0; m < MC; ++m) {
-      T v = acc[m];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) res[m][r] = v;
-    }
+    constexpr int LV = MC == 1 ? 0 : (MC == 2 ? 1 : (MC == 4 ? 2 : 3));
+    const T v = reduce_lanes<T, MC>(acc, lane);
+    if ((lane & ((32 >> LV) - 1)) == 0) res[lane >> (5 - LV)][r] = v;
   }
   __syncthreads();
   for (int idx = threadIdx.x; idx < MC * kTileL; idx += blockDim.x) {
@@ -143,9 +192,12 @@ static int launch_plain_t(const gcamb_grid *g, const Table &t, const T *S, int M
   double x_lo = 1e-12;
   if (XP >= 0 && emode_x_lo(g, &x_lo))
     return fail(GCAMB_EINVAL, "los_transfer: eps_cut too large for the l = 2 limit of the polarisation kernels");
+  // rows stop at their own prefix: temperature on flat j_l grids only (the
+  // polarisation and tensor sources carry 1/x^2, 1/x factors)
+  const double *xthr = (XP < 0 && !E && g->kernel == 0 && !g->curved) ? g->d_xthr : nullptr;
   los_plain_kernel<T, MC, XP, E><<<grid, 256, smem, st>>>(static_cast<const T *>(t.d_data), t.d_nkb, t.d_off,
                                                           g->nk, g->nlt, g->nl, g->d_lrow, g->ntau, S, M, Delta,
-                                                          g->d_k, g->d_tau, g->tau0, g->d_wtau, x_lo);
+                                                          g->d_k, g->d_tau, g->tau0, g->d_wtau, x_lo, xthr);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "los_transfer: launch");
   return GCAMB_OK;
