@@ -36,9 +36,11 @@ def grid(nk=95, ntau=64, lmax=100):
                              lmax)
 
 
-@pytest.mark.parametrize("nk_in,M", [(30, 3), (2, 2), (3, 1), (200, 5)])
-def test_interp_matches_oracle(nk_in, M):
-    g = grid()
+@pytest.mark.parametrize("nk_in,M,ntau", [(30, 3, 64), (2, 2, 64), (3, 1, 64), (200, 5, 64), (30, 3, 63)])
+def test_interp_matches_oracle(nk_in, M, ntau):
+    """ntau = 64: the FP32 evaluation takes four tau columns a thread; 63:
+    one column a thread."""
+    g = grid(ntau=ntau)
     rng = np.random.default_rng(nk_in)
     k_in = np.geomspace(1e-4, 0.3, nk_in)
     k_in[1:-1] *= np.exp(rng.uniform(-0.01, 0.01, max(0, nk_in - 2)))  # uneven spacing
