@@ -573,6 +573,8 @@ def run_features(args):
     build.build()
     peaks, peak_src = load_peaks()
     wl = synth.workload("features_lmax2500")
+    if args.nk:  # profiling case: the transfer grid's k range with this many nodes
+        wl.k = synth.log_grid(float(wl.k[0]), float(wl.k[-1]), args.nk)
     k_ode = synth.log_grid(float(wl.k[0]), float(wl.k[-1]), 1000)
     M = wl.M
     p = synth.model_params(M, seed=0)
