@@ -399,9 +399,9 @@ def los_cl(g: Grid, S, Pk, mode: int, Cl=None, ws=None, stream=None):
     """Fused batched Eqs. (1)-(2) on the tensor cores: S[M][nk][ntau] FP32 -> Cl[M][nl] FP64."""
     import torch
     M = S.shape[0]
-    need = los_cl_workspace(g, M, mode)
+    need = los_cl_workspace(g, M, mode) if M > 0 else 0  # M = 0: the call writes nothing
     if ws is None:
-        ws = torch.empty(need, dtype=torch.uint8, device=S.device)
+        ws = torch.empty(max(1, need), dtype=torch.uint8, device=S.device)
     if Cl is None:
         Cl = torch.empty((M, g.nl), dtype=torch.float64, device=S.device)
     _check(lib().gcamb_los_cl(g.handle, _dev(S, torch.float32, (M, g.nk, g.ntau), "S"),
