@@ -254,6 +254,13 @@ def run_uneven(args):
     ms, clocks = _timed_region(lambda: gcamb.plan_launch(plan, S, P, C, ws), steps, dev)
     gcamb.sync()
     info = gcamb.plan_info(plan)
+    # whole-step roofline (the graph's three launches are not timed apart):
+    # the table's active entries once (4 B hi+lo; tf32 8 B) and every
+    # source's own k prefix once (FP32)
+    peaks, peak_src = load_peaks()
+    pair = 8 if mode == gcamb.TF32X3 else 4
+    alg = gcamb.grid_info(g)["active"] * pair + int(nkm.astype(np.int64).sum()) * wl.ntau * 4
+    achieved = alg / (ms / steps * 1e-3) / 1e9
     line = {"metric": "C_l spectra/sec, uneven batch (1000 sources, l_max U{1500..6000})",
             "value": wl.M * steps / (ms * 1e-3), "unit": "spectra/s", "n_gpus": 1, "steps": steps,
             "warmup": args.warmup, "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
@@ -265,6 +272,10 @@ def run_uneven(args):
                        "ctas": info["ctas"], "graph_captures": info["captures"], "graph_replays": info["replays"],
                        "table_build_s": table_s, "first_launch_s_incl_tuning": first_s,
                        "table_gb": gcamb.table_bytes(g, mode) / 1e9},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_source": peak_src,
+                         "scope": "whole step: split pass + tensor-core kernel + reduce",
+                         "algorithmic_bytes": alg},
             "clocks": clocks, "gpu_launches": 3 * steps}
     print(json.dumps(line), flush=True)
 
