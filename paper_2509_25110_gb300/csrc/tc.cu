@@ -71,7 +71,7 @@ struct TcParams {
   const TcItem *items;
   int *counter;          // next item to hand out (zeroed before each launch)
   int nitems;
-  float *partial;        // [n_items][NT][128]
+  float *partial;        // [n_items * LP][NT][128] (TE: [n_items][3 NT/2][128])
   int *err;
   int nlt, n_mt, nkbs, mpad;
 };
@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(TcRoles<FUSED, TE, LP>::kThreadsT, 1)
     }
     for (int b = 0; b < TB; ++b) {
       mbar_init(tfull0 + 8 * b, 1);
-      mbar_init(tempty0 + 8 * b, kEpiWarps);  // the 8 epilogue warps of the pair's tile
+      mbar_init(tempty0 + 8 * b, kEpiWarps);  // the 8 epilogue warps of the accumulator pair's tile
     }
     mbar_init(drain, 1);
     *abort_flag = 0;
