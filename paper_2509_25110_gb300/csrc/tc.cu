@@ -894,12 +894,15 @@ __device__ __forceinline__ double prefix_weight(const double *__restrict__ wk, c
 // with the source's own k weights; (wq D')^2 is then the unscaled term.
 // Every epilogue weight forms 4 pi w_k P in FP64 and takes its square root in
 // FP32 (wq within 2^-24 relative; the same expression on every path).
+// Rows at or beyond their source tile's longest k prefix (tile_nk) are left
+// out: no work item of that tile reaches them.
 template <int MODE, int CACHE>
 __global__ void __launch_bounds__(256) split_rows_kernel(const float *__restrict__ S, const double *__restrict__ Pk,
                                                          const double *__restrict__ wk, const double *__restrict__ kk,
                                                          int M, int nk, int ntau, int NT, int n_mt, int nkbs,
                                                          int mpad, int sJ, const int *__restrict__ perm,
-                                                         const int *__restrict__ nk_m, int vec,
+                                                         const int *__restrict__ nk_m,
+                                                         const int *__restrict__ tile_nk, int vec,
                                                          char *__restrict__ sp, float *__restrict__ wq) {
   constexpr int EPC = MODE == kTF32 ? 4 : 8;  // elements per 16-byte chunk
   const int lane = threadIdx.x & 31;
@@ -907,6 +910,7 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const float *__restrict
   if (row >= (size_t)nk * mpad) return;
   const int q = (int)(row / mpad), mfull = (int)(row - (size_t)q * mpad);
   const int mt = mfull / NT, n = mfull - mt * NT;
+  if (q >= tile_nk[mt]) return;
   const bool live = mfull < M && q < nk_m[mfull];
   const int mc = live ? perm[mfull] : 0;
   const float *src = S + ((size_t)mc * nk + q) * ntau;
@@ -1226,7 +1230,7 @@ struct TcPlan {
   bool te = false;     // temperature + E-mode: NT models per tile, 2 NT operand rows
   int lp = 1;          // l-tiles per item (2: adjacent tiles share the item's source blocks)
   std::vector<int> blob;
-  size_t o_items = 0, o_tile_ptr = 0, o_tile_items = 0, o_perm = 0, o_nkm = 0, o_lmaxm = 0;
+  size_t o_items = 0, o_tile_ptr = 0, o_tile_items = 0, o_perm = 0, o_nkm = 0, o_lmaxm = 0, o_tnk = 0;
   std::vector<double> cost;  // per item
   int *d_blob = nullptr;
   bool own_blob = false;
@@ -1468,6 +1472,7 @@ void plan_build(const gcamb_grid *g, int M, int mode, int nt, const int *lmax_c,
   pl.o_perm = put(perm.data(), perm.size());
   pl.o_nkm = put(nkm.data(), nkm.size());
   pl.o_lmaxm = put(lmm.data(), lmm.size());
+  pl.o_tnk = put(tile_nk.data(), tile_nk.size());
   if (pl.blob.empty()) pl.blob.push_back(0);
   // workspace: split sources (not with the fused kernel), weights, fp16 row
   // scales (fused fp16), k-chunk partials
@@ -1543,7 +1548,7 @@ int launch_tc(const gcamb_grid *g, const TcPlan &pl, const float *S, const doubl
   float *sc = reinterpret_cast<float *>(ws + pl.off_sc);
   float *part = reinterpret_cast<float *>(ws + pl.off_part);
   const int *B = pl.d_blob;
-  const int *perm = B + pl.o_perm, *nkm = B + pl.o_nkm, *lmm = B + pl.o_lmaxm;
+  const int *perm = B + pl.o_perm, *nkm = B + pl.o_nkm, *lmm = B + pl.o_lmaxm, *tnk = B + pl.o_tnk;
   const bool fused = kCanFuse && pl.fused;
   CUtensorMap tm;
   memset(&tm, 0, sizeof tm);
@@ -1570,10 +1575,10 @@ int launch_tc(const gcamb_grid *g, const TcPlan &pl, const float *S, const doubl
     }
     else if (MODE == kF16 && pl.nkbs * (TcGeom<MODE>::kRowB / 16) <= 32 * 8)
       split_rows_kernel<MODE, 8><<<nblk, 256, 0, st>>>(S, Pk, g->d_wk, g->d_k, pl.M, g->nk, g->ntau, NT, pl.n_mt,
-                                                       pl.nkbs, pl.mpad, t.scale_exp, perm, nkm, vec, sp, wp);
+                                                       pl.nkbs, pl.mpad, t.scale_exp, perm, nkm, tnk, vec, sp, wp);
     else
       split_rows_kernel<MODE, 0><<<nblk, 256, 0, st>>>(S, Pk, g->d_wk, g->d_k, pl.M, g->nk, g->ntau, NT, pl.n_mt,
-                                                       pl.nkbs, pl.mpad, t.scale_exp, perm, nkm, vec, sp, wp);
+                                                       pl.nkbs, pl.mpad, t.scale_exp, perm, nkm, tnk, vec, sp, wp);
   }
   if (pl.nitems > 0) {
     int *ctr = reinterpret_cast<int *>(ws + pl.off_ctr);
