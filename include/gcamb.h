@@ -305,8 +305,10 @@ int gcamb_los_cl_workspace(const gcamb_grid *g, int M, int mode, size_t *bytes);
  * weighted by 4 pi w_k P_m(k) and summed over k without being stored.
  * hi*hi is accumulated apart from hi*lo + lo*hi (two TMEM accumulators), so
  * the main chain takes a third of the accumulate steps.  Partial sums over
- * k-chunks of at most 64 nodes are FP32; the final sum over chunks is FP64 in
- * a fixed order (deterministic).  GCAMB_F16X3 scales the table by one power
+ * k-chunks of at most 64 nodes are FP32; the final sum over chunks runs in a
+ * fixed order (deterministic) as a TwoSum pair of FP32 numbers, read out in
+ * FP64.  Two adjacent 128-multipole tiles share each loaded and split source
+ * block (bf16/fp16 with 64- or 128-source tiles).  GCAMB_F16X3 scales the table by one power
  * of two per grid and each (k, source) row of S by its own power of two so
  * that both land in fp16's normal range; the scales are removed exactly.
  *   S[M][nk][ntau]   device float
@@ -317,6 +319,11 @@ int gcamb_los_cl_workspace(const gcamb_grid *g, int M, int mode, size_t *bytes);
  * mode: GCAMB_BF16X3, GCAMB_F16X3 or GCAMB_TF32X3; requires
  * gcamb_bessel_table(g, mode).  For GCAMB_F16X3 the per-row scale is clamped
  * to 2^-40..2^80, so rows whose largest |S| is below ~1e-20 lose precision.
+ * M = 0 returns GCAMB_OK and writes nothing.
+ * Environment (tuning switches, read when a plan is built; the results agree
+ * within the bounds the tests state): GCAMB_TC_NT=64|128|256 source-tile
+ * width; GCAMB_TC_FUSED=0 splits the sources in a separate pass instead of in
+ * shared memory; GCAMB_TC_LP=1 one multipole tile per work item instead of two.
  * Errors: GCAMB_EINVAL, GCAMB_ESTATE, GCAMB_EUNSUPPORTED (device is not
  * sm_103), GCAMB_ECUDA; GCAMB_ETIMEOUT is reported by gcamb_sync.
  */
