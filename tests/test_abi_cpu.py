@@ -109,3 +109,17 @@ def test_active_count_bounds_true_activity(L, orc):
     assert info["active"] >= true_active
     assert info["active"] <= 1.25 * true_active
     assert info["stored_plain64"] >= info["active"]
+
+
+def test_plan_info_fields_match_the_header():
+    """The binding names as many plan-info fields as the header's
+    GCAMB_PLAN_INFO_N, and reads that many (no short or long buffer)."""
+    import inspect
+
+    from paper_2509_25110_gb300 import gcamb
+    txt = open(os.path.join(ROOT, "include", "gcamb.h")).read()
+    n = int(re.search(r"#define\s+GCAMB_PLAN_INFO_N\s+(\d+)", txt).group(1))
+    src = inspect.getsource(gcamb.plan_info)
+    keys = re.search(r"keys\s*=\s*\(([^)]*)\)", src).group(1)
+    assert len(re.findall(r'"(\w+)"', keys)) == n
+    assert "(ctypes.c_int64 * %d)" % n in src
