@@ -290,7 +290,7 @@ def run_emulator(args):
     build.build()
     wl = synth.workload(WORKLOAD)
     g = gcamb.grid_create(wl.k, wl.tau, wl.tau0, wl.lmin, wl.lmax)
-    steps = args.steps if args.steps != 600 else 40000
+    steps = args.steps if args.steps != 600 else 80000
     e, rep, (Xh, Ch) = emulator.train(g, steps=steps, log=lambda m: print(m, file=sys.stderr, flush=True))
     acc = emulator.accuracy(e, Xh, Ch)
     served = emulator.served_by_tolerance(e, Xh, Ch)
