@@ -38,6 +38,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "C_l spectra/sec at l_max=2500: batched split-precision vs plain FP64, rel err ≤1e-5"
 WORKLOAD = "batched_lmax2500"
+ORACLE_GROUP = 16  # sources per oracle call (its per-(k, tau) j_l is shared by them)
 
 
 def parse_args():
@@ -46,9 +47,10 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=600)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="bf16x3")
+    ap.add_argument("--mode", default="f16x3")
     ap.add_argument("--e2e-steps", type=int, default=20)
-    ap.add_argument("--cpu-models", type=int, default=16)
+    ap.add_argument("--cpu-models", type=int, default=256,
+                    help="sources of the timed batch checked against the oracle (default: all 256)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nk", type=int, default=0,
                     help="profiling case: the same k range with this many nodes (default: the workload's 2000)")
@@ -131,7 +133,10 @@ class ClockSampler:
 # ------------------------------------------------------------------ reference arm
 
 def run_reference(args):
-    """The FP64 CPU oracle as it stands, on host cores, one bounded sample per step."""
+    """The FP64 CPU oracle as it stands, on host cores, one bounded sample per
+    step: 16 sources of the batch on a subset of the k nodes (the oracle's
+    cost is linear in the k nodes; 16 sources share each (k, tau) Bessel
+    evaluation, as in each oracle call of the GPU arm's accuracy check)."""
     import numpy as np
 
     import oracle
@@ -143,38 +148,45 @@ def run_reference(args):
         return
     ob.build()
     wl = synth.workload(WORKLOAD)
-    p = synth.model_params(1, seed=0)
-    # per step: one source on a subset of k nodes (a fraction of a spectrum);
-    # sized so that warm-up + steps finish in about two minutes
+    p = synth.model_params(ORACLE_GROUP, seed=0)
+
+    def inputs(qs):  # FP32-rounded sources and P(k) of the batch's first sources on the k nodes qs
+        return (synth.sources(wl.k[qs], wl.tau, p).astype(np.float32).astype(np.float64),
+                synth.primordial(wl.k[qs], p))
+    # per step: sized so that warm-up + steps finish in about two minutes
     budget = 120.0 / max(1, args.steps + args.warmup)
-    nks = 64
+    nks = 32
     while True:
         qs = np.unique(np.linspace(0, wl.nk - 1, nks).astype(int))
-        S = synth.sources(wl.k[qs], wl.tau, p)
-        P = synth.primordial(wl.k[qs], p)
+        S, P = inputs(qs)
         t0 = time.perf_counter()
         oracle.los_cl(wl.k[qs], wl.tau, wl.tau0, wl.lmin, wl.lmax, S, P, want_delta=False)
         dt = time.perf_counter() - t0
-        if dt <= budget or nks <= 4:
+        if dt <= budget or nks <= 2:
             break
-        nks = max(4, int(nks * budget / dt * 0.8))
-    frac = qs.size / wl.nk
+        nks = max(2, int(nks * budget / dt * 0.8))
+    spectra = ORACLE_GROUP * qs.size / wl.nk
     for _ in range(args.warmup):
         oracle.los_cl(wl.k[qs], wl.tau, wl.tau0, wl.lmin, wl.lmax, S, P, want_delta=False)
     t0 = time.perf_counter()
     for _ in range(args.steps):
         oracle.los_cl(wl.k[qs], wl.tau, wl.tau0, wl.lmin, wl.lmax, S, P, want_delta=False)
     dt = time.perf_counter() - t0
-    value = frac * args.steps / dt
+    value = spectra * args.steps / dt
     cores = oracle.num_threads()
-    sample = "1 source x %d of %d k nodes per step (%.4f spectra), all 1000 tau, l 2..2500" % (qs.size, wl.nk, frac)
+    sample = "%d sources x %d of %d k nodes per step (%.2f spectra), all %d tau, l %d..%d" % (
+        ORACLE_GROUP, qs.size, wl.nk, spectra, wl.ntau, wl.lmin, wl.lmax)
+    q16 = np.unique(np.linspace(0, wl.nk - 1, 16).astype(int))
+    S16, P16 = inputs(q16)
+    one = oracle_sample_rates(wl, S16, P16, q16)
     line = {
         "metric": METRIC, "value": value, "unit": "spectra/s", "impl": "reference", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "M": 256, "lmax": 2500, "nk": 2000, "ntau": 1000,
+        "config": {"workload": WORKLOAD, "M": wl.M, "lmax": wl.lmax, "nk": wl.nk, "ntau": wl.ntau,
                    "reference": "FP64 CPU oracle (oracle/gcamb_oracle.c), dense tau sums"},
-        "cpu_baseline": {"value": value, "unit": "spectra/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "spectra/s", "cores": cores, "kind": "oracle", "sample": sample,
+                         "same_sample_1_core_vs_all": one},
         "e2e": {"value": value, "unit": "spectra/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -194,6 +206,35 @@ def committed_traffic(name, mode):
     except Exception:
         pass
     return None
+
+
+def l_range_errors(rel, lmin, lmax):
+    """Max relative error over [sources] within each multipole range."""
+    import numpy as np
+    ls = np.arange(lmin, lmax + 1)
+    out = {}
+    for a, b in ((2, 30), (30, 500), (500, 1500), (1500, lmax + 1)):
+        sel = (ls >= a) & (ls < b)
+        if sel.any():
+            out["[%d,%d]" % (a, b - 1)] = float(rel[:, sel].max())
+    return out
+
+
+def oracle_sample_rates(wl, S, P, qs):
+    """The oracle on sources S [M][qs][ntau] and P [M][qs] at the k nodes qs
+    of the grid, at one thread and at all threads; rates in spectra/s (the
+    fraction of a spectrum the sample covers, per second)."""
+    import oracle
+    spectra = S.shape[0] * qs.size / wl.nk
+    out = {"sample": "%d sources x %d of %d k nodes (%.2f spectra), all %d tau, l %d..%d"
+                     % (S.shape[0], qs.size, wl.nk, spectra, wl.ntau, wl.lmin, wl.lmax)}
+    for name, nt in (("one_core", 1), ("all_cores", 0)):
+        t0 = time.perf_counter()
+        oracle.los_cl(wl.k[qs], wl.tau, wl.tau0, wl.lmin, wl.lmax, S, P, want_delta=False, nthreads=nt)
+        dt = time.perf_counter() - t0
+        out[name] = {"value": spectra / dt, "unit": "spectra/s", "cores": 1 if nt == 1 else oracle.num_threads(),
+                     "seconds": dt}
+    return out
 
 
 # ------------------------------------------------------------------ other workloads
@@ -341,7 +382,7 @@ def run_te(args):
     gcamb.profile_enable(True)
     ms, clocks = _timed_region(lambda: gcamb.los_cl_te(g, ST, SP, P, out=out, ws=ws), steps, dev)
     gcamb.sync()
-    kern = {gcamb.K_NAMES[i]: gcamb.profile_read(i) for i in (gcamb.K_SPLIT, gcamb.K_TC, gcamb.K_REDUCE)}
+    kern = {gcamb.K_NAMES[i]: gcamb.profile_read(i) for i in (gcamb.K_SPLIT, gcamb.K_WEIGHTS, gcamb.K_TC, gcamb.K_REDUCE)}
     gcamb.profile_enable(False)
     tc_ms, tc_n = kern["los_cl_tc"]
     tc_avg_s = tc_ms / max(1, tc_n) * 1e-3
@@ -609,8 +650,8 @@ def run_features(args):
     gcamb.profile_enable(True)
     ms, clocks = _timed_region(step, steps, dev)
     gcamb.sync()
-    kern = {gcamb.K_NAMES[i]: gcamb.profile_read(i) for i in (gcamb.K_INTERP, gcamb.K_SPLIT, gcamb.K_TC,
-                                                               gcamb.K_REDUCE)}
+    kern = {gcamb.K_NAMES[i]: gcamb.profile_read(i) for i in (gcamb.K_INTERP, gcamb.K_SPLIT, gcamb.K_WEIGHTS,
+                                                               gcamb.K_TC, gcamb.K_REDUCE)}
     gcamb.profile_enable(False)
     tc_ms, tc_n = kern["los_cl_tc"]
     tc_s = tc_ms / max(1, tc_n) * 1e-3
@@ -977,23 +1018,42 @@ def main():
     gcamb.sync()
     plain64_rate = 4 / (plain_ms * 1e-3)
 
-    # ---------------- CPU baseline: the oracle on a bounded sample (rank 0, N = 1)
+    # ---------------- CPU baseline and accuracy: the oracle on the host cores
+    # (rank 0, N = 1).  One all-core run over the timed batch's sources on
+    # the full grid gives the error of every checked spectrum (per l range)
+    # and the all-core rate; the same sources on 16 of the k nodes give the
+    # one-core and all-core rates of one sample (the oracle's cost is linear
+    # in the k nodes, so the rates are comparable).
     cpu = None
     err = None
+    err_by_l = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         from oracle import build as ob
         ob.build()
-        mc = args.cpu_models
-        Sc = S[:mc].double().cpu().numpy()
-        Pc = P[:mc].cpu().numpy()
-        t0 = time.perf_counter()
-        _, Cr = oracle.los_cl(wl.k, wl.tau, wl.tau0, wl.lmin, wl.lmax, Sc, Pc, want_delta=False)
-        dt = time.perf_counter() - t0
-        cpu = {"value": mc / dt, "unit": "spectra/s", "cores": oracle.num_threads(), "kind": "oracle",
-               "sample": "%d of the 256 sources, full grid (2000 k x 1000 tau, l 2..2500), %.1f s" % (mc, dt)}
+        mc = min(args.cpu_models, M)
+        Cr = np.empty((mc, wl.nl))
+        dt = 0.0
+        for m0 in range(0, mc, ORACLE_GROUP):
+            m1 = min(mc, m0 + ORACLE_GROUP)
+            Sc = S[m0:m1].double().cpu().numpy()
+            Pc = P[m0:m1].cpu().numpy()
+            t0 = time.perf_counter()
+            _, Cr[m0:m1] = oracle.los_cl(wl.k, wl.tau, wl.tau0, wl.lmin, wl.lmax, Sc, Pc, want_delta=False)
+            dt += time.perf_counter() - t0
         rel = np.abs(C[:mc].cpu().numpy() / Cr - 1)
         err = float(rel.max())
+        err_by_l = l_range_errors(rel, wl.lmin, wl.lmax)
+        cores = oracle.num_threads()
+        q16 = np.unique(np.linspace(0, wl.nk - 1, 16).astype(int))
+        Sg = S[:ORACLE_GROUP].double().cpu().numpy()
+        Pg = P[:ORACLE_GROUP].cpu().numpy()
+        one = oracle_sample_rates(wl, np.ascontiguousarray(Sg[:, q16, :]), np.ascontiguousarray(Pg[:, q16]), q16)
+        cpu = {"value": mc / dt, "unit": "spectra/s", "cores": cores, "kind": "oracle",
+               "sample": "%d of the %d sources of the timed batch in calls of %d, full grid (%d k x %d tau, "
+                         "l %d..%d), %.1f s; the same run checks their C_l"
+                         % (mc, M, ORACLE_GROUP, wl.nk, wl.ntau, wl.lmin, wl.lmax, dt),
+               "same_sample_1_core_vs_all": one}
 
     props = torch.cuda.get_device_properties(dev)
     # the work plan of the timed launches (a uniform plan of the same batch:
@@ -1009,7 +1069,9 @@ def main():
                    "table": "resident, built once per grid: %.2f ms (first build %.2f ms), not in the step" % (
                        table_ms, first_table_ms),
                    "first_call_ms": first_call_ms, "max_rel_err_vs_oracle": err,
-                   "max_rel_err_sample": "%d sources" % args.cpu_models if err is not None else None,
+                   "max_rel_err_by_l": err_by_l,
+                   "max_rel_err_sample": ("%d of %d sources, every l" % (min(args.cpu_models, M), M)
+                                          if err is not None else None),
                    "plain64_spectra_per_s": plain64_rate, "speedup_vs_plain64": value / world / plain64_rate,
                    "active_entries": info["active"], "kernel_ms": {k: (v[0] / max(1, v[1])) for k, v in kern.items()},
                    "work_items": pinfo["items"], "l_tiles_per_item": pinfo["lp"], "ctas": pinfo["ctas"],

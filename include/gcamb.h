@@ -305,9 +305,10 @@ int gcamb_los_cl_workspace(const gcamb_grid *g, int M, int mode, size_t *bytes);
  * weighted by 4 pi w_k P_m(k) and summed over k without being stored.
  * hi*hi is accumulated apart from hi*lo + lo*hi (two TMEM accumulators), so
  * the main chain takes a third of the accumulate steps.  Partial sums over
- * k-chunks of at most 64 nodes are FP32; the final sum over chunks runs in a
- * fixed order (deterministic) as a TwoSum pair of FP32 numbers, read out in
- * FP64.  Two adjacent 128-multipole tiles share each loaded and split source
+ * k-chunks of at most 16 nodes with stored blocks are FP32 (each within
+ * 15 * 2^-24 of the exact sum of its positive terms, relative); the final sum
+ * over chunks runs in a fixed order (deterministic) as a TwoSum pair of FP32
+ * numbers, read out in FP64.  Two adjacent 128-multipole tiles share each loaded and split source
  * block (bf16/fp16 with 64- or 128-source tiles).  GCAMB_F16X3 scales the table by one power
  * of two per grid and each (k, source) row of S by its own power of two so
  * that both land in fp16's normal range; the scales are removed exactly.
@@ -323,7 +324,9 @@ int gcamb_los_cl_workspace(const gcamb_grid *g, int M, int mode, size_t *bytes);
  * Environment (tuning switches, read when a plan is built; the results agree
  * within the bounds the tests state): GCAMB_TC_NT=64|128|256 source-tile
  * width; GCAMB_TC_FUSED=0 splits the sources in a separate pass instead of in
- * shared memory; GCAMB_TC_LP=1 one multipole tile per work item instead of two.
+ * shared memory; GCAMB_TC_LP=1 one multipole tile per work item instead of two;
+ * GCAMB_TC_KSUB=1..64 k nodes per FP32 chunk sum instead of 16 (1: every k's
+ * term is its own partial, and C_l is the FP64 sum of the FP32 terms).
  * Errors: GCAMB_EINVAL, GCAMB_ESTATE, GCAMB_EUNSUPPORTED (device is not
  * sm_103), GCAMB_ECUDA; GCAMB_ETIMEOUT is reported by gcamb_sync.
  */
@@ -544,16 +547,22 @@ int gcamb_synth_sources(const gcamb_grid *g, const float *X, int M, float *S, do
  * Limits and behaviour:
  *  - Problems whose scratch exceeds 64 MiB are rejected with GCAMB_EINVAL
  *    (the message gives the bytes needed); use gcamb_los_cl for them.  The
- *    scratch holds the k-chunk partial sums, 64 KB per work item at 128
- *    sources per tile (about 4 items per SM, and at least one per 64 k per
- *    l-tile per source tile), and 4-8 bytes per (k, source) of weights.
+ *    scratch holds the k-chunk partial sums, 64 KB per (chunk of up to 16 k,
+ *    l-tile, source tile) at 128 sources per tile, and 4-8 bytes per
+ *    (k, source) of weights.
  *    When the sources cannot be read in place (ntau not a multiple of 4, or
  *    the TF32X3 mode) it also holds the split sources, about 4 bytes per
  *    (k, tau, source), which with 1000 tau nodes limits nk * M to about
  *    15,000.
- *  - The first call on a device looks up the buffer's device address
- *    (cudaGetSymbolAddress) and caches it; make that first call before any
- *    stream capture.
+ *  - Every call looks up the buffer's device address on the current device
+ *    (cudaGetSymbolAddress).  The first call on a device may load the
+ *    library's device code there (lazy module loading), which sets the
+ *    buffer up; make it before any stream capture on that device.
+ *  - A call on a stream that is being captured is refused with
+ *    GCAMB_EUNSUPPORTED: the work list is copied up from host memory that
+ *    lives only for the call.
+ *  - The device error word used when status is NULL is set up by the grid's
+ *    first device call (gcamb_bessel_table), not here.
  *  - All calls share the one buffer, and each call overwrites all of the
  *    scratch it uses before reading it, so nothing has to start at zero.
  *    Calls whose device work overlaps (on different streams, or from
@@ -574,10 +583,10 @@ int gcamb_sync(void *stream);
 #define GCAMB_K_TABLE     0  /* Bessel table generation */
 #define GCAMB_K_LOS_PLAIN 1  /* plain transfer, Eq. (2) */
 #define GCAMB_K_CL        2  /* Eq. (1) k-sum of stored transfers */
-#define GCAMB_K_SPLIT     3  /* hi/lo split of the sources (batched path) */
-#define GCAMB_K_WEIGHTS   4  /* 4 pi w_k P(k) weights (batched path) */
+#define GCAMB_K_SPLIT     3  /* split pass: hi/lo planes and weights of the sources (batched path) */
+#define GCAMB_K_WEIGHTS   4  /* sqrt(4 pi w_k P(k)) weights, fp16 row scales, TE tails (batched path) */
 #define GCAMB_K_TC        5  /* tensor-core contraction + square + k-chunk sum */
-#define GCAMB_K_REDUCE    6  /* FP64 sum of the k-chunk partials */
+#define GCAMB_K_REDUCE    6  /* fixed-order sum of the k-chunk partials (compensated), read out in FP64 */
 #define GCAMB_K_INTERP    7  /* splines: sources onto the transfer k grid, C_l onto every l */
 #define GCAMB_K_COUNT     8
 

@@ -159,6 +159,10 @@ int ensure_device_grid(gcamb_grid *g) {
   };
   if ((e = upi(&g->d_lrow, g->lrow)) != cudaSuccess) return cuda_fail(e, "grid upload");
   if ((e = upi(&g->d_rowof, g->rowof)) != cudaSuccess) return cuda_fail(e, "grid upload");
+  // the mapped error word is set up here, with the grid's first device copy,
+  // so that no later call (the allocation-free entry point in particular)
+  // has to allocate it
+  if (!device_error_flag()) return fail(GCAMB_ECUDA, "grid upload: error flag allocation");
   return GCAMB_OK;
 }
 

@@ -11,8 +11,9 @@
 // The buffer is a file-scope __device__ array of kFixedScratchBytes (64 MiB).
 // Every device that loads this module holds it until the process exits.  In
 // host code the array's name is only a host-side stand-in, so its device
-// address is fetched once per device with cudaGetSymbolAddress and cached.
-#include <mutex>
+// address is looked up with cudaGetSymbolAddress, on the current device, at
+// every call (a lookup costs no device work, and a cached address would go
+// stale if the context were torn down and the module loaded again).
 #include <string>
 
 #include "internal.h"
@@ -21,26 +22,14 @@ namespace gcamb {
 namespace {
 
 constexpr size_t kFixedScratchBytes = size_t(64) << 20;
-constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) unsigned char g_fixed_scratch[kFixedScratchBytes];
 
-std::mutex g_fixed_mu;
-char *g_fixed_addr[kMaxDevices] = {};
-
 int fixed_scratch(char **out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return cuda_fail(e, "los_cl_noalloc: cudaGetDevice");
-  if (dev < 0 || dev >= kMaxDevices) return fail(GCAMB_EUNSUPPORTED, "los_cl_noalloc: device index too large");
-  std::lock_guard<std::mutex> lk(g_fixed_mu);
-  if (!g_fixed_addr[dev]) {
-    void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_fixed_scratch);
-    if (e != cudaSuccess || !p) return cuda_fail(e, "los_cl_noalloc: cudaGetSymbolAddress");
-    g_fixed_addr[dev] = static_cast<char *>(p);
-  }
-  *out = g_fixed_addr[dev];
+  void *p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_fixed_scratch);
+  if (e != cudaSuccess || !p) return cuda_fail(e, "los_cl_noalloc: cudaGetSymbolAddress");
+  *out = static_cast<char *>(p);
   return GCAMB_OK;
 }
 
@@ -64,6 +53,14 @@ extern "C" int gcamb_los_cl_noalloc(const gcamb_grid *g, const float *S, const d
   cudaDeviceGetAttribute(&maj, cudaDevAttrComputeCapabilityMajor, dev);
   cudaDeviceGetAttribute(&mnr, cudaDevAttrComputeCapabilityMinor, dev);
   if (maj != 10 || mnr != 3) return fail(GCAMB_EUNSUPPORTED, "los_cl_noalloc: needs an sm_103 device");
+  // The work list is uploaded from host memory that lives only for this
+  // call, which a captured copy would read again at every replay: refuse
+  // to run inside a stream capture.
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t ce = cudaStreamIsCapturing((cudaStream_t)stream, &cs);
+  if (ce != cudaSuccess) return cuda_fail(ce, "los_cl_noalloc: cudaStreamIsCapturing");
+  if (cs != cudaStreamCaptureStatusNone)
+    return fail(GCAMB_EUNSUPPORTED, "los_cl_noalloc: not available inside a stream capture");
   char *scratch = nullptr;
   int rc = fixed_scratch(&scratch);
   if (rc) return rc;

@@ -7,9 +7,10 @@
 // Algorithm 1 window).  Both operands are split into hi + lo parts (bf16 or
 // tf32) and D_k accumulates hi*hi + hi*lo + lo*hi in FP32 in tensor memory.
 // The epilogue squares D_k, weights it by 4 pi w_k P_m(k) (Eq. 1) and adds it
-// to per-thread FP32 sums over a chunk of at most 64 k; a second kernel adds
-// the chunk sums in a fixed order (TwoSum pairs, read out in FP64).  D_k
-// never leaves the SM.
+// to per-thread FP32 sums over a chunk of at most 16 k (each chunk sum of
+// n <= 16 positive terms is within (n - 1) 2^-24 of their exact sum); a second
+// kernel adds the chunk sums in a fixed order (TwoSum pairs, read out in
+// FP64).  D_k never leaves the SM.
 //
 // Work item = (l-tile, source tile, contiguous k-chunk); with LP = 2 (fused
 // uniform batches) two adjacent l-tiles that share each source block.  One
@@ -47,14 +48,17 @@ namespace {
 
 constexpr int kEpiWarps = 8;
 constexpr int kConvWarps = 4;
-constexpr int kKChunkMax = 64;     // k per work item: bounds the FP32 partial-sum length
+constexpr int kKChunkMax = 64;     // k per work item
+constexpr int kKSub = 16;          // records (k) per FP32 chunk sum: each item's sums are flushed to
+                                   // their own partial every kKSub records (GCAMB_TC_KSUB overrides it)
 constexpr int kSmemBudget = 196608;
 
 // Work item: first l-tile, source tile, k range [qb, qe), and its number of
 // l-tiles (LP = 2 plans: 2, or 1 where the source tile's l_max stops before
-// the second tile or no tile follows).
+// the second tile or no tile follows); pbase: its first partial slot (one
+// slot per chunk of ksub non-empty k, each holding LP tiles' sums).
 struct TcItem {
-  int lt, mt, qb, qe, ntl, pad[3];
+  int lt, mt, qb, qe, ntl, pbase, pad[2];
 };
 
 struct TcParams {
@@ -71,7 +75,8 @@ struct TcParams {
   const TcItem *items;
   int *counter;          // next item to hand out (zeroed before each launch)
   int nitems;
-  float *partial;        // [n_items * LP][NT][128] (TE: [n_items][3 NT/2][128])
+  int ksub;              // non-empty k per FP32 chunk sum (partial slot)
+  float *partial;        // [n_slots * LP][NT][128] (TE: [n_slots][3 NT/2][128])
   int *err;
   int nlt, n_mt, nkbs, mpad;
 };
@@ -348,6 +353,7 @@ __global__ void __launch_bounds__(TcRoles<FUSED, TE, LP>::kThreadsT, 1)
         }
         __syncwarp();
         if (lane == 0) {
+          int rc = 0;  // records of this item so far: chunk rc / ksub, slot pbase + rc / ksub
           for (int j = 0; j < cnt && ok; ++j) {
             const int q = it.qb + j;
             const int nb0 = q_nb[j];
@@ -363,8 +369,11 @@ __global__ void __launch_bounds__(TcRoles<FUSED, TE, LP>::kThreadsT, 1)
             volatile int *hdr = reinterpret_cast<volatile int *>(rec);
             hdr[0] = q;
             hdr[1] = LP == 2 ? (nb0 | (nb1 << 16)) : nb;  // LP = 2: both tiles' block counts (< 2^15 each)
-            hdr[2] = item;
-            hdr[3] = it.mt | (q == it.qb ? kFirst : 0) | (q == it.qe - 1 ? kLast : 0) | (TE && it.lt == 0 ? kL2 : 0);
+            hdr[2] = it.pbase + rc / p.ksub;                // the chunk's partial slot
+            const int rs = rc % p.ksub;
+            hdr[3] = it.mt | (rs == 0 ? kFirst : 0) | ((rs == p.ksub - 1 || q == it.qe - 1) ? kLast : 0) |
+                     (TE && it.lt == 0 ? kL2 : 0);
+            ++rc;
             const uint32_t kb_bar = kfull0 + 8 * ks;
             karmed[ks] = (int)kph;
             if constexpr (TE) {
@@ -715,7 +724,7 @@ __global__ void __launch_bounds__(TcRoles<FUSED, TE, LP>::kThreadsT, 1)
         const volatile int *hdr = reinterpret_cast<const volatile int *>(rec);
         const int nb = hdr[1];
         if (nb < 0) break;
-        const int item = hdr[2], flags = hdr[3];
+        const int item = hdr[2], flags = hdr[3];  // item: the chunk's partial slot
         const int buf = n % NB;
         const uint32_t use = (uint32_t)(n / NB);
         if (!mbar_wait(tfull0 + 8 * buf, use & 1u, abort_flag, p.err)) break;
@@ -790,7 +799,7 @@ __global__ void __launch_bounds__(TcRoles<FUSED, TE, LP>::kThreadsT, 1)
         const volatile int *hdr = reinterpret_cast<const volatile int *>(rec);
         const int hv = hdr[1];
         if (hv < 0) break;
-        const int item = hdr[2], flags = hdr[3];
+        const int item = hdr[2], flags = hdr[3];  // item: the chunk's partial slot
         if (flags & kFirst) {
 #pragma unroll
           for (int j = 0; j < C::kColsPerThread; ++j) acc[j] = 0.f;
@@ -835,7 +844,7 @@ __global__ void __launch_bounds__(TcRoles<FUSED, TE, LP>::kThreadsT, 1)
           kph ^= 1u;
         }
         if (flags & kLast) {
-          // k-chunk sums of (item, tile): partial index item * LP + tile
+          // k-chunk sums of (chunk slot, tile): partial index slot * LP + tile
           float *part = p.partial + ((size_t)item * LP + tile) * NT * 128;
 #pragma unroll
           for (int j = 0; j < C::kColsPerThread; ++j) part[(size_t)(col0 + j) * 128 + row] = acc[j];
@@ -1229,6 +1238,8 @@ struct TcPlan {
   bool fused = false;  // sources converted inside the tensor-core kernel (no split pass)
   bool te = false;     // temperature + E-mode: NT models per tile, 2 NT operand rows
   int lp = 1;          // l-tiles per item (2: adjacent tiles share the item's source blocks)
+  int ksub = kKSub;    // non-empty k per FP32 chunk sum
+  int nslots = 0;      // chunk slots (each lp tiles' partials)
   std::vector<int> blob;
   size_t o_items = 0, o_tile_ptr = 0, o_tile_items = 0, o_perm = 0, o_nkm = 0, o_lmaxm = 0, o_tnk = 0;
   std::vector<double> cost;  // per item
@@ -1283,6 +1294,17 @@ int want_lp(int mode, int nt, bool te) {
   if (const char *e = getenv("GCAMB_TC_LP"))
     if (e[0] == '1') return 1;
   return 2;
+}
+
+// Non-empty k per FP32 chunk sum of the epilogue (the partial-sum length):
+// kKSub, or GCAMB_TC_KSUB = 1..64 (1: every k's term is its own partial, so
+// the reduce's compensated sum is the FP64 sum of the FP32 terms).
+int want_ksub() {
+  if (const char *e = getenv("GCAMB_TC_KSUB")) {
+    const int v = atoi(e);
+    if (v >= 1 && v <= kKChunkMax) return v;
+  }
+  return kKSub;
 }
 
 using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -1401,7 +1423,7 @@ void plan_build(const gcamb_grid *g, int M, int mode, int nt, const int *lmax_c,
         const double kc = kcost(q, lt, ntl);
         if (kc == 0.0) continue;
         if (qb >= 0 && q - qb + 1 > kKChunkMax) {
-          items.push_back({lt, mt, qb, qlast + 1, ntl, {0, 0, 0}});
+          items.push_back({lt, mt, qb, qlast + 1, ntl, 0, {0, 0}});
           pl.cost.push_back(c);
           qb = -1;
         }
@@ -1412,13 +1434,13 @@ void plan_build(const gcamb_grid *g, int M, int mode, int nt, const int *lmax_c,
         }
         c += kc;
         if (c >= target || q - qb + 1 >= kKChunkMax) {
-          items.push_back({lt, mt, qb, q + 1, ntl, {0, 0, 0}});
+          items.push_back({lt, mt, qb, q + 1, ntl, 0, {0, 0}});
           pl.cost.push_back(c);
           qb = -1;
         }
       }
       if (qb >= 0) {
-        items.push_back({lt, mt, qb, qlast + 1, ntl, {0, 0, 0}});
+        items.push_back({lt, mt, qb, qlast + 1, ntl, 0, {0, 0}});
         pl.cost.push_back(c);
       }
     }
@@ -1442,12 +1464,26 @@ void plan_build(const gcamb_grid *g, int M, int mode, int nt, const int *lmax_c,
     pl.cost.swap(sc);
   }
   pl.nctas = std::max(1, std::min(sms, pl.nitems));
-  // per (l-tile, source tile): its items' partials in increasing k (fixed
-  // reduce order); item i writes partial i * lp + s for its tile lt + s
+  // chunk slots: an item's FP32 sums are flushed every ksub non-empty k (the
+  // producer's records), each chunk to its own slot of lp tiles' partials
+  pl.ksub = want_ksub();
+  std::vector<int> nchunk(pl.nitems);
+  pl.nslots = 0;
+  for (int i = 0; i < pl.nitems; ++i) {
+    int rec = 0;
+    for (int q = items[i].qb; q < items[i].qe; ++q)
+      if (kcost(q, items[i].lt, items[i].ntl) > 0.0) ++rec;
+    nchunk[i] = (rec + pl.ksub - 1) / pl.ksub;
+    items[i].pbase = pl.nslots;
+    pl.nslots += nchunk[i];
+  }
+  // per (l-tile, source tile): its chunks' partials in increasing k (fixed
+  // reduce order); chunk c of item i writes partial (pbase + c) * lp + s for
+  // its tile lt + s
   pl.ntile = g->nlt * pl.n_mt;
   std::vector<int> tile_ptr(pl.ntile + 1, 0);
-  for (const auto &x : items)
-    for (int sub = 0; sub < x.ntl; ++sub) tile_ptr[(x.lt + sub) * pl.n_mt + x.mt + 1]++;
+  for (int i = 0; i < pl.nitems; ++i)
+    for (int sub = 0; sub < items[i].ntl; ++sub) tile_ptr[(items[i].lt + sub) * pl.n_mt + items[i].mt + 1] += nchunk[i];
   for (int i = 0; i < pl.ntile; ++i) tile_ptr[i + 1] += tile_ptr[i];
   std::vector<int> tile_items(tile_ptr[pl.ntile]);
   {
@@ -1455,8 +1491,9 @@ void plan_build(const gcamb_grid *g, int M, int mode, int nt, const int *lmax_c,
     for (int i = 0; i < pl.nitems; ++i) idx[i] = i;
     std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return items[a].qb < items[b].qb; });
     for (int i : idx)
-      for (int sub = 0; sub < items[i].ntl; ++sub)
-        tile_items[fill[(items[i].lt + sub) * pl.n_mt + items[i].mt]++] = i * lp + sub;
+      for (int c = 0; c < nchunk[i]; ++c)
+        for (int sub = 0; sub < items[i].ntl; ++sub)
+          tile_items[fill[(items[i].lt + sub) * pl.n_mt + items[i].mt]++] = (items[i].pbase + c) * lp + sub;
   }
   // blob
   pl.blob.clear();
@@ -1481,7 +1518,7 @@ void plan_build(const gcamb_grid *g, int M, int mode, int nt, const int *lmax_c,
   const size_t sp_bytes = pl.fused ? 0 : (size_t)g->nk * pl.n_mt * pl.nkbs * 2 * row_b * pl.NT;
   const size_t wp_bytes = (size_t)g->nk * pl.mpad * sizeof(float);
   const size_t sc_bytes = (te || (pl.fused && mode == GCAMB_F16X3)) ? wp_bytes : 0;
-  const size_t part_bytes = std::max<size_t>(1, pl.nitems) * lp * (te ? 3 : 1) * pl.NT * 128 * sizeof(float);
+  const size_t part_bytes = std::max<size_t>(1, pl.nslots) * lp * (te ? 3 : 1) * pl.NT * 128 * sizeof(float);
   pl.off_sp = 0;
   pl.off_wp = align256(sp_bytes);
   pl.off_sc = pl.off_wp + align256(wp_bytes);
@@ -1509,7 +1546,7 @@ TcPlan *get_plan(const gcamb_grid *g, int M, int mode, int *rc) {
   const int nt = pick_nt(M);
   for (auto &e : g_plans)
     if (e.first == g && !e.second->te && e.second->M == M && e.second->mode == mode && e.second->NT == nt &&
-        e.second->fused == want_fused(g, mode, nt, true) &&
+        e.second->fused == want_fused(g, mode, nt, true) && e.second->ksub == want_ksub() &&
         e.second->lp == (e.second->nkbs < 32768 ? want_lp(mode, nt, false) : 1))
       return e.second;
   TcPlan *pl = new TcPlan();
@@ -1559,7 +1596,9 @@ int launch_tc(const gcamb_grid *g, const TcPlan &pl, const float *S, const doubl
     const size_t rows = (size_t)g->nk * pl.mpad;
     const int vec = (g->ntau % 4 == 0) && (reinterpret_cast<uintptr_t>(S) % 16 == 0);
     const unsigned nblk = (unsigned)((rows + 7) / 8);
-    ProfScope prof(GCAMB_K_SPLIT, st);
+    // the fused kernel's inputs (weights; fp16: and the row scales) are
+    // traced as weights, the split pass (which also writes the weights) as split
+    ProfScope prof(fused ? GCAMB_K_WEIGHTS : GCAMB_K_SPLIT, st);
     if (fused && MODE == kBF16)
       weights_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(Pk, g->d_wk, g->d_k, pl.M, g->nk, pl.mpad, perm,
                                                                      nkm, wp);
@@ -1583,7 +1622,7 @@ int launch_tc(const gcamb_grid *g, const TcPlan &pl, const float *S, const doubl
   if (pl.nitems > 0) {
     int *ctr = reinterpret_cast<int *>(ws + pl.off_ctr);
     TcParams prm{static_cast<const char *>(t.d_data), nullptr, t.d_off, t.d_nkb, sp, wp, sc, nullptr, -1,
-                 pl.items(B), ctr, pl.nitems, part, use_err_word ? err_word : device_error_flag(), g->nlt, pl.n_mt,
+                 pl.items(B), ctr, pl.nitems, pl.ksub, part, use_err_word ? err_word : device_error_flag(), g->nlt, pl.n_mt,
                  pl.nkbs, pl.mpad};
     if (!prm.err && !use_err_word) return fail(GCAMB_ECUDA, "los_cl: error flag allocation");
     int rc;
@@ -1657,7 +1696,8 @@ TcPlan *get_plan_te(const gcamb_grid *g, int M, int *rc) {
   std::lock_guard<std::mutex> lk(g_plan_mu);
   const int h = pick_h_te(M);
   for (auto &e : g_plans)
-    if (e.first == g && e.second->te && e.second->M == M && e.second->NT == h) return e.second;
+    if (e.first == g && e.second->te && e.second->M == M && e.second->NT == h && e.second->ksub == want_ksub())
+      return e.second;
   TcPlan *pl = new TcPlan();
   plan_build(g, M, GCAMB_BF16X3, h, nullptr, nullptr, *pl, true);
   if ((*rc = upload_blob(*pl)) == GCAMB_OK) *rc = build_ix2(g, *pl);
@@ -1689,7 +1729,7 @@ int launch_tc_te(const gcamb_grid *g, const TcPlan &pl, const float *ST, const f
   if (int rc = encode_sources(&tm1, ST, pl.M, g->nk, g->ntau, H)) return rc;
   if (int rc = encode_sources(&tm2, SP, pl.M, g->nk, g->ntau, H)) return rc;
   {
-    ProfScope prof(GCAMB_K_SPLIT, st);
+    ProfScope prof(GCAMB_K_WEIGHTS, st);
     const size_t rows = (size_t)g->nk * pl.mpad;
     te_weights_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(Pk, g->d_wk, g->d_k, g->d_tau, g->tau0, xlo,
                                                                       g->d_wtau, SP, pl.M, g->nk, g->ntau, pl.mpad, wp,
@@ -1702,7 +1742,7 @@ int launch_tc_te(const gcamb_grid *g, const TcPlan &pl, const float *ST, const f
                        ? g->rowof[2 - g->lmin]
                        : -1;
     TcParams prm{static_cast<const char *>(t.d_data), nullptr, t.d_off, t.d_nkb, nullptr, wp, tail, ix2, r2,
-                 pl.items(B), ctr, pl.nitems, part, device_error_flag(), g->nlt, pl.n_mt, pl.nkbs, pl.mpad};
+                 pl.items(B), ctr, pl.nitems, pl.ksub, part, device_error_flag(), g->nlt, pl.n_mt, pl.nkbs, pl.mpad};
     if (!prm.err) return fail(GCAMB_ECUDA, "los_cl_te: error flag allocation");
     if (int rc = launch_tc_kernel<NT, kBF16, true, 1>(g, pl, tm1, tm2, prm, st)) return rc;
   }
@@ -1732,7 +1772,7 @@ int launch_tc_pair(const gcamb_grid *gx, const gcamb_grid *gy, const TcPlan &pl,
   if (int rc = encode_sources(&tm1, SX, pl.M, gx->nk, gx->ntau, H)) return rc;
   if (int rc = encode_sources(&tm2, SY, pl.M, gx->nk, gx->ntau, H)) return rc;
   {
-    ProfScope prof(GCAMB_K_SPLIT, st);
+    ProfScope prof(GCAMB_K_WEIGHTS, st);
     const size_t rows = (size_t)gx->nk * pl.mpad;
     // weights; no small-x tails (the kernel tables hold the series): x_lo < 0
     te_weights_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(Pk, gx->d_wk, gx->d_k, gx->d_tau, gx->tau0, -1.0,
@@ -1742,7 +1782,7 @@ int launch_tc_pair(const gcamb_grid *gx, const gcamb_grid *gy, const TcPlan &pl,
   if (pl.nitems > 0) {
     int *ctr = reinterpret_cast<int *>(ws + pl.off_ctr);
     TcParams prm{static_cast<const char *>(tx.d_data), static_cast<const char *>(ty.d_data), tx.d_off, tx.d_nkb,
-                 nullptr, wp, tail, nullptr, -1, pl.items(B), ctr, pl.nitems, part, device_error_flag(), gx->nlt,
+                 nullptr, wp, tail, nullptr, -1, pl.items(B), ctr, pl.nitems, pl.ksub, part, device_error_flag(), gx->nlt,
                  pl.n_mt, pl.nkbs, pl.mpad};
     if (!prm.err) return fail(GCAMB_ECUDA, "los_cl_pair: error flag allocation");
     if (int rc = launch_tc_kernel<NT, kBF16, true, 2>(gx, pl, tm1, tm2, prm, st)) return rc;

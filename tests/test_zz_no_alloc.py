@@ -68,3 +68,63 @@ def test_noalloc_rejects_problems_beyond_its_buffer():
         gcamb.los_cl_noalloc(g, S, P, gcamb.F16X3, C)
     assert ei.value.code == gcamb.EINVAL
     assert "scratch" in str(ei.value)
+
+
+_FRESH = r"""
+import numpy as np, torch
+from paper_2509_25110_gb300 import gcamb, synth
+k = synth.log_grid(1e-4, 0.3, 40)
+tau = synth.uniform_grid(200.0, 14000.0, 256)
+M = 24
+g = gcamb.grid_create(k, tau, 14000.0, 2, 300)
+gcamb.bessel_table(g, gcamb.F16X3)
+p = synth.model_params(M, seed=21)
+S = torch.as_tensor(synth.sources(k, tau, p).astype(np.float32), device="cuda")
+P = torch.as_tensor(synth.primordial(k, p), device="cuda")
+C = torch.full((M, g.nl), float("nan"), dtype=torch.float64, device="cuda")
+gcamb.los_cl_noalloc(g, S, P, gcamb.F16X3, C)   # the first batched call of the process, no status word
+gcamb.sync()
+ref = gcamb.los_cl(g, S, P, gcamb.F16X3).cpu().numpy()
+got = C.cpu().numpy()
+assert np.all(np.isfinite(got))
+np.testing.assert_allclose(got, ref, rtol=1e-5, atol=0)
+print("FRESH_OK")
+"""
+
+
+def test_noalloc_without_status_word_in_a_fresh_process():
+    # status = NULL reports a timeout through the library's error word, which
+    # the grid's first device call has set up: the entry point itself still
+    # allocates nothing, even as the first library launch of a process
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _FRESH], cwd=root, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-2000:]
+    assert "FRESH_OK" in r.stdout
+
+
+def test_noalloc_refuses_a_capturing_stream():
+    k = synth.log_grid(1e-4, 0.3, 32)
+    tau = synth.uniform_grid(200.0, 14000.0, 128)
+    g = gcamb.grid_create(k, tau, 14000.0, 2, 200)
+    gcamb.bessel_table(g, gcamb.F16X3)
+    S, P = _inputs(k, tau, 8, 14)
+    C = torch.empty((8, g.nl), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        graph.capture_begin()
+        try:
+            with pytest.raises(gcamb.GcambError) as ei:
+                gcamb.los_cl_noalloc(g, S, P, gcamb.F16X3, C, stream=s)
+        finally:
+            graph.capture_end()
+    assert ei.value.code == gcamb.EUNSUPPORTED
+    assert "capture" in str(ei.value)
+    # the call still works outside the capture
+    gcamb.los_cl_noalloc(g, S, P, gcamb.F16X3, C)
+    gcamb.sync()
+    np.testing.assert_allclose(C.cpu().numpy(), gcamb.los_cl(g, S, P, gcamb.F16X3).cpu().numpy(), rtol=TOL, atol=0)
