@@ -56,9 +56,11 @@ constexpr int kSmemBudget = 196608;
 // Work item: first l-tile, source tile, k range [qb, qe), and its number of
 // l-tiles (LP = 2 plans: 2, or 1 where the source tile's l_max stops before
 // the second tile or no tile follows); pbase: its first partial slot (one
-// slot per chunk of ksub non-empty k, each holding LP tiles' sums).
+// slot per chunk of ksub non-empty k, each holding LP tiles' sums); chain:
+// (LP = 2 plans) an item of l-tile 0 alone whose hi*hi sum is spread over
+// three accumulators (see the MMA warp).
 struct TcItem {
-  int lt, mt, qb, qe, ntl, pbase, pad[2];
+  int lt, mt, qb, qe, ntl, pbase, chain, pad;
 };
 
 struct TcParams {
@@ -76,6 +78,7 @@ struct TcParams {
   int *counter;          // next item to hand out (zeroed before each launch)
   int nitems;
   int ksub;              // non-empty k per FP32 chunk sum (partial slot)
+  int chain_free;        // LP = 2: a k at which the item's second tile has no blocks is a chain record
   float *partial;        // [n_slots * LP][NT][128] (TE: [n_slots][3 NT/2][128])
   int *err;
   int nlt, n_mt, nkbs, mpad;
@@ -165,6 +168,8 @@ __device__ __forceinline__ void tmem_ld(uint32_t taddr, float (&v)[W]) {
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
+  } else if constexpr (W == 2) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(taddr));
   } else if constexpr (W == 4) {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
                  : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
@@ -213,8 +218,9 @@ struct TcCfg {
 
 // Warp roles.  LP = 2 keeps each role in whole warpgroups (warps 2, 3 idle)
 // so that the warpgroups can trade registers: launched at 80 a thread (24
-// warps), the producer/MMA and converter warpgroups drop to 64 and the four
-// epilogue warpgroups take 88 (8 x 64 + 16 x 88 = 24 x 80).
+// warps), the producer/MMA warpgroup drops to 40, the converter warpgroup to
+// 56, and the four epilogue warpgroups take 96 (4 x 40 + 4 x 56 + 16 x 96 =
+// 24 x 80).
 template <bool FUSED, int TE = 0, int LP = 1>
 struct TcRoles {
   static constexpr int kConv = FUSED ? kConvWarps : 0;
@@ -222,7 +228,9 @@ struct TcRoles {
   static constexpr int kEpi0 = kConv0 + kConv;    // first epilogue warp
   static constexpr int kEpi = kEpiWarps * LP;
   static constexpr int kThreadsT = 32 * (kEpi0 + kEpi);
-  static constexpr int kRegLow = 64, kRegHigh = 88;  // LP = 2 split
+  // LP = 2 split (launched at 80 a thread): producer/MMA warpgroup, converter
+  // warpgroup, four epilogue warpgroups: 4 x 40 + 4 x 56 + 16 x 96 = 24 x 80
+  static constexpr int kRegCtl = 40, kRegConv = 56, kRegHigh = 96;
 };
 
 // Per-k record, written by the producer into a ring in shared memory:
@@ -231,6 +239,11 @@ struct TcRoles {
 // scales; TE: the NT/2 models' weights and small-x tails.  nb < 0 ends the
 // work.  kL2: the item's l-tile is the first (it may hold l = 2).
 constexpr int kFirst = 1 << 16, kLast = 1 << 17, kL2 = 1 << 18;
+// LP = 2, chain record (the item's first l-tile only at this k): its hi*hi
+// products go round-robin by tau-block into three accumulators (the tile's
+// own D_hh and the other tile's pair), its corrections into the tile's D_x
+// (see the MMA warp).
+constexpr int kChain = 1 << 19;
 
 // TE = 2 (pair): two fields X, Y of kernel grids with the same layout (for
 // instance the tensor T and E kernels): each stage holds a block of both
@@ -290,7 +303,9 @@ __global__ void __launch_bounds__(TcRoles<FUSED, TE, LP>::kThreadsT, 1)
     }
     for (int b = 0; b < TB; ++b) {
       mbar_init(tfull0 + 8 * b, 1);
-      mbar_init(tempty0 + 8 * b, kEpiWarps);  // the 8 epilogue warps of the accumulator pair's tile
+      // the 8 epilogue warps of the accumulator pair's tile (LP = 2: two
+      // arrivals each, or one from each of the 16 warps on a chain item)
+      mbar_init(tempty0 + 8 * b, LP == 2 ? 2 * kEpiWarps : kEpiWarps);
     }
     mbar_init(drain, 1);
     *abort_flag = 0;
@@ -313,11 +328,8 @@ __global__ void __launch_bounds__(TcRoles<FUSED, TE, LP>::kThreadsT, 1)
 
   // Roles.  Each register change sits in its warpgroups' own branch, so that
   // the code it covers is compiled to its budget.
-  if (warp < R::kEpi0) {
-    if constexpr (LP == 2 && FUSED) {
-      static_assert(R::kThreadsT == 768 && R::kEpi0 == 8, "LP = 2 register split: 6 warpgroups");
-      asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(R::kRegLow));
-    }
+  // producer (warp 0) and MMA issuer (warp 1)
+  auto control_role = [&]() {
     if (warp == 0) {
       // ---------------- producer: items from the counter; the whole warp loads
       // the item's block counts and table offsets into shared memory (one
@@ -372,7 +384,8 @@ __global__ void __launch_bounds__(TcRoles<FUSED, TE, LP>::kThreadsT, 1)
             hdr[2] = it.pbase + rc / p.ksub;                // the chunk's partial slot
             const int rs = rc % p.ksub;
             hdr[3] = it.mt | (rs == 0 ? kFirst : 0) | ((rs == p.ksub - 1 || q == it.qe - 1) ? kLast : 0) |
-                     (TE && it.lt == 0 ? kL2 : 0);
+                     (TE && it.lt == 0 ? kL2 : 0) |
+                     (LP == 2 && (it.chain || (p.chain_free && nb1 == 0)) ? kChain : 0);
             ++rc;
             const uint32_t kb_bar = kfull0 + 8 * ks;
             karmed[ks] = (int)kph;
@@ -480,6 +493,7 @@ __global__ void __launch_bounds__(TcRoles<FUSED, TE, LP>::kThreadsT, 1)
           if (!mbar_wait(kfull0 + 8 * ks, kph, abort_flag, p.err)) break;
           const int hv = reinterpret_cast<volatile int *>(kslots + ks * C::kSlotBytes)[1];
           if (hv < 0) break;
+          const int hfl = reinterpret_cast<volatile int *>(kslots + ks * C::kSlotBytes)[3];
           mbar_arrive(kempty0 + 8 * ks);
           if (++ks == KS) {
             ks = 0;
@@ -498,6 +512,63 @@ __global__ void __launch_bounds__(TcRoles<FUSED, TE, LP>::kThreadsT, 1)
               dt[t] = tmem + (uint32_t)(bt[t] * 2 * NT);
             }
             bool ok = true;
+            if (hfl & kChain) {
+              // Chain record (the item's first tile only: the second has no
+              // blocks at this k, or the item is l-tile 0 alone).  The tensor cores add each MMA's
+              // products to the FP32 accumulator after dropping their bits
+              // below a quarter ulp of the largest term and truncate the sum,
+              // so every accumulate step loses a little relative to the running
+              // sum.  Three accumulators that each take every third tau-block
+              // hold about a third of the sum each, which cuts the loss to
+              // about a third.  D_hh of block kb: kb % 3 == 0 -> this tile's
+              // D_hh (with its D_x, one N = 2 NT MMA), 1 -> the other pair's
+              // D_hh, 2 -> the other pair's D_x; every correction goes to this
+              // tile's D_x.  Both pairs are waited for (empty) and committed
+              // (full); the epilogue reads the chains that received a block.
+#pragma unroll
+              for (int t = 0; t < 2; ++t)
+                if (ok && !mbar_wait(tempty0 + 8 * bt[t], ((uint32_t)(nt2[t] / NB) & 1u) ^ 1u, abort_flag, p.err))
+                  ok = false;
+              if (!ok) break;
+              tc_fence_after();
+              const uint32_t dx0 = dt[0] + (uint32_t)NT;
+              for (int kb = 0; kb < nbt[0] && ok; ++kb) {
+                if ((FUSED && !mbar_wait(conv0 + 8 * stage, phase, abort_flag, p.err)) ||
+                    !mbar_wait(full0 + 8 * stage, phase, abort_flag, p.err)) {
+                  ok = false;
+                  break;
+                }
+                tc_fence_after();
+                const uint32_t sa = smem_u32(smem + stage * C::kStageBytes);
+                const uint32_t sb = sa + 2 * C::kABytes;
+                const int c = kb % 3;
+                const uint32_t dhh = c == 0 ? dt[0] : (c == 1 ? dt[1] : dt[1] + (uint32_t)NT);
+#pragma unroll
+                for (int kk = 0; kk < G::kKSteps; ++kk) {
+                  const uint64_t ah = G::desc(sa + kk * 32), al = G::desc(sa + G::kPlaneA + kk * 32);
+                  const uint64_t bh = G::desc(sb + kk * 32), bl = G::desc(sb + NT * G::kRowB + kk * 32);
+                  if (c == 0) {
+                    mma<MODE>(dhh, ah, bh, idesc2, (kb | kk) ? 1u : 0u);  // [D_hh | D_x] (+)= A_hi [B_hi | B_lo]
+                  } else {
+                    mma<MODE>(dhh, ah, bh, idesc, (kb > c || kk) ? 1u : 0u);  // first written at kb == c
+                    mma<MODE>(dx0, ah, bl, idesc, 1u);
+                  }
+                  mma<MODE>(dx0, al, bh, idesc, 1u);
+                }
+                mma_commit(empty0 + 8 * stage);
+                if (++stage == S) {
+                  stage = 0;
+                  phase ^= 1u;
+                }
+              }
+              if (!ok) break;
+#pragma unroll
+              for (int t = 0; t < 2; ++t) {
+                mma_commit(tfull0 + 8 * bt[t]);
+                ++nt2[t];
+              }
+              continue;
+            }
             for (int kb = 0; kb < nb && ok; ++kb) {
               if ((FUSED && !mbar_wait(conv0 + 8 * stage, phase, abort_flag, p.err)) ||
                   !mbar_wait(full0 + 8 * stage, phase, abort_flag, p.err)) {
@@ -605,9 +676,10 @@ __global__ void __launch_bounds__(TcRoles<FUSED, TE, LP>::kThreadsT, 1)
         mma_commit(drain);
         mbar_wait(drain, 0, nullptr, p.err);
       }
-    } else if (warp < R::kConv0) {
-      // LP = 2: warps 2, 3 have no role
-    } else if (FUSED) {
+    }
+  };
+  // converters (fused only)
+  auto convert_role = [&]() {
       // ---------------- converters: the stage's FP32 tile [NT][32] becomes the
       // hi and lo planes [NT][64 B] (64-byte swizzle) in the same bytes.  Thread
       // ct owns float4 column c4 of rows r0 + 16 j; every row it writes has the
@@ -700,6 +772,22 @@ __global__ void __launch_bounds__(TcRoles<FUSED, TE, LP>::kThreadsT, 1)
           if (!ok) break;
         }
       }
+  };
+  if (warp < R::kEpi0) {
+    if constexpr (LP == 2 && FUSED) {
+      // LP = 2: warps 2, 3 have no role; the producer/MMA warpgroup and the
+      // converter warpgroup each drop to their own budget
+      static_assert(R::kThreadsT == 768 && R::kEpi0 == 8 && R::kConv0 == 4, "LP = 2 register split: 6 warpgroups");
+      if (warp >= R::kConv0) {
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(R::kRegConv));
+        convert_role();
+      } else {
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(R::kRegCtl));
+        control_role();
+      }
+    } else {
+      if (warp < R::kConv0) control_role();
+      else if (FUSED) convert_role();
     }
   } else {
     if constexpr (LP == 2 && FUSED) asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(R::kRegHigh));
@@ -780,8 +868,10 @@ __global__ void __launch_bounds__(TcRoles<FUSED, TE, LP>::kThreadsT, 1)
       }
     } else {
       // ---------------- epilogue: acc += (sqrt(4 pi w_k P) (D_hh + D_x))^2
-      // (LP = 2: warps 8 t .. 8 t + 7 of the epilogue serve tile t)
+      // (LP = 2: warps 8 t .. 8 t + 7 of the epilogue serve tile t; on a
+      // chain record tile 0's D_hh is the sum of three accumulators)
       constexpr int CW = C::kChunk;
+      constexpr int CWC = 2;  // chain records: TMEM load width (four accumulators per column)
       const int sp = warp & 3;  // a warp reads the TMEM lanes 32 (warp mod 4) .. + 31
       const int grp = (warp - R::kEpi0) >> 2;
       const int half = grp & 1, tile = grp >> 1;
@@ -790,7 +880,7 @@ __global__ void __launch_bounds__(TcRoles<FUSED, TE, LP>::kThreadsT, 1)
       float acc[C::kColsPerThread];
 #pragma unroll
       for (int j = 0; j < C::kColsPerThread; ++j) acc[j] = 0.f;
-      int n = 0;
+      int nu[2] = {0, 0};  // uses so far of each tile's accumulator pair (LP = 1: tile 0 only)
       int ks = 0;
       uint32_t kph = 0;
       while (true) {
@@ -804,11 +894,66 @@ __global__ void __launch_bounds__(TcRoles<FUSED, TE, LP>::kThreadsT, 1)
 #pragma unroll
           for (int j = 0; j < C::kColsPerThread; ++j) acc[j] = 0.f;
         }
+        const bool chain = LP == 2 && (flags & kChain);
+        if (chain) {
+          // chain record: tile 0's warps read both pairs (tile 0's D_hh and
+          // D_x, and the chains 1, 2 in the other pair) for their usual
+          // columns; a chain that took no block (fewer than three blocks) is
+          // read but not added (its columns hold whatever they held).  Tile
+          // 1's warps follow the other pair's phase and release it with them.
+          const int nb0 = hv & 0xFFFF;
+          int btc[2];
+#pragma unroll
+          for (int t = 0; t < 2; ++t) btc[t] = (nu[t] % NB) * LP + t;
+          if (!mbar_wait(tfull0 + 8 * btc[tile], (uint32_t)(nu[tile] / NB) & 1u, abort_flag, p.err)) break;
+          if (tile == 0) {
+            tc_fence_after();
+            const float *wr = reinterpret_cast<const float *>(rec + 16) + col0;
+            const uint32_t ta0 = tmem + ((uint32_t)(sp * 32) << 16) + (uint32_t)(btc[0] * 2 * NT + col0);
+            const uint32_t d1 = (uint32_t)((btc[1] - btc[0]) * 2 * NT);
+            const bool u1 = nb0 > 1, u2 = nb0 > 2;
+            // D_hh = (h0 + h1) + h2, in two load rounds (register budget)
+#pragma unroll
+            for (int c = 0; c < C::kColsPerThread / CWC; ++c) {
+              const uint32_t ta = ta0 + c * CWC;
+              float x[CWC], y[CWC];
+              tmem_ld<CWC>(ta, x);
+              tmem_ld<CWC>(ta + d1, y);
+              tmem_wait_ld();
+#pragma unroll
+              for (int j = 0; j < CWC; ++j) x[j] = u1 ? x[j] + y[j] : x[j];
+              tmem_ld<CWC>(ta + NT + d1, y);
+              tmem_wait_ld();
+#pragma unroll
+              for (int j = 0; j < CWC; ++j) x[j] = u2 ? x[j] + y[j] : x[j];
+              tmem_ld<CWC>(ta + NT, y);
+              tmem_wait_ld();
+#pragma unroll
+              for (int j = 0; j < CWC; ++j) {
+                const float t = wr[c * CWC + j] * (x[j] + y[j]);
+                acc[c * CWC + j] = fmaf(t, t, acc[c * CWC + j]);
+              }
+            }
+            tc_fence_before();
+          }
+          __syncwarp();
+          // 16 arrivals each: tile 0's pair two from each tile-0 warp, the
+          // other pair one from each of the 16 warps
+          if (lane == 0) {
+            if (tile == 0) mbar_arrive_n(tempty0 + 8 * btc[0], 2u);
+            mbar_arrive(tempty0 + 8 * btc[1]);
+          }
+          ++nu[0];
+          ++nu[1];
+        }
         // this tile's blocks at this k (LP = 2: none when only the other tile has some)
-        const int nbt = LP == 2 ? ((hv >> (16 * tile)) & 0xFFFF) : hv;
+        const int nbt = chain ? 0 : (LP == 2 ? ((hv >> (16 * tile)) & 0xFFFF) : hv);
+        if constexpr (LP == 2) {  // the other tile's pair (its use count; its warps consume it)
+          if (!chain && ((hv >> (16 * (tile ^ 1))) & 0xFFFF) > 0) ++nu[tile ^ 1];
+        }
         if (nbt > 0) {
-          const int bt = (n % NB) * LP + tile;
-          const uint32_t use = (uint32_t)(n / NB);
+          const int bt = (nu[tile] % NB) * LP + tile;
+          const uint32_t use = (uint32_t)(nu[tile] / NB);
           if (!mbar_wait(tfull0 + 8 * bt, use & 1u, abort_flag, p.err)) break;
           tc_fence_after();
           const float4 *w4 = reinterpret_cast<const float4 *>(rec + 16) + col0 / 4;
@@ -834,8 +979,9 @@ __global__ void __launch_bounds__(TcRoles<FUSED, TE, LP>::kThreadsT, 1)
           }
           tc_fence_before();
           __syncwarp();
-          if (lane == 0) mbar_arrive(tempty0 + 8 * bt);
-          ++n;
+          // LP = 2: the barrier counts 16 arrivals (all 16 warps on a chain item)
+          if (lane == 0) mbar_arrive_n(tempty0 + 8 * bt, LP == 2 ? 2u : 1u);
+          ++nu[tile];
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(kempty0 + 8 * ks);
@@ -1239,6 +1385,7 @@ struct TcPlan {
   bool te = false;     // temperature + E-mode: NT models per tile, 2 NT operand rows
   int lp = 1;          // l-tiles per item (2: adjacent tiles share the item's source blocks)
   int ksub = kKSub;    // non-empty k per FP32 chunk sum
+  int chain = 0;       // lp = 2: 1, chain records where an item's second tile is idle; 2, also l-tile 0 alone
   int nslots = 0;      // chunk slots (each lp tiles' partials)
   std::vector<int> blob;
   size_t o_items = 0, o_tile_ptr = 0, o_tile_items = 0, o_perm = 0, o_nkm = 0, o_lmaxm = 0, o_tnk = 0;
@@ -1294,6 +1441,19 @@ int want_lp(int mode, int nt, bool te) {
   if (const char *e = getenv("GCAMB_TC_LP"))
     if (e[0] == '1') return 1;
   return 2;
+}
+
+// Chain records of lp = 2 plans: 1 (the default), at every k where an
+// item's second l-tile has no blocks, the first tile's hi*hi sum is spread
+// over three accumulators (the second tile's pair is free); 2, l-tile 0 is
+// also given items of its own, so that all of its k are chain records;
+// 0, none (GCAMB_TC_CHAIN=0|1|2).
+int want_chain() {
+  if (const char *e = getenv("GCAMB_TC_CHAIN")) {
+    if (e[0] == '0') return 0;
+    if (e[0] == '2') return 2;
+  }
+  return 1;
 }
 
 // Non-empty k per FP32 chunk sum of the epilogue (the partial-sum length):
@@ -1392,8 +1552,15 @@ void plan_build(const gcamb_grid *g, int M, int mode, int nt, const int *lmax_c,
   // (first of two adjacent l-tiles, ...), active where either tile is, the
   // cost weighing the stages (the longer tile) and the second tile's MMAs
   // l-tiles of the item that starts at tile lt for source tile mt
+  // chain items (lp = 2): l-tile 0 alone, its hi*hi sum spread over three
+  // accumulators (the MMA warp's chain mode); the pairs then start at tile 1
+  pl.chain = lp == 2 ? want_chain() : 0;
+  std::vector<int> starts;
+  for (int lt = 0; lt < g->nlt; lt += (pl.chain == 2 && lt == 0) ? 1 : lp) starts.push_back(lt);
+  auto chain_of = [&](int lt) { return pl.chain == 2 && lt == 0; };
   auto ntl_of = [&](int lt, int mt) {
-    return (lp == 2 && lt + 1 < g->nlt && tile_lm[mt] >= g->lrow[(size_t)(lt + 1) * kTileL]) ? 2 : 1;
+    return (lp == 2 && !chain_of(lt) && lt + 1 < g->nlt && tile_lm[mt] >= g->lrow[(size_t)(lt + 1) * kTileL]) ? 2
+                                                                                                             : 1;
   };
   auto kcost = [&](int q, int lt, int ntl) -> double {
     const int a = t.nkb[(size_t)q * g->nlt + lt];
@@ -1402,7 +1569,7 @@ void plan_build(const gcamb_grid *g, int M, int mode, int nt, const int *lmax_c,
     return std::max(a, b) + 0.5 * std::min(a, b) + 0.5;
   };
   double total = 0.0;
-  for (int lt = 0; lt < g->nlt; lt += lp)
+  for (int lt : starts)
     for (int mt = 0; mt < pl.n_mt; ++mt) {
       if (tile_lm[mt] < g->lrow[(size_t)lt * kTileL]) continue;
       for (int q = 0; q < tile_nk[mt]; ++q) total += kcost(q, lt, ntl_of(lt, mt));
@@ -1411,7 +1578,7 @@ void plan_build(const gcamb_grid *g, int M, int mode, int nt, const int *lmax_c,
   const double target = std::max(4.0, total / (sms * 4.0));
   std::vector<TcItem> items;
   pl.cost.clear();
-  for (int lt = 0; lt < g->nlt; lt += lp)
+  for (int lt : starts)
     for (int mt = 0; mt < pl.n_mt; ++mt) {
       if (tile_lm[mt] < g->lrow[(size_t)lt * kTileL]) continue;
       // an item spans at most kKChunkMax k and starts and ends at a k with
@@ -1423,7 +1590,7 @@ void plan_build(const gcamb_grid *g, int M, int mode, int nt, const int *lmax_c,
         const double kc = kcost(q, lt, ntl);
         if (kc == 0.0) continue;
         if (qb >= 0 && q - qb + 1 > kKChunkMax) {
-          items.push_back({lt, mt, qb, qlast + 1, ntl, 0, {0, 0}});
+          items.push_back({lt, mt, qb, qlast + 1, ntl, 0, chain_of(lt) ? 1 : 0, 0});
           pl.cost.push_back(c);
           qb = -1;
         }
@@ -1434,13 +1601,13 @@ void plan_build(const gcamb_grid *g, int M, int mode, int nt, const int *lmax_c,
         }
         c += kc;
         if (c >= target || q - qb + 1 >= kKChunkMax) {
-          items.push_back({lt, mt, qb, q + 1, ntl, 0, {0, 0}});
+          items.push_back({lt, mt, qb, q + 1, ntl, 0, chain_of(lt) ? 1 : 0, 0});
           pl.cost.push_back(c);
           qb = -1;
         }
       }
       if (qb >= 0) {
-        items.push_back({lt, mt, qb, qlast + 1, ntl, 0, {0, 0}});
+        items.push_back({lt, mt, qb, qlast + 1, ntl, 0, chain_of(lt) ? 1 : 0, 0});
         pl.cost.push_back(c);
       }
     }
@@ -1547,6 +1714,7 @@ TcPlan *get_plan(const gcamb_grid *g, int M, int mode, int *rc) {
   for (auto &e : g_plans)
     if (e.first == g && !e.second->te && e.second->M == M && e.second->mode == mode && e.second->NT == nt &&
         e.second->fused == want_fused(g, mode, nt, true) && e.second->ksub == want_ksub() &&
+        e.second->chain == (e.second->lp == 2 ? want_chain() : 0) &&
         e.second->lp == (e.second->nkbs < 32768 ? want_lp(mode, nt, false) : 1))
       return e.second;
   TcPlan *pl = new TcPlan();
@@ -1622,7 +1790,7 @@ int launch_tc(const gcamb_grid *g, const TcPlan &pl, const float *S, const doubl
   if (pl.nitems > 0) {
     int *ctr = reinterpret_cast<int *>(ws + pl.off_ctr);
     TcParams prm{static_cast<const char *>(t.d_data), nullptr, t.d_off, t.d_nkb, sp, wp, sc, nullptr, -1,
-                 pl.items(B), ctr, pl.nitems, pl.ksub, part, use_err_word ? err_word : device_error_flag(), g->nlt, pl.n_mt,
+                 pl.items(B), ctr, pl.nitems, pl.ksub, pl.chain >= 1 ? 1 : 0, part, use_err_word ? err_word : device_error_flag(), g->nlt, pl.n_mt,
                  pl.nkbs, pl.mpad};
     if (!prm.err && !use_err_word) return fail(GCAMB_ECUDA, "los_cl: error flag allocation");
     int rc;
@@ -1742,7 +1910,7 @@ int launch_tc_te(const gcamb_grid *g, const TcPlan &pl, const float *ST, const f
                        ? g->rowof[2 - g->lmin]
                        : -1;
     TcParams prm{static_cast<const char *>(t.d_data), nullptr, t.d_off, t.d_nkb, nullptr, wp, tail, ix2, r2,
-                 pl.items(B), ctr, pl.nitems, pl.ksub, part, device_error_flag(), g->nlt, pl.n_mt, pl.nkbs, pl.mpad};
+                 pl.items(B), ctr, pl.nitems, pl.ksub, pl.chain >= 1 ? 1 : 0, part, device_error_flag(), g->nlt, pl.n_mt, pl.nkbs, pl.mpad};
     if (!prm.err) return fail(GCAMB_ECUDA, "los_cl_te: error flag allocation");
     if (int rc = launch_tc_kernel<NT, kBF16, true, 1>(g, pl, tm1, tm2, prm, st)) return rc;
   }
@@ -1782,7 +1950,7 @@ int launch_tc_pair(const gcamb_grid *gx, const gcamb_grid *gy, const TcPlan &pl,
   if (pl.nitems > 0) {
     int *ctr = reinterpret_cast<int *>(ws + pl.off_ctr);
     TcParams prm{static_cast<const char *>(tx.d_data), static_cast<const char *>(ty.d_data), tx.d_off, tx.d_nkb,
-                 nullptr, wp, tail, nullptr, -1, pl.items(B), ctr, pl.nitems, pl.ksub, part, device_error_flag(), gx->nlt,
+                 nullptr, wp, tail, nullptr, -1, pl.items(B), ctr, pl.nitems, pl.ksub, pl.chain >= 1 ? 1 : 0, part, device_error_flag(), gx->nlt,
                  pl.n_mt, pl.nkbs, pl.mpad};
     if (!prm.err) return fail(GCAMB_ECUDA, "los_cl_pair: error flag allocation");
     if (int rc = launch_tc_kernel<NT, kBF16, true, 2>(gx, pl, tm1, tm2, prm, st)) return rc;

@@ -96,7 +96,9 @@ def test_fused_conversion_matches_split_pass_bitwise(monkeypatch, mode, nk, ntau
 ])
 def test_paired_l_tiles_match_single_tiles(monkeypatch, mode, nk, ntau, lmin, lmax, M):
     """Two adjacent 128-multipole tiles per work item (each loaded and split
-    source block multiplies both tables) against one tile per item.  Each
+    source block multiplies both tables) against one tile per item, with
+    l-tile 0 paired too (GCAMB_TC_CHAIN=0; its chain items are tested
+    below).  Each
     (k, l-tile) product D_k is the same sequence of MMAs on the same operand
     bits and each k's term (w (D_hh + D_x))^2 the same FP32 value; only the
     k-chunks over which the epilogue sums the terms in FP32 differ.  A chunk
@@ -105,6 +107,7 @@ def test_paired_l_tiles_match_single_tiles(monkeypatch, mode, nk, ntau, lmin, lm
     2 * 16 * 2^-24.  The uniform plan of the same batch runs the paired kernel
     and gives the paired result bit for bit."""
     k, tau, S, P = case(nk, ntau, lmin, lmax, M)
+    monkeypatch.setenv("GCAMB_TC_CHAIN", "0")  # l-tile 0 paired as well: the same MMA sequences
     monkeypatch.setenv("GCAMB_TC_LP", "1")
     C1, g = run(k, tau, S, P, lmin, lmax, mode)
     monkeypatch.delenv("GCAMB_TC_LP", raising=False)
@@ -129,6 +132,7 @@ def test_split_pass_paired_l_tiles_match_single_tiles(monkeypatch, mode, nk, nta
     l-tiles per item against one tile per item: the bound of the fused test."""
     k, tau, S, P = case(nk, ntau, lmin, lmax, M)
     monkeypatch.setenv("GCAMB_TC_FUSED", "0")
+    monkeypatch.setenv("GCAMB_TC_CHAIN", "0")
     monkeypatch.setenv("GCAMB_TC_LP", "1")
     C1, g = run(k, tau, S, P, lmin, lmax, mode)
     monkeypatch.delenv("GCAMB_TC_LP", raising=False)
@@ -137,6 +141,38 @@ def test_split_pass_paired_l_tiles_match_single_tiles(monkeypatch, mode, nk, nta
     assert (np.abs(C2 - C1) / C1).max() <= 2 * 16 * 2.0 ** -24
     info = gcamb.plan_info(gcamb.plan_create(g, M, mode=mode))
     assert info["fused"] == 0 and info["lp"] == 2
+
+
+@pytest.mark.parametrize("chain", ["1", "2"])
+@pytest.mark.parametrize("mode,fused", [(gcamb.F16X3, "1"), (gcamb.BF16X3, "1"), (gcamb.F16X3, "0")])
+def test_chain_records_cut_the_accumulation_loss_at_low_l(orc, monkeypatch, mode, fused, chain):
+    """The tensor cores add each MMA's products to the FP32 accumulator after
+    dropping their bits below a quarter ulp of the largest term, and truncate
+    the sum; the loss of every accumulate step is relative to the running sum
+    and always towards zero.  On long same-sign tau sums (low l, small k) it
+    builds up to a bias of several 1e-6.  Chain records spread a tile's
+    hi*hi products over three accumulators, each holding about a third of
+    the sum: at every k where an item's second l-tile is idle (chain 1, the
+    default), and in addition at every k of l-tile 0 (chain 2).  The error
+    at l < 30 must fall (mean over sources and l, to at most 0.6 of the
+    single-accumulator error) and stay within 1e-5 on every l; the results
+    differ by no more than the single accumulator's error."""
+    k, tau, S, P = case(160, 1000, 2, 300, 64, seed=7)
+    monkeypatch.setenv("GCAMB_TC_FUSED", fused)
+    monkeypatch.setenv("GCAMB_TC_CHAIN", "0")
+    C0, g = run(k, tau, S, P, 2, 300, mode)
+    monkeypatch.setenv("GCAMB_TC_CHAIN", chain)
+    C3, _ = run(k, tau, S, P, 2, 300, mode, g)
+    info = gcamb.plan_info(gcamb.plan_create(g, 64, mode=mode))
+    assert info["lp"] == 2
+    sel = [0, 9, 21, 33, 47, 63]
+    _, Cr = orc.los_cl(k, tau, 14000.0, 2, 300, S[sel].astype(np.float64), P[sel], want_delta=False)
+    e0 = np.abs(C0[sel] / Cr - 1)
+    e3 = np.abs(C3[sel] / Cr - 1)
+    low = slice(0, 28)
+    assert e3[:, low].mean() <= 0.6 * e0[:, low].mean(), (e3[:, low].mean(), e0[:, low].mean())
+    assert e3.max() <= (1e-5 if mode == gcamb.F16X3 else 6 * 2.0 ** -16), e3.max()
+    assert (np.abs(C3 - C0) / C0).max() <= 2 * max(e0.max(), 1e-6)
 
 
 @pytest.mark.parametrize("mode,fused", [(gcamb.F16X3, "1"), (gcamb.BF16X3, "1"), (gcamb.F16X3, "0")])
