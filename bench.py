@@ -270,7 +270,8 @@ def run_uneven(args):
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     build.build()
-    mode = {"bf16x3": gcamb.BF16X3, "tf32x3": gcamb.TF32X3, "f16x3": gcamb.F16X3}[args.mode]
+    mode = {"bf16x3": gcamb.BF16X3, "tf32x3": gcamb.TF32X3, "f16x3": gcamb.F16X3,
+            "plain32": gcamb.PLAIN32}[args.mode]
     wl = synth.workload("uneven_lmax6000")
     p = synth.model_params(wl.M, seed=0, lmax_range=(1500, 6000))
     lm = p.lmax.astype(np.int32)
@@ -301,11 +302,19 @@ def run_uneven(args):
     peaks, peak_src = load_peaks()
     pair = 8 if mode == gcamb.TF32X3 else 4
     alg = gcamb.grid_info(g)["active"] * pair + int(nkm.astype(np.int64).sum()) * wl.ntau * 4
+    scope = "whole step: split pass + tensor-core kernel + reduce"
+    if mode == gcamb.PLAIN32:
+        # plain kernels: the table once per 8 sources (one CTA's source chunk),
+        # the sources once, the FP32 transfer functions written and read once
+        alg = (gcamb.grid_info(g)["active"] * 4 * ((wl.M + 7) // 8) + int(nkm.astype(np.int64).sum()) * wl.ntau * 4
+               + 2 * 4 * int(nkm.astype(np.int64).sum()) * g.nl)
+        scope = "whole step: plain FP32 transfer kernel + prefix C_l kernel per chunk of 16 sources"
     achieved = alg / (ms / steps * 1e-3) / 1e9
     line = {"metric": "C_l spectra/sec, uneven batch (1000 sources, l_max U{1500..6000})",
             "value": wl.M * steps / (ms * 1e-3), "unit": "spectra/s", "n_gpus": 1, "steps": steps,
             "warmup": args.warmup, "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {gcamb.BF16X3: "bf16", gcamb.F16X3: "f16", gcamb.TF32X3: "tf32"}[mode],
+            "vs_baseline": None,
+            "dtype": {gcamb.BF16X3: "bf16", gcamb.F16X3: "f16", gcamb.TF32X3: "tf32", gcamb.PLAIN32: "f32"}[mode],
             "data": "synthetic",
             "config": {"workload": "uneven_lmax6000", "M": wl.M, "nk_master": wl.nk, "ntau": wl.ntau,
                        "lmax": wl.lmax, "mode": args.mode, "tile": info["tile"], "items": info["items"],
@@ -315,9 +324,9 @@ def run_uneven(args):
                        "table_gb": gcamb.table_bytes(g, mode) / 1e9},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_source": peak_src,
-                         "scope": "whole step: split pass + tensor-core kernel + reduce",
-                         "algorithmic_bytes": alg},
-            "clocks": clocks, "gpu_launches": 3 * steps}
+                         "scope": scope, "algorithmic_bytes": alg},
+            "clocks": clocks,
+            "gpu_launches": (2 * info["items"] if mode == gcamb.PLAIN32 else 3) * steps}
     print(json.dumps(line), flush=True)
 
 

@@ -384,8 +384,14 @@ int gcamb_los_cl_pair(const gcamb_grid *gx, const gcamb_grid *gy, const float *S
  *   lmax_m[M], nk_m[M]  host int, or both NULL (every source uses the whole
  *                       grid, as gcamb_los_cl); lmin <= lmax_m <= lmax,
  *                       1 <= nk_m <= nk.  Copied.
- *   mode                GCAMB_BF16X3, GCAMB_F16X3 or GCAMB_TF32X3; the grid's
- *                       table for this mode must be built.
+ *   mode                GCAMB_BF16X3, GCAMB_F16X3 or GCAMB_TF32X3 (the
+ *                       tensor-core kernel), or GCAMB_PLAIN32 (FP32 on the
+ *                       plain CUDA-core kernels, in chunks of 16 sources in
+ *                       the caller's order: each chunk's transfer functions
+ *                       over its longest k prefix and highest l-tile, then
+ *                       each source's C_l over its own prefix; tune is
+ *                       ignored, the plan info's "items" is the number of
+ *                       chunks); the grid's table for this mode must be built.
  *   tune                0: source-tile width from a heuristic;
  *                       1: the first gcamb_plan_launch times the candidate
  *                       widths (64, 128, 256 sources) on its inputs and keeps

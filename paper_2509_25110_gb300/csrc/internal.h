@@ -118,6 +118,11 @@ int launch_cl_cross(const gcamb_grid *g, const void *DX, const void *DY, int d_d
                     double *Cl, cudaStream_t st);
 int launch_cl(const gcamb_grid *g, const void *Delta, int d_dtype, const double *Pk, int M, double *Cl,
               cudaStream_t st);
+// Uneven batch in FP32 on the plain kernels (plain.cu): per-source k prefix
+// and l_max (host copies lmax_c, nk_c; device copies d_lmax, d_nk).
+size_t plain_plan_workspace_bytes(const gcamb_grid *g, int M);
+int launch_plain_plan(const gcamb_grid *g, const float *S, const double *Pk, int M, const int *lmax_c,
+                      const int *nk_c, const int *d_lmax, const int *d_nk, double *Cl, void *ws, cudaStream_t st);
 
 // Tensor-core batched path (tc.cu).
 size_t los_cl_workspace_bytes(const gcamb_grid *g, int M, int mode);

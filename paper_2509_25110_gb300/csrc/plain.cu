@@ -405,6 +405,87 @@ int launch_cl_cross(const gcamb_grid *g, const void *DX, const void *DY, int d_d
   return GCAMB_OK;
 }
 
+// Uneven batch in FP32 on the CUDA cores: C_l[m][row] of one chunk of
+// sources (m0 .. m0 + mc), each on its own k prefix [0, nk_m) with the
+// trapezoid in ln k of that prefix (the last node of a shorter prefix takes
+// half its interval) and zero above its own l_max; Delta [mc][nk][nl] FP32 of
+// the chunk (rows beyond the chunk's l-tiles and k beyond its longest prefix
+// are not read: they belong to no source's sum).  FP64 sum in increasing k.
+__global__ void __launch_bounds__(256) cl_prefix_kernel(const float *__restrict__ Delta, const double *__restrict__ Pk,
+                                                        const double *__restrict__ wk, const double *__restrict__ kk,
+                                                        int nk, int nl, const int *__restrict__ lrow,
+                                                        const int *__restrict__ lmax_m, const int *__restrict__ nk_m,
+                                                        int m0, double *__restrict__ Cl) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  const int mi = blockIdx.y, m = m0 + mi;
+  if (row >= nl) return;
+  double acc = 0.0;
+  if (lrow[row] <= lmax_m[m]) {
+    const int nkm = nk_m[m];
+    const float *d = Delta + (size_t)mi * nk * nl + row;
+    const double *p = Pk + (size_t)m * nk;
+    const double four_pi = 4.0 * 3.14159265358979323846;
+    for (int q = 0; q < nkm; ++q) {
+      // trapezoid in ln k on the prefix [0, nkm)
+      const double w = (nkm == nk || q + 1 < nkm) ? wk[q] : (q > 0 ? 0.5 * (log(kk[q]) - log(kk[q - 1])) : 0.0);
+      const double v = (double)d[(size_t)q * nl];
+      acc = fma(four_pi * w * p[q], v * v, acc);
+    }
+  }
+  Cl[(size_t)m * nl + row] = acc;
+}
+
+// Sources per launch pair of the FP32 plan (the Delta buffer of a chunk).
+constexpr int kPlainChunk = 16;
+
+size_t plain_plan_workspace_bytes(const gcamb_grid *g, int M) {
+  const int mc = M < kPlainChunk ? M : kPlainChunk;
+  return (size_t)(mc > 0 ? mc : 1) * g->nk * g->nl * sizeof(float);
+}
+
+int launch_plain_plan(const gcamb_grid *g, const float *S, const double *Pk, int M, const int *lmax_c,
+                      const int *nk_c, const int *d_lmax, const int *d_nk, double *Cl, void *ws, cudaStream_t st) {
+  const Table &t = g->tab[GCAMB_PLAIN32];
+  float *D = static_cast<float *>(ws);
+  for (int m0 = 0; m0 < M; m0 += kPlainChunk) {
+    const int mc = M - m0 < kPlainChunk ? M - m0 : kPlainChunk;
+    // the chunk's longest k prefix and highest l-tile (host copies of the plan)
+    int nkc = 1, ltc = 0;
+    for (int j = m0; j < m0 + mc; ++j) {
+      nkc = nk_c[j] > nkc ? nk_c[j] : nkc;
+      int r = g->rowof[lmax_c[j] - g->lmin];
+      for (int l = lmax_c[j]; r < 0 && l > g->lmin; --l) r = g->rowof[l - 1 - g->lmin];
+      const int lt = (r < 0 ? 0 : r) / kTileL;
+      ltc = lt > ltc ? lt : ltc;
+    }
+    int max_ext = 0;
+    for (int v : t.nkb) max_ext = max_ext > v ? max_ext : v;
+    max_ext *= 64;
+    constexpr int MC = 8;
+    const size_t smem = (size_t)MC * max_ext * sizeof(float);
+    if (smem > 200 * 1024) return fail(GCAMB_EINVAL, "plan_launch: tau grid too long for the plain kernel");
+    cudaError_t e = cudaFuncSetAttribute(los_plain_kernel<float, MC, -1, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(smem > 0 ? smem : 16));
+    if (e != cudaSuccess) return cuda_fail(e, "plan_launch: smem attribute");
+    const double *xthr = (g->kernel == 0 && !g->curved) ? g->d_xthr : nullptr;
+    {
+      ProfScope prof(GCAMB_K_LOS_PLAIN, st);
+      dim3 grid(ltc + 1, nkc, (mc + MC - 1) / MC);
+      los_plain_kernel<float, MC, -1, false><<<grid, 256, smem, st>>>(
+          static_cast<const float *>(t.d_data), t.d_nkb, t.d_off, g->nk, g->nlt, g->nl, g->d_lrow, g->ntau,
+          S + (size_t)m0 * g->nk * g->ntau, mc, D, g->d_k, g->d_tau, g->tau0, g->d_wtau, 1e-12, xthr);
+    }
+    {
+      ProfScope prof(GCAMB_K_CL, st);
+      dim3 grid((g->nl + 255) / 256, mc);
+      cl_prefix_kernel<<<grid, 256, 0, st>>>(D, Pk, g->d_wk, g->d_k, g->nk, g->nl, g->d_lrow, d_lmax, d_nk, m0, Cl);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "plan_launch: FP32 launch");
+  }
+  return GCAMB_OK;
+}
+
 int launch_cl(const gcamb_grid *g, const void *Delta, int d_dtype, const double *Pk, int M, double *Cl,
               cudaStream_t st) {
   if (M > 65535) return fail(GCAMB_EINVAL, "cl: too many sources for one launch");

@@ -2095,6 +2095,8 @@ uint64_t fnv1a(uint64_t h, const void *p, size_t n) {
 struct gcamb_plan {
   const gcamb_grid *g = nullptr;
   int M = 0, mode = 0;
+  bool plain = false;                       // GCAMB_PLAIN32: the plain kernels, chunks of sources
+  int *d_lmax = nullptr, *d_nk = nullptr;   // plain: device copies of the per-source l_max, k prefix
   bool tune = false, tuned = false;
   std::vector<int> lmax_c, nk_c;
   gcamb::TcPlan cand[3];
@@ -2179,8 +2181,8 @@ int gcamb_plan_create(gcamb_grid *g, int M, const int *lmax_m, const int *nk_m, 
   if (!out) return fail(GCAMB_EINVAL, "plan_create: out is NULL");
   *out = nullptr;
   if (!g) return fail(GCAMB_EINVAL, "plan_create: NULL grid");
-  if (mode != GCAMB_BF16X3 && mode != GCAMB_TF32X3 && mode != GCAMB_F16X3)
-    return fail(GCAMB_EINVAL, "plan_create: mode must be GCAMB_BF16X3, GCAMB_F16X3 or GCAMB_TF32X3");
+  if (mode != GCAMB_BF16X3 && mode != GCAMB_TF32X3 && mode != GCAMB_F16X3 && mode != GCAMB_PLAIN32)
+    return fail(GCAMB_EINVAL, "plan_create: mode must be GCAMB_BF16X3, GCAMB_F16X3, GCAMB_TF32X3 or GCAMB_PLAIN32");
   if (M < 1) return fail(GCAMB_EINVAL, "plan_create: M must be >= 1");
   if (!g->tab[mode].built) return fail(GCAMB_ESTATE, "plan_create: build the table for this mode first");
   if ((lmax_m == nullptr) != (nk_m == nullptr))
@@ -2199,6 +2201,26 @@ int gcamb_plan_create(gcamb_grid *g, int M, const int *lmax_m, const int *nk_m, 
   if (lmax_m) {
     p->lmax_c.assign(lmax_m, lmax_m + M);
     p->nk_c.assign(nk_m, nk_m + M);
+  }
+  if (mode == GCAMB_PLAIN32) {
+    // FP32 on the plain kernels: per-source prefixes on the device, no work list
+    p->plain = true;
+    if (!lmax_m) {
+      p->lmax_c.assign(M, g->lmax);
+      p->nk_c.assign(M, g->nk);
+    }
+    cudaError_t e = cudaMalloc(&p->d_lmax, M * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_nk, M * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_lmax, p->lmax_c.data(), M * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_nk, p->nk_c.data(), M * sizeof(int), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      const int rc = cuda_fail(e, "plan_create: per-source arrays");
+      gcamb_plan_destroy(p);
+      return rc;
+    }
+    p->chosen = 0;
+    *out = p;
+    return GCAMB_OK;
   }
   // the key identifies grid, batch and device for the tile cache
   uint64_t h = 1469598103934665603ull;
@@ -2237,6 +2259,8 @@ int gcamb_plan_destroy(gcamb_plan *p) {
   if (!p) return GCAMB_OK;
   if (p->exec) cudaGraphExecDestroy(p->exec);
   if (p->cap) cudaStreamDestroy(p->cap);
+  cudaFree(p->d_lmax);
+  cudaFree(p->d_nk);
   for (auto &c : p->cand) c.release();
   delete p;
   return GCAMB_OK;
@@ -2245,6 +2269,7 @@ int gcamb_plan_destroy(gcamb_plan *p) {
 int gcamb_plan_workspace(const gcamb_plan *p, size_t *bytes) {
   if (!p || !bytes) return fail(GCAMB_EINVAL, "plan_workspace: NULL argument");
   size_t b = 0;
+  if (p->plain) b = plain_plan_workspace_bytes(p->g, p->M);
   for (int c = 0; c < 3; ++c)
     if (p->have[c]) b = std::max(b, p->cand[c].ws_bytes);
   *bytes = b;
@@ -2253,15 +2278,15 @@ int gcamb_plan_workspace(const gcamb_plan *p, size_t *bytes) {
 
 int gcamb_plan_info(const gcamb_plan *p, int64_t *info) {
   if (!p || !info) return fail(GCAMB_EINVAL, "plan_info: NULL argument");
-  const TcPlan *c = p->chosen >= 0 ? &p->cand[p->chosen] : nullptr;
+  const TcPlan *c = (p->chosen >= 0 && !p->plain) ? &p->cand[p->chosen] : nullptr;
   info[0] = c ? c->NT : 0;
-  info[1] = c ? c->nitems : 0;
+  info[1] = c ? c->nitems : (p->plain ? (p->M + 15) / 16 : 0);  // plain: source chunks
   info[2] = c ? c->nctas : 0;
   info[3] = p->captures;
   info[4] = p->replays;
   info[5] = p->tuned ? 1 : 0;
   info[6] = p->M;
-  info[7] = c ? (int64_t)c->ws_bytes : 0;
+  info[7] = c ? (int64_t)c->ws_bytes : (p->plain ? (int64_t)plain_plan_workspace_bytes(p->g, p->M) : 0);
   info[8] = c && c->fused ? 1 : 0;
   info[9] = c ? c->lp : 0;
   return GCAMB_OK;
@@ -2278,7 +2303,7 @@ int gcamb_plan_launch(gcamb_plan *p, const float *S, const double *Pk, double *C
   cudaStream_t st = (cudaStream_t)stream;
   char *w = static_cast<char *>(ws);
   if (!device_error_flag()) return fail(GCAMB_ECUDA, "plan_launch: error flag allocation");
-  if (p->chosen < 0) {
+  if (!p->plain && p->chosen < 0) {
     // autotune: time every candidate tile on these inputs, keep the fastest
     float best = 1e30f;
     int bi = -1;
@@ -2320,7 +2345,9 @@ int gcamb_plan_launch(gcamb_plan *p, const float *S, const double *Pk, double *C
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "plan_launch: begin capture");
-    const int rc = launch_plan(p->g, p->cand[p->chosen], S, Pk, Cl, w, p->cap);
+    const int rc = p->plain ? launch_plain_plan(p->g, S, Pk, p->M, p->lmax_c.data(), p->nk_c.data(), p->d_lmax,
+                                                p->d_nk, Cl, w, p->cap)
+                            : launch_plan(p->g, p->cand[p->chosen], S, Pk, Cl, w, p->cap);
     e = cudaStreamEndCapture(p->cap, &graph);
     if (rc) {
       if (graph) cudaGraphDestroy(graph);

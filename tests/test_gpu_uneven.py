@@ -4,7 +4,8 @@ source tiles) against the FP64 oracle run on each source's own grid.
 
 Each source m is checked against the oracle on k[0..nk_m) (trapezoid in ln k
 on that prefix) and l <= lmax_m; C_l above lmax_m must be exactly zero.
-Tolerance: 1e-5 relative (F16X3), as for the uniform batched path."""
+Tolerance: 1e-5 relative (F16X3, and the FP32 plans of the plain kernels),
+as for the uniform batched path."""
 import os
 
 import numpy as np
@@ -97,6 +98,47 @@ def test_uneven_paired_l_tiles_match_single_tiles(monkeypatch, orc, mode):
     sel = [int(np.argmin(lm)), int(np.argmax(lm)), 5, 150]
     check_against_oracle(orc, k, tau, 14000.0, lmin, C2, S.cpu().numpy(), P.cpu().numpy(), lm, nkm, sel,
                          tol=TOL if mode == gcamb.F16X3 else 6 * 2.0 ** -16)
+
+
+def test_uneven_plain32_plan_matches_oracle(orc):
+    """The FP32 form of the uneven batch: a plan in GCAMB_PLAIN32 runs the
+    plain CUDA-core kernels on chunks of sources, each summed over its own k
+    prefix (trapezoid in ln k on the prefix) and zero above its own l_max;
+    captured once in a CUDA graph and replayed.  Against the oracle on the
+    FP32-rounded sources: 1e-5 relative, every source checked."""
+    nk, ntau, lmin, lmax, M = 60, 200, 2, 500, 37
+    k = synth.master_linear_k(nk, 0.05)
+    tau = synth.uniform_grid(200.0, 14000.0, ntau)
+    p, lm, nkm = uneven_batch(M, nk, 100, lmax, seed=25)
+    S = synth.sources(k, tau, p).astype(np.float32)
+    P = synth.primordial(k, p)
+    g = gcamb.grid_create(k, tau, 14000.0, lmin, lmax)
+    gcamb.bessel_table(g, gcamb.PLAIN32)
+    plan = gcamb.plan_create(g, M, lm, nkm, gcamb.PLAIN32)
+    St, Pt = torch.as_tensor(S, device="cuda"), torch.as_tensor(P, device="cuda")
+    C1 = gcamb.plan_launch(plan, St, Pt)
+    C1 = C1.cpu().numpy()
+    C2 = gcamb.plan_launch(plan, St, Pt).cpu().numpy()
+    gcamb.sync()
+    info = gcamb.plan_info(plan)
+    assert info["captures"] == 1 and info["replays"] == 2 and info["tile"] == 0
+    assert np.array_equal(C1, C2)
+    check_against_oracle(orc, k, tau, 14000.0, lmin, C1, S, P, lm, nkm, range(M))
+
+
+def test_uniform_plain32_plan_equals_plain_path():
+    k = synth.log_grid(1e-4, 0.3, 50)
+    tau = synth.uniform_grid(200.0, 14000.0, 300)
+    M = 20
+    p = synth.model_params(M, seed=26)
+    S = torch.as_tensor(synth.sources(k, tau, p).astype(np.float32), device="cuda")
+    P = torch.as_tensor(synth.primordial(k, p), device="cuda")
+    g = gcamb.grid_create(k, tau, 14000.0, 2, 400)
+    gcamb.bessel_table(g, gcamb.PLAIN32)
+    ref = gcamb.cl(g, gcamb.los_transfer(g, S, gcamb.PLAIN32), P).cpu().numpy()
+    got = gcamb.plan_launch(gcamb.plan_create(g, M, mode=gcamb.PLAIN32), S, P).cpu().numpy()
+    gcamb.sync()
+    assert np.array_equal(got, ref)
 
 
 def test_uniform_plan_equals_los_cl():
