@@ -58,6 +58,9 @@ def parse_args():
                     choices=["batched", "uneven", "emulator", "te", "tensor", "features", "lsampled", "curved"],
                     help="batched (the headline), uneven (1000 sources, l_max <= 6000, plan + graph), "
                          "emulator (train on 100k spectra, serve)")
+    ap.add_argument("--sources", type=int, default=0,
+                    help="uneven workload: the first N of its 1000 sources (profiling case)")
+    ap.add_argument("--no-tune", action="store_true", help="uneven workload: the heuristic tile, no timing of candidates")
     ap.add_argument("--kernel-only", action="store_true",
                     help="profiling case: only warm-up + timed steps, one short line, no e2e/plain/CPU legs")
     return ap.parse_args()
@@ -273,6 +276,8 @@ def run_uneven(args):
     mode = {"bf16x3": gcamb.BF16X3, "tf32x3": gcamb.TF32X3, "f16x3": gcamb.F16X3,
             "plain32": gcamb.PLAIN32}[args.mode]
     wl = synth.workload("uneven_lmax6000")
+    if args.sources:
+        wl.M = min(wl.M, args.sources)
     p = synth.model_params(wl.M, seed=0, lmax_range=(1500, 6000))
     lm = p.lmax.astype(np.int32)
     nkm = synth.uneven_nk(lm).astype(np.int32)
@@ -283,7 +288,7 @@ def run_uneven(args):
     table_s = time.perf_counter() - t0
     X = torch.as_tensor(synth.emulator_features(p), device=dev)
     S, P = gcamb.synth_sources(g, X)
-    plan = gcamb.plan_create(g, wl.M, lm, nkm, mode, tune=True)
+    plan = gcamb.plan_create(g, wl.M, lm, nkm, mode, tune=not args.no_tune)
     ws = torch.empty(gcamb.plan_workspace(plan), dtype=torch.uint8, device=dev)
     C = torch.empty((wl.M, g.nl), dtype=torch.float64, device=dev)
     t0 = time.perf_counter()
@@ -310,7 +315,7 @@ def run_uneven(args):
                + 2 * 4 * int(nkm.astype(np.int64).sum()) * g.nl)
         scope = "whole step: plain FP32 transfer kernel + prefix C_l kernel per chunk of 16 sources"
     achieved = alg / (ms / steps * 1e-3) / 1e9
-    line = {"metric": "C_l spectra/sec, uneven batch (1000 sources, l_max U{1500..6000})",
+    line = {"metric": "C_l spectra/sec, uneven batch (%d sources, l_max U{1500..6000})" % wl.M,
             "value": wl.M * steps / (ms * 1e-3), "unit": "spectra/s", "n_gpus": 1, "steps": steps,
             "warmup": args.warmup, "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None,
