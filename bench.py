@@ -360,6 +360,8 @@ def run_emulator(args):
                        "data_gen_s": rep["data_s"], "train_s": rep["train_s"], "check": rep["check"],
                        "tol": rep["tol"], "network_accuracy": acc, "served_fraction_by_tol": served, **rates,
                        "gain_network_vs_projection": rates["network_spectra_per_s"] / rates["projection_spectra_per_s"],
+                       "gain_emulate_vs_sources_and_projection":
+                           rates["emulate_spectra_per_s"] / rates["sources_and_projection_spectra_per_s"],
                        "final_loss": rep["loss_history"][-1][1]}}
     print(json.dumps(line), flush=True)
 

@@ -13,7 +13,11 @@ kernels, with a projection fallback), through the C ABI.
 * training lowers the loss; requests outside the trusted cells are answered
   by the projection path exactly, the rest by the network;
 * checkpoints round-trip and reject corruption;
-* the network serves spectra faster than the projection path it stands in for.
+* a network trained by the library, checked at the target tolerance and at
+  the smallest tolerance at which it serves: served spectra within it,
+  the others from the projection, and the gain over the projection that the
+  served share buys;
+* the network's own pass is faster than the projection path it stands in for.
 """
 import time
 
@@ -190,10 +194,63 @@ def test_training_fallback_and_checkpoint(tmp_path):
     assert ei.value.code == gcamb.EINVAL
 
 
-def test_network_serves_faster_than_the_projection():
-    """What the network gains over the method without it: spectra per second
-    of trusted requests against the batched projection on the 256-source,
-    l_max = 2500 grid, same GPU."""
+def test_trained_network_gain_at_a_stated_tolerance():
+    """What a network trained by the library gains over the method without
+    it, stated with its tolerance and served fraction.  A network of the
+    workload's shape (9-512-512-512-2499) is trained on 20,000 spectra of the
+    batched path (3,000 Adam steps, the library's kernels) and checked on
+    2,048 held-out spectra: first at the target tolerance 1e-3 (the served
+    fraction is reported; at this training length it is 0), then at the
+    smallest of 3e-3, 1e-2, 3e-2, 1e-1, 3e-1 at which some cell is trusted.
+    There, every served spectrum must be within the tolerance of the
+    projection, every other one comes back from the projection path, and the
+    emulator's rate on those requests must beat the projection's by the
+    served share (1 / (1 - served) of it, less a margin for timing noise),
+    the method being what the fallback runs: the sources regenerated from the
+    request's features, then the projection."""
+    from paper_2509_25110_gb300 import emulator
+    wl = synth.workload("batched_lmax2500")
+    g = gcamb.grid_create(wl.k, wl.tau, wl.tau0, wl.lmin, wl.lmax)
+    e, rep, (Xh, Ch) = emulator.train(g, n_train=20000, n_hold=2048, steps=3000, batch=4096)
+    assert rep["loss_history"][-1][1] < rep["loss_history"][0][1]
+    at_target = gcamb.emu_check(e, Xh, Ch, tol=1e-3, min_count=32)
+    assert 0.0 <= at_target["frac_served"] <= 1.0
+    tol = None
+    for t in (3e-3, 1e-2, 3e-2, 1e-1, 3e-1):
+        chk = gcamb.emu_check(e, Xh, Ch, tol=t, min_count=32)
+        if chk["frac_served"] > 0:
+            tol = t
+            break
+    assert tol is not None, "no cell trusted even at 0.3"
+    Cl, fb = gcamb.emulate(e, Xh)
+    gcamb.sync()
+    fb = fb.cpu().numpy().astype(bool)
+    served = 1.0 - fb.mean()
+    assert served > 0
+    ref = Ch.cpu().numpy()
+    got = Cl.cpu().numpy()
+    assert np.abs(got[~fb] / ref[~fb] - 1).max() <= tol
+    # fallback answers are the projection's (F16X3) of the regenerated sources
+    # (here recomputed in a batch of another size, hence another source-tile
+    # width: both within 1e-5 of the exact C_l)
+    idx = np.flatnonzero(fb)[:64]
+    if idx.size:
+        S, P = gcamb.synth_sources(g, Xh[torch.as_tensor(idx, device="cuda")].contiguous())
+        proj = gcamb.los_cl(g, S, P, gcamb.F16X3).cpu().numpy()
+        gcamb.sync()
+        np.testing.assert_allclose(got[idx], proj, rtol=2e-5, atol=0)
+    rates = emulator.serve_rates(e, g, Xh, reps=3)
+    base = rates["sources_and_projection_spectra_per_s"]
+    print("emulator at tol %g: served %.3f, %.3g spectra/s against %.3g for sources + projection "
+          "(projection alone %.3g; target 1e-3 served %.3f)" % (
+              tol, served, rates["emulate_spectra_per_s"], base, rates["projection_spectra_per_s"],
+              at_target["frac_served"]))
+    assert rates["emulate_spectra_per_s"] > 0.8 * base / max(1e-9, 1.0 - served)
+
+
+def test_network_pass_is_faster_than_the_projection():
+    """The network's own pass (every populated cell trusted) against the
+    batched projection on the 256-source, l_max = 2500 grid, same GPU."""
     wl = synth.workload("batched_lmax2500")
     g = gcamb.grid_create(wl.k, wl.tau, wl.tau0, wl.lmin, wl.lmax)
     e = gcamb.emu_create(g, width=512, depth=3, max_batch=4096, seed=4)
@@ -218,5 +275,5 @@ def test_network_serves_faster_than_the_projection():
         gcamb.los_cl(g, S, P, gcamb.F16X3)
     gcamb.sync()
     proj_rate = 5 * 256 / (time.perf_counter() - t0)
-    print("emulator %.3g spectra/s, projection %.3g spectra/s" % (emu_rate, proj_rate))
+    print("network %.3g spectra/s, projection %.3g spectra/s" % (emu_rate, proj_rate))
     assert emu_rate > 5 * proj_rate
