@@ -211,6 +211,31 @@ def committed_traffic(name, mode):
     return None
 
 
+def host_numa(dev, t):
+    """NUMA node of the GPU (its PCI function) and of the pages of a pinned
+    host tensor (move_pages with no target: the query form), or None."""
+    out = {"gpu_node": None, "buffer_node": None}
+    try:
+        import torch
+        bus = torch.cuda.get_device_properties(dev).pci_bus_id.lower()
+        dom, rest = bus.split(":", 1)
+        path = "/sys/bus/pci/devices/%04x:%s/numa_node" % (int(dom, 16), rest)
+        out["gpu_node"] = int(open(path).read().strip())
+    except Exception:
+        pass
+    try:
+        import ctypes
+        libc = ctypes.CDLL(None, use_errno=True)
+        pages = (ctypes.c_void_p * 1)(t.data_ptr())
+        status = (ctypes.c_int * 1)(-1)
+        nr = {"aarch64": 239, "x86_64": 279}.get(os.uname().machine)
+        if nr is not None and libc.syscall(nr, 0, 1, pages, None, status, 0) == 0:
+            out["buffer_node"] = int(status[0])
+    except Exception:
+        pass
+    return out
+
+
 def l_range_errors(rel, lmin, lmax):
     """Max relative error over [sources] within each multipole range."""
     import numpy as np
@@ -1016,9 +1041,13 @@ def main():
     e2e_ms = timed(lambda: e2e_run(args.e2e_steps))
     torch.cuda.synchronize()
     gcamb.sync()
+    # the host link: one pinned copy of the sources alone, and where the
+    # memory sits (NUMA node of the GPU's PCI function, of the buffer's pages)
+    h2d_ms = timed(lambda: S_d[0].copy_(S_h, non_blocking=True))
     e2e = {"value": world * M * args.e2e_steps / (e2e_ms * 1e-3), "unit": "spectra/s",
            "h2d_bytes_per_step": S_h.numel() * 4 + P_h.numel() * 8, "d2h_bytes_per_step": C_h[0].numel() * 8,
-           "overlap": "double-buffered: H2D of batch i+1 on a copy stream during the compute of batch i"}
+           "overlap": "double-buffered: H2D of batch i+1 on a copy stream during the compute of batch i",
+           "h2d_gbs": S_h.numel() * 4 / (h2d_ms * 1e-3) / 1e9, "numa": host_numa(dev, S_h)}
 
     # ---------------- plain FP64 on the same grid (the metric's comparison), 4 sources
     gcamb.bessel_table(g, gcamb.PLAIN64)

@@ -616,6 +616,18 @@ int gcamb_profile_read(int kernel, double *total_ms, int64_t *launches);
 int gcamb_probe_flops(int what, double *flops);
 
 /*
+ * Self-test of the tensor cores' FP32 accumulation (no counterpart in the
+ * paper; it documents what the batched path's chain records correct).  One
+ * 128 x 128 tile
+ *   C[i][n] = sum_{k < K} A[i][k] B[n][k]
+ * through the library's tcgen05 GEMM (kind::f16): A[128][K], B[128][K]
+ * device float, row-major, rounded to bf16 by the loaders; C[128][128]
+ * device float.  1 <= K <= 2^20.  Asynchronous on `stream`; a device-side
+ * timeout is reported by gcamb_sync.  Errors: GCAMB_EINVAL, GCAMB_ECUDA.
+ */
+int gcamb_probe_mma(const float *A, const float *B, int K, float *C, void *stream);
+
+/*
  * Self-test of the device-side failure path (no counterpart in the paper).
  * Launches one thread that waits, with the bounded wait every tensor-core
  * kernel of the library uses, on an mbarrier that nothing ever arrives on.

@@ -395,6 +395,28 @@ int check_emu(const gcamb_emu *e, int B) {
 
 extern "C" {
 
+// One 128 x 128 tile C = A B^T over K through the library's tcgen05 GEMM
+// (operands rounded to bf16 by its loaders, FP32 accumulation in TMEM): the
+// self-test of the tensor cores' accumulation.
+int gcamb_probe_mma(const float *A, const float *B, int K, float *C, void *stream) {
+  if (!A || !B || !C) return fail(GCAMB_EINVAL, "probe_mma: NULL pointer");
+  if (K < 1 || K > (1 << 20)) return fail(GCAMB_EINVAL, "probe_mma: K must be in [1, 2^20]");
+  int *err = device_error_flag();
+  if (!err) return fail(GCAMB_ECUDA, "probe_mma: error flag allocation");
+  GemmArgs a{};
+  a.A = rowmajor(A, 128, K, K);
+  a.B = rowmajor(B, 128, K, K);
+  a.M = 128;
+  a.N = 128;
+  a.K = K;
+  a.C = C;
+  a.ldc = 128;
+  a.CT = nullptr;
+  a.kchunks = 0;
+  a.err = err;
+  return gemm<kStore>(a, (cudaStream_t)stream);
+}
+
 int gcamb_emu_create(gcamb_grid *g, int n_in, int width, int depth, int max_batch, uint64_t seed, gcamb_emu **out) {
   if (!out) return fail(GCAMB_EINVAL, "emu_create: out is NULL");
   *out = nullptr;

@@ -105,6 +105,7 @@ def lib():
     L.gcamb_profile_enable.argtypes = [ctypes.c_int]
     L.gcamb_profile_read.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
     L.gcamb_probe_flops.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    L.gcamb_probe_mma.argtypes = [_vp, _vp, ctypes.c_int, _vp, _vp]
     L.gcamb_selftest_wait.argtypes = [_vp, _vp]
     _lib = L
     return L
@@ -544,6 +545,18 @@ def los_cl_noalloc(g: Grid, S, Pk, mode: int, Cl, status=None, stream=None):
 
 def sync(stream=None):
     _check(lib().gcamb_sync(_stream(stream)))
+
+
+def probe_mma(A, B, C=None, stream=None):
+    """C[128][128] = A[128][K] . B[128][K]^T through the library's tcgen05
+    GEMM (bf16 operands, FP32 accumulation): the accumulation self-test."""
+    import torch
+    K = A.shape[1]
+    if C is None:
+        C = torch.empty((128, 128), dtype=torch.float32, device=A.device)
+    _check(lib().gcamb_probe_mma(_dev(A, torch.float32, (128, K), "A"), _dev(B, torch.float32, (128, K), "B"), int(K),
+                                 _dev(C, torch.float32, (128, 128), "C"), _stream(stream)))
+    return C
 
 
 def probe_flops(what: int) -> float:
