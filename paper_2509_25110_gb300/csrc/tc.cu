@@ -1387,6 +1387,7 @@ struct TcPlan {
   int ksub = kKSub;    // non-empty k per FP32 chunk sum
   int chain = 0;       // lp = 2: 1, chain records where an item's second tile is idle; 2, also l-tile 0 alone
   int nslots = 0;      // chunk slots (each lp tiles' partials)
+  int tail = 0;        // the tail setting the items were cut with (tail_key)
   std::vector<int> blob;
   size_t o_items = 0, o_tile_ptr = 0, o_tile_items = 0, o_perm = 0, o_nkm = 0, o_lmaxm = 0, o_tnk = 0;
   std::vector<double> cost;  // per item
@@ -1454,6 +1455,29 @@ int want_chain() {
     if (e[0] == '2') return 2;
   }
   return 1;
+}
+
+// The tail of the work list: the share of the cost, handed out last, whose
+// items are cut into pieces, and the pieces per item (GCAMB_TC_TAIL=frac:parts;
+// 0:1 none).
+void want_tail(double *frac, int *parts) {
+  *frac = 0.1;
+  *parts = 4;
+  if (const char *e = getenv("GCAMB_TC_TAIL")) {
+    double f = 0.0;
+    int n = 1;
+    if (sscanf(e, "%lf:%d", &f, &n) == 2 && f >= 0.0 && f <= 1.0 && n >= 1 && n <= 64) {
+      *frac = f;
+      *parts = n;
+    }
+  }
+}
+
+int tail_key() {
+  double f = 0.0;
+  int n = 1;
+  want_tail(&f, &n);
+  return (int)(f * 1000.0 + 0.5) * 100 + n;
 }
 
 // Non-empty k per FP32 chunk sum of the epilogue (the partial-sum length):
@@ -1630,7 +1654,64 @@ void plan_build(const gcamb_grid *g, int M, int mode, int nt, const int *lmax_c,
     items.swap(sorted);
     pl.cost.swap(sc);
   }
+  // the tail: the items handed out last (the last `frac` of the cost) are cut
+  // into `parts` pieces of about equal cost, so that the persistent CTAs run
+  // out of work closer together
+  {
+    double frac = 0.0;
+    int parts = 1;
+    want_tail(&frac, &parts);
+    if (frac > 0.0 && parts > 1) {
+      double tot = 0.0;
+      for (double c : pl.cost) tot += c;
+      std::vector<TcItem> out;
+      std::vector<double> oc;
+      double before = 0.0;
+      for (int i = 0; i < pl.nitems; ++i) {
+        const TcItem it = items[i];
+        const double c = pl.cost[i];
+        if (before < (1.0 - frac) * tot || c <= 0.0) {
+          out.push_back(it);
+          oc.push_back(c);
+        } else {
+          const double piece = c / parts;
+          double acc = 0.0;
+          int qb = it.qb;
+          for (int q = it.qb; q < it.qe; ++q) {
+            const double kc = kcost(q, it.lt, it.ntl);
+            acc += kc;
+            // cut after a k with blocks once a piece's cost is reached (the
+            // next piece starts at the next k with blocks)
+            if (kc > 0.0 && acc >= piece && q + 1 < it.qe) {
+              int qn = q + 1;
+              while (qn < it.qe && kcost(qn, it.lt, it.ntl) == 0.0) ++qn;
+              if (qn >= it.qe) break;
+              TcItem a = it;
+              a.qb = qb;
+              a.qe = q + 1;
+              out.push_back(a);
+              oc.push_back(acc);
+              qb = qn;
+              acc = 0.0;
+              q = qn - 1;
+            }
+          }
+          TcItem a = it;
+          a.qb = qb;
+          out.push_back(a);
+          double rest = 0.0;
+          for (int q = qb; q < it.qe; ++q) rest += kcost(q, it.lt, it.ntl);
+          oc.push_back(rest);
+        }
+        before += c;
+      }
+      items.swap(out);
+      pl.cost.swap(oc);
+      pl.nitems = (int)items.size();
+    }
+  }
   pl.nctas = std::max(1, std::min(sms, pl.nitems));
+  pl.tail = tail_key();
   // chunk slots: an item's FP32 sums are flushed every ksub non-empty k (the
   // producer's records), each chunk to its own slot of lp tiles' partials
   pl.ksub = want_ksub();
@@ -1714,6 +1795,7 @@ TcPlan *get_plan(const gcamb_grid *g, int M, int mode, int *rc) {
   for (auto &e : g_plans)
     if (e.first == g && !e.second->te && e.second->M == M && e.second->mode == mode && e.second->NT == nt &&
         e.second->fused == want_fused(g, mode, nt, true) && e.second->ksub == want_ksub() &&
+        e.second->tail == tail_key() &&
         e.second->chain == (e.second->lp == 2 ? want_chain() : 0) &&
         e.second->lp == (e.second->nkbs < 32768 ? want_lp(mode, nt, false) : 1))
       return e.second;
