@@ -326,7 +326,11 @@ int gcamb_los_cl_workspace(const gcamb_grid *g, int M, int mode, size_t *bytes);
  * width; GCAMB_TC_FUSED=0 splits the sources in a separate pass instead of in
  * shared memory; GCAMB_TC_LP=1 one multipole tile per work item instead of two;
  * GCAMB_TC_KSUB=1..64 k nodes per FP32 chunk sum instead of 16 (1: every k's
- * term is its own partial, and C_l is the FP64 sum of the FP32 terms).
+ * term is its own partial, and C_l is the FP64 sum of the FP32 terms);
+ * GCAMB_TC_CHAIN=0|1|2 chain records (a tile's hi*hi tau-sum spread over three
+ * TMEM accumulators): none, where an item's second l-tile is idle (default),
+ * or also l-tile 0 in items of its own; GCAMB_TC_TAIL=frac:parts the share of
+ * the cost handed out last whose items are cut into parts (default 0.1:4).
  * Errors: GCAMB_EINVAL, GCAMB_ESTATE, GCAMB_EUNSUPPORTED (device is not
  * sm_103), GCAMB_ECUDA; GCAMB_ETIMEOUT is reported by gcamb_sync.
  */
