@@ -1184,34 +1184,54 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const float *__restrict
 }
 
 // Row scales and epilogue weights of the fused fp16 path (a uniform batch,
-// sources in caller order): one warp per (source, k) row, taken in memory
-// order so that the 4 KB rows stream; 16-byte loads when vec.  Same scale
-// rule as the split pass: 2^s with the row's largest |S| in [2^13, 2^14),
-// s clamped to [-40, 80]; wq = sqrt(4 pi w_k P) 2^-(sJ + s).
+// sources in caller order): one warp per two adjacent (source, k) rows, taken
+// in memory order so that the 4 KB rows stream; with vec, every lane has its
+// eight 16-byte loads of the two rows in flight before it takes a maximum.
+// Same scale rule as the split pass: 2^s with the row's largest |S| in
+// [2^13, 2^14), s clamped to [-40, 80]; wq = sqrt(4 pi w_k P) 2^-(sJ + s).
 __global__ void __launch_bounds__(256) rowscale_kernel(const float *__restrict__ S, const double *__restrict__ Pk,
                                                        const double *__restrict__ wk, int M, int nk, int ntau,
                                                        int mpad, int sJ, int vec, float *__restrict__ wq,
                                                        float *__restrict__ sc) {
   const int lane = threadIdx.x & 31;
-  const size_t r = (size_t)blockIdx.x * 8 + (threadIdx.x >> 5);  // m * nk + q
-  if (r >= (size_t)M * nk) return;
-  const int m = (int)(r / nk), q = (int)(r - (size_t)m * nk);
-  const float *src = S + r * ntau;
-  float mx = 0.f;
+  const size_t rows = (size_t)M * nk;
+  const size_t r0 = ((size_t)blockIdx.x * 8 + (threadIdx.x >> 5)) * 2;  // m * nk + q of the first row
+  if (r0 >= rows) return;
+  const bool two = r0 + 1 < rows;
+  const float *a = S + r0 * ntau, *b = a + ntau;  // the second row follows the first
+  float mx0 = 0.f, mx1 = 0.f;
   if (vec) {
-    const float4 *s4 = reinterpret_cast<const float4 *>(src);
+    const float4 *a4 = reinterpret_cast<const float4 *>(a), *b4 = reinterpret_cast<const float4 *>(b);
     const int n4 = ntau >> 2;
-#pragma unroll 8
-    for (int c = lane; c < n4; c += 32) {
-      const float4 f = __ldg(s4 + c);
-      mx = fmaxf(mx, fmaxf(fmaxf(fabsf(f.x), fabsf(f.y)), fmaxf(fabsf(f.z), fabsf(f.w))));
+    for (int c0 = 0; c0 < n4; c0 += 128) {
+      float4 fa[4], fb[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int c = c0 + lane + 32 * u;
+        fa[u] = c < n4 ? __ldg(a4 + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+        fb[u] = (two && c < n4) ? __ldg(b4 + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        mx0 = fmaxf(mx0, fmaxf(fmaxf(fabsf(fa[u].x), fabsf(fa[u].y)), fmaxf(fabsf(fa[u].z), fabsf(fa[u].w))));
+        mx1 = fmaxf(mx1, fmaxf(fmaxf(fabsf(fb[u].x), fabsf(fb[u].y)), fmaxf(fabsf(fb[u].z), fabsf(fb[u].w))));
+      }
     }
   } else {
-    for (int t = lane; t < ntau; t += 32) mx = fmaxf(mx, fabsf(__ldg(src + t)));
+    for (int t = lane; t < ntau; t += 32) {
+      mx0 = fmaxf(mx0, fabsf(__ldg(a + t)));
+      if (two) mx1 = fmaxf(mx1, fabsf(__ldg(b + t)));
+    }
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if (lane == 0) {
+  for (int o = 16; o > 0; o >>= 1) {
+    mx0 = fmaxf(mx0, __shfl_xor_sync(0xffffffffu, mx0, o));
+    mx1 = fmaxf(mx1, __shfl_xor_sync(0xffffffffu, mx1, o));
+  }
+  if (lane < (two ? 2 : 1)) {  // lane j writes row r0 + j
+    const size_t r = r0 + lane;
+    const float mx = lane ? mx1 : mx0;
+    const int m = (int)(r / nk), q = (int)(r - (size_t)m * nk);
     int s = 0;
     if (mx > 0.f) {
       int e;
@@ -1859,7 +1879,7 @@ int launch_tc(const gcamb_grid *g, const TcPlan &pl, const float *S, const doubl
         if (e == cudaSuccess) e = cudaMemsetAsync(sc, 0, (size_t)g->nk * pl.mpad * sizeof(float), st);
         if (e != cudaSuccess) return cuda_fail(e, "los_cl: weight reset");
       }
-      rowscale_kernel<<<(unsigned)(((size_t)pl.M * g->nk + 7) / 8), 256, 0, st>>>(
+      rowscale_kernel<<<(unsigned)(((size_t)pl.M * g->nk + 15) / 16), 256, 0, st>>>(
           S, Pk, g->d_wk, pl.M, g->nk, g->ntau, pl.mpad, t.scale_exp, vec, wp, sc);
     }
     else if (MODE == kF16 && pl.nkbs * (TcGeom<MODE>::kRowB / 16) <= 32 * 8)
