@@ -1882,6 +1882,9 @@ int launch_tc(const gcamb_grid *g, const TcPlan &pl, const float *S, const doubl
       rowscale_kernel<<<(unsigned)(((size_t)pl.M * g->nk + 15) / 16), 256, 0, st>>>(
           S, Pk, g->d_wk, pl.M, g->nk, g->ntau, pl.mpad, t.scale_exp, vec, wp, sc);
     }
+    else if (MODE == kF16 && pl.nkbs * (TcGeom<MODE>::kRowB / 16) <= 32 * 4)  // rows of up to 1024 tau
+      split_rows_kernel<MODE, 4><<<nblk, 256, 0, st>>>(S, Pk, g->d_wk, g->d_k, pl.M, g->nk, g->ntau, NT, pl.n_mt,
+                                                       pl.nkbs, pl.mpad, t.scale_exp, perm, nkm, tnk, vec, sp, wp);
     else if (MODE == kF16 && pl.nkbs * (TcGeom<MODE>::kRowB / 16) <= 32 * 8)
       split_rows_kernel<MODE, 8><<<nblk, 256, 0, st>>>(S, Pk, g->d_wk, g->d_k, pl.M, g->nk, g->ntau, NT, pl.n_mt,
                                                        pl.nkbs, pl.mpad, t.scale_exp, perm, nkm, tnk, vec, sp, wp);
