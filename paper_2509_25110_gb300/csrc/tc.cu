@@ -424,8 +424,10 @@ __global__ void __launch_bounds__(TcRoles<FUSED, TE, LP>::kThreadsT, 1)
                            full0 + 8 * stage);
                 if constexpr (FUSED)
                   tma_load_3d(sa + 2 * C::kABytes, &tm_src, kb * 32, q, it.mt * NT, full0 + 8 * stage);
-                else
-                  bulk_g2s(sa + 2 * C::kABytes, b + (size_t)kb * C::kBBytes, C::kBBytes, full0 + 8 * stage);
+                else  // split sources: evict first, so that L2 keeps the table blocks the other source
+                      // tiles' items read next (uneven 1000-source batch: 16.56 -> 16.35 ms per step)
+                  bulk_g2s_hint(sa + 2 * C::kABytes, b + (size_t)kb * C::kBBytes, C::kBBytes, full0 + 8 * stage,
+                                l2_policy_evict_first());
                 if (++stage == S) {
                   stage = 0;
                   phase ^= 1u;
