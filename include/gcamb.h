@@ -396,20 +396,26 @@ int gcamb_los_cl_pair(const gcamb_grid *gx, const gcamb_grid *gy, const float *S
  *                       each source's C_l over its own prefix; tune is
  *                       ignored, the plan info's "items" is the number of
  *                       chunks); the grid's table for this mode must be built.
- *   tune                0: source-tile width from a heuristic;
- *                       1: the first gcamb_plan_launch times the candidate
- *                       widths (64, 128, 256 sources) on its inputs and keeps
- *                       the fastest.  If the environment variable
- *                       GCAMB_TUNE_CACHE names a file, choices are appended
- *                       there (one JSON object per line, keyed by device,
- *                       grid and batch) and reused by later plans.
+ *   tune                0: source-tile width from a heuristic, the default
+ *                       work-list settings;
+ *                       1: the first gcamb_plan_launch times every
+ *                       candidate on its inputs and keeps the fastest:
+ *                       source-tile width (64, 128, 256 sources) x multipole
+ *                       tiles per item (2 where the mode allows, 1) x tail
+ *                       (the last 10% of the cost cut into items of a quarter
+ *                       size, or no cut) x items per CTA (4; at width 128
+ *                       also 8, shorter k chunks): up to 14 candidates.  If
+ *                       the environment variable GCAMB_TUNE_CACHE names a
+ *                       file, choices are appended there (one JSON object
+ *                       per line, keyed by device, grid and batch) and
+ *                       reused by later plans.
  * Sources are processed sorted by l_max (descending), so that at each (k,
  * l-tile) the sources that need it are a prefix of the source tiles; work
  * items are spread over one persistent CTA per SM, longest first.
  */
 typedef struct gcamb_plan gcamb_plan;
 
-#define GCAMB_PLAN_INFO_N 10
+#define GCAMB_PLAN_INFO_N 12
 
 int gcamb_plan_create(gcamb_grid *g, int M, const int *lmax_m, const int *nk_m, int mode, int tune,
                       gcamb_plan **out);
@@ -440,7 +446,10 @@ int gcamb_plan_launch(gcamb_plan *p, const float *S, const double *Pk, double *C
  * [6] M, [7] workspace bytes of the width in use, [8] 1 if the sources are
  * read in place (fused kernel, no split pass: uniform batches only), [9]
  * multipole tiles per work item (2 when adjacent 128-multipole tiles share
- * each loaded and split source block: the in-place kernel; else 1).
+ * each loaded and split source block; else 1), [10] work items of about
+ * equal cost per persistent CTA (4 or 8: the k-chunk length), [11] the tail
+ * of the work list, 100 x round(1000 x share) + pieces (10004: the last 10%
+ * of the cost in items cut into 4 pieces; 1: no tail cut).
  */
 int gcamb_plan_info(const gcamb_plan *p, int64_t *info);
 

@@ -1409,7 +1409,8 @@ struct TcPlan {
   int ksub = kKSub;    // non-empty k per FP32 chunk sum
   int chain = 0;       // lp = 2: 1, chain records where an item's second tile is idle; 2, also l-tile 0 alone
   int nslots = 0;      // chunk slots (each lp tiles' partials)
-  int tail = 0;        // the tail setting the items were cut with (tail_key)
+  int tail = 0;        // the tail setting the items were cut with (as tail_key)
+  int per_cta = 4;     // items of about equal cost per persistent CTA
   std::vector<int> blob;
   size_t o_items = 0, o_tile_ptr = 0, o_tile_items = 0, o_perm = 0, o_nkm = 0, o_lmaxm = 0, o_tnk = 0;
   std::vector<double> cost;  // per item
@@ -1553,13 +1554,25 @@ int num_sms() {
   return sms > 0 ? sms : 148;
 }
 
+// Work-list settings a plan's autotuner chooses among (null: the defaults
+// and the environment's switches): lp 1 forces one l-tile per item (0: the
+// default, two where the mode allows); the tail (the share of the cost
+// handed out last and the pieces each of its items is cut into); per_cta,
+// the items of about equal cost per persistent CTA (the k-chunk length).
+struct PlanCfg {
+  int lp = 0;
+  double tail_frac = 0.1;
+  int tail_parts = 4;
+  int per_cta = 4;
+};
+
 // lmax_c / nk_c: per-source l_max and k-prefix length in the caller's order,
 // or null for a uniform batch (every source uses the whole grid).
 //
 // te: a temperature + E-mode plan (uniform, fused bf16): nt models per tile,
 // each with a temperature and a polarisation operand row.
 void plan_build(const gcamb_grid *g, int M, int mode, int nt, const int *lmax_c, const int *nk_c, TcPlan &pl,
-                bool te = false) {
+                bool te = false, const PlanCfg *cfg = nullptr) {
   const ModeLayout lay = mode_layout(mode);
   const Table &t = g->tab[mode];
   pl.mode = mode;
@@ -1584,6 +1597,7 @@ void plan_build(const gcamb_grid *g, int M, int mode, int nt, const int *lmax_c,
   // the pass beat the fused kernel (48.0k against 43.8k spectra/s)
   pl.fused = te || want_fused(g, mode, nt, pl.uniform);
   pl.lp = pl.nkbs < 32768 ? want_lp(mode, nt, te) : 1;  // LP = 2 records pack two block counts in 16 bits
+  if (cfg && cfg->lp == 1) pl.lp = 1;
   const int lp = pl.lp;
   for (int j = 0; j < M; ++j) {
     nkm[j] = nk_of(perm[j]);
@@ -1621,7 +1635,8 @@ void plan_build(const gcamb_grid *g, int M, int mode, int nt, const int *lmax_c,
       for (int q = 0; q < tile_nk[mt]; ++q) total += kcost(q, lt, ntl_of(lt, mt));
     }
   const int sms = num_sms();
-  const double target = std::max(4.0, total / (sms * 4.0));
+  pl.per_cta = cfg ? cfg->per_cta : 4;
+  const double target = std::max(4.0, total / (sms * (double)pl.per_cta));
   std::vector<TcItem> items;
   pl.cost.clear();
   for (int lt : starts)
@@ -1682,7 +1697,13 @@ void plan_build(const gcamb_grid *g, int M, int mode, int nt, const int *lmax_c,
   {
     double frac = 0.0;
     int parts = 1;
-    want_tail(&frac, &parts);
+    if (cfg) {
+      frac = cfg->tail_frac;
+      parts = cfg->tail_parts;
+    } else {
+      want_tail(&frac, &parts);
+    }
+    pl.tail = (int)(frac * 1000.0 + 0.5) * 100 + parts;
     if (frac > 0.0 && parts > 1) {
       double tot = 0.0;
       for (double c : pl.cost) tot += c;
@@ -1733,7 +1754,7 @@ void plan_build(const gcamb_grid *g, int M, int mode, int nt, const int *lmax_c,
     }
   }
   pl.nctas = std::max(1, std::min(sms, pl.nitems));
-  pl.tail = tail_key();
+
   // chunk slots: an item's FP32 sums are flushed every ksub non-empty k (the
   // producer's records), each chunk to its own slot of lp tiles' partials
   pl.ksub = want_ksub();
@@ -2185,7 +2206,35 @@ void drop_plans(const gcamb_grid *g) {
 namespace gcamb {
 namespace {
 
-constexpr int kCandNT[3] = {64, 128, 256};
+// The autotuner's candidates: source-tile width x l-tiles per item x tail x
+// items per CTA (the k-chunk length); at most kMaxCand.
+constexpr int kMaxCand = 16;
+
+struct Cand {
+  int nt;
+  PlanCfg cfg;
+};
+
+std::vector<Cand> tune_candidates(int M, int mode) {
+  std::vector<Cand> out;
+  for (int nt : {64, 128, 256}) {
+    if (nt > 128 && M <= 128) continue;  // one tile would hold the whole batch at 128
+    for (int lp : {2, 1}) {
+      if (lp == 2 && (nt > 128 || mode == GCAMB_TF32X3)) continue;
+      for (int tl = 0; tl < 2; ++tl)
+        for (int per : {4, 8}) {
+          if (per == 8 && nt != 128) continue;
+          Cand c{nt, PlanCfg()};
+          c.cfg.lp = lp;
+          c.cfg.tail_frac = tl ? 0.0 : 0.1;
+          c.cfg.tail_parts = tl ? 1 : 4;
+          c.cfg.per_cta = per;
+          out.push_back(c);
+        }
+    }
+  }
+  return out;
+}
 
 uint64_t fnv1a(uint64_t h, const void *p, size_t n) {
   const unsigned char *c = static_cast<const unsigned char *>(p);
@@ -2206,8 +2255,10 @@ struct gcamb_plan {
   int *d_lmax = nullptr, *d_nk = nullptr;   // plain: device copies of the per-source l_max, k prefix
   bool tune = false, tuned = false;
   std::vector<int> lmax_c, nk_c;
-  gcamb::TcPlan cand[3];
-  bool have[3] = {false, false, false};
+  gcamb::TcPlan cand[gcamb::kMaxCand];
+  gcamb::Cand spec[gcamb::kMaxCand];
+  bool have[gcamb::kMaxCand] = {};
+  int ncand = 0;
   int chosen = -1;
   cudaGraphExec_t exec = nullptr;
   cudaStream_t cap = nullptr;  // private stream the graph is captured on
@@ -2224,33 +2275,53 @@ std::string tune_cache_path() {
   return e ? std::string(e) : std::string();
 }
 
-// One JSON object per line: {"key": "...", "nt": 128, "ms": 1.234}
-int tune_cache_lookup(const std::string &key) {
+// One JSON object per line: {"key": "...", "nt": 128, "lp": 2, "tail_frac":
+// 0.1, "tail_parts": 4, "per_cta": 4, "ms": 1.234}; the last line with the
+// key wins.
+bool tune_cache_lookup(const std::string &key, Cand *c) {
   const std::string path = tune_cache_path();
-  if (path.empty()) return -1;
+  if (path.empty()) return false;
   FILE *f = fopen(path.c_str(), "r");
-  if (!f) return -1;
+  if (!f) return false;
   char line[1024];
-  int nt = -1;
+  bool found = false;
+  auto num = [](const std::string &s, const char *name, double *v) {
+    const std::string pat = std::string("\"") + name + "\": ";
+    const size_t n = s.find(pat);
+    if (n == std::string::npos) return false;
+    *v = atof(s.c_str() + n + pat.size());
+    return true;
+  };
   while (fgets(line, sizeof line, f)) {
     const std::string s(line);
     const size_t k = s.find("\"key\": \"");
     if (k == std::string::npos) continue;
     const size_t b = k + 8, e = s.find('"', b);
     if (e == std::string::npos || s.substr(b, e - b) != key) continue;
-    const size_t n = s.find("\"nt\": ");
-    if (n != std::string::npos) nt = atoi(s.c_str() + n + 6);
+    double nt, lp, tf, tp, pc;
+    if (num(s, "nt", &nt) && num(s, "lp", &lp) && num(s, "tail_frac", &tf) && num(s, "tail_parts", &tp) &&
+        num(s, "per_cta", &pc) && (nt == 64 || nt == 128 || nt == 256) && (lp == 1 || lp == 2) && tf >= 0 &&
+        tf <= 1 && tp >= 1 && tp <= 64 && pc >= 1 && pc <= 64) {
+      c->nt = (int)nt;
+      c->cfg.lp = (int)lp;
+      c->cfg.tail_frac = tf;
+      c->cfg.tail_parts = (int)tp;
+      c->cfg.per_cta = (int)pc;
+      found = true;
+    }
   }
   fclose(f);
-  return nt;
+  return found;
 }
 
-void tune_cache_store(const std::string &key, int nt, double ms) {
+void tune_cache_store(const std::string &key, const Cand &c, double ms) {
   const std::string path = tune_cache_path();
   if (path.empty()) return;
   FILE *f = fopen(path.c_str(), "a");
   if (!f) return;
-  fprintf(f, "{\"key\": \"%s\", \"nt\": %d, \"ms\": %.6f}\n", key.c_str(), nt, ms);
+  fprintf(f, "{\"key\": \"%s\", \"nt\": %d, \"lp\": %d, \"tail_frac\": %.3f, \"tail_parts\": %d, "
+          "\"per_cta\": %d, \"ms\": %.6f}\n",
+          key.c_str(), c.nt, c.cfg.lp, c.cfg.tail_frac, c.cfg.tail_parts, c.cfg.per_cta, ms);
   fclose(f);
 }
 
@@ -2340,24 +2411,31 @@ int gcamb_plan_create(gcamb_grid *g, int M, const int *lmax_m, const int *nk_m, 
     h = fnv1a(h, nk_m, M * sizeof(int));
   }
   char kb[256];
-  snprintf(kb, sizeof kb, "v1|sm%d|%d|%d|%d|%d|%g|%d|%d|%016llx", num_sms(), g->nk, g->ntau, g->lmin, g->lmax,
+  snprintf(kb, sizeof kb, "v2|sm%d|%d|%d|%d|%d|%g|%d|%d|%016llx", num_sms(), g->nk, g->ntau, g->lmin, g->lmax,
            g->eps_cut, M, mode, (unsigned long long)h);
   p->key = kb;
-  int cached = p->tune ? tune_cache_lookup(p->key) : -1;
-  for (int c = 0; c < 3; ++c) {
-    const int nt = kCandNT[c];
-    const bool want = p->tune ? (cached < 0 ? (nt <= 128 || M > 128) : nt == cached) : nt == pick_nt(M);
-    if (!want) continue;
-    plan_build(g, M, mode, nt, lmax_m, nk_m, p->cand[c]);
+  // candidates: the cached choice, every tuning candidate, or the heuristic
+  // width with the default settings (and the environment's switches)
+  Cand cached{};
+  const bool hit = p->tune && tune_cache_lookup(p->key, &cached);
+  std::vector<Cand> list;
+  if (hit) list.push_back(cached);
+  else if (p->tune) list = tune_candidates(M, mode);
+  else list.push_back(Cand{pick_nt(M), PlanCfg()});
+  const bool defaults = !p->tune;  // heuristic plans keep the environment's switches (GCAMB_TC_LP, _TAIL)
+  for (size_t c = 0; c < list.size() && (int)c < kMaxCand; ++c) {
+    plan_build(g, M, mode, list[c].nt, lmax_m, nk_m, p->cand[c], false, defaults ? nullptr : &list[c].cfg);
     int rc = upload_blob(p->cand[c]);
     if (rc) {
       gcamb_plan_destroy(p);
       return rc;
     }
+    p->spec[c] = list[c];
     p->have[c] = true;
-    if (!p->tune || cached == nt) p->chosen = c;
+    p->ncand = (int)c + 1;
   }
-  if (p->chosen >= 0 && cached >= 0) p->tuned = true;
+  if (!p->tune || hit) p->chosen = 0;
+  if (hit) p->tuned = true;
   *out = p;
   return GCAMB_OK;
 }
@@ -2377,7 +2455,7 @@ int gcamb_plan_workspace(const gcamb_plan *p, size_t *bytes) {
   if (!p || !bytes) return fail(GCAMB_EINVAL, "plan_workspace: NULL argument");
   size_t b = 0;
   if (p->plain) b = plain_plan_workspace_bytes(p->g, p->M);
-  for (int c = 0; c < 3; ++c)
+  for (int c = 0; c < p->ncand; ++c)
     if (p->have[c]) b = std::max(b, p->cand[c].ws_bytes);
   *bytes = b;
   return GCAMB_OK;
@@ -2396,6 +2474,8 @@ int gcamb_plan_info(const gcamb_plan *p, int64_t *info) {
   info[7] = c ? (int64_t)c->ws_bytes : (p->plain ? (int64_t)plain_plan_workspace_bytes(p->g, p->M) : 0);
   info[8] = c && c->fused ? 1 : 0;
   info[9] = c ? c->lp : 0;
+  info[10] = c ? c->per_cta : 0;
+  info[11] = c ? c->tail : 0;
   return GCAMB_OK;
 }
 
@@ -2414,7 +2494,7 @@ int gcamb_plan_launch(gcamb_plan *p, const float *S, const double *Pk, double *C
     // autotune: time every candidate tile on these inputs, keep the fastest
     float best = 1e30f;
     int bi = -1;
-    for (int c = 0; c < 3; ++c) {
+    for (int c = 0; c < p->ncand; ++c) {
       if (!p->have[c]) continue;
       float ms = 0.f;
       int rc = plan_time(p, c, S, Pk, Cl, w, st, &ms);
@@ -2427,8 +2507,8 @@ int gcamb_plan_launch(gcamb_plan *p, const float *S, const double *Pk, double *C
     if (bi < 0) return fail(GCAMB_ESTATE, "plan_launch: no candidate tile");
     p->chosen = bi;
     p->tuned = true;
-    tune_cache_store(p->key, p->cand[bi].NT, best);
-    for (int c = 0; c < 3; ++c)
+    tune_cache_store(p->key, p->spec[bi], best);
+    for (int c = 0; c < p->ncand; ++c)
       if (c != bi && p->have[c]) {
         p->cand[c].release();
         p->have[c] = false;
