@@ -56,6 +56,7 @@ def run(k, tau, S, P, lmin, lmax, mode, g=None):
     (120, 333, 2, 300, 100),   # NT = 128, ragged tau block, ragged source tile
     (64, 200, 0, 129, 300),    # three source tiles of 128, lmin = 0, tile boundary at 128
     (70, 332, 2, 300, 100),    # sources read in place (ntau % 4 == 0): ragged tau block and source tile
+    (63, 200, 2, 300, 5),      # an odd number of (source, k) rows: the row-scale pass's last warp has one
 ])
 def test_los_cl_matches_oracle(orc, mode, nk, ntau, lmin, lmax, M):
     k, tau, S, P = case(nk, ntau, lmin, lmax, M)
