@@ -397,14 +397,16 @@ int gcamb_los_cl_pair(const gcamb_grid *gx, const gcamb_grid *gy, const float *S
  *                       ignored, the plan info's "items" is the number of
  *                       chunks); the grid's table for this mode must be built.
  *   tune                0: source-tile width from a heuristic, the default
- *                       work-list settings;
+ *                       work-list settings (items ending at multiples of 16
+ *                       k nodes, 12 for a uniform batch; the tail cut);
  *                       1: the first gcamb_plan_launch times every
  *                       candidate on its inputs and keeps the fastest:
  *                       source-tile width (64, 128, 256 sources) x multipole
- *                       tiles per item (2 where the mode allows, 1) x tail
- *                       (the last 10% of the cost cut into items of a quarter
- *                       size, or no cut) x items per CTA (4; at width 128
- *                       also 8, shorter k chunks): up to 14 candidates.  If
+ *                       tiles per item (2 where the mode allows, 1) x work
+ *                       items (ending at multiples of 16 or 8 k nodes, or of
+ *                       equal cost, with the last 10% of the cost cut into
+ *                       items of a quarter size; or at multiples of 16
+ *                       without that cut): up to 20 candidates.  If
  *                       the environment variable GCAMB_TUNE_CACHE names a
  *                       file, choices are appended there (one JSON object
  *                       per line, keyed by device, grid and batch) and
@@ -415,7 +417,7 @@ int gcamb_los_cl_pair(const gcamb_grid *gx, const gcamb_grid *gy, const float *S
  */
 typedef struct gcamb_plan gcamb_plan;
 
-#define GCAMB_PLAN_INFO_N 12
+#define GCAMB_PLAN_INFO_N 13
 
 int gcamb_plan_create(gcamb_grid *g, int M, const int *lmax_m, const int *nk_m, int mode, int tune,
                       gcamb_plan **out);
@@ -447,9 +449,10 @@ int gcamb_plan_launch(gcamb_plan *p, const float *S, const double *Pk, double *C
  * read in place (fused kernel, no split pass: uniform batches only), [9]
  * multipole tiles per work item (2 when adjacent 128-multipole tiles share
  * each loaded and split source block; else 1), [10] work items of about
- * equal cost per persistent CTA (4 or 8: the k-chunk length), [11] the tail
- * of the work list, 100 x round(1000 x share) + pieces (10004: the last 10%
- * of the cost in items cut into 4 pieces; 1: no tail cut).
+ * equal cost per persistent CTA (used when [12] is 0), [11] the tail of the
+ * work list, 100 x round(1000 x share) + pieces (10004: the last 10% of the
+ * cost in items cut into 4 pieces; 1: no tail cut), [12] kalign: every work
+ * item ends at a multiple of kalign k nodes (0: items of equal cost).
  */
 int gcamb_plan_info(const gcamb_plan *p, int64_t *info);
 

@@ -1410,7 +1410,8 @@ struct TcPlan {
   int chain = 0;       // lp = 2: 1, chain records where an item's second tile is idle; 2, also l-tile 0 alone
   int nslots = 0;      // chunk slots (each lp tiles' partials)
   int tail = 0;        // the tail setting the items were cut with (as tail_key)
-  int per_cta = 4;     // items of about equal cost per persistent CTA
+  int per_cta = 4;     // items of about equal cost per persistent CTA (kalign 0)
+  int kalign = 0;      // items end at multiples of kalign k (0: at the cost target)
   std::vector<int> blob;
   size_t o_items = 0, o_tile_ptr = 0, o_tile_items = 0, o_perm = 0, o_nkm = 0, o_lmaxm = 0, o_tnk = 0;
   std::vector<double> cost;  // per item
@@ -1496,6 +1497,22 @@ void want_tail(double *frac, int *parts) {
   }
 }
 
+// k-aligned work items (GCAMB_TC_KALIGN=n, 0: items of equal cost instead):
+// by default 12 k for uniform batches and 16 for uneven and temperature +
+// E-mode plans (measured on the 256-source l_max = 2500 batch, F16X3:
+// 1.535 ms per step with items of equal cost, 1.502 / 1.501 / 1.508 / 1.544 /
+// 1.567 / 1.651 ms at 8 / 12 / 16 / 20 / 24 / 32 k; the 1000-source uneven
+// batch 16.39 ms against 15.97 / 15.67 / 15.54 / 15.82 / 15.75 ms at 8 / 12 /
+// 16 / 20 / 24 k; the TE batch 2.93 ms against 2.79 / 2.69 / 2.66 ms at 8 /
+// 12 / 16 k).
+int want_kalign(bool uniform, bool te = false) {
+  if (const char *e = getenv("GCAMB_TC_KALIGN")) {
+    const int v = atoi(e);
+    if (v >= 0 && v <= kKChunkMax) return v;
+  }
+  return uniform && !te ? 12 : 16;
+}
+
 int tail_key() {
   double f = 0.0;
   int n = 1;
@@ -1557,13 +1574,15 @@ int num_sms() {
 // Work-list settings a plan's autotuner chooses among (null: the defaults
 // and the environment's switches): lp 1 forces one l-tile per item (0: the
 // default, two where the mode allows); the tail (the share of the cost
-// handed out last and the pieces each of its items is cut into); per_cta,
-// the items of about equal cost per persistent CTA (the k-chunk length).
+// handed out last and the pieces each of its items is cut into); kalign,
+// items cut at multiples of kalign k, or (0) per_cta items of about equal
+// cost per persistent CTA.
 struct PlanCfg {
   int lp = 0;
   double tail_frac = 0.1;
   int tail_parts = 4;
   int per_cta = 4;
+  int kalign = 0;
 };
 
 // lmax_c / nk_c: per-source l_max and k-prefix length in the caller's order,
@@ -1637,6 +1656,11 @@ void plan_build(const gcamb_grid *g, int M, int mode, int nt, const int *lmax_c,
   const int sms = num_sms();
   pl.per_cta = cfg ? cfg->per_cta : 4;
   const double target = std::max(4.0, total / (sms * (double)pl.per_cta));
+  // k-aligned items: every item ends at a multiple of kalign (then the items
+  // of all l-tile pairs and source tiles that cover the same k run together
+  // and share the source blocks in L2), or, with kalign 0, at the cost target
+  const int kalign = cfg ? cfg->kalign : want_kalign(pl.uniform, te);
+  pl.kalign = kalign;
   std::vector<TcItem> items;
   pl.cost.clear();
   for (int lt : starts)
@@ -1661,7 +1685,7 @@ void plan_build(const gcamb_grid *g, int M, int mode, int nt, const int *lmax_c,
           c = 0.0;
         }
         c += kc;
-        if (c >= target || q - qb + 1 >= kKChunkMax) {
+        if ((kalign > 0 ? (q + 1) % kalign == 0 : c >= target) || q - qb + 1 >= kKChunkMax) {
           items.push_back({lt, mt, qb, q + 1, ntl, 0, chain_of(lt) ? 1 : 0, 0});
           pl.cost.push_back(c);
           qb = -1;
@@ -1838,7 +1862,7 @@ TcPlan *get_plan(const gcamb_grid *g, int M, int mode, int *rc) {
   for (auto &e : g_plans)
     if (e.first == g && !e.second->te && e.second->M == M && e.second->mode == mode && e.second->NT == nt &&
         e.second->fused == want_fused(g, mode, nt, true) && e.second->ksub == want_ksub() &&
-        e.second->tail == tail_key() &&
+        e.second->tail == tail_key() && e.second->kalign == want_kalign(true) &&
         e.second->chain == (e.second->lp == 2 ? want_chain() : 0) &&
         e.second->lp == (e.second->nkbs < 32768 ? want_lp(mode, nt, false) : 1))
       return e.second;
@@ -1992,7 +2016,8 @@ TcPlan *get_plan_te(const gcamb_grid *g, int M, int *rc) {
   std::lock_guard<std::mutex> lk(g_plan_mu);
   const int h = pick_h_te(M);
   for (auto &e : g_plans)
-    if (e.first == g && e.second->te && e.second->M == M && e.second->NT == h && e.second->ksub == want_ksub())
+    if (e.first == g && e.second->te && e.second->M == M && e.second->NT == h && e.second->ksub == want_ksub() &&
+        e.second->kalign == want_kalign(true, true))
       return e.second;
   TcPlan *pl = new TcPlan();
   plan_build(g, M, GCAMB_BF16X3, h, nullptr, nullptr, *pl, true);
@@ -2206,9 +2231,10 @@ void drop_plans(const gcamb_grid *g) {
 namespace gcamb {
 namespace {
 
-// The autotuner's candidates: source-tile width x l-tiles per item x tail x
-// items per CTA (the k-chunk length); at most kMaxCand.
-constexpr int kMaxCand = 16;
+// The autotuner's candidates: source-tile width x l-tiles per item x work
+// items (k-aligned at 16 or 8 k, or of equal cost, with the tail cut; and
+// k-aligned at 16 k without it); at most kMaxCand.
+constexpr int kMaxCand = 24;
 
 struct Cand {
   int nt;
@@ -2221,16 +2247,17 @@ std::vector<Cand> tune_candidates(int M, int mode) {
     if (nt > 128 && M <= 128) continue;  // one tile would hold the whole batch at 128
     for (int lp : {2, 1}) {
       if (lp == 2 && (nt > 128 || mode == GCAMB_TF32X3)) continue;
-      for (int tl = 0; tl < 2; ++tl)
-        for (int per : {4, 8}) {
-          if (per == 8 && nt != 128) continue;
-          Cand c{nt, PlanCfg()};
-          c.cfg.lp = lp;
-          c.cfg.tail_frac = tl ? 0.0 : 0.1;
-          c.cfg.tail_parts = tl ? 1 : 4;
-          c.cfg.per_cta = per;
-          out.push_back(c);
-        }
+      // (kalign, tail cut): 16, 8 and equal-cost items with the tail cut, 16 without
+      const int ka[4] = {16, 8, 0, 16};
+      for (int v = 0; v < 4; ++v) {
+        Cand c{nt, PlanCfg()};
+        c.cfg.lp = lp;
+        c.cfg.kalign = ka[v];
+        c.cfg.tail_frac = v == 3 ? 0.0 : 0.1;
+        c.cfg.tail_parts = v == 3 ? 1 : 4;
+        c.cfg.per_cta = 4;
+        out.push_back(c);
+      }
     }
   }
   return out;
@@ -2276,8 +2303,8 @@ std::string tune_cache_path() {
 }
 
 // One JSON object per line: {"key": "...", "nt": 128, "lp": 2, "tail_frac":
-// 0.1, "tail_parts": 4, "per_cta": 4, "ms": 1.234}; the last line with the
-// key wins.
+// 0.1, "tail_parts": 4, "per_cta": 4, "kalign": 16, "ms": 1.234}; the last
+// line with the key wins.
 bool tune_cache_lookup(const std::string &key, Cand *c) {
   const std::string path = tune_cache_path();
   if (path.empty()) return false;
@@ -2298,15 +2325,17 @@ bool tune_cache_lookup(const std::string &key, Cand *c) {
     if (k == std::string::npos) continue;
     const size_t b = k + 8, e = s.find('"', b);
     if (e == std::string::npos || s.substr(b, e - b) != key) continue;
-    double nt, lp, tf, tp, pc;
+    double nt, lp, tf, tp, pc, ka;
     if (num(s, "nt", &nt) && num(s, "lp", &lp) && num(s, "tail_frac", &tf) && num(s, "tail_parts", &tp) &&
-        num(s, "per_cta", &pc) && (nt == 64 || nt == 128 || nt == 256) && (lp == 1 || lp == 2) && tf >= 0 &&
-        tf <= 1 && tp >= 1 && tp <= 64 && pc >= 1 && pc <= 64) {
+        num(s, "per_cta", &pc) && num(s, "kalign", &ka) && (nt == 64 || nt == 128 || nt == 256) &&
+        (lp == 1 || lp == 2) && tf >= 0 && tf <= 1 && tp >= 1 && tp <= 64 && pc >= 1 && pc <= 64 && ka >= 0 &&
+        ka <= kKChunkMax) {
       c->nt = (int)nt;
       c->cfg.lp = (int)lp;
       c->cfg.tail_frac = tf;
       c->cfg.tail_parts = (int)tp;
       c->cfg.per_cta = (int)pc;
+      c->cfg.kalign = (int)ka;
       found = true;
     }
   }
@@ -2320,8 +2349,8 @@ void tune_cache_store(const std::string &key, const Cand &c, double ms) {
   FILE *f = fopen(path.c_str(), "a");
   if (!f) return;
   fprintf(f, "{\"key\": \"%s\", \"nt\": %d, \"lp\": %d, \"tail_frac\": %.3f, \"tail_parts\": %d, "
-          "\"per_cta\": %d, \"ms\": %.6f}\n",
-          key.c_str(), c.nt, c.cfg.lp, c.cfg.tail_frac, c.cfg.tail_parts, c.cfg.per_cta, ms);
+          "\"per_cta\": %d, \"kalign\": %d, \"ms\": %.6f}\n",
+          key.c_str(), c.nt, c.cfg.lp, c.cfg.tail_frac, c.cfg.tail_parts, c.cfg.per_cta, c.cfg.kalign, ms);
   fclose(f);
 }
 
@@ -2411,7 +2440,7 @@ int gcamb_plan_create(gcamb_grid *g, int M, const int *lmax_m, const int *nk_m, 
     h = fnv1a(h, nk_m, M * sizeof(int));
   }
   char kb[256];
-  snprintf(kb, sizeof kb, "v2|sm%d|%d|%d|%d|%d|%g|%d|%d|%016llx", num_sms(), g->nk, g->ntau, g->lmin, g->lmax,
+  snprintf(kb, sizeof kb, "v3|sm%d|%d|%d|%d|%d|%g|%d|%d|%016llx", num_sms(), g->nk, g->ntau, g->lmin, g->lmax,
            g->eps_cut, M, mode, (unsigned long long)h);
   p->key = kb;
   // candidates: the cached choice, every tuning candidate, or the heuristic
@@ -2476,6 +2505,7 @@ int gcamb_plan_info(const gcamb_plan *p, int64_t *info) {
   info[9] = c ? c->lp : 0;
   info[10] = c ? c->per_cta : 0;
   info[11] = c ? c->tail : 0;
+  info[12] = c ? c->kalign : 0;
   return GCAMB_OK;
 }
 

@@ -506,10 +506,10 @@ def plan_workspace(p: Plan) -> int:
 
 
 def plan_info(p: Plan) -> dict:
-    a = (ctypes.c_int64 * 12)()
+    a = (ctypes.c_int64 * 13)()
     _check(lib().gcamb_plan_info(p.handle, a))
     keys = ("tile", "items", "ctas", "captures", "replays", "tuned", "M", "workspace", "fused", "lp", "items_per_cta",
-            "tail")
+            "tail", "kalign")
     return dict(zip(keys, [int(v) for v in a]))
 
 

@@ -191,8 +191,11 @@ def test_k_sum_in_chunks_of_16_against_exact_sum_of_the_terms(monkeypatch, mode,
     is the FP64 sum of the FP32-rounded terms: the default must be within
     (15 + 1) * 2^-24 of it (the one extra 2^-24: the rounding of each term
     there, which the fused multiply-add of the chunk sum does not make).
-    GCAMB_TC_KSUB=64, the longest chunk, must be within 64 * 2^-24."""
+    GCAMB_TC_KSUB=64, the longest chunk, must be within 64 * 2^-24.  Items of
+    equal cost (GCAMB_TC_KALIGN=0), so that an item spans several chunks; the
+    default k-aligned items (12 k) hold one chunk each."""
     k, tau, S, P = case(nk, ntau, lmin, lmax, M)
+    monkeypatch.setenv("GCAMB_TC_KALIGN", "0")
     monkeypatch.setenv("GCAMB_TC_FUSED", fused)
     monkeypatch.setenv("GCAMB_TC_KSUB", "1")
     C1, g = run(k, tau, S, P, lmin, lmax, mode)

@@ -178,7 +178,7 @@ def test_graph_replay_and_tuning(tmp_path, monkeypatch):
     c2 = C.cpu().numpy()
     info = gcamb.plan_info(plan)
     assert info["tuned"] == 1 and info["tile"] in (64, 128, 256)
-    assert info["lp"] in (1, 2) and info["items_per_cta"] in (4, 8) and info["tail"] in (1, 10004)
+    assert info["lp"] in (1, 2) and info["kalign"] in (0, 8, 16) and info["tail"] in (1, 10004)
     assert info["captures"] == 1 and info["replays"] == 2
     assert np.array_equal(c1, c2)
     # the cache line records the whole choice (width, tiles per item, tail, items per CTA)
@@ -187,12 +187,13 @@ def test_graph_replay_and_tuning(tmp_path, monkeypatch):
     assert len(lines) == 1
     rec = lines[0]
     assert rec["nt"] == info["tile"] and rec["lp"] == info["lp"] and rec["per_cta"] == info["items_per_cta"]
+    assert rec["kalign"] == info["kalign"]
     assert round(rec["tail_frac"] * 1000) * 100 + rec["tail_parts"] == info["tail"]
     # the same batch again: the width comes from the cache, no timing
     plan2 = gcamb.plan_create(g, M, lm, nkm, gcamb.F16X3, tune=True)
     info2 = gcamb.plan_info(plan2)
     assert info2["tuned"] == 1 and info2["tile"] == info["tile"]
-    assert (info2["lp"], info2["items_per_cta"], info2["tail"]) == (info["lp"], info["items_per_cta"], info["tail"])
+    assert (info2["lp"], info2["kalign"], info2["tail"]) == (info["lp"], info["kalign"], info["tail"])
     c3 = gcamb.plan_launch(plan2, S, P).cpu().numpy()
     gcamb.sync()
     assert np.array_equal(c3, c1)
