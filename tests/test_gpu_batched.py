@@ -209,6 +209,26 @@ def test_k_sum_in_chunks_of_16_against_exact_sum_of_the_terms(monkeypatch, mode,
     assert not np.array_equal(C16, C64)  # the chunk length reaches the kernel
 
 
+@pytest.mark.parametrize("mode", [gcamb.F16X3, gcamb.BF16X3])
+def test_k_aligned_items_match_equal_cost_items(monkeypatch, mode):
+    """Work items cut at multiples of 12 k (the default for a uniform batch)
+    against items of equal cost (GCAMB_TC_KALIGN=0): every (k, l-tile)
+    product is the same MMA sequence and every k's term the same FP32 value;
+    only the chunks the epilogue sums in FP32 differ (at most 16 terms each,
+    within 15 * 2^-24), so the C_l agree within 2 * 16 * 2^-24."""
+    k, tau, S, P = case(300, 200, 2, 500, 200)
+    monkeypatch.setenv("GCAMB_TC_KALIGN", "0")
+    C0, g = run(k, tau, S, P, 2, 500, mode)
+    monkeypatch.delenv("GCAMB_TC_KALIGN", raising=False)
+    C12, _ = run(k, tau, S, P, 2, 500, mode, g)
+    monkeypatch.setenv("GCAMB_TC_KALIGN", "5")
+    C5, _ = run(k, tau, S, P, 2, 500, mode, g)
+    assert np.all(C0 > 0) and np.all(np.isfinite(C12)) and np.all(np.isfinite(C5))
+    assert (np.abs(C12 - C0) / C0).max() <= 2 * 16 * 2.0 ** -24
+    assert (np.abs(C5 - C0) / C0).max() <= 2 * 16 * 2.0 ** -24
+    assert not np.array_equal(C12, C0)  # the cut reaches the work list
+
+
 def test_identical_models_and_permutation():
     k, tau, S, P = case(64, 300, 2, 400, 5)
     Srep = np.repeat(S[:1], 70, axis=0)
