@@ -976,14 +976,14 @@ def main():
     shard.barrier()
     gcamb.sync()
     ms = e0.elapsed_time(e1)
-    if args.kernel_only:
-        gcamb.profile_enable(False)
-        print(json.dumps({"workload": WORKLOAD, "nk": wl.nk, "mode": args.mode, "steps": args.steps,
-                          "ms_per_step": ms / args.steps}), flush=True)
-        return
     kern = {gcamb.K_NAMES[i]: gcamb.profile_read(i) for i in (gcamb.K_SPLIT, gcamb.K_WEIGHTS, gcamb.K_TC,
                                                                gcamb.K_REDUCE)}
     gcamb.profile_enable(False)
+    if args.kernel_only:
+        print(json.dumps({"workload": WORKLOAD, "nk": wl.nk, "mode": args.mode, "steps": args.steps,
+                          "ms_per_step": ms / args.steps, "table_compressed": gcamb.table_compressed(g, mode),
+                          "kernel_ms": {k: (v[0] / max(1, v[1])) for k, v in kern.items()}}), flush=True)
+        return
     ms = shard.max_over_ranks(ms, dev)
     value = shard.job_rate(world, M, args.steps, ms)
     launches = sum(n for _, n in kern.values())
@@ -1120,6 +1120,7 @@ def main():
                    "l2": "inputs larger than L2 (sources 2.05 GB fp32, table %.2f GB)" % (gcamb.table_bytes(g, mode) / 1e9),
                    "table": "resident, built once per grid: %.2f ms (first build %.2f ms), not in the step" % (
                        table_ms, first_table_ms),
+                   "table_compressed": gcamb.table_compressed(g, mode),
                    "first_call_ms": first_call_ms, "max_rel_err_vs_oracle": err,
                    "max_rel_err_by_l": err_by_l,
                    "max_rel_err_sample": ("%d of %d sources, every l" % (min(args.cpu_models, M), M)

@@ -129,6 +129,19 @@ int gcamb_bessel_table(gcamb_grid *g, int mode, void *stream);
 int gcamb_table_bytes(const gcamb_grid *g, int mode, size_t *bytes);
 
 /*
+ * Whether the built table of `mode` lives in compressible device memory
+ * (host int*: 1 yes, 0 no).  The table kernels' output is the same either
+ * way; compression only changes how the memory system moves the table's
+ * zero-padded blocks (the rows of a 128-multipole tile beyond their own
+ * tau-prefix, Algorithm 1's window per multipole) between DRAM and L2.
+ * The library asks for it where the device supports generic compression;
+ * GCAMB_TABLE_COMPRESS=0 in the environment asks for plain cudaMalloc.
+ * Errors: GCAMB_EINVAL (NULL argument, unknown mode), GCAMB_ESTATE (table
+ * not built).
+ */
+int gcamb_table_compressed(const gcamb_grid *g, int mode, int *compressed);
+
+/*
  * Spherical Bessel functions by the table's device routine:
  *   x[n]              device double, x >= 0
  *   out[n][lmax+1]    device double, j_0..j_lmax at each x

@@ -375,7 +375,7 @@ int gcamb_grid_destroy(gcamb_grid *g) {
   if (!g) return GCAMB_OK;
   drop_plans(g);
   for (auto &t : g->tab) {
-    cudaFree(t.d_data);
+    table_free(t);
     cudaFree(t.d_nkb);
     cudaFree(t.d_off);
   }
@@ -420,6 +420,15 @@ int gcamb_grid_weights(const gcamb_grid *g, double *wtau, double *wk) {
   if (!g) return fail(GCAMB_EINVAL, "grid_weights: NULL grid");
   if (wtau) std::memcpy(wtau, g->wtau.data(), g->wtau.size() * sizeof(double));
   if (wk) std::memcpy(wk, g->wk.data(), g->wk.size() * sizeof(double));
+  return GCAMB_OK;
+}
+
+int gcamb_table_compressed(const gcamb_grid *g, int mode, int *compressed) {
+  if (!g || !compressed) return fail(GCAMB_EINVAL, "table_compressed: NULL argument");
+  if (!mode_layout(mode).kb) return fail(GCAMB_EINVAL, "table_compressed: unknown mode");
+  const Table &t = g->tab[mode];
+  if (!t.built) return fail(GCAMB_ESTATE, "table_compressed: build the table for this mode first");
+  *compressed = t.vmm ? 1 : 0;
   return GCAMB_OK;
 }
 

@@ -11,10 +11,12 @@
 //            j_0 for x < 1.  A first backward pass finds the scale, a second
 //            writes the scaled values, so no per-thread order buffer is kept.
 // Recurrence: j_{l-1} + j_{l+1} = (2l+1)/x j_l (both directions).
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include <cmath>
+#include <cstdlib>
 #include <mutex>
 #include <vector>
 
@@ -510,6 +512,138 @@ __global__ void sph_bessel_kernel(const double *__restrict__ x, int n, int lmax,
   bessel_orders(x[i], 0, lmax, xs, nxs, s);
 }
 
+// ------------------------------------------------------------------ table memory
+//
+// Each stored tau-block holds all 128 multipoles of its tile, but a tile's
+// upper multipoles have shorter tau-prefixes than its lowest, so the blocks
+// beyond them carry rows of zeros (and the 16-bit split formats flush the
+// tiny values of the evanescent region, x < l, to zero as well).  Generic
+// compression of device memory lets the memory system move such lines
+// between DRAM and L2 in compressed form; it is transparent to the kernels.
+// The driver's virtual-memory calls are looked up at run time (the library
+// links only the CUDA runtime).
+namespace {
+
+struct VmmApi {
+  CUresult (*attr)(int *, CUdevice_attribute, CUdevice) = nullptr;
+  CUresult (*gran)(size_t *, const CUmemAllocationProp *, CUmemAllocationGranularity_flags) = nullptr;
+  CUresult (*create)(CUmemGenericAllocationHandle *, size_t, const CUmemAllocationProp *, unsigned long long) = nullptr;
+  CUresult (*props)(CUmemAllocationProp *, CUmemGenericAllocationHandle) = nullptr;
+  CUresult (*reserve)(CUdeviceptr *, size_t, size_t, CUdeviceptr, unsigned long long) = nullptr;
+  CUresult (*map)(CUdeviceptr, size_t, size_t, CUmemGenericAllocationHandle, unsigned long long) = nullptr;
+  CUresult (*access)(CUdeviceptr, size_t, const CUmemAccessDesc *, size_t) = nullptr;
+  CUresult (*unmap)(CUdeviceptr, size_t) = nullptr;
+  CUresult (*addr_free)(CUdeviceptr, size_t) = nullptr;
+  CUresult (*release)(CUmemGenericAllocationHandle) = nullptr;
+  bool ok = false;
+};
+
+template <class F>
+bool driver_fn(const char *name, F &fn) {
+  void *f = nullptr;
+  cudaDriverEntryPointQueryResult q{};
+  if (cudaGetDriverEntryPointByVersion(name, &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !f) {
+    cudaGetLastError();
+    return false;
+  }
+  fn = reinterpret_cast<F>(f);
+  return true;
+}
+
+const VmmApi &vmm_api() {
+  static VmmApi a;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    a.ok = driver_fn("cuDeviceGetAttribute", a.attr) && driver_fn("cuMemGetAllocationGranularity", a.gran) &&
+           driver_fn("cuMemCreate", a.create) && driver_fn("cuMemGetAllocationPropertiesFromHandle", a.props) &&
+           driver_fn("cuMemAddressReserve", a.reserve) && driver_fn("cuMemMap", a.map) &&
+           driver_fn("cuMemSetAccess", a.access) && driver_fn("cuMemUnmap", a.unmap) &&
+           driver_fn("cuMemAddressFree", a.addr_free) && driver_fn("cuMemRelease", a.release);
+  });
+  return a;
+}
+
+// Compressible memory of `bytes` on the current device, or false (nothing held).
+bool vmm_compressed_alloc(Table &t, size_t bytes) {
+  const char *env = std::getenv("GCAMB_TABLE_COMPRESS");
+  if (env && env[0] == '0') return false;
+  const VmmApi &a = vmm_api();
+  if (!a.ok) return false;
+  int dev = 0, sup = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (a.attr(&sup, CU_DEVICE_ATTRIBUTE_GENERIC_COMPRESSION_SUPPORTED, (CUdevice)dev) != CUDA_SUCCESS || !sup)
+    return false;
+  CUmemAllocationProp prop{};
+  prop.type = CU_MEM_ALLOCATION_TYPE_PINNED;
+  prop.location.type = CU_MEM_LOCATION_TYPE_DEVICE;
+  prop.location.id = dev;
+  prop.allocFlags.compressionType = CU_MEM_ALLOCATION_COMP_GENERIC;
+  size_t gran = 0;
+  if (a.gran(&gran, &prop, CU_MEM_ALLOC_GRANULARITY_RECOMMENDED) != CUDA_SUCCESS || gran == 0) return false;
+  const size_t sz = (bytes + gran - 1) / gran * gran;
+  CUmemGenericAllocationHandle h = 0;
+  if (a.create(&h, sz, &prop, 0) != CUDA_SUCCESS) return false;
+  CUmemAllocationProp got{};
+  bool done = false;
+  CUdeviceptr ptr = 0;
+  // the driver may grant the memory without compression: then it is not kept
+  if (a.props(&got, h) == CUDA_SUCCESS && got.allocFlags.compressionType == CU_MEM_ALLOCATION_COMP_GENERIC &&
+      a.reserve(&ptr, sz, 0, 0, 0) == CUDA_SUCCESS) {
+    if (a.map(ptr, sz, 0, h, 0) == CUDA_SUCCESS) {
+      CUmemAccessDesc acc{};
+      acc.location = prop.location;
+      acc.flags = CU_MEM_ACCESS_FLAGS_PROT_READWRITE;
+      if (a.access(ptr, sz, &acc, 1) == CUDA_SUCCESS) done = true;
+      else a.unmap(ptr, sz);
+    }
+    if (!done) a.addr_free(ptr, sz);
+  }
+  if (!done) {
+    a.release(h);
+    return false;
+  }
+  t.d_data = reinterpret_cast<void *>(ptr);
+  t.vmm = (unsigned long long)h;
+  t.mapped = sz;
+  return true;
+}
+
+}  // namespace
+
+int table_alloc(Table &t, size_t bytes) {
+  t.vmm = 0;
+  t.mapped = 0;
+  if (vmm_compressed_alloc(t, bytes)) return GCAMB_OK;
+  cudaError_t e = cudaMalloc(&t.d_data, bytes);
+  if (e != cudaSuccess) {
+    t.d_data = nullptr;
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? fail(GCAMB_ENOMEM, "bessel_table: device allocation")
+                                          : cuda_fail(e, "bessel_table: cudaMalloc");
+  }
+  return GCAMB_OK;
+}
+
+void table_free(Table &t) {
+  if (t.vmm) {
+    const VmmApi &a = vmm_api();
+    cudaDeviceSynchronize();  // no kernel may still read the table (cudaFree waits the same way)
+    const CUdeviceptr ptr = reinterpret_cast<CUdeviceptr>(t.d_data);
+    a.unmap(ptr, t.mapped);
+    a.addr_free(ptr, t.mapped);
+    a.release((CUmemGenericAllocationHandle)t.vmm);
+  } else if (t.d_data) {
+    cudaFree(t.d_data);
+  }
+  t.d_data = nullptr;
+  t.vmm = 0;
+  t.mapped = 0;
+}
+
 int launch_bessel_table(gcamb_grid *g, int mode, cudaStream_t st) {
   Table &t = g->tab[mode];
   const ModeLayout lay = mode_layout(mode);
@@ -539,13 +673,8 @@ int launch_bessel_table(gcamb_grid *g, int mode, cudaStream_t st) {
       t.scale_exp = wmax > 0.0 ? 14 - e - (g->kernel ? 2 : 0) : 0;
     }
     t.bytes = (size_t)nb * lay.block_bytes();
+    if (int rc = table_alloc(t, std::max<size_t>(t.bytes, 256))) return rc;
     cudaError_t e;
-    if ((e = cudaMalloc(&t.d_data, std::max<size_t>(t.bytes, 256))) != cudaSuccess) {
-      t.d_data = nullptr;
-      cudaGetLastError();
-      return e == cudaErrorMemoryAllocation ? fail(GCAMB_ENOMEM, "bessel_table: device allocation")
-                                            : cuda_fail(e, "bessel_table: cudaMalloc");
-    }
     if ((e = cudaMalloc(&t.d_nkb, t.nkb.size() * sizeof(int32_t))) != cudaSuccess) return cuda_fail(e, "bessel_table");
     if ((e = cudaMalloc(&t.d_off, t.off.size() * sizeof(int64_t))) != cudaSuccess) return cuda_fail(e, "bessel_table");
     if ((e = cudaMemcpy(t.d_nkb, t.nkb.data(), t.nkb.size() * sizeof(int32_t), cudaMemcpyHostToDevice)) != cudaSuccess)

@@ -52,7 +52,17 @@ struct Table {
   int64_t *d_off = nullptr;
   size_t bytes = 0;
   int scale_exp = 0;          // F16X3: entries are w_i j_l 2^scale_exp
+  // d_data from the driver's virtual-memory API with generic compression
+  // (table_alloc): the allocation handle and the mapped size; 0 for cudaMalloc
+  unsigned long long vmm = 0;
+  size_t mapped = 0;
 };
+
+// Table memory: compressible device memory where the device grants it
+// (GCAMB_TABLE_COMPRESS=0 asks for cudaMalloc), else cudaMalloc.  table_free
+// waits for the device before it unmaps, as cudaFree does.
+int table_alloc(Table &t, size_t bytes);
+void table_free(Table &t);
 
 }  // namespace gcamb
 

@@ -280,8 +280,11 @@ __global__ void __launch_bounds__(TcRoles<FUSED, TE, LP>::kThreadsT, 1)
   int32_t *q_nb = reinterpret_cast<int32_t *>(q_off + LP * kKChunkMax);      // [LP][kKChunkMax]
   uint64_t *bars = reinterpret_cast<uint64_t *>(kslots + KS * C::kSlotBytes + C::kQBytes);
   // bars: full[S], empty[S], conv[S], kfull[KS], kempty[KS], tfull[TB],
-  //       tempty[TB], drain, (tmem slot), (abort); accumulator pair
-  //       buf * LP + tile sits at TMEM column (buf * LP + tile) * 2 NT
+  //       tempty[TB], drain, (tmem slot), (abort), src[S]; accumulator pair
+  //       buf * LP + tile sits at TMEM column (buf * LP + tile) * 2 NT.
+  // Fused kernels: a stage's source box (and TE's 1/x^2) completes on src,
+  // its table blocks on full, so that the converters split the sources while
+  // the table blocks are still landing; the MMA waits for conv and full.
   uint64_t *b1 = bars + 3 * S + 2 * KS;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(b1 + 2 * TB + 1);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(b1 + 2 * TB + 2);
@@ -289,6 +292,7 @@ __global__ void __launch_bounds__(TcRoles<FUSED, TE, LP>::kThreadsT, 1)
   const uint32_t kfull0 = smem_u32(bars + 3 * S), kempty0 = smem_u32(bars + 3 * S + KS);
   const uint32_t tfull0 = smem_u32(b1), tempty0 = smem_u32(b1 + TB);
   const uint32_t drain = smem_u32(b1 + 2 * TB);
+  const uint32_t src0 = smem_u32(b1 + 2 * TB + 3);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
@@ -296,6 +300,7 @@ __global__ void __launch_bounds__(TcRoles<FUSED, TE, LP>::kThreadsT, 1)
       mbar_init(full0 + 8 * s, 1);
       mbar_init(empty0 + 8 * s, 1);
       mbar_init(conv0 + 8 * s, R::kConv > 0 ? R::kConv : 1);
+      if (FUSED) mbar_init(src0 + 8 * s, 1);
     }
     for (int s = 0; s < KS; ++s) {
       mbar_init(kfull0 + 8 * s, 1);
@@ -415,17 +420,24 @@ __global__ void __launch_bounds__(TcRoles<FUSED, TE, LP>::kThreadsT, 1)
               const uint32_t sa = smem_u32(smem + stage * C::kStageBytes);
               armed_phase[stage] = (int)phase;
               if constexpr (LP == 2) {
-                // the tiles' blocks while each has some, then the source block
+                // the tiles' blocks while each has some, and the source block (fused: the
+                // source box first, on its own barrier, which the converters wait for alone)
                 const bool u0 = kb < nb0, u1 = kb < nb1;
-                mbar_expect_tx(full0 + 8 * stage, (u0 ? C::kABytes : 0) + (u1 ? C::kABytes : 0) + C::kBBytes);
+                const uint32_t tb = (u0 ? C::kABytes : 0) + (u1 ? C::kABytes : 0);
+                if constexpr (FUSED) {
+                  mbar_expect_tx(src0 + 8 * stage, C::kBBytes);
+                  tma_load_3d(sa + 2 * C::kABytes, &tm_src, kb * 32, q, it.mt * NT, src0 + 8 * stage);
+                  mbar_expect_tx(full0 + 8 * stage, tb);
+                } else {
+                  mbar_expect_tx(full0 + 8 * stage, tb + C::kBBytes);
+                }
                 if (u0) bulk_g2s(sa, a + (size_t)kb * C::kABytes, C::kABytes, full0 + 8 * stage);
                 if (u1)
                   bulk_g2s(sa + C::kABytes, p.table + ((size_t)q_off[kKChunkMax + j] + kb) * C::kABytes, C::kABytes,
                            full0 + 8 * stage);
-                if constexpr (FUSED)
-                  tma_load_3d(sa + 2 * C::kABytes, &tm_src, kb * 32, q, it.mt * NT, full0 + 8 * stage);
-                else  // split sources: evict first, so that L2 keeps the table blocks the other source
-                      // tiles' items read next (uneven 1000-source batch: 16.56 -> 16.35 ms per step)
+                if constexpr (!FUSED)  // split sources: evict first, so that L2 keeps the table blocks the other
+                                       // source tiles' items read next (uneven 1000-source batch: 16.56 -> 16.35 ms
+                                       // per step)
                   bulk_g2s_hint(sa + 2 * C::kABytes, b + (size_t)kb * C::kBBytes, C::kBBytes, full0 + 8 * stage,
                                 l2_policy_evict_first());
                 if (++stage == S) {
@@ -434,20 +446,27 @@ __global__ void __launch_bounds__(TcRoles<FUSED, TE, LP>::kThreadsT, 1)
                 }
                 continue;
               }
-              mbar_expect_tx(full0 + 8 * stage, C::kStageBytes + (TE == 1 ? 128 : 0));
+              constexpr uint32_t kTabBytes = (TE == 2 ? 2 : 1) * C::kABytes;
+              // fused: the source box (and TE's 1/x^2) on src, the table blocks on full
+              const uint32_t sbar = FUSED ? src0 + 8 * stage : full0 + 8 * stage;
+              if constexpr (FUSED) {
+                mbar_expect_tx(sbar, C::kBBytes + (TE == 1 ? 128 : 0));
+                mbar_expect_tx(full0 + 8 * stage, kTabBytes);
+              } else {
+                mbar_expect_tx(full0 + 8 * stage, C::kStageBytes);
+              }
               bulk_g2s(sa, a + (size_t)kb * C::kABytes, C::kABytes, full0 + 8 * stage);
               if constexpr (TE == 2)  // the second field's table block
                 bulk_g2s(sa + C::kABytes, p.table2 + (size_t)q_off[j] * C::kABytes + (size_t)kb * C::kABytes,
                          C::kABytes, full0 + 8 * stage);
               if constexpr (TE == 1)  // the block's 32 values of 1/x^2
-                bulk_g2s(smem_u32(fbuf + stage * 128), p.ix2 + ((size_t)q * p.nkbs + kb) * 32, 128, full0 + 8 * stage);
+                bulk_g2s(smem_u32(fbuf + stage * 128), p.ix2 + ((size_t)q * p.nkbs + kb) * 32, 128, sbar);
               constexpr int kBOff = (TE == 2 ? 2 : 1) * C::kABytes;  // the source region of the stage
               if constexpr (TE) {  // FP32 boxes [NT/2 models][1 k][32 tau] of the two fields
-                tma_load_3d(sa + kBOff, &tm_src, kb * 32, q, it.mt * (NT / 2), full0 + 8 * stage);
-                tma_load_3d(sa + kBOff + (NT / 2) * 128, &tm_src2, kb * 32, q, it.mt * (NT / 2),
-                            full0 + 8 * stage);
+                tma_load_3d(sa + kBOff, &tm_src, kb * 32, q, it.mt * (NT / 2), sbar);
+                tma_load_3d(sa + kBOff + (NT / 2) * 128, &tm_src2, kb * 32, q, it.mt * (NT / 2), sbar);
               } else if constexpr (FUSED)  // FP32 box [NT sources][1 k][32 tau]; zero beyond ntau and M
-                tma_load_3d(sa + kBOff, &tm_src, kb * 32, q, it.mt * NT, full0 + 8 * stage);
+                tma_load_3d(sa + kBOff, &tm_src, kb * 32, q, it.mt * NT, sbar);
               else
                 bulk_g2s(sa + kBOff, b + (size_t)kb * C::kBBytes, C::kBBytes, full0 + 8 * stage);
               if (++stage == S) {
@@ -468,7 +487,10 @@ __global__ void __launch_bounds__(TcRoles<FUSED, TE, LP>::kThreadsT, 1)
         }
         // no copy may still be landing when the CTA exits
         for (int s = 0; s < S; ++s)
-          if (armed_phase[s] >= 0) mbar_wait(full0 + 8 * s, (uint32_t)armed_phase[s], nullptr, p.err);
+          if (armed_phase[s] >= 0) {
+            mbar_wait(full0 + 8 * s, (uint32_t)armed_phase[s], nullptr, p.err);
+            if (FUSED) mbar_wait(src0 + 8 * s, (uint32_t)armed_phase[s], nullptr, p.err);
+          }
         for (int s = 0; s < KS; ++s)
           if (karmed[s] >= 0) mbar_wait(kfull0 + 8 * s, (uint32_t)karmed[s], nullptr, p.err);
       }
@@ -716,7 +738,7 @@ __global__ void __launch_bounds__(TcRoles<FUSED, TE, LP>::kThreadsT, 1)
           }
           bool ok = true;
           for (int kb = 0; kb < nb; ++kb) {
-            const bool w2 = mbar_wait(full0 + 8 * stage, phase, abort_flag, p.err);
+            const bool w2 = mbar_wait(src0 + 8 * stage, phase, abort_flag, p.err);  // the source box alone
             unsigned char *sb = smem + stage * C::kStageBytes + ((TE == 2 || LP == 2) ? 2 : 1) * C::kABytes;
             const float4 *raw = reinterpret_cast<const float4 *>(sb);
             float4 v[RJ];
@@ -873,7 +895,7 @@ __global__ void __launch_bounds__(TcRoles<FUSED, TE, LP>::kThreadsT, 1)
       // (LP = 2: warps 8 t .. 8 t + 7 of the epilogue serve tile t; on a
       // chain record tile 0's D_hh is the sum of three accumulators)
       constexpr int CW = C::kChunk;
-      constexpr int CWC = 2;  // chain records: TMEM load width (four accumulators per column)
+      constexpr int CWC = 2;  // chain records: TMEM load width (four accumulators, one wait per chunk)
       const int sp = warp & 3;  // a warp reads the TMEM lanes 32 (warp mod 4) .. + 31
       const int grp = (warp - R::kEpi0) >> 2;
       const int half = grp & 1, tile = grp >> 1;
@@ -914,25 +936,22 @@ __global__ void __launch_bounds__(TcRoles<FUSED, TE, LP>::kThreadsT, 1)
             const uint32_t ta0 = tmem + ((uint32_t)(sp * 32) << 16) + (uint32_t)(btc[0] * 2 * NT + col0);
             const uint32_t d1 = (uint32_t)((btc[1] - btc[0]) * 2 * NT);
             const bool u1 = nb0 > 1, u2 = nb0 > 2;
-            // D_hh = (h0 + h1) + h2, in two load rounds (register budget)
+            // D_hh = (h0 + h1) + h2: the four accumulators of CWC columns are loaded
+            // before one wait (4 CWC registers: the budget of the usual 2 CW)
 #pragma unroll
             for (int c = 0; c < C::kColsPerThread / CWC; ++c) {
               const uint32_t ta = ta0 + c * CWC;
-              float x[CWC], y[CWC];
-              tmem_ld<CWC>(ta, x);
-              tmem_ld<CWC>(ta + d1, y);
-              tmem_wait_ld();
-#pragma unroll
-              for (int j = 0; j < CWC; ++j) x[j] = u1 ? x[j] + y[j] : x[j];
-              tmem_ld<CWC>(ta + NT + d1, y);
-              tmem_wait_ld();
-#pragma unroll
-              for (int j = 0; j < CWC; ++j) x[j] = u2 ? x[j] + y[j] : x[j];
-              tmem_ld<CWC>(ta + NT, y);
+              float h0[CWC], h1[CWC], h2[CWC], dx[CWC];
+              tmem_ld<CWC>(ta, h0);
+              tmem_ld<CWC>(ta + d1, h1);
+              tmem_ld<CWC>(ta + NT + d1, h2);
+              tmem_ld<CWC>(ta + NT, dx);
               tmem_wait_ld();
 #pragma unroll
               for (int j = 0; j < CWC; ++j) {
-                const float t = wr[c * CWC + j] * (x[j] + y[j]);
+                float x = u1 ? h0[j] + h1[j] : h0[j];
+                x = u2 ? x + h2[j] : x;
+                const float t = wr[c * CWC + j] * (x + dx[j]);
                 acc[c * CWC + j] = fmaf(t, t, acc[c * CWC + j]);
               }
             }

@@ -53,6 +53,7 @@ def lib():
     L.gcamb_grid_weights.argtypes = [_vp, _dp, _dp]
     L.gcamb_bessel_table.argtypes = [_vp, ctypes.c_int, _vp]
     L.gcamb_table_bytes.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
+    L.gcamb_table_compressed.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
     L.gcamb_sph_bessel.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp]
     L.gcamb_los_transfer.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp]
     L.gcamb_cl.argtypes = [_vp, _vp, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp]
@@ -289,6 +290,13 @@ def table_bytes(g: Grid, mode: int) -> int:
     b = ctypes.c_size_t()
     _check(lib().gcamb_table_bytes(g.handle, int(mode), ctypes.byref(b)))
     return int(b.value)
+
+
+def table_compressed(g: Grid, mode: int) -> bool:
+    """True when the built table of `mode` lives in compressible device memory."""
+    c = ctypes.c_int()
+    _check(lib().gcamb_table_compressed(g.handle, int(mode), ctypes.byref(c)))
+    return bool(c.value)
 
 
 def sph_bessel(x, lmax: int, out=None, stream=None):

@@ -290,3 +290,29 @@ def test_batched_lmax2500_full_size_sampled(orc, mode):
                        P[sel].cpu().numpy(), want_delta=False)
     err = np.abs(C[sel] / Cr - 1)
     assert err.max() <= 1e-5, err.max()
+
+
+@pytest.mark.parametrize("mode", [gcamb.F16X3, gcamb.PLAIN64])
+def test_compressed_table_gives_the_same_bits(monkeypatch, mode):
+    """A table in compressible device memory (the library's default where the
+    device supports it) and one from cudaMalloc (GCAMB_TABLE_COMPRESS=0) give
+    bit-identical results: compression changes only how the memory system
+    moves the zero-padded blocks between DRAM and L2."""
+    k, tau, S, P = case(160, 1000, 2, 700, 64, seed=5)
+    out = {}
+    for env in ("1", "0"):
+        monkeypatch.setenv("GCAMB_TABLE_COMPRESS", env)
+        g = gcamb.grid_create(k, tau, 14000.0, 2, 700)
+        gcamb.bessel_table(g, mode)
+        comp = gcamb.table_compressed(g, mode)
+        if mode == gcamb.PLAIN64:
+            D = gcamb.los_transfer(g, torch.as_tensor(S.astype(np.float64), device="cuda"), mode)
+            C = gcamb.cl(g, D, torch.as_tensor(P, device="cuda"))
+        else:
+            C = gcamb.los_cl(g, torch.as_tensor(S, device="cuda"), torch.as_tensor(P, device="cuda"), mode)
+        gcamb.sync()
+        out[env] = (C.cpu().numpy(), comp)
+        gcamb.grid_destroy(g)
+    assert not out["0"][1], "GCAMB_TABLE_COMPRESS=0 must give a plain allocation"
+    print("table compressed by default: %s" % out["1"][1])
+    assert np.array_equal(out["1"][0], out["0"][0])
