@@ -56,6 +56,23 @@ def test_grid_create_rejects(L, bad):
     assert ei.value.code == gcamb.EINVAL
 
 
+def test_table_compressed_argument_errors(L):
+    """Host-side checks of gcamb_table_compressed: an unknown mode and a NULL
+    pointer are EINVAL, a table that was never built is ESTATE."""
+    wl = synth.workload("plain_lmax500")
+    g = gcamb.grid_create(wl.k, wl.tau, wl.tau0, wl.lmin, wl.lmax)
+    out = ctypes.c_int(-1)
+    assert L.gcamb_table_compressed(g.handle, 99, ctypes.byref(out)) == gcamb.EINVAL
+    assert L.gcamb_table_compressed(g.handle, gcamb.F16X3, None) == gcamb.EINVAL
+    assert L.gcamb_table_compressed(None, gcamb.F16X3, ctypes.byref(out)) == gcamb.EINVAL
+    assert L.gcamb_table_compressed(g.handle, gcamb.F16X3, ctypes.byref(out)) == gcamb.ESTATE
+    assert "build the table" in gcamb.last_error()
+    with pytest.raises(gcamb.GcambError) as ei:
+        gcamb.table_compressed(g, gcamb.PLAIN64)
+    assert ei.value.code == gcamb.ESTATE
+    gcamb.grid_destroy(g)
+
+
 def test_weights_match_trapezoid(L, orc):
     wl = synth.workload("plain_lmax500")
     g = gcamb.grid_create(wl.k, wl.tau, wl.tau0, wl.lmin, wl.lmax)
