@@ -329,7 +329,8 @@ int gcamb_los_cl_workspace(const gcamb_grid *g, int M, int mode, size_t *bytes);
  *   Pk[M][nk]        device double, >= 0 (a power spectrum; the epilogue
  *                    weights by sqrt(4 pi w_k P))
  *   Cl[M][nl]        device double
- *   ws, ws_bytes     device workspace of at least gcamb_los_cl_workspace bytes
+ *   ws, ws_bytes     device workspace of at least gcamb_los_cl_workspace bytes,
+ *                    16-byte aligned (GCAMB_EINVAL otherwise)
  * mode: GCAMB_BF16X3, GCAMB_F16X3 or GCAMB_TF32X3; requires
  * gcamb_bessel_table(g, mode).  For GCAMB_F16X3 the per-row scale is clamped
  * to 2^-40..2^80, so rows whose largest |S| is below ~1e-20 lose precision.
@@ -363,7 +364,7 @@ int gcamb_los_cl(const gcamb_grid *g, const float *S, const double *Pk, int M, i
  *   Pk[M][nk]             device double, >= 0
  *   ClTT, ClEE, ClTE[M][nl]  device double
  *   ws, ws_bytes          device workspace of at least
- *                         gcamb_los_cl_te_workspace bytes
+ *                         gcamb_los_cl_te_workspace bytes, 16-byte aligned
  * mode: GCAMB_BF16X3 (the only one); requires gcamb_bessel_table(g, mode).
  * Errors: GCAMB_EINVAL (mode, pointers, alignment, workspace, eps_cut too
  * large for the l = 2 limit), GCAMB_ESTATE (no table), GCAMB_EUNSUPPORTED
@@ -444,7 +445,8 @@ int gcamb_plan_workspace(const gcamb_plan *p, size_t *bytes);
 
 /*
  * Runs the plan: S[M][nk][ntau] device float (rows k >= nk_m[m] are
- * ignored), Pk[M][nk] device double (>= 0), Cl[M][nl] device double.
+ * ignored), Pk[M][nk] device double (>= 0), Cl[M][nl] device double, ws a
+ * 16-byte aligned device workspace of gcamb_plan_workspace bytes.
  * The first launch (and any launch whose pointers or stream differ from the
  * previous one) captures the split, contraction and reduction launches into a
  * CUDA graph; later launches replay it.  The first launch of a tuning plan

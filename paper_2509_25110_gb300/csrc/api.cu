@@ -542,6 +542,7 @@ int gcamb_los_cl(const gcamb_grid *g, const float *S, const double *Pk, int M, i
   if (!is_sm103()) return fail(GCAMB_EUNSUPPORTED, "los_cl: the tensor-core path needs an sm_103 device");
   size_t need = los_cl_workspace_bytes(g, M, mode);
   if (!ws || ws_bytes < need) return fail(GCAMB_EINVAL, "los_cl: workspace missing or too small");
+  if (reinterpret_cast<uintptr_t>(ws) % 16) return fail(GCAMB_EINVAL, "los_cl: workspace must be 16-byte aligned");
   return launch_los_cl(g, S, Pk, M, mode, Cl, ws, ws_bytes, (cudaStream_t)stream);
 }
 
@@ -578,6 +579,7 @@ int gcamb_los_cl_te(const gcamb_grid *g, const float *ST, const float *SP, const
   if (!ST || !SP || !Pk || !ClTT || !ClEE || !ClTE) return fail(GCAMB_EINVAL, "los_cl_te: NULL pointer");
   if (!is_sm103()) return fail(GCAMB_EUNSUPPORTED, "los_cl_te: the tensor-core path needs an sm_103 device");
   if (!ws) return fail(GCAMB_EINVAL, "los_cl_te: workspace missing");
+  if (reinterpret_cast<uintptr_t>(ws) % 16) return fail(GCAMB_EINVAL, "los_cl_te: workspace must be 16-byte aligned");
   return launch_los_cl_te(g, ST, SP, Pk, M, ClTT, ClEE, ClTE, ws, ws_bytes, (cudaStream_t)stream);
 }
 
@@ -593,6 +595,7 @@ int gcamb_los_cl_pair(const gcamb_grid *gx, const gcamb_grid *gy, const float *S
   if (M == 0) return GCAMB_OK;
   if (!SX || !SY || !Pk || !ClXX || !ClYY || !ClXY || !ws) return fail(GCAMB_EINVAL, "los_cl_pair: NULL pointer");
   if (!is_sm103()) return fail(GCAMB_EUNSUPPORTED, "los_cl_pair: the tensor-core path needs an sm_103 device");
+  if (reinterpret_cast<uintptr_t>(ws) % 16) return fail(GCAMB_EINVAL, "los_cl_pair: workspace must be 16-byte aligned");
   return launch_los_cl_pair(gx, gy, SX, SY, Pk, M, ClXX, ClYY, ClXY, ws, ws_bytes, (cudaStream_t)stream);
 }
 

@@ -1303,36 +1303,50 @@ struct PairSum {
   __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
+// The partial-slot indices of a tile, kReduceIdx at a time, staged in shared
+// memory by the block, so that each thread's partial loads wait on no index
+// load of their own.
+constexpr int kReduceIdx = 1024;
+
 // C[m][row] = sum over the tile's items (fixed order) of the FP32 chunk sums
 // (PairSum); zero above the source's own l_max.  row: output index, whose
-// multipole is lrow[row].
+// multipole is lrow[row].  A block takes one source of the tile (its 128
+// rows); each thread keeps 16 partial loads in flight.
 __global__ void __launch_bounds__(128) reduce_kernel(const float *__restrict__ partial, const int *__restrict__ tile_ptr,
                                                      const int *__restrict__ tile_items, int NT, int n_mt, int M,
                                                      int nl, const int *__restrict__ lrow,
                                                      const int *__restrict__ perm, const int *__restrict__ lmax_m,
                                                      double *__restrict__ Cl) {
+  __shared__ int idx[kReduceIdx];
   const int r = threadIdx.x;
   const int ml = blockIdx.x;       // source within the tile
   const int tile = blockIdx.y;     // lt * n_mt + mt
   const int lt = tile / n_mt, mt = tile - lt * n_mt;
   const int m = mt * NT + ml;
   const int row = lt * kTileL + r;
-  if (m >= M || row >= nl) return;
+  if (m >= M) return;  // the whole block
+  const bool live = row < nl && lrow[row] <= lmax_m[m];
+  const float *col = partial + (size_t)ml * 128 + r;
   PairSum acc;
-  if (lrow[row] <= lmax_m[m]) {
-    // sequential order; the loads of eight items are issued together
-    const int e1 = tile_ptr[tile + 1];
-    int e = tile_ptr[tile];
-    for (; e + 8 <= e1; e += 8) {
-      float v[8];
+  const int e0 = tile_ptr[tile], e1 = tile_ptr[tile + 1];
+  for (int c0 = e0; c0 < e1; c0 += kReduceIdx) {
+    const int n = min(kReduceIdx, e1 - c0);
+    __syncthreads();
+    for (int i = r; i < n; i += 128) idx[i] = tile_items[c0 + i];
+    __syncthreads();
+    if (!live) continue;
+    // sequential order; the loads of sixteen items are issued together
+    int i = 0;
+    for (; i + 16 <= n; i += 16) {
+      float v[16];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = partial[((size_t)tile_items[e + u] * NT + ml) * 128 + r];
+      for (int u = 0; u < 16; ++u) v[u] = col[(size_t)idx[i + u] * NT * 128];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) acc.add(v[u]);
+      for (int u = 0; u < 16; ++u) acc.add(v[u]);
     }
-    for (; e < e1; ++e) acc.add(partial[((size_t)tile_items[e] * NT + ml) * 128 + r]);
+    for (; i < n; ++i) acc.add(col[(size_t)idx[i] * NT * 128]);
   }
-  Cl[(size_t)perm[m] * nl + row] = acc.value();
+  if (row < nl) Cl[(size_t)perm[m] * nl + row] = acc.value();
 }
 
 // 1/x^2 of every node, x = k (tau0 - tau_i), in FP32 for the converters:
@@ -1393,21 +1407,52 @@ __global__ void __launch_bounds__(128) reduce_te_kernel(const float *__restrict_
                                                         int nl, const int *__restrict__ lrow, int scale_cl,
                                                         double *__restrict__ ClTT, double *__restrict__ ClEE,
                                                         double *__restrict__ ClTE) {
+  __shared__ int idx[kReduceIdx];
   const int r = threadIdx.x;
   const int ml = blockIdx.x;
   const int tile = blockIdx.y;
   const int lt = tile / n_mt, mt = tile - lt * n_mt;
   const int m = mt * H + ml;
   const int row = lt * kTileL + r;
-  if (m >= M || row >= nl) return;
-  const int l = lrow[row];
+  if (m >= M) return;  // the whole block
+  const bool live = row < nl;
+  const float *col = partial + (size_t)ml * 128 + r;
+  const size_t slot = (size_t)3 * H * 128;
   PairSum tt, ee, te;
-  for (int e = tile_ptr[tile]; e < tile_ptr[tile + 1]; ++e) {
-    const float *pp = partial + (size_t)tile_items[e] * 3 * H * 128 + (size_t)ml * 128 + r;
-    tt.add(pp[0]);
-    ee.add(pp[(size_t)H * 128]);
-    te.add(pp[(size_t)2 * H * 128]);
+  const int e0 = tile_ptr[tile], e1 = tile_ptr[tile + 1];
+  for (int c0 = e0; c0 < e1; c0 += kReduceIdx) {
+    const int n = min(kReduceIdx, e1 - c0);
+    __syncthreads();
+    for (int i = r; i < n; i += 128) idx[i] = tile_items[c0 + i];
+    __syncthreads();
+    if (!live) continue;
+    // sequential order; the loads of eight items (three sums each) are issued together
+    int i = 0;
+    for (; i + 8 <= n; i += 8) {
+      float a[8], b[8], c[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const float *pp = col + (size_t)idx[i + u] * slot;
+        a[u] = pp[0];
+        b[u] = pp[(size_t)H * 128];
+        c[u] = pp[(size_t)2 * H * 128];
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        tt.add(a[u]);
+        ee.add(b[u]);
+        te.add(c[u]);
+      }
+    }
+    for (; i < n; ++i) {
+      const float *pp = col + (size_t)idx[i] * slot;
+      tt.add(pp[0]);
+      ee.add(pp[(size_t)H * 128]);
+      te.add(pp[(size_t)2 * H * 128]);
+    }
   }
+  if (!live) return;
+  const int l = lrow[row];
   // E-mode (scale_cl): C^EE = c_l^2 sum, C^TE = c_l sum; pairs of kernel grids: none
   const double c2 = !scale_cl ? 1.0 : (l >= 2 ? (double)(l + 2) * (l + 1) * l * (l - 1) : 0.0);
   const size_t o = (size_t)m * nl + row;
