@@ -525,6 +525,7 @@ __global__ void sph_bessel_kernel(const double *__restrict__ x, int n, int lmax,
 namespace {
 
 struct VmmApi {
+  CUresult (*dev_get)(CUdevice *, int) = nullptr;
   CUresult (*attr)(int *, CUdevice_attribute, CUdevice) = nullptr;
   CUresult (*gran)(size_t *, const CUmemAllocationProp *, CUmemAllocationGranularity_flags) = nullptr;
   CUresult (*create)(CUmemGenericAllocationHandle *, size_t, const CUmemAllocationProp *, unsigned long long) = nullptr;
@@ -555,7 +556,8 @@ const VmmApi &vmm_api() {
   static VmmApi a;
   static std::once_flag once;
   std::call_once(once, [] {
-    a.ok = driver_fn("cuDeviceGetAttribute", a.attr) && driver_fn("cuMemGetAllocationGranularity", a.gran) &&
+    a.ok = driver_fn("cuDeviceGet", a.dev_get) && driver_fn("cuDeviceGetAttribute", a.attr) &&
+           driver_fn("cuMemGetAllocationGranularity", a.gran) &&
            driver_fn("cuMemCreate", a.create) && driver_fn("cuMemGetAllocationPropertiesFromHandle", a.props) &&
            driver_fn("cuMemAddressReserve", a.reserve) && driver_fn("cuMemMap", a.map) &&
            driver_fn("cuMemSetAccess", a.access) && driver_fn("cuMemUnmap", a.unmap) &&
@@ -575,7 +577,9 @@ bool vmm_compressed_alloc(Table &t, size_t bytes) {
     cudaGetLastError();
     return false;
   }
-  if (a.attr(&sup, CU_DEVICE_ATTRIBUTE_GENERIC_COMPRESSION_SUPPORTED, (CUdevice)dev) != CUDA_SUCCESS || !sup)
+  CUdevice cudev = 0;
+  if (a.dev_get(&cudev, dev) != CUDA_SUCCESS ||
+      a.attr(&sup, CU_DEVICE_ATTRIBUTE_GENERIC_COMPRESSION_SUPPORTED, cudev) != CUDA_SUCCESS || !sup)
     return false;
   CUmemAllocationProp prop{};
   prop.type = CU_MEM_ALLOCATION_TYPE_PINNED;

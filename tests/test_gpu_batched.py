@@ -292,7 +292,7 @@ def test_batched_lmax2500_full_size_sampled(orc, mode):
     assert err.max() <= 1e-5, err.max()
 
 
-@pytest.mark.parametrize("mode", [gcamb.F16X3, gcamb.PLAIN64])
+@pytest.mark.parametrize("mode", [gcamb.F16X3, gcamb.BF16X3, gcamb.TF32X3, gcamb.PLAIN64])
 def test_compressed_table_gives_the_same_bits(monkeypatch, mode):
     """A table in compressible device memory (the library's default where the
     device supports it) and one from cudaMalloc (GCAMB_TABLE_COMPRESS=0) give

@@ -199,3 +199,27 @@ def test_te_errors():
     assert gcamb.lib().gcamb_los_cl_te(g.handle, None, None, None, 0, gcamb.BF16X3, None, None, None, None, 0,
                                        None) == gcamb.OK
     gcamb.sync()
+
+
+def test_te_k_sum_in_chunks_against_every_term_reduce(monkeypatch):
+    """Eq. (1)'s k-sums of the TE kernel: FP32 sums of at most 16 k's terms
+    (the default) against GCAMB_TC_KSUB=1, where every k's term is its own
+    partial and the reduce forms the FP64 sum of the FP32-rounded terms.  The
+    TT and EE terms are positive, so each chunk sum is within 15 * 2^-24 of
+    their exact sum (one more 2^-24 for the rounding of each term there); the
+    TE terms change sign, and Cauchy-Schwarz bounds the sum of their moduli by
+    sqrt(TT EE), the scale the TE difference is held to.  With 2000 k nodes
+    the first multipole tile has about 2000 partials with KSUB=1, more than the
+    1024 indices the reduce stages in shared memory at a time."""
+    wl = workload(2, 300, 2000, 128, 40)
+    ST, SP, P = inputs(wl, seed=8)
+    monkeypatch.setenv("GCAMB_TC_KSUB", "1")
+    tt1, ee1, te1, _ = run_te(wl, ST, SP, P)
+    monkeypatch.delenv("GCAMB_TC_KSUB", raising=False)
+    tt, ee, te, _ = run_te(wl, ST, SP, P)
+    assert np.all(tt1 > 0) and np.all(ee1 > 0) and np.all(np.isfinite(te))
+    bound = 16 * 2.0 ** -24
+    assert (np.abs(tt - tt1) / tt1).max() <= bound
+    assert (np.abs(ee - ee1) / ee1).max() <= bound
+    assert (np.abs(te - te1) / np.sqrt(tt1 * ee1)).max() <= bound
+    assert not np.array_equal(tt, tt1)  # the chunk length reaches the kernel
