@@ -359,7 +359,8 @@ int gcamb_los_cl(const gcamb_grid *g, const float *S, const double *Pk, int M, i
  * The two sources of a model are adjacent operand rows of one product with
  * the shared bf16 hi/lo table (the table is read once for both); the
  * polarisation rows are scaled by 1/x^2 while they are split in shared
- * memory, and the row sums by c_l (EE: c_l^2) in the FP64 reduce.
+ * memory, and the row sums by c_l (EE: c_l^2) in the reduce, which adds
+ * the FP32 k-chunk sums as compensated pairs and reads them out in FP64.
  *   ST, SP[M][nk][ntau]   device float, 16-byte aligned, ntau % 4 == 0
  *   Pk[M][nk]             device double, >= 0
  *   ClTT, ClEE, ClTE[M][nl]  device double
