@@ -326,6 +326,35 @@ def run_uneven(args):
     ms, clocks = _timed_region(lambda: gcamb.plan_launch(plan, S, P, C, ws), steps, dev)
     gcamb.sync()
     info = gcamb.plan_info(plan)
+    # accuracy: the sources of the smallest, the median and the largest l_max
+    # against the oracle, each on its own k prefix and l_max (run on the
+    # FP32 sources the plan reads), max relative error per multipole range
+    acc = None
+    if not args.no_cpu_baseline:
+        import oracle
+        Ch = C.cpu().numpy()
+        order = np.argsort(lm, kind="stable")
+        sel = [int(order[0]), int(order[len(order) // 2]), int(order[-1])]
+        ranges = ((2, 30), (30, 500), (500, 1500), (1500, 2501), (2501, 6001))
+        worst = {}
+        per = []
+        t0 = time.perf_counter()
+        for m in sel:
+            q, L = int(nkm[m]), int(lm[m])
+            Sm = S[m, :q].double().cpu().numpy()
+            Pm = P[m, :q].cpu().numpy()
+            _, cr = oracle.los_cl(wl.k[:q], wl.tau, wl.tau0, wl.lmin, L, Sm[None], Pm[None], want_delta=False)
+            err = np.abs(Ch[m, :L - wl.lmin + 1] / cr[0] - 1)
+            ls = np.arange(wl.lmin, L + 1)
+            for a, b in ranges:
+                w = (ls >= a) & (ls < b)
+                if w.any():
+                    key = "[%d,%d]" % (a, b - 1)
+                    worst[key] = max(worst.get(key, 0.0), float(err[w].max()))
+            per.append({"source": m, "lmax": L, "nk": q, "max_rel_err": float(err.max()),
+                        "zero_above_lmax": bool(np.all(Ch[m, L - wl.lmin + 1:] == 0.0))})
+        acc = {"max_rel_err_vs_oracle": max(r["max_rel_err"] for r in per), "max_rel_err_by_l": worst,
+               "sources": per, "oracle_s": time.perf_counter() - t0, "oracle_threads": oracle.num_threads()}
     # whole-step roofline (the graph's three launches are not timed apart):
     # the table's active entries once (4 B hi+lo; tf32 8 B) and every
     # source's own k prefix once (FP32)
@@ -351,7 +380,7 @@ def run_uneven(args):
                        "sources_read_in_place": bool(info["fused"]),
                        "ctas": info["ctas"], "graph_captures": info["captures"], "graph_replays": info["replays"],
                        "table_build_s": table_s, "first_launch_s_incl_tuning": first_s,
-                       "table_gb": gcamb.table_bytes(g, mode) / 1e9},
+                       "table_gb": gcamb.table_bytes(g, mode) / 1e9, "accuracy": acc},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_source": peak_src,
                          "scope": scope, "algorithmic_bytes": alg},
