@@ -253,14 +253,16 @@ def test_uneven_lmax6000_full_size_sampled(orc):
 
 
 
-def test_uneven_high_multipoles_match_oracle(orc):
-    """Multipoles above 2500 on the tensor-core path: an uneven F16X3 batch
-    with l_max ~ U{2500..6000} on a coarse linear k grid to 0.5, each
-    source's k prefix scaled with its l_max by the uneven workload's law (so
+@pytest.mark.parametrize("mode", [gcamb.F16X3, gcamb.PLAIN32, gcamb.TF32X3, gcamb.BF16X3])
+def test_uneven_high_multipoles_match_oracle(orc, mode):
+    """Multipoles above 2500 in plans: an uneven batch (F16X3 on the tensor
+    cores, and the FP32 plan of the plain kernels) with l_max ~
+    U{2500..6000} on a coarse linear k grid to 0.5, each source's k prefix
+    scaled with its l_max by the uneven workload's law (so
     that k_max (tau0 - tau_0) exceeds l_max: every multipole of a source has
     support), checked against the oracle at 1e-5 on every l of the sources
     of the smallest, the median and the largest l_max and two more, each on
-    its own k prefix."""
+    its own k prefix (BF16X3: its coarse-grid bound 6 * 2^-16)."""
     nk, ntau, lmin, lmax, M = 400, 300, 2, 6000, 40
     k = synth.master_linear_k(nk, 0.5)
     tau = synth.uniform_grid(200.0, 14000.0, ntau)
@@ -271,12 +273,13 @@ def test_uneven_high_multipoles_match_oracle(orc):
     S = synth.sources(k, tau, p).astype(np.float32)
     P = synth.primordial(k, p)
     g = gcamb.grid_create(k, tau, 14000.0, lmin, lmax)
-    gcamb.bessel_table(g, gcamb.F16X3)
-    plan = gcamb.plan_create(g, M, lm, nkm, gcamb.F16X3)
+    gcamb.bessel_table(g, mode)
+    plan = gcamb.plan_create(g, M, lm, nkm, mode)
     C = gcamb.plan_launch(plan, torch.as_tensor(S, device="cuda"), torch.as_tensor(P, device="cuda"))
     gcamb.sync()
     C = C.cpu().numpy()
     order = np.argsort(lm, kind="stable")
     sel = sorted({int(order[0]), int(order[M // 2]), int(order[-1]), 5, 29})
     assert lm[order[-1]] > 5000
-    check_against_oracle(orc, k, tau, 14000.0, lmin, C, S, P, lm, nkm, sel)
+    check_against_oracle(orc, k, tau, 14000.0, lmin, C, S, P, lm, nkm, sel,
+                         tol=6 * 2.0 ** -16 if mode == gcamb.BF16X3 else TOL)
