@@ -98,3 +98,24 @@ def test_zero_sources_is_a_no_op():
     gcamb.los_cl(g, S0, P0, gcamb.BF16X3, Cl[:0])
     gcamb.sync()
     assert torch.all(Cl == -7.0)
+
+
+def test_misaligned_workspace_is_rejected():
+    """A workspace pointer that is not 16-byte aligned is refused with
+    GCAMB_EINVAL before any launch (bulk copies and vector loads read it);
+    the output keeps its sentinel, and an aligned workspace then works."""
+    k, tau, S, P = inputs(20, 64, 3)
+    g = gcamb.grid_create(k, tau, 14000.0, 2, 100)
+    gcamb.bessel_table(g, gcamb.F16X3)
+    need = gcamb.los_cl_workspace(g, 3, gcamb.F16X3)
+    buf = torch.empty(need + 64, dtype=torch.uint8, device="cuda")
+    Cl = torch.full((3, g.nl), -7.0, dtype=torch.float64, device="cuda")
+    St, Pt = torch.as_tensor(S, device="cuda"), torch.as_tensor(P, device="cuda")
+    with pytest.raises(gcamb.GcambError) as ei:
+        gcamb.los_cl(g, St, Pt, gcamb.F16X3, Cl, buf[4:4 + need])
+    assert ei.value.code == gcamb.EINVAL and "aligned" in gcamb.last_error()
+    gcamb.sync()
+    assert torch.all(Cl == -7.0)
+    gcamb.los_cl(g, St, Pt, gcamb.F16X3, Cl, buf[:need])
+    gcamb.sync()
+    assert torch.all(torch.isfinite(Cl)) and torch.all(Cl > 0)
