@@ -56,6 +56,25 @@ def test_grid_create_rejects(L, bad):
     assert ei.value.code == gcamb.EINVAL
 
 
+def test_plain_c_client(L, tmp_path):
+    """The header compiles as C99 with -pedantic and no warnings, and a plain
+    C program linked against libgcamb.so (no Python, no torch) runs the
+    host-side entry points as documented (tests/c_abi_host.c)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    exe = str(tmp_path / "c_abi_host")
+    libdir = os.path.dirname(gcamb.LIB_PATH)
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        os.path.join(ROOT, "tests", "c_abi_host.c"), "-L", libdir, "-lgcamb", "-lm",
+                        "-Wl,-rpath," + libdir, "-o", exe], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0 and out.stdout.strip() == "ok", out.stdout + out.stderr
+
+
 def test_table_compressed_argument_errors(L):
     """Host-side checks of gcamb_table_compressed: an unknown mode and a NULL
     pointer are EINVAL, a table that was never built is ESTATE."""
