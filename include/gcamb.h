@@ -344,7 +344,10 @@ int gcamb_los_cl_workspace(const gcamb_grid *g, int M, int mode, size_t *bytes);
  * GCAMB_TC_CHAIN=0|1|2 chain records (a tile's hi*hi tau-sum spread over three
  * TMEM accumulators): none, where an item's second l-tile is idle (default),
  * or also l-tile 0 in items of its own; GCAMB_TC_TAIL=frac:parts the share of
- * the cost handed out last whose items are cut into parts (default 0.1:4).
+ * the cost handed out last whose items are cut into parts (default 0.1:4);
+ * GCAMB_TC_KALIGN=n work items end at multiples of n k nodes (0: items of
+ * equal cost; default 12, or 6 where items of 12 k would give a CTA fewer
+ * than four; gcamb_los_cl_noalloc keeps 12).
  * Errors: GCAMB_EINVAL, GCAMB_ESTATE, GCAMB_EUNSUPPORTED (device is not
  * sm_103), GCAMB_ECUDA; GCAMB_ETIMEOUT is reported by gcamb_sync.
  */

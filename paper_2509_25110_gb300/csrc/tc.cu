@@ -1480,6 +1480,7 @@ struct TcPlan {
   int tail = 0;        // the tail setting the items were cut with (as tail_key)
   int per_cta = 4;     // items of about equal cost per persistent CTA (kalign 0)
   int kalign = 0;      // items end at multiples of kalign k (0: at the cost target)
+  int kalign_req = 0;  // the requested alignment (the plan cache's key; kalign may be half of it)
   std::vector<int> blob;
   size_t o_items = 0, o_tile_ptr = 0, o_tile_items = 0, o_perm = 0, o_nkm = 0, o_lmaxm = 0, o_tnk = 0;
   std::vector<double> cost;  // per item
@@ -1581,6 +1582,13 @@ int want_kalign(bool uniform, bool te = false) {
   return uniform && !te ? 12 : 16;
 }
 
+bool kalign_from_env() {
+  const char *e = getenv("GCAMB_TC_KALIGN");
+  if (!e) return false;
+  const int v = atoi(e);
+  return v >= 0 && v <= kKChunkMax;
+}
+
 int tail_key() {
   double f = 0.0;
   int n = 1;
@@ -1659,7 +1667,7 @@ struct PlanCfg {
 // te: a temperature + E-mode plan (uniform, fused bf16): nt models per tile,
 // each with a temperature and a polarisation operand row.
 void plan_build(const gcamb_grid *g, int M, int mode, int nt, const int *lmax_c, const int *nk_c, TcPlan &pl,
-                bool te = false, const PlanCfg *cfg = nullptr) {
+                bool te = false, const PlanCfg *cfg = nullptr, bool halve_if_few = false) {
   const ModeLayout lay = mode_layout(mode);
   const Table &t = g->tab[mode];
   pl.mode = mode;
@@ -1727,43 +1735,59 @@ void plan_build(const gcamb_grid *g, int M, int mode, int nt, const int *lmax_c,
   // k-aligned items: every item ends at a multiple of kalign (then the items
   // of all l-tile pairs and source tiles that cover the same k run together
   // and share the source blocks in L2), or, with kalign 0, at the cost target
-  const int kalign = cfg ? cfg->kalign : want_kalign(pl.uniform, te);
-  pl.kalign = kalign;
+  const int kalign_req = cfg ? cfg->kalign : want_kalign(pl.uniform, te);
+  pl.kalign_req = kalign_req;
   std::vector<TcItem> items;
-  pl.cost.clear();
-  for (int lt : starts)
-    for (int mt = 0; mt < pl.n_mt; ++mt) {
-      if (tile_lm[mt] < g->lrow[(size_t)lt * kTileL]) continue;
-      // an item spans at most kKChunkMax k and starts and ends at a k with
-      // stored blocks
-      const int ntl = ntl_of(lt, mt);
-      int qb = -1, qlast = -1;
-      double c = 0.0;
-      for (int q = 0; q < tile_nk[mt]; ++q) {
-        const double kc = kcost(q, lt, ntl);
-        if (kc == 0.0) continue;
-        if (qb >= 0 && q - qb + 1 > kKChunkMax) {
+  auto build_items = [&](int kalign) {
+    items.clear();
+    pl.cost.clear();
+    for (int lt : starts)
+      for (int mt = 0; mt < pl.n_mt; ++mt) {
+        if (tile_lm[mt] < g->lrow[(size_t)lt * kTileL]) continue;
+        // an item spans at most kKChunkMax k and starts and ends at a k with
+        // stored blocks
+        const int ntl = ntl_of(lt, mt);
+        int qb = -1, qlast = -1;
+        double c = 0.0;
+        for (int q = 0; q < tile_nk[mt]; ++q) {
+          const double kc = kcost(q, lt, ntl);
+          if (kc == 0.0) continue;
+          if (qb >= 0 && q - qb + 1 > kKChunkMax) {
+            items.push_back({lt, mt, qb, qlast + 1, ntl, 0, chain_of(lt) ? 1 : 0, 0});
+            pl.cost.push_back(c);
+            qb = -1;
+          }
+          qlast = q;
+          if (qb < 0) {
+            qb = q;
+            c = 0.0;
+          }
+          c += kc;
+          if ((kalign > 0 ? (q + 1) % kalign == 0 : c >= target) || q - qb + 1 >= kKChunkMax) {
+            items.push_back({lt, mt, qb, q + 1, ntl, 0, chain_of(lt) ? 1 : 0, 0});
+            pl.cost.push_back(c);
+            qb = -1;
+          }
+        }
+        if (qb >= 0) {
           items.push_back({lt, mt, qb, qlast + 1, ntl, 0, chain_of(lt) ? 1 : 0, 0});
           pl.cost.push_back(c);
-          qb = -1;
-        }
-        qlast = q;
-        if (qb < 0) {
-          qb = q;
-          c = 0.0;
-        }
-        c += kc;
-        if ((kalign > 0 ? (q + 1) % kalign == 0 : c >= target) || q - qb + 1 >= kKChunkMax) {
-          items.push_back({lt, mt, qb, q + 1, ntl, 0, chain_of(lt) ? 1 : 0, 0});
-          pl.cost.push_back(c);
-          qb = -1;
         }
       }
-      if (qb >= 0) {
-        items.push_back({lt, mt, qb, qlast + 1, ntl, 0, chain_of(lt) ? 1 : 0, 0});
-        pl.cost.push_back(c);
-      }
-    }
+  };
+  int kalign = kalign_req;
+  build_items(kalign);
+  // a uniform batch on one or two multipole tiles has few items per CTA, and
+  // the CTAs run out of work unevenly: items of half the k range (130 sampled
+  // multipoles, 256 sources: 310k -> 338k spectra/s at 6 k instead of 12).
+  // Not for the fixed buffer of the allocation-free entry point, which would
+  // hold twice the partials.
+  if (halve_if_few && !cfg && pl.uniform && !te && !kalign_from_env() && kalign >= 12 &&
+      (int)items.size() < 4 * sms) {
+    kalign /= 2;
+    build_items(kalign);
+  }
+  pl.kalign = kalign;
   pl.nitems = (int)items.size();
   // hand-out order: by k position (high k first), so that the CTAs working at
   // any moment share the source blocks of nearby k in L2; one persistent CTA
@@ -1930,12 +1954,12 @@ TcPlan *get_plan(const gcamb_grid *g, int M, int mode, int *rc) {
   for (auto &e : g_plans)
     if (e.first == g && !e.second->te && e.second->M == M && e.second->mode == mode && e.second->NT == nt &&
         e.second->fused == want_fused(g, mode, nt, true) && e.second->ksub == want_ksub() &&
-        e.second->tail == tail_key() && e.second->kalign == want_kalign(true) &&
+        e.second->tail == tail_key() && e.second->kalign_req == want_kalign(true) &&
         e.second->chain == (e.second->lp == 2 ? want_chain() : 0) &&
         e.second->lp == (e.second->nkbs < 32768 ? want_lp(mode, nt, false) : 1))
       return e.second;
   TcPlan *pl = new TcPlan();
-  plan_build(g, M, mode, nt, nullptr, nullptr, *pl);
+  plan_build(g, M, mode, nt, nullptr, nullptr, *pl, false, nullptr, true);
   if ((*rc = upload_blob(*pl)) != GCAMB_OK) {
     pl->release();
     delete pl;
@@ -2085,7 +2109,7 @@ TcPlan *get_plan_te(const gcamb_grid *g, int M, int *rc) {
   const int h = pick_h_te(M);
   for (auto &e : g_plans)
     if (e.first == g && e.second->te && e.second->M == M && e.second->NT == h && e.second->ksub == want_ksub() &&
-        e.second->kalign == want_kalign(true, true))
+        e.second->kalign_req == want_kalign(true, true))
       return e.second;
   TcPlan *pl = new TcPlan();
   plan_build(g, M, GCAMB_BF16X3, h, nullptr, nullptr, *pl, true);
@@ -2521,7 +2545,8 @@ int gcamb_plan_create(gcamb_grid *g, int M, const int *lmax_m, const int *nk_m, 
   else list.push_back(Cand{pick_nt(M), PlanCfg()});
   const bool defaults = !p->tune;  // heuristic plans keep the environment's switches (GCAMB_TC_LP, _TAIL)
   for (size_t c = 0; c < list.size() && (int)c < kMaxCand; ++c) {
-    plan_build(g, M, mode, list[c].nt, lmax_m, nk_m, p->cand[c], false, defaults ? nullptr : &list[c].cfg);
+    plan_build(g, M, mode, list[c].nt, lmax_m, nk_m, p->cand[c], false, defaults ? nullptr : &list[c].cfg,
+               defaults);  // a default plan cuts its items as gcamb_los_cl's does
     int rc = upload_blob(p->cand[c]);
     if (rc) {
       gcamb_plan_destroy(p);
