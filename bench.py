@@ -326,10 +326,11 @@ def run_uneven(args):
     ms, clocks = _timed_region(lambda: gcamb.plan_launch(plan, S, P, C, ws), steps, dev)
     gcamb.sync()
     info = gcamb.plan_info(plan)
-    # accuracy: the sources of the smallest, the median and the largest l_max
-    # against the oracle, each on its own k prefix and l_max (run on the
-    # FP32 sources the plan reads), max relative error per multipole range
-    acc = None
+    # the CPU baseline and the accuracy: the oracle on the sources of the
+    # smallest, the median and the largest l_max, each on its own k prefix
+    # and l_max (run on the FP32 sources the plan reads); max relative error
+    # per multipole range
+    acc = cpu = None
     if not args.no_cpu_baseline:
         import oracle
         Ch = C.cpu().numpy()
@@ -353,8 +354,13 @@ def run_uneven(args):
                     worst[key] = max(worst.get(key, 0.0), float(err[w].max()))
             per.append({"source": m, "lmax": L, "nk": q, "max_rel_err": float(err.max()),
                         "zero_above_lmax": bool(np.all(Ch[m, L - wl.lmin + 1:] == 0.0))})
+        dt = time.perf_counter() - t0
         acc = {"max_rel_err_vs_oracle": max(r["max_rel_err"] for r in per), "max_rel_err_by_l": worst,
-               "sources": per, "oracle_s": time.perf_counter() - t0, "oracle_threads": oracle.num_threads()}
+               "sources": per, "oracle_s": dt, "oracle_threads": oracle.num_threads()}
+        cpu = {"value": len(sel) / dt, "unit": "spectra/s", "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": "the sources of the smallest, the median and the largest l_max (%s), each on its own "
+                         "k prefix, 1000 tau, %.1f s; the same run checks their C_l"
+                         % (", ".join(str(r["lmax"]) for r in per), dt)}
     # whole-step roofline (the graph's three launches are not timed apart):
     # the table's active entries once (4 B hi+lo; tf32 8 B) and every
     # source's own k prefix once (FP32)
@@ -384,6 +390,7 @@ def run_uneven(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_source": peak_src,
                          "scope": scope, "algorithmic_bytes": alg},
+            "cpu_baseline": cpu,
             "clocks": clocks,
             "gpu_launches": (2 * info["items"] if mode == gcamb.PLAIN32 else 3) * steps}
     print(json.dumps(line), flush=True)
