@@ -119,3 +119,36 @@ def test_misaligned_workspace_is_rejected():
     gcamb.los_cl(g, St, Pt, gcamb.F16X3, Cl, buf[:need])
     gcamb.sync()
     assert torch.all(torch.isfinite(Cl)) and torch.all(Cl > 0)
+
+
+def test_side_stream_gives_the_same_bits():
+    """Every launch of the batched path goes on the caller's stream: the same
+    batch through gcamb_los_cl, a plan (graph) and the TE kernel on a
+    non-default stream (inputs made on the default stream, which the side
+    stream waits for) gives the default stream's results bit for bit, and
+    the side stream's completion alone makes them visible."""
+    k, tau, S, P = inputs(40, 128, 70)
+    g = gcamb.grid_create(k, tau, 14000.0, 2, 300)
+    gcamb.bessel_table(g, gcamb.F16X3)
+    gcamb.bessel_table(g, gcamb.BF16X3)
+    St, Pt = torch.as_tensor(S, device="cuda"), torch.as_tensor(P, device="cuda")
+    SPt = torch.as_tensor(0.5 * S[:, :, ::-1].copy(), device="cuda")
+    ref = gcamb.los_cl(g, St, Pt, gcamb.F16X3)
+    plan = gcamb.plan_create(g, 70, mode=gcamb.F16X3)
+    ref_p = gcamb.plan_launch(plan, St, Pt)
+    ref_te = gcamb.los_cl_te(g, St, SPt, Pt)
+    gcamb.sync()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        Cl = torch.full_like(ref, -1.0)
+        Cp = torch.full_like(ref, -1.0)
+        te = tuple(torch.full_like(ref, -1.0) for _ in range(3))
+        gcamb.los_cl(g, St, Pt, gcamb.F16X3, Cl, stream=side)
+        plan2 = gcamb.plan_create(g, 70, mode=gcamb.F16X3)
+        gcamb.plan_launch(plan2, St, Pt, Cp, stream=side)
+        gcamb.los_cl_te(g, St, SPt, Pt, out=te, stream=side)
+    side.synchronize()
+    assert torch.equal(Cl, ref) and torch.equal(Cp, ref_p) and torch.equal(Cp, ref)
+    for a, b in zip(te, ref_te):
+        assert torch.equal(a, b)
