@@ -152,3 +152,54 @@ def test_side_stream_gives_the_same_bits():
     assert torch.equal(Cl, ref) and torch.equal(Cp, ref_p) and torch.equal(Cp, ref)
     for a, b in zip(te, ref_te):
         assert torch.equal(a, b)
+
+
+def test_two_host_threads_share_the_library():
+    """Two host threads, each with its own grid and stream, call the library
+    at the same time (ctypes releases the interpreter lock around each call):
+    plan caches, tables and error text are per grid or per thread, so each
+    thread gets the C_l a single thread gets, bit for bit, and an error one
+    thread provokes is reported to that thread only."""
+    import threading
+    cases = [inputs(30, 96, 40, seed=11), inputs(36, 128, 90, seed=12)]
+    refs = []
+    for k, tau, S, P in cases:
+        g = gcamb.grid_create(k, tau, 14000.0, 2, 260)
+        gcamb.bessel_table(g, gcamb.F16X3)
+        refs.append(gcamb.los_cl(g, torch.as_tensor(S, device="cuda"), torch.as_tensor(P, device="cuda"),
+                                 gcamb.F16X3).cpu())
+        gcamb.sync()
+        gcamb.grid_destroy(g)
+    out, errs = [None, None], []
+
+    def work(i):
+        try:
+            k, tau, S, P = cases[i]
+            st = torch.cuda.Stream()
+            with torch.cuda.stream(st):
+                g = gcamb.grid_create(k, tau, 14000.0, 2, 260)
+                gcamb.bessel_table(g, gcamb.F16X3, stream=st)
+                St, Pt = torch.as_tensor(S, device="cuda"), torch.as_tensor(P, device="cuda")
+                st.synchronize()
+                for _ in range(5):
+                    C = gcamb.los_cl(g, St, Pt, gcamb.F16X3, stream=st)
+                    if i == 1:  # an argument error on this thread only
+                        with pytest.raises(gcamb.GcambError):
+                            gcamb.grid_create(k[::-1].copy(), tau, 14000.0, 2, 260)
+                        assert "increasing" in gcamb.last_error()
+                st.synchronize()
+                if i == 0:  # the other thread's errors do not reach this one
+                    assert "increasing" not in gcamb.last_error()
+                out[i] = C.cpu()
+                gcamb.grid_destroy(g)
+        except Exception as e:  # reported below, on the main thread
+            errs.append(repr(e))
+
+    ts = [threading.Thread(target=work, args=(i,)) for i in range(2)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    assert not errs, errs
+    for i in range(2):
+        assert torch.equal(out[i], refs[i])
