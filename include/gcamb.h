@@ -416,7 +416,8 @@ int gcamb_los_cl_pair(const gcamb_grid *gx, const gcamb_grid *gy, const float *S
  *                       chunks); the grid's table for this mode must be built.
  *   tune                0: source-tile width from a heuristic, the default
  *                       work-list settings (items ending at multiples of 16
- *                       k nodes, 12 for a uniform batch; the tail cut);
+ *                       k nodes; 12 for a uniform batch, 6 where that would
+ *                       give a CTA fewer than four items; the tail cut);
  *                       1: the first gcamb_plan_launch times every
  *                       candidate on its inputs and keeps the fastest:
  *                       source-tile width (64, 128, 256 sources) x multipole
@@ -432,6 +433,8 @@ int gcamb_los_cl_pair(const gcamb_grid *gx, const gcamb_grid *gy, const float *S
  * Sources are processed sorted by l_max (descending), so that at each (k,
  * l-tile) the sources that need it are a prefix of the source tiles; work
  * items are spread over one persistent CTA per SM, longest first.
+ * A plan refers to its grid and the grid's table: destroy the plan before
+ * the grid (a plan used after its grid is destroyed reads freed memory).
  */
 typedef struct gcamb_plan gcamb_plan;
 
