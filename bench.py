@@ -55,7 +55,8 @@ def parse_args():
     ap.add_argument("--nk", type=int, default=0,
                     help="profiling case: the same k range with this many nodes (default: the workload's 2000)")
     ap.add_argument("--workload", default="batched",
-                    choices=["batched", "uneven", "emulator", "te", "tensor", "features", "lsampled", "curved"],
+                    choices=["batched", "uneven", "emulator", "te", "tensor", "features", "lsampled", "curved",
+                             "plain"],
                     help="batched (the headline), uneven (1000 sources, l_max <= 6000, plan + graph), "
                          "emulator (train on 100k spectra, serve)")
     ap.add_argument("--sources", type=int, default=0,
@@ -393,6 +394,106 @@ def run_uneven(args):
             "cpu_baseline": cpu,
             "clocks": clocks,
             "gpu_launches": (2 * info["items"] if mode == gcamb.PLAIN32 else 3) * steps}
+    print(json.dumps(line), flush=True)
+
+
+def run_plain(args):
+    """The plain path on the two single-model grids: l_max = 500 (300 k log
+    1e-4..0.3, 400 tau) and the high-accuracy l_max = 5000 (3000 k log
+    1e-5..1, 2000 tau dense near tau*), one model a step: Eq. (2) on the CUDA
+    cores (gcamb_los_transfer) and Eq. (1) (gcamb_cl), FP64 and FP32.  The
+    oracle on the same model over the whole grid gives the accuracy and the
+    CPU baseline (l_max = 500 also at one thread)."""
+    import numpy as np
+    import torch
+
+    from paper_2509_25110_gb300 import build, gcamb, synth
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    build.build()
+    peaks, peak_src = load_peaks()
+    fp64_peak = gcamb.probe_flops(0)
+    grids = {}
+    for wname in ("plain_lmax500", "plain_lmax5000"):
+        wl = synth.workload(wname)
+        p = synth.model_params(1, seed=0)
+        S = synth.sources(wl.k, wl.tau, p)
+        P = synth.primordial(wl.k, p)
+        g = gcamb.grid_create(wl.k, wl.tau, wl.tau0, wl.lmin, wl.lmax)
+        info = gcamb.grid_info(g)
+        Pt = torch.as_tensor(P, device=dev)
+        res = {}
+        for name, mode, dt, eb in (("plain64", gcamb.PLAIN64, torch.float64, 8),
+                                   ("plain32", gcamb.PLAIN32, torch.float32, 4)):
+            gcamb.bessel_table(g, mode)
+            Sd = torch.as_tensor(S, dtype=dt, device=dev)
+            D = torch.empty((1, wl.nk, wl.nl), dtype=dt, device=dev)
+            C = torch.empty((1, wl.nl), dtype=torch.float64, device=dev)
+
+            def step():
+                gcamb.los_transfer(g, Sd, mode, D)
+                gcamb.cl(g, D, Pt, C)
+            for _ in range(max(3, args.warmup)):
+                step()
+            gcamb.sync()
+            steps = max(3, min(args.steps, 50))
+            gcamb.profile_enable(True)
+            ms, clocks = _timed_region(step, steps, dev)
+            gcamb.sync()
+            kms, kn = gcamb.profile_read(gcamb.K_LOS_PLAIN)
+            gcamb.profile_enable(False)
+            pms = kms / max(1, kn)
+            # one model streams the table: its active entries once (8 B FP64,
+            # 4 B FP32), the sources once and the transfer functions written
+            # once; 2 flop per active (l, k, tau)
+            alg = info["active"] * eb + wl.nk * wl.ntau * eb + wl.nk * wl.nl * eb
+            flops = 2.0 * info["active"]
+            res[name] = {"spectra_per_s": steps / (ms * 1e-3), "ms_per_step": ms / steps, "projection_ms": pms,
+                         "hbm_frac": alg / (pms * 1e-3) / 1e9 / peaks["hbm_gbs"], "algorithmic_bytes": alg,
+                         "clocks": clocks, "C": C.cpu().numpy()[0]}
+            if mode == gcamb.PLAIN64:
+                res[name]["fp64_frac"] = flops / (pms * 1e-3) / fp64_peak
+        grids[wname] = (wl, S, P, res, info)
+    # the oracle on the same model, whole grids
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        from oracle import build as ob
+        ob.build()
+        for wname, (wl, S, P, res, info) in grids.items():
+            t0 = time.perf_counter()
+            _, cr = oracle.los_cl(wl.k, wl.tau, wl.tau0, wl.lmin, wl.lmax, S, P, want_delta=False)
+            dt = time.perf_counter() - t0
+            cr = cr[0]
+            for name in res:
+                res[name]["max_rel_err_vs_oracle"] = float(np.max(np.abs(res[name]["C"] / cr - 1)))
+            res["oracle"] = {"seconds": dt, "cores": oracle.num_threads()}
+            if wname == "plain_lmax500":
+                t0 = time.perf_counter()
+                oracle.los_cl(wl.k, wl.tau, wl.tau0, wl.lmin, wl.lmax, S, P, want_delta=False, nthreads=1)
+                res["oracle_one_core"] = {"seconds": time.perf_counter() - t0, "cores": 1}
+        o = grids["plain_lmax5000"][3]["oracle"]
+        cpu = {"value": 1.0 / o["seconds"], "unit": "spectra/s", "cores": o["cores"], "kind": "oracle",
+               "sample": "the whole l_max = 5000 grid, one model, %.1f s (l_max = 500: %.2f s at %d threads, "
+                         "%.2f s at one)" % (o["seconds"], grids["plain_lmax500"][3]["oracle"]["seconds"],
+                                             o["cores"], grids["plain_lmax500"][3]["oracle_one_core"]["seconds"])}
+    for _, (_, _, _, res, _) in grids.items():
+        for name in ("plain64", "plain32"):
+            res[name].pop("C")
+    wl5, _, _, r5, info5 = grids["plain_lmax5000"]
+    main = r5["plain64"]
+    line = {"metric": "C_l spectra/sec, plain FP64 path, l_max=5000 high-accuracy grid (1 model)",
+            "value": main["spectra_per_s"], "unit": "spectra/s", "n_gpus": 1, "steps": max(3, min(args.steps, 50)),
+            "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "plain_lmax5000", "M": 1, "lmax": wl5.lmax, "nk": wl5.nk, "ntau": wl5.ntau,
+                       "active_entries": info5["active"],
+                       "lmax5000": r5, "lmax500": grids["plain_lmax500"][3]},
+            "roofline": {"bound": "fp64 alu", "achieved": 2.0 * info5["active"] / (main["projection_ms"] * 1e-3) / 1e12,
+                         "peak": fp64_peak / 1e12, "unit": "TFLOP/s", "frac": main["fp64_frac"], "traffic": None,
+                         "peak_source": "measured (gcamb_probe_flops, FP64 FMA)",
+                         "hbm_view": {"frac": main["hbm_frac"], "peak_gbs": peaks["hbm_gbs"], "peak_source": peak_src}},
+            "cpu_baseline": cpu, "clocks": main["clocks"], "gpu_launches": 2 * max(3, min(args.steps, 50))}
     print(json.dumps(line), flush=True)
 
 
@@ -918,6 +1019,9 @@ def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "plain":
+        run_plain(args)
         return
     if args.workload == "uneven":
         run_uneven(args)
