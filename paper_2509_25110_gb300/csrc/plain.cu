@@ -103,35 +103,61 @@ __global__ void __launch_bounds__(256) los_plain_kernel(const T *__restrict__ ta
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const T *chunk = table + (size_t)off[e_idx] * (kTileL * KB);
-  for (int r = warp; r < kTileL; r += 8) {
-    T acc[MC];
+  // A warp takes RV adjacent rows at a time, so that it holds V = MC RV = 8
+  // sums a lane and their cross-lane reduction costs 7 + 2 adds a lane for
+  // the 8 sums (5 a sum one at a time: on GB300's narrow FP64 pipe that was
+  // a third of the plain FP64 path's work for one source).
+  constexpr int RV = 8 / MC, V = MC * RV;
+  static_assert(kTileL % (8 * RV) == 0, "rows per warp pass");
+  for (int rb = warp * RV; rb < kTileL; rb += 8 * RV) {
+    T acc[V];  // acc[m * RV + i]: source m, row rb + i
 #pragma unroll
-    for (int m = 0; m < MC; ++m) acc[m] = T(0);
-    if (row0 + r < nl) {
-      int nbr = nb;  // blocks this row needs
-      if (xthr) {
-        const double xe = xthr[row0 + r], kq = kk[q];
-        nbr = 0;
-        for (int b0 = 0; b0 < nb; b0 += 32) {
-          const int b = b0 + lane;
-          nbr += __popc(__ballot_sync(0xffffffffu, b < nb && kq * (tau0 - tau[b * KB]) >= xe));
+    for (int j = 0; j < V; ++j) acc[j] = T(0);
+    int nbr[RV];  // blocks each row needs
+    int nbmax = 0;
+#pragma unroll
+    for (int i = 0; i < RV; ++i) {
+      nbr[i] = 0;
+      if (row0 + rb + i < nl) {
+        nbr[i] = nb;
+        if (xthr) {
+          const double xe = xthr[row0 + rb + i], kq = kk[q];
+          nbr[i] = 0;
+          for (int b0 = 0; b0 < nb; b0 += 32) {
+            const int b = b0 + lane;
+            nbr[i] += __popc(__ballot_sync(0xffffffffu, b < nb && kq * (tau0 - tau[b * KB]) >= xe));
+          }
         }
       }
-      const T *row = chunk + r * KB + lane;
-      for (int b = 0; b < nbr; ++b) {
-        const T ja = __ldg(row + (size_t)b * kTileL * KB);
-        const T jb = __ldg(row + (size_t)b * kTileL * KB + 32);
-        const int t = b * KB + lane;
+      nbmax = max(nbmax, nbr[i]);
+    }
+    const T *rows = chunk + rb * KB + lane;
+    for (int b = 0; b < nbmax; ++b) {
+      const int t = b * KB + lane;
+      T sa[MC], sb[MC];
+#pragma unroll
+      for (int m = 0; m < MC; ++m) {
+        sa[m] = s[m * ext + t];
+        sb[m] = s[m * ext + t + 32];
+      }
+#pragma unroll
+      for (int i = 0; i < RV; ++i) {
+        if (b >= nbr[i]) continue;  // the same for every lane
+        const T *row = rows + i * KB + (size_t)b * kTileL * KB;
+        const T ja = __ldg(row), jb = __ldg(row + 32);
 #pragma unroll
         for (int m = 0; m < MC; ++m) {
-          acc[m] = fma(ja, s[m * ext + t], acc[m]);
-          acc[m] = fma(jb, s[m * ext + t + 32], acc[m]);
+          acc[m * RV + i] = fma(ja, sa[m], acc[m * RV + i]);
+          acc[m * RV + i] = fma(jb, sb[m], acc[m * RV + i]);
         }
       }
     }
-    constexpr int LV = MC == 1 ? 0 : (MC == 2 ? 1 : (MC == 4 ? 2 : 3));
-    const T v = reduce_lanes<T, MC>(acc, lane);
-    if ((lane & ((32 >> LV) - 1)) == 0) res[lane >> (5 - LV)][r] = v;
+    // lane L holds the total of sum L >> 2
+    const T v = reduce_lanes<T, V>(acc, lane);
+    if ((lane & 3) == 0) {
+      const int j = lane >> 2;
+      res[j / RV][rb + j % RV] = v;
+    }
   }
   __syncthreads();
   for (int idx = threadIdx.x; idx < MC * kTileL; idx += blockDim.x) {
